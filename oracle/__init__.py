@@ -1,0 +1,299 @@
+"""CPU oracle for the disentangled 4D Gaussian frame renderer.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path
+(the CUDA library and its binding) never imports, links or executes it, and it
+imports nothing from the product package.
+
+``oracle.c`` holds the arithmetic (FP64 renderer, FP32 binning mirror, FP64
+adjoint); this module only marshals numpy arrays into it.  Scenes and cameras
+are the containers from :mod:`synth` (float32 arrays); the FP64 functions
+widen them exactly to double.
+
+Parity status of each function (see the pin tests in ``tests/test_oracle_*``):
+  preprocess        pinned (closed-form single Gaussian, SH vs scipy, quaternion
+                    vs scipy Rotation, Jacobian vs finite differences, conic vs
+                    numpy inverse, slicing-first equivalence)
+  render            pinned (closed-form footprint, two-Gaussian Eq. 4, static
+                    reduction, time-shift equivalence, monotone transmittance)
+  bin_f32           pinned (agrees with the FP64 preprocess; rectangle covers
+                    every pixel with alpha >= 1/255)
+  backward          pinned (central finite differences of ``render``)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "oracle.c"
+_LIB_PATH = _HERE / "_build" / "liboracle.so"
+_lib = None
+
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_float_p = ctypes.POINTER(ctypes.c_float)
+c_int32_p = ctypes.POINTER(ctypes.c_int32)
+c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
+
+
+def build(force: bool = False) -> Path:
+    """Compile oracle.c into a shared library (gcc, OpenMP, no FP contraction)."""
+    _LIB_PATH.parent.mkdir(parents=True, exist_ok=True)
+    if not force and _LIB_PATH.exists() and _LIB_PATH.stat().st_mtime >= _SRC.stat().st_mtime:
+        return _LIB_PATH
+    tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp.so")
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-std=c11", str(_SRC), "-o", str(tmp), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)] + [
+        (k, c_double_p) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
+                                  "quats", "opacity_logit", "sh", "cov3d")]
+
+
+class _SceneF32(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)] + [
+        (k, c_float_p) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
+                                 "quats", "opacity_logit")]
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("T", ctypes.c_double * 3), ("fx", ctypes.c_double),
+                ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class _CameraF32(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("T", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class _G2D(ctypes.Structure):
+    _fields_ = [("drawn", c_int32_p)] + [(k, c_double_p) for k in (
+        "u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max")]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(str(build()))
+        _lib.orc_num_threads.restype = ctypes.c_int
+        _lib.orc_preprocess.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
+                                        ctypes.c_int, ctypes.POINTER(_G2D)]
+        _lib.orc_render_pixels.argtypes = [ctypes.POINTER(_G2D), ctypes.c_int, ctypes.POINTER(_Camera),
+                                           c_double_p, ctypes.c_int64, c_int32_p, c_int32_p, ctypes.c_double,
+                                           c_double_p, c_double_p, c_int32_p, c_double_p]
+        _lib.orc_bin_f32.argtypes = [ctypes.POINTER(_SceneF32), ctypes.POINTER(_CameraF32), ctypes.c_float,
+                                     ctypes.c_int32, c_uint32_p, c_int32_p, c_int32_p, c_uint32_p, c_int32_p,
+                                     c_float_p]
+        _lib.orc_emit_keys.restype = ctypes.c_int64
+        _lib.orc_emit_keys.argtypes = [ctypes.c_int32, c_uint32_p, c_int32_p, c_uint32_p, ctypes.c_int32,
+                                       ctypes.c_int64, c_uint32_p, c_uint32_p, c_uint32_p]
+        _lib.orc_sh_basis.argtypes = [c_double_p, ctypes.c_int, c_double_p]
+        _lib.orc_quat_to_rot.argtypes = [c_double_p, c_double_p]
+        if hasattr(_lib, "orc_backward"):
+            _lib.orc_backward.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
+                                          c_double_p, c_double_p, ctypes.POINTER(_Scene)]
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None else None
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _Keep:
+    """Holds the arrays a ctypes struct points into."""
+
+    def __init__(self):
+        self.refs = []
+
+    def d(self, a):
+        if a is None:
+            return None
+        a = _d(a)
+        self.refs.append(a)
+        return _p(a, ctypes.c_double)
+
+
+def _scene64(scene, keep: _Keep, cov3d=None):
+    s = _Scene()
+    s.n = scene.n
+    s.sh_degree = scene.sh_degree
+    for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh"):
+        setattr(s, k, keep.d(getattr(scene, k)))
+    s.cov3d = keep.d(cov3d)
+    return s
+
+
+def _camera64(cam):
+    c = _Camera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float64).reshape(9)]
+    c.T[:] = [float(x) for x in np.asarray(cam.T, np.float64).reshape(3)]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def sh_basis(d, degree: int = 3) -> np.ndarray:
+    d = _d(d)
+    out = np.zeros(16)
+    lib().orc_sh_basis(_p(d, ctypes.c_double), degree, _p(out, ctypes.c_double))
+    return out[: (degree + 1) ** 2]
+
+
+def quat_to_rot(q) -> np.ndarray:
+    q = _d(q)
+    R = np.zeros(9)
+    lib().orc_quat_to_rot(_p(q, ctypes.c_double), _p(R, ctypes.c_double))
+    return R.reshape(3, 3)
+
+
+def preprocess(scene, cam, t: float, temporal_cull: bool = True, cov3d=None) -> dict:
+    """FP64 dynamic 2D Gaussians at time t (dict of numpy arrays, length N)."""
+    n = scene.n
+    keep = _Keep()
+    s = _scene64(scene, keep, cov3d)
+    c = _camera64(cam)
+    out = dict(drawn=np.zeros(n, np.int32), u=np.zeros(n), v=np.zeros(n), depth=np.zeros(n),
+               conic=np.zeros((n, 3)), cov2d=np.zeros((n, 3)), opacity_t=np.zeros(n),
+               rgb=np.zeros((n, 3)), lambda_max=np.zeros(n))
+    g = _G2D(_p(out["drawn"], ctypes.c_int32), *[_p(out[k], ctypes.c_double) for k in (
+        "u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max")])
+    lib().orc_preprocess(ctypes.byref(s), ctypes.byref(c), float(t), int(temporal_cull), ctypes.byref(g))
+    out["drawn"] = out["drawn"].astype(bool)
+    return out
+
+
+def default_eps_px(cam) -> float:
+    """Absolute FP32 error budget (pixels) of a projected mean: 2^-20 max(W, H)."""
+    return float(2.0 ** -20 * max(cam.width, cam.height))
+
+
+def render_g2d(g: dict, cam, pixels=None, bg=(0.0, 0.0, 0.0), eps_px=None) -> dict:
+    """Per-pixel brute-force compositing of precomputed FP64 2D Gaussians.
+
+    ``pixels`` is None (whole image, row-major) or an (M, 2) int array of (x, y).
+    Returns rgb (H,W,3) or (M,3), T, ncontrib and slack (see oracle.c)."""
+    n = len(g["u"])
+    fields = ("u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max")
+    gg = {k: _d(g[k]) for k in fields}
+    drawn = np.ascontiguousarray(g["drawn"], dtype=np.int32)
+    s = _G2D(_p(drawn, ctypes.c_int32), *[_p(gg[k], ctypes.c_double) for k in fields])
+    keep = [drawn] + list(gg.values())
+    c = _camera64(cam)
+    if pixels is None:
+        m = cam.width * cam.height
+        px = py = None
+        shape = (cam.height, cam.width)
+    else:
+        pixels = np.asarray(pixels, np.int32).reshape(-1, 2)
+        m = pixels.shape[0]
+        px = np.ascontiguousarray(pixels[:, 0])
+        py = np.ascontiguousarray(pixels[:, 1])
+        shape = (m,)
+    rgb = np.zeros(shape + (3,))
+    T = np.zeros(shape)
+    nc = np.zeros(shape, np.int32)
+    slack = np.zeros(shape)
+    bgv = _d(np.asarray(bg, np.float64))
+    eps = default_eps_px(cam) if eps_px is None else float(eps_px)
+    lib().orc_render_pixels(ctypes.byref(s), n, ctypes.byref(c), _p(bgv, ctypes.c_double), m,
+                            _p(px, ctypes.c_int32), _p(py, ctypes.c_int32), eps,
+                            _p(rgb, ctypes.c_double), _p(T, ctypes.c_double), _p(nc, ctypes.c_int32),
+                            _p(slack, ctypes.c_double))
+    del keep
+    return dict(rgb=rgb, T=T, ncontrib=nc, slack=slack)
+
+
+def render(scene, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0), temporal_cull: bool = True,
+           cov3d=None, eps_px=None) -> dict:
+    """Render one frame (or the listed pixels) of ``scene`` at time ``t`` in FP64."""
+    g = preprocess(scene, cam, t, temporal_cull=temporal_cull, cov3d=cov3d)
+    out = render_g2d(g, cam, pixels=pixels, bg=bg, eps_px=eps_px)
+    out["g2d"] = g
+    return out
+
+
+def bin_f32(scene, cam, t: float, tile: int) -> dict:
+    """FP32 binning mirror: depth key bits, radius, rect, tile count, flags, uv."""
+    n = scene.n
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    arrs = {k: f(getattr(scene, k)) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
+                                               "quats", "opacity_logit")}
+    s = _SceneF32(n, scene.sh_degree, *[_p(arrs[k], ctypes.c_float) for k in (
+        "means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit")])
+    c = _CameraF32()
+    c.R[:] = [float(x) for x in f(cam.R).reshape(9)]
+    c.T[:] = [float(x) for x in f(cam.T).reshape(3)]
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.width, c.height = int(cam.width), int(cam.height)
+    out = dict(depth_key=np.zeros(n, np.uint32), radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
+               tiles_touched=np.zeros(n, np.uint32), flags=np.zeros(n, np.int32), uv=np.zeros((n, 2), np.float32))
+    lib().orc_bin_f32(ctypes.byref(s), ctypes.byref(c), ctypes.c_float(t), int(tile),
+                      _p(out["depth_key"], ctypes.c_uint32), _p(out["radius"], ctypes.c_int32),
+                      _p(out["rect"], ctypes.c_int32), _p(out["tiles_touched"], ctypes.c_uint32),
+                      _p(out["flags"], ctypes.c_int32), _p(out["uv"], ctypes.c_float))
+    out["tiles_x"] = (cam.width + tile - 1) // tile
+    out["tiles_y"] = (cam.height + tile - 1) // tile
+    return out
+
+
+def tile_list(b: dict) -> dict:
+    """Sorted (tile, depth_bits, id) list of an ``bin_f32`` result (sort by tile,
+    then depth bits, then id), plus per-tile [start, end) ranges."""
+    n = len(b["depth_key"])
+    total = int(b["tiles_touched"].astype(np.int64).sum())
+    tile = np.zeros(total, np.uint32)
+    depth = np.zeros(total, np.uint32)
+    ids = np.zeros(total, np.uint32)
+    k = lib().orc_emit_keys(n, _p(b["depth_key"], ctypes.c_uint32), _p(np.ascontiguousarray(b["rect"]), ctypes.c_int32),
+                            _p(b["tiles_touched"], ctypes.c_uint32), int(b["tiles_x"]), total,
+                            _p(tile, ctypes.c_uint32), _p(depth, ctypes.c_uint32), _p(ids, ctypes.c_uint32))
+    assert k == total
+    order = np.lexsort((ids, depth, tile))
+    tile, depth, ids = tile[order], depth[order], ids[order]
+    ntiles = int(b["tiles_x"] * b["tiles_y"])
+    starts = np.searchsorted(tile, np.arange(ntiles), side="left")
+    ends = np.searchsorted(tile, np.arange(ntiles), side="right")
+    return dict(tile=tile, depth=depth, id=ids, ranges=np.stack([starts, ends], axis=1).astype(np.uint32))
+
+
+def backward(scene, cam, t: float, dl_drgb, bg=(0.0, 0.0, 0.0)) -> dict:
+    """FP64 adjoint: gradients of sum(dl_drgb * image) w.r.t. every raw parameter."""
+    keep = _Keep()
+    s = _scene64(scene, keep)
+    c = _camera64(cam)
+    grads = {k: np.zeros(np.asarray(getattr(scene, k)).shape) for k in (
+        "means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh")}
+    gs = _Scene()
+    gs.n, gs.sh_degree = scene.n, scene.sh_degree
+    for k, v in grads.items():
+        setattr(gs, k, _p(v, ctypes.c_double))
+    gs.cov3d = None
+    dl = _d(dl_drgb)
+    bgv = _d(np.asarray(bg, np.float64))
+    lib().orc_backward(ctypes.byref(s), ctypes.byref(c), float(t), _p(dl, ctypes.c_double),
+                       _p(bgv, ctypes.c_double), ctypes.byref(gs))
+    return grads
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

@@ -1,0 +1,546 @@
+/*
+ * oracle.c -- plain, slow CPU reference for rendering one frame of a
+ * disentangled 4D Gaussian scene at time t (Disentangled 4D Gaussian
+ * Splatting, arXiv 2503.22159).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code with the CUDA path.
+ *
+ * Contents
+ *   orc_preprocess      FP64: activations, deferred temporal slice, camera
+ *                       transform, projection to a 2D Gaussian, SH colour.
+ *   orc_render_pixels   FP64: per-pixel brute force over *all* drawn
+ *                       Gaussians, depth sort, front-to-back compositing
+ *                       (Eq. 4), plus an error budget ("slack") per pixel for
+ *                       decisions that sit within FP32 reach of a threshold.
+ *   orc_bin_f32         FP32 mirror of the binning arithmetic in a fixed,
+ *                       documented operation order (no FMA contraction; the
+ *                       file is compiled with -ffp-contract=off) giving depth
+ *                       key bits, radius, tile rectangle and tile count, with
+ *                       an FP64 shadow that flags decisions that pass through
+ *                       a transcendental within 3e-5 relative of a threshold.
+ *   orc_backward        FP64 adjoint (reverse mode) of the whole frame with
+ *                       respect to the raw per-Gaussian parameters.
+ *
+ * Readings of the paper (where it is silent, garbled or inconsistent):
+ *   - Time shift: Eq. 7's mu(t) = mu + (t - mu_t) V (the definition the
+ *     disentangled velocity V3D = V/W comes from, Sec. III-B-1); Eq. 15 and
+ *     Algorithm 1 print the opposite sign (mu_t - t), which equals V -> -V.
+ *   - Temporal factor: exp(-1/2 (t - mu_t)^2 / s_t^2) with s_t = sqrt(W) and
+ *     lambda = 1/W (Eq. 6-7; Eq. 6 misprints x for t).  It multiplies the
+ *     3DGS opacity.
+ *   - The 2D mean is the exact perspective projection of the time-shifted
+ *     camera-space mean P_view + tau V_view (Eq. 12, 15); Eq. 13's ray-space
+ *     velocity is not used to render.
+ *   - Depth for sorting is camera-space z (3DGS convention).
+ *   - SH colour is evaluated in the direction of the time-shifted mean.
+ *   - 3DGS constants (the paper defers to 3DGS for rasterisation): near 0.2,
+ *     +0.3 px^2 dilation, Jacobian clamp 1.3 x half-FoV, alpha <= 0.99, skip
+ *     alpha < 1/255, stop before blending when T(1-alpha) < 1e-4, black
+ *     background; tile radius 3.33 sqrt(lambda_max) (3.33^2 > 2 ln 255, so
+ *     every pixel with alpha >= 1/255 lies inside the square).
+ *   - Compositing product runs over j = 1..i-1 (Eq. 4 misprints j = i).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_NEAR 0.2
+#define ORC_DILATION 0.3
+#define ORC_ALPHA_MAX 0.99
+#define ORC_ALPHA_MIN (1.0 / 255.0)
+#define ORC_T_MIN 1e-4
+#define ORC_RADIUS_K 3.33
+#define ORC_JAC_CLAMP 1.3
+
+typedef struct {
+    int32_t n, sh_degree;
+    const double *means;         /* N x 3 */
+    const double *t_mean;        /* N */
+    const double *velocity;      /* N x 3 */
+    const double *log_scales;    /* N x 3 */
+    const double *log_t_scale;   /* N */
+    const double *quats;         /* N x 4, (w,x,y,z), not necessarily unit */
+    const double *opacity_logit; /* N */
+    const double *sh;            /* N x (deg+1)^2 x 3 */
+    const double *cov3d;         /* optional N x 6 (xx,xy,xz,yy,yz,zz): replaces scales+quats */
+} orc_scene;
+
+typedef struct {
+    double R[9], T[3];           /* world -> camera, row-major */
+    double fx, fy, cx, cy;
+    int32_t width, height;
+} orc_camera;
+
+typedef struct {                 /* per-Gaussian FP64 2D Gaussian, all arrays length N */
+    int32_t *drawn;
+    double *u, *v, *depth;
+    double *conic;               /* N x 3 (a, b, c): inverse of the 2D covariance */
+    double *cov2d;               /* N x 3 (xx, xy, yy) including the dilation */
+    double *opacity_t;           /* sigmoid(logit) * temporal factor */
+    double *rgb;                 /* N x 3 */
+    double *lambda_max;
+} orc_g2d;
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------------
+ * Real spherical harmonics up to degree 3, coefficient k = l^2 + l + m, in the
+ * convention Y_lm = sqrt2 Im Y_l^|m| (m<0), Y_l^0 (m=0), sqrt2 Re Y_l^m (m>0)
+ * of the complex harmonics *with* the Condon-Shortley phase (the basis the
+ * 3DGS colour model uses).  Constants from their closed forms.
+ * ------------------------------------------------------------------------- */
+void orc_sh_basis(const double d[3], int degree, double *Y) {
+    const double pi = 3.14159265358979323846;
+    double x = d[0], y = d[1], z = d[2];
+    Y[0] = 0.5 * sqrt(1.0 / pi);
+    if (degree < 1) return;
+    double c1 = sqrt(3.0 / (4.0 * pi));
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    if (degree < 2) return;
+    double xx = x * x, yy = y * y, zz = z * z;
+    double a = 0.5 * sqrt(15.0 / pi), b = 0.25 * sqrt(5.0 / pi), c = 0.25 * sqrt(15.0 / pi);
+    Y[4] = a * x * y;
+    Y[5] = -a * y * z;
+    Y[6] = b * (2.0 * zz - xx - yy);
+    Y[7] = -a * x * z;
+    Y[8] = c * (xx - yy);
+    if (degree < 3) return;
+    double e = 0.25 * sqrt(35.0 / (2.0 * pi)), f = 0.5 * sqrt(105.0 / pi);
+    double g = 0.25 * sqrt(21.0 / (2.0 * pi)), h = 0.25 * sqrt(7.0 / pi);
+    double k = 0.25 * sqrt(105.0 / pi);
+    Y[9] = -e * y * (3.0 * xx - yy);
+    Y[10] = f * x * y * z;
+    Y[11] = -g * y * (4.0 * zz - xx - yy);
+    Y[12] = h * z * (2.0 * zz - 3.0 * xx - 3.0 * yy);
+    Y[13] = -g * x * (4.0 * zz - xx - yy);
+    Y[14] = k * z * (xx - yy);
+    Y[15] = -e * x * (xx - 3.0 * yy);
+}
+
+/* Rotation matrix of the unit quaternion (w,x,y,z), row-major. */
+void orc_quat_to_rot(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - w * z);       R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);       R[7] = 2.0 * (y * z + w * x);       R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+static void matmul3(const double *A, const double *B, double *C) { /* C = A B, 3x3 */
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double s = 0.0;
+            for (int k = 0; k < 3; k++) s += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = s;
+        }
+}
+static void transpose3(const double *A, double *At) {
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) At[3 * j + i] = A[3 * i + j];
+}
+
+/* 3D covariance of Gaussian i: Sigma3D = R S S^T R^T (Algorithm 1, "calculate
+ * 3D covariance"), or the covariance supplied directly. */
+static void cov3d_of(const orc_scene *sc, int i, double S3[9]) {
+    if (sc->cov3d) {
+        const double *c = sc->cov3d + 6 * (size_t)i;
+        S3[0] = c[0]; S3[1] = c[1]; S3[2] = c[2];
+        S3[3] = c[1]; S3[4] = c[3]; S3[5] = c[4];
+        S3[6] = c[2]; S3[7] = c[4]; S3[8] = c[5];
+        return;
+    }
+    const double *q = sc->quats + 4 * (size_t)i;
+    double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+    double R[9], M[9], Mt[9];
+    orc_quat_to_rot(qn, R);
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) M[3 * r + c] = R[3 * r + c] * exp(sc->log_scales[3 * (size_t)i + c]);
+    transpose3(M, Mt);
+    matmul3(M, Mt, S3);
+}
+
+static void cam_position(const orc_camera *cam, double p[3]) { /* -R^T T */
+    for (int j = 0; j < 3; j++)
+        p[j] = -(cam->R[0 * 3 + j] * cam->T[0] + cam->R[1 * 3 + j] * cam->T[1] + cam->R[2 * 3 + j] * cam->T[2]);
+}
+
+/* ---------------------------------------------------------------------------
+ * orc_preprocess: per Gaussian, the dynamic 2D Gaussian at time t.
+ *   tau = t - mu_t;  mu(t) = mu + tau V3D                       (Eq. 7)
+ *   o_hat = sigmoid(logit) exp(-tau^2 / (2 s_t^2)), s_t = e^{log s_t}   (Eq. 6-7)
+ *   X = R_cam mu(t) + T_cam = P_view + tau V_view               (Eq. 9-11, 15)
+ *   (u, v) = (fx X/Z + cx, fy Y/Z + cy)                          (Eq. 12)
+ *   J = d(u,v)/dX at X (x/z, y/z clamped)                       (Eq. 14)
+ *   Sigma' = J R_cam Sigma3D R_cam^T J^T + 0.3 I                (Eq. 16)
+ *   conic = Sigma'^{-1}; colour = max(0, SH . Y(dir) + 0.5)
+ * temporal_cull: also drop o_hat < 1/255 (lossless: alpha < 1/255 everywhere).
+ * ------------------------------------------------------------------------- */
+void orc_preprocess(const orc_scene *sc, const orc_camera *cam, double t, int temporal_cull, orc_g2d *out) {
+    const int n = sc->n, ncoef = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+    double campos[3];
+    cam_position(cam, campos);
+    const double limx = ORC_JAC_CLAMP * (0.5 * cam->width) / cam->fx;
+    const double limy = ORC_JAC_CLAMP * (0.5 * cam->height) / cam->fy;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; i++) {
+        out->drawn[i] = 0;
+        double tau = t - sc->t_mean[i];
+        double m[3], X[3];
+        for (int j = 0; j < 3; j++) m[j] = sc->means[3 * (size_t)i + j] + tau * sc->velocity[3 * (size_t)i + j];
+        for (int r = 0; r < 3; r++)
+            X[r] = cam->R[3 * r + 0] * m[0] + cam->R[3 * r + 1] * m[1] + cam->R[3 * r + 2] * m[2] + cam->T[r];
+        double o = 1.0 / (1.0 + exp(-sc->opacity_logit[i]));
+        double st = exp(sc->log_t_scale[i]);
+        double oh = o * exp(-0.5 * tau * tau / (st * st));
+        out->opacity_t[i] = oh;
+        out->depth[i] = X[2];
+        if (!(X[2] > ORC_NEAR)) continue;
+        if (temporal_cull && !(oh >= ORC_ALPHA_MIN)) continue;
+        double Z = X[2];
+        double xz = X[0] / Z, yz = X[1] / Z;
+        double xzc = fmin(limx, fmax(-limx, xz)), yzc = fmin(limy, fmax(-limy, yz));
+        double J[6] = {cam->fx / Z, 0.0, -cam->fx * xzc / Z, 0.0, cam->fy / Z, -cam->fy * yzc / Z};
+        double S3[9], Wt[9], A[9], Sc[9];
+        cov3d_of(sc, i, S3);
+        matmul3(cam->R, S3, A);
+        transpose3(cam->R, Wt);
+        matmul3(A, Wt, Sc); /* Sigma_cam = W Sigma3D W^T */
+        double JS[6];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++) JS[3 * r + c] = J[3 * r] * Sc[c] + J[3 * r + 1] * Sc[3 + c] + J[3 * r + 2] * Sc[6 + c];
+        double c00 = JS[0] * J[0] + JS[1] * J[1] + JS[2] * J[2] + ORC_DILATION;
+        double c01 = JS[0] * J[3] + JS[1] * J[4] + JS[2] * J[5];
+        double c11 = JS[3] * J[3] + JS[4] * J[4] + JS[5] * J[5] + ORC_DILATION;
+        double det = c00 * c11 - c01 * c01;
+        if (!(det > 0.0)) continue;
+        out->cov2d[3 * (size_t)i + 0] = c00;
+        out->cov2d[3 * (size_t)i + 1] = c01;
+        out->cov2d[3 * (size_t)i + 2] = c11;
+        out->conic[3 * (size_t)i + 0] = c11 / det;
+        out->conic[3 * (size_t)i + 1] = -c01 / det;
+        out->conic[3 * (size_t)i + 2] = c00 / det;
+        double mid = 0.5 * (c00 + c11);
+        out->lambda_max[i] = mid + sqrt(fmax(0.1, mid * mid - det));
+        out->u[i] = cam->fx * xz + cam->cx;
+        out->v[i] = cam->fy * yz + cam->cy;
+        double d[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};
+        double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        d[0] /= dn; d[1] /= dn; d[2] /= dn;
+        double Y[16];
+        orc_sh_basis(d, sc->sh_degree, Y);
+        for (int ch = 0; ch < 3; ch++) {
+            double s = 0.0;
+            for (int k = 0; k < ncoef; k++) s += sc->sh[((size_t)i * ncoef + k) * 3 + ch] * Y[k];
+            out->rgb[3 * (size_t)i + ch] = fmax(0.0, s + 0.5);
+        }
+        out->drawn[i] = 1;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * orc_render_pixels: per pixel (centre x+0.5, y+0.5), brute force over every
+ * drawn Gaussian (Eq. 1 evaluated with the 2D conic, Eq. 4 compositing):
+ *   p = -1/2 (a dx^2 + c dy^2) - b dx dy; skip p > 0;
+ *   alpha = min(0.99, o_hat e^p); skip alpha < 1/255;
+ *   sort the kept by (depth, index); T = 1;
+ *   for each: stop if T (1 - alpha) < 1e-4; C += alpha T c; T *= 1 - alpha.
+ *   out = C + T bg.
+ * Besides the colour it returns T, the number of blended Gaussians, and a
+ * per-pixel slack: an upper bound on how far an FP32 evaluation of the same
+ * definition may legitimately move the colour because a discrete decision
+ * (alpha vs 1/255, T(1-alpha) vs 1e-4, p vs 0, the order of two nearly equal
+ * depths) sits within FP32 reach of its threshold.  eps_px is the absolute
+ * error budget of an FP32 projected mean in pixels.
+ * ------------------------------------------------------------------------- */
+typedef struct { double depth; int32_t idx; double alpha; double w; int near_alpha; } orc_cand;
+
+static int cand_cmp(const void *pa, const void *pb) {
+    const orc_cand *a = (const orc_cand *)pa, *b = (const orc_cand *)pb;
+    if (a->depth < b->depth) return -1;
+    if (a->depth > b->depth) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+void orc_render_pixels(const orc_g2d *g, int n, const orc_camera *cam, const double bg[3],
+                       int64_t npix, const int32_t *px, const int32_t *py, double eps_px,
+                       double *out_rgb, double *out_T, int32_t *out_ncontrib, double *out_slack) {
+    /* compact list of drawn Gaussians */
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    int nd = 0;
+    for (int i = 0; i < n; i++)
+        if (g->drawn[i]) ids[nd++] = i;
+    const int64_t W = cam->width;
+    if (npix < 0) npix = (int64_t)cam->width * cam->height;
+#pragma omp parallel
+    {
+        size_t cap = 1024;
+        orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * cap);
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t q = 0; q < npix; q++) {
+            double x = (px ? px[q] : (int32_t)(q % W)) + 0.5;
+            double y = (py ? py[q] : (int32_t)(q / W)) + 0.5;
+            size_t nc = 0;
+            double slack = 0.0;
+            for (int k = 0; k < nd; k++) {
+                int i = ids[k];
+                double dx = g->u[i] - x, dy = g->v[i] - y;
+                double a = g->conic[3 * (size_t)i], b = g->conic[3 * (size_t)i + 1], c = g->conic[3 * (size_t)i + 2];
+                double p = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
+                /* FP32 relative error budget of alpha for this pair */
+                double gx = fabs(a * dx + b * dy), gy = fabs(b * dx + c * dy);
+                double w = 2e-5 + (gx + gy) * eps_px + 4e-7 * fabs(p);
+                int near_p = fabs(p) <= (gx + gy) * eps_px + 1e-6;
+                if (p > 0.0 && !near_p) continue;
+                double alpha = fmin(ORC_ALPHA_MAX, g->opacity_t[i] * exp(fmin(p, 0.0)));
+                int near_alpha = fabs(alpha - ORC_ALPHA_MIN) <= w * ORC_ALPHA_MIN || near_p;
+                if (p > 0.0 || alpha < ORC_ALPHA_MIN) {
+                    if (!near_alpha) continue;
+                    alpha = -alpha; /* excluded here, but within reach of inclusion */
+                }
+                if (nc == cap) { cap *= 2; cand = (orc_cand *)realloc(cand, sizeof(orc_cand) * cap); }
+                cand[nc].depth = g->depth[i];
+                cand[nc].idx = i;
+                cand[nc].alpha = alpha;
+                cand[nc].w = w;
+                cand[nc].near_alpha = near_alpha;
+                nc++;
+            }
+            qsort(cand, nc, sizeof(orc_cand), cand_cmp);
+            double T = 1.0, C[3] = {0, 0, 0}, wT = 0.0, cmax = 0.0;
+            int32_t ncontrib = 0;
+            for (size_t k = 0; k < nc; k++) {
+                const double *c = g->rgb + 3 * (size_t)cand[k].idx;
+                double cm = fmax(c[0], fmax(c[1], c[2]));
+                if (cm > cmax) cmax = cm;
+            }
+            int32_t last = -1;
+            double prev_depth = -1.0, prev_alpha = 0.0;
+            for (size_t k = 0; k < nc; k++) {
+                double alpha = cand[k].alpha;
+                if (cand[k].near_alpha) slack += 2.0 * fabs(alpha) * (1.0 + cand[k].w) * cmax * T + 1e-7;
+                if (alpha < 0.0) continue; /* not blended in FP64 */
+                /* nearly equal depths: FP32 keys may order the pair the other way */
+                if (last >= 0 && fabs(cand[k].depth - prev_depth) <= 4e-6 * fmax(fabs(prev_depth), fabs(cand[k].depth)))
+                    slack += 2.0 * prev_alpha * alpha * cmax * (T / (1.0 - prev_alpha)) + 1e-7;
+                double test = T * (1.0 - alpha);
+                /* accumulated FP32 relative error of T, and the stop decision */
+                double wstop = wT + cand[k].w * alpha / (1.0 - alpha) + 1e-6;
+                if (fabs(test - ORC_T_MIN) <= wstop * ORC_T_MIN) slack += T * alpha * cmax + 2.0 * ORC_T_MIN * cmax;
+                if (test < ORC_T_MIN) break;
+                const double *c = g->rgb + 3 * (size_t)cand[k].idx;
+                for (int ch = 0; ch < 3; ch++) C[ch] += alpha * T * c[ch];
+                T = test;
+                wT = wstop;
+                ncontrib++;
+                last = (int32_t)k;
+                prev_depth = cand[k].depth;
+                prev_alpha = alpha;
+            }
+            for (int ch = 0; ch < 3; ch++) out_rgb[3 * q + ch] = C[ch] + T * bg[ch];
+            if (out_T) out_T[q] = T;
+            if (out_ncontrib) out_ncontrib[q] = ncontrib;
+            if (out_slack) out_slack[q] = slack;
+        }
+        free(cand);
+    }
+    free(ids);
+}
+
+/* ---------------------------------------------------------------------------
+ * orc_bin_f32: FP32 mirror of the binning arithmetic (per Gaussian: depth key
+ * bits, radius, tile rectangle, tile count) in the fixed operation order that
+ * the GPU preprocess also follows, so that tile/key lists can be compared bit
+ * for bit.  Every product and sum below is a separately rounded IEEE single
+ * operation evaluated left to right as parenthesised; sqrt and division are
+ * correctly rounded; this file is compiled with -ffp-contract=off.
+ *
+ *   tau = t - mu_t;  m_j = mu_j + tau*v_j
+ *   X_r = ((R_r0*m_0 + R_r1*m_1) + R_r2*m_2) + T_r
+ *   cull !(Z > 0.2)
+ *   o = 1/(1 + expf(-logit)); st = expf(lst); o_hat = o * expf((-0.5*(tau*tau))/(st*st))
+ *   cull !(o_hat >= 1/255)
+ *   xz = X/Z, yz = Y/Z; u = fx*xz + cx; v = fy*yz + cy
+ *   limx = 1.3*((0.5*W)/fx); xzc = min(limx, max(-limx, xz)) (same for y)
+ *   J00 = fx/Z, J02 = -(fx*xzc)/Z, J11 = fy/Z, J12 = -(fy*yzc)/Z
+ *   qn = q / sqrtf(((w*w + x*x) + y*y) + z*z); R(qn) as in orc_quat_to_rot
+ *   with 1 - 2*(a*a + b*b) and 2*(a*b -/+ c*d); M_ij = R_ij * expf(ls_j)
+ *   Tj_0 = J00*W_0j + J02*W_2j; Tj_1 = J11*W_1j + J12*W_2j   (T = J W)
+ *   TM_ij = (T_i0*M_0j + T_i1*M_1j) + T_i2*M_2j              (TM = J W M)
+ *   s00 = ((TM00^2 + TM01^2) + TM02^2) + 0.3; s11 likewise;
+ *   s01 = (TM00*TM10 + TM01*TM11) + TM02*TM12
+ *   det = s00*s11 - s01*s01; cull !(det > 0)
+ *   mid = 0.5*(s00 + s11); lam = mid + sqrtf(max(0.1, mid*mid - det))
+ *   r = (int) ceilf(3.33 * sqrtf(lam))
+ *   cull unless u, v finite; x0 = floorf((u - r)/tile), x1 = floorf((u + r)/tile),
+ *   cull if x1 < 0 or x0 > tiles_x - 1, then clamp to [0, tiles_x-1] (same in y)
+ *   tiles = (x1 - x0 + 1)(y1 - y0 + 1); depth key = bits of Z
+ * Flags (FP64 shadow of the same quantities): bit 0 -- 3.33 sqrt(lambda_max)
+ * within 3e-5 relative of an integer (radius decided through expf of the
+ * scales); bit 1 -- o_hat within 3e-5 relative of 1/255.  Only these two
+ * decisions depend on a transcendental function, whose FP32 result may differ
+ * by an ulp between libraries; a flagged Gaussian is excluded from bit-exact
+ * comparison.  A culled Gaussian has depth key 0xFFFFFFFF and 0 tiles.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n, sh_degree;
+    const float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit;
+} orc_scene_f32;
+
+typedef struct { float R[9], T[3], fx, fy, cx, cy; int32_t width, height; } orc_camera_f32;
+
+void orc_bin_f32(const orc_scene_f32 *sc, const orc_camera_f32 *cam, float t, int32_t tile,
+                 uint32_t *depth_key, int32_t *radius, int32_t *rect /* N x 4: x0,x1,y0,y1 */,
+                 uint32_t *tiles_touched, int32_t *flags, float *uv /* N x 2, may be NULL */) {
+    const int n = sc->n;
+    const int32_t tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
+    const float limx = 1.3f * ((0.5f * (float)cam->width) / cam->fx);
+    const float limy = 1.3f * ((0.5f * (float)cam->height) / cam->fy);
+    const float tilef = (float)tile;
+    const float amin = (float)(1.0 / 255.0);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; i++) {
+        depth_key[i] = 0xFFFFFFFFu;
+        radius[i] = 0;
+        rect[4 * (size_t)i + 0] = rect[4 * (size_t)i + 1] = rect[4 * (size_t)i + 2] = rect[4 * (size_t)i + 3] = 0;
+        tiles_touched[i] = 0;
+        flags[i] = 0;
+        if (uv) { uv[2 * (size_t)i] = 0.f; uv[2 * (size_t)i + 1] = 0.f; }
+        const float *mu = sc->means + 3 * (size_t)i, *vel = sc->velocity + 3 * (size_t)i;
+        float tau = t - sc->t_mean[i];
+        float m0 = mu[0] + tau * vel[0], m1 = mu[1] + tau * vel[1], m2 = mu[2] + tau * vel[2];
+        const float *R = cam->R;
+        float X = ((R[0] * m0 + R[1] * m1) + R[2] * m2) + cam->T[0];
+        float Y = ((R[3] * m0 + R[4] * m1) + R[5] * m2) + cam->T[1];
+        float Z = ((R[6] * m0 + R[7] * m1) + R[8] * m2) + cam->T[2];
+        if (!(Z > 0.2f)) continue;
+        /* opacity and the temporal factor (transcendental decision) */
+        float o = 1.0f / (1.0f + expf(-sc->opacity_logit[i]));
+        float st = expf(sc->log_t_scale[i]);
+        float oh = o * expf((-0.5f * (tau * tau)) / (st * st));
+        {
+            double tau64 = (double)t - (double)sc->t_mean[i];
+            double o64 = 1.0 / (1.0 + exp(-(double)sc->opacity_logit[i]));
+            double st64 = exp((double)sc->log_t_scale[i]);
+            double oh64 = o64 * exp(-0.5 * tau64 * tau64 / (st64 * st64));
+            if (fabs(oh64 - 1.0 / 255.0) <= 3e-5 * (1.0 / 255.0)) flags[i] |= 2;
+        }
+        if (!(oh >= amin)) continue;
+        float xz = X / Z, yz = Y / Z;
+        float u = cam->fx * xz + cam->cx, v = cam->fy * yz + cam->cy;
+        float xzc = fminf(limx, fmaxf(-limx, xz)), yzc = fminf(limy, fmaxf(-limy, yz));
+        float J00 = cam->fx / Z, J02 = -(cam->fx * xzc) / Z;
+        float J11 = cam->fy / Z, J12 = -(cam->fy * yzc) / Z;
+        const float *q = sc->quats + 4 * (size_t)i;
+        float qn2 = ((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3];
+        float qn = sqrtf(qn2);
+        float w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+        float Rq[9];
+        Rq[0] = 1.0f - 2.0f * (y * y + z * z); Rq[1] = 2.0f * (x * y - w * z);       Rq[2] = 2.0f * (x * z + w * y);
+        Rq[3] = 2.0f * (x * y + w * z);       Rq[4] = 1.0f - 2.0f * (x * x + z * z); Rq[5] = 2.0f * (y * z - w * x);
+        Rq[6] = 2.0f * (x * z - w * y);       Rq[7] = 2.0f * (y * z + w * x);       Rq[8] = 1.0f - 2.0f * (x * x + y * y);
+        const float *ls = sc->log_scales + 3 * (size_t)i;
+        float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+        float M[9];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) M[3 * r + c] = Rq[3 * r + c] * s[c];
+        float Tm[6];
+        for (int j = 0; j < 3; j++) {
+            Tm[j] = J00 * R[j] + J02 * R[6 + j];
+            Tm[3 + j] = J11 * R[3 + j] + J12 * R[6 + j];
+        }
+        float TM[6];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++)
+                TM[3 * r + c] = (Tm[3 * r + 0] * M[0 * 3 + c] + Tm[3 * r + 1] * M[1 * 3 + c]) + Tm[3 * r + 2] * M[2 * 3 + c];
+        float s00 = ((TM[0] * TM[0] + TM[1] * TM[1]) + TM[2] * TM[2]) + 0.3f;
+        float s01 = (TM[0] * TM[3] + TM[1] * TM[4]) + TM[2] * TM[5];
+        float s11 = ((TM[3] * TM[3] + TM[4] * TM[4]) + TM[5] * TM[5]) + 0.3f;
+        float det = s00 * s11 - s01 * s01;
+        if (!(det > 0.0f)) continue;
+        float mid = 0.5f * (s00 + s11);
+        float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+        float rf = ceilf(3.33f * sqrtf(lam));
+        /* FP64 shadow of the radius decision */
+        {
+            double q64[4] = {q[0], q[1], q[2], q[3]};
+            double nq = sqrt(q64[0] * q64[0] + q64[1] * q64[1] + q64[2] * q64[2] + q64[3] * q64[3]);
+            for (int k = 0; k < 4; k++) q64[k] /= nq;
+            double R64[9], M64[9], T64[6], TM64[6];
+            orc_quat_to_rot(q64, R64);
+            double Z64 = 0.0, X64 = 0.0, Y64 = 0.0, mm[3];
+            double tau64 = (double)t - (double)sc->t_mean[i];
+            for (int j = 0; j < 3; j++) mm[j] = (double)mu[j] + tau64 * (double)vel[j];
+            X64 = (double)R[0] * mm[0] + (double)R[1] * mm[1] + (double)R[2] * mm[2] + (double)cam->T[0];
+            Y64 = (double)R[3] * mm[0] + (double)R[4] * mm[1] + (double)R[5] * mm[2] + (double)cam->T[1];
+            Z64 = (double)R[6] * mm[0] + (double)R[7] * mm[1] + (double)R[8] * mm[2] + (double)cam->T[2];
+            double lx = 1.3 * (0.5 * cam->width) / (double)cam->fx, ly = 1.3 * (0.5 * cam->height) / (double)cam->fy;
+            double xzc64 = fmin(lx, fmax(-lx, X64 / Z64)), yzc64 = fmin(ly, fmax(-ly, Y64 / Z64));
+            double j00 = (double)cam->fx / Z64, j02 = -(double)cam->fx * xzc64 / Z64;
+            double j11 = (double)cam->fy / Z64, j12 = -(double)cam->fy * yzc64 / Z64;
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) M64[3 * r + c] = R64[3 * r + c] * exp((double)ls[c]);
+            for (int j = 0; j < 3; j++) {
+                T64[j] = j00 * (double)R[j] + j02 * (double)R[6 + j];
+                T64[3 + j] = j11 * (double)R[3 + j] + j12 * (double)R[6 + j];
+            }
+            for (int r = 0; r < 2; r++)
+                for (int c = 0; c < 3; c++)
+                    TM64[3 * r + c] = T64[3 * r] * M64[c] + T64[3 * r + 1] * M64[3 + c] + T64[3 * r + 2] * M64[6 + c];
+            double a00 = TM64[0] * TM64[0] + TM64[1] * TM64[1] + TM64[2] * TM64[2] + 0.3;
+            double a01 = TM64[0] * TM64[3] + TM64[1] * TM64[4] + TM64[2] * TM64[5];
+            double a11 = TM64[3] * TM64[3] + TM64[4] * TM64[4] + TM64[5] * TM64[5] + 0.3;
+            double d64 = a00 * a11 - a01 * a01, m64 = 0.5 * (a00 + a11);
+            double rr = 3.33 * sqrt(m64 + sqrt(fmax(0.1, m64 * m64 - d64)));
+            if (fabs(rr - nearbyint(rr)) <= 3e-5 * rr) flags[i] |= 1;
+        }
+        if (!(isfinite(u) && isfinite(v))) continue;
+        float fx0 = floorf((u - rf) / tilef), fx1 = floorf((u + rf) / tilef);
+        float fy0 = floorf((v - rf) / tilef), fy1 = floorf((v + rf) / tilef);
+        if (!(fx1 >= 0.0f) || !(fx0 <= (float)(tiles_x - 1))) continue;
+        if (!(fy1 >= 0.0f) || !(fy0 <= (float)(tiles_y - 1))) continue;
+        int32_t x0 = (int32_t)fmaxf(fx0, 0.0f), x1 = (int32_t)fminf(fx1, (float)(tiles_x - 1));
+        int32_t y0 = (int32_t)fmaxf(fy0, 0.0f), y1 = (int32_t)fminf(fy1, (float)(tiles_y - 1));
+        uint32_t bits;
+        memcpy(&bits, &Z, 4);
+        depth_key[i] = bits;
+        radius[i] = (int32_t)rf;
+        rect[4 * (size_t)i + 0] = x0; rect[4 * (size_t)i + 1] = x1;
+        rect[4 * (size_t)i + 2] = y0; rect[4 * (size_t)i + 3] = y1;
+        tiles_touched[i] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+        if (uv) { uv[2 * (size_t)i] = u; uv[2 * (size_t)i + 1] = v; }
+    }
+}
+
+/* Emit the unsorted (tile, depth_bits, id) triples of all binned Gaussians in
+ * index order, tiles of one Gaussian row-major; returns the count written. */
+int64_t orc_emit_keys(int32_t n, const uint32_t *depth_key, const int32_t *rect, const uint32_t *tiles_touched,
+                      int32_t tiles_x, int64_t cap, uint32_t *tile_out, uint32_t *depth_out, uint32_t *id_out) {
+    int64_t k = 0;
+    for (int32_t i = 0; i < n; i++) {
+        if (!tiles_touched[i]) continue;
+        for (int32_t ty = rect[4 * (size_t)i + 2]; ty <= rect[4 * (size_t)i + 3]; ty++)
+            for (int32_t tx = rect[4 * (size_t)i + 0]; tx <= rect[4 * (size_t)i + 1]; tx++) {
+                if (k < cap) {
+                    tile_out[k] = (uint32_t)(ty * tiles_x + tx);
+                    depth_out[k] = depth_key[i];
+                    id_out[k] = (uint32_t)i;
+                }
+                k++;
+            }
+    }
+    return k;
+}

@@ -1,0 +1,82 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a temporary copy of ``oracle/oracle.c`` (on the
+CPU; the real oracle is untouched), builds it, points the pin tests at the
+mutant, and requires at least one of the named pins to fail.
+"""
+import importlib.util
+import os
+import shutil
+
+import pytest
+
+import tests.test_oracle_pins as pins
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = [
+    ("dropped dilation", "#define ORC_DILATION 0.3", "#define ORC_DILATION 0.0",
+     ["test_single_gaussian_on_axis_closed_form"]),
+    ("time shift sign (Eq. 7 vs Alg. 1)",
+     "m[j] = sc->means[3 * (size_t)i + j] + tau * sc->velocity", "m[j] = sc->means[3 * (size_t)i + j] - tau * sc->velocity",
+     ["test_moving_gaussian_closed_form", "test_disentangled_equals_slicing_first"]),
+    ("temporal factor without the 1/2", "double oh = o * exp(-0.5 * tau * tau / (st * st));",
+     "double oh = o * exp(-tau * tau / (st * st));", ["test_moving_gaussian_closed_form"]),
+    ("Jacobian off-diagonal sign", "-cam->fx * xzc / Z, 0.0, cam->fy / Z, -cam->fy * yzc / Z",
+     "cam->fx * xzc / Z, 0.0, cam->fy / Z, -cam->fy * yzc / Z", ["test_single_gaussian_off_axis_closed_form"]),
+    ("fx / fy swapped in the Jacobian", "double J[6] = {cam->fx / Z, 0.0,", "double J[6] = {cam->fy / Z, 0.0,",
+     ["test_single_gaussian_on_axis_closed_form"]),
+    ("camera rotation transposed", "X[r] = cam->R[3 * r + 0] * m[0] + cam->R[3 * r + 1] * m[1] + cam->R[3 * r + 2] * m[2]",
+     "X[r] = cam->R[0 + r] * m[0] + cam->R[3 + r] * m[1] + cam->R[6 + r] * m[2]",
+     ["test_single_gaussian_on_axis_closed_form"]),
+    ("conic off-diagonal sign", "out->conic[3 * (size_t)i + 1] = -c01 / det;", "out->conic[3 * (size_t)i + 1] = c01 / det;",
+     ["test_single_gaussian_off_axis_closed_form"]),
+    ("pixel centre without +0.5", "double x = (px ? px[q] : (int32_t)(q % W)) + 0.5;",
+     "double x = (px ? px[q] : (int32_t)(q % W));", ["test_single_gaussian_on_axis_closed_form"]),
+    ("blend after the stop test", "if (test < ORC_T_MIN) break;", "if (test < 0.0) break;", ["test_composite_golden"]),
+    ("no alpha clamp", "double alpha = fmin(ORC_ALPHA_MAX,", "double alpha = fmin(1.0,", ["test_composite_golden"]),
+    ("back-to-front order", "if (a->depth < b->depth) return -1;\n    if (a->depth > b->depth) return 1;",
+     "if (a->depth < b->depth) return 1;\n    if (a->depth > b->depth) return -1;", ["test_composite_golden"]),
+    ("quaternion order xyzw", "double w = q[0], x = q[1], y = q[2], z = q[3];",
+     "double x = q[0], y = q[1], z = q[2], w = q[3];", ["test_quat_to_rot_matches_scipy"]),
+    ("SH degree-1 sign", "Y[1] = -c1 * y;", "Y[1] = c1 * y;", ["test_sh_basis_matches_scipy"]),
+    ("SH direction of the static mean",
+     "double d[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};",
+     "double d[3] = {sc->means[3 * (size_t)i] - campos[0], sc->means[3 * (size_t)i + 1] - campos[1], sc->means[3 * (size_t)i + 2] - campos[2]};",
+     ["test_time_shift_equivalence"]),
+    ("colour not clamped at zero", "out->rgb[3 * (size_t)i + ch] = fmax(0.0, s + 0.5);",
+     "out->rgb[3 * (size_t)i + ch] = s + 0.5;", ["test_negative_colour_is_clamped"]),
+    ("FP32 radius factor 3.0", "float rf = ceilf(3.33f * sqrtf(lam));", "float rf = ceilf(3.0f * sqrtf(lam));",
+     ["test_bin_f32_agrees_with_fp64", "test_tile_rect_covers_alpha_support"]),
+    ("FP32 rect with truncation", "float fx0 = floorf((u - rf) / tilef)", "float fx0 = floorf((u - rf) / tilef) + 1.0f",
+     ["test_tile_rect_covers_alpha_support"]),
+]
+
+
+def _load_mutant(tmp, name, old, new):
+    d = tmp / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), d, ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    src = (d / "oracle.c").read_text()
+    assert src.count(old) == 1, f"mutation anchor not unique/found: {name}"
+    (d / "oracle.c").write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{abs(hash(name))}", d / "__init__.py")
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build(force=True)
+    return mod
+
+
+@pytest.mark.parametrize("name,old,new,tests", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(tmp_path, monkeypatch, name, old, new, tests):
+    mod = _load_mutant(tmp_path, name, old, new)
+    monkeypatch.setattr(pins, "oracle", mod)
+    caught = []
+    for tname in tests:
+        fn = getattr(pins, tname)
+        argsets = [dict(rotated=False), dict(rotated=True)] if tname == "test_single_gaussian_on_axis_closed_form" else [{}]
+        for kw in argsets:
+            try:
+                fn(**kw)
+            except (AssertionError, FloatingPointError, ValueError, ZeroDivisionError):
+                caught.append(tname)
+    assert caught, f"no pin caught the mutant '{name}'"

@@ -1,0 +1,434 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+None of these checks re-types the oracle's general formula: each compares it
+with a closed form of a special case, a library routine (scipy spherical
+harmonics and rotations, numpy inverse / eigenvalues), the definition of a 4D
+Gaussian (Eq. 5-7), or an invariant that must hold for any input.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+C0 = 0.5 / math.sqrt(math.pi)
+
+
+def scene64(means, rgb=None, opacity=None, log_scales=None, quats=None, velocity=None, t_mean=None,
+            log_t_scale=None, sh=None, sh_degree=0):
+    """A float64 scene for exact oracle pins (opacity given as a probability)."""
+    means = np.asarray(means, np.float64).reshape(-1, 3)
+    n = len(means)
+    if sh is None:
+        rgb = np.full((n, 3), 0.5) if rgb is None else np.asarray(rgb, np.float64).reshape(n, 3)
+        sh = ((rgb - 0.5) / C0).reshape(n, 1, 3)
+        sh_degree = 0
+    op = np.full(n, 0.5) if opacity is None else np.asarray(opacity, np.float64)
+    with np.errstate(divide="ignore"):
+        logit = np.where(op >= 1.0, 60.0, np.log(op / (1.0 - op)))
+    return synth.Scene(
+        means=means,
+        t_mean=np.zeros(n) if t_mean is None else np.asarray(t_mean, np.float64),
+        velocity=np.zeros((n, 3)) if velocity is None else np.asarray(velocity, np.float64).reshape(n, 3),
+        log_scales=np.full((n, 3), math.log(0.05)) if log_scales is None else np.asarray(log_scales, np.float64).reshape(n, 3),
+        log_t_scale=np.full(n, 30.0) if log_t_scale is None else np.asarray(log_t_scale, np.float64),
+        quats=np.tile([1.0, 0, 0, 0], (n, 1)) if quats is None else np.asarray(quats, np.float64).reshape(n, 4),
+        opacity_logit=logit, sh=np.asarray(sh, np.float64), sh_degree=sh_degree)
+
+
+def camera(width=64, height=48, fx=60.0, fy=45.0, cx=None, cy=None, R=None, T=None):
+    """A camera kept in float64 (the synth container rounds to float32 for the GPU)."""
+    cam = synth.Camera(R=np.eye(3), T=np.zeros(3), fx=fx, fy=fy, cx=0.0, cy=0.0, width=width, height=height)
+    cam.R = np.eye(3) if R is None else np.asarray(R, np.float64)
+    cam.T = np.zeros(3) if T is None else np.asarray(T, np.float64)
+    cam.fx, cam.fy = float(fx), float(fy)
+    cam.cx = width / 2 + 0.5 if cx is None else float(cx)
+    cam.cy = height / 2 + 0.5 if cy is None else float(cy)
+    return cam
+
+
+def rot_y(th):
+    c, s = math.cos(th), math.sin(th)
+    return np.array([[c, 0, s], [0, 1, 0], [-s, 0, c]])
+
+
+# ---------------------------------------------------------------------------
+# library pins
+# ---------------------------------------------------------------------------
+
+def test_sh_basis_matches_scipy():
+    """Real SH (Condon-Shortley phase, sqrt2 Re/Im) against scipy's complex harmonics."""
+    from scipy.special import sph_harm_y
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        ours = oracle.sh_basis(d, 3)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                Y = complex(sph_harm_y(l, abs(m), theta, phi))
+                ref = Y.real if m == 0 else math.sqrt(2) * (Y.imag if m < 0 else Y.real)
+                assert ours[l * l + l + m] == pytest.approx(ref, abs=1e-12), (l, m)
+
+
+def test_sh_basis_orthonormal():
+    """Gauss-Legendre x uniform-phi quadrature of Y_i Y_j over the sphere is the identity."""
+    xs, ws = np.polynomial.legendre.leggauss(12)
+    nphi = 24
+    G = np.zeros((16, 16))
+    for z, w in zip(xs, ws):
+        r = math.sqrt(1 - z * z)
+        for k in range(nphi):
+            ph = 2 * math.pi * k / nphi
+            Y = oracle.sh_basis([r * math.cos(ph), r * math.sin(ph), z], 3)
+            G += w * (2 * math.pi / nphi) * np.outer(Y, Y)
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_quat_to_rot_matches_scipy():
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        ref = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy is scalar-last
+        np.testing.assert_allclose(oracle.quat_to_rot(q), ref, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# closed forms
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rotated", [False, True])
+def test_single_gaussian_on_axis_closed_form(rotated):
+    """On the optical axis, axis-aligned: Sigma' = diag(fx^2 sx^2/Z^2 + 0.3, fy^2 sy^2/Z^2 + 0.3)
+    (Eq. 14, 16), and every pixel is min(0.99, o e^p) c (Eq. 1, 4)."""
+    Z, sx, sy, o, c = 4.0, 0.07, 0.03, 0.7, np.array([0.9, 0.3, 0.6])
+    R = rot_y(0.4) if rotated else np.eye(3)
+    mu = R.T @ np.array([0.0, 0.0, Z])          # camera-space (0, 0, Z)
+    # rotated camera: isotropic Gaussian so that Sigma_cam does not depend on R
+    ls = [math.log(sx), math.log(sx if rotated else sy), math.log(0.05)]
+    sy_eff = sx if rotated else sy
+    sc = scene64([mu], rgb=[c], opacity=[o], log_scales=[ls])
+    if rotated:
+        sc.log_scales[0, 2] = math.log(sx)
+    cam = camera(R=R)
+    out = oracle.render(sc, cam, 0.0)
+    g = out["g2d"]
+    s00 = cam.fx ** 2 * sx ** 2 / Z ** 2 + 0.3
+    s11 = cam.fy ** 2 * sy_eff ** 2 / Z ** 2 + 0.3
+    assert g["u"][0] == pytest.approx(cam.cx, abs=1e-12)
+    assert g["v"][0] == pytest.approx(cam.cy, abs=1e-12)
+    np.testing.assert_allclose(g["cov2d"][0], [s00, 0.0, s11], atol=1e-12)
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    dx, dy = xs + 0.5 - cam.cx, ys + 0.5 - cam.cy
+    a = np.minimum(0.99, o * np.exp(-0.5 * (dx ** 2 / s00 + dy ** 2 / s11)))
+    a = np.where(a >= 1 / 255, a, 0.0)
+    np.testing.assert_allclose(out["rgb"], a[..., None] * c, atol=1e-12)
+    np.testing.assert_allclose(out["T"], 1.0 - a, atol=1e-12)
+
+
+def test_negative_colour_is_clamped():
+    """The 3DGS colour model clamps SH . Y + 0.5 at zero per channel: a Gaussian whose
+    degree-0 colour is (-0.4, 0.5, 1.2) renders (0, 0.5 alpha, 1.2 alpha)."""
+    sc = scene64([[0.0, 0.0, 3.0]], rgb=[[-0.4, 0.5, 1.2]], opacity=[0.6])
+    cam = camera()
+    out = oracle.render(sc, cam, 0.0, pixels=[[cam.width // 2, cam.height // 2]])
+    np.testing.assert_allclose(out["rgb"][0], [0.0, 0.3, 0.72], atol=1e-12)
+
+
+def test_single_gaussian_off_axis_closed_form():
+    """Off axis at (X, Y, Z), axis-aligned Sigma = diag(sx^2, sy^2, sz^2): from Eq. 14/16
+    Sigma'_00 = fx^2 (sx^2/Z^2 + X^2 sz^2/Z^4) + 0.3, Sigma'_01 = fx fy X Y sz^2 / Z^4,
+    Sigma'_11 = fy^2 (sy^2/Z^2 + Y^2 sz^2/Z^4) + 0.3."""
+    X, Y, Z = 0.6, -0.4, 3.0
+    sx, sy, sz = 0.05, 0.08, 0.2
+    sc = scene64([[X, Y, Z]], log_scales=[[math.log(sx), math.log(sy), math.log(sz)]])
+    cam = camera(width=96, height=80, fx=70.0, fy=55.0)
+    g = oracle.preprocess(sc, cam, 0.0)
+    fx, fy = cam.fx, cam.fy
+    expect = [fx ** 2 * (sx ** 2 / Z ** 2 + X ** 2 * sz ** 2 / Z ** 4) + 0.3,
+              fx * fy * X * Y * sz ** 2 / Z ** 4,
+              fy ** 2 * (sy ** 2 / Z ** 2 + Y ** 2 * sz ** 2 / Z ** 4) + 0.3]
+    np.testing.assert_allclose(g["cov2d"][0], expect, rtol=1e-12)
+    assert g["u"][0] == pytest.approx(fx * X / Z + cam.cx, abs=1e-12)
+    assert g["v"][0] == pytest.approx(fy * Y / Z + cam.cy, abs=1e-12)
+    np.testing.assert_allclose(g["conic"][0], np.linalg.inv([[expect[0], expect[1]], [expect[1], expect[2]]])
+                               .reshape(4)[[0, 1, 3]], rtol=1e-12)
+
+
+def test_moving_gaussian_closed_form():
+    """Time-shifted mean mu + (t - mu_t) V (Eq. 7) projects to u(t) = fx (X + tau Vx)/(Z + tau Vz) + cx,
+    and the temporal factor is 1 at tau = 0 and e^{-1/2} at tau = +-s_t (Eq. 6)."""
+    X, Y, Z = 0.3, 0.2, 3.0
+    V = np.array([0.5, -0.25, 1.0])
+    mu_t, s_t, o = 0.4, 0.15, 0.8
+    sc = scene64([[X, Y, Z]], velocity=[V], opacity=[o], t_mean=[mu_t], log_t_scale=[math.log(s_t)])
+    cam = camera()
+    for t in (mu_t, mu_t + s_t, mu_t - s_t, 0.9):
+        tau = t - mu_t
+        g = oracle.preprocess(sc, cam, t, temporal_cull=False)
+        assert g["u"][0] == pytest.approx(cam.fx * (X + tau * V[0]) / (Z + tau * V[2]) + cam.cx, abs=1e-12)
+        assert g["v"][0] == pytest.approx(cam.fy * (Y + tau * V[1]) / (Z + tau * V[2]) + cam.cy, abs=1e-12)
+        assert g["depth"][0] == pytest.approx(Z + tau * V[2], abs=1e-14)
+    assert oracle.preprocess(sc, cam, mu_t)["opacity_t"][0] == pytest.approx(o, abs=1e-15)
+    for t in (mu_t + s_t, mu_t - s_t):
+        assert oracle.preprocess(sc, cam, t)["opacity_t"][0] == pytest.approx(o * math.exp(-0.5), abs=1e-15)
+
+
+def test_projection_jacobian_matches_finite_differences():
+    """Sigma' - 0.3 I equals J_fd W Sigma3D W^T J_fd^T with J_fd the central difference of the
+    pinhole map (u, v)(X) (Eq. 14, 16), away from the Jacobian clamp."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(5)
+    R = Rotation.from_rotvec([0.2, -0.3, 0.1]).as_matrix()
+    cam = camera(width=200, height=160, fx=150.0, fy=140.0, R=R, T=[0.1, -0.2, 0.3])
+    n = 30
+    means = np.column_stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5, 0.5, n), rng.uniform(2.5, 5.0, n)])
+    means = (R.T @ (means - cam.T).T).T  # place them in front of the camera
+    q = rng.standard_normal((n, 4))
+    ls = rng.normal(-2.5, 0.4, (n, 3))
+    sc = scene64(means, quats=q, log_scales=ls)
+    g = oracle.preprocess(sc, cam, 0.0)
+    Rc, Tc = cam.R.astype(np.float64), cam.T.astype(np.float64)
+
+    def uv(Xc):
+        return np.array([cam.fx * Xc[0] / Xc[2] + cam.cx, cam.fy * Xc[1] / Xc[2] + cam.cy])
+
+    for i in range(n):
+        Xc = Rc @ means[i] + Tc
+        h = 1e-5
+        J = np.column_stack([(uv(Xc + h * e) - uv(Xc - h * e)) / (2 * h) for e in np.eye(3)])
+        Rq = Rotation.from_quat(np.roll(q[i] / np.linalg.norm(q[i]), -1)).as_matrix()
+        S3 = Rq @ np.diag(np.exp(2 * ls[i])) @ Rq.T
+        ref = J @ Rc @ S3 @ Rc.T @ J.T
+        got = g["cov2d"][i]
+        np.testing.assert_allclose([got[0] - 0.3, got[1], got[2] - 0.3], [ref[0, 0], ref[0, 1], ref[1, 1]],
+                                   rtol=1e-7, atol=1e-9)
+        inv = np.linalg.inv([[got[0], got[1]], [got[1], got[2]]])
+        np.testing.assert_allclose(g["conic"][i], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-12)
+        assert g["lambda_max"][i] >= np.linalg.eigvalsh([[got[0], got[1]], [got[1], got[2]]]).max() - 1e-12
+
+
+def test_composite_golden():
+    """Eq. 4 worked by hand (tests/golden/eq4_composite.json)."""
+    data = json.load(open(os.path.join(GOLDEN, "eq4_composite.json")))
+    cam = camera(width=8, height=8, fx=10.0, fy=10.0, cx=4.5, cy=4.5)
+    for case in data["cases"]:
+        L = case["layers"]
+        sc = scene64([[0.0, 0.0, l["depth"]] for l in L], rgb=[l["rgb"] for l in L],
+                     opacity=[l["opacity"] for l in L])
+        out = oracle.render(sc, cam, 0.0, pixels=[[4, 4]])
+        np.testing.assert_allclose(out["rgb"][0], case["expect_rgb"], atol=1e-12, err_msg=case["name"])
+        assert out["T"][0] == pytest.approx(case["expect_T"], abs=1e-12), case["name"]
+        assert out["ncontrib"][0] == case["expect_ncontrib"], case["name"]
+
+
+def test_radius_factor_covers_alpha_threshold():
+    """3.33^2 > 2 ln 255, so alpha >= 1/255 implies |d| < 3.33 sqrt(lambda_max)."""
+    assert 3.33 ** 2 > 2 * math.log(255.0)
+    assert 3.32 ** 2 < 2 * math.log(255.0)
+
+
+# ---------------------------------------------------------------------------
+# the paper's structural identities
+# ---------------------------------------------------------------------------
+
+def _random_4d(rng, n):
+    """Random SPD 4D covariances R4 S4^2 R4^T (Eq. 5) with R4 from a QR factorisation."""
+    out = []
+    for _ in range(n):
+        Q, Rr = np.linalg.qr(rng.standard_normal((4, 4)))
+        Q = Q * np.sign(np.diag(Rr))
+        s = np.exp(rng.normal([-3.0, -3.0, -3.0, -1.5], 0.3))
+        out.append(Q @ np.diag(s ** 2) @ Q.T)
+    return np.array(out)
+
+
+def test_conditional_slice_identity():
+    """The 4D Gaussian density factorises into the temporal marginal times the conditional 3D
+    Gaussian with Sigma3D = U - V V^T / W and mean mu + (t - mu_t) V / W (Eq. 6-7)."""
+    rng = np.random.default_rng(6)
+    for S4 in _random_4d(rng, 10):
+        mu4 = rng.standard_normal(4)
+        U, V, W = S4[:3, :3], S4[:3, 3], S4[3, 3]
+        inv4 = np.linalg.inv(S4)
+        S3 = U - np.outer(V, V) / W
+        inv3 = np.linalg.inv(S3)
+        for _ in range(5):
+            x, t = mu4[:3] + 0.1 * rng.standard_normal(3), mu4[3] + 0.3 * rng.standard_normal()
+            d4 = np.append(x - mu4[:3], t - mu4[3])
+            lhs = -0.5 * d4 @ inv4 @ d4
+            m3 = mu4[:3] + (t - mu4[3]) * V / W
+            rhs = -0.5 * (t - mu4[3]) ** 2 / W - 0.5 * (x - m3) @ inv3 @ (x - m3)
+            assert lhs == pytest.approx(rhs, rel=1e-9, abs=1e-9)
+
+
+def test_disentangled_equals_slicing_first():
+    """Rendering the disentangled parameters (V3D = V/W, s_t = sqrt W, Sigma3D = U - VV^T/W)
+    equals slicing each 4D Gaussian at t first (Eq. 7) and rendering the static 3D result."""
+    rng = np.random.default_rng(7)
+    n = 60
+    S4 = _random_4d(rng, n)
+    mu = np.column_stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.6, 0.6, n), rng.uniform(2.5, 4.0, n)])
+    mu_t = rng.uniform(0, 1, n)
+    op = 1 / (1 + np.exp(-rng.normal(0, 1, n)))
+    rgb = rng.uniform(0, 1, (n, 3))
+    U, V, W = S4[:, :3, :3], S4[:, :3, 3], S4[:, 3, 3]
+    S3 = U - np.einsum("ni,nj->nij", V, V) / W[:, None, None]
+    cov6 = S3[:, [0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]
+    cam = camera(width=48, height=40, fx=40.0, fy=40.0)
+    for t in (0.1, 0.5, 0.85):
+        dis = scene64(mu, rgb=rgb, opacity=op, velocity=V / W[:, None], t_mean=mu_t,
+                      log_t_scale=0.5 * np.log(W))
+        a = oracle.render(dis, cam, t, cov3d=cov6, temporal_cull=False)
+        m3 = mu + (t - mu_t)[:, None] * V / W[:, None]
+        op_t = op * np.exp(-0.5 * (t - mu_t) ** 2 / W)
+        sl = scene64(m3, rgb=rgb, opacity=op_t, t_mean=np.full(n, t))
+        b = oracle.render(sl, cam, t, cov3d=cov6, temporal_cull=False)
+        np.testing.assert_allclose(a["rgb"], b["rgb"], atol=1e-12)
+        assert np.abs(a["rgb"]).max() > 0.05
+
+
+def test_static_reduction_time_invariant():
+    """V = 0 and s_t -> infinity reduce to static 3DGS: the same image at every t."""
+    w = synth.tiny_workload(200)
+    sc = w.scene
+    st = synth.Scene(**{k: v.copy() for k, v in sc.arrays().items()}, sh_degree=sc.sh_degree)
+    st.velocity[:] = 0
+    st.log_t_scale[:] = 30.0
+    cam = synth.pinhole(64, 64)
+    imgs = [oracle.render(st, cam, t)["rgb"] for t in (0.0, 0.37, 1.0)]
+    assert np.abs(imgs[0]).max() > 0.05
+    for im in imgs[1:]:
+        assert np.array_equal(im, imgs[0])
+
+
+def test_time_shift_equivalence():
+    """Rendering at t equals a static scene whose means are pre-shifted to mu + tau V and whose
+    opacity is pre-multiplied by the temporal factor (Algorithm 1's deferred slice); SH degree 3
+    so the view direction of the shifted mean matters."""
+    sc = synth.make_scene(150, 11, "tiny", sh_degree=3)
+    cam = synth.pinhole(64, 64)
+    t = 0.3
+    a = oracle.render(sc, cam, t, temporal_cull=False)
+    g = a["g2d"]
+    tau = t - sc.t_mean.astype(np.float64)
+    st = synth.Scene(**{k: np.asarray(v, np.float64).copy() for k, v in sc.arrays().items()}, sh_degree=3)
+    st.means = sc.means.astype(np.float64) + tau[:, None] * sc.velocity.astype(np.float64)
+    st.velocity[:] = 0
+    oh = g["opacity_t"]
+    st.opacity_logit = np.log(oh / (1 - oh))
+    st.log_t_scale[:] = 30.0
+    st.t_mean[:] = t
+    b = oracle.render(st, cam, t, temporal_cull=False)
+    np.testing.assert_allclose(a["rgb"], b["rgb"], atol=1e-12)
+    # with the view direction of the *static* mean the images would differ
+    assert np.abs(a["rgb"]).max() > 0.05
+
+
+def test_temporal_cull_is_lossless():
+    """Dropping Gaussians with o_hat < 1/255 cannot change any pixel (alpha < 1/255 everywhere)."""
+    sc = synth.make_scene(400, 12, "tiny")
+    cam = synth.pinhole(64, 64)
+    for t in (0.0, 0.5, 1.0):
+        a = oracle.render(sc, cam, t, temporal_cull=True)
+        b = oracle.render(sc, cam, t, temporal_cull=False)
+        assert a["g2d"]["drawn"].sum() < b["g2d"]["drawn"].sum() or t == 0.5
+        assert np.array_equal(a["rgb"], b["rgb"])
+
+
+def test_transmittance_and_colour_bounds():
+    """1e-4 <= T <= 1 (stop-before-blend), and 0 <= C <= (1 - T) max c (Eq. 4 is a
+    sub-convex combination of the colours)."""
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    out = oracle.render(w.scene, cam, t)
+    T, rgb = out["T"], out["rgb"]
+    assert T.min() >= 1e-4 and T.max() <= 1.0
+    cmax = out["g2d"]["rgb"][out["g2d"]["drawn"]].max()
+    assert rgb.min() >= 0.0
+    assert np.all(rgb <= (1 - T)[..., None] * cmax + 1e-12)
+
+
+def test_transmittance_monotone_in_added_layers():
+    """Adding a Gaussian in front never increases T at any pixel."""
+    sc = synth.make_scene(120, 13, "tiny")
+    cam = synth.pinhole(48, 48)
+    base = oracle.render(sc, cam, 0.5, temporal_cull=False)
+    extra = scene64([[0.05, -0.02, 1.5]], opacity=[0.9], log_scales=[[math.log(0.1)] * 3], t_mean=[0.5])
+    both = synth.Scene(**{k: np.concatenate([np.asarray(getattr(sc, k), np.float64), getattr(extra, k)])
+                          for k in sc.arrays()}, sh_degree=0)
+    more = oracle.render(both, cam, 0.5, temporal_cull=False)
+    assert np.all(more["T"] <= base["T"] + 1e-15)
+    assert (more["T"] < base["T"] - 1e-6).sum() > 10
+
+
+# ---------------------------------------------------------------------------
+# FP32 binning mirror
+# ---------------------------------------------------------------------------
+
+def test_bin_f32_agrees_with_fp64():
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    b = oracle.bin_f32(w.scene, cam, t, 16)
+    g = oracle.preprocess(w.scene, cam, t)
+    ok = b["tiles_touched"] > 0
+    assert ok.sum() > 900
+    assert np.all(g["drawn"][ok])
+    np.testing.assert_allclose(b["uv"][ok, 0], g["u"][ok], atol=1e-3)
+    np.testing.assert_allclose(b["uv"][ok, 1], g["v"][ok], atol=1e-3)
+    depth = b["depth_key"][ok].view(np.float32).astype(np.float64)
+    np.testing.assert_allclose(depth, g["depth"][ok], rtol=1e-6)
+    r64 = np.ceil(3.33 * np.sqrt(g["lambda_max"][ok]))
+    unflagged = b["flags"][ok] == 0
+    assert np.array_equal(b["radius"][ok][unflagged], r64[unflagged].astype(np.int32))
+    rect = b["rect"][ok]
+    assert np.array_equal(b["tiles_touched"][ok], ((rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)))
+
+
+def test_tile_rect_covers_alpha_support():
+    """Every pixel where a Gaussian's FP64 alpha reaches 1/255 lies in a tile of its FP32 rect."""
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    tile = 16
+    b = oracle.bin_f32(w.scene, cam, t, tile)
+    g = oracle.preprocess(w.scene, cam, t)
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    px, py = xs.ravel() + 0.5, ys.ravel() + 0.5
+    tx, ty = xs.ravel() // tile, ys.ravel() // tile
+    checked = 0
+    for i in np.nonzero(g["drawn"])[0]:
+        a, bb, c = g["conic"][i]
+        dx, dy = g["u"][i] - px, g["v"][i] - py
+        p = -0.5 * (a * dx * dx + c * dy * dy) - bb * dx * dy
+        alpha = np.minimum(0.99, g["opacity_t"][i] * np.exp(np.minimum(p, 0)))
+        hit = (p <= 0) & (alpha >= 1 / 255)
+        if not hit.any():
+            continue
+        assert b["tiles_touched"][i] > 0
+        x0, x1, y0, y1 = b["rect"][i]
+        assert np.all((tx[hit] >= x0) & (tx[hit] <= x1) & (ty[hit] >= y0) & (ty[hit] <= y1)), i
+        checked += 1
+    assert checked > 900
+
+
+def test_tile_list_sorted_and_ranges():
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    b = oracle.bin_f32(w.scene, cam, t, 16)
+    L = oracle.tile_list(b)
+    key = (L["tile"].astype(np.uint64) << np.uint64(32)) | L["depth"].astype(np.uint64)
+    assert np.all(np.diff(key.astype(np.float64)) >= 0) or np.all(key[1:] >= key[:-1])
+    assert len(L["tile"]) == int(b["tiles_touched"].sum())
+    r = L["ranges"]
+    assert r[0, 0] == 0 and r[-1, 1] == len(L["tile"])
+    assert np.all(r[1:, 0] == r[:-1, 1])
+    for tid in range(len(r)):
+        assert np.all(L["tile"][r[tid, 0]:r[tid, 1]] == tid)
