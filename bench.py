@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Frame-render benchmark of the disentangled 4D Gaussian renderer.
+
+Workload: the seeded synthetic scene shaped like the paper's Plenoptic Video
+setting -- 300,000 dynamic Gaussians with SH degree 3 in a 20-unit box,
+1352x1014 pixels, a smooth 300-timestamp camera orbit (t_k = k/299).  One
+step = one whole frame (preprocess, binning sort, blend) at the next orbit
+pose and timestamp.  ``value`` is frames/s of the whole job (N GPUs render
+independent frames: replicas, weak scaling); device time from CUDA events on
+the launching stream, L2 flushed (256 MiB write) before every frame, outside
+the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(FP64 brute force, all host cores) on a bounded sample of the same frames.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s at 1352x1014, 300k Gaussians; served p50/p99 ms vs per-frame loop"
+FP32_OPS_PER_EVAL = 14      # dx, dy, quadratic form (5), exp (2), opacity product, min, two compares, skip test
+FP32_OPS_PER_BLEND = 7      # 1 - alpha, T (1 - alpha), stop compare, alpha T, three colour FMAs
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["scene", "tiny", "large"], default="scene")
+    p.add_argument("--tile", type=int, default=16)
+    p.add_argument("--batch", type=int, default=256)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    return p.parse_args()
+
+
+def workload(name):
+    import synth
+    if name == "tiny":
+        w = synth.tiny_workload()
+        w.frames = w.frames * 300
+        return w
+    if name == "large":
+        return synth.large_workload()
+    return synth.scene_workload()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_selector(dev, local: int) -> str:
+    """nvidia-smi -i argument for this process's device (UUID when torch knows it)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local)
+
+
+def traffic_for(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
+    taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        ent = data[kernel]
+        src = os.path.join(ROOT, ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != ent["source_sha"]:
+            return None
+        return ent["bytes_per_launch_full"]
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+
+def oracle_frame_sample(scene, cam, t, budget_s: float):
+    """FP64 oracle on one frame: full preprocess + brute-force compositing of a
+    band of pixel rows sized to ~budget_s; returns the extrapolated frame time."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    g = oracle.preprocess(scene, cam, t)
+    t_pre = time.perf_counter() - t0
+    W, H = cam.width, cam.height
+    r0 = H // 2
+    pix = np.column_stack([np.arange(W), np.full(W, r0)])
+    t0 = time.perf_counter()
+    oracle.render_g2d(g, cam, pixels=pix)
+    t_row = max(time.perf_counter() - t0, 1e-6)
+    rows = int(max(1, min(H - 1, round(max(budget_s - t_pre - t_row, 0.0) / t_row))))
+    pix = np.column_stack([np.tile(np.arange(W), rows), np.repeat(np.arange(r0 + 1 - rows // 2, r0 + 1 - rows // 2 + rows), W)])
+    pix[:, 1] = np.clip(pix[:, 1], 0, H - 1)
+    t0 = time.perf_counter()
+    oracle.render_g2d(g, cam, pixels=pix)
+    t_rows = time.perf_counter() - t0
+    total_rows = rows + 1
+    frame_s = t_pre + (t_rows + t_row) * H / total_rows
+    return frame_s, dict(rows=total_rows, height=H, t_pre=t_pre, t_rows=t_rows + t_row, n=scene.n)
+
+
+def cpu_baseline(w, frame_idx: int, budget_s: float):
+    import oracle
+    cam, t = w.frames[frame_idx]
+    frame_s, info = oracle_frame_sample(w.scene, cam, t, budget_s)
+    return {"value": 1.0 / frame_s, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"frame {frame_idx}: FP64 preprocess of all {info['n']} Gaussians "
+                       f"({info['t_pre']:.2f} s) + per-pixel brute force over all Gaussians for "
+                       f"{info['rows']} of {info['height']} pixel rows ({info['t_rows']:.2f} s), "
+                       f"extrapolated to the full frame")}
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = workload(args.workload)
+    steps, warm = args.steps, args.warmup
+    per_step = max(0.5, 150.0 / max(1, steps + warm))
+    nf = len(w.frames)
+    frame_times = []
+    for k in range(warm + steps):
+        cam, t = w.frames[k % nf]
+        fs, info = oracle_frame_sample(w.scene, cam, t, per_step)
+        if k >= warm:
+            frame_times.append(fs)
+    total = sum(frame_times)
+    value = steps / total
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * total / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(w, args),
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": (f"each step: one orbit frame, FP64 preprocess of all Gaussians + brute-force "
+                                    f"compositing of a band of pixel rows sized to ~{per_step:.1f} s, "
+                                    f"extrapolated to the full frame")},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(w, args):
+    cam, _ = w.frames[0]
+    return {"workload": w.name, "gaussians": w.scene.n, "sh_degree": w.scene.sh_degree, "width": cam.width,
+            "height": cam.height, "timestamps": len(w.frames), "tile": args.tile, "batch": args.batch,
+            "l2": "flushed before every frame (256 MiB write, outside the timed events)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_info()
+    w = workload(args.workload)
+    nf = len(w.frames)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, nf // 2, args.cpu_seconds)   # before the first CUDA call
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_22159_gb300 as d4
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    stream = torch.cuda.current_stream(dev)
+    scene = d4.DeviceScene.from_host(w.scene, dev)
+    cfg = d4.config_struct(args.tile, args.batch)
+    cam0 = w.frames[0][0]
+    K, W = args.steps, args.warmup
+    order = [(rank + world * k) % nf for k in range(W + K)]
+
+    # size the key capacity on this rank's frames (untimed)
+    r = d4.Renderer(scene.n, cam0, tile=args.tile, batch=args.batch, key_capacity=64 * scene.n, device=dev)
+    max_keys = 0
+    for fi in sorted(set(order)):
+        cam, t = w.frames[fi]
+        r.render(scene, cam, t)
+        max_keys = max(max_keys, int(r.stats(cam)["n_keys"]))
+    r._alloc(int(max_keys * 1.02) + 4096)
+    out = torch.empty((cam0.height, cam0.width, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    launches = d4.d4dgs_launches_per_frame(scene.n, cam0, cfg)
+
+    def frame(fi, ev=None):
+        cam, t = w.frames[fi]
+        if ev:
+            ev[0].record(stream)
+        d4.d4dgs_preprocess(scene, cam, t, cfg, r.ws, stream)
+        if ev:
+            ev[1].record(stream)
+        d4.d4dgs_sort(scene.n, cam, cfg, r.ws, stream)
+        if ev:
+            ev[2].record(stream)
+        d4.d4dgs_blend(scene.n, cam, cfg, r.ws, out, stream)
+        if ev:
+            ev[3].record(stream)
+
+    for k in range(W):
+        flush.fill_(k & 255)
+        frame(order[k])
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    clocks = ClockSampler(gpu_selector(dev, local))
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for k in range(K):
+        flush.fill_((k + 1) & 255)
+        frame(order[W + k], events[k])
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    stage = np.array([[events[k][i].elapsed_time(events[k][i + 1]) for i in range(3)] for k in range(K)])
+    step_ms = stage.sum(axis=1)
+    elapsed = float(step_ms.sum())
+    if pg:
+        t = torch.tensor([elapsed], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed = float(t.item())
+    # status of the last frame (every frame was sized beforehand)
+    st = r.stats(w.frames[order[-1]][0])
+    if st["status"] != 0:
+        raise RuntimeError(f"frame reported {d4._abi.strerror(st['status'])}")
+
+    # instrumented blend counts on the same frames (untimed) -> ALU roofline of the blend
+    counts = torch.zeros(2, dtype=torch.int64, device=dev)
+    evals = blends = 0
+    nkeys = []
+    for k in range(K):
+        fi = order[W + k]
+        cam, t = w.frames[fi]
+        d4.d4dgs_preprocess(scene, cam, t, cfg, r.ws, stream)
+        d4.d4dgs_sort(scene.n, cam, cfg, r.ws, stream)
+        d4.d4dgs_blend_profile(scene.n, cam, cfg, r.ws, out, counts, stream)
+        c = counts.cpu().numpy()
+        evals += int(c[0])
+        blends += int(c[1])
+        nkeys.append(int(r.stats(cam)["n_keys"]))
+
+    peaks, peak_kind = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_mhz = clk["sm_mhz"] if clk else peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
+    blend_ms = float(stage[:, 2].sum())
+    alu_ops = FP32_OPS_PER_EVAL * evals + FP32_OPS_PER_BLEND * blends
+    alu_achieved = alu_ops / (blend_ms * 1e-3) / 1e12
+    alu_peak = sms * 128 * sm_mhz * 1e6 / 1e12
+    pre_ms = float(stage[:, 0].sum()) / K
+    sort_ms = float(stage[:, 1].sum()) / K
+    shares = {"preprocess": float(stage[:, 0].sum()) / elapsed, "sort": float(stage[:, 1].sum()) / elapsed,
+              "blend": blend_ms / elapsed}
+    n = scene.n
+    sh_bytes = 4 * 3 * (w.scene.sh_degree + 1) ** 2
+    pre_bytes = n * (64 + sh_bytes + 64)     # params + SH read, 48 B record + key, count, rect written
+    roof_blend = {"kernel": "blend_kernel", "bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                  "unit": "TOP/s (FP32 lane ops)", "frac": alu_achieved / alu_peak,
+                  "traffic": traffic_for("blend_kernel"),
+                  "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock of this run)",
+                  "ops": f"{FP32_OPS_PER_EVAL} per evaluated (pixel, Gaussian) pair + {FP32_OPS_PER_BLEND} per blended pair",
+                  "evaluated_pairs_per_frame": evals / K, "blended_pairs_per_frame": blends / K}
+    roof_pre = {"kernel": "preprocess_kernel", "bound": "hbm",
+                "achieved": pre_bytes / (pre_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": pre_bytes / (pre_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "traffic": traffic_for("preprocess_kernel")}
+    ms_per_step = elapsed / K
+    value = world * K / (elapsed * 1e-3)
+
+    # end to end through the host-buffer entry point (H2D of the scene, D2H of the image)
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).pin_memory() for k in d4.SCENE_FIELDS}
+        host["sh_degree"] = w.scene.sh_degree
+        dbuf = torch.empty(d4.d4dgs_scene_bytes(n, w.scene.sh_degree), dtype=torch.uint8, device=dev)
+        himg = torch.empty((cam0.height, cam0.width, 3), dtype=torch.float32).pin_memory()
+        h2d = sum(int(v.numel() * v.element_size()) for k, v in host.items() if k != "sh_degree")
+        d2h = int(himg.numel() * 4)
+        E = args.e2e_steps
+        for k in range(2):
+            cam, t = w.frames[order[k]]
+            d4.d4dgs_render_host(host, cam, t, cfg, dbuf, r.ws, out, himg, stream)
+        t0 = time.perf_counter()
+        for k in range(E):
+            cam, t = w.frames[order[(W + k) % len(order)]]
+            d4.d4dgs_render_host(host, cam, t, cfg, dbuf, r.ws, out, himg, stream)
+        te = time.perf_counter() - t0
+        if pg:
+            tt = torch.tensor([te], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": world * E / te, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": E, "api": "d4dgs_render_host"}
+
+    if rank != 0:
+        return 0
+    dominant = roof_blend if shares["blend"] >= shares["preprocess"] else roof_pre
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": config_dict(w, args),
+        "roofline": dominant,
+        "roofline_preprocess": roof_pre,
+        "stages_ms": {"preprocess": pre_ms, "sort": sort_ms, "blend": blend_ms / K, "shares": shares},
+        "keys_per_frame": {"mean": float(np.mean(nkeys)), "max": int(np.max(nkeys))},
+        "gpu_launches": int(launches * K), "launches_per_frame": launches,
+        "wall_s_timed_region": t_wall, "peaks": peak_kind,
+        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

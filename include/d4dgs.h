@@ -1,0 +1,212 @@
+/*
+ * d4dgs.h -- C ABI of the GB300 (sm_103a) renderer for disentangled 4D
+ * Gaussian splatting (Feng et al., "Disentangled 4D Gaussian Splatting",
+ * arXiv 2503.22159).
+ *
+ * The library renders one frame of a dynamic scene at time t: the temporal
+ * terms of every Gaussian are applied in the paper's deferred, disentangled
+ * form (a time-shifted mean and a temporally modulated opacity, Sec. III-B-1,
+ * Eq. 7-8), the Gaussian is projected to a dynamic 2D Gaussian (Sec.
+ * III-B-2, Eq. 9-16; Algorithm 1), binned into screen tiles by (tile | depth)
+ * keys and alpha-composited front to back per pixel (Sec. III-A, Eq. 4; the
+ * 3DGS "fast rasterization" the paper reuses).
+ *
+ * Conventions shared by every entry point
+ *   - All array pointers are DEVICE pointers owned by the caller (except the
+ *     *_host entry points, which take host pointers).  The library never
+ *     allocates device memory inside a call; scratch lives in a caller-owned
+ *     workspace whose size d4dgs_workspace_bytes() returns.
+ *   - Calls are asynchronous and stream-ordered on `stream`.  Argument errors
+ *     are returned at call time.  Errors found on the device (key capacity
+ *     exceeded, a bounded spin-wait that gave up) are latched in a status word
+ *     inside the workspace and reported by d4dgs_read_stats() after the stream
+ *     has been synchronised.
+ *   - Parameters are raw (pre-activation): scales and temporal scale as logs,
+ *     opacity as a logit, quaternions (w,x,y,z) not necessarily normalised.
+ *   - Thread safety: calls on different workspaces may run concurrently; two
+ *     calls in flight on the same workspace race.
+ *   - Return value: D4DGS_OK (0) or a negative D4DGS_ERR_* code.
+ */
+#ifndef D4DGS_H
+#define D4DGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *d4dgs_stream_t;
+
+enum {
+    D4DGS_OK = 0,
+    D4DGS_ERR_INVALID_ARG = -1,          /* a pointer, size or enum out of range */
+    D4DGS_ERR_WORKSPACE_TOO_SMALL = -2,  /* ws_bytes below what the call needs */
+    D4DGS_ERR_CAPACITY = -3,             /* more (tile, Gaussian) keys than the workspace holds */
+    D4DGS_ERR_TIMEOUT = -4,              /* a bounded spin-wait on the device gave up */
+    D4DGS_ERR_CUDA = -5                  /* a CUDA runtime call or launch failed */
+};
+
+/* Per-Gaussian raw parameters, structure of arrays, float32, N rows each.
+ * This is the paper's disentangled parameter set (Eq. 8): 4D scale (three
+ * log spatial scales + log temporal scale s_t), 4D mean (mu_xyz, mu_t),
+ * quaternion q and velocity V3D, plus the 3DGS opacity and SH colour. */
+typedef struct {
+    const float *means;          /* N x 3 : mu_x, mu_y, mu_z                        */
+    const float *t_mean;         /* N     : mu_t                                    */
+    const float *velocity;       /* N x 3 : V3D = V / W (Sec. III-B-1)              */
+    const float *log_scales;     /* N x 3 : log s_x, log s_y, log s_z               */
+    const float *log_t_scale;    /* N     : log s_t, s_t = sqrt(W)                  */
+    const float *quats;          /* N x 4 : (w, x, y, z), any non-zero norm         */
+    const float *opacity_logit;  /* N     : sigmoid gives the 3DGS opacity          */
+    const float *sh;             /* N x (deg+1)^2 x 3 : real SH coefficients, RGB   */
+    int32_t n;                   /* N >= 0                                          */
+    int32_t sh_degree;           /* 0..3                                            */
+} d4dgs_scene;
+
+/* Gradients with respect to the raw parameters, same shapes as d4dgs_scene,
+ * device float32, caller-owned; every array is overwritten. */
+typedef struct {
+    float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
+} d4dgs_scene_grad;
+
+/* Pinhole camera (Algorithm 1 inputs P_camera, R_camera).  World -> camera
+ * X_cam = R X_world + T, R row-major; the camera looks along +z, x right,
+ * y down; u = fx X/Z + cx, v = fy Y/Z + cy; pixel (x, y) has its centre at
+ * (x + 0.5, y + 0.5). */
+typedef struct {
+    float R[9];
+    float T[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;       /* 1 .. 16384 */
+} d4dgs_camera;
+
+/* Rasteriser settings.  tile: 8, 16 or 32 pixels; batch: Gaussians staged
+ * per shared-memory batch in the blend, 64, 128 or 256 (<= tile*tile);
+ * bg: background colour added with the final transmittance. */
+typedef struct {
+    int32_t tile;
+    int32_t batch;
+    float bg[3];
+} d4dgs_config;
+
+/* Counters read back after a frame (host struct). */
+typedef struct {
+    int32_t status;              /* D4DGS_OK or the first device-side error      */
+    int64_t n_keys;              /* total (tile, Gaussian) pairs of the frame     */
+    int64_t key_capacity;        /* pairs the workspace can hold                  */
+    int64_t n_visible;           /* Gaussians that touch at least one tile        */
+} d4dgs_stats;
+
+/* Byte offsets of the workspace buffers (test and profiling hook).  All
+ * offsets are from the workspace base; buffers are 256-byte aligned. */
+typedef struct {
+    int64_t records;             /* N x 12 float: (u,v,a,b) (c,o_hat,depth,radius) (r,g,b,0) */
+    int64_t depth_keys;          /* N uint32: float bits of camera z, 0xFFFFFFFF if culled   */
+    int64_t tiles_touched;       /* N uint32                                                 */
+    int64_t rect;                /* N x 4 uint16: x0, x1, y0, y1 (inclusive tile indices)    */
+    int64_t depth_order;         /* N uint32: Gaussian ids sorted by (depth key, id)         */
+    int64_t tile_keys;           /* key_capacity uint32: tile id of each pair, sorted         */
+    int64_t tile_vals;           /* key_capacity uint32: Gaussian id of each pair, sorted     */
+    int64_t ranges;              /* tiles x 2 uint32: [start, end) of each tile's list        */
+    int64_t final_T;             /* H x W float: transmittance after the last blend           */
+    int64_t n_contrib;           /* H x W uint32: list positions walked up to the last blend  */
+    int64_t control;             /* device status word and counters                           */
+    int64_t key_capacity;
+    int32_t tiles_x, tiles_y;
+    int32_t depth_passes, tile_passes;
+} d4dgs_layout;
+
+/* Bytes of workspace for N Gaussians, this camera and config, and room for
+ * key_capacity (tile, Gaussian) pairs.  Returns 0 on invalid arguments. */
+size_t d4dgs_workspace_bytes(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, int64_t key_capacity);
+
+/* Layout of a workspace of ws_bytes for (n, cam, cfg); the key capacity is
+ * whatever fits.  Returns D4DGS_ERR_WORKSPACE_TOO_SMALL if not even zero
+ * keys fit. */
+int d4dgs_workspace_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, size_t ws_bytes,
+                           d4dgs_layout *out);
+
+/* Stage 1 -- per-Gaussian preprocess at time t (Algorithm 1: the camera
+ * transform of the mean and velocity, the deferred temporal slice
+ * P_view,t = P_view + tau V_view with tau = t - mu_t (Eq. 7, 15), the
+ * temporal opacity factor exp(-tau^2 / (2 s_t^2)) (Eq. 6), projection of
+ * the mean (Eq. 12) and of the covariance Sigma' = J W Sigma3D W^T J^T + 0.3 I
+ * (Eq. 14, 16), the conic, the tile rectangle of radius
+ * ceil(3.33 sqrt(lambda_max)), the depth key and the SH colour in the
+ * direction of the time-shifted mean).  Writes the 2D records, depth keys,
+ * tile counts and rectangles into the workspace; resets the workspace's
+ * status word and counters for a new frame. */
+int d4dgs_preprocess(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                     void *ws, size_t ws_bytes, d4dgs_stream_t stream);
+
+/* Stage 2 -- binning of the preprocessed frame (the 3DGS fast rasteriser's
+ * tile/depth ordering, Sec. III-B-2): onesweep radix sort of the depth keys,
+ * exclusive scan of the tile counts in depth order fused with the
+ * duplication of one (tile, Gaussian) pair per covered tile, onesweep radix
+ * sort of the pairs by tile (stable, so each tile's list stays in
+ * (depth, id) order) and per-tile [start, end) ranges. */
+int d4dgs_sort(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
+               d4dgs_stream_t stream);
+
+/* Stage 3 -- per-pixel front-to-back alpha compositing over the tile's
+ * list (Eq. 4 with alpha = min(0.99, o_hat exp(p)), p = -1/2 d^T conic d,
+ * skip alpha < 1/255, stop before blending once T (1 - alpha) < 1e-4).
+ * out_rgb: H x W x 3 float32 device, caller-owned, overwritten with
+ * C + T bg; also stores T and the list position of the last blend per pixel
+ * in the workspace for the backward pass. */
+int d4dgs_blend(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
+                float *out_rgb, d4dgs_stream_t stream);
+
+/* Profiling variant of d4dgs_blend: the same compositing, plus the totals of
+ * (pixel, Gaussian) pairs evaluated (counts[0]) and blended (counts[1]) over
+ * the frame, accumulated into `counts` (2 x uint64 DEVICE memory,
+ * caller-owned, zeroed by the call).  Slower than d4dgs_blend; used to turn
+ * a blend time into an FP32 throughput. */
+int d4dgs_blend_profile(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
+                        float *out_rgb, uint64_t *counts, d4dgs_stream_t stream);
+
+/* Stages 1-3 in order: one frame of `scene` seen by `cam` at time t
+ * (Algorithm 1 for one timestamp). */
+int d4dgs_render(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                 void *ws, size_t ws_bytes, float *out_rgb, d4dgs_stream_t stream);
+
+/* Backward of d4dgs_render (Sec. III-B-2, "differentiable projection-first
+ * splatting"): given dL/dC (H x W x 3 float32 device) and the workspace of
+ * the forward call with the same scene, camera, t and config, writes
+ * dL/d(raw parameters) into `grad` (overwritten).  The per-tile lists are
+ * replayed back to front from the stored final T; no per-pixel lists are
+ * kept. */
+int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                          void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
+                          d4dgs_stream_t stream);
+
+/* Synchronises `stream`, then copies the status word and counters of the
+ * last frame rendered in `ws` into *out (host).  Returns out->status. */
+int d4dgs_read_stats(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, const void *ws,
+                     size_t ws_bytes, d4dgs_stats *out, d4dgs_stream_t stream);
+
+/* d4dgs_render with HOST inputs and output: copies the scene (host arrays,
+ * same layout as d4dgs_scene, ideally pinned) into the device staging area
+ * `dev_scene_buf` (at least d4dgs_scene_bytes(n, deg) bytes, caller-owned),
+ * renders, and copies the image back into host `out_rgb_host`; all on
+ * `stream`, and the call returns after the stream has finished. */
+size_t d4dgs_scene_bytes(int32_t n, int32_t sh_degree);
+int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                      void *dev_scene_buf, size_t dev_scene_bytes, void *ws, size_t ws_bytes,
+                      void *dev_rgb, float *out_rgb_host, d4dgs_stream_t stream);
+
+/* Number of kernel launches one d4dgs_render issues for (n, cam, cfg) (the
+ * launch count of a frame, not counting memsets). */
+int d4dgs_launches_per_frame(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg);
+
+/* Human-readable text of a status code (static storage). */
+const char *d4dgs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* D4DGS_H */

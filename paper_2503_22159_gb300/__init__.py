@@ -1,0 +1,223 @@
+"""GB300-native (sm_103a) renderer for disentangled 4D Gaussian splatting.
+
+Thin Python binding over the C ABI of ``include/d4dgs.h`` (libd4dgs.so).
+PyTorch provides device memory and the current CUDA stream; every step of the
+frame runs in the library's own kernels.  The functions keep the C names:
+
+    d4dgs_workspace_bytes, d4dgs_workspace_layout, d4dgs_preprocess,
+    d4dgs_sort, d4dgs_blend, d4dgs_render, d4dgs_render_backward,
+    d4dgs_read_stats, d4dgs_render_host, d4dgs_launches_per_frame
+
+plus two conveniences: :class:`DeviceScene` (the scene's arrays as device
+tensors) and :class:`Renderer` (workspace ownership and key-capacity sizing).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import (D4DGS_ERR_CAPACITY, D4DGS_ERR_CUDA, D4DGS_ERR_INVALID_ARG, D4DGS_ERR_TIMEOUT,
+                   D4DGS_ERR_WORKSPACE_TOO_SMALL, D4DGS_OK, D4DGSError)
+
+SCENE_FIELDS = ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh")
+
+__all__ = ["DeviceScene", "Renderer", "camera_struct", "config_struct", "d4dgs_workspace_bytes",
+           "d4dgs_workspace_layout", "d4dgs_preprocess", "d4dgs_sort", "d4dgs_blend", "d4dgs_blend_profile",
+           "d4dgs_render",
+           "d4dgs_render_backward", "d4dgs_read_stats", "d4dgs_render_host", "d4dgs_launches_per_frame",
+           "D4DGSError", "D4DGS_OK", "D4DGS_ERR_CAPACITY", "D4DGS_ERR_TIMEOUT", "D4DGS_ERR_INVALID_ARG",
+           "D4DGS_ERR_WORKSPACE_TOO_SMALL", "D4DGS_ERR_CUDA"]
+
+
+def _stream_handle(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+class DeviceScene:
+    """The raw parameters of one scene as contiguous float32 device tensors."""
+
+    def __init__(self, tensors: dict, sh_degree: int):
+        self.t = {k: tensors[k] for k in SCENE_FIELDS}
+        self.sh_degree = int(sh_degree)
+        self.n = int(self.t["means"].shape[0])
+        for k, v in self.t.items():
+            if v.dtype != torch.float32 or not v.is_contiguous() or not v.is_cuda:
+                raise ValueError(f"scene field {k} must be a contiguous float32 CUDA tensor")
+
+    @classmethod
+    def from_host(cls, scene, device="cuda") -> "DeviceScene":
+        """From any object with the SCENE_FIELDS arrays (e.g. synth.Scene)."""
+        t = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), dtype=np.float32)).to(device)
+             for k in SCENE_FIELDS}
+        return cls(t, scene.sh_degree)
+
+    def struct(self) -> _abi.d4dgs_scene:
+        s = _abi.d4dgs_scene(*[self.t[k].data_ptr() for k in SCENE_FIELDS], self.n, self.sh_degree)
+        return s
+
+    def zeros_like_grad(self) -> dict:
+        return {k: torch.zeros_like(v) for k, v in self.t.items()}
+
+
+def camera_struct(cam) -> _abi.d4dgs_camera:
+    c = _abi.d4dgs_camera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float32).reshape(9)]
+    c.T[:] = [float(x) for x in np.asarray(cam.T, np.float32).reshape(3)]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0)) -> _abi.d4dgs_config:
+    g = _abi.d4dgs_config()
+    g.tile, g.batch = int(tile), int(batch)
+    g.bg[:] = [float(x) for x in bg]
+    return g
+
+
+def d4dgs_workspace_bytes(n: int, cam, cfg, key_capacity: int) -> int:
+    b = _abi.load().d4dgs_workspace_bytes(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg),
+                                          int(key_capacity))
+    if b == 0:
+        raise D4DGSError(D4DGS_ERR_INVALID_ARG, "d4dgs_workspace_bytes")
+    return int(b)
+
+
+def d4dgs_workspace_layout(n: int, cam, cfg, ws_bytes: int) -> dict:
+    L = _abi.d4dgs_layout()
+    _abi.check(_abi.load().d4dgs_workspace_layout(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg),
+                                                  int(ws_bytes), ctypes.byref(L)), "d4dgs_workspace_layout")
+    return {k: getattr(L, k) for k, _ in L._fields_}
+
+
+def _ws(ws: torch.Tensor):
+    if ws.dtype != torch.uint8 or not ws.is_cuda or not ws.is_contiguous():
+        raise ValueError("workspace must be a contiguous uint8 CUDA tensor")
+    return ctypes.c_void_p(ws.data_ptr()), ws.numel()
+
+
+def d4dgs_preprocess(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tensor, stream=None):
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_preprocess(ctypes.byref(scene.struct()), ctypes.byref(camera_struct(cam)),
+                                            float(t), ctypes.byref(cfg), p, nb, _stream_handle(stream)),
+               "d4dgs_preprocess")
+
+
+def d4dgs_sort(n: int, cam, cfg, ws: torch.Tensor, stream=None):
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_sort(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg), p, nb,
+                                      _stream_handle(stream)), "d4dgs_sort")
+
+
+def d4dgs_blend(n: int, cam, cfg, ws: torch.Tensor, out: torch.Tensor, stream=None):
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_blend(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg), p, nb,
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "d4dgs_blend")
+
+
+def d4dgs_blend_profile(n: int, cam, cfg, ws: torch.Tensor, out: torch.Tensor, counts: torch.Tensor, stream=None):
+    """Instrumented blend: also totals the evaluated and blended (pixel, Gaussian) pairs into
+    ``counts`` (a 2-element int64 CUDA tensor)."""
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_blend_profile(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg), p, nb,
+                                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(counts.data_ptr()),
+                                               _stream_handle(stream)), "d4dgs_blend_profile")
+
+
+def d4dgs_render(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tensor, out: torch.Tensor, stream=None):
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_render(ctypes.byref(scene.struct()), ctypes.byref(camera_struct(cam)), float(t),
+                                        ctypes.byref(cfg), p, nb, ctypes.c_void_p(out.data_ptr()),
+                                        _stream_handle(stream)), "d4dgs_render")
+
+
+def d4dgs_render_backward(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tensor, dl_drgb: torch.Tensor,
+                          grads: dict, stream=None):
+    p, nb = _ws(ws)
+    g = _abi.d4dgs_scene_grad(*[grads[k].data_ptr() for k in SCENE_FIELDS])
+    _abi.check(_abi.load().d4dgs_render_backward(ctypes.byref(scene.struct()), ctypes.byref(camera_struct(cam)),
+                                                 float(t), ctypes.byref(cfg), p, nb,
+                                                 ctypes.c_void_p(dl_drgb.data_ptr()), ctypes.byref(g),
+                                                 _stream_handle(stream)), "d4dgs_render_backward")
+
+
+def d4dgs_read_stats(n: int, cam, cfg, ws: torch.Tensor, stream=None) -> dict:
+    p, nb = _ws(ws)
+    s = _abi.d4dgs_stats()
+    _abi.load().d4dgs_read_stats(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg), p, nb,
+                                 ctypes.byref(s), _stream_handle(stream))
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def d4dgs_scene_bytes(n: int, sh_degree: int) -> int:
+    return int(_abi.load().d4dgs_scene_bytes(int(n), int(sh_degree)))
+
+
+def d4dgs_render_host(host_scene, cam, t: float, cfg, dev_scene_buf: torch.Tensor, ws: torch.Tensor,
+                      dev_rgb: torch.Tensor, out_host: torch.Tensor, stream=None):
+    """Render from HOST scene arrays (torch CPU tensors, ideally pinned) into a host image; the
+    host->device copies, the frame and the device->host copy all run inside the call."""
+    s = _abi.d4dgs_scene(*[host_scene[k].data_ptr() for k in SCENE_FIELDS], int(host_scene["means"].shape[0]),
+                         int(host_scene["sh_degree"]))
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_render_host(ctypes.byref(s), ctypes.byref(camera_struct(cam)), float(t),
+                                             ctypes.byref(cfg), ctypes.c_void_p(dev_scene_buf.data_ptr()),
+                                             dev_scene_buf.numel(), p, nb, ctypes.c_void_p(dev_rgb.data_ptr()),
+                                             ctypes.c_void_p(out_host.data_ptr()), _stream_handle(stream)),
+               "d4dgs_render_host")
+
+
+def d4dgs_launches_per_frame(n: int, cam, cfg) -> int:
+    return int(_abi.load().d4dgs_launches_per_frame(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg)))
+
+
+class Renderer:
+    """Owns a workspace for (N, camera size, tile, batch) and grows its key
+    capacity when a frame reports D4DGS_ERR_CAPACITY."""
+
+    def __init__(self, n: int, cam, tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0),
+                 key_capacity: int | None = None, device="cuda"):
+        self.n, self.device = int(n), torch.device(device)
+        self.cfg = config_struct(tile, batch, bg)
+        self.width, self.height = int(cam.width), int(cam.height)
+        self.cam0 = cam
+        cap = key_capacity if key_capacity is not None else max(1 << 16, 16 * self.n)
+        self._alloc(cap)
+
+    def _alloc(self, cap: int):
+        self.key_capacity = int(min(cap, (1 << 30) - 1))
+        nbytes = d4dgs_workspace_bytes(self.n, self.cam0, self.cfg, self.key_capacity)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def layout(self, cam=None) -> dict:
+        return d4dgs_workspace_layout(self.n, cam or self.cam0, self.cfg, self.ws.numel())
+
+    def render(self, scene: DeviceScene, cam, t: float, out: torch.Tensor | None = None, check: bool = True,
+               stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device=self.device)
+        for _ in range(8):
+            d4dgs_render(scene, cam, t, self.cfg, self.ws, out, stream)
+            if not check:
+                return out
+            st = d4dgs_read_stats(self.n, cam, self.cfg, self.ws, stream)
+            if st["status"] == D4DGS_ERR_CAPACITY:
+                self._alloc(int(st["n_keys"] * 1.25) + 1024)
+                continue
+            if st["status"] != D4DGS_OK:
+                raise D4DGSError(st["status"], "render")
+            return out
+        raise D4DGSError(D4DGS_ERR_CAPACITY, "render")
+
+    def stats(self, cam=None, stream=None) -> dict:
+        return d4dgs_read_stats(self.n, cam or self.cam0, self.cfg, self.ws, stream)
+
+    def view(self, name: str, dtype, count: int, cam=None) -> torch.Tensor:
+        """A typed view of one workspace buffer (test and profiling hook)."""
+        off = self.layout(cam)[name]
+        itemsize = torch.empty((), dtype=dtype).element_size()
+        return self.ws[off: off + count * itemsize].view(dtype)

@@ -1,0 +1,321 @@
+// api.cu -- the C ABI (include/d4dgs.h): workspace layout, argument checks,
+// stage sequencing on the caller's stream, status readback.
+#include <math.h>
+#include <string.h>
+
+#include "d4dgs_internal.cuh"
+
+namespace d4dgs {
+
+namespace {
+
+int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+int ceil_log2(int64_t v) {
+    int b = 0;
+    while (((int64_t)1 << b) < v) b++;
+    return b;
+}
+
+bool valid_camera(const d4dgs_camera *c) {
+    if (!c) return false;
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384) return false;
+    for (int i = 0; i < 9; i++)
+        if (!isfinite(c->R[i])) return false;
+    for (int i = 0; i < 3; i++)
+        if (!isfinite(c->T[i])) return false;
+    if (!isfinite(c->fx) || !isfinite(c->fy) || !isfinite(c->cx) || !isfinite(c->cy)) return false;
+    return c->fx > 0.0f && c->fy > 0.0f;
+}
+
+bool valid_config(const d4dgs_config *g) {
+    if (!g) return false;
+    if (g->tile != 8 && g->tile != 16 && g->tile != 32) return false;
+    if (g->batch != 64 && g->batch != 128 && g->batch != 256) return false;
+    for (int i = 0; i < 3; i++)
+        if (!isfinite(g->bg[i])) return false;
+    return true;
+}
+
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+int check_scene(const d4dgs_scene *s) {
+    if (!s || s->n < 0 || s->sh_degree < 0 || s->sh_degree > 3) return D4DGS_ERR_INVALID_ARG;
+    if (s->n == 0) return D4DGS_OK;
+    const void *ps[] = {s->means, s->t_mean, s->velocity, s->log_scales, s->log_t_scale, s->quats, s->opacity_logit, s->sh};
+    for (const void *p : ps)
+        if (!p || !aligned(p, 4)) return D4DGS_ERR_INVALID_ARG;
+    if (!aligned(s->quats, 16)) return D4DGS_ERR_INVALID_ARG;
+    if ((s->sh_degree == 1 || s->sh_degree == 3) && !aligned(s->sh, 16)) return D4DGS_ERR_INVALID_ARG;
+    return D4DGS_OK;
+}
+
+int num_sms_current() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    int v = 1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    if (dev >= 0 && dev < 64) cache[dev] = v;
+    return v;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? D4DGS_OK : D4DGS_ERR_CUDA; }
+
+}  // namespace
+
+bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, int64_t cap, Layout *L) {
+    if (n < 0 || !valid_camera(cam) || !valid_config(cfg) || cap < 0 || cap > (int64_t)((1u << 30) - 1u)) return false;
+    Layout l;
+    l.n = n;
+    l.width = cam->width;
+    l.height = cam->height;
+    l.tile = cfg->tile;
+    l.tiles_x = (cam->width + cfg->tile - 1) / cfg->tile;
+    l.tiles_y = (cam->height + cfg->tile - 1) / cfg->tile;
+    l.ntiles = l.tiles_x * l.tiles_y;
+    l.pixels = (int64_t)cam->width * cam->height;
+    l.depth_passes = 4;
+    l.tile_bits = ceil_log2(l.ntiles);
+    l.tile_passes = (l.tile_bits + 7) / 8;
+    int sh = 0;
+    for (int p = 0; p < l.tile_passes; p++) {
+        const int left = l.tile_bits - sh, passes_left = l.tile_passes - p;
+        const int b = (left + passes_left - 1) / passes_left;
+        l.tile_shift[p] = sh;
+        l.tile_pass_bits[p] = b;
+        sh += b;
+    }
+    l.cap = cap;
+    l.parts_depth = n > 0 ? ((int64_t)n + kSortItems - 1) / kSortItems : 1;
+    l.parts_dup = n > 0 ? ((int64_t)n + kDupItems - 1) / kDupItems : 1;
+    l.parts_tile = cap > 0 ? (cap + kSortItems - 1) / kSortItems : 1;
+    int64_t off = 0;
+    l.control = off; off += align256((int64_t)kCtlWords * 4);
+    l.ranges = off; off += align256((int64_t)l.ntiles * 8);
+    l.lb_depth = off; off += align256((int64_t)l.depth_passes * l.parts_depth * kRadix * 4);
+    l.lb_dup = off; off += align256(l.parts_dup * 8);
+    l.lb_tile = off; off += align256((int64_t)(l.tile_passes > 0 ? l.tile_passes : 1) * l.parts_tile * kRadix * 4);
+    l.zero_end = off;
+    l.records = off; off += align256((int64_t)n * 48);
+    for (int b = 0; b < 2; b++) { l.depth_keys[b] = off; off += align256((int64_t)n * 4); }
+    for (int b = 0; b < 2; b++) { l.depth_vals[b] = off; off += align256((int64_t)n * 4); }
+    l.tiles_touched = off; off += align256((int64_t)n * 4);
+    l.rect = off; off += align256((int64_t)n * 8);
+    l.final_T = off; off += align256(l.pixels * 4);
+    l.n_contrib = off; off += align256(l.pixels * 4);
+    for (int b = 0; b < 2; b++) { l.tile_keys[b] = off; off += align256(cap * 4); }
+    for (int b = 0; b < 2; b++) { l.tile_vals[b] = off; off += align256(cap * 4); }
+    l.total = off;
+    *L = l;
+    return true;
+}
+
+bool layout_for_bytes(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, size_t ws_bytes, Layout *L) {
+    Layout l0;
+    if (!make_layout(n, cam, cfg, 0, &l0) || (size_t)l0.total > ws_bytes) return false;
+    int64_t lo = 0, hi = (int64_t)((ws_bytes - (size_t)l0.total) / 16) + 1;
+    if (hi > (int64_t)((1u << 30) - 1u)) hi = (int64_t)((1u << 30) - 1u);
+    Layout t;
+    while (lo < hi) {   // largest cap whose layout fits
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (make_layout(n, cam, cfg, mid, &t) && (size_t)t.total <= ws_bytes) lo = mid; else hi = mid - 1;
+    }
+    return make_layout(n, cam, cfg, lo, L);
+}
+
+}  // namespace d4dgs
+
+using namespace d4dgs;
+
+extern "C" {
+
+size_t d4dgs_workspace_bytes(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, int64_t key_capacity) {
+    Layout L;
+    if (!make_layout(n, cam, cfg, key_capacity, &L)) return 0;
+    return (size_t)L.total;
+}
+
+int d4dgs_workspace_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, size_t ws_bytes,
+                           d4dgs_layout *out) {
+    if (!out || n < 0 || !valid_camera(cam) || !valid_config(cfg)) return D4DGS_ERR_INVALID_ARG;
+    Layout L;
+    if (!layout_for_bytes(n, cam, cfg, ws_bytes, &L)) return D4DGS_ERR_WORKSPACE_TOO_SMALL;
+    out->records = L.records;
+    out->depth_keys = L.depth_keys[0];
+    out->tiles_touched = L.tiles_touched;
+    out->rect = L.rect;
+    out->depth_order = L.depth_vals[L.depth_passes & 1];
+    out->tile_keys = L.tile_keys[L.tile_passes & 1];
+    out->tile_vals = L.tile_vals[L.tile_passes & 1];
+    out->ranges = L.ranges;
+    out->final_T = L.final_T;
+    out->n_contrib = L.n_contrib;
+    out->control = L.control;
+    out->key_capacity = L.cap;
+    out->tiles_x = L.tiles_x;
+    out->tiles_y = L.tiles_y;
+    out->depth_passes = L.depth_passes;
+    out->tile_passes = L.tile_passes;
+    return D4DGS_OK;
+}
+
+static int prepare(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
+                   Layout *L) {
+    if (n < 0 || !valid_camera(cam) || !valid_config(cfg) || !ws || !aligned(ws, 256)) return D4DGS_ERR_INVALID_ARG;
+    if (!layout_for_bytes(n, cam, cfg, ws_bytes, L)) return D4DGS_ERR_WORKSPACE_TOO_SMALL;
+    return D4DGS_OK;
+}
+
+int d4dgs_preprocess(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                     void *ws, size_t ws_bytes, d4dgs_stream_t stream) {
+    int rc = check_scene(scene);
+    if (rc) return rc;
+    if (!isfinite(t)) return D4DGS_ERR_INVALID_ARG;
+    Layout L;
+    if ((rc = prepare(scene->n, cam, cfg, ws, ws_bytes, &L))) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(ws, 0, (size_t)L.zero_end, st);
+    if (e != cudaSuccess) return D4DGS_ERR_CUDA;
+    return cuda_status(launch_preprocess(*scene, make_cam_args(cam, cfg->tile), t, L, ws, st, num_sms_current()));
+}
+
+int d4dgs_sort(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
+               d4dgs_stream_t stream) {
+    Layout L;
+    int rc = prepare(n, cam, cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    return cuda_status(launch_sort(L, ws, reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
+}
+
+int d4dgs_blend(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
+                float *out_rgb, d4dgs_stream_t stream) {
+    Layout L;
+    int rc = prepare(n, cam, cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!out_rgb || !aligned(out_rgb, 4)) return D4DGS_ERR_INVALID_ARG;
+    return cuda_status(launch_blend(L, *cfg, ws, out_rgb, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int d4dgs_blend_profile(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
+                        float *out_rgb, uint64_t *counts, d4dgs_stream_t stream) {
+    Layout L;
+    int rc = prepare(n, cam, cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!out_rgb || !counts || !aligned(counts, 8)) return D4DGS_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(counts, 0, 2 * sizeof(uint64_t), st) != cudaSuccess) return D4DGS_ERR_CUDA;
+    return cuda_status(launch_blend(L, *cfg, ws, out_rgb, st, reinterpret_cast<unsigned long long *>(counts)));
+}
+
+int d4dgs_render(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg, void *ws,
+                 size_t ws_bytes, float *out_rgb, d4dgs_stream_t stream) {
+    if (!out_rgb || !aligned(out_rgb, 4)) return D4DGS_ERR_INVALID_ARG;
+    int rc = d4dgs_preprocess(scene, cam, t, cfg, ws, ws_bytes, stream);
+    if (rc) return rc;
+    if ((rc = d4dgs_sort(scene->n, cam, cfg, ws, ws_bytes, stream))) return rc;
+    return d4dgs_blend(scene->n, cam, cfg, ws, ws_bytes, out_rgb, stream);
+}
+
+int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                          void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
+                          d4dgs_stream_t stream) {
+    int rc = check_scene(scene);
+    if (rc) return rc;
+    if (!isfinite(t) || !dl_drgb || !grad) return D4DGS_ERR_INVALID_ARG;
+    if (scene->n > 0) {
+        float *gp[] = {grad->means, grad->t_mean, grad->velocity, grad->log_scales, grad->log_t_scale, grad->quats,
+                       grad->opacity_logit, grad->sh};
+        for (float *p : gp)
+            if (!p || !aligned(p, 4)) return D4DGS_ERR_INVALID_ARG;
+    }
+    Layout L;
+    if ((rc = prepare(scene->n, cam, cfg, ws, ws_bytes, &L))) return rc;
+    return cuda_status(launch_backward(*scene, make_cam_args(cam, cfg->tile), t, *cfg, L, ws, dl_drgb, *grad,
+                                       reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
+}
+
+int d4dgs_read_stats(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, const void *ws, size_t ws_bytes,
+                     d4dgs_stats *out, d4dgs_stream_t stream) {
+    if (!out) return D4DGS_ERR_INVALID_ARG;
+    Layout L;
+    int rc = prepare(n, cam, cfg, const_cast<void *>(ws), ws_bytes, &L);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return D4DGS_ERR_CUDA;
+    uint32_t words[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(words, static_cast<const char *>(ws) + L.control, sizeof(words), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return D4DGS_ERR_CUDA;
+    out->status = (words[kCtlStatus] & kStatusTimeout) ? D4DGS_ERR_TIMEOUT
+                  : (words[kCtlStatus] & kStatusCapacity) ? D4DGS_ERR_CAPACITY
+                                                          : D4DGS_OK;
+    out->n_keys = words[kCtlNumKeys];
+    out->key_capacity = L.cap;
+    out->n_visible = words[kCtlNumVisible];
+    return out->status;
+}
+
+size_t d4dgs_scene_bytes(int32_t n, int32_t sh_degree) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3) return 0;
+    const int64_t k = (int64_t)(sh_degree + 1) * (sh_degree + 1);
+    const int64_t cols[8] = {3, 1, 3, 3, 1, 4, 1, 3 * k};
+    int64_t off = 0;
+    for (int64_t c : cols) off += (((int64_t)n * c * 4) + 255) & ~(int64_t)255;
+    return (size_t)off;
+}
+
+int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                      void *dev_scene_buf, size_t dev_scene_bytes, void *ws, size_t ws_bytes, void *dev_rgb,
+                      float *out_rgb_host, d4dgs_stream_t stream) {
+    if (!host_scene || host_scene->n < 0 || host_scene->sh_degree < 0 || host_scene->sh_degree > 3)
+        return D4DGS_ERR_INVALID_ARG;
+    if (!dev_scene_buf || !aligned(dev_scene_buf, 256) || !dev_rgb || !out_rgb_host || !valid_camera(cam))
+        return D4DGS_ERR_INVALID_ARG;
+    const int32_t n = host_scene->n;
+    if (dev_scene_bytes < d4dgs_scene_bytes(n, host_scene->sh_degree)) return D4DGS_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t k = (int64_t)(host_scene->sh_degree + 1) * (host_scene->sh_degree + 1);
+    const float *src[8] = {host_scene->means, host_scene->t_mean, host_scene->velocity, host_scene->log_scales,
+                           host_scene->log_t_scale, host_scene->quats, host_scene->opacity_logit, host_scene->sh};
+    const int64_t cols[8] = {3, 1, 3, 3, 1, 4, 1, 3 * k};
+    float *dst[8];
+    int64_t off = 0;
+    for (int a = 0; a < 8; a++) {
+        dst[a] = reinterpret_cast<float *>(static_cast<char *>(dev_scene_buf) + off);
+        const size_t bytes = (size_t)n * cols[a] * 4;
+        if (n > 0) {
+            if (!src[a]) return D4DGS_ERR_INVALID_ARG;
+            if (cudaMemcpyAsync(dst[a], src[a], bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return D4DGS_ERR_CUDA;
+        }
+        off += ((int64_t)bytes + 255) & ~(int64_t)255;
+    }
+    d4dgs_scene dev{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], n, host_scene->sh_degree};
+    int rc = d4dgs_render(&dev, cam, t, cfg, ws, ws_bytes, static_cast<float *>(dev_rgb), stream);
+    if (rc) return rc;
+    const size_t img = (size_t)cam->width * cam->height * 3 * sizeof(float);
+    if (cudaMemcpyAsync(out_rgb_host, dev_rgb, img, cudaMemcpyDeviceToHost, st) != cudaSuccess) return D4DGS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return D4DGS_ERR_CUDA;
+    return D4DGS_OK;
+}
+
+int d4dgs_launches_per_frame(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg) {
+    Layout L;
+    if (!make_layout(n, cam, cfg, 0, &L)) return D4DGS_ERR_INVALID_ARG;
+    if (n == 0) return 1;   // only the blend (background)
+    return 1 + sort_launch_count(L) + 1;
+}
+
+const char *d4dgs_strerror(int code) {
+    switch (code) {
+        case D4DGS_OK: return "ok";
+        case D4DGS_ERR_INVALID_ARG: return "invalid argument";
+        case D4DGS_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+        case D4DGS_ERR_CAPACITY: return "more (tile, Gaussian) pairs than the workspace key capacity";
+        case D4DGS_ERR_TIMEOUT: return "a bounded device spin-wait timed out";
+        case D4DGS_ERR_CUDA: return "CUDA runtime error";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

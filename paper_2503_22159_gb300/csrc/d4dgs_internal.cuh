@@ -1,0 +1,115 @@
+// d4dgs_internal.cuh -- shared definitions of the sm_103a renderer: workspace
+// layout, control-block words, kernel entry declarations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/d4dgs.h"
+
+namespace d4dgs {
+
+// ---- rasteriser constants (3DGS conventions the paper reuses, Sec. III-B-2)
+constexpr float kNear = 0.2f;          // near plane on camera z
+constexpr float kDilation = 0.3f;      // px^2 added to the 2D covariance diagonal
+constexpr float kJacClamp = 1.3f;      // x/z, y/z clamp, times half the field of view
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kRadiusK = 3.33f;      // 3.33^2 > 2 ln 255: covers every alpha >= 1/255
+
+// ---- sort geometry
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 15;                              // keys per thread
+constexpr int kSortItems = kSortThreads * kSortIPT;       // 3840 keys per partition
+constexpr int kRadix = 256;                               // digit bins (<= 8 bits per pass)
+constexpr int kDupThreads = 256;
+constexpr int kDupIPT = 8;
+constexpr int kDupItems = kDupThreads * kDupIPT;          // 2048 depth-ordered Gaussians per partition
+
+// ---- control block (uint32 words at layout.control)
+enum : int {
+    kCtlStatus = 0,        // bit 0: key capacity exceeded, bit 1: spin-wait timeout
+    kCtlNumKeys = 1,       // total (tile, Gaussian) pairs of the frame (clamped reads use min(cap))
+    kCtlNumVisible = 2,    // Gaussians with at least one tile
+    kCtlPartBase = 4,      // partition counters: depth passes 4..7, dup 8, tile passes 9..11
+    kCtlDepthHist = 64,    // 4 x 256 digit counts of the depth keys
+    kCtlTileHist = 64 + 4 * kRadix,   // 3 x 256 digit counts of the tile keys
+    kCtlWords = 2048
+};
+constexpr uint32_t kStatusCapacity = 1u;
+constexpr uint32_t kStatusTimeout = 2u;
+
+// Bounded spin: polls before a wait gives up and latches kStatusTimeout.
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+struct Layout {
+    int32_t n = 0, width = 0, height = 0, tile = 0, tiles_x = 0, tiles_y = 0, ntiles = 0;
+    int64_t pixels = 0;
+    int32_t depth_passes = 4;
+    int32_t tile_bits = 0, tile_passes = 0;
+    int32_t tile_shift[3] = {0, 0, 0}, tile_pass_bits[3] = {0, 0, 0};
+    int64_t cap = 0;
+    int64_t parts_depth = 0, parts_dup = 0, parts_tile = 0;
+    // zero-initialised region [0, zero_end)
+    int64_t control = 0, ranges = 0, lb_depth = 0, lb_dup = 0, lb_tile = 0, zero_end = 0;
+    // the rest
+    int64_t records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
+    int64_t final_T = 0, n_contrib = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {0, 0};
+    int64_t total = 0;
+};
+
+// Fills `L` for a workspace holding `cap` keys; returns false on bad arguments.
+bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, int64_t cap, Layout *L);
+// Largest capacity whose layout fits in ws_bytes; false if none fits.
+bool layout_for_bytes(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, size_t ws_bytes, Layout *L);
+
+template <typename T>
+__host__ __device__ inline T *at(void *ws, int64_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
+}
+
+// Camera constants passed by value to the kernels.
+struct CamArgs {
+    float R[9], T[3];
+    float fx, fy, cx, cy;
+    float campos[3];       // -R^T T, for the SH view direction
+    int32_t width, height, tile, tiles_x, tiles_y;
+};
+CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile);
+
+// ---- launchers (each returns the cudaError_t of its launch)
+cudaError_t launch_preprocess(const d4dgs_scene &s, const CamArgs &c, float t, const Layout &L, void *ws,
+                              cudaStream_t st, int num_sms);
+cudaError_t launch_sort(const Layout &L, void *ws, cudaStream_t st, int num_sms);
+cudaError_t launch_blend(const Layout &L, const d4dgs_config &cfg, void *ws, float *out_rgb, cudaStream_t st,
+                         unsigned long long *counts = nullptr);
+cudaError_t launch_backward(const d4dgs_scene &s, const CamArgs &c, float t, const d4dgs_config &cfg,
+                            const Layout &L, void *ws, const float *dl_drgb, const d4dgs_scene_grad &g,
+                            cudaStream_t st, int num_sms);
+int sort_launch_count(const Layout &L);
+
+// ---- device helpers
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_volatile_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_volatile_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace d4dgs

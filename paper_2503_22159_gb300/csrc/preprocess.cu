@@ -1,0 +1,263 @@
+// preprocess.cu -- K1: one thread per Gaussian, the per-frame preprocess of
+// Algorithm 1 fused into one pass over the scene (HBM-bound: 64 B of
+// geometry + up to 192 B of SH read per Gaussian, 64 B written).
+//
+//   tau = t - mu_t;  mu(t) = mu + tau V3D                      (Eq. 7)
+//   X = R_cam mu(t) + T_cam  (= P_view + tau V_view)           (Eq. 9-11, 15)
+//   o_hat = sigmoid(logit) * exp(-tau^2 / (2 s_t^2))           (Eq. 6-7)
+//   (u, v) = (fx X/Z + cx, fy Y/Z + cy)                         (Eq. 12)
+//   J at the time-shifted mean, x/z and y/z clamped             (Eq. 14)
+//   Sigma' = (J W M)(J W M)^T + 0.3 I,  M = R(q) diag(s)        (Eq. 16; Sigma3D = M M^T)
+//   radius = ceil(3.33 sqrt(lambda_max)), tile rectangle, depth key = bits(Z)
+//   colour = max(0, SH . Y(normalize(mu(t) - campos)) + 0.5)
+//
+// The quantities that decide binning (Z, u, v, Sigma', lambda_max, radius,
+// rectangle) use explicitly rounded single-precision operations in a fixed
+// order (__fmul_rn/__fadd_rn/__fdiv_rn/__fsqrt_rn are never contracted into
+// FMAs), so a CPU evaluation in the same order reproduces the tile lists bit
+// for bit; only exp() of the scales and of the opacity terms may differ by an
+// ulp between math libraries.
+#include "d4dgs_internal.cuh"
+
+namespace d4dgs {
+
+namespace {
+
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float dvd(float a, float b) { return __fdiv_rn(a, b); }
+
+// Real SH basis (Condon-Shortley phase; coefficient k = l^2 + l + m), constants
+// from their closed forms.
+constexpr float kC0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+constexpr float kC1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+constexpr float kC2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+constexpr float kC2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+constexpr float kC2c = 0.54627421529603959f;  // sqrt(15/pi)/4
+constexpr float kC3e = 0.59004358992664352f;  // sqrt(35/(2 pi))/4
+constexpr float kC3f = 2.8906114426405538f;   // sqrt(105/pi)/2
+constexpr float kC3g = 0.45704579946446577f;  // sqrt(21/(2 pi))/4
+constexpr float kC3h = 0.3731763325901154f;   // sqrt(7/pi)/4
+constexpr float kC3k = 1.4453057213202769f;   // sqrt(105/pi)/4
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
+    Y[0] = kC0;
+    if (DEG >= 1) {
+        Y[1] = -kC1 * y;
+        Y[2] = kC1 * z;
+        Y[3] = -kC1 * x;
+    }
+    if (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kC2a * x * y;
+        Y[5] = -kC2a * y * z;
+        Y[6] = kC2b * (2.0f * zz - xx - yy);
+        Y[7] = -kC2a * x * z;
+        Y[8] = kC2c * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -kC3e * y * (3.0f * xx - yy);
+            Y[10] = kC3f * x * y * z;
+            Y[11] = -kC3g * y * (4.0f * zz - xx - yy);
+            Y[12] = kC3h * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = -kC3g * x * (4.0f * zz - xx - yy);
+            Y[14] = kC3k * z * (xx - yy);
+            Y[15] = -kC3e * x * (xx - 3.0f * yy);
+        }
+    }
+}
+
+struct SceneArgs {
+    const float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(256)
+preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ rec,
+                  uint32_t *__restrict__ depth_keys, uint32_t *__restrict__ tiles_touched,
+                  ushort4 *__restrict__ rect, uint32_t *__restrict__ ctl) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    __shared__ uint32_t hist[4 * kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+
+    const float limx = mul(kJacClamp, dvd(mul(0.5f, (float)c.width), c.fx));
+    const float limy = mul(kJacClamp, dvd(mul(0.5f, (float)c.height), c.fy));
+    const float tilef = (float)c.tile;
+    uint32_t nvis = 0;
+
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t key = 0xFFFFFFFFu, tiles = 0;
+        ushort4 rc = make_ushort4(0, 0, 0, 0);
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+        do {
+            // ---- deferred temporal slice and camera transform (binning order)
+            const float tau = sub(t, __ldg(s.t_mean + i));
+            const float m0 = add(__ldg(s.means + 3 * i + 0), mul(tau, __ldg(s.velocity + 3 * i + 0)));
+            const float m1 = add(__ldg(s.means + 3 * i + 1), mul(tau, __ldg(s.velocity + 3 * i + 1)));
+            const float m2 = add(__ldg(s.means + 3 * i + 2), mul(tau, __ldg(s.velocity + 3 * i + 2)));
+            const float *R = c.R;
+            const float X = add(add(add(mul(R[0], m0), mul(R[1], m1)), mul(R[2], m2)), c.T[0]);
+            const float Y = add(add(add(mul(R[3], m0), mul(R[4], m1)), mul(R[5], m2)), c.T[1]);
+            const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
+            if (!(Z > kNear)) break;
+            // ---- temporal opacity
+            const float o = dvd(1.0f, add(1.0f, expf(-__ldg(s.opacity_logit + i))));
+            const float st = expf(__ldg(s.log_t_scale + i));
+            const float oh = mul(o, expf(dvd(mul(-0.5f, mul(tau, tau)), mul(st, st))));
+            if (!(oh >= kAlphaMin)) break;
+            // ---- projection of the mean and the Jacobian at the shifted mean
+            const float xz = dvd(X, Z), yz = dvd(Y, Z);
+            const float u = add(mul(c.fx, xz), c.cx), v = add(mul(c.fy, yz), c.cy);
+            const float xzc = fminf(limx, fmaxf(-limx, xz)), yzc = fminf(limy, fmaxf(-limy, yz));
+            const float J00 = dvd(c.fx, Z), J02 = dvd(-mul(c.fx, xzc), Z);
+            const float J11 = dvd(c.fy, Z), J12 = dvd(-mul(c.fy, yzc), Z);
+            // ---- 3D covariance factor M = R(q) diag(s)
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(s.quats) + i);
+            const float qn = __fsqrt_rn(add(add(add(mul(q.x, q.x), mul(q.y, q.y)), mul(q.z, q.z)), mul(q.w, q.w)));
+            const float qw = dvd(q.x, qn), qx = dvd(q.y, qn), qy = dvd(q.z, qn), qz = dvd(q.w, qn);
+            float Rq[9];
+            Rq[0] = sub(1.0f, mul(2.0f, add(mul(qy, qy), mul(qz, qz))));
+            Rq[1] = mul(2.0f, sub(mul(qx, qy), mul(qw, qz)));
+            Rq[2] = mul(2.0f, add(mul(qx, qz), mul(qw, qy)));
+            Rq[3] = mul(2.0f, add(mul(qx, qy), mul(qw, qz)));
+            Rq[4] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qz, qz))));
+            Rq[5] = mul(2.0f, sub(mul(qy, qz), mul(qw, qx)));
+            Rq[6] = mul(2.0f, sub(mul(qx, qz), mul(qw, qy)));
+            Rq[7] = mul(2.0f, add(mul(qy, qz), mul(qw, qx)));
+            Rq[8] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qy, qy))));
+            const float sc[3] = {expf(__ldg(s.log_scales + 3 * i + 0)), expf(__ldg(s.log_scales + 3 * i + 1)),
+                                 expf(__ldg(s.log_scales + 3 * i + 2))};
+            float M[9];
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) M[3 * r + k] = mul(Rq[3 * r + k], sc[k]);
+            // ---- T = J W (2x3), TM = T M, Sigma' = TM TM^T + 0.3 I
+            float Tm[6];
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                Tm[j] = add(mul(J00, R[j]), mul(J02, R[6 + j]));
+                Tm[3 + j] = add(mul(J11, R[3 + j]), mul(J12, R[6 + j]));
+            }
+            float TM[6];
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    TM[3 * r + k] = add(add(mul(Tm[3 * r + 0], M[k]), mul(Tm[3 * r + 1], M[3 + k])), mul(Tm[3 * r + 2], M[6 + k]));
+            const float s00 = add(add(add(mul(TM[0], TM[0]), mul(TM[1], TM[1])), mul(TM[2], TM[2])), kDilation);
+            const float s01 = add(add(mul(TM[0], TM[3]), mul(TM[1], TM[4])), mul(TM[2], TM[5]));
+            const float s11 = add(add(add(mul(TM[3], TM[3]), mul(TM[4], TM[4])), mul(TM[5], TM[5])), kDilation);
+            const float det = sub(mul(s00, s11), mul(s01, s01));
+            if (!(det > 0.0f)) break;
+            const float mid = mul(0.5f, add(s00, s11));
+            const float lam = add(mid, __fsqrt_rn(fmaxf(0.1f, sub(mul(mid, mid), det))));
+            const float rf = ceilf(mul(kRadiusK, __fsqrt_rn(lam)));
+            // ---- tile rectangle (inclusive tile indices)
+            if (!(isfinite(u) && isfinite(v))) break;
+            const float fx0 = floorf(dvd(sub(u, rf), tilef)), fx1 = floorf(dvd(add(u, rf), tilef));
+            const float fy0 = floorf(dvd(sub(v, rf), tilef)), fy1 = floorf(dvd(add(v, rf), tilef));
+            if (!(fx1 >= 0.0f) || !(fx0 <= (float)(c.tiles_x - 1))) break;
+            if (!(fy1 >= 0.0f) || !(fy0 <= (float)(c.tiles_y - 1))) break;
+            const int x0 = (int)fmaxf(fx0, 0.0f), x1 = (int)fminf(fx1, (float)(c.tiles_x - 1));
+            const int y0 = (int)fmaxf(fy0, 0.0f), y1 = (int)fminf(fy1, (float)(c.tiles_y - 1));
+            rc = make_ushort4((unsigned short)x0, (unsigned short)x1, (unsigned short)y0, (unsigned short)y1);
+            tiles = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+            key = __float_as_uint(Z);
+            nvis++;
+            // ---- conic (rendering only; ordinary arithmetic from here on)
+            const float inv_det = 1.0f / det;
+            // ---- view-dependent colour in the direction of the shifted mean
+            float dx = m0 - c.campos[0], dy = m1 - c.campos[1], dz = m2 - c.campos[2];
+            const float inv_n = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= inv_n; dy *= inv_n; dz *= inv_n;
+            float Yb[16];
+            sh_basis<DEG>(dx, dy, dz, Yb);
+            float col[3] = {0.5f, 0.5f, 0.5f};
+            const float *shp = s.sh + (size_t)i * (3 * K);
+            if constexpr ((3 * K) % 4 == 0) {
+                // 16-byte aligned rows (degree 1 and 3): vector loads
+                const float4 *sh4 = reinterpret_cast<const float4 *>(shp);
+                float buf[3 * K];
+#pragma unroll
+                for (int j = 0; j < (3 * K) / 4; j++) {
+                    const float4 w4 = __ldg(sh4 + j);
+                    buf[4 * j] = w4.x; buf[4 * j + 1] = w4.y; buf[4 * j + 2] = w4.z; buf[4 * j + 3] = w4.w;
+                }
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    col[0] = fmaf(buf[3 * k + 0], Yb[k], col[0]);
+                    col[1] = fmaf(buf[3 * k + 1], Yb[k], col[1]);
+                    col[2] = fmaf(buf[3 * k + 2], Yb[k], col[2]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    col[0] = fmaf(__ldg(shp + 3 * k + 0), Yb[k], col[0]);
+                    col[1] = fmaf(__ldg(shp + 3 * k + 1), Yb[k], col[1]);
+                    col[2] = fmaf(__ldg(shp + 3 * k + 2), Yb[k], col[2]);
+                }
+            }
+            r0 = make_float4(u, v, s11 * inv_det, -s01 * inv_det);
+            r1 = make_float4(s00 * inv_det, oh, Z, rf);
+            r2 = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f), fmaxf(col[2], 0.0f), 0.0f);
+        } while (0);
+        rec[3 * (size_t)i + 0] = r0;
+        rec[3 * (size_t)i + 1] = r1;
+        rec[3 * (size_t)i + 2] = r2;
+        depth_keys[i] = key;
+        tiles_touched[i] = tiles;
+        rect[i] = rc;
+#pragma unroll
+        for (int p = 0; p < 4; p++) atomicAdd(&hist[p * kRadix + ((key >> (8 * p)) & 0xFFu)], 1u);
+    }
+    // visible count (warp-aggregated) and the digit histograms of the depth keys
+    nvis = __reduce_add_sync(0xFFFFFFFFu, nvis);
+    if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(ctl + kCtlNumVisible, nvis);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x)
+        if (hist[i]) atomicAdd(ctl + kCtlDepthHist + i, hist[i]);
+}
+
+}  // namespace
+
+CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile) {
+    CamArgs a;
+    for (int i = 0; i < 9; i++) a.R[i] = cam->R[i];
+    for (int i = 0; i < 3; i++) a.T[i] = cam->T[i];
+    a.fx = cam->fx; a.fy = cam->fy; a.cx = cam->cx; a.cy = cam->cy;
+    for (int j = 0; j < 3; j++) {
+        double p = -((double)cam->R[0 + j] * cam->T[0] + (double)cam->R[3 + j] * cam->T[1] + (double)cam->R[6 + j] * cam->T[2]);
+        a.campos[j] = (float)p;
+    }
+    a.width = cam->width; a.height = cam->height; a.tile = tile;
+    a.tiles_x = (cam->width + tile - 1) / tile;
+    a.tiles_y = (cam->height + tile - 1) / tile;
+    return a;
+}
+
+cudaError_t launch_preprocess(const d4dgs_scene &sc, const CamArgs &c, float t, const Layout &L, void *ws,
+                              cudaStream_t st, int num_sms) {
+    if (sc.n == 0) return cudaSuccess;
+    SceneArgs s{sc.means, sc.t_mean, sc.velocity, sc.log_scales, sc.log_t_scale, sc.quats, sc.opacity_logit, sc.sh};
+    const int threads = 256;
+    int blocks = (sc.n + threads - 1) / threads;
+    const int max_blocks = num_sms * 8;   // persistent-ish: bounds the histogram flushes
+    if (blocks > max_blocks) blocks = max_blocks;
+    float4 *rec = at<float4>(ws, L.records);
+    uint32_t *dk = at<uint32_t>(ws, L.depth_keys[0]);
+    uint32_t *tt = at<uint32_t>(ws, L.tiles_touched);
+    ushort4 *rc = at<ushort4>(ws, L.rect);
+    uint32_t *ctl = at<uint32_t>(ws, L.control);
+    switch (sc.sh_degree) {
+        case 0: preprocess_kernel<0><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl); break;
+        case 1: preprocess_kernel<1><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl); break;
+        case 2: preprocess_kernel<2><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl); break;
+        default: preprocess_kernel<3><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace d4dgs

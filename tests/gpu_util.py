@@ -1,0 +1,84 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C
+ABI and read its workspace buffers back; compare against the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+
+# Image tolerances (max-abs and mean-abs in [0,1] RGB) plus the oracle's
+# per-pixel slack for decisions within FP32 reach of a threshold.
+MAX_ABS = 2e-3
+MEAN_ABS = 1e-4
+
+
+def d4():
+    import paper_2503_22159_gb300 as m
+    return m
+
+
+def render(scene, cam, t, tile=16, batch=256, bg=(0.0, 0.0, 0.0), cap=None):
+    m = d4()
+    ds = m.DeviceScene.from_host(scene)
+    r = m.Renderer(scene.n, cam, tile=tile, batch=batch, bg=bg, key_capacity=cap)
+    img = r.render(ds, cam, t)
+    torch.cuda.synchronize()
+    return r, ds, img
+
+
+def _u32(r, name, count, cam):
+    if count == 0:
+        return np.zeros(0, np.uint32)
+    return r.view(name, torch.int32, count, cam).cpu().numpy().view(np.uint32)
+
+
+def gpu_records(r, n, cam):
+    return r.view("records", torch.float32, 12 * n, cam).cpu().numpy().reshape(n, 12)
+
+
+def gpu_lists(r, cam):
+    st = r.stats(cam)
+    k = int(st["n_keys"])
+    L = r.layout(cam)
+    ntiles = L["tiles_x"] * L["tiles_y"]
+    tiles = _u32(r, "tile_keys", k, cam)
+    ids = _u32(r, "tile_vals", k, cam)
+    ranges = _u32(r, "ranges", 2 * ntiles, cam).reshape(ntiles, 2)
+    return dict(tile=tiles, id=ids, ranges=ranges, stats=st)
+
+
+def expected_lists(scene, cam, t, tile):
+    b = oracle.bin_f32(scene, cam, t, tile)
+    return b, oracle.tile_list(b)
+
+
+def compare_lists(got, b, exp):
+    """Bit-exact (tile, id) sequence after removing the Gaussians the mirror
+    flags (decisions through exp() within 3e-5 of a threshold)."""
+    flagged = np.nonzero(b["flags"])[0]
+    keep_g = ~np.isin(got["id"], flagged)
+    keep_e = ~np.isin(exp["id"], flagged)
+    gt, gi = got["tile"][keep_g], got["id"][keep_g]
+    et, ei = exp["tile"][keep_e], exp["id"][keep_e]
+    assert len(gt) == len(et), (len(gt), len(et), len(flagged))
+    assert np.array_equal(gt, et)
+    assert np.array_equal(gi, ei)
+    if len(flagged) == 0:
+        assert np.array_equal(got["ranges"], exp["ranges"])
+    return len(flagged)
+
+
+def compare_image(got, ref, where=""):
+    """|gpu - oracle| <= MAX_ABS + slack per pixel channel; mean-abs <= MEAN_ABS."""
+    got = np.asarray(got, np.float64)
+    err = np.abs(got - ref["rgb"])
+    slack = ref["slack"][..., None]
+    bad = err > MAX_ABS + slack
+    assert not bad.any(), f"{where}: {int(bad.sum())} channels beyond tolerance, max err {err.max():.3g}"
+    flagged = ref["slack"] > 0
+    strict = err[~flagged]
+    if strict.size:
+        assert strict.max() <= MAX_ABS, f"{where}: unflagged max err {strict.max():.3g}"
+    assert err.mean() <= MEAN_ABS, f"{where}: mean abs err {err.mean():.3g}"
+    return dict(max=float(err.max()), mean=float(err.mean()), flagged=int(flagged.sum()))

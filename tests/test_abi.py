@@ -1,0 +1,124 @@
+"""The C ABI without a GPU: the library loads, exports every symbol that
+include/d4dgs.h declares, and its host-side logic (workspace sizing, layout,
+argument checks) behaves as documented.  No kernel is launched here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def d4():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_22159_gb300 as d4
+    return d4
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "d4dgs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(d4dgs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("d4dgs_preprocess", "d4dgs_render", "d4dgs_render_backward", "d4dgs_sort", "d4dgs_blend",
+              "d4dgs_workspace_bytes", "d4dgs_read_stats", "d4dgs_strerror"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(d4):
+    lib = d4._abi.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) <= set(d4._abi.PROTOTYPES), "binding misses a declared function"
+
+
+def test_strerror(d4):
+    assert d4._abi.strerror(0) == "ok"
+    assert "capacity" in d4._abi.strerror(d4.D4DGS_ERR_CAPACITY)
+
+
+def test_workspace_bytes_monotone_and_layout(d4):
+    cam = synth.pinhole(1352, 1014)
+    cfg = d4.config_struct(16, 256)
+    b0 = d4.d4dgs_workspace_bytes(300_000, cam, cfg, 0)
+    b1 = d4.d4dgs_workspace_bytes(300_000, cam, cfg, 1_000_000)
+    assert b1 > b0 + 16 * 1_000_000
+    L = d4.d4dgs_workspace_layout(300_000, cam, cfg, b1)
+    assert L["key_capacity"] == 1_000_000
+    assert (L["tiles_x"], L["tiles_y"]) == (85, 64)
+    assert L["tile_passes"] == 2 and L["depth_passes"] == 4
+    offs = [L[k] for k in ("records", "depth_keys", "tiles_touched", "rect", "depth_order", "tile_keys",
+                           "tile_vals", "ranges", "final_T", "n_contrib", "control")]
+    assert all(o % 256 == 0 for o in offs)
+    assert max(offs) < b1
+    with pytest.raises(d4.D4DGSError):
+        d4.d4dgs_workspace_layout(300_000, cam, cfg, b0 - 1)
+
+
+@pytest.mark.parametrize("w,h,tile,passes", [(128, 128, 16, 1), (1352, 1014, 16, 2), (2704, 2028, 8, 3),
+                                             (16, 16, 16, 0), (7, 5, 32, 0)])
+def test_tile_pass_count(d4, w, h, tile, passes):
+    cam = synth.pinhole(w, h)
+    cfg = d4.config_struct(tile, 64)
+    L = d4.d4dgs_workspace_layout(10, cam, cfg, d4.d4dgs_workspace_bytes(10, cam, cfg, 100))
+    ntiles = math.ceil(w / tile) * math.ceil(h / tile)
+    assert L["tile_passes"] == passes
+    assert 2 ** (8 * passes) >= ntiles
+
+
+def test_invalid_arguments_rejected_on_host(d4):
+    cfg = d4.config_struct(16, 256)
+    cam = synth.pinhole(64, 64)
+    assert d4._abi.load().d4dgs_workspace_bytes(10, ctypes.byref(d4.camera_struct(cam)),
+                                                ctypes.byref(d4.config_struct(12, 256)), 10) == 0
+    assert d4._abi.load().d4dgs_workspace_bytes(10, ctypes.byref(d4.camera_struct(cam)),
+                                                ctypes.byref(d4.config_struct(16, 100)), 10) == 0
+    bad = synth.pinhole(64, 64)
+    bad.fx = float("nan")
+    assert d4._abi.load().d4dgs_workspace_bytes(10, ctypes.byref(d4.camera_struct(bad)), ctypes.byref(cfg), 10) == 0
+    # a render call with a NaN camera or NaN time is refused before anything is launched
+    s = d4._abi.d4dgs_scene(*([0] * 8), 0, 0)
+    lib = d4._abi.load()
+    rc = lib.d4dgs_render(ctypes.byref(s), ctypes.byref(d4.camera_struct(bad)), 0.0, ctypes.byref(cfg),
+                          ctypes.c_void_p(256), 1 << 20, ctypes.c_void_p(256), None)
+    assert rc == d4.D4DGS_ERR_INVALID_ARG
+    rc = lib.d4dgs_render(ctypes.byref(s), ctypes.byref(d4.camera_struct(cam)), float("nan"), ctypes.byref(cfg),
+                          ctypes.c_void_p(256), 1 << 20, ctypes.c_void_p(256), None)
+    assert rc == d4.D4DGS_ERR_INVALID_ARG
+    # misaligned quaternion pointer
+    s = d4._abi.d4dgs_scene(256, 256, 256, 256, 256, 260, 256, 256, 5, 0)
+    rc = lib.d4dgs_preprocess(ctypes.byref(s), ctypes.byref(d4.camera_struct(cam)), 0.0, ctypes.byref(cfg),
+                              ctypes.c_void_p(256), 1 << 20, None)
+    assert rc == d4.D4DGS_ERR_INVALID_ARG
+    # too-small workspace
+    s = d4._abi.d4dgs_scene(256, 256, 256, 256, 256, 256, 256, 256, 5, 0)
+    rc = lib.d4dgs_preprocess(ctypes.byref(s), ctypes.byref(d4.camera_struct(cam)), 0.0, ctypes.byref(cfg),
+                              ctypes.c_void_p(256), 1024, None)
+    assert rc == d4.D4DGS_ERR_WORKSPACE_TOO_SMALL
+
+
+def test_launch_count(d4):
+    cam = synth.pinhole(1352, 1014)
+    cfg = d4.config_struct(16, 256)
+    # preprocess + 4 depth passes + dup + 2 tile passes + ranges + blend
+    assert d4.d4dgs_launches_per_frame(300_000, cam, cfg) == 10
+
+
+def test_product_does_not_import_oracle():
+    """The product package never reaches the CPU oracle (no fallback path)."""
+    pkg = os.path.join(ROOT, "paper_2503_22159_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src and "orc_" not in src, f

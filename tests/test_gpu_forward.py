@@ -1,0 +1,235 @@
+"""Parity of the CUDA forward path with the CPU oracle (needs a GPU).
+
+Stage by stage: the preprocess records against the FP64 oracle, the tile/key
+lists bit for bit against the FP32 binning mirror, and the image against the
+FP64 per-pixel brute force; then edge cases and invariants."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+def medium(n=20_000, w=333, h=257, seed=5, deg=1, frame=40):
+    """A ragged medium case: image sizes that are not tile multiples, several
+    sort partitions, SH degree 1 on the 20-unit box seen from the orbit."""
+    scene = synth.make_scene(n, seed, "box20", sh_degree=deg)
+    cam, t = synth.orbit(1, w, h, 300)[frame]
+    return scene, cam, t
+
+
+# ---------------------------------------------------------------------------
+# stage parity
+# ---------------------------------------------------------------------------
+
+def test_preprocess_matches_oracle():
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    m = gu.d4()
+    ds = m.DeviceScene.from_host(w.scene)
+    r = m.Renderer(w.scene.n, cam)
+    m.d4dgs_preprocess(ds, cam, t, r.cfg, r.ws)
+    torch.cuda.synchronize()
+    rec = gu.gpu_records(r, w.scene.n, cam)
+    L = r.layout(cam)
+    keys = r.view("depth_keys", torch.int32, w.scene.n, cam).cpu().numpy().view(np.uint32)
+    tt = r.view("tiles_touched", torch.int32, w.scene.n, cam).cpu().numpy()
+    rect = r.view("rect", torch.int16, 4 * w.scene.n, cam).cpu().numpy().view(np.uint16).reshape(-1, 4)
+    b = oracle.bin_f32(w.scene, cam, t, 16)
+    g = oracle.preprocess(w.scene, cam, t)
+    flag = b["flags"] != 0
+    # integer / bit outputs: exact against the FP32 mirror
+    assert np.array_equal(keys[~flag], b["depth_key"][~flag])
+    assert np.array_equal(tt[~flag], b["tiles_touched"][~flag].astype(np.int32))
+    vis = (b["tiles_touched"] > 0) & ~flag
+    assert np.array_equal(rect[vis].astype(np.int32), b["rect"][vis])
+    assert np.array_equal(rec[vis, 7].astype(np.int32), b["radius"][vis])
+    # float outputs: against FP64
+    np.testing.assert_allclose(rec[vis, 0], g["u"][vis], atol=2e-4)
+    np.testing.assert_allclose(rec[vis, 1], g["v"][vis], atol=2e-4)
+    np.testing.assert_allclose(rec[vis, 2:4], g["conic"][vis, :2], rtol=2e-4, atol=1e-6)
+    np.testing.assert_allclose(rec[vis, 4], g["conic"][vis, 2], rtol=2e-4, atol=1e-6)
+    np.testing.assert_allclose(rec[vis, 5], g["opacity_t"][vis], rtol=2e-6)
+    np.testing.assert_allclose(rec[vis, 6], g["depth"][vis], rtol=1e-6)
+    np.testing.assert_allclose(rec[vis, 8:11], g["rgb"][vis], atol=2e-6)
+    assert L["key_capacity"] > 0
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_lists_bit_exact_tiny(tile):
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    r, _, _ = gu.render(w.scene, cam, t, tile=tile, batch=64)
+    got = gu.gpu_lists(r, cam)
+    b, exp = gu.expected_lists(w.scene, cam, t, tile)
+    assert got["stats"]["status"] == 0
+    assert got["stats"]["n_keys"] == len(exp["tile"])
+    nflag = gu.compare_lists(got, b, exp)
+    assert nflag == 0
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_lists_bit_exact_medium_ragged(tile):
+    scene, cam, t = medium()
+    r, _, _ = gu.render(scene, cam, t, tile=tile, batch=128)
+    got = gu.gpu_lists(r, cam)
+    b, exp = gu.expected_lists(scene, cam, t, tile)
+    assert len(exp["tile"]) > 10 * 3840, "the case should span many sort partitions"
+    nflag = gu.compare_lists(got, b, exp)
+    assert nflag <= 3
+
+
+def test_image_parity_tiny():
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    _, _, img = gu.render(w.scene, cam, t)
+    ref = oracle.render(w.scene, cam, t)
+    s = gu.compare_image(img.cpu().numpy(), ref, "tiny")
+    assert s["flagged"] < 0.02 * cam.width * cam.height
+
+
+def test_image_parity_medium_sampled():
+    scene, cam, t = medium()
+    _, _, img = gu.render(scene, cam, t)
+    rng = np.random.default_rng(0)
+    pix = np.column_stack([rng.integers(0, cam.width, 2500), rng.integers(0, cam.height, 2500)])
+    pix = np.concatenate([pix, np.column_stack([np.arange(cam.width), np.full(cam.width, cam.height - 1)])])
+    ref = oracle.render(scene, cam, t, pixels=pix)
+    got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
+    gu.compare_image(got, ref, "medium")
+
+
+@pytest.mark.parametrize("tile,batch", [(8, 64), (8, 256), (16, 64), (16, 128), (32, 128), (32, 256)])
+def test_image_identical_across_tile_and_batch(tile, batch):
+    """Every pixel walks the same (depth, id)-ordered Gaussians with the same
+    FP32 operations whatever the tile size and staging depth: bit-identical."""
+    scene, cam, t = medium(n=5000, w=200, h=150)
+    _, _, base = gu.render(scene, cam, t, tile=16, batch=256)
+    _, _, img = gu.render(scene, cam, t, tile=tile, batch=batch)
+    assert torch.equal(base, img)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and invariants
+# ---------------------------------------------------------------------------
+
+def test_empty_scene_is_background():
+    scene = synth.make_scene(0, 0, "tiny")
+    cam = synth.pinhole(40, 30)
+    r, _, img = gu.render(scene, cam, 0.5, bg=(0.25, 0.5, 0.75))
+    assert torch.equal(img, torch.tensor([0.25, 0.5, 0.75], device=img.device).expand_as(img))
+    assert r.stats(cam)["n_keys"] == 0
+
+
+def test_all_behind_camera_is_background():
+    w = synth.tiny_workload(300)
+    cam = synth.pinhole(64, 64)
+    cam.T = np.array([0.0, 0.0, -10.0], np.float32)   # every Gaussian ends at z < 0.2
+    r, _, img = gu.render(w.scene, cam, 0.5)
+    assert float(img.abs().max()) == 0.0
+    assert r.stats(cam)["n_visible"] == 0
+
+
+def test_background_colour_parity():
+    w = synth.tiny_workload(500)
+    cam, t = w.frames[0]
+    bg = (0.2, 0.5, 0.8)
+    _, _, img = gu.render(w.scene, cam, t, bg=bg)
+    ref = oracle.render(w.scene, cam, t, bg=bg)
+    gu.compare_image(img.cpu().numpy(), ref, "bg")
+
+
+def test_huge_and_near_plane_gaussians():
+    """Gaussians that cover every tile, sit just beyond the near plane, or
+    straddle it."""
+    sc = synth.make_scene(64, 9, "tiny")
+    sc.means[:8] = [[0.0, 0.0, 0.3]] * 8
+    sc.log_scales[:8] = math.log(0.5)
+    sc.means[8:16, 2] = np.linspace(0.15, 0.25, 8)
+    sc.velocity[:16] = 0
+    cam = synth.pinhole(96, 80)
+    r, _, img = gu.render(sc, cam, 0.5)
+    ref = oracle.render(sc, cam, 0.5)
+    gu.compare_image(img.cpu().numpy(), ref, "huge")
+    b, exp = gu.expected_lists(sc, cam, 0.5, 16)
+    gu.compare_lists(gu.gpu_lists(r, cam), b, exp)
+
+
+def test_single_gaussian():
+    sc = synth.make_scene(1, 3, "tiny")
+    sc.means[0] = [0.05, -0.02, 3.0]
+    cam = synth.pinhole(64, 48)
+    _, _, img = gu.render(sc, cam, float(sc.t_mean[0]))
+    ref = oracle.render(sc, cam, float(sc.t_mean[0]))
+    gu.compare_image(img.cpu().numpy(), ref, "single")
+    assert float(img.max()) > 0.01
+
+
+def test_capacity_overflow_reported_without_writing_out_of_bounds():
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    m = gu.d4()
+    ds = m.DeviceScene.from_host(w.scene)
+    r = m.Renderer(w.scene.n, cam, key_capacity=1000)
+    guard = torch.full((1 << 20,), 7, dtype=torch.uint8, device="cuda")
+    out = torch.empty((cam.height, cam.width, 3), device="cuda")
+    m.d4dgs_render(ds, cam, t, r.cfg, r.ws, out)
+    st = m.d4dgs_read_stats(w.scene.n, cam, r.cfg, r.ws)
+    assert st["status"] == m.D4DGS_ERR_CAPACITY
+    assert st["n_keys"] > 1000
+    assert int((guard != 7).sum()) == 0
+    img = r.render(ds, cam, t)   # grows the workspace and re-renders
+    ref = oracle.render(w.scene, cam, t)
+    gu.compare_image(img.cpu().numpy(), ref, "after-grow")
+
+
+def test_deterministic():
+    scene, cam, t = medium(n=8000, w=160, h=120)
+    _, _, a = gu.render(scene, cam, t)
+    _, _, b = gu.render(scene, cam, t)
+    assert torch.equal(a, b)
+
+
+def test_static_reduction_bit_identical_over_time():
+    """V = 0 and s_t -> infinity: the GPU image must not depend on t at all."""
+    sc = synth.make_scene(2000, 21, "tiny")
+    sc.velocity[:] = 0
+    sc.log_t_scale[:] = 30.0
+    cam = synth.pinhole(128, 96)
+    imgs = [gu.render(sc, cam, t)[2] for t in (0.0, 0.31, 1.0)]
+    assert float(imgs[0].max()) > 0.05
+    assert torch.equal(imgs[0], imgs[1]) and torch.equal(imgs[0], imgs[2])
+
+
+def test_nan_camera_rejected():
+    w = synth.tiny_workload(10)
+    cam = synth.pinhole(32, 32)
+    m = gu.d4()
+    ds = m.DeviceScene.from_host(w.scene)
+    r = m.Renderer(10, cam)
+    bad = synth.pinhole(32, 32)
+    bad.cx = float("nan")
+    out = torch.empty((32, 32, 3), device="cuda")
+    with pytest.raises(m.D4DGSError) as e:
+        m.d4dgs_render(ds, bad, 0.5, r.cfg, r.ws, out)
+    assert e.value.code == m.D4DGS_ERR_INVALID_ARG
+
+
+def test_render_host_matches_device_path():
+    w = synth.tiny_workload()
+    cam, t = w.frames[0]
+    r, ds, img = gu.render(w.scene, cam, t)
+    m = gu.d4()
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).pin_memory() for k in m.SCENE_FIELDS}
+    host["sh_degree"] = w.scene.sh_degree
+    buf = torch.empty(m.d4dgs_scene_bytes(w.scene.n, w.scene.sh_degree), dtype=torch.uint8, device="cuda")
+    dev_rgb = torch.empty_like(img)
+    out = torch.empty(img.shape, dtype=torch.float32).pin_memory()
+    m.d4dgs_render_host(host, cam, t, r.cfg, buf, r.ws, dev_rgb, out)
+    assert torch.equal(out, img.cpu())

@@ -1,0 +1,75 @@
+"""Parity at the benchmark's full size and launch configuration (needs a GPU):
+300,000 SH-3 Gaussians, 1352x1014, tile 16, batch 256, frames of the orbit.
+
+The whole preprocess and the whole (tile, Gaussian) list are compared (bit for
+bit where the arithmetic is fixed); the image on sampled pixels that the
+oracle computes one by one."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scene_w():
+    return synth.scene_workload()
+
+
+@pytest.fixture(scope="module")
+def gpu_renderer(scene_w):
+    m = gu.d4()
+    ds = m.DeviceScene.from_host(scene_w.scene)
+    cam0 = scene_w.frames[0][0]
+    r = m.Renderer(scene_w.scene.n, cam0, tile=16, batch=256, key_capacity=40 * scene_w.scene.n)
+    return m, ds, r
+
+
+@pytest.mark.parametrize("k", [150])
+def test_scene_preprocess_and_lists(scene_w, gpu_renderer, k):
+    m, ds, r = gpu_renderer
+    cam, t = scene_w.frames[k]
+    r.render(ds, cam, t)
+    torch.cuda.synchronize()
+    n = scene_w.scene.n
+    rec = gu.gpu_records(r, n, cam)
+    b = oracle.bin_f32(scene_w.scene, cam, t, 16)
+    g = oracle.preprocess(scene_w.scene, cam, t)
+    flag = b["flags"] != 0
+    vis = (b["tiles_touched"] > 0) & ~flag
+    assert vis.sum() > 100_000
+    assert np.array_equal(rec[vis, 7].astype(np.int32), b["radius"][vis])
+    assert np.array_equal(rec[vis, 6].view(np.uint32), b["depth_key"][vis])
+    np.testing.assert_allclose(rec[vis, 0], g["u"][vis], atol=2e-3)
+    np.testing.assert_allclose(rec[vis, 1], g["v"][vis], atol=2e-3)
+    np.testing.assert_allclose(rec[vis, 5], g["opacity_t"][vis], rtol=5e-6)
+    np.testing.assert_allclose(rec[vis, 8:11], g["rgb"][vis], atol=1e-5)
+    np.testing.assert_allclose(rec[vis, 2], g["conic"][vis, 0], rtol=1e-3, atol=1e-7)
+    np.testing.assert_allclose(rec[vis, 4], g["conic"][vis, 2], rtol=1e-3, atol=1e-7)
+    got = gu.gpu_lists(r, cam)
+    exp = oracle.tile_list(b)
+    assert got["stats"]["status"] == 0
+    nflag = gu.compare_lists(got, b, exp)
+    assert nflag < 1e-3 * n
+
+
+@pytest.mark.parametrize("k", [0, 150, 299])
+def test_scene_image_sampled(scene_w, gpu_renderer, k):
+    m, ds, r = gpu_renderer
+    cam, t = scene_w.frames[k]
+    img = r.render(ds, cam, t)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(k)
+    pix = np.column_stack([rng.integers(0, cam.width, 1500), rng.integers(0, cam.height, 1500)])
+    pix = np.concatenate([pix, np.column_stack([np.arange(cam.width), np.full(cam.width, 7 * k % cam.height)])])
+    # the last column and row (ragged bottom tile row: 1014 = 63 * 16 + 6)
+    pix = np.concatenate([pix, np.column_stack([np.full(cam.height, cam.width - 1), np.arange(cam.height)])])
+    ref = oracle.render(scene_w.scene, cam, t, pixels=pix)
+    got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
+    s = gu.compare_image(got, ref, f"scene frame {k}")
+    assert float(np.abs(ref["rgb"]).max()) > 0.1
+    assert s["flagged"] < 0.05 * len(pix)
