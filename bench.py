@@ -268,7 +268,7 @@ def run_ours(args):
     order = [(rank + world * k) % nf for k in range(W + K)]
 
     # size the key capacity on this rank's frames (untimed)
-    r = d4.Renderer(scene.n, cam0, tile=args.tile, batch=args.batch, key_capacity=64 * scene.n, device=dev)
+    r = d4.Renderer(scene.n, cam0, tile=args.tile, batch=args.batch, key_capacity=160 * scene.n, device=dev)
     max_keys = 0
     for fi in sorted(set(order)):
         cam, t = w.frames[fi]

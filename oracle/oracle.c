@@ -18,8 +18,8 @@
  *                       documented operation order (no FMA contraction; the
  *                       file is compiled with -ffp-contract=off) giving depth
  *                       key bits, radius, tile rectangle and tile count, with
- *                       an FP64 shadow that flags decisions that pass through
- *                       a transcendental within 3e-5 relative of a threshold.
+ *                       flags on decisions that pass through expf within
+ *                       3e-6 relative of a threshold.
  *   orc_backward        FP64 adjoint (reverse mode) of the whole frame with
  *                       respect to the raw per-Gaussian parameters.
  *
@@ -302,7 +302,10 @@ void orc_render_pixels(const orc_g2d *g, int n, const orc_camera *cam, const dou
                 double p = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
                 /* FP32 relative error budget of alpha for this pair */
                 double gx = fabs(a * dx + b * dy), gy = fabs(b * dx + c * dy);
-                double w = 2e-5 + (gx + gy) * eps_px + 4e-7 * fabs(p);
+                /* FP32 conic: relative error ~ cond * 2^-22 from the cancellation in det */
+                const double *cv = g->cov2d + 3 * (size_t)i;
+                double cond = (fabs(cv[0] * cv[2]) + cv[1] * cv[1]) / (cv[0] * cv[2] - cv[1] * cv[1]);
+                double w = 2e-5 + (gx + gy) * eps_px + fabs(p) * (4e-7 + cond * 2.4e-7);
                 int near_p = fabs(p) <= (gx + gy) * eps_px + 1e-6;
                 if (p > 0.0 && !near_p) continue;
                 double alpha = fmin(ORC_ALPHA_MAX, g->opacity_t[i] * exp(fmin(p, 0.0)));
@@ -388,12 +391,15 @@ void orc_render_pixels(const orc_g2d *g, int n, const orc_camera *cam, const dou
  *   cull unless u, v finite; x0 = floorf((u - r)/tile), x1 = floorf((u + r)/tile),
  *   cull if x1 < 0 or x0 > tiles_x - 1, then clamp to [0, tiles_x-1] (same in y)
  *   tiles = (x1 - x0 + 1)(y1 - y0 + 1); depth key = bits of Z
- * Flags (FP64 shadow of the same quantities): bit 0 -- 3.33 sqrt(lambda_max)
- * within 3e-5 relative of an integer (radius decided through expf of the
- * scales); bit 1 -- o_hat within 3e-5 relative of 1/255.  Only these two
- * decisions depend on a transcendental function, whose FP32 result may differ
- * by an ulp between libraries; a flagged Gaussian is excluded from bit-exact
- * comparison.  A culled Gaussian has depth key 0xFFFFFFFF and 0 tiles.
+ * Flags: bit 0 -- 3.33 sqrt(lambda_max) within 3e-6 relative of an integer;
+ * bit 1 -- o_hat within 3e-6 relative of 1/255.  Every operation above is
+ * correctly rounded and reproducible on any IEEE machine except expf, whose
+ * FP32 result may differ by one or two ulps between math libraries; through
+ * the chain (s -> Sigma' -> lambda_max, three exps -> o_hat) that moves these
+ * two quantities by at most ~1.5e-6 relative, so a decision further than 3e-6
+ * from its threshold is the same everywhere.  A flagged Gaussian is excluded
+ * from bit-exact comparison.  A culled Gaussian has depth key 0xFFFFFFFF and
+ * 0 tiles.
  * ------------------------------------------------------------------------- */
 typedef struct {
     int32_t n, sh_degree;
@@ -431,13 +437,7 @@ void orc_bin_f32(const orc_scene_f32 *sc, const orc_camera_f32 *cam, float t, in
         float o = 1.0f / (1.0f + expf(-sc->opacity_logit[i]));
         float st = expf(sc->log_t_scale[i]);
         float oh = o * expf((-0.5f * (tau * tau)) / (st * st));
-        {
-            double tau64 = (double)t - (double)sc->t_mean[i];
-            double o64 = 1.0 / (1.0 + exp(-(double)sc->opacity_logit[i]));
-            double st64 = exp((double)sc->log_t_scale[i]);
-            double oh64 = o64 * exp(-0.5 * tau64 * tau64 / (st64 * st64));
-            if (fabs(oh64 - 1.0 / 255.0) <= 3e-5 * (1.0 / 255.0)) flags[i] |= 2;
-        }
+        if (fabsf(oh - amin) <= 3e-6f * amin) flags[i] |= 2;
         if (!(oh >= amin)) continue;
         float xz = X / Z, yz = Y / Z;
         float u = cam->fx * xz + cam->cx, v = cam->fy * yz + cam->cy;
@@ -474,38 +474,9 @@ void orc_bin_f32(const orc_scene_f32 *sc, const orc_camera_f32 *cam, float t, in
         float mid = 0.5f * (s00 + s11);
         float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
         float rf = ceilf(3.33f * sqrtf(lam));
-        /* FP64 shadow of the radius decision */
-        {
-            double q64[4] = {q[0], q[1], q[2], q[3]};
-            double nq = sqrt(q64[0] * q64[0] + q64[1] * q64[1] + q64[2] * q64[2] + q64[3] * q64[3]);
-            for (int k = 0; k < 4; k++) q64[k] /= nq;
-            double R64[9], M64[9], T64[6], TM64[6];
-            orc_quat_to_rot(q64, R64);
-            double Z64 = 0.0, X64 = 0.0, Y64 = 0.0, mm[3];
-            double tau64 = (double)t - (double)sc->t_mean[i];
-            for (int j = 0; j < 3; j++) mm[j] = (double)mu[j] + tau64 * (double)vel[j];
-            X64 = (double)R[0] * mm[0] + (double)R[1] * mm[1] + (double)R[2] * mm[2] + (double)cam->T[0];
-            Y64 = (double)R[3] * mm[0] + (double)R[4] * mm[1] + (double)R[5] * mm[2] + (double)cam->T[1];
-            Z64 = (double)R[6] * mm[0] + (double)R[7] * mm[1] + (double)R[8] * mm[2] + (double)cam->T[2];
-            double lx = 1.3 * (0.5 * cam->width) / (double)cam->fx, ly = 1.3 * (0.5 * cam->height) / (double)cam->fy;
-            double xzc64 = fmin(lx, fmax(-lx, X64 / Z64)), yzc64 = fmin(ly, fmax(-ly, Y64 / Z64));
-            double j00 = (double)cam->fx / Z64, j02 = -(double)cam->fx * xzc64 / Z64;
-            double j11 = (double)cam->fy / Z64, j12 = -(double)cam->fy * yzc64 / Z64;
-            for (int r = 0; r < 3; r++)
-                for (int c = 0; c < 3; c++) M64[3 * r + c] = R64[3 * r + c] * exp((double)ls[c]);
-            for (int j = 0; j < 3; j++) {
-                T64[j] = j00 * (double)R[j] + j02 * (double)R[6 + j];
-                T64[3 + j] = j11 * (double)R[3 + j] + j12 * (double)R[6 + j];
-            }
-            for (int r = 0; r < 2; r++)
-                for (int c = 0; c < 3; c++)
-                    TM64[3 * r + c] = T64[3 * r] * M64[c] + T64[3 * r + 1] * M64[3 + c] + T64[3 * r + 2] * M64[6 + c];
-            double a00 = TM64[0] * TM64[0] + TM64[1] * TM64[1] + TM64[2] * TM64[2] + 0.3;
-            double a01 = TM64[0] * TM64[3] + TM64[1] * TM64[4] + TM64[2] * TM64[5];
-            double a11 = TM64[3] * TM64[3] + TM64[4] * TM64[4] + TM64[5] * TM64[5] + 0.3;
-            double d64 = a00 * a11 - a01 * a01, m64 = 0.5 * (a00 + a11);
-            double rr = 3.33 * sqrt(m64 + sqrt(fmax(0.1, m64 * m64 - d64)));
-            if (fabs(rr - nearbyint(rr)) <= 3e-5 * rr) flags[i] |= 1;
+        {   /* radius decided within reach of an ulp difference in expf of the scales */
+            const double rr = 3.33 * sqrt((double)lam);
+            if (fabs(rr - nearbyint(rr)) <= 3e-6 * rr) flags[i] |= 1;
         }
         if (!(isfinite(u) && isfinite(v))) continue;
         float fx0 = floorf((u - rf) / tilef), fx1 = floorf((u + rf) / tilef);

