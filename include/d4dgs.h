@@ -198,6 +198,25 @@ int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, fl
                       void *dev_scene_buf, size_t dev_scene_bytes, void *ws, size_t ws_bytes,
                       void *dev_rgb, float *out_rgb_host, d4dgs_stream_t stream);
 
+/* d4dgs_render for callers that cannot allocate device memory when they
+ * render (the paper has no counterpart; this is a library convenience).  The
+ * scratch is a fixed 64 MiB array inside the library's device module: each
+ * GPU that loads the library holds it until the process exits, and the call
+ * itself allocates nothing.  The caller passes the scene and the output image
+ * (H x W x 3 float32 device) as for d4dgs_render.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Returns D4DGS_ERR_WORKSPACE_TOO_SMALL when N and the image size leave
+ *     no room for keys in 64 MiB; a frame with more (tile, Gaussian) pairs
+ *     than fit is reported as D4DGS_ERR_CAPACITY only through `stats`.
+ *   - stats: optional host struct; when non-NULL the call synchronises
+ *     `stream` and fills it (returning stats->status), otherwise the call is
+ *     asynchronous.
+ *   - All calls share the array; calls whose work overlaps on the GPU race. */
+int d4dgs_render_static(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                        float *out_rgb, d4dgs_stats *stats, d4dgs_stream_t stream);
+
 /* Number of kernel launches one d4dgs_render issues for (n, cam, cfg) (the
  * launch count of a frame, not counting memsets). */
 int d4dgs_launches_per_frame(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg);
