@@ -108,8 +108,9 @@ typedef struct {
     int64_t tiles_touched;       /* N uint32                                                 */
     int64_t rect;                /* N x 4 uint16: x0, x1, y0, y1 (inclusive tile indices)    */
     int64_t depth_order;         /* N uint32: Gaussian ids sorted by (depth key, id)         */
-    int64_t tile_keys;           /* key_capacity uint32: tile id of each pair, sorted         */
-    int64_t tile_vals;           /* key_capacity uint32: Gaussian id of each pair, sorted     */
+    int64_t tile_keys;           /* key_capacity uint32, sorted by tile: (tile << id_bits) | id
+                                    when packed, else the tile id                               */
+    int64_t tile_vals;           /* key_capacity uint32 Gaussian ids when not packed, else -1  */
     int64_t ranges;              /* tiles x 2 uint32: [start, end) of each tile's list        */
     int64_t final_T;             /* H x W float: transmittance after the last blend           */
     int64_t n_contrib;           /* H x W uint32: list positions walked up to the last blend  */
@@ -117,6 +118,8 @@ typedef struct {
     int64_t key_capacity;
     int32_t tiles_x, tiles_y;
     int32_t depth_passes, tile_passes;
+    int32_t id_bits;             /* ceil(log2 N) */
+    int32_t packed;              /* 1: pairs packed in one uint32 (tile bits + id_bits <= 32) */
 } d4dgs_layout;
 
 /* Bytes of workspace for N Gaussians, this camera and config, and room for

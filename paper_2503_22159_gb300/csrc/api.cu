@@ -87,17 +87,20 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
         l.tile_pass_bits[p] = b;
         sh += b;
     }
+    l.id_bits = ceil_log2(n > 1 ? n : 2);
+    l.packed = (l.id_bits + l.tile_bits) <= 32;
     l.cap = cap;
     l.parts_depth = n > 0 ? ((int64_t)n + kSortItems - 1) / kSortItems : 1;
     l.parts_dup = n > 0 ? ((int64_t)n + kDupItems - 1) / kDupItems : 1;
     l.parts_tile = cap > 0 ? (cap + kSortItems - 1) / kSortItems : 1;
     int64_t off = 0;
     l.control = off; off += align256((int64_t)kCtlWords * 4);
-    l.ranges = off; off += align256((int64_t)l.ntiles * 8);
+    l.grid = off; off += align256((int64_t)(l.tiles_x + 1) * (l.tiles_y + 1) * 4);
     l.lb_depth = off; off += align256((int64_t)l.depth_passes * l.parts_depth * kRadix * 4);
     l.lb_dup = off; off += align256(l.parts_dup * 8);
     l.lb_tile = off; off += align256((int64_t)(l.tile_passes > 0 ? l.tile_passes : 1) * l.parts_tile * kRadix * 4);
     l.zero_end = off;
+    l.ranges = off; off += align256((int64_t)l.ntiles * 8);
     l.records = off; off += align256((int64_t)n * 48);
     for (int b = 0; b < 2; b++) { l.depth_keys[b] = off; off += align256((int64_t)n * 4); }
     for (int b = 0; b < 2; b++) { l.depth_vals[b] = off; off += align256((int64_t)n * 4); }
@@ -106,7 +109,8 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.final_T = off; off += align256(l.pixels * 4);
     l.n_contrib = off; off += align256(l.pixels * 4);
     for (int b = 0; b < 2; b++) { l.tile_keys[b] = off; off += align256(cap * 4); }
-    for (int b = 0; b < 2; b++) { l.tile_vals[b] = off; off += align256(cap * 4); }
+    if (!l.packed)
+        for (int b = 0; b < 2; b++) { l.tile_vals[b] = off; off += align256(cap * 4); }
     l.total = off;
     *L = l;
     return true;
@@ -115,7 +119,7 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
 bool layout_for_bytes(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, size_t ws_bytes, Layout *L) {
     Layout l0;
     if (!make_layout(n, cam, cfg, 0, &l0) || (size_t)l0.total > ws_bytes) return false;
-    int64_t lo = 0, hi = (int64_t)((ws_bytes - (size_t)l0.total) / 16) + 1;
+    int64_t lo = 0, hi = (int64_t)((ws_bytes - (size_t)l0.total) / 8) + 1;
     if (hi > (int64_t)((1u << 30) - 1u)) hi = (int64_t)((1u << 30) - 1u);
     Layout t;
     while (lo < hi) {   // largest cap whose layout fits
@@ -147,8 +151,8 @@ int d4dgs_workspace_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_confi
     out->tiles_touched = L.tiles_touched;
     out->rect = L.rect;
     out->depth_order = L.depth_vals[L.depth_passes & 1];
-    out->tile_keys = L.tile_keys[L.tile_passes & 1];
-    out->tile_vals = L.tile_vals[L.tile_passes & 1];
+    out->tile_keys = L.tile_keys[L.final_buf()];
+    out->tile_vals = L.packed ? -1 : L.tile_vals[L.final_buf()];
     out->ranges = L.ranges;
     out->final_T = L.final_T;
     out->n_contrib = L.n_contrib;
@@ -158,6 +162,8 @@ int d4dgs_workspace_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_confi
     out->tiles_y = L.tiles_y;
     out->depth_passes = L.depth_passes;
     out->tile_passes = L.tile_passes;
+    out->id_bits = L.id_bits;
+    out->packed = L.packed ? 1 : 0;
     return D4DGS_OK;
 }
 
@@ -302,8 +308,7 @@ int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, fl
 int d4dgs_launches_per_frame(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg) {
     Layout L;
     if (!make_layout(n, cam, cfg, 0, &L)) return D4DGS_ERR_INVALID_ARG;
-    if (n == 0) return 1;   // only the blend (background)
-    return 1 + sort_launch_count(L) + 1;
+    return (n > 0 ? 1 : 0) + sort_launch_count(L) + 1;
 }
 
 const char *d4dgs_strerror(int code) {

@@ -23,8 +23,8 @@ namespace {
 // render path).
 template <int TS, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TS *TS)
-blend_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids, const float4 *__restrict__ rec,
-             uint32_t n, int width, int height, int tiles_x, float bg0, float bg1, float bg2, float *__restrict__ out_rgb,
+blend_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids, uint32_t id_mask,
+             const float4 *__restrict__ rec, uint32_t n, uint32_t cap, int width, int height, int tiles_x, float bg0, float bg1, float bg2, float *__restrict__ out_rgb,
              float *__restrict__ out_T, uint32_t *__restrict__ out_nc, unsigned long long *counts) {
     constexpr int NT = TS * TS;
     __shared__ float4 s_g[BATCH];    // u, v, A = -a/2, B = -b
@@ -36,7 +36,9 @@ blend_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
     const int px = tx * TS + (int)(threadIdx.x % TS), py = ty * TS + (int)(threadIdx.x / TS);
     const bool inside = px < width && py < height;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const uint2 rg = ranges[tile];
+    uint2 rg = ranges[tile];
+    rg.y = min(rg.y, cap);   // ranges are written clamped; this keeps every read in bounds regardless
+    rg.x = min(rg.x, rg.y);
 
     float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
     uint32_t last = 0;
@@ -48,7 +50,7 @@ blend_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
         for (int k = threadIdx.x; k < BATCH; k += NT) {
             const uint32_t j = start + (uint32_t)k;
             if (j < rg.y) {
-                uint32_t id = ids[j];
+                uint32_t id = ids[j] & id_mask;
                 if (id >= n) id = 0;   // only after a timed-out sort pass; keeps the gather in bounds
                 const float4 r0 = rec[3 * (size_t)id + 0];
                 const float4 r1 = rec[3 * (size_t)id + 1];
@@ -103,18 +105,24 @@ blend_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
     }
 }
 
+// The Gaussian id of sorted pair j is ids[j] & id_mask.
+const uint32_t *pair_ids(const Layout &L, void *ws) {
+    return at<uint32_t>(ws, L.packed ? L.tile_keys[L.final_buf()] : L.tile_vals[L.final_buf()]);
+}
+uint32_t id_mask(const Layout &L) { return L.packed ? (uint32_t)((1ull << L.id_bits) - 1ull) : 0xFFFFFFFFu; }
+
 template <int TS, int BATCH>
 cudaError_t launch_ts(const Layout &L, const d4dgs_config &cfg, void *ws, float *out_rgb, cudaStream_t st,
                       unsigned long long *counts) {
     if (counts)
         blend_kernel<TS, BATCH, true><<<L.ntiles, TS * TS, 0, st>>>(
-            at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_vals[L.tile_passes & 1]), at<float4>(ws, L.records),
-            (uint32_t)L.n, L.width, L.height, L.tiles_x, cfg.bg[0], cfg.bg[1], cfg.bg[2], out_rgb, at<float>(ws, L.final_T),
+            at<uint2>(ws, L.ranges), pair_ids(L, ws), id_mask(L), at<float4>(ws, L.records),
+            (uint32_t)L.n, (uint32_t)L.cap, L.width, L.height, L.tiles_x, cfg.bg[0], cfg.bg[1], cfg.bg[2], out_rgb, at<float>(ws, L.final_T),
             at<uint32_t>(ws, L.n_contrib), counts);
     else
         blend_kernel<TS, BATCH, false><<<L.ntiles, TS * TS, 0, st>>>(
-            at<uint2>(ws, L.ranges), at<uint32_t>(ws, L.tile_vals[L.tile_passes & 1]), at<float4>(ws, L.records),
-            (uint32_t)L.n, L.width, L.height, L.tiles_x, cfg.bg[0], cfg.bg[1], cfg.bg[2], out_rgb, at<float>(ws, L.final_T),
+            at<uint2>(ws, L.ranges), pair_ids(L, ws), id_mask(L), at<float4>(ws, L.records),
+            (uint32_t)L.n, (uint32_t)L.cap, L.width, L.height, L.tiles_x, cfg.bg[0], cfg.bg[1], cfg.bg[2], out_rgb, at<float>(ws, L.final_T),
             at<uint32_t>(ws, L.n_contrib), nullptr);
     return cudaGetLastError();
 }

@@ -24,15 +24,14 @@ constexpr int kSortIPT = 15;                              // keys per thread
 constexpr int kSortItems = kSortThreads * kSortIPT;       // 3840 keys per partition
 constexpr int kRadix = 256;                               // digit bins (<= 8 bits per pass)
 constexpr int kDupThreads = 256;
-constexpr int kDupIPT = 8;
-constexpr int kDupItems = kDupThreads * kDupIPT;          // 2048 depth-ordered Gaussians per partition
+constexpr int kDupItems = kDupThreads;                    // depth-ordered Gaussians per scan partition
 
 // ---- control block (uint32 words at layout.control)
 enum : int {
     kCtlStatus = 0,        // bit 0: key capacity exceeded, bit 1: spin-wait timeout
     kCtlNumKeys = 1,       // total (tile, Gaussian) pairs of the frame (clamped reads use min(cap))
     kCtlNumVisible = 2,    // Gaussians with at least one tile
-    kCtlPartBase = 4,      // partition counters: depth passes 4..7, dup 8, tile passes 9..11
+    kCtlPartBase = 4,      // partition counters: depth passes 4..7, scan+emit 8, tile passes 9..11
     kCtlDepthHist = 64,    // 4 x 256 digit counts of the depth keys
     kCtlTileHist = 64 + 4 * kRadix,   // 3 x 256 digit counts of the tile keys
     kCtlWords = 2048
@@ -49,14 +48,21 @@ struct Layout {
     int32_t depth_passes = 4;
     int32_t tile_bits = 0, tile_passes = 0;
     int32_t tile_shift[3] = {0, 0, 0}, tile_pass_bits[3] = {0, 0, 0};
+    // pairs are packed as (tile << id_bits | id) in one uint32 when they fit,
+    // else kept as a tile key plus a separate Gaussian-id value
+    int32_t id_bits = 0;
+    bool packed = true;
     int64_t cap = 0;
     int64_t parts_depth = 0, parts_dup = 0, parts_tile = 0;
     // zero-initialised region [0, zero_end)
-    int64_t control = 0, ranges = 0, lb_depth = 0, lb_dup = 0, lb_tile = 0, zero_end = 0;
+    int64_t control = 0, grid = 0, lb_depth = 0, lb_dup = 0, lb_tile = 0, zero_end = 0;
     // the rest
-    int64_t records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
-    int64_t final_T = 0, n_contrib = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {0, 0};
+    int64_t ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
+    int64_t final_T = 0, n_contrib = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
     int64_t total = 0;
+    int32_t grid_w() const { return tiles_x + 1; }
+    // index of the final sorted pair buffer
+    int final_buf() const { return tile_passes & 1; }
 };
 
 // Fills `L` for a workspace holding `cap` keys; returns false on bad arguments.

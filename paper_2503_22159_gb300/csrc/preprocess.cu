@@ -76,7 +76,7 @@ template <int DEG>
 __global__ void __launch_bounds__(256)
 preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ rec,
                   uint32_t *__restrict__ depth_keys, uint32_t *__restrict__ tiles_touched,
-                  ushort4 *__restrict__ rect, uint32_t *__restrict__ ctl) {
+                  ushort4 *__restrict__ rect, uint32_t *__restrict__ ctl, int *__restrict__ grid) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ uint32_t hist[4 * kRadix];
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) hist[i] = 0;
@@ -165,6 +165,12 @@ preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ r
             const int y0 = (int)fmaxf(fy0, 0.0f), y1 = (int)fminf(fy1, (float)(c.tiles_y - 1));
             rc = make_ushort4((unsigned short)x0, (unsigned short)x1, (unsigned short)y0, (unsigned short)y1);
             tiles = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+            // per-tile pair counts as a 2D difference grid ((tiles_x+1) x (tiles_y+1))
+            const int gw = c.tiles_x + 1;
+            atomicAdd(grid + y0 * gw + x0, 1);
+            atomicAdd(grid + y0 * gw + x1 + 1, -1);
+            atomicAdd(grid + (y1 + 1) * gw + x0, -1);
+            atomicAdd(grid + (y1 + 1) * gw + x1 + 1, 1);
             key = __float_as_uint(Z);
             nvis++;
             // ---- conic (rendering only; ordinary arithmetic from here on)
@@ -251,11 +257,12 @@ cudaError_t launch_preprocess(const d4dgs_scene &sc, const CamArgs &c, float t, 
     uint32_t *tt = at<uint32_t>(ws, L.tiles_touched);
     ushort4 *rc = at<ushort4>(ws, L.rect);
     uint32_t *ctl = at<uint32_t>(ws, L.control);
+    int *grid = at<int>(ws, L.grid);
     switch (sc.sh_degree) {
-        case 0: preprocess_kernel<0><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl); break;
-        case 1: preprocess_kernel<1><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl); break;
-        case 2: preprocess_kernel<2><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl); break;
-        default: preprocess_kernel<3><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl); break;
+        case 0: preprocess_kernel<0><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl, grid); break;
+        case 1: preprocess_kernel<1><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl, grid); break;
+        case 2: preprocess_kernel<2><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl, grid); break;
+        default: preprocess_kernel<3><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl, grid); break;
     }
     return cudaGetLastError();
 }

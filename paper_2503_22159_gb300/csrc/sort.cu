@@ -1,17 +1,24 @@
 // sort.cu -- binning of the preprocessed frame into per-tile, depth-ordered
 // lists (the 3DGS fast rasteriser's (tile | depth) ordering, Sec. III-B-2):
 //
+//   0. tilecount: the per-tile pair counts, accumulated by the preprocess as a
+//      2D difference grid (4 atomics per Gaussian rectangle), are integrated
+//      into counts, exclusive-scanned into each tile's [start, end) range and
+//      reduced into the digit histograms of every tile-sort pass; no pass over
+//      the pairs is needed for either;
 //   1. onesweep LSD radix sort of the N depth keys (4 passes of 8 bits; the
-//      first pass generates the Gaussian ids as values), giving the Gaussians
-//      in (depth, id) order;
-//   2. dup: exclusive scan of the tile counts in that order, fused with the
-//      emission of one (tile, id) pair per covered tile (chained scan with
-//      decoupled look-back), plus the digit histograms of the tile ids;
-//   3. onesweep LSD radix sort of the pairs by tile id (ceil(log2 tiles) bits
-//      in <= 8-bit passes).  The sort is stable, so every tile's list stays in
-//      (depth, id) order -- the same order a (tile << 32 | depth) key sort gives,
-//      with 4-byte instead of 8-byte keys and 2 passes instead of 6 at 1352x1014;
-//   4. ranges: [start, end) of every tile's run.
+//      first pass generates the Gaussian ids as values): Gaussians in
+//      (depth, id) order;
+//   2. emit: exclusive scan of the tile counts in that order (chained scan with
+//      decoupled look-back over 256-Gaussian partitions) fused with the
+//      emission of one pair per covered tile, a warp per Gaussian writing its
+//      pairs as one coalesced run.  A pair is packed as (tile << id_bits | id)
+//      in one uint32 when it fits (otherwise tile key + id value);
+//   3. onesweep LSD radix sort of the pairs by their tile bits
+//      (ceil(log2 tiles) bits in <= 8-bit passes).  The sort is stable, so
+//      every tile's list stays in (depth, id) order -- the order a
+//      (tile << 32 | depth) sort gives, with 4-byte instead of 12-byte records
+//      and 2 passes instead of 6 at 1352x1014 / 16 px.
 //
 // Each onesweep pass is one persistent launch: CTAs take partitions in launch
 // order from an atomic counter, rank their keys with warp match-any, publish
@@ -59,18 +66,19 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
 }
 
 // One onesweep pass over `count` keys (count read on the device when
-// count_ptr is given, clamped to count_cap).  digit = (key >> shift) & mask.
-template <bool IOTA>
-__global__ void __launch_bounds__(kSortThreads)
+// count_ptr is given, clamped to count_cap); digit = (key >> shift) & mask.
+// KV: keys carry a separate uint32 value (IOTA: the value is the key's index).
+template <bool KV, bool IOTA>
+__global__ void __launch_bounds__(kSortThreads, KV ? 3 : 4)
 onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *count_ptr,
                 uint32_t count_const, uint32_t count_cap, int shift, uint32_t mask,
                 const uint32_t *__restrict__ hist, uint32_t *lookback, uint32_t *part_counter, uint32_t *status) {
     __shared__ uint32_t s_warp_hist[8][kRadix];
     __shared__ uint32_t s_keys[kSortItems];
-    __shared__ uint32_t s_vals[kSortItems];
+    __shared__ uint32_t s_vals[KV ? kSortItems : 1];
+    __shared__ uint32_t s_delta[kRadix];   // global_start - local_start of each digit
     __shared__ uint32_t s_local_start[kRadix];
-    __shared__ uint32_t s_global_start[kRadix];
     __shared__ uint32_t s_scan[8];
     __shared__ uint32_t s_part;
 
@@ -92,14 +100,14 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         const uint32_t base = part * kSortItems;
 
         // ---- load (warp-striped: item k of lane l is base + warp*32*IPT + k*32 + l)
-        uint32_t keys[kSortIPT], vals[kSortIPT], rank[kSortIPT];
+        uint32_t keys[kSortIPT], vals[KV ? kSortIPT : 1], rank[kSortIPT];
         const uint32_t wbase = base + warp * 32 * kSortIPT + lane;
 #pragma unroll
         for (int k = 0; k < kSortIPT; k++) {
             const uint32_t idx = wbase + k * 32;
             const bool ok = idx < count;
             keys[k] = ok ? keys_in[idx] : 0xFFFFFFFFu;
-            vals[k] = IOTA ? idx : (ok ? vals_in[idx] : 0u);
+            if (KV) vals[KV ? k : 0] = IOTA ? idx : (ok ? vals_in[idx] : 0u);
         }
         // ---- stable rank within the warp (match-any on the digit)
 #pragma unroll
@@ -150,7 +158,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
             }
             st_volatile_u32(lb + d, kFlagInc | ((excl + bcount) & kValMask));
         }
-        s_global_start[d] = hist_excl + excl;
+        s_delta[d] = hist_excl + excl - lstart;
         __syncthreads();
         // ---- scatter into shared memory in digit order
 #pragma unroll
@@ -158,41 +166,99 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
             const uint32_t dd = (keys[k] >> shift) & mask;
             const uint32_t pos = s_local_start[dd] + s_warp_hist[warp][dd] + rank[k];
             s_keys[pos] = keys[k];
-            s_vals[pos] = vals[k];
+            if (KV) s_vals[KV ? pos : 0] = vals[KV ? k : 0];
         }
         __syncthreads();
         // ---- write out: consecutive threads write consecutive positions of a digit run
         for (int i = tid; i < kSortItems; i += kSortThreads) {
             const uint32_t key = s_keys[i];
-            const uint32_t dd = (key >> shift) & mask;
-            const uint32_t dest = s_global_start[dd] + (uint32_t)i - s_local_start[dd];
+            const uint32_t dest = (uint32_t)i + s_delta[(key >> shift) & mask];
             if (dest < count) {
                 keys_out[dest] = key;
-                vals_out[dest] = s_vals[i];
+                if (KV) vals_out[dest] = s_vals[KV ? i : 0];
             }
         }
         __syncthreads();
     }
 }
 
-// Scan of the tile counts in depth order fused with the pair emission.
-__global__ void __launch_bounds__(kDupThreads)
-dup_kernel(const uint32_t *__restrict__ order, uint32_t n, const uint32_t *__restrict__ tiles_touched,
-           const ushort4 *__restrict__ rect, int tiles_x, uint32_t cap, uint32_t *__restrict__ tile_keys,
-           uint32_t *__restrict__ tile_vals, unsigned long long *lookback, uint32_t *ctl, int tile_passes,
-           int sh0, int sh1, int sh2, uint32_t mk0, uint32_t mk1, uint32_t mk2) {
-    __shared__ uint32_t s_incl[kDupItems];
-    __shared__ uint32_t s_ids[kDupItems];
-    __shared__ ushort4 s_rect[kDupItems];
+// Per-tile pair counts from the 2D difference grid; ranges; digit histograms of
+// the tile passes; the total K and the capacity check.  One CTA.
+__global__ void __launch_bounds__(1024)
+tilecount_kernel(int *grid, int tiles_x, int tiles_y, uint2 *__restrict__ ranges, uint32_t *ctl, uint32_t cap,
+                 int tile_passes, int sh0, int sh1, int sh2, uint32_t mk0, uint32_t mk1, uint32_t mk2) {
+    __shared__ unsigned long long s_warp[32];
     __shared__ uint32_t s_hist[3 * kRadix];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    const int gw = tiles_x + 1, gh = tiles_y + 1;
+    for (int i = tid; i < 3 * kRadix; i += nt) s_hist[i] = 0;
+    for (int r = tid; r < gh; r += nt) {          // integrate along x
+        int acc = 0;
+        for (int x = 0; x < gw; x++) { acc += grid[r * gw + x]; grid[r * gw + x] = acc; }
+    }
+    __syncthreads();
+    for (int c = tid; c < gw; c += nt) {          // then along y
+        int acc = 0;
+        for (int y = 0; y < gh; y++) { acc += grid[y * gw + c]; grid[y * gw + c] = acc; }
+    }
+    __syncthreads();
+    // exclusive scan over tiles in row-major order, one contiguous chunk per thread
+    const int ntiles = tiles_x * tiles_y;
+    const int chunk = (ntiles + nt - 1) / nt;
+    const int t0 = min(tid * chunk, ntiles), t1 = min(t0 + chunk, ntiles);
+    unsigned long long sum = 0;
+    for (int t = t0; t < t1; t++) sum += (unsigned)grid[(t / tiles_x) * gw + (t % tiles_x)];
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+    for (int w = 0; w < nt / 32; w++) {
+        if (w < warp) before += s_warp[w];
+        all += s_warp[w];
+    }
+    unsigned long long run = before + x - sum;
+    for (int t = t0; t < t1; t++) {
+        const uint32_t c = (uint32_t)grid[(t / tiles_x) * gw + (t % tiles_x)];
+        const unsigned long long a = run < cap ? run : cap, b = run + c < cap ? run + c : cap;
+        ranges[t] = make_uint2((uint32_t)a, (uint32_t)b);
+        // digit counts of the pairs that fit in the capacity (the ones that get sorted)
+        const uint32_t kept = (uint32_t)(b - a);
+        if (kept) {
+            atomicAdd(&s_hist[(t >> sh0) & mk0], kept);
+            if (tile_passes > 1) atomicAdd(&s_hist[kRadix + ((t >> sh1) & mk1)], kept);
+            if (tile_passes > 2) atomicAdd(&s_hist[2 * kRadix + ((t >> sh2) & mk2)], kept);
+        }
+        run += c;
+    }
+    __syncthreads();
+    for (int i = tid; i < tile_passes * kRadix; i += nt) ctl[kCtlTileHist + i] = s_hist[i];
+    if (tid == 0) {
+        ctl[kCtlNumKeys] = all > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)all;
+        if (all > cap) atomicOr(ctl + kCtlStatus, kStatusCapacity);
+    }
+}
+
+// Scan of the tile counts in depth order fused with the pair emission.
+template <bool PACKED>
+__global__ void __launch_bounds__(kDupThreads)
+emit_kernel(const uint32_t *__restrict__ order, uint32_t n, const uint32_t *__restrict__ tiles_touched,
+            const ushort4 *__restrict__ rect, int tiles_x, uint32_t cap, int id_bits,
+            uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, unsigned long long *lookback,
+            uint32_t *ctl) {
+    __shared__ uint32_t s_off[kDupItems], s_cnt[kDupItems], s_id[kDupItems];
+    __shared__ ushort4 s_rect[kDupItems];
     __shared__ uint32_t s_scan[8];
-    __shared__ uint32_t s_part, s_total;
+    __shared__ uint32_t s_part;
     __shared__ unsigned long long s_excl;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *status = ctl + kCtlStatus;
     uint32_t *part_counter = ctl + kCtlPartBase + 4;
-    for (int i = tid; i < 3 * kRadix; i += kDupThreads) s_hist[i] = 0;
     const uint32_t num_parts = (n + kDupItems - 1) / kDupItems;
 
     for (;;) {
@@ -200,33 +266,24 @@ dup_kernel(const uint32_t *__restrict__ order, uint32_t n, const uint32_t *__res
         __syncthreads();
         const uint32_t part = s_part;
         if (part >= num_parts) break;
-        const uint32_t base = part * kDupItems;
-        // ---- blocked load: thread t owns positions base + t*IPT + k
-        uint32_t cnt[kDupIPT];
-        uint32_t run = 0;
-#pragma unroll
-        for (int k = 0; k < kDupIPT; k++) {
-            const uint32_t pos = base + tid * kDupIPT + k;
-            uint32_t id = 0, c = 0;
-            ushort4 r = make_ushort4(0, 0, 0, 0);
-            if (pos < n) {
-                id = order[pos];
-                if (id < n) {   // always true unless an earlier pass gave up on a spin-wait
-                    c = tiles_touched[id];
-                    if (c) r = rect[id];
-                } else {
-                    id = 0;
-                }
+        const uint32_t pos = part * kDupItems + tid;
+        uint32_t id = 0, c = 0;
+        ushort4 r = make_ushort4(0, 0, 0, 0);
+        if (pos < n) {
+            id = order[pos];
+            if (id < n) {   // always true unless an earlier pass gave up on a spin-wait
+                c = tiles_touched[id];
+                if (c) r = rect[id];
+            } else {
+                id = 0;
             }
-            s_ids[tid * kDupIPT + k] = id;
-            s_rect[tid * kDupIPT + k] = r;
-            run += c;
-            cnt[k] = run;   // thread-local inclusive prefix
         }
         uint32_t total;
-        const uint32_t texcl = block_exclusive_scan_256(run, s_scan, &total);
-#pragma unroll
-        for (int k = 0; k < kDupIPT; k++) s_incl[tid * kDupIPT + k] = texcl + cnt[k];
+        const uint32_t local = block_exclusive_scan_256(c, s_scan, &total);
+        s_off[tid] = local;
+        s_cnt[tid] = c;
+        s_id[tid] = id;
+        s_rect[tid] = r;
         if (tid == 0) {
             unsigned long long excl = 0;
             unsigned long long *lb = lookback + part;
@@ -251,54 +308,35 @@ dup_kernel(const uint32_t *__restrict__ order, uint32_t n, const uint32_t *__res
                 st_volatile_u64(lb, kFlagInc64 | ((excl + total) & kValMask64));
             }
             s_excl = excl;
-            s_total = total;
-            if (part == num_parts - 1) {
-                const unsigned long long all = excl + total;
-                ctl[kCtlNumKeys] = all > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)all;
-                if (all > cap) atomicOr(status, kStatusCapacity);
-            }
         }
         __syncthreads();
-        // ---- emission: pair j of this partition belongs to the first item with incl > j
-        const uint32_t tot = s_total;
+        // ---- emission: warp w writes the pairs of Gaussians w*32 .. w*32+31, one run each
         const unsigned long long gexcl = s_excl;
-        for (uint32_t j = tid; j < tot; j += kDupThreads) {
-            int lo = 0, hi = kDupItems - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_incl[mid] > j) hi = mid; else lo = mid + 1;
-            }
-            const uint32_t start = lo ? s_incl[lo - 1] : 0u;
-            const uint32_t l = j - start;
-            const ushort4 r = s_rect[lo];
-            const uint32_t w = (uint32_t)r.y - (uint32_t)r.x + 1u;
-            const uint32_t ty = (uint32_t)r.z + l / w, tx = (uint32_t)r.x + l % w;
-            const uint32_t tile = ty * (uint32_t)tiles_x + tx;
-            const unsigned long long o = gexcl + j;
-            if (o < cap) {
-                tile_keys[o] = tile;
-                tile_vals[o] = s_ids[lo];
-                atomicAdd(&s_hist[(tile >> sh0) & mk0], 1u);
-                if (tile_passes > 1) atomicAdd(&s_hist[kRadix + ((tile >> sh1) & mk1)], 1u);
-                if (tile_passes > 2) atomicAdd(&s_hist[2 * kRadix + ((tile >> sh2) & mk2)], 1u);
+        for (int q = warp * 32; q < warp * 32 + 32; q++) {
+            const uint32_t cq = s_cnt[q];
+            if (!cq) continue;
+            const ushort4 rq = s_rect[q];
+            const uint32_t gid = s_id[q];
+            const int wdt = (int)rq.y - (int)rq.x + 1;
+            const float inv_w = 1.0f / (float)wdt;
+            const unsigned long long off = gexcl + s_off[q];
+            for (uint32_t j = lane; j < cq; j += 32) {
+                int ty = __float2int_rz((float)j * inv_w);
+                int tx = (int)j - ty * wdt;
+                if (tx < 0) { ty--; tx += wdt; } else if (tx >= wdt) { ty++; tx -= wdt; }
+                const uint32_t tile = (uint32_t)(((int)rq.z + ty) * tiles_x + (int)rq.x + tx);
+                const unsigned long long o = off + j;
+                if (o < cap) {
+                    if (PACKED) {
+                        keys_out[o] = (tile << id_bits) | gid;
+                    } else {
+                        keys_out[o] = tile;
+                        vals_out[o] = gid;
+                    }
+                }
             }
         }
         __syncthreads();
-    }
-    __syncthreads();
-    for (int i = tid; i < tile_passes * kRadix; i += kDupThreads)
-        if (s_hist[i]) atomicAdd(ctl + kCtlTileHist + i, s_hist[i]);
-}
-
-// [start, end) of every tile's run in the sorted pairs (ranges pre-zeroed).
-__global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *ctl, uint32_t cap,
-                              uint32_t ntiles, uint2 *__restrict__ ranges) {
-    const uint32_t k = min(ctl[kCtlNumKeys], cap);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
-        const uint32_t t = keys[i];
-        if (t >= ntiles) continue;   // only after a timed-out pass; keeps every write in bounds
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-        if (i + 1 == k || keys[i + 1] != t) ranges[t].y = i + 1;
     }
 }
 
@@ -310,18 +348,29 @@ int occupancy_blocks(const void *fn, int threads) {
 
 }  // namespace
 
-int sort_launch_count(const Layout &L) { return L.depth_passes + 1 + L.tile_passes + 1; }
+int sort_launch_count(const Layout &L) { return L.n == 0 ? 1 : 1 + L.depth_passes + 1 + L.tile_passes; }
 
 cudaError_t launch_sort(const Layout &L, void *ws, cudaStream_t st, int num_sms) {
-    if (L.n == 0) return cudaSuccess;
     uint32_t *ctl = at<uint32_t>(ws, L.control);
     uint32_t *status = ctl + kCtlStatus;
-    static int occ_sort_iota = 0, occ_sort = 0, occ_dup = 0;
-    if (!occ_sort) {
-        occ_sort_iota = occupancy_blocks((const void *)onesweep_kernel<true>, kSortThreads);
-        occ_sort = occupancy_blocks((const void *)onesweep_kernel<false>, kSortThreads);
-        occ_dup = occupancy_blocks((const void *)dup_kernel, kDupThreads);
+    static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_emit_p = 0, occ_emit_u = 0;
+    if (!occ_kv) {
+        occ_iota = occupancy_blocks((const void *)onesweep_kernel<true, true>, kSortThreads);
+        occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false>, kSortThreads);
+        occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false>, kSortThreads);
+        occ_emit_p = occupancy_blocks((const void *)emit_kernel<true>, kDupThreads);
+        occ_emit_u = occupancy_blocks((const void *)emit_kernel<false>, kDupThreads);
     }
+    uint32_t sh[3], mk[3];
+    for (int p = 0; p < 3; p++) {
+        sh[p] = (uint32_t)L.tile_shift[p];
+        mk[p] = L.tile_pass_bits[p] ? (1u << L.tile_pass_bits[p]) - 1u : 0u;
+    }
+    // ---- 0. per-tile counts, ranges, tile digit histograms
+    tilecount_kernel<<<1, 1024, 0, st>>>(at<int>(ws, L.grid), L.tiles_x, L.tiles_y, at<uint2>(ws, L.ranges), ctl,
+                                         (uint32_t)L.cap, L.tile_passes, sh[0], sh[1], sh[2], mk[0], mk[1], mk[2]);
+    // (always launched: it writes every tile's range, all empty when N = 0)
+    if (L.n == 0) return cudaGetLastError();
     // ---- 1. depth sort: depth_keys[0] -> ... -> depth_keys[0] (4 passes), ids in depth_vals[0]
     const uint32_t n = (uint32_t)L.n;
     for (int p = 0; p < L.depth_passes; p++) {
@@ -332,58 +381,51 @@ cudaError_t launch_sort(const Layout &L, void *ws, cudaStream_t st, int num_sms)
         const uint32_t *hist = ctl + kCtlDepthHist + p * kRadix;
         uint32_t *lb = at<uint32_t>(ws, L.lb_depth) + (size_t)p * L.parts_depth * kRadix;
         uint32_t *pc = ctl + kCtlPartBase + p;
-        int64_t grid = L.parts_depth;
-        if (p == 0) {
-            grid = grid < (int64_t)occ_sort_iota * num_sms ? grid : (int64_t)occ_sort_iota * num_sms;
-            onesweep_kernel<true><<<(int)grid, kSortThreads, 0, st>>>(kin, nullptr, kout, vout, nullptr, n, n, 8 * p,
-                                                                      0xFFu, hist, lb, pc, status);
-        } else {
-            grid = grid < (int64_t)occ_sort * num_sms ? grid : (int64_t)occ_sort * num_sms;
-            onesweep_kernel<false><<<(int)grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, nullptr, n, n, 8 * p,
+        const int64_t gmax = (int64_t)(p == 0 ? occ_iota : occ_kv) * num_sms;
+        const int grid = (int)(L.parts_depth < gmax ? L.parts_depth : gmax);
+        if (p == 0)
+            onesweep_kernel<true, true><<<grid, kSortThreads, 0, st>>>(kin, nullptr, kout, vout, nullptr, n, n, 8 * p,
                                                                        0xFFu, hist, lb, pc, status);
-        }
+        else
+            onesweep_kernel<true, false><<<grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, nullptr, n, n, 8 * p,
+                                                                        0xFFu, hist, lb, pc, status);
     }
     const uint32_t *order = at<uint32_t>(ws, L.depth_vals[L.depth_passes & 1]);
-    // ---- 2. scan + duplicate
+    // ---- 2. scan + emission in depth order
     {
-        int64_t grid = L.parts_dup;
-        const int64_t gmax = (int64_t)occ_dup * num_sms;
-        if (grid > gmax) grid = gmax;
-        uint32_t m[3], sh[3];
-        for (int p = 0; p < 3; p++) {
-            sh[p] = (uint32_t)L.tile_shift[p];
-            m[p] = (1u << L.tile_pass_bits[p]) - 1u;
-        }
-        dup_kernel<<<(int)grid, kDupThreads, 0, st>>>(
-            order, n, at<uint32_t>(ws, L.tiles_touched), at<ushort4>(ws, L.rect), L.tiles_x, (uint32_t)L.cap,
-            at<uint32_t>(ws, L.tile_keys[0]), at<uint32_t>(ws, L.tile_vals[0]),
-            at<unsigned long long>(ws, L.lb_dup), ctl, L.tile_passes, sh[0], sh[1], sh[2], m[0], m[1], m[2]);
+        const int64_t gmax = (int64_t)(L.packed ? occ_emit_p : occ_emit_u) * num_sms;
+        const int grid = (int)(L.parts_dup < gmax ? L.parts_dup : gmax);
+        uint32_t *vals0 = L.packed ? nullptr : at<uint32_t>(ws, L.tile_vals[0]);
+        if (L.packed)
+            emit_kernel<true><<<grid, kDupThreads, 0, st>>>(order, n, at<uint32_t>(ws, L.tiles_touched),
+                                                            at<ushort4>(ws, L.rect), L.tiles_x, (uint32_t)L.cap,
+                                                            L.id_bits, at<uint32_t>(ws, L.tile_keys[0]), vals0,
+                                                            at<unsigned long long>(ws, L.lb_dup), ctl);
+        else
+            emit_kernel<false><<<grid, kDupThreads, 0, st>>>(order, n, at<uint32_t>(ws, L.tiles_touched),
+                                                             at<ushort4>(ws, L.rect), L.tiles_x, (uint32_t)L.cap,
+                                                             L.id_bits, at<uint32_t>(ws, L.tile_keys[0]), vals0,
+                                                             at<unsigned long long>(ws, L.lb_dup), ctl);
     }
-    // ---- 3. tile sort
+    // ---- 3. stable sort of the pairs by tile bits
+    const int key_shift = L.packed ? L.id_bits : 0;
     for (int p = 0; p < L.tile_passes; p++) {
         const uint32_t *kin = at<uint32_t>(ws, L.tile_keys[p & 1]);
         uint32_t *kout = at<uint32_t>(ws, L.tile_keys[(p + 1) & 1]);
-        const uint32_t *vin = at<uint32_t>(ws, L.tile_vals[p & 1]);
-        uint32_t *vout = at<uint32_t>(ws, L.tile_vals[(p + 1) & 1]);
         const uint32_t *hist = ctl + kCtlTileHist + p * kRadix;
         uint32_t *lb = at<uint32_t>(ws, L.lb_tile) + (size_t)p * L.parts_tile * kRadix;
         uint32_t *pc = ctl + kCtlPartBase + 5 + p;
-        int64_t grid = L.parts_tile;
-        const int64_t gmax = (int64_t)occ_sort * num_sms;
-        if (grid > gmax) grid = gmax;
+        const int64_t gmax = (int64_t)(L.packed ? occ_k : occ_kv) * num_sms;
+        int64_t grid = L.parts_tile < gmax ? L.parts_tile : gmax;
         if (grid < 1) grid = 1;
-        onesweep_kernel<false><<<(int)grid, kSortThreads, 0, st>>>(
-            kin, vin, kout, vout, ctl + kCtlNumKeys, 0u, (uint32_t)L.cap, L.tile_shift[p],
-            (1u << L.tile_pass_bits[p]) - 1u, hist, lb, pc, status);
-    }
-    // ---- 4. ranges
-    {
-        const uint32_t *keys = at<uint32_t>(ws, L.tile_keys[L.tile_passes & 1]);
-        int64_t grid = (L.cap + 255) / 256;
-        if (grid > (int64_t)num_sms * 16) grid = (int64_t)num_sms * 16;
-        if (grid < 1) grid = 1;
-        ranges_kernel<<<(int)grid, 256, 0, st>>>(keys, ctl, (uint32_t)L.cap, (uint32_t)L.ntiles,
-                                                at<uint2>(ws, L.ranges));
+        if (L.packed)
+            onesweep_kernel<false, false><<<(int)grid, kSortThreads, 0, st>>>(
+                kin, nullptr, kout, nullptr, ctl + kCtlNumKeys, 0u, (uint32_t)L.cap, key_shift + L.tile_shift[p],
+                mk[p], hist, lb, pc, status);
+        else
+            onesweep_kernel<true, false><<<(int)grid, kSortThreads, 0, st>>>(
+                kin, at<uint32_t>(ws, L.tile_vals[p & 1]), kout, at<uint32_t>(ws, L.tile_vals[(p + 1) & 1]),
+                ctl + kCtlNumKeys, 0u, (uint32_t)L.cap, L.tile_shift[p], mk[p], hist, lb, pc, status);
     }
     return cudaGetLastError();
 }

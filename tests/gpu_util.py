@@ -42,10 +42,15 @@ def gpu_lists(r, cam):
     k = int(st["n_keys"])
     L = r.layout(cam)
     ntiles = L["tiles_x"] * L["tiles_y"]
-    tiles = _u32(r, "tile_keys", k, cam)
-    ids = _u32(r, "tile_vals", k, cam)
+    keys = _u32(r, "tile_keys", k, cam)
+    if L["packed"]:
+        tiles = keys >> np.uint32(L["id_bits"])
+        ids = keys & np.uint32((1 << L["id_bits"]) - 1)
+    else:
+        tiles = keys
+        ids = _u32(r, "tile_vals", k, cam)
     ranges = _u32(r, "ranges", 2 * ntiles, cam).reshape(ntiles, 2)
-    return dict(tile=tiles, id=ids, ranges=ranges, stats=st)
+    return dict(tile=tiles, id=ids, ranges=ranges, stats=st, packed=bool(L["packed"]))
 
 
 def expected_lists(scene, cam, t, tile):

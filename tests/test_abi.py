@@ -52,13 +52,14 @@ def test_workspace_bytes_monotone_and_layout(d4):
     cfg = d4.config_struct(16, 256)
     b0 = d4.d4dgs_workspace_bytes(300_000, cam, cfg, 0)
     b1 = d4.d4dgs_workspace_bytes(300_000, cam, cfg, 1_000_000)
-    assert b1 > b0 + 16 * 1_000_000
+    assert b1 > b0 + 8 * 1_000_000   # two packed uint32 pair buffers
     L = d4.d4dgs_workspace_layout(300_000, cam, cfg, b1)
     assert L["key_capacity"] == 1_000_000
     assert (L["tiles_x"], L["tiles_y"]) == (85, 64)
     assert L["tile_passes"] == 2 and L["depth_passes"] == 4
+    assert L["id_bits"] == 19 and L["packed"] == 1 and L["tile_vals"] == -1
     offs = [L[k] for k in ("records", "depth_keys", "tiles_touched", "rect", "depth_order", "tile_keys",
-                           "tile_vals", "ranges", "final_T", "n_contrib", "control")]
+                           "ranges", "final_T", "n_contrib", "control")]
     assert all(o % 256 == 0 for o in offs)
     assert max(offs) < b1
     with pytest.raises(d4.D4DGSError):
@@ -110,8 +111,17 @@ def test_invalid_arguments_rejected_on_host(d4):
 def test_launch_count(d4):
     cam = synth.pinhole(1352, 1014)
     cfg = d4.config_struct(16, 256)
-    # preprocess + 4 depth passes + dup + 2 tile passes + ranges + blend
+    # preprocess + tile counts + 4 depth passes + scan/emit + 2 tile passes + blend
     assert d4.d4dgs_launches_per_frame(300_000, cam, cfg) == 10
+
+
+def test_packing_decision(d4):
+    cfg8 = d4.config_struct(8, 64)
+    cam = synth.pinhole(2560, 2048)
+    L = d4.d4dgs_workspace_layout(40_000, cam, cfg8, d4.d4dgs_workspace_bytes(40_000, cam, cfg8, 1000))
+    assert L["id_bits"] == 16 and L["packed"] == 0 and L["tile_vals"] > 0 and L["tile_passes"] == 3
+    L = d4.d4dgs_workspace_layout(20_000, cam, cfg8, d4.d4dgs_workspace_bytes(20_000, cam, cfg8, 1000))
+    assert L["id_bits"] == 15 and L["packed"] == 1
 
 
 def test_product_does_not_import_oracle():

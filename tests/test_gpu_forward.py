@@ -85,6 +85,20 @@ def test_lists_bit_exact_medium_ragged(tile):
     assert nflag <= 5
 
 
+def test_lists_bit_exact_unpacked_pairs():
+    """40,000 Gaussians (16 id bits) on 2560x2048 at 8-px tiles (17 tile bits) do not fit a
+    32-bit packed pair: the sort runs on tile keys with separate id values."""
+    scene = synth.make_scene(40_000, 8, "box20", sh_degree=0)
+    scene.log_scales -= 1.5   # smaller splats keep the pair count moderate
+    cam, t = synth.orbit(2, 2560, 2048, 300)[100]
+    r, _, _ = gu.render(scene, cam, t, tile=8, batch=64)
+    got = gu.gpu_lists(r, cam)
+    assert not got["packed"]
+    b, exp = gu.expected_lists(scene, cam, t, 8)
+    assert r.layout(cam)["tile_passes"] == 3
+    gu.compare_lists(got, b, exp)
+
+
 def test_image_parity_tiny():
     w = synth.tiny_workload()
     cam, t = w.frames[0]
