@@ -103,7 +103,7 @@ typedef struct {
 /* Byte offsets of the workspace buffers (test and profiling hook).  All
  * offsets are from the workspace base; buffers are 256-byte aligned. */
 typedef struct {
-    int64_t records;             /* N x 12 float: (u,v,a,b) (c,o_hat,depth,radius) (r,g,b,0) */
+    int64_t records;             /* N x 12 float: (u,v,a,b) (c,o_hat,depth,radius) (r,g,b,log2 o_hat) */
     int64_t depth_keys;          /* N uint32: float bits of camera z, 0xFFFFFFFF if culled   */
     int64_t tiles_touched;       /* N uint32                                                 */
     int64_t rect;                /* N x 4 uint16: x0, x1, y0, y1 (inclusive tile indices)    */

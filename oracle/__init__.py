@@ -66,6 +66,11 @@ class _SceneF32(ctypes.Structure):
                                  "quats", "opacity_logit")]
 
 
+class _SceneGrad(ctypes.Structure):
+    _fields_ = [(k, c_double_p) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats",
+                                          "opacity_logit", "sh")]
+
+
 class _Camera(ctypes.Structure):
     _fields_ = [("R", ctypes.c_double * 9), ("T", ctypes.c_double * 3), ("fx", ctypes.c_double),
                 ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
@@ -101,9 +106,10 @@ def lib():
                                        ctypes.c_int64, c_uint32_p, c_uint32_p, c_uint32_p]
         _lib.orc_sh_basis.argtypes = [c_double_p, ctypes.c_int, c_double_p]
         _lib.orc_quat_to_rot.argtypes = [c_double_p, c_double_p]
-        if hasattr(_lib, "orc_backward"):
-            _lib.orc_backward.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
-                                          c_double_p, c_double_p, ctypes.POINTER(_Scene)]
+        _lib.orc_backward.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
+                                      c_double_p, c_double_p, ctypes.POINTER(_SceneGrad)]
+        _lib.orc_fingerprint.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_uint64)]
     return _lib
 
 
@@ -277,22 +283,31 @@ def tile_list(b: dict) -> dict:
 
 
 def backward(scene, cam, t: float, dl_drgb, bg=(0.0, 0.0, 0.0)) -> dict:
-    """FP64 adjoint: gradients of sum(dl_drgb * image) w.r.t. every raw parameter."""
+    """FP64 adjoint: gradients of sum(dl_drgb * image) w.r.t. every raw parameter
+    (dl_drgb: (H, W, 3); the render uses the temporal cull, as render() does)."""
     keep = _Keep()
     s = _scene64(scene, keep)
     c = _camera64(cam)
     grads = {k: np.zeros(np.asarray(getattr(scene, k)).shape) for k in (
         "means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh")}
-    gs = _Scene()
-    gs.n, gs.sh_degree = scene.n, scene.sh_degree
-    for k, v in grads.items():
-        setattr(gs, k, _p(v, ctypes.c_double))
-    gs.cov3d = None
+    gs = _SceneGrad(*[_p(grads[k], ctypes.c_double) for k in (
+        "means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh")])
     dl = _d(dl_drgb)
+    assert dl.shape == (cam.height, cam.width, 3)
     bgv = _d(np.asarray(bg, np.float64))
     lib().orc_backward(ctypes.byref(s), ctypes.byref(c), float(t), _p(dl, ctypes.c_double),
                        _p(bgv, ctypes.c_double), ctypes.byref(gs))
     return grads
+
+
+def fingerprint(scene, cam, t: float) -> np.ndarray:
+    """Per-pixel hash of the blended contributor list (and of active alpha clamps)."""
+    keep = _Keep()
+    s = _scene64(scene, keep)
+    c = _camera64(cam)
+    out = np.zeros(cam.width * cam.height, np.uint64)
+    lib().orc_fingerprint(ctypes.byref(s), ctypes.byref(c), float(t), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    return out
 
 
 if __name__ == "__main__":  # pragma: no cover

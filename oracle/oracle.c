@@ -515,3 +515,355 @@ int64_t orc_emit_keys(int32_t n, const uint32_t *depth_key, const int32_t *rect,
     }
     return k;
 }
+
+/* ---------------------------------------------------------------------------
+ * orc_backward: FP64 adjoint of orc_preprocess + orc_render_pixels (full
+ * frame, temporal cull on) for the loss L = sum(dl_drgb * image).
+ *
+ * Compositing (Eq. 4), back to front over each pixel's blended list with
+ * G = dL/dC, B = the colour behind (starting at bg, B <- alpha c + (1-alpha) B):
+ *   dL/dc_i = alpha_i T_i G,   dL/dalpha_i = T_i G.(c_i - B_{i+1})
+ *   alpha = min(0.99, o_hat e^p): dalpha/dp = alpha, dalpha/do_hat = e^p
+ *   (zero when the 0.99 clamp is active); p = -1/2(a dx^2 + c dy^2) - b dx dy.
+ * Then per Gaussian, the chain of orc_preprocess in reverse:
+ *   conic = Sigma'^-1 -> Sigma' = TM TM^T + 0.3 I -> TM = J W M ->
+ *   J(X) (with the x/z, y/z clamp) and M = R(q/|q|) diag(e^ls);
+ *   (u, v)(X); X = R_cam mu(t) + T_cam; mu(t) = mu + tau V; tau = t - mu_t;
+ *   o_hat = sigmoid(logit) exp(-tau^2 / (2 e^(2 lst)));
+ *   colour = max(0, SH . Y(d) + 0.5), d = (mu(t) - campos)/|mu(t) - campos|.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
+} orc_scene_grad;
+
+/* d Y_k / d(x, y, z) of orc_sh_basis, treating x, y, z as independent. */
+static void sh_basis_grad(const double d[3], int degree, double dY[16][3]) {
+    const double pi = 3.14159265358979323846;
+    double x = d[0], y = d[1], z = d[2];
+    memset(dY, 0, sizeof(double) * 16 * 3);
+    if (degree < 1) return;
+    double c1 = sqrt(3.0 / (4.0 * pi));
+    dY[1][1] = -c1;
+    dY[2][2] = c1;
+    dY[3][0] = -c1;
+    if (degree < 2) return;
+    double xx = x * x, yy = y * y, zz = z * z;
+    double a = 0.5 * sqrt(15.0 / pi), b = 0.25 * sqrt(5.0 / pi), c = 0.25 * sqrt(15.0 / pi);
+    dY[4][0] = a * y; dY[4][1] = a * x;
+    dY[5][1] = -a * z; dY[5][2] = -a * y;
+    dY[6][0] = -2.0 * b * x; dY[6][1] = -2.0 * b * y; dY[6][2] = 4.0 * b * z;
+    dY[7][0] = -a * z; dY[7][2] = -a * x;
+    dY[8][0] = 2.0 * c * x; dY[8][1] = -2.0 * c * y;
+    if (degree < 3) return;
+    double e = 0.25 * sqrt(35.0 / (2.0 * pi)), f = 0.5 * sqrt(105.0 / pi);
+    double g = 0.25 * sqrt(21.0 / (2.0 * pi)), h = 0.25 * sqrt(7.0 / pi);
+    double k = 0.25 * sqrt(105.0 / pi);
+    dY[9][0] = -6.0 * e * x * y; dY[9][1] = -e * (3.0 * xx - 3.0 * yy);
+    dY[10][0] = f * y * z; dY[10][1] = f * x * z; dY[10][2] = f * x * y;
+    dY[11][0] = 2.0 * g * x * y; dY[11][1] = -g * (4.0 * zz - xx - 3.0 * yy); dY[11][2] = -8.0 * g * y * z;
+    dY[12][0] = -6.0 * h * x * z; dY[12][1] = -6.0 * h * y * z; dY[12][2] = h * (6.0 * zz - 3.0 * xx - 3.0 * yy);
+    dY[13][0] = -g * (4.0 * zz - 3.0 * xx - yy); dY[13][1] = 2.0 * g * x * y; dY[13][2] = -8.0 * g * x * z;
+    dY[14][0] = 2.0 * k * x * z; dY[14][1] = -2.0 * k * y * z; dY[14][2] = k * (xx - yy);
+    dY[15][0] = -e * (3.0 * xx - 3.0 * yy); dY[15][1] = 6.0 * e * x * y;
+}
+
+/* dR/dq for R = orc_quat_to_rot(q): dL/dq from dL/dR (both row-major). */
+static void quat_rot_backward(const double q[4], const double dR[9], double dq[4]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    dq[0] = 2.0 * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    dq[1] = 2.0 * (y * dR[1] + z * dR[2] + y * dR[3] - 2.0 * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                   2.0 * x * dR[8]);
+    dq[2] = 2.0 * (-2.0 * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                   2.0 * y * dR[8]);
+    dq[3] = 2.0 * (-2.0 * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.0 * z * dR[4] + y * dR[5] + x * dR[6] +
+                   y * dR[7]);
+}
+
+typedef struct { int32_t idx; double alpha, raw_alpha, T; } orc_blended;
+
+void orc_backward(const orc_scene *sc, const orc_camera *cam, double t, const double *dl_drgb, const double bg[3],
+                  orc_scene_grad *out) {
+    const int n = sc->n, ncoef = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    orc_g2d g;
+    g.drawn = (int32_t *)calloc(n > 0 ? n : 1, sizeof(int32_t));
+    double *buf = (double *)calloc((size_t)(n > 0 ? n : 1) * 15, sizeof(double));
+    g.u = buf; g.v = buf + n; g.depth = buf + 2 * (size_t)n; g.conic = buf + 3 * (size_t)n;
+    g.cov2d = buf + 6 * (size_t)n; g.opacity_t = buf + 9 * (size_t)n; g.rgb = buf + 10 * (size_t)n;
+    g.lambda_max = buf + 13 * (size_t)n;
+    orc_preprocess(sc, cam, t, 1, &g);
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    int nd = 0;
+    for (int i = 0; i < n; i++)
+        if (g.drawn[i]) ids[nd++] = i;
+    /* per-Gaussian gradients of the 2D quantities: u, v, a, b, c, o_hat, r, g, b */
+    double *g2 = (double *)calloc((size_t)(n > 0 ? n : 1) * 9, sizeof(double));
+#pragma omp parallel
+    {
+        double *loc = (double *)calloc((size_t)(n > 0 ? n : 1) * 9, sizeof(double));
+        size_t cap = 1024;
+        orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * cap);
+        orc_blended *bl = (orc_blended *)malloc(sizeof(orc_blended) * cap);
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t q = 0; q < npix; q++) {
+            double x = (double)(q % cam->width) + 0.5, y = (double)(q / cam->width) + 0.5;
+            size_t nc = 0;
+            for (int k = 0; k < nd; k++) {
+                int i = ids[k];
+                double dx = g.u[i] - x, dy = g.v[i] - y;
+                const double *cn = g.conic + 3 * (size_t)i;
+                double p = -0.5 * (cn[0] * dx * dx + cn[2] * dy * dy) - cn[1] * dx * dy;
+                if (p > 0.0) continue;
+                double alpha = fmin(ORC_ALPHA_MAX, g.opacity_t[i] * exp(p));
+                if (alpha < ORC_ALPHA_MIN) continue;
+                if (nc == cap) {
+                    cap *= 2;
+                    cand = (orc_cand *)realloc(cand, sizeof(orc_cand) * cap);
+                    bl = (orc_blended *)realloc(bl, sizeof(orc_blended) * cap);
+                }
+                cand[nc].depth = g.depth[i];
+                cand[nc].idx = i;
+                cand[nc].alpha = alpha;
+                nc++;
+            }
+            qsort(cand, nc, sizeof(orc_cand), cand_cmp);
+            double T = 1.0;
+            size_t nb = 0;
+            for (size_t k = 0; k < nc; k++) {
+                double alpha = cand[k].alpha;
+                double test = T * (1.0 - alpha);
+                if (test < ORC_T_MIN) break;
+                int i = cand[k].idx;
+                const double *cn = g.conic + 3 * (size_t)i;
+                double dx = g.u[i] - x, dy = g.v[i] - y;
+                double p = -0.5 * (cn[0] * dx * dx + cn[2] * dy * dy) - cn[1] * dx * dy;
+                bl[nb].idx = i;
+                bl[nb].alpha = alpha;
+                bl[nb].raw_alpha = g.opacity_t[i] * exp(p);
+                bl[nb].T = T;
+                nb++;
+                T = test;
+            }
+            const double *G = dl_drgb + 3 * q;
+            double B[3] = {bg[0], bg[1], bg[2]};
+            for (size_t kk = nb; kk-- > 0;) {
+                int i = bl[kk].idx;
+                double alpha = bl[kk].alpha, Ti = bl[kk].T;
+                const double *c = g.rgb + 3 * (size_t)i;
+                double *gi = loc + 9 * (size_t)i;
+                double dalpha = 0.0;
+                for (int ch = 0; ch < 3; ch++) {
+                    gi[6 + ch] += alpha * Ti * G[ch];
+                    dalpha += Ti * G[ch] * (c[ch] - B[ch]);
+                    B[ch] = alpha * c[ch] + (1.0 - alpha) * B[ch];
+                }
+                if (bl[kk].raw_alpha > ORC_ALPHA_MAX) continue;   /* clamped: no gradient through alpha */
+                const double *cn = g.conic + 3 * (size_t)i;
+                double dx = g.u[i] - x, dy = g.v[i] - y;
+                double dp = dalpha * alpha;
+                gi[5] += dalpha * alpha / g.opacity_t[i];
+                gi[0] += -dp * (cn[0] * dx + cn[1] * dy);
+                gi[1] += -dp * (cn[1] * dx + cn[2] * dy);
+                gi[2] += -0.5 * dp * dx * dx;
+                gi[3] += -dp * dx * dy;
+                gi[4] += -0.5 * dp * dy * dy;
+            }
+        }
+#pragma omp critical
+        for (size_t j = 0; j < (size_t)n * 9; j++) g2[j] += loc[j];
+        free(loc);
+        free(cand);
+        free(bl);
+    }
+    /* per Gaussian: chain rule back to the raw parameters */
+    double campos[3];
+    cam_position(cam, campos);
+    const double limx = ORC_JAC_CLAMP * (0.5 * cam->width) / cam->fx;
+    const double limy = ORC_JAC_CLAMP * (0.5 * cam->height) / cam->fy;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; i++) {
+        double *gm = out->means + 3 * (size_t)i, *gv = out->velocity + 3 * (size_t)i;
+        double *gls = out->log_scales + 3 * (size_t)i, *gq = out->quats + 4 * (size_t)i;
+        double *gsh = out->sh + (size_t)i * ncoef * 3;
+        for (int j = 0; j < 3; j++) gm[j] = gv[j] = gls[j] = 0.0;
+        for (int j = 0; j < 4; j++) gq[j] = 0.0;
+        for (int j = 0; j < ncoef * 3; j++) gsh[j] = 0.0;
+        out->t_mean[i] = out->log_t_scale[i] = out->opacity_logit[i] = 0.0;
+        if (!g.drawn[i]) continue;
+        const double *G2 = g2 + 9 * (size_t)i;
+        /* ---- forward quantities */
+        double tau = t - sc->t_mean[i];
+        double m[3], X[3];
+        for (int j = 0; j < 3; j++) m[j] = sc->means[3 * (size_t)i + j] + tau * sc->velocity[3 * (size_t)i + j];
+        for (int r = 0; r < 3; r++)
+            X[r] = cam->R[3 * r] * m[0] + cam->R[3 * r + 1] * m[1] + cam->R[3 * r + 2] * m[2] + cam->T[r];
+        double Z = X[2], xz = X[0] / Z, yz = X[1] / Z;
+        int clx = xz < -limx || xz > limx, cly = yz < -limy || yz > limy;
+        double xzc = fmin(limx, fmax(-limx, xz)), yzc = fmin(limy, fmax(-limy, yz));
+        double J[6] = {cam->fx / Z, 0.0, -cam->fx * xzc / Z, 0.0, cam->fy / Z, -cam->fy * yzc / Z};
+        const double *q = sc->quats + 4 * (size_t)i;
+        double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+        double Rq[9], s[3], M[9];
+        orc_quat_to_rot(qn, Rq);
+        for (int j = 0; j < 3; j++) s[j] = exp(sc->log_scales[3 * (size_t)i + j]);
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) M[3 * r + c] = Rq[3 * r + c] * s[c];
+        double Tm[6], TM[6];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++) Tm[3 * r + c] = J[3 * r] * cam->R[c] + J[3 * r + 1] * cam->R[3 + c] + J[3 * r + 2] * cam->R[6 + c];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++) TM[3 * r + c] = Tm[3 * r] * M[c] + Tm[3 * r + 1] * M[3 + c] + Tm[3 * r + 2] * M[6 + c];
+        const double *cv = g.cov2d + 3 * (size_t)i;
+        double s00 = cv[0], s01 = cv[1], s11 = cv[2], det = s00 * s11 - s01 * s01, det2 = det * det;
+        /* ---- conic -> Sigma' */
+        double ga = G2[2], gb = G2[3], gc = G2[4];
+        double d00 = ga * (-s11 * s11 / det2) + gb * (s01 * s11 / det2) + gc * (1.0 / det - s00 * s11 / det2);
+        double d11 = ga * (1.0 / det - s11 * s00 / det2) + gb * (s01 * s00 / det2) + gc * (-s00 * s00 / det2);
+        double d01 = ga * (2.0 * s11 * s01 / det2) + gb * (-1.0 / det - 2.0 * s01 * s01 / det2) + gc * (2.0 * s00 * s01 / det2);
+        /* ---- Sigma' = TM TM^T + 0.3 I -> TM */
+        double dTM[6];
+        for (int k = 0; k < 3; k++) {
+            dTM[k] = 2.0 * d00 * TM[k] + d01 * TM[3 + k];
+            dTM[3 + k] = 2.0 * d11 * TM[3 + k] + d01 * TM[k];
+        }
+        /* ---- TM = Tm M -> Tm, M ; Tm = J W -> J */
+        double dTm[6] = {0}, dM[9] = {0}, dJ[6] = {0};
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++)
+                for (int c = 0; c < 3; c++) {
+                    dTm[3 * r + k] += dTM[3 * r + c] * M[3 * k + c];
+                    dM[3 * k + c] += Tm[3 * r + k] * dTM[3 * r + c];
+                }
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++)
+                for (int c = 0; c < 3; c++) dJ[3 * r + k] += dTm[3 * r + c] * cam->R[3 * k + c];
+        /* ---- J(X) and (u, v)(X) -> X */
+        double dX[3] = {0, 0, 0};
+        double fx = cam->fx, fy = cam->fy;
+        dX[2] += dJ[0] * (-fx / (Z * Z)) + dJ[4] * (-fy / (Z * Z));
+        if (!clx) {
+            dX[0] += dJ[2] * (-fx / (Z * Z));
+            dX[2] += dJ[2] * (2.0 * fx * X[0] / (Z * Z * Z));
+        } else {
+            dX[2] += dJ[2] * (fx * xzc / (Z * Z));
+        }
+        if (!cly) {
+            dX[1] += dJ[5] * (-fy / (Z * Z));
+            dX[2] += dJ[5] * (2.0 * fy * X[1] / (Z * Z * Z));
+        } else {
+            dX[2] += dJ[5] * (fy * yzc / (Z * Z));
+        }
+        dX[0] += G2[0] * fx / Z;
+        dX[2] += -G2[0] * fx * X[0] / (Z * Z);
+        dX[1] += G2[1] * fy / Z;
+        dX[2] += -G2[1] * fy * X[1] / (Z * Z);
+        /* ---- M = R(qn) diag(s) -> qn, ls */
+        double dRq[9];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) dRq[3 * r + c] = dM[3 * r + c] * s[c];
+        for (int c = 0; c < 3; c++) {
+            double ds = 0.0;
+            for (int r = 0; r < 3; r++) ds += dM[3 * r + c] * Rq[3 * r + c];
+            gls[c] = ds * s[c];
+        }
+        double dqn[4];
+        quat_rot_backward(qn, dRq, dqn);
+        double dot = dqn[0] * qn[0] + dqn[1] * qn[1] + dqn[2] * qn[2] + dqn[3] * qn[3];
+        for (int j = 0; j < 4; j++) gq[j] = (dqn[j] - qn[j] * dot) / nq;
+        /* ---- colour: clamp, SH coefficients, view direction */
+        double dir[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};
+        double dn = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        double d[3] = {dir[0] / dn, dir[1] / dn, dir[2] / dn};
+        double Y[16], dY[16][3];
+        orc_sh_basis(d, sc->sh_degree, Y);
+        sh_basis_grad(d, sc->sh_degree, dY);
+        double dd[3] = {0, 0, 0};
+        for (int ch = 0; ch < 3; ch++) {
+            double raw = 0.5;
+            for (int k = 0; k < ncoef; k++) raw += sc->sh[((size_t)i * ncoef + k) * 3 + ch] * Y[k];
+            if (raw < 0.0) continue;   /* clamped at zero */
+            double gcol = G2[6 + ch];
+            for (int k = 0; k < ncoef; k++) {
+                gsh[3 * k + ch] = gcol * Y[k];
+                for (int j = 0; j < 3; j++) dd[j] += gcol * sc->sh[((size_t)i * ncoef + k) * 3 + ch] * dY[k][j];
+            }
+        }
+        double ddot = dd[0] * d[0] + dd[1] * d[1] + dd[2] * d[2];
+        double dm[3];
+        for (int j = 0; j < 3; j++) dm[j] = (dd[j] - d[j] * ddot) / dn;
+        /* ---- X = R_cam m + T_cam -> m */
+        for (int j = 0; j < 3; j++) dm[j] += cam->R[j] * dX[0] + cam->R[3 + j] * dX[1] + cam->R[6 + j] * dX[2];
+        /* ---- m = mu + tau V, o_hat(tau), tau = t - mu_t */
+        double dtau = 0.0;
+        for (int j = 0; j < 3; j++) {
+            gm[j] = dm[j];
+            gv[j] = tau * dm[j];
+            dtau += sc->velocity[3 * (size_t)i + j] * dm[j];
+        }
+        double oh = g.opacity_t[i], st = exp(sc->log_t_scale[i]);
+        double sig = 1.0 / (1.0 + exp(-sc->opacity_logit[i]));
+        double goh = G2[5];
+        out->opacity_logit[i] = goh * oh * (1.0 - sig);
+        dtau += goh * oh * (-tau / (st * st));
+        out->log_t_scale[i] = goh * oh * tau * tau / (st * st);
+        out->t_mean[i] = -dtau;
+    }
+    free(g2);
+    free(ids);
+    free(buf);
+    free(g.drawn);
+}
+
+/* Per-pixel fingerprint of the blended contributor lists (for finite
+ * differences: a parameter step that changes any pixel's list crosses a
+ * discontinuity of the image). */
+void orc_fingerprint(const orc_scene *sc, const orc_camera *cam, double t, uint64_t *out) {
+    const int n = sc->n;
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    orc_g2d g;
+    g.drawn = (int32_t *)calloc(n > 0 ? n : 1, sizeof(int32_t));
+    double *buf = (double *)calloc((size_t)(n > 0 ? n : 1) * 15, sizeof(double));
+    g.u = buf; g.v = buf + n; g.depth = buf + 2 * (size_t)n; g.conic = buf + 3 * (size_t)n;
+    g.cov2d = buf + 6 * (size_t)n; g.opacity_t = buf + 9 * (size_t)n; g.rgb = buf + 10 * (size_t)n;
+    g.lambda_max = buf + 13 * (size_t)n;
+    orc_preprocess(sc, cam, t, 1, &g);
+#pragma omp parallel
+    {
+        size_t cap = 1024;
+        orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * cap);
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t q = 0; q < npix; q++) {
+            double x = (double)(q % cam->width) + 0.5, y = (double)(q / cam->width) + 0.5;
+            size_t nc = 0;
+            for (int i = 0; i < n; i++) {
+                if (!g.drawn[i]) continue;
+                double dx = g.u[i] - x, dy = g.v[i] - y;
+                const double *cn = g.conic + 3 * (size_t)i;
+                double p = -0.5 * (cn[0] * dx * dx + cn[2] * dy * dy) - cn[1] * dx * dy;
+                if (p > 0.0) continue;
+                double alpha = fmin(ORC_ALPHA_MAX, g.opacity_t[i] * exp(p));
+                if (alpha < ORC_ALPHA_MIN) continue;
+                if (nc == cap) { cap *= 2; cand = (orc_cand *)realloc(cand, sizeof(orc_cand) * cap); }
+                cand[nc].depth = g.depth[i];
+                cand[nc].idx = i;
+                cand[nc].alpha = alpha;
+                nc++;
+            }
+            qsort(cand, nc, sizeof(orc_cand), cand_cmp);
+            double T = 1.0;
+            uint64_t h = 1469598103934665603ull;
+            for (size_t k = 0; k < nc; k++) {
+                double test = T * (1.0 - cand[k].alpha);
+                if (test < ORC_T_MIN) break;
+                h = (h ^ (uint64_t)(cand[k].idx + 1)) * 1099511628211ull;
+                h ^= (cand[k].alpha >= 0.99) ? 0x9E3779B97F4A7C15ull : 0ull;   /* alpha clamp active */
+                T = test;
+            }
+            out[q] = h;
+        }
+        free(cand);
+    }
+    free(buf);
+    free(g.drawn);
+}

@@ -108,6 +108,7 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.rect = off; off += align256((int64_t)n * 8);
     l.final_T = off; off += align256(l.pixels * 4);
     l.n_contrib = off; off += align256(l.pixels * 4);
+    l.grad2d = off; off += align256((int64_t)n * 48);
     for (int b = 0; b < 2; b++) { l.tile_keys[b] = off; off += align256(cap * 4); }
     if (!l.packed)
         for (int b = 0; b < 2; b++) { l.tile_vals[b] = off; off += align256(cap * 4); }

@@ -1,11 +1,429 @@
-// backward.cu -- K7/K8: adjoint of the frame render.
+// backward.cu -- adjoint of the frame render ("differentiable projection-first
+// splatting", Sec. III-B-2), in two kernels:
+//
+// K7 blend_backward_kernel: one CTA per tile replays the tile's list back to
+//   front from each pixel's last blended position, recovering T_i = T_{i+1} /
+//   (1 - alpha_i) from the stored final T (no per-pixel lists are kept), with
+//   G = dL/dC and B = the colour behind (B <- alpha c + (1 - alpha) B):
+//     dL/dc_i = alpha_i T_i G,   dL/dalpha_i = T_i G.(c_i - B)
+//     alpha = min(0.99, o_hat e^p): dalpha/dp = alpha, dalpha/do_hat = e^p
+//     p = -1/2 (a dx^2 + c dy^2) - b dx dy  ->  d/du, d/dv, d/da, d/db, d/dc
+//   alpha is recomputed with exactly the forward's single-precision operations,
+//   so every skip / blend decision matches the forward.  Per-Gaussian sums
+//   (u, v, a, b, c, o_hat, r, g, b) are reduced over each warp only when a
+//   lane contributed, gathered per batch in shared memory and added to global
+//   memory once per (tile, Gaussian).
+// K8 preprocess_backward_kernel: one thread per Gaussian, the chain rule of
+//   the preprocess in reverse (conic -> Sigma' -> J W M -> J(X), R(q), scales;
+//   (u, v)(X); SH colour and its view direction; X(mu(t)); mu(t) = mu + tau V;
+//   o_hat(logit, tau, log s_t); tau = t - mu_t), writing every raw gradient.
 #include "d4dgs_internal.cuh"
 
 namespace d4dgs {
 
-cudaError_t launch_backward(const d4dgs_scene &, const CamArgs &, float, const d4dgs_config &, const Layout &, void *,
-                            const float *, const d4dgs_scene_grad &, cudaStream_t, int) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLog2AlphaMin = -7.9943534368588578f;   // log2(1/255)
+constexpr int kG2 = 12;   // floats per Gaussian in the 2D gradient buffer (9 used)
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+template <int TS, int BATCH>
+__global__ void __launch_bounds__(TS *TS)
+blend_backward_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids, uint32_t id_mask,
+                      const float4 *__restrict__ rec, uint32_t n, uint32_t cap, int width, int height, int tiles_x,
+                      float bg0, float bg1, float bg2, const float *__restrict__ final_T,
+                      const uint32_t *__restrict__ n_contrib, const float *__restrict__ dl_drgb,
+                      float *__restrict__ g2) {
+    constexpr int NT = TS * TS;
+    constexpr int NW = NT / 32;
+    __shared__ float4 s_g[BATCH];     // u, v, A, B      (forward exponent form)
+    __shared__ float2 s_h[BATCH];     // C, L
+    __shared__ float4 s_c[BATCH];     // r, g, b
+    __shared__ float4 s_k[BATCH];     // a, b, c, o_hat  (natural conic)
+    __shared__ uint32_t s_id[BATCH];
+    __shared__ float s_acc[BATCH][9];
+    __shared__ uint32_t s_maxlast;
+
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int lane = threadIdx.x & 31;
+    const int px = tx * TS + (int)(threadIdx.x % TS), py = ty * TS + (int)(threadIdx.x / TS);
+    const bool inside = px < width && py < height;
+    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    uint2 rg = ranges[tile];
+    rg.y = min(rg.y, cap);
+    rg.x = min(rg.x, rg.y);
+
+    float T = 1.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f, B0 = bg0, B1 = bg1, B2 = bg2;
+    uint32_t last = 0;
+    if (inside) {
+        const size_t p = (size_t)py * width + px;
+        T = final_T[p];
+        last = min(n_contrib[p], rg.y - rg.x);
+        G0 = dl_drgb[3 * p + 0];
+        G1 = dl_drgb[3 * p + 1];
+        G2 = dl_drgb[3 * p + 2];
+    }
+    if (threadIdx.x == 0) s_maxlast = 0;
+    __syncthreads();
+    atomicMax(&s_maxlast, last);
+    __syncthreads();
+    const uint32_t maxlast = s_maxlast;
+
+    // positions are 1-based: list entry rg.x + pos - 1; walk pos = maxlast .. 1 in batches
+    for (int32_t hi = (int32_t)maxlast; hi > 0; hi -= BATCH) {
+        const int32_t lo = max(hi - BATCH, 0);   // this batch covers positions lo+1 .. hi
+        const int nb = hi - lo;
+        for (int k = threadIdx.x; k < nb; k += NT) {
+            uint32_t id = ids[rg.x + (uint32_t)(lo + k)] & id_mask;
+            if (id >= n) id = 0;
+            const float4 r0 = rec[3 * (size_t)id + 0];
+            const float4 r1 = rec[3 * (size_t)id + 1];
+            const float4 r2 = rec[3 * (size_t)id + 2];
+            s_g[k] = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
+            s_h[k] = make_float2(-0.5f * kLog2e * r1.x, r2.w);
+            s_c[k] = r2;
+            s_k[k] = make_float4(r0.z, r0.w, r1.x, r1.y);
+            s_id[k] = id;
+#pragma unroll
+            for (int j = 0; j < 9; j++) s_acc[k][j] = 0.0f;
+        }
+        __syncthreads();
+        for (int k = nb - 1; k >= 0; k--) {
+            const uint32_t pos = (uint32_t)(lo + k + 1);
+            float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
+            bool contrib = false;
+            if (pos <= last) {
+                const float4 g = s_g[k];
+                const float2 h = s_h[k];
+                const float dx = g.x - pxf;
+                const float axx = g.z * dx * dx, bx = g.w * dx;
+                const float dy = g.y - pyf;
+                const float p2 = fmaf(fmaf(h.x, dy, bx), dy, axx);
+                const float q = p2 + h.y;
+                if (p2 <= 0.0f && q >= kLog2AlphaMin) {
+                    const float raw = exp2f(q);
+                    const float alpha = fminf(kAlphaMax, raw);
+                    const float Ti = T / (1.0f - alpha);
+                    const float4 c = s_c[k];
+                    const float w = alpha * Ti;
+                    gr = w * G0;
+                    gg = w * G1;
+                    gbl = w * G2;
+                    const float dalpha = Ti * (G0 * (c.x - B0) + G1 * (c.y - B1) + G2 * (c.z - B2));
+                    B0 = alpha * c.x + (1.0f - alpha) * B0;
+                    B1 = alpha * c.y + (1.0f - alpha) * B1;
+                    B2 = alpha * c.z + (1.0f - alpha) * B2;
+                    T = Ti;
+                    if (raw <= kAlphaMax) {
+                        const float4 kk = s_k[k];
+                        const float dp = dalpha * alpha;
+                        go = dp / kk.w;
+                        gu = -dp * (kk.x * dx + kk.y * dy);
+                        gv = -dp * (kk.y * dx + kk.z * dy);
+                        ga = -0.5f * dp * dx * dx;
+                        gb = -dp * dx * dy;
+                        gc = -0.5f * dp * dy * dy;
+                    }
+                    contrib = true;
+                }
+            }
+            if (__any_sync(0xFFFFFFFFu, contrib)) {
+                gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga); gb = warp_sum(gb); gc = warp_sum(gc);
+                go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl);
+                if (lane == 0) {
+                    float *acc = s_acc[k];
+                    atomicAdd(acc + 0, gu); atomicAdd(acc + 1, gv); atomicAdd(acc + 2, ga);
+                    atomicAdd(acc + 3, gb); atomicAdd(acc + 4, gc); atomicAdd(acc + 5, go);
+                    atomicAdd(acc + 6, gr); atomicAdd(acc + 7, gg); atomicAdd(acc + 8, gbl);
+                }
+            }
+        }
+        __syncthreads();
+        // flush: one set of global atomics per (tile, Gaussian) that received anything
+        for (int k = threadIdx.x; k < nb; k += NT) {
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < 9; j++) any |= s_acc[k][j] != 0.0f;
+            if (any) {
+                float *dst = g2 + (size_t)s_id[k] * kG2;
+#pragma unroll
+                for (int j = 0; j < 9; j++)
+                    if (s_acc[k][j] != 0.0f) atomicAdd(dst + j, s_acc[k][j]);
+            }
+        }
+        __syncthreads();
+    }
+    (void)NW;
+}
+
+// ---------------------------------------------------------------------------
+// K8
+constexpr float kC1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+constexpr float kC2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+constexpr float kC2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+constexpr float kC2c = 0.54627421529603959f;  // sqrt(15/pi)/4
+constexpr float kC3e = 0.59004358992664352f;  // sqrt(35/(2 pi))/4
+constexpr float kC3f = 2.8906114426405538f;   // sqrt(105/pi)/2
+constexpr float kC3g = 0.45704579946446577f;  // sqrt(21/(2 pi))/4
+constexpr float kC3h = 0.3731763325901154f;   // sqrt(7/pi)/4
+constexpr float kC3k = 1.4453057213202769f;   // sqrt(105/pi)/4
+constexpr float kC0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+
+// SH basis and its partial derivatives in x, y, z (independent variables).
+template <int DEG>
+__device__ __forceinline__ void sh_basis_and_grad(float x, float y, float z, float *Y, float (*dY)[3]) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) dY[k][0] = dY[k][1] = dY[k][2] = 0.0f;
+    Y[0] = kC0;
+    if (DEG >= 1) {
+        Y[1] = -kC1 * y; dY[1][1] = -kC1;
+        Y[2] = kC1 * z;  dY[2][2] = kC1;
+        Y[3] = -kC1 * x; dY[3][0] = -kC1;
+    }
+    if (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kC2a * x * y;                 dY[4][0] = kC2a * y; dY[4][1] = kC2a * x;
+        Y[5] = -kC2a * y * z;                dY[5][1] = -kC2a * z; dY[5][2] = -kC2a * y;
+        Y[6] = kC2b * (2.0f * zz - xx - yy); dY[6][0] = -2.0f * kC2b * x; dY[6][1] = -2.0f * kC2b * y; dY[6][2] = 4.0f * kC2b * z;
+        Y[7] = -kC2a * x * z;                dY[7][0] = -kC2a * z; dY[7][2] = -kC2a * x;
+        Y[8] = kC2c * (xx - yy);             dY[8][0] = 2.0f * kC2c * x; dY[8][1] = -2.0f * kC2c * y;
+        if (DEG >= 3) {
+            Y[9] = -kC3e * y * (3.0f * xx - yy);
+            dY[9][0] = -6.0f * kC3e * x * y; dY[9][1] = -kC3e * (3.0f * xx - 3.0f * yy);
+            Y[10] = kC3f * x * y * z;
+            dY[10][0] = kC3f * y * z; dY[10][1] = kC3f * x * z; dY[10][2] = kC3f * x * y;
+            Y[11] = -kC3g * y * (4.0f * zz - xx - yy);
+            dY[11][0] = 2.0f * kC3g * x * y; dY[11][1] = -kC3g * (4.0f * zz - xx - 3.0f * yy); dY[11][2] = -8.0f * kC3g * y * z;
+            Y[12] = kC3h * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            dY[12][0] = -6.0f * kC3h * x * z; dY[12][1] = -6.0f * kC3h * y * z; dY[12][2] = kC3h * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = -kC3g * x * (4.0f * zz - xx - yy);
+            dY[13][0] = -kC3g * (4.0f * zz - 3.0f * xx - yy); dY[13][1] = 2.0f * kC3g * x * y; dY[13][2] = -8.0f * kC3g * x * z;
+            Y[14] = kC3k * z * (xx - yy);
+            dY[14][0] = 2.0f * kC3k * x * z; dY[14][1] = -2.0f * kC3k * y * z; dY[14][2] = kC3k * (xx - yy);
+            Y[15] = -kC3e * x * (xx - 3.0f * yy);
+            dY[15][0] = -kC3e * (3.0f * xx - 3.0f * yy); dY[15][1] = 6.0f * kC3e * x * y;
+        }
+    }
+}
+
+struct SceneArgs {
+    const float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
+};
+struct GradArgs {
+    float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(256)
+preprocess_backward_kernel(SceneArgs s, GradArgs o, CamArgs c, float t, int n, const float4 *__restrict__ rec,
+                           const uint32_t *__restrict__ tiles_touched, const float *__restrict__ g2) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float *gsh = o.sh + (size_t)i * 3 * K;
+    if (tiles_touched[i] == 0) {   // culled or off screen: no pixel depends on it
+        for (int j = 0; j < 3; j++) o.means[3 * i + j] = o.velocity[3 * i + j] = o.log_scales[3 * i + j] = 0.0f;
+        for (int j = 0; j < 4; j++) o.quats[4 * i + j] = 0.0f;
+        for (int j = 0; j < 3 * K; j++) gsh[j] = 0.0f;
+        o.t_mean[i] = o.log_t_scale[i] = o.opacity_logit[i] = 0.0f;
+        return;
+    }
+    const float *G = g2 + (size_t)i * kG2;
+    const float gU = G[0], gV = G[1], gA = G[2], gB = G[3], gCc = G[4], gO = G[5];
+    const float gcol[3] = {G[6], G[7], G[8]};
+    // ---- forward quantities (the decisions use the forward's rounded operations)
+    const float tau = __fsub_rn(t, s.t_mean[i]);
+    const float vel[3] = {s.velocity[3 * i], s.velocity[3 * i + 1], s.velocity[3 * i + 2]};
+    const float m[3] = {__fadd_rn(s.means[3 * i], __fmul_rn(tau, vel[0])),
+                        __fadd_rn(s.means[3 * i + 1], __fmul_rn(tau, vel[1])),
+                        __fadd_rn(s.means[3 * i + 2], __fmul_rn(tau, vel[2]))};
+    const float *R = c.R;
+    float Xc[3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+        Xc[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(R[3 * r], m[0]), __fmul_rn(R[3 * r + 1], m[1])),
+                                    __fmul_rn(R[3 * r + 2], m[2])), c.T[r]);
+    const float Z = Xc[2];
+    const float xz = __fdiv_rn(Xc[0], Z), yz = __fdiv_rn(Xc[1], Z);
+    const float limx = __fmul_rn(kJacClamp, __fdiv_rn(__fmul_rn(0.5f, (float)c.width), c.fx));
+    const float limy = __fmul_rn(kJacClamp, __fdiv_rn(__fmul_rn(0.5f, (float)c.height), c.fy));
+    const bool clx = xz < -limx || xz > limx, cly = yz < -limy || yz > limy;
+    const float xzc = fminf(limx, fmaxf(-limx, xz)), yzc = fminf(limy, fmaxf(-limy, yz));
+    const float iz = 1.0f / Z;
+    const float J00 = c.fx * iz, J02 = -c.fx * xzc * iz, J11 = c.fy * iz, J12 = -c.fy * yzc * iz;
+    const float4 q4 = reinterpret_cast<const float4 *>(s.quats)[i];
+    const float qraw[4] = {q4.x, q4.y, q4.z, q4.w};
+    const float qn = sqrtf(qraw[0] * qraw[0] + qraw[1] * qraw[1] + qraw[2] * qraw[2] + qraw[3] * qraw[3]);
+    const float qw = qraw[0] / qn, qx = qraw[1] / qn, qy = qraw[2] / qn, qz = qraw[3] / qn;
+    const float Rq[9] = {1.0f - 2.0f * (qy * qy + qz * qz), 2.0f * (qx * qy - qw * qz), 2.0f * (qx * qz + qw * qy),
+                         2.0f * (qx * qy + qw * qz), 1.0f - 2.0f * (qx * qx + qz * qz), 2.0f * (qy * qz - qw * qx),
+                         2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)};
+    const float sc[3] = {expf(s.log_scales[3 * i]), expf(s.log_scales[3 * i + 1]), expf(s.log_scales[3 * i + 2])};
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) M[3 * r + k] = Rq[3 * r + k] * sc[k];
+    float Tm[6];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        Tm[j] = J00 * R[j] + J02 * R[6 + j];
+        Tm[3 + j] = J11 * R[3 + j] + J12 * R[6 + j];
+    }
+    float TM[6];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) TM[3 * r + k] = Tm[3 * r] * M[k] + Tm[3 * r + 1] * M[3 + k] + Tm[3 * r + 2] * M[6 + k];
+    const float s00 = TM[0] * TM[0] + TM[1] * TM[1] + TM[2] * TM[2] + kDilation;
+    const float s01 = TM[0] * TM[3] + TM[1] * TM[4] + TM[2] * TM[5];
+    const float s11 = TM[3] * TM[3] + TM[4] * TM[4] + TM[5] * TM[5] + kDilation;
+    const float det = s00 * s11 - s01 * s01;
+    const float id2 = 1.0f / (det * det), idet = 1.0f / det;
+    // ---- conic -> Sigma'
+    const float d00 = gA * (-s11 * s11 * id2) + gB * (s01 * s11 * id2) + gCc * (idet - s00 * s11 * id2);
+    const float d11 = gA * (idet - s11 * s00 * id2) + gB * (s01 * s00 * id2) + gCc * (-s00 * s00 * id2);
+    const float d01 = gA * (2.0f * s11 * s01 * id2) + gB * (-idet - 2.0f * s01 * s01 * id2) + gCc * (2.0f * s00 * s01 * id2);
+    // ---- Sigma' = TM TM^T + 0.3 I -> TM -> Tm, M -> J
+    float dTM[6];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        dTM[k] = 2.0f * d00 * TM[k] + d01 * TM[3 + k];
+        dTM[3 + k] = 2.0f * d11 * TM[3 + k] + d01 * TM[k];
+    }
+    float dTm[6], dM[9];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) dTm[3 * r + k] = dTM[3 * r] * M[3 * k] + dTM[3 * r + 1] * M[3 * k + 1] + dTM[3 * r + 2] * M[3 * k + 2];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) dM[3 * k + cc] = Tm[k] * dTM[cc] + Tm[3 + k] * dTM[3 + cc];
+    const float dJ00 = dTm[0] * R[0] + dTm[1] * R[1] + dTm[2] * R[2];
+    const float dJ02 = dTm[0] * R[6] + dTm[1] * R[7] + dTm[2] * R[8];
+    const float dJ11 = dTm[3] * R[3] + dTm[4] * R[4] + dTm[5] * R[5];
+    const float dJ12 = dTm[3] * R[6] + dTm[4] * R[7] + dTm[5] * R[8];
+    // ---- J(X), (u, v)(X) -> X
+    float dX[3] = {0.0f, 0.0f, 0.0f};
+    const float iz2 = iz * iz;
+    dX[2] += -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2;
+    if (!clx) { dX[0] += -dJ02 * c.fx * iz2; dX[2] += dJ02 * 2.0f * c.fx * Xc[0] * iz2 * iz; }
+    else dX[2] += dJ02 * c.fx * xzc * iz2;
+    if (!cly) { dX[1] += -dJ12 * c.fy * iz2; dX[2] += dJ12 * 2.0f * c.fy * Xc[1] * iz2 * iz; }
+    else dX[2] += dJ12 * c.fy * yzc * iz2;
+    dX[0] += gU * c.fx * iz;
+    dX[2] += -gU * c.fx * Xc[0] * iz2;
+    dX[1] += gV * c.fy * iz;
+    dX[2] += -gV * c.fy * Xc[1] * iz2;
+    // ---- M = R(qn) diag(s) -> quaternion, log-scales
+    float dR[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) dR[3 * r + k] = dM[3 * r + k] * sc[k];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        o.log_scales[3 * i + k] = (dM[k] * Rq[k] + dM[3 + k] * Rq[3 + k] + dM[6 + k] * Rq[6 + k]) * sc[k];
+    float dq[4];
+    dq[0] = 2.0f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+    dq[1] = 2.0f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.0f * qx * dR[4] - qw * dR[5] + qz * dR[6] + qw * dR[7] - 2.0f * qx * dR[8]);
+    dq[2] = 2.0f * (-2.0f * qy * dR[0] + qx * dR[1] + qw * dR[2] + qx * dR[3] + qz * dR[5] - qw * dR[6] + qz * dR[7] - 2.0f * qy * dR[8]);
+    dq[3] = 2.0f * (-2.0f * qz * dR[0] - qw * dR[1] + qx * dR[2] + qw * dR[3] - 2.0f * qz * dR[4] + qy * dR[5] + qx * dR[6] + qy * dR[7]);
+    const float qdot = dq[0] * qw + dq[1] * qx + dq[2] * qy + dq[3] * qz;
+    const float qv[4] = {qw, qx, qy, qz};
+#pragma unroll
+    for (int j = 0; j < 4; j++) o.quats[4 * i + j] = (dq[j] - qv[j] * qdot) / qn;
+    // ---- colour: clamp, SH coefficients, view direction
+    float dir[3] = {m[0] - c.campos[0], m[1] - c.campos[1], m[2] - c.campos[2]};
+    const float inv_n = rsqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    const float d[3] = {dir[0] * inv_n, dir[1] * inv_n, dir[2] * inv_n};
+    float Yb[16], dY[16][3];
+    sh_basis_and_grad<DEG>(d[0], d[1], d[2], Yb, dY);
+    const float *shp = s.sh + (size_t)i * 3 * K;
+    float dd[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float raw = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; k++) raw = fmaf(shp[3 * k + ch], Yb[k], raw);
+        const float gch = raw < 0.0f ? 0.0f : gcol[ch];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            gsh[3 * k + ch] = gch * Yb[k];
+            dd[0] += gch * shp[3 * k + ch] * dY[k][0];
+            dd[1] += gch * shp[3 * k + ch] * dY[k][1];
+            dd[2] += gch * shp[3 * k + ch] * dY[k][2];
+        }
+    }
+    const float ddot = dd[0] * d[0] + dd[1] * d[1] + dd[2] * d[2];
+    float dm[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) dm[j] = (dd[j] - d[j] * ddot) * inv_n + R[j] * dX[0] + R[3 + j] * dX[1] + R[6 + j] * dX[2];
+    // ---- mu(t) = mu + tau V; o_hat(tau); tau = t - mu_t
+    float dtau = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        o.means[3 * i + j] = dm[j];
+        o.velocity[3 * i + j] = tau * dm[j];
+        dtau += vel[j] * dm[j];
+    }
+    const float oh = rec[3 * (size_t)i + 1].y;
+    const float st = expf(s.log_t_scale[i]);
+    const float sig = 1.0f / (1.0f + expf(-s.opacity_logit[i]));
+    o.opacity_logit[i] = gO * oh * (1.0f - sig);
+    dtau += gO * oh * (-tau / (st * st));
+    o.log_t_scale[i] = gO * oh * tau * tau / (st * st);
+    o.t_mean[i] = -dtau;
+}
+
+const uint32_t *pair_ids(const Layout &L, void *ws) {
+    return at<uint32_t>(ws, L.packed ? L.tile_keys[L.final_buf()] : L.tile_vals[L.final_buf()]);
+}
+uint32_t id_mask(const Layout &L) { return L.packed ? (uint32_t)((1ull << L.id_bits) - 1ull) : 0xFFFFFFFFu; }
+
+template <int TS, int BATCH>
+void launch_bb(const Layout &L, const d4dgs_config &cfg, void *ws, const float *dl, cudaStream_t st) {
+    blend_backward_kernel<TS, BATCH><<<L.ntiles, TS * TS, 0, st>>>(
+        at<uint2>(ws, L.ranges), pair_ids(L, ws), id_mask(L), at<float4>(ws, L.records), (uint32_t)L.n,
+        (uint32_t)L.cap, L.width, L.height, L.tiles_x, cfg.bg[0], cfg.bg[1], cfg.bg[2], at<float>(ws, L.final_T),
+        at<uint32_t>(ws, L.n_contrib), dl, at<float>(ws, L.grad2d));
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const d4dgs_scene &sc, const CamArgs &c, float t, const d4dgs_config &cfg,
+                            const Layout &L, void *ws, const float *dl_drgb, const d4dgs_scene_grad &g,
+                            cudaStream_t st, int num_sms) {
+    (void)num_sms;
+    if (L.n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(at<char>(ws, L.grad2d), 0, (size_t)L.n * kG2 * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    switch (L.tile) {   // the staging depth of the backward follows the tile size
+        case 8: launch_bb<8, 64>(L, cfg, ws, dl_drgb, st); break;
+        case 16: launch_bb<16, 128>(L, cfg, ws, dl_drgb, st); break;
+        default: launch_bb<32, 128>(L, cfg, ws, dl_drgb, st); break;
+    }
+    SceneArgs s{sc.means, sc.t_mean, sc.velocity, sc.log_scales, sc.log_t_scale, sc.quats, sc.opacity_logit, sc.sh};
+    GradArgs o{g.means, g.t_mean, g.velocity, g.log_scales, g.log_t_scale, g.quats, g.opacity_logit, g.sh};
+    const int blocks = (sc.n + 255) / 256;
+    const float4 *rec = at<float4>(ws, L.records);
+    const uint32_t *tt = at<uint32_t>(ws, L.tiles_touched);
+    const float *g2 = at<float>(ws, L.grad2d);
+    switch (sc.sh_degree) {
+        case 0: preprocess_backward_kernel<0><<<blocks, 256, 0, st>>>(s, o, c, t, sc.n, rec, tt, g2); break;
+        case 1: preprocess_backward_kernel<1><<<blocks, 256, 0, st>>>(s, o, c, t, sc.n, rec, tt, g2); break;
+        case 2: preprocess_backward_kernel<2><<<blocks, 256, 0, st>>>(s, o, c, t, sc.n, rec, tt, g2); break;
+        default: preprocess_backward_kernel<3><<<blocks, 256, 0, st>>>(s, o, c, t, sc.n, rec, tt, g2); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace d4dgs

@@ -58,7 +58,7 @@ struct Layout {
     int64_t control = 0, grid = 0, lb_depth = 0, lb_dup = 0, lb_tile = 0, zero_end = 0;
     // the rest
     int64_t ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
-    int64_t final_T = 0, n_contrib = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
+    int64_t final_T = 0, n_contrib = 0, grad2d = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
     int64_t total = 0;
     int32_t grid_w() const { return tiles_x + 1; }
     // index of the final sorted pair buffer

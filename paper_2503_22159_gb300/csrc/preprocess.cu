@@ -208,7 +208,7 @@ preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ r
             }
             r0 = make_float4(u, v, s11 * inv_det, -s01 * inv_det);
             r1 = make_float4(s00 * inv_det, oh, Z, rf);
-            r2 = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f), fmaxf(col[2], 0.0f), 0.0f);
+            r2 = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f), fmaxf(col[2], 0.0f), log2f(oh));
         } while (0);
         rec[3 * (size_t)i + 0] = r0;
         rec[3 * (size_t)i + 1] = r1;
