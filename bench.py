@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=2000)
     return p.parse_args()
 
 
@@ -238,6 +240,31 @@ def config_dict(w, args):
 # GPU leg
 # ---------------------------------------------------------------------------
 
+def run_serving(args, dev, d4):
+    """Serving on the same device: two resident scenes (300k and 1M SH-3 Gaussians),
+    Poisson requests at 500/s with mixed pose, timestamp and resolution; the
+    per-frame loop and continuous batching replay the same trace."""
+    import copy
+
+    import synth
+    from paper_2503_22159_gb300 import serving
+    cfg = d4.config_struct(16, 256)
+    scenes = {"A-300k": d4.DeviceScene.from_host(synth.make_scene(300_000, 0, "box20", sh_degree=3), dev),
+              "B-1M": d4.DeviceScene.from_host(synth.make_scene(1_000_000, 1, "box20", sh_degree=3), dev)}
+    reqs = serving.make_trace(scenes, n_requests=args.serve_requests, rate_hz=500.0, seed=4)
+    caps = serving.calibrate_capacity(scenes, reqs, cfg, dev)
+    out = {"trace": {"requests": len(reqs), "rate_hz": 500.0, "seed": 4,
+                     "resolutions": ["640x480", "1352x1014", "1920x1080", "2704x2028"],
+                     "scenes": {k: v.n for k, v in scenes.items()}}}
+    loop = serving.serve_loop(scenes, copy.deepcopy(reqs), cfg, caps, device=dev)
+    out["per_frame_loop"] = loop.as_dict()
+    batched = serving.serve_batched(scenes, copy.deepcopy(reqs), cfg, caps, device=dev, max_views=16,
+                                    budget_bytes=120 << 30, graph=True)
+    out["continuous_batching"] = batched.as_dict()
+    out["batched_vs_loop_fps"] = batched.frames_per_s / loop.frames_per_s
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -392,6 +419,10 @@ def run_ours(args):
         e2e = {"value": world * E / te, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": E, "api": "d4dgs_render_host"}
 
+    serving_out = None
+    if not args.no_serving and world == 1:
+        serving_out = run_serving(args, dev, d4)
+
     if rank != 0:
         return 0
     dominant = roof_blend if shares["blend"] >= shares["preprocess"] else roof_pre
@@ -405,7 +436,7 @@ def run_ours(args):
         "keys_per_frame": {"mean": float(np.mean(nkeys)), "max": int(np.max(nkeys))},
         "gpu_launches": int(launches * K), "launches_per_frame": launches,
         "wall_s_timed_region": t_wall, "peaks": peak_kind,
-        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out,
     }
     print(json.dumps(line), flush=True)
     if pg:

@@ -186,6 +186,45 @@ int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, flo
                           void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
                           d4dgs_stream_t stream);
 
+/* ---- batched multi-view rendering (serving) -------------------------------
+ * V <= 32 frames rendered by ONE launch of each kernel (preprocess, sort
+ * passes, blend), each frame with its own scene, camera, time, resolution,
+ * workspace and output -- the multi-frame parallel rendering the paper notes
+ * for fixed viewpoints (Sec. IV-C), generalised to mixed requests.  All views
+ * of a batch share the config (tile, batch, bg) and must agree on the layout
+ * class that d4dgs_workspace_layout reports (packed, tile_passes).
+ * Kernels are persistent with device-side work distribution, so the launch
+ * sequence of d4dgs_render_batch does not depend on the batch's contents and
+ * can be captured once as a CUDA graph; with args_dev the first kernel reads
+ * the descriptors from device memory, which the caller refreshes (e.g. by a
+ * captured host-to-device copy) before each replay. */
+typedef struct {
+    const d4dgs_scene *scene;    /* host struct of device arrays                     */
+    d4dgs_camera cam;
+    float t;
+    void *ws;                    /* this view's workspace (as for d4dgs_render)      */
+    size_t ws_bytes;
+    float *out_rgb;              /* H x W x 3 float32 device output                  */
+} d4dgs_view;
+
+/* Size of one encoded batch (host or device copy). */
+size_t d4dgs_batch_args_bytes(void);
+/* Device scratch of a batched launch (work counters + descriptor table). */
+size_t d4dgs_batch_area_bytes(void);
+/* Host only: validates the views and encodes them into args_host (at least
+ * d4dgs_batch_args_bytes()).  D4DGS_ERR_INVALID_ARG if they cannot share a
+ * launch. */
+int d4dgs_batch_encode(int32_t nviews, const d4dgs_view *views, const d4dgs_config *cfg, void *args_host,
+                       size_t args_bytes);
+/* Renders an encoded batch on `stream`.  args_host: the encoded batch (read
+ * on the host for the launch configuration); args_dev: NULL (descriptors
+ * travel as kernel parameters) or a device copy of the same bytes, 16-byte
+ * aligned, read by the first kernel.  batch_area: >= d4dgs_batch_area_bytes()
+ * of device memory, 256-byte aligned, caller-owned.  Per-view status via
+ * d4dgs_read_stats on each view's workspace. */
+int d4dgs_render_batch(const void *args_host, const void *args_dev, void *batch_area, size_t batch_area_bytes,
+                       d4dgs_stream_t stream);
+
 /* Synchronises `stream`, then copies the status word and counters of the
  * last frame rendered in `ws` into *out (host).  Returns out->status. */
 int d4dgs_read_stats(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, const void *ws,

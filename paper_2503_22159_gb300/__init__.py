@@ -24,7 +24,7 @@ from ._abi import (D4DGS_ERR_CAPACITY, D4DGS_ERR_CUDA, D4DGS_ERR_INVALID_ARG, D4
 
 SCENE_FIELDS = ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh")
 
-__all__ = ["DeviceScene", "Renderer", "camera_struct", "config_struct", "d4dgs_workspace_bytes",
+__all__ = ["DeviceScene", "Renderer", "BatchRenderer", "camera_struct", "config_struct", "d4dgs_workspace_bytes",
            "d4dgs_workspace_layout", "d4dgs_preprocess", "d4dgs_sort", "d4dgs_blend", "d4dgs_blend_profile",
            "d4dgs_render",
            "d4dgs_render_backward", "d4dgs_read_stats", "d4dgs_render_host", "d4dgs_launches_per_frame",
@@ -173,6 +173,95 @@ def d4dgs_render_host(host_scene, cam, t: float, cfg, dev_scene_buf: torch.Tenso
 
 def d4dgs_launches_per_frame(n: int, cam, cfg) -> int:
     return int(_abi.load().d4dgs_launches_per_frame(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg)))
+
+
+class BatchRenderer:
+    """Renders up to 32 views with one launch per kernel (d4dgs_render_batch).
+
+    Views share the config and the layout class (packed pairs, tile passes).
+    ``graph=True`` captures the launch sequence once per stream as a CUDA
+    graph whose first node copies the freshly encoded descriptors (pinned host
+    buffer -> device) before the kernels run, so one graph serves every batch
+    of its class."""
+
+    def __init__(self, cfg, device="cuda"):
+        lib = _abi.load()
+        self.cfg, self.device = cfg, torch.device(device)
+        self.args_bytes = int(lib.d4dgs_batch_args_bytes())
+        self.area_bytes = int(lib.d4dgs_batch_area_bytes())
+        self._graphs = {}
+        self._slots = {}
+
+    def _slot(self, stream):
+        key = int(stream.cuda_stream)
+        if key not in self._slots:
+            self._slots[key] = dict(
+                area=torch.empty(self.area_bytes, dtype=torch.uint8, device=self.device),
+                host=torch.empty(self.args_bytes, dtype=torch.uint8).pin_memory(),
+                dev=torch.empty(self.args_bytes, dtype=torch.uint8, device=self.device))
+        return self._slots[key]
+
+    def encode(self, views, host: torch.Tensor):
+        """views: list of (DeviceScene, camera, t, workspace tensor, output tensor)."""
+        n = len(views)
+        arr = (_abi.d4dgs_view * n)()
+        keep = []
+        for i, (scene, cam, t, ws, out) in enumerate(views):
+            st = scene.struct()
+            keep.append(st)
+            arr[i].scene = ctypes.addressof(st)
+            arr[i].cam = camera_struct(cam)
+            arr[i].t = float(t)
+            arr[i].ws = ws.data_ptr()
+            arr[i].ws_bytes = ws.numel()
+            arr[i].out_rgb = out.data_ptr()
+        _abi.check(_abi.load().d4dgs_batch_encode(n, arr, ctypes.byref(self.cfg), ctypes.c_void_p(host.data_ptr()),
+                                                  self.args_bytes), "d4dgs_batch_encode")
+
+    def render(self, views, stream=None, graph: bool = False):
+        stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        slot = self._slot(stream)
+        if not graph:
+            host = torch.empty(self.args_bytes, dtype=torch.uint8)
+            self.encode(views, host)
+            _abi.check(_abi.load().d4dgs_render_batch(ctypes.c_void_p(host.data_ptr()), None,
+                                                      ctypes.c_void_p(slot["area"].data_ptr()), self.area_bytes,
+                                                      _stream_handle(stream)), "d4dgs_render_batch")
+            return
+        # graph mode: the pinned host copy must not change while an earlier replay may still read it
+        if "event" in slot:
+            slot["event"].synchronize()
+        self.encode(views, slot["host"])
+        key = (int(stream.cuda_stream), self._class_key(slot["host"]))
+        g = self._graphs.get(key)
+        if g is None:
+            # one eager launch first: the library's one-time queries must not run under capture
+            _abi.check(_abi.load().d4dgs_render_batch(ctypes.c_void_p(slot["host"].data_ptr()), None,
+                                                      ctypes.c_void_p(slot["area"].data_ptr()), self.area_bytes,
+                                                      _stream_handle(stream)), "d4dgs_render_batch")
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream(self.device)
+            side.wait_stream(stream)
+            with torch.cuda.graph(g, stream=side):
+                slot["dev"].copy_(slot["host"], non_blocking=True)
+                _abi.check(_abi.load().d4dgs_render_batch(ctypes.c_void_p(slot["host"].data_ptr()),
+                                                          ctypes.c_void_p(slot["dev"].data_ptr()),
+                                                          ctypes.c_void_p(slot["area"].data_ptr()), self.area_bytes,
+                                                          _stream_handle(side)), "d4dgs_render_batch")
+            stream.wait_stream(side)
+            self._graphs[key] = g
+        with torch.cuda.stream(stream):
+            g.replay()
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        slot["event"] = ev
+
+    @staticmethod
+    def _class_key(host: torch.Tensor):
+        # nviews, tile, batch, packed, tile_passes (leading int32 fields of the encoded batch)
+        head = host[:20].view(torch.int32).tolist()
+        return (head[1], head[2], head[3], head[4])
 
 
 class Renderer:

@@ -42,6 +42,11 @@ class d4dgs_config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("bg", ctypes.c_float * 3)]
 
 
+class d4dgs_view(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("cam", d4dgs_camera), ("t", ctypes.c_float), ("ws", ctypes.c_void_p),
+                ("ws_bytes", ctypes.c_size_t), ("out_rgb", ctypes.c_void_p)]
+
+
 class d4dgs_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("n_keys", ctypes.c_int64), ("key_capacity", ctypes.c_int64),
                 ("n_visible", ctypes.c_int64)]
@@ -80,6 +85,10 @@ PROTOTYPES = {
                                          ctypes.c_size_t, _vp, ctypes.c_size_t, _vp, _vp, _vp]),
     "d4dgs_render_static": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),
                                            _vp, _P(d4dgs_stats), _vp]),
+    "d4dgs_batch_args_bytes": (ctypes.c_size_t, []),
+    "d4dgs_batch_area_bytes": (ctypes.c_size_t, []),
+    "d4dgs_batch_encode": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_view), _P(d4dgs_config), _vp, ctypes.c_size_t]),
+    "d4dgs_render_batch": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "d4dgs_launches_per_frame": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_camera), _P(d4dgs_config)]),
     "d4dgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI (include/d4dgs.h): workspace layout, argument checks,
 // stage sequencing on the caller's stream, status readback.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include "d4dgs_internal.cuh"
@@ -78,7 +79,8 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.pixels = (int64_t)cam->width * cam->height;
     l.depth_passes = 4;
     l.tile_bits = ceil_log2(l.ntiles);
-    l.tile_passes = (l.tile_bits + 7) / 8;
+    // at least two passes, so frames of different sizes (up to 65536 tiles) can share a batched launch
+    l.tile_passes = (l.tile_bits + 7) / 8 < 2 ? 2 : (l.tile_bits + 7) / 8;
     int sh = 0;
     for (int p = 0; p < l.tile_passes; p++) {
         const int left = l.tile_bits - sh, passes_left = l.tile_passes - p;
@@ -100,6 +102,7 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.lb_dup = off; off += align256(l.parts_dup * 8);
     l.lb_tile = off; off += align256((int64_t)(l.tile_passes > 0 ? l.tile_passes : 1) * l.parts_tile * kRadix * 4);
     l.zero_end = off;
+    l.batch = off; off += align256(kBatchAreaBytes);
     l.ranges = off; off += align256((int64_t)l.ntiles * 8);
     l.records = off; off += align256((int64_t)n * 48);
     for (int b = 0; b < 2; b++) { l.depth_keys[b] = off; off += align256((int64_t)n * 4); }
@@ -128,6 +131,80 @@ bool layout_for_bytes(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cf
         if (make_layout(n, cam, cfg, mid, &t) && (size_t)t.total <= ws_bytes) lo = mid; else hi = mid - 1;
     }
     return make_layout(n, cam, cfg, lo, L);
+}
+
+void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4dgs_config &cfg, const Layout &L,
+               void *ws, float *out_rgb, View *v) {
+    View x;
+    memset(&x, 0, sizeof(x));
+    x.means = s.means; x.t_mean = s.t_mean; x.velocity = s.velocity; x.log_scales = s.log_scales;
+    x.log_t_scale = s.log_t_scale; x.quats = s.quats; x.opacity_logit = s.opacity_logit; x.sh = s.sh;
+    x.n = s.n;
+    x.sh_degree = s.sh_degree;
+    x.t = t;
+    for (int i = 0; i < 3; i++) x.bg[i] = cfg.bg[i];
+    x.cam = make_cam_args(&cam, cfg.tile);
+    x.out_rgb = out_rgb;
+    x.zero_base = at<char>(ws, 0);
+    x.zero_bytes = L.zero_end;
+    x.ctl = at<uint32_t>(ws, L.control);
+    x.grid = at<int>(ws, L.grid);
+    x.rec = at<float4>(ws, L.records);
+    for (int b = 0; b < 2; b++) {
+        x.dkeys[b] = at<uint32_t>(ws, L.depth_keys[b]);
+        x.dvals[b] = at<uint32_t>(ws, L.depth_vals[b]);
+        x.tkeys[b] = at<uint32_t>(ws, L.tile_keys[b]);
+        x.tvals[b] = L.packed ? nullptr : at<uint32_t>(ws, L.tile_vals[b]);
+    }
+    x.tiles_touched = at<uint32_t>(ws, L.tiles_touched);
+    x.rect = at<ushort4>(ws, L.rect);
+    x.ranges = at<uint2>(ws, L.ranges);
+    x.final_T = at<float>(ws, L.final_T);
+    x.n_contrib = at<uint32_t>(ws, L.n_contrib);
+    x.grad2d = at<float>(ws, L.grad2d);
+    x.lb_depth = at<uint32_t>(ws, L.lb_depth);
+    x.lb_tile = at<uint32_t>(ws, L.lb_tile);
+    x.lb_dup = at<unsigned long long>(ws, L.lb_dup);
+    x.cap = (uint32_t)L.cap;
+    x.id_bits = L.id_bits;
+    x.packed = L.packed ? 1 : 0;
+    x.tile_passes = L.tile_passes;
+    x.ntiles = L.ntiles;
+    for (int p = 0; p < 3; p++) {
+        x.tile_shift[p] = L.tile_shift[p];
+        x.tile_mask[p] = L.tile_pass_bits[p] ? (1u << L.tile_pass_bits[p]) - 1u : 0u;
+    }
+    x.parts_depth = (int32_t)L.parts_depth;
+    x.parts_dup = (int32_t)L.parts_dup;
+    x.parts_tile = (int32_t)L.parts_tile;
+    *v = x;
+}
+
+bool finish_batch(BatchArgs *b) {
+    if (b->nviews < 1 || b->nviews > kMaxViews) return false;
+    int64_t chunks = 0, dparts = 0, uparts = 0, tiles = 0;
+    b->max_n = 0;
+    b->packed = b->v[0].packed;
+    b->tile_passes = b->v[0].tile_passes;
+    for (int i = 0; i < b->nviews; i++) {
+        View &v = b->v[i];
+        if (v.packed != b->packed || v.tile_passes != b->tile_passes || v.cam.tile != b->tile) return false;
+        v.chunk_base = (int32_t)chunks;
+        v.depth_part_base = (int32_t)dparts;
+        v.dup_part_base = (int32_t)uparts;
+        v.tile_base = (int32_t)tiles;
+        chunks += (v.n + kPreChunk - 1) / kPreChunk;
+        dparts += v.parts_depth;
+        uparts += v.parts_dup;
+        tiles += v.ntiles;
+        if (v.n > b->max_n) b->max_n = v.n;
+    }
+    if (chunks > INT32_MAX || tiles > INT32_MAX) return false;
+    b->total_chunks = (int32_t)chunks;
+    b->total_depth_parts = (int32_t)dparts;
+    b->total_dup_parts = (int32_t)uparts;
+    b->total_tiles = (int32_t)tiles;
+    return true;
 }
 
 }  // namespace d4dgs
@@ -175,54 +252,90 @@ static int prepare(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, 
     return D4DGS_OK;
 }
 
+// One frame as a batch of one view; the scene may be null for stages that
+// only read the table the preprocess installed (its n must then match).
+static int single(const d4dgs_scene *scene, int32_t n, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                  void *ws, size_t ws_bytes, float *out_rgb, BatchArgs *b, Layout *L) {
+    int rc = prepare(n, cam, cfg, ws, ws_bytes, L);
+    if (rc) return rc;
+    d4dgs_scene empty{};
+    empty.n = n;
+    memset(b, 0, offsetof(BatchArgs, v) + sizeof(View));
+    b->nviews = 1;
+    b->tile = cfg->tile;
+    b->batch = cfg->batch;
+    make_view(scene ? *scene : empty, *cam, t, *cfg, *L, ws, out_rgb, &b->v[0]);
+    return finish_batch(b) ? D4DGS_OK : D4DGS_ERR_INVALID_ARG;
+}
+
 int d4dgs_preprocess(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
                      void *ws, size_t ws_bytes, d4dgs_stream_t stream) {
     int rc = check_scene(scene);
     if (rc) return rc;
     if (!isfinite(t)) return D4DGS_ERR_INVALID_ARG;
+    static thread_local BatchArgs b;
     Layout L;
-    if ((rc = prepare(scene->n, cam, cfg, ws, ws_bytes, &L))) return rc;
+    if ((rc = single(scene, scene->n, cam, t, cfg, ws, ws_bytes, nullptr, &b, &L))) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(ws, 0, (size_t)L.zero_end, st);
-    if (e != cudaSuccess) return D4DGS_ERR_CUDA;
-    return cuda_status(launch_preprocess(*scene, make_cam_args(cam, cfg->tile), t, L, ws, st, num_sms_current()));
+    char *ba = at<char>(ws, L.batch);
+    const int sms = num_sms_current();
+    cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    return cuda_status(e);
 }
 
 int d4dgs_sort(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
                d4dgs_stream_t stream) {
+    static thread_local BatchArgs b;
     Layout L;
-    int rc = prepare(n, cam, cfg, ws, ws_bytes, &L);
+    int rc = single(nullptr, n, cam, 0.0f, cfg, ws, ws_bytes, nullptr, &b, &L);
     if (rc) return rc;
-    return cuda_status(launch_sort(L, ws, reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
+    return cuda_status(launch_sort(b, at<char>(ws, L.batch), reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
 }
 
 int d4dgs_blend(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
                 float *out_rgb, d4dgs_stream_t stream) {
-    Layout L;
-    int rc = prepare(n, cam, cfg, ws, ws_bytes, &L);
-    if (rc) return rc;
     if (!out_rgb || !aligned(out_rgb, 4)) return D4DGS_ERR_INVALID_ARG;
-    return cuda_status(launch_blend(L, *cfg, ws, out_rgb, reinterpret_cast<cudaStream_t>(stream)));
+    static thread_local BatchArgs b;
+    Layout L;
+    int rc = single(nullptr, n, cam, 0.0f, cfg, ws, ws_bytes, out_rgb, &b, &L);
+    if (rc) return rc;
+    return cuda_status(launch_blend(b, at<char>(ws, L.batch), reinterpret_cast<cudaStream_t>(stream),
+                                    num_sms_current(), out_rgb));
 }
 
 int d4dgs_blend_profile(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
                         float *out_rgb, uint64_t *counts, d4dgs_stream_t stream) {
-    Layout L;
-    int rc = prepare(n, cam, cfg, ws, ws_bytes, &L);
-    if (rc) return rc;
     if (!out_rgb || !counts || !aligned(counts, 8)) return D4DGS_ERR_INVALID_ARG;
+    static thread_local BatchArgs b;
+    Layout L;
+    int rc = single(nullptr, n, cam, 0.0f, cfg, ws, ws_bytes, out_rgb, &b, &L);
+    if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ba = at<char>(ws, L.batch);
+    // the blend's work counter is reset so that the same frame can be blended again
+    if (cudaMemsetAsync(ba + 4 * kBaBlend, 0, 4, st) != cudaSuccess) return D4DGS_ERR_CUDA;
     if (cudaMemsetAsync(counts, 0, 2 * sizeof(uint64_t), st) != cudaSuccess) return D4DGS_ERR_CUDA;
-    return cuda_status(launch_blend(L, *cfg, ws, out_rgb, st, reinterpret_cast<unsigned long long *>(counts)));
+    return cuda_status(launch_blend(b, ba, st, num_sms_current(), out_rgb, reinterpret_cast<unsigned long long *>(counts)));
 }
 
 int d4dgs_render(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg, void *ws,
                  size_t ws_bytes, float *out_rgb, d4dgs_stream_t stream) {
     if (!out_rgb || !aligned(out_rgb, 4)) return D4DGS_ERR_INVALID_ARG;
-    int rc = d4dgs_preprocess(scene, cam, t, cfg, ws, ws_bytes, stream);
+    int rc = check_scene(scene);
     if (rc) return rc;
-    if ((rc = d4dgs_sort(scene->n, cam, cfg, ws, ws_bytes, stream))) return rc;
-    return d4dgs_blend(scene->n, cam, cfg, ws, ws_bytes, out_rgb, stream);
+    if (!isfinite(t)) return D4DGS_ERR_INVALID_ARG;
+    static thread_local BatchArgs b;
+    Layout L;
+    if ((rc = single(scene, scene->n, cam, t, cfg, ws, ws_bytes, out_rgb, &b, &L))) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ba = at<char>(ws, L.batch);
+    const int sms = num_sms_current();
+    cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
+    return cuda_status(e);
 }
 
 int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
@@ -237,10 +350,53 @@ int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, flo
         for (float *p : gp)
             if (!p || !aligned(p, 4)) return D4DGS_ERR_INVALID_ARG;
     }
+    static thread_local BatchArgs b;
     Layout L;
-    if ((rc = prepare(scene->n, cam, cfg, ws, ws_bytes, &L))) return rc;
-    return cuda_status(launch_backward(*scene, make_cam_args(cam, cfg->tile), t, *cfg, L, ws, dl_drgb, *grad,
-                                       reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
+    if ((rc = single(scene, scene->n, cam, t, cfg, ws, ws_bytes, nullptr, &b, &L))) return rc;
+    return cuda_status(launch_backward(b, at<char>(ws, L.batch), dl_drgb, *grad, reinterpret_cast<cudaStream_t>(stream),
+                                       num_sms_current()));
+}
+
+size_t d4dgs_batch_args_bytes(void) { return sizeof(BatchArgs); }
+size_t d4dgs_batch_area_bytes(void) { return (size_t)kBatchAreaBytes; }
+
+int d4dgs_batch_encode(int32_t nviews, const d4dgs_view *views, const d4dgs_config *cfg, void *args_host,
+                       size_t args_bytes) {
+    if (nviews < 1 || nviews > kMaxViews || !views || !valid_config(cfg) || !args_host ||
+        args_bytes < sizeof(BatchArgs))
+        return D4DGS_ERR_INVALID_ARG;
+    BatchArgs *b = static_cast<BatchArgs *>(args_host);
+    memset(b, 0, sizeof(BatchArgs));
+    b->nviews = nviews;
+    b->tile = cfg->tile;
+    b->batch = cfg->batch;
+    for (int i = 0; i < nviews; i++) {
+        const d4dgs_view &q = views[i];
+        int rc = check_scene(q.scene);
+        if (rc) return rc;
+        if (!isfinite(q.t) || !q.out_rgb || !aligned(q.out_rgb, 4)) return D4DGS_ERR_INVALID_ARG;
+        Layout L;
+        if ((rc = prepare(q.scene->n, &q.cam, cfg, q.ws, q.ws_bytes, &L))) return rc;
+        make_view(*q.scene, q.cam, q.t, *cfg, L, q.ws, q.out_rgb, &b->v[i]);
+    }
+    return finish_batch(b) ? D4DGS_OK : D4DGS_ERR_INVALID_ARG;
+}
+
+int d4dgs_render_batch(const void *args_host, const void *args_dev, void *batch_area, size_t batch_area_bytes,
+                       d4dgs_stream_t stream) {
+    if (!args_host || !batch_area || !aligned(batch_area, 256) || batch_area_bytes < (size_t)kBatchAreaBytes)
+        return D4DGS_ERR_INVALID_ARG;
+    if (args_dev && !aligned(args_dev, 16)) return D4DGS_ERR_INVALID_ARG;
+    const BatchArgs &b = *static_cast<const BatchArgs *>(args_host);
+    if (b.nviews < 1 || b.nviews > kMaxViews) return D4DGS_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ba = static_cast<char *>(batch_area);
+    const int sms = num_sms_current();
+    cudaError_t e = launch_clear(b, args_dev, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
+    return cuda_status(e);
 }
 
 int d4dgs_read_stats(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, const void *ws, size_t ws_bytes,
@@ -309,7 +465,8 @@ int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, fl
 int d4dgs_launches_per_frame(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg) {
     Layout L;
     if (!make_layout(n, cam, cfg, 0, &L)) return D4DGS_ERR_INVALID_ARG;
-    return (n > 0 ? 1 : 0) + sort_launch_count(L) + 1;
+    // clear + preprocess + sort stages + blend
+    return 1 + (n > 0 ? 1 : 0) + sort_launch_count(n, L.tile_passes) + 1;
 }
 
 const char *d4dgs_strerror(int code) {

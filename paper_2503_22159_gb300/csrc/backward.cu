@@ -35,11 +35,18 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 template <int TS, int BATCH>
 __global__ void __launch_bounds__(TS *TS)
-blend_backward_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids, uint32_t id_mask,
-                      const float4 *__restrict__ rec, uint32_t n, uint32_t cap, int width, int height, int tiles_x,
-                      float bg0, float bg1, float bg2, const float *__restrict__ final_T,
-                      const uint32_t *__restrict__ n_contrib, const float *__restrict__ dl_drgb,
-                      float *__restrict__ g2) {
+blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_drgb) {
+    const View &v = view_of(ba, 0);
+    const uint2 *ranges = v.ranges;
+    const uint32_t id_mask = v.packed ? (uint32_t)((1ull << v.id_bits) - 1ull) : 0xFFFFFFFFu;
+    const uint32_t *ids = v.packed ? v.tkeys[v.tile_passes & 1] : v.tvals[v.tile_passes & 1];
+    const float4 *rec = v.rec;
+    const uint32_t n = (uint32_t)v.n, cap = v.cap;
+    const int width = v.cam.width, height = v.cam.height, tiles_x = v.cam.tiles_x;
+    const float bg0 = v.bg[0], bg1 = v.bg[1], bg2 = v.bg[2];
+    const float *final_T = v.final_T;
+    const uint32_t *n_contrib = v.n_contrib;
+    float *g2 = v.grad2d;
     constexpr int NT = TS * TS;
     constexpr int NW = NT / 32;
     __shared__ float4 s_g[BATCH];     // u, v, A, B      (forward exponent form)
@@ -222,8 +229,16 @@ struct GradArgs {
 
 template <int DEG>
 __global__ void __launch_bounds__(256)
-preprocess_backward_kernel(SceneArgs s, GradArgs o, CamArgs c, float t, int n, const float4 *__restrict__ rec,
-                           const uint32_t *__restrict__ tiles_touched, const float *__restrict__ g2) {
+preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
+    const View &vw = view_of(ba, 0);
+    const SceneArgs s{vw.means, vw.t_mean, vw.velocity, vw.log_scales, vw.log_t_scale, vw.quats, vw.opacity_logit,
+                      vw.sh};
+    const CamArgs &c = vw.cam;
+    const float t = vw.t;
+    const int n = vw.n;
+    const float4 *__restrict__ rec = vw.rec;
+    const uint32_t *__restrict__ tiles_touched = vw.tiles_touched;
+    const float *__restrict__ g2 = vw.grad2d;
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -384,44 +399,32 @@ preprocess_backward_kernel(SceneArgs s, GradArgs o, CamArgs c, float t, int n, c
     o.t_mean[i] = -dtau;
 }
 
-const uint32_t *pair_ids(const Layout &L, void *ws) {
-    return at<uint32_t>(ws, L.packed ? L.tile_keys[L.final_buf()] : L.tile_vals[L.final_buf()]);
-}
-uint32_t id_mask(const Layout &L) { return L.packed ? (uint32_t)((1ull << L.id_bits) - 1ull) : 0xFFFFFFFFu; }
-
 template <int TS, int BATCH>
-void launch_bb(const Layout &L, const d4dgs_config &cfg, void *ws, const float *dl, cudaStream_t st) {
-    blend_backward_kernel<TS, BATCH><<<L.ntiles, TS * TS, 0, st>>>(
-        at<uint2>(ws, L.ranges), pair_ids(L, ws), id_mask(L), at<float4>(ws, L.records), (uint32_t)L.n,
-        (uint32_t)L.cap, L.width, L.height, L.tiles_x, cfg.bg[0], cfg.bg[1], cfg.bg[2], at<float>(ws, L.final_T),
-        at<uint32_t>(ws, L.n_contrib), dl, at<float>(ws, L.grad2d));
+void launch_bb(const char *ba, int ntiles, const float *dl, cudaStream_t st) {
+    blend_backward_kernel<TS, BATCH><<<ntiles, TS * TS, 0, st>>>(ba, dl);
 }
 
 }  // namespace
 
-cudaError_t launch_backward(const d4dgs_scene &sc, const CamArgs &c, float t, const d4dgs_config &cfg,
-                            const Layout &L, void *ws, const float *dl_drgb, const d4dgs_scene_grad &g,
-                            cudaStream_t st, int num_sms) {
+cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb,
+                            const d4dgs_scene_grad &g, cudaStream_t st, int num_sms) {
     (void)num_sms;
-    if (L.n == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(at<char>(ws, L.grad2d), 0, (size_t)L.n * kG2 * sizeof(float), st);
+    const View &v = args.v[0];
+    if (v.n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(v.grad2d, 0, (size_t)v.n * kG2 * sizeof(float), st);
     if (e != cudaSuccess) return e;
-    switch (L.tile) {   // the staging depth of the backward follows the tile size
-        case 8: launch_bb<8, 64>(L, cfg, ws, dl_drgb, st); break;
-        case 16: launch_bb<16, 128>(L, cfg, ws, dl_drgb, st); break;
-        default: launch_bb<32, 128>(L, cfg, ws, dl_drgb, st); break;
+    switch (args.tile) {   // the staging depth of the backward follows the tile size
+        case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, st); break;
+        case 16: launch_bb<16, 128>(batch_area, v.ntiles, dl_drgb, st); break;
+        default: launch_bb<32, 128>(batch_area, v.ntiles, dl_drgb, st); break;
     }
-    SceneArgs s{sc.means, sc.t_mean, sc.velocity, sc.log_scales, sc.log_t_scale, sc.quats, sc.opacity_logit, sc.sh};
     GradArgs o{g.means, g.t_mean, g.velocity, g.log_scales, g.log_t_scale, g.quats, g.opacity_logit, g.sh};
-    const int blocks = (sc.n + 255) / 256;
-    const float4 *rec = at<float4>(ws, L.records);
-    const uint32_t *tt = at<uint32_t>(ws, L.tiles_touched);
-    const float *g2 = at<float>(ws, L.grad2d);
-    switch (sc.sh_degree) {
-        case 0: preprocess_backward_kernel<0><<<blocks, 256, 0, st>>>(s, o, c, t, sc.n, rec, tt, g2); break;
-        case 1: preprocess_backward_kernel<1><<<blocks, 256, 0, st>>>(s, o, c, t, sc.n, rec, tt, g2); break;
-        case 2: preprocess_backward_kernel<2><<<blocks, 256, 0, st>>>(s, o, c, t, sc.n, rec, tt, g2); break;
-        default: preprocess_backward_kernel<3><<<blocks, 256, 0, st>>>(s, o, c, t, sc.n, rec, tt, g2); break;
+    const int blocks = (v.n + 255) / 256;
+    switch (v.sh_degree) {
+        case 0: preprocess_backward_kernel<0><<<blocks, 256, 0, st>>>(batch_area, o); break;
+        case 1: preprocess_backward_kernel<1><<<blocks, 256, 0, st>>>(batch_area, o); break;
+        case 2: preprocess_backward_kernel<2><<<blocks, 256, 0, st>>>(batch_area, o); break;
+        default: preprocess_backward_kernel<3><<<blocks, 256, 0, st>>>(batch_area, o); break;
     }
     return cudaGetLastError();
 }

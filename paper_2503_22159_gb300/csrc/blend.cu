@@ -57,87 +57,108 @@ __device__ __forceinline__ bool blend_step(PixelState &px, float p, float L, con
 
 // COUNT: instrumented variant for profiling, which also totals the (pixel,
 // Gaussian) pairs evaluated and blended into counts[0..1] (not used on the
-// render path).
+// render path).  Persistent: CTAs take tiles of the views' flattened tiles.
 template <int TS, int BATCH, bool COUNT>
-__global__ void __launch_bounds__(TS *TS / 2)
-blend_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids, uint32_t id_mask,
-             const float4 *__restrict__ rec, uint32_t n, uint32_t cap, int width, int height, int tiles_x,
-             float bg0, float bg1, float bg2, float *__restrict__ out_rgb, float *__restrict__ out_T,
-             uint32_t *__restrict__ out_nc, unsigned long long *counts) {
+__global__ void __launch_bounds__(TS *TS / 2, TS == 8 ? 16 : (TS == 16 ? 12 : 3))
+blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts) {
     constexpr int NT = TS * TS / 2;
     __shared__ float4 s_g[BATCH];    // u, v, A, B
     __shared__ float2 s_h[BATCH];    // C, L
     __shared__ float4 s_c[BATCH];    // r, g, b
-
-    const int tile = blockIdx.x;
-    const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int lx = (int)(threadIdx.x % TS), ly = 2 * (int)(threadIdx.x / TS);
-    const int px = tx * TS + lx, py0 = ty * TS + ly, py1 = py0 + 1;
-    const bool in0 = px < width && py0 < height, in1 = px < width && py1 < height;
-    const float pxf = (float)px + 0.5f, pyf0 = (float)py0 + 0.5f, pyf1 = (float)py1 + 0.5f;
-    uint2 rg = ranges[tile];
-    rg.y = min(rg.y, cap);   // ranges are written clamped; this keeps every read in bounds regardless
-    rg.x = min(rg.x, rg.y);
-
-    PixelState a{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in0};
-    PixelState b{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in1};
+    __shared__ int32_t s_item;
+    uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
+    const int nviews = (int)bw[kBaNViews];
+    const int total = (int)bw[kBaTotalTiles];
     uint32_t n_eval = 0, n_blend = 0;
 
-    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-        if (__syncthreads_count(!(a.done && b.done)) == 0) break;
-        for (int k = threadIdx.x; k < BATCH; k += NT) {
-            const uint32_t j = start + (uint32_t)k;
-            if (j < rg.y) {
-                uint32_t id = ids[j] & id_mask;
-                if (id >= n) id = 0;   // only after a timed-out sort pass; keeps the gather in bounds
-                const float4 r0 = rec[3 * (size_t)id + 0];
-                const float4 r1 = rec[3 * (size_t)id + 1];
-                const float4 r2 = rec[3 * (size_t)id + 2];
-                s_g[k] = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
-                s_h[k] = make_float2(-0.5f * kLog2e * r1.x, r2.w);
-                s_c[k] = r2;
-            }
-        }
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int32_t)atomicAdd(bw + kBaBlend, 1u);
         __syncthreads();
-        const int nb = (int)min((uint32_t)BATCH, rg.y - start);
-        if (!(a.done && b.done)) {
-            for (int k = 0; k < nb; k++) {
-                const float4 g = s_g[k];
-                const float2 h = s_h[k];
-                const float dx = g.x - pxf;
-                const float axx = g.z * dx * dx, bx = g.w * dx;
-                const uint32_t pos = start - rg.x + (uint32_t)k + 1u;
-                if (!a.done) {
-                    const float dy = g.y - pyf0;
-                    const float p = fmaf(fmaf(h.x, dy, bx), dy, axx);
-                    const bool bl = blend_step(a, p, h.y, &s_c[k], pos);
-                    if (COUNT) { n_eval++; n_blend += bl; }
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        int vi = 0;
+        for (int u = 1; u < nviews; u++)
+            if (view_of(ba, u).tile_base <= item) vi = u;
+        const View &v = view_of(ba, vi);
+        const int tile = item - v.tile_base;
+        const int tiles_x = v.cam.tiles_x, width = v.cam.width, height = v.cam.height;
+        const uint32_t n = (uint32_t)v.n, cap = v.cap;
+        const bool packed = v.packed != 0;
+        const uint32_t id_mask = packed ? (uint32_t)((1ull << v.id_bits) - 1ull) : 0xFFFFFFFFu;
+        const uint32_t *ids = packed ? v.tkeys[v.tile_passes & 1] : v.tvals[v.tile_passes & 1];
+        const float4 *rec = v.rec;
+        float *out_rgb = (out0 && vi == 0) ? out0 : v.out_rgb;
+
+        const int tx = tile % tiles_x, ty = tile / tiles_x;
+        const int lx = (int)(threadIdx.x % TS), ly = 2 * (int)(threadIdx.x / TS);
+        const int px = tx * TS + lx, py0 = ty * TS + ly, py1 = py0 + 1;
+        const bool in0 = px < width && py0 < height, in1 = px < width && py1 < height;
+        const float pxf = (float)px + 0.5f, pyf0 = (float)py0 + 0.5f, pyf1 = (float)py1 + 0.5f;
+        uint2 rg = v.ranges[tile];
+        rg.y = min(rg.y, cap);   // ranges are written clamped; this keeps every read in bounds regardless
+        rg.x = min(rg.x, rg.y);
+
+        PixelState a{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in0};
+        PixelState b{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in1};
+
+        for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+            if (__syncthreads_count(!(a.done && b.done)) == 0) break;
+            for (int k = threadIdx.x; k < BATCH; k += NT) {
+                const uint32_t j = start + (uint32_t)k;
+                if (j < rg.y) {
+                    uint32_t id = ids[j] & id_mask;
+                    if (id >= n) id = 0;   // only after a timed-out sort pass; keeps the gather in bounds
+                    const float4 r0 = rec[3 * (size_t)id + 0];
+                    const float4 r1 = rec[3 * (size_t)id + 1];
+                    const float4 r2 = rec[3 * (size_t)id + 2];
+                    s_g[k] = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
+                    s_h[k] = make_float2(-0.5f * kLog2e * r1.x, r2.w);
+                    s_c[k] = r2;
                 }
-                if (!b.done) {
-                    const float dy = g.y - pyf1;
-                    const float p = fmaf(fmaf(h.x, dy, bx), dy, axx);
-                    const bool bl = blend_step(b, p, h.y, &s_c[k], pos);
-                    if (COUNT) { n_eval++; n_blend += bl; }
+            }
+            __syncthreads();
+            const int nb = (int)min((uint32_t)BATCH, rg.y - start);
+            if (!(a.done && b.done)) {
+                for (int k = 0; k < nb; k++) {
+                    const float4 g = s_g[k];
+                    const float2 h = s_h[k];
+                    const float dx = g.x - pxf;
+                    const float axx = g.z * dx * dx, bx = g.w * dx;
+                    const uint32_t pos = start - rg.x + (uint32_t)k + 1u;
+                    if (!a.done) {
+                        const float dy = g.y - pyf0;
+                        const float p = fmaf(fmaf(h.x, dy, bx), dy, axx);
+                        const bool bl = blend_step(a, p, h.y, &s_c[k], pos);
+                        if (COUNT) { n_eval++; n_blend += bl; }
+                    }
+                    if (!b.done) {
+                        const float dy = g.y - pyf1;
+                        const float p = fmaf(fmaf(h.x, dy, bx), dy, axx);
+                        const bool bl = blend_step(b, p, h.y, &s_c[k], pos);
+                        if (COUNT) { n_eval++; n_blend += bl; }
+                    }
+                    if (a.done && b.done) break;
                 }
-                if (a.done && b.done) break;
             }
         }
-    }
-    if (in0) {
-        const size_t p = (size_t)py0 * width + px;
-        out_rgb[3 * p + 0] = a.c0 + a.T * bg0;
-        out_rgb[3 * p + 1] = a.c1 + a.T * bg1;
-        out_rgb[3 * p + 2] = a.c2 + a.T * bg2;
-        out_T[p] = a.T;
-        out_nc[p] = a.last;
-    }
-    if (in1) {
-        const size_t p = (size_t)py1 * width + px;
-        out_rgb[3 * p + 0] = b.c0 + b.T * bg0;
-        out_rgb[3 * p + 1] = b.c1 + b.T * bg1;
-        out_rgb[3 * p + 2] = b.c2 + b.T * bg2;
-        out_T[p] = b.T;
-        out_nc[p] = b.last;
+        const float bg0 = v.bg[0], bg1 = v.bg[1], bg2 = v.bg[2];
+        if (in0) {
+            const size_t p = (size_t)py0 * width + px;
+            out_rgb[3 * p + 0] = a.c0 + a.T * bg0;
+            out_rgb[3 * p + 1] = a.c1 + a.T * bg1;
+            out_rgb[3 * p + 2] = a.c2 + a.T * bg2;
+            v.final_T[p] = a.T;
+            v.n_contrib[p] = a.last;
+        }
+        if (in1) {
+            const size_t p = (size_t)py1 * width + px;
+            out_rgb[3 * p + 0] = b.c0 + b.T * bg0;
+            out_rgb[3 * p + 1] = b.c1 + b.T * bg1;
+            out_rgb[3 * p + 2] = b.c2 + b.T * bg2;
+            v.final_T[p] = b.T;
+            v.n_contrib[p] = b.last;
+        }
     }
     if (COUNT) {
         const unsigned long long e = __reduce_add_sync(0xFFFFFFFFu, n_eval);
@@ -149,38 +170,31 @@ blend_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
     }
 }
 
-// The Gaussian id of sorted pair j is ids[j] & id_mask.
-const uint32_t *pair_ids(const Layout &L, void *ws) {
-    return at<uint32_t>(ws, L.packed ? L.tile_keys[L.final_buf()] : L.tile_vals[L.final_buf()]);
-}
-uint32_t id_mask(const Layout &L) { return L.packed ? (uint32_t)((1ull << L.id_bits) - 1ull) : 0xFFFFFFFFu; }
-
 template <int TS, int BATCH>
-cudaError_t launch_ts(const Layout &L, const d4dgs_config &cfg, void *ws, float *out_rgb, cudaStream_t st,
-                      unsigned long long *counts) {
-    auto args = [&](auto kernel) {
-        kernel<<<L.ntiles, TS * TS / 2, 0, st>>>(at<uint2>(ws, L.ranges), pair_ids(L, ws), id_mask(L),
-                                                 at<float4>(ws, L.records), (uint32_t)L.n, (uint32_t)L.cap,
-                                                 L.width, L.height, L.tiles_x, cfg.bg[0], cfg.bg[1], cfg.bg[2],
-                                                 out_rgb, at<float>(ws, L.final_T), at<uint32_t>(ws, L.n_contrib),
-                                                 counts);
+cudaError_t launch_ts(char *ba, cudaStream_t st, int num_sms, float *out0, unsigned long long *counts) {
+    auto go = [&](auto kernel) {
+        static int occ = 0;   // per instantiation; queried once, before any graph capture uses it
+        if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TS * TS / 2, 0) != cudaSuccess ||
+                     occ < 1))
+            occ = 1;
+        kernel<<<occ * num_sms, TS * TS / 2, 0, st>>>(ba, out0, counts);
     };
-    if (counts) args(blend_kernel<TS, BATCH, true>);
-    else args(blend_kernel<TS, BATCH, false>);
+    if (counts) go(blend_kernel<TS, BATCH, true>);
+    else go(blend_kernel<TS, BATCH, false>);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_blend(const Layout &L, const d4dgs_config &cfg, void *ws, float *out_rgb, cudaStream_t st,
+cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, float *out0,
                          unsigned long long *counts) {
-    if (L.ntiles == 0) return cudaSuccess;
-#define D4DGS_BATCHES(TS)                                                           \
-    if (cfg.batch == 64) return launch_ts<TS, 64>(L, cfg, ws, out_rgb, st, counts);   \
-    if (cfg.batch == 128) return launch_ts<TS, 128>(L, cfg, ws, out_rgb, st, counts); \
-    if (cfg.batch == 256) return launch_ts<TS, 256>(L, cfg, ws, out_rgb, st, counts); \
+    if (args.total_tiles == 0) return cudaSuccess;
+#define D4DGS_BATCHES(TS)                                                                        \
+    if (args.batch == 64) return launch_ts<TS, 64>(batch_area, st, num_sms, out0, counts);         \
+    if (args.batch == 128) return launch_ts<TS, 128>(batch_area, st, num_sms, out0, counts);       \
+    if (args.batch == 256) return launch_ts<TS, 256>(batch_area, st, num_sms, out0, counts);       \
     return cudaErrorInvalidValue;
-    switch (L.tile) {
+    switch (args.tile) {
         case 8: D4DGS_BATCHES(8)
         case 16: D4DGS_BATCHES(16)
         case 32: D4DGS_BATCHES(32)

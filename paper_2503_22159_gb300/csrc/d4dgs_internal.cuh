@@ -58,7 +58,7 @@ struct Layout {
     int64_t control = 0, grid = 0, lb_depth = 0, lb_dup = 0, lb_tile = 0, zero_end = 0;
     // the rest
     int64_t ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
-    int64_t final_T = 0, n_contrib = 0, grad2d = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
+    int64_t final_T = 0, n_contrib = 0, grad2d = 0, batch = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
     int64_t total = 0;
     int32_t grid_w() const { return tiles_x + 1; }
     // index of the final sorted pair buffer
@@ -75,7 +75,7 @@ __host__ __device__ inline T *at(void *ws, int64_t off) {
     return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
 }
 
-// Camera constants passed by value to the kernels.
+// Camera constants of one view.
 struct CamArgs {
     float R[9], T[3];
     float fx, fy, cx, cy;
@@ -84,16 +84,87 @@ struct CamArgs {
 };
 CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile);
 
-// ---- launchers (each returns the cudaError_t of its launch)
-cudaError_t launch_preprocess(const d4dgs_scene &s, const CamArgs &c, float t, const Layout &L, void *ws,
-                              cudaStream_t st, int num_sms);
-cudaError_t launch_sort(const Layout &L, void *ws, cudaStream_t st, int num_sms);
-cudaError_t launch_blend(const Layout &L, const d4dgs_config &cfg, void *ws, float *out_rgb, cudaStream_t st,
+// Everything the kernels need about one frame (scene, camera, time, settings
+// and the absolute addresses of its workspace buffers).  A launch processes a
+// table of up to kMaxViews of them; a single frame is a table of one.
+constexpr int kMaxViews = 32;
+struct View {
+    const float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
+    int32_t n, sh_degree;
+    float t;
+    float bg[3];
+    CamArgs cam;
+    float *out_rgb;
+    char *zero_base;                 // [zero_base, zero_base + zero_bytes) is cleared per frame
+    int64_t zero_bytes;
+    uint32_t *ctl;
+    int *grid;
+    float4 *rec;
+    uint32_t *dkeys[2], *dvals[2], *tiles_touched;
+    ushort4 *rect;
+    uint2 *ranges;
+    float *final_T;
+    uint32_t *n_contrib;
+    float *grad2d;
+    uint32_t *tkeys[2], *tvals[2];
+    uint32_t *lb_depth, *lb_tile;
+    unsigned long long *lb_dup;
+    uint32_t cap;
+    int32_t id_bits, packed, tile_passes, ntiles;
+    int32_t tile_shift[3];
+    uint32_t tile_mask[3];
+    int32_t parts_depth, parts_dup, parts_tile;
+    // first flattened work item of this view within its table
+    int32_t chunk_base, depth_part_base, dup_part_base, tile_base;
+};
+
+// Descriptor table as kernel parameters (it travels by value: 32 views fit in
+// the parameter space) plus the totals of the flattened work spaces.
+struct BatchArgs {
+    int32_t nviews;
+    int32_t tile, batch, packed, tile_passes;   // shared by every view of a launch
+    int32_t total_chunks, total_depth_parts, total_dup_parts, total_tiles;
+    int32_t max_n;
+    View v[kMaxViews];
+};
+
+// Batch area (device): work counters of every launch, launch totals, and the
+// descriptor table written by the first kernel of a frame.
+enum : int {
+    kBaChunk = 0,          // preprocess chunk counter
+    kBaDepth = 1,          // 1..4 depth passes
+    kBaDup = 5,            // scan + emit
+    kBaTile = 6,           // 6..8 tile passes
+    kBaBlend = 9,
+    kBaBack = 10,
+    kBaNViews = 16, kBaTotalChunks, kBaTotalDepthParts, kBaTotalDupParts, kBaTotalTiles,
+    kBaWords = 64
+};
+constexpr int64_t kBatchTableOffset = 256;
+constexpr int64_t kBatchAreaBytes = kBatchTableOffset + (int64_t)sizeof(View) * kMaxViews;
+constexpr int kPreChunk = 256;   // Gaussians per preprocess work item
+
+// Fill `v` for one frame in workspace `ws` with layout `L`.
+void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4dgs_config &cfg, const Layout &L,
+               void *ws, float *out_rgb, View *v);
+// Fill the flattened bases and totals; false if the views cannot share a launch.
+bool finish_batch(BatchArgs *b);
+
+// ---- launchers (each returns the cudaError_t of its launches).  `args` is the
+// host copy; `args_dev`, when not null, is a device copy the first kernel reads
+// instead of its by-value parameter (for CUDA graphs whose descriptors change).
+cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batch_area, cudaStream_t st, int num_sms);
+cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms);
+cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms);
+cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, float *out0,
                          unsigned long long *counts = nullptr);
-cudaError_t launch_backward(const d4dgs_scene &s, const CamArgs &c, float t, const d4dgs_config &cfg,
-                            const Layout &L, void *ws, const float *dl_drgb, const d4dgs_scene_grad &g,
-                            cudaStream_t st, int num_sms);
-int sort_launch_count(const Layout &L);
+cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb,
+                            const d4dgs_scene_grad &g, cudaStream_t st, int num_sms);
+int sort_launch_count(int n, int tile_passes);
+
+__device__ __forceinline__ const View &view_of(const char *batch_area, int v) {
+    return reinterpret_cast<const View *>(batch_area + kBatchTableOffset)[v];
+}
 
 // ---- device helpers
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {

@@ -68,43 +68,35 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
     }
 }
 
-struct SceneArgs {
-    const float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
-};
-
+// One Gaussian of view v: writes its 2D record, depth key, tile count and
+// rectangle, adds its rectangle to the view's difference grid, and counts it in
+// the shared depth-digit histogram.
 template <int DEG>
-__global__ void __launch_bounds__(256)
-preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ rec,
-                  uint32_t *__restrict__ depth_keys, uint32_t *__restrict__ tiles_touched,
-                  ushort4 *__restrict__ rect, uint32_t *__restrict__ ctl, int *__restrict__ grid) {
+__device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *hist, uint32_t &nvis) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    __shared__ uint32_t hist[4 * kRadix];
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-
+    const CamArgs &c = vw.cam;
+    const float t = vw.t;
     const float limx = mul(kJacClamp, dvd(mul(0.5f, (float)c.width), c.fx));
     const float limy = mul(kJacClamp, dvd(mul(0.5f, (float)c.height), c.fy));
     const float tilef = (float)c.tile;
-    uint32_t nvis = 0;
-
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    {
         uint32_t key = 0xFFFFFFFFu, tiles = 0;
         ushort4 rc = make_ushort4(0, 0, 0, 0);
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         do {
             // ---- deferred temporal slice and camera transform (binning order)
-            const float tau = sub(t, __ldg(s.t_mean + i));
-            const float m0 = add(__ldg(s.means + 3 * i + 0), mul(tau, __ldg(s.velocity + 3 * i + 0)));
-            const float m1 = add(__ldg(s.means + 3 * i + 1), mul(tau, __ldg(s.velocity + 3 * i + 1)));
-            const float m2 = add(__ldg(s.means + 3 * i + 2), mul(tau, __ldg(s.velocity + 3 * i + 2)));
+            const float tau = sub(t, __ldg(vw.t_mean + i));
+            const float m0 = add(__ldg(vw.means + 3 * i + 0), mul(tau, __ldg(vw.velocity + 3 * i + 0)));
+            const float m1 = add(__ldg(vw.means + 3 * i + 1), mul(tau, __ldg(vw.velocity + 3 * i + 1)));
+            const float m2 = add(__ldg(vw.means + 3 * i + 2), mul(tau, __ldg(vw.velocity + 3 * i + 2)));
             const float *R = c.R;
             const float X = add(add(add(mul(R[0], m0), mul(R[1], m1)), mul(R[2], m2)), c.T[0]);
             const float Y = add(add(add(mul(R[3], m0), mul(R[4], m1)), mul(R[5], m2)), c.T[1]);
             const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
             if (!(Z > kNear)) break;
             // ---- temporal opacity
-            const float o = dvd(1.0f, add(1.0f, expf(-__ldg(s.opacity_logit + i))));
-            const float st = expf(__ldg(s.log_t_scale + i));
+            const float o = dvd(1.0f, add(1.0f, expf(-__ldg(vw.opacity_logit + i))));
+            const float st = expf(__ldg(vw.log_t_scale + i));
             const float oh = mul(o, expf(dvd(mul(-0.5f, mul(tau, tau)), mul(st, st))));
             if (!(oh >= kAlphaMin)) break;
             // ---- projection of the mean and the Jacobian at the shifted mean
@@ -114,7 +106,7 @@ preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ r
             const float J00 = dvd(c.fx, Z), J02 = dvd(-mul(c.fx, xzc), Z);
             const float J11 = dvd(c.fy, Z), J12 = dvd(-mul(c.fy, yzc), Z);
             // ---- 3D covariance factor M = R(q) diag(s)
-            const float4 q = __ldg(reinterpret_cast<const float4 *>(s.quats) + i);
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(vw.quats) + i);
             const float qn = __fsqrt_rn(add(add(add(mul(q.x, q.x), mul(q.y, q.y)), mul(q.z, q.z)), mul(q.w, q.w)));
             const float qw = dvd(q.x, qn), qx = dvd(q.y, qn), qy = dvd(q.z, qn), qz = dvd(q.w, qn);
             float Rq[9];
@@ -127,8 +119,8 @@ preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ r
             Rq[6] = mul(2.0f, sub(mul(qx, qz), mul(qw, qy)));
             Rq[7] = mul(2.0f, add(mul(qy, qz), mul(qw, qx)));
             Rq[8] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qy, qy))));
-            const float sc[3] = {expf(__ldg(s.log_scales + 3 * i + 0)), expf(__ldg(s.log_scales + 3 * i + 1)),
-                                 expf(__ldg(s.log_scales + 3 * i + 2))};
+            const float sc[3] = {expf(__ldg(vw.log_scales + 3 * i + 0)), expf(__ldg(vw.log_scales + 3 * i + 1)),
+                                 expf(__ldg(vw.log_scales + 3 * i + 2))};
             float M[9];
 #pragma unroll
             for (int r = 0; r < 3; r++)
@@ -167,10 +159,10 @@ preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ r
             tiles = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
             // per-tile pair counts as a 2D difference grid ((tiles_x+1) x (tiles_y+1))
             const int gw = c.tiles_x + 1;
-            atomicAdd(grid + y0 * gw + x0, 1);
-            atomicAdd(grid + y0 * gw + x1 + 1, -1);
-            atomicAdd(grid + (y1 + 1) * gw + x0, -1);
-            atomicAdd(grid + (y1 + 1) * gw + x1 + 1, 1);
+            atomicAdd(vw.grid + y0 * gw + x0, 1);
+            atomicAdd(vw.grid + y0 * gw + x1 + 1, -1);
+            atomicAdd(vw.grid + (y1 + 1) * gw + x0, -1);
+            atomicAdd(vw.grid + (y1 + 1) * gw + x1 + 1, 1);
             key = __float_as_uint(Z);
             nvis++;
             // ---- conic (rendering only; ordinary arithmetic from here on)
@@ -182,7 +174,7 @@ preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ r
             float Yb[16];
             sh_basis<DEG>(dx, dy, dz, Yb);
             float col[3] = {0.5f, 0.5f, 0.5f};
-            const float *shp = s.sh + (size_t)i * (3 * K);
+            const float *shp = vw.sh + (size_t)i * (3 * K);
             if constexpr ((3 * K) % 4 == 0) {
                 // 16-byte aligned rows (degree 1 and 3): vector loads
                 const float4 *sh4 = reinterpret_cast<const float4 *>(shp);
@@ -210,21 +202,97 @@ preprocess_kernel(SceneArgs s, CamArgs c, float t, int n, float4 *__restrict__ r
             r1 = make_float4(s00 * inv_det, oh, Z, rf);
             r2 = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f), fmaxf(col[2], 0.0f), log2f(oh));
         } while (0);
-        rec[3 * (size_t)i + 0] = r0;
-        rec[3 * (size_t)i + 1] = r1;
-        rec[3 * (size_t)i + 2] = r2;
-        depth_keys[i] = key;
-        tiles_touched[i] = tiles;
-        rect[i] = rc;
+        vw.rec[3 * (size_t)i + 0] = r0;
+        vw.rec[3 * (size_t)i + 1] = r1;
+        vw.rec[3 * (size_t)i + 2] = r2;
+        vw.dkeys[0][i] = key;
+        vw.tiles_touched[i] = tiles;
+        vw.rect[i] = rc;
 #pragma unroll
         for (int p = 0; p < 4; p++) atomicAdd(&hist[p * kRadix + ((key >> (8 * p)) & 0xFFu)], 1u);
     }
-    // visible count (warp-aggregated) and the digit histograms of the depth keys
-    nvis = __reduce_add_sync(0xFFFFFFFFu, nvis);
-    if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(ctl + kCtlNumVisible, nvis);
+}
+
+// Flush a CTA's depth-digit histogram and visible count into view v.
+__device__ __forceinline__ void flush_view(const View &v, uint32_t *hist, uint32_t &nvis) {
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x)
-        if (hist[i]) atomicAdd(ctl + kCtlDepthHist + i, hist[i]);
+    const uint32_t w = __reduce_add_sync(0xFFFFFFFFu, nvis);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(v.ctl + kCtlNumVisible, w);
+    nvis = 0;
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
+        if (hist[i]) atomicAdd(v.ctl + kCtlDepthHist + i, hist[i]);
+        hist[i] = 0;
+    }
+    __syncthreads();
+}
+
+// Persistent: CTAs take 256-Gaussian chunks of the views' flattened Gaussians.
+__global__ void __launch_bounds__(256) preprocess_kernel(const char *__restrict__ ba) {
+    __shared__ uint32_t hist[4 * kRadix];
+    __shared__ int32_t s_chunk;
+    const uint32_t *bw = reinterpret_cast<const uint32_t *>(ba);
+    const int nviews = (int)bw[kBaNViews];
+    const int total = (int)bw[kBaTotalChunks];
+    uint32_t *counter = const_cast<uint32_t *>(bw) + kBaChunk;
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) hist[i] = 0;
+    uint32_t nvis = 0;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = (int32_t)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int chunk = s_chunk;
+        __syncthreads();
+        if (chunk >= total) break;
+        int vi = 0;
+        for (int u = 1; u < nviews; u++)
+            if (view_of(ba, u).chunk_base <= chunk) vi = u;
+        const View &v = view_of(ba, vi);
+        if (vi != cur) {
+            if (cur >= 0) flush_view(view_of(ba, cur), hist, nvis);
+            cur = vi;
+        }
+        const int i = (chunk - v.chunk_base) * kPreChunk + (int)threadIdx.x;
+        if (i < v.n) {
+            switch (v.sh_degree) {
+                case 0: preprocess_one<0>(v, i, hist, nvis); break;
+                case 1: preprocess_one<1>(v, i, hist, nvis); break;
+                case 2: preprocess_one<2>(v, i, hist, nvis); break;
+                default: preprocess_one<3>(v, i, hist, nvis); break;
+            }
+        }
+    }
+    if (cur >= 0) flush_view(view_of(ba, cur), hist, nvis);
+}
+
+// First kernel of a frame or batch: installs the descriptor table (from the
+// by-value parameter, or from args_dev when given), the launch totals, zeroed
+// work counters, and clears every view's per-frame region.
+__global__ void __launch_bounds__(256)
+clear_kernel(const __grid_constant__ BatchArgs args, const BatchArgs *args_dev, char *__restrict__ ba) {
+    const BatchArgs *A = args_dev ? args_dev : &args;
+    const int nviews = A->nviews;
+    if (blockIdx.x == 0) {
+        uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
+        for (int i = threadIdx.x; i < kBaWords; i += blockDim.x) bw[i] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bw[kBaNViews] = (uint32_t)nviews;
+            bw[kBaTotalChunks] = (uint32_t)A->total_chunks;
+            bw[kBaTotalDepthParts] = (uint32_t)A->total_depth_parts;
+            bw[kBaTotalDupParts] = (uint32_t)A->total_dup_parts;
+            bw[kBaTotalTiles] = (uint32_t)A->total_tiles;
+        }
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(A->v);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(ba + kBatchTableOffset);
+        const int words = nviews * (int)(sizeof(View) / 4);
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    }
+    for (int vi = 0; vi < nviews; vi++) {
+        uint4 *z = reinterpret_cast<uint4 *>(A->v[vi].zero_base);
+        const int64_t words = A->v[vi].zero_bytes / 16;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+            z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
 }
 
 }  // namespace
@@ -244,26 +312,16 @@ CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile) {
     return a;
 }
 
-cudaError_t launch_preprocess(const d4dgs_scene &sc, const CamArgs &c, float t, const Layout &L, void *ws,
-                              cudaStream_t st, int num_sms) {
-    if (sc.n == 0) return cudaSuccess;
-    SceneArgs s{sc.means, sc.t_mean, sc.velocity, sc.log_scales, sc.log_t_scale, sc.quats, sc.opacity_logit, sc.sh};
-    const int threads = 256;
-    int blocks = (sc.n + threads - 1) / threads;
-    const int max_blocks = num_sms * 8;   // persistent-ish: bounds the histogram flushes
-    if (blocks > max_blocks) blocks = max_blocks;
-    float4 *rec = at<float4>(ws, L.records);
-    uint32_t *dk = at<uint32_t>(ws, L.depth_keys[0]);
-    uint32_t *tt = at<uint32_t>(ws, L.tiles_touched);
-    ushort4 *rc = at<ushort4>(ws, L.rect);
-    uint32_t *ctl = at<uint32_t>(ws, L.control);
-    int *grid = at<int>(ws, L.grid);
-    switch (sc.sh_degree) {
-        case 0: preprocess_kernel<0><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl, grid); break;
-        case 1: preprocess_kernel<1><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl, grid); break;
-        case 2: preprocess_kernel<2><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl, grid); break;
-        default: preprocess_kernel<3><<<blocks, threads, 0, st>>>(s, c, t, sc.n, rec, dk, tt, rc, ctl, grid); break;
-    }
+cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batch_area, cudaStream_t st,
+                         int num_sms) {
+    clear_kernel<<<num_sms * 2, 256, 0, st>>>(args, static_cast<const BatchArgs *>(args_dev), batch_area);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms) {
+    if (args.total_chunks == 0) return cudaSuccess;
+    // persistent grid: 8 resident CTAs of 256 threads per SM
+    preprocess_kernel<<<num_sms * 8, 256, 0, st>>>(batch_area);
     return cudaGetLastError();
 }
 

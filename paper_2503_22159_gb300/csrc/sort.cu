@@ -65,38 +65,81 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
     return wsum + x - v;
 }
 
-// One onesweep pass over `count` keys (count read on the device when
-// count_ptr is given, clamped to count_cap); digit = (key >> shift) & mask.
-// KV: keys carry a separate uint32 value (IOTA: the value is the key's index).
-template <bool KV, bool IOTA>
+// Partition bases of a pass over the views of a launch (prefix sums of each
+// view's partition count), in shared memory; returns the total.
+template <bool TILE>
+__device__ __forceinline__ uint32_t pass_bases(const char *ba, int nviews, uint32_t *s_base) {
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int u = 0; u < nviews; u++) {
+            const View &v = view_of(ba, u);
+            s_base[u] = acc;
+            uint32_t parts;
+            if (TILE) {
+                const uint32_t k = min(v.ctl[kCtlNumKeys], v.cap);
+                parts = (k + kSortItems - 1) / kSortItems;
+            } else {
+                parts = (uint32_t)v.parts_depth;
+            }
+            acc += parts;
+        }
+        s_base[nviews] = acc;
+    }
+    __syncthreads();
+    return s_base[nviews];
+}
+
+// One onesweep pass over every view of the launch.  TILE = false: depth pass
+// `pass` (keys = depth bits, 8-bit digits, values = ids; IOTA generates them);
+// TILE = true: tile pass `pass` of the (tile, id) pairs (count read on the
+// device).  KV: keys carry a separate uint32 value.
+template <bool KV, bool IOTA, bool TILE>
 __global__ void __launch_bounds__(kSortThreads, KV ? 3 : 4)
-onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *count_ptr,
-                uint32_t count_const, uint32_t count_cap, int shift, uint32_t mask,
-                const uint32_t *__restrict__ hist, uint32_t *lookback, uint32_t *part_counter, uint32_t *status) {
+onesweep_kernel(char *__restrict__ ba, int pass) {
     __shared__ uint32_t s_warp_hist[8][kRadix];
     __shared__ uint32_t s_keys[kSortItems];
     __shared__ uint32_t s_vals[KV ? kSortItems : 1];
     __shared__ uint32_t s_delta[kRadix];   // global_start - local_start of each digit
     __shared__ uint32_t s_local_start[kRadix];
+    __shared__ uint32_t s_hist_excl[kRadix];
+    __shared__ uint32_t s_base[kMaxViews + 1];
     __shared__ uint32_t s_scan[8];
     __shared__ uint32_t s_part;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t count = count_const;
-    if (count_ptr) count = min(*count_ptr, count_cap);
-    const uint32_t num_parts = (count + kSortItems - 1) / kSortItems;
-
-    // exclusive digit offsets of this pass (identical for every partition)
-    uint32_t tot;
-    const uint32_t hist_excl = block_exclusive_scan_256(hist[tid], s_scan, &tot);
+    uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
+    const int nviews = (int)bw[kBaNViews];
+    uint32_t *part_counter = bw + (TILE ? kBaTile : kBaDepth) + pass;
+    const uint32_t total = pass_bases<TILE>(ba, nviews, s_base);
+    int cur = -1;
 
     for (;;) {
         if (tid == 0) s_part = atomicAdd(part_counter, 1u);
         for (int i = tid; i < 8 * kRadix; i += kSortThreads) (&s_warp_hist[0][0])[i] = 0;
         __syncthreads();
-        const uint32_t part = s_part;
-        if (part >= num_parts) break;
+        const uint32_t g = s_part;
+        if (g >= total) break;
+        int vi = 0;
+        for (int u = 1; u < nviews; u++)
+            if (s_base[u] <= g) vi = u;
+        const View &v = view_of(ba, vi);
+        const uint32_t part = g - s_base[vi];
+        const uint32_t *keys_in = TILE ? v.tkeys[pass & 1] : v.dkeys[pass & 1];
+        uint32_t *keys_out = TILE ? v.tkeys[(pass + 1) & 1] : v.dkeys[(pass + 1) & 1];
+        const uint32_t *vals_in = TILE ? v.tvals[pass & 1] : v.dvals[pass & 1];
+        uint32_t *vals_out = TILE ? v.tvals[(pass + 1) & 1] : v.dvals[(pass + 1) & 1];
+        const uint32_t count = TILE ? min(v.ctl[kCtlNumKeys], v.cap) : (uint32_t)v.n;
+        const int shift = TILE ? (v.packed ? v.id_bits : 0) + v.tile_shift[pass] : 8 * pass;
+        const uint32_t mask = TILE ? v.tile_mask[pass] : 0xFFu;
+        uint32_t *lookback = TILE ? v.lb_tile + (size_t)pass * v.parts_tile * kRadix
+                                  : v.lb_depth + (size_t)pass * v.parts_depth * kRadix;
+        uint32_t *status = v.ctl + kCtlStatus;
+        if (vi != cur) {   // exclusive digit offsets of this view's pass
+            const uint32_t *hist = v.ctl + (TILE ? kCtlTileHist : kCtlDepthHist) + pass * kRadix;
+            uint32_t tot;
+            s_hist_excl[tid] = block_exclusive_scan_256(hist[tid], s_scan, &tot);
+            cur = vi;
+        }
         const uint32_t base = part * kSortItems;
 
         // ---- load (warp-striped: item k of lane l is base + warp*32*IPT + k*32 + l)
@@ -145,20 +188,20 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
             int64_t j = (int64_t)part - 1;
             uint32_t spins = 0;
             while (j >= 0) {
-                const uint32_t v = ld_volatile_u32(lookback + (size_t)j * kRadix + d);
-                const uint32_t flag = v & kFlagMask;
+                const uint32_t val = ld_volatile_u32(lookback + (size_t)j * kRadix + d);
+                const uint32_t flag = val & kFlagMask;
                 if (flag == 0u) {
                     if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); break; }
                     if (spins > 32) __nanosleep(64);
                     continue;
                 }
-                excl += v & kValMask;
+                excl += val & kValMask;
                 if (flag == kFlagInc) break;
                 --j;
             }
             st_volatile_u32(lb + d, kFlagInc | ((excl + bcount) & kValMask));
         }
-        s_delta[d] = hist_excl + excl - lstart;
+        s_delta[d] = s_hist_excl[d] + excl - lstart;
         __syncthreads();
         // ---- scatter into shared memory in digit order
 #pragma unroll
@@ -182,13 +225,23 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     }
 }
 
-// Per-tile pair counts from the 2D difference grid; ranges; digit histograms of
-// the tile passes; the total K and the capacity check.  One CTA.
-__global__ void __launch_bounds__(1024)
-tilecount_kernel(int *grid, int tiles_x, int tiles_y, uint2 *__restrict__ ranges, uint32_t *ctl, uint32_t cap,
-                 int tile_passes, int sh0, int sh1, int sh2, uint32_t mk0, uint32_t mk1, uint32_t mk2) {
+// Per-tile pair counts from the view's 2D difference grid; ranges; digit
+// histograms of the tile passes; the total K and the capacity check.  One CTA
+// per view.
+__global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba) {
     __shared__ unsigned long long s_warp[32];
     __shared__ uint32_t s_hist[3 * kRadix];
+    const uint32_t *bw = reinterpret_cast<const uint32_t *>(ba);
+    if ((int)blockIdx.x >= (int)bw[kBaNViews]) return;
+    const View &v = view_of(ba, blockIdx.x);
+    int *grid = v.grid;
+    const int tiles_x = v.cam.tiles_x, tiles_y = v.cam.tiles_y;
+    uint2 *ranges = v.ranges;
+    uint32_t *ctl = v.ctl;
+    const uint32_t cap = v.cap;
+    const int tile_passes = v.tile_passes;
+    const int sh0 = v.tile_shift[0], sh1 = v.tile_shift[1], sh2 = v.tile_shift[2];
+    const uint32_t mk0 = v.tile_mask[0], mk1 = v.tile_mask[1], mk2 = v.tile_mask[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     const int gw = tiles_x + 1, gh = tiles_y + 1;
     for (int i = tid; i < 3 * kRadix; i += nt) s_hist[i] = 0;
@@ -243,13 +296,9 @@ tilecount_kernel(int *grid, int tiles_x, int tiles_y, uint2 *__restrict__ ranges
     }
 }
 
-// Scan of the tile counts in depth order fused with the pair emission.
-template <bool PACKED>
-__global__ void __launch_bounds__(kDupThreads)
-emit_kernel(const uint32_t *__restrict__ order, uint32_t n, const uint32_t *__restrict__ tiles_touched,
-            const ushort4 *__restrict__ rect, int tiles_x, uint32_t cap, int id_bits,
-            uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, unsigned long long *lookback,
-            uint32_t *ctl) {
+// Scan of the tile counts in depth order fused with the pair emission, over
+// 256-Gaussian partitions of every view of the launch.
+__global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba) {
     __shared__ uint32_t s_off[kDupItems], s_cnt[kDupItems], s_id[kDupItems];
     __shared__ ushort4 s_rect[kDupItems];
     __shared__ uint32_t s_scan[8];
@@ -257,61 +306,73 @@ emit_kernel(const uint32_t *__restrict__ order, uint32_t n, const uint32_t *__re
     __shared__ unsigned long long s_excl;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t *status = ctl + kCtlStatus;
-    uint32_t *part_counter = ctl + kCtlPartBase + 4;
-    const uint32_t num_parts = (n + kDupItems - 1) / kDupItems;
+    uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
+    const int nviews = (int)bw[kBaNViews];
+    const uint32_t total = bw[kBaTotalDupParts];
+    uint32_t *part_counter = bw + kBaDup;
 
     for (;;) {
         if (tid == 0) s_part = atomicAdd(part_counter, 1u);
         __syncthreads();
-        const uint32_t part = s_part;
-        if (part >= num_parts) break;
+        const uint32_t g = s_part;
+        if (g >= total) break;
+        int vi = 0;
+        for (int u = 1; u < nviews; u++)
+            if ((uint32_t)view_of(ba, u).dup_part_base <= g) vi = u;
+        const View &v = view_of(ba, vi);
+        const uint32_t part = g - (uint32_t)v.dup_part_base;
+        const uint32_t n = (uint32_t)v.n;
+        const uint32_t *order = v.dvals[0];   // after the 4 depth passes
         const uint32_t pos = part * kDupItems + tid;
         uint32_t id = 0, c = 0;
         ushort4 r = make_ushort4(0, 0, 0, 0);
         if (pos < n) {
             id = order[pos];
             if (id < n) {   // always true unless an earlier pass gave up on a spin-wait
-                c = tiles_touched[id];
-                if (c) r = rect[id];
+                c = v.tiles_touched[id];
+                if (c) r = v.rect[id];
             } else {
                 id = 0;
             }
         }
-        uint32_t total;
-        const uint32_t local = block_exclusive_scan_256(c, s_scan, &total);
+        uint32_t ptotal;
+        const uint32_t local = block_exclusive_scan_256(c, s_scan, &ptotal);
         s_off[tid] = local;
         s_cnt[tid] = c;
         s_id[tid] = id;
         s_rect[tid] = r;
         if (tid == 0) {
             unsigned long long excl = 0;
-            unsigned long long *lb = lookback + part;
+            unsigned long long *lb = v.lb_dup + part;
             if (part == 0) {
-                st_volatile_u64(lb, kFlagInc64 | (unsigned long long)total);
+                st_volatile_u64(lb, kFlagInc64 | (unsigned long long)ptotal);
             } else {
-                st_volatile_u64(lb, kFlagAgg64 | (unsigned long long)total);
+                st_volatile_u64(lb, kFlagAgg64 | (unsigned long long)ptotal);
                 int64_t j = (int64_t)part - 1;
                 uint32_t spins = 0;
                 while (j >= 0) {
-                    const unsigned long long v = ld_volatile_u64(lookback + j);
-                    const unsigned long long flag = v & kFlagMask64;
+                    const unsigned long long val = ld_volatile_u64(v.lb_dup + j);
+                    const unsigned long long flag = val & kFlagMask64;
                     if (flag == 0ull) {
-                        if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); break; }
+                        if (++spins > kSpinLimit) { atomicOr(v.ctl + kCtlStatus, kStatusTimeout); break; }
                         if (spins > 32) __nanosleep(64);
                         continue;
                     }
-                    excl += v & kValMask64;
+                    excl += val & kValMask64;
                     if (flag == kFlagInc64) break;
                     --j;
                 }
-                st_volatile_u64(lb, kFlagInc64 | ((excl + total) & kValMask64));
+                st_volatile_u64(lb, kFlagInc64 | ((excl + ptotal) & kValMask64));
             }
             s_excl = excl;
         }
         __syncthreads();
         // ---- emission: warp w writes the pairs of Gaussians w*32 .. w*32+31, one run each
         const unsigned long long gexcl = s_excl;
+        const int tiles_x = v.cam.tiles_x, id_bits = v.id_bits;
+        const bool packed = v.packed != 0;
+        const unsigned long long cap = v.cap;
+        uint32_t *keys_out = v.tkeys[0], *vals_out = v.tvals[0];
         for (int q = warp * 32; q < warp * 32 + 32; q++) {
             const uint32_t cq = s_cnt[q];
             if (!cq) continue;
@@ -327,7 +388,7 @@ emit_kernel(const uint32_t *__restrict__ order, uint32_t n, const uint32_t *__re
                 const uint32_t tile = (uint32_t)(((int)rq.z + ty) * tiles_x + (int)rq.x + tx);
                 const unsigned long long o = off + j;
                 if (o < cap) {
-                    if (PACKED) {
+                    if (packed) {
                         keys_out[o] = (tile << id_bits) | gid;
                     } else {
                         keys_out[o] = tile;
@@ -348,84 +409,37 @@ int occupancy_blocks(const void *fn, int threads) {
 
 }  // namespace
 
-int sort_launch_count(const Layout &L) { return L.n == 0 ? 1 : 1 + L.depth_passes + 1 + L.tile_passes; }
+int sort_launch_count(int n, int tile_passes) { return n == 0 ? 1 : 1 + 4 + 1 + tile_passes; }
 
-cudaError_t launch_sort(const Layout &L, void *ws, cudaStream_t st, int num_sms) {
-    uint32_t *ctl = at<uint32_t>(ws, L.control);
-    uint32_t *status = ctl + kCtlStatus;
-    static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_emit_p = 0, occ_emit_u = 0;
+cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
+    static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0, occ_emit = 0;
     if (!occ_kv) {
-        occ_iota = occupancy_blocks((const void *)onesweep_kernel<true, true>, kSortThreads);
-        occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false>, kSortThreads);
-        occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false>, kSortThreads);
-        occ_emit_p = occupancy_blocks((const void *)emit_kernel<true>, kDupThreads);
-        occ_emit_u = occupancy_blocks((const void *)emit_kernel<false>, kDupThreads);
+        occ_iota = occupancy_blocks((const void *)onesweep_kernel<true, true, false>, kSortThreads);
+        occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false, false>, kSortThreads);
+        occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false, true>, kSortThreads);
+        occ_tkv = occupancy_blocks((const void *)onesweep_kernel<true, false, true>, kSortThreads);
+        occ_emit = occupancy_blocks((const void *)emit_kernel, kDupThreads);
     }
-    uint32_t sh[3], mk[3];
-    for (int p = 0; p < 3; p++) {
-        sh[p] = (uint32_t)L.tile_shift[p];
-        mk[p] = L.tile_pass_bits[p] ? (1u << L.tile_pass_bits[p]) - 1u : 0u;
-    }
-    // ---- 0. per-tile counts, ranges, tile digit histograms
-    tilecount_kernel<<<1, 1024, 0, st>>>(at<int>(ws, L.grid), L.tiles_x, L.tiles_y, at<uint2>(ws, L.ranges), ctl,
-                                         (uint32_t)L.cap, L.tile_passes, sh[0], sh[1], sh[2], mk[0], mk[1], mk[2]);
-    // (always launched: it writes every tile's range, all empty when N = 0)
-    if (L.n == 0) return cudaGetLastError();
-    // ---- 1. depth sort: depth_keys[0] -> ... -> depth_keys[0] (4 passes), ids in depth_vals[0]
-    const uint32_t n = (uint32_t)L.n;
-    for (int p = 0; p < L.depth_passes; p++) {
-        const uint32_t *kin = at<uint32_t>(ws, L.depth_keys[p & 1]);
-        uint32_t *kout = at<uint32_t>(ws, L.depth_keys[(p + 1) & 1]);
-        const uint32_t *vin = at<uint32_t>(ws, L.depth_vals[p & 1]);
-        uint32_t *vout = at<uint32_t>(ws, L.depth_vals[(p + 1) & 1]);
-        const uint32_t *hist = ctl + kCtlDepthHist + p * kRadix;
-        uint32_t *lb = at<uint32_t>(ws, L.lb_depth) + (size_t)p * L.parts_depth * kRadix;
-        uint32_t *pc = ctl + kCtlPartBase + p;
-        const int64_t gmax = (int64_t)(p == 0 ? occ_iota : occ_kv) * num_sms;
-        const int grid = (int)(L.parts_depth < gmax ? L.parts_depth : gmax);
+    // ---- 0. per-tile counts, ranges, tile digit histograms (always: ranges are written for every tile)
+    // fixed grid (blocks beyond the table's view count return at once), so that a
+    // captured launch serves batches of any size
+    tilecount_kernel<<<kMaxViews, 1024, 0, st>>>(batch_area);
+    if (args.max_n == 0) return cudaGetLastError();
+    // ---- 1. depth sort (4 passes), ids in dvals[0]
+    for (int p = 0; p < 4; p++) {
         if (p == 0)
-            onesweep_kernel<true, true><<<grid, kSortThreads, 0, st>>>(kin, nullptr, kout, vout, nullptr, n, n, 8 * p,
-                                                                       0xFFu, hist, lb, pc, status);
+            onesweep_kernel<true, true, false><<<occ_iota * num_sms, kSortThreads, 0, st>>>(batch_area, p);
         else
-            onesweep_kernel<true, false><<<grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, nullptr, n, n, 8 * p,
-                                                                        0xFFu, hist, lb, pc, status);
+            onesweep_kernel<true, false, false><<<occ_kv * num_sms, kSortThreads, 0, st>>>(batch_area, p);
     }
-    const uint32_t *order = at<uint32_t>(ws, L.depth_vals[L.depth_passes & 1]);
     // ---- 2. scan + emission in depth order
-    {
-        const int64_t gmax = (int64_t)(L.packed ? occ_emit_p : occ_emit_u) * num_sms;
-        const int grid = (int)(L.parts_dup < gmax ? L.parts_dup : gmax);
-        uint32_t *vals0 = L.packed ? nullptr : at<uint32_t>(ws, L.tile_vals[0]);
-        if (L.packed)
-            emit_kernel<true><<<grid, kDupThreads, 0, st>>>(order, n, at<uint32_t>(ws, L.tiles_touched),
-                                                            at<ushort4>(ws, L.rect), L.tiles_x, (uint32_t)L.cap,
-                                                            L.id_bits, at<uint32_t>(ws, L.tile_keys[0]), vals0,
-                                                            at<unsigned long long>(ws, L.lb_dup), ctl);
-        else
-            emit_kernel<false><<<grid, kDupThreads, 0, st>>>(order, n, at<uint32_t>(ws, L.tiles_touched),
-                                                             at<ushort4>(ws, L.rect), L.tiles_x, (uint32_t)L.cap,
-                                                             L.id_bits, at<uint32_t>(ws, L.tile_keys[0]), vals0,
-                                                             at<unsigned long long>(ws, L.lb_dup), ctl);
-    }
+    emit_kernel<<<occ_emit * num_sms, kDupThreads, 0, st>>>(batch_area);
     // ---- 3. stable sort of the pairs by tile bits
-    const int key_shift = L.packed ? L.id_bits : 0;
-    for (int p = 0; p < L.tile_passes; p++) {
-        const uint32_t *kin = at<uint32_t>(ws, L.tile_keys[p & 1]);
-        uint32_t *kout = at<uint32_t>(ws, L.tile_keys[(p + 1) & 1]);
-        const uint32_t *hist = ctl + kCtlTileHist + p * kRadix;
-        uint32_t *lb = at<uint32_t>(ws, L.lb_tile) + (size_t)p * L.parts_tile * kRadix;
-        uint32_t *pc = ctl + kCtlPartBase + 5 + p;
-        const int64_t gmax = (int64_t)(L.packed ? occ_k : occ_kv) * num_sms;
-        int64_t grid = L.parts_tile < gmax ? L.parts_tile : gmax;
-        if (grid < 1) grid = 1;
-        if (L.packed)
-            onesweep_kernel<false, false><<<(int)grid, kSortThreads, 0, st>>>(
-                kin, nullptr, kout, nullptr, ctl + kCtlNumKeys, 0u, (uint32_t)L.cap, key_shift + L.tile_shift[p],
-                mk[p], hist, lb, pc, status);
+    for (int p = 0; p < args.tile_passes; p++) {
+        if (args.packed)
+            onesweep_kernel<false, false, true><<<occ_k * num_sms, kSortThreads, 0, st>>>(batch_area, p);
         else
-            onesweep_kernel<true, false><<<(int)grid, kSortThreads, 0, st>>>(
-                kin, at<uint32_t>(ws, L.tile_vals[p & 1]), kout, at<uint32_t>(ws, L.tile_vals[(p + 1) & 1]),
-                ctl + kCtlNumKeys, 0u, (uint32_t)L.cap, L.tile_shift[p], mk[p], hist, lb, pc, status);
+            onesweep_kernel<true, false, true><<<occ_tkv * num_sms, kSortThreads, 0, st>>>(batch_area, p);
     }
     return cudaGetLastError();
 }

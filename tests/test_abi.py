@@ -66,8 +66,8 @@ def test_workspace_bytes_monotone_and_layout(d4):
         d4.d4dgs_workspace_layout(300_000, cam, cfg, b0 - 1)
 
 
-@pytest.mark.parametrize("w,h,tile,passes", [(128, 128, 16, 1), (1352, 1014, 16, 2), (2704, 2028, 8, 3),
-                                             (16, 16, 16, 0), (7, 5, 32, 0)])
+@pytest.mark.parametrize("w,h,tile,passes", [(128, 128, 16, 2), (1352, 1014, 16, 2), (2704, 2028, 8, 3),
+                                             (16, 16, 16, 2), (7, 5, 32, 2), (4096, 4096, 8, 3)])
 def test_tile_pass_count(d4, w, h, tile, passes):
     cam = synth.pinhole(w, h)
     cfg = d4.config_struct(tile, 64)
@@ -111,8 +111,8 @@ def test_invalid_arguments_rejected_on_host(d4):
 def test_launch_count(d4):
     cam = synth.pinhole(1352, 1014)
     cfg = d4.config_struct(16, 256)
-    # preprocess + tile counts + 4 depth passes + scan/emit + 2 tile passes + blend
-    assert d4.d4dgs_launches_per_frame(300_000, cam, cfg) == 10
+    # clear + preprocess + tile counts + 4 depth passes + scan/emit + 2 tile passes + blend
+    assert d4.d4dgs_launches_per_frame(300_000, cam, cfg) == 11
 
 
 def test_packing_decision(d4):
