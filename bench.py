@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["scene", "tiny", "large"], default="scene")
-    p.add_argument("--tile", type=int, default=16)
+    p.add_argument("--tile", default="auto", help="8, 16, 32 or auto (autotuner sweep)")
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -69,6 +69,22 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def rank_frames(rank: int, world: int, n_frames: int, count: int):
+    """Frames of one replica: rank r takes frames r, r + world, r + 2 world, ...
+    (independent frames: no data exchange between ranks)."""
+    return [(rank + world * k) % n_frames for k in range(count)]
+
+
+def reduce_max(value: float, pg, device=None) -> float:
+    """Max over ranks (the job's time is its slowest replica's)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
 
 
 def load_peaks():
@@ -289,10 +305,17 @@ def run_ours(args):
         pg = dist
     stream = torch.cuda.current_stream(dev)
     scene = d4.DeviceScene.from_host(w.scene, dev)
+    tune_table = None
+    if args.tile == "auto":
+        from paper_2503_22159_gb300 import autotune
+        probe = [w.frames[k] for k in (0, nf // 2, nf - 1)]
+        (tile, batch), tune_table = autotune.tune(scene, probe, device=dev, force=True)
+        args.tile, args.batch = tile, batch
+    args.tile = int(args.tile)
     cfg = d4.config_struct(args.tile, args.batch)
     cam0 = w.frames[0][0]
     K, W = args.steps, args.warmup
-    order = [(rank + world * k) % nf for k in range(W + K)]
+    order = rank_frames(rank, world, nf, W + K)
 
     # size the key capacity on this rank's frames (untimed)
     r = d4.Renderer(scene.n, cam0, tile=args.tile, batch=args.batch, key_capacity=160 * scene.n, device=dev)
@@ -341,11 +364,7 @@ def run_ours(args):
     clk = clocks.stop()
     stage = np.array([[events[k][i].elapsed_time(events[k][i + 1]) for i in range(3)] for k in range(K)])
     step_ms = stage.sum(axis=1)
-    elapsed = float(step_ms.sum())
-    if pg:
-        t = torch.tensor([elapsed], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = reduce_max(float(step_ms.sum()), pg, dev)
     # status of the last frame (every frame was sized beforehand)
     st = r.stats(w.frames[order[-1]][0])
     if st["status"] != 0:
@@ -411,11 +430,7 @@ def run_ours(args):
         for k in range(E):
             cam, t = w.frames[order[(W + k) % len(order)]]
             d4.d4dgs_render_host(host, cam, t, cfg, dbuf, r.ws, out, himg, stream)
-        te = time.perf_counter() - t0
-        if pg:
-            tt = torch.tensor([te], device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            te = float(tt.item())
+        te = reduce_max(time.perf_counter() - t0, pg, dev)
         e2e = {"value": world * E / te, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": E, "api": "d4dgs_render_host"}
 
@@ -437,6 +452,7 @@ def run_ours(args):
         "gpu_launches": int(launches * K), "launches_per_frame": launches,
         "wall_s_timed_region": t_wall, "peaks": peak_kind,
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out,
+        "autotune": {"chosen": f"{args.tile}/{args.batch}", "ms_per_frame": tune_table} if tune_table else None,
     }
     print(json.dumps(line), flush=True)
     if pg:

@@ -387,17 +387,23 @@ void orc_render_pixels(const orc_g2d *g, int n, const orc_camera *cam, const dou
  *   s01 = (TM00*TM10 + TM01*TM11) + TM02*TM12
  *   det = s00*s11 - s01*s01; cull !(det > 0)
  *   mid = 0.5*(s00 + s11); lam = mid + sqrtf(max(0.1, mid*mid - det))
- *   r = (int) ceilf(3.33 * sqrtf(lam))
- *   cull unless u, v finite; x0 = floorf((u - r)/tile), x1 = floorf((u + r)/tile),
- *   cull if x1 < 0 or x0 > tiles_x - 1, then clamp to [0, tiles_x-1] (same in y)
+ *   r = (int) ceilf(3.33 * sqrtf(lam))   (the 2D Gaussian's radius)
+ *   cull unless u, v finite
+ *   k2 = ((2*logf(255*o_hat))*1.0008) + 0.0008;  rx = ceilf(sqrtf(k2*s00)), ry = ceilf(sqrtf(k2*s11))
+ *   (bounding box of d^T Sigma'^-1 d <= k2: outside it o_hat e^p < 1/255)
+ *   x0 = floorf((u - rx)/tile), x1 = floorf((u + rx)/tile),
+ *   cull if x1 < 0 or x0 > tiles_x - 1, then clamp to [0, tiles_x-1] (same in y with ry)
  *   tiles = (x1 - x0 + 1)(y1 - y0 + 1); depth key = bits of Z
- * Flags: bit 0 -- 3.33 sqrt(lambda_max) within 3e-6 relative of an integer;
- * bit 1 -- o_hat within 3e-6 relative of 1/255.  Every operation above is
- * correctly rounded and reproducible on any IEEE machine except expf, whose
- * FP32 result may differ by one or two ulps between math libraries; through
- * the chain (s -> Sigma' -> lambda_max, three exps -> o_hat) that moves these
- * two quantities by at most ~1.5e-6 relative, so a decision further than 3e-6
- * from its threshold is the same everywhere.  A flagged Gaussian is excluded
+ * Flags: bit 0 -- sqrt(k2 s00) or sqrt(k2 s11) within 3e-6 relative of an
+ * integer (rectangle); bit 1 -- o_hat within 3e-6 relative of 1/255 (cull);
+ * bit 2 -- 3.33 sqrt(lambda_max) within 3e-6 of an integer (the radius field
+ * only: it does not take part in binning).
+ * Every operation above is correctly rounded and reproducible on any IEEE
+ * machine except expf and logf, whose FP32 results may differ by one or two
+ * ulps between math libraries; through the chains (s -> Sigma' -> radii, three
+ * exps -> o_hat -> k2) that moves these quantities by at most ~1.5e-6
+ * relative, so a decision further than 3e-6 from its threshold is the same
+ * everywhere.  A flagged Gaussian is excluded
  * from bit-exact comparison.  A culled Gaussian has depth key 0xFFFFFFFF and
  * 0 tiles.
  * ------------------------------------------------------------------------- */
@@ -474,13 +480,18 @@ void orc_bin_f32(const orc_scene_f32 *sc, const orc_camera_f32 *cam, float t, in
         float mid = 0.5f * (s00 + s11);
         float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
         float rf = ceilf(3.33f * sqrtf(lam));
-        {   /* radius decided within reach of an ulp difference in expf of the scales */
-            const double rr = 3.33 * sqrt((double)lam);
-            if (fabs(rr - nearbyint(rr)) <= 3e-6 * rr) flags[i] |= 1;
-        }
         if (!(isfinite(u) && isfinite(v))) continue;
-        float fx0 = floorf((u - rf) / tilef), fx1 = floorf((u + rf) / tilef);
-        float fy0 = floorf((v - rf) / tilef), fy1 = floorf((v + rf) / tilef);
+        float k2 = ((2.0f * logf(255.0f * oh)) * 1.0008f) + 0.0008f;
+        float ex = sqrtf(k2 * s00), ey = sqrtf(k2 * s11);
+        float rx = ceilf(ex), ry = ceilf(ey);
+        {   /* radii decided within reach of an ulp difference in expf / logf */
+            const double rr = 3.33 * sqrt((double)lam);
+            if (fabs(rr - nearbyint(rr)) <= 3e-6 * rr) flags[i] |= 4;
+            if (fabs((double)ex - nearbyint((double)ex)) <= 3e-6 * ex) flags[i] |= 1;
+            if (fabs((double)ey - nearbyint((double)ey)) <= 3e-6 * ey) flags[i] |= 1;
+        }
+        float fx0 = floorf((u - rx) / tilef), fx1 = floorf((u + rx) / tilef);
+        float fy0 = floorf((v - ry) / tilef), fy1 = floorf((v + ry) / tilef);
         if (!(fx1 >= 0.0f) || !(fx0 <= (float)(tiles_x - 1))) continue;
         if (!(fy1 >= 0.0f) || !(fy0 <= (float)(tiles_y - 1))) continue;
         int32_t x0 = (int32_t)fmaxf(fx0, 0.0f), x1 = (int32_t)fminf(fx1, (float)(tiles_x - 1));

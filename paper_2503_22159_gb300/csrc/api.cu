@@ -395,7 +395,7 @@ int d4dgs_render_batch(const void *args_host, const void *args_dev, void *batch_
     cudaError_t e = launch_clear(b, args_dev, ba, st, sms);
     if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
     if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
-    if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
+    if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr, nullptr, /*persist=*/true);
     return cuda_status(e);
 }
 

@@ -58,8 +58,10 @@ __device__ __forceinline__ bool blend_step(PixelState &px, float p, float L, con
 // COUNT: instrumented variant for profiling, which also totals the (pixel,
 // Gaussian) pairs evaluated and blended into counts[0..1] (not used on the
 // render path).  Persistent: CTAs take tiles of the views' flattened tiles.
-template <int TS, int BATCH, bool COUNT>
-__global__ void __launch_bounds__(TS *TS / 2, TS == 8 ? 16 : (TS == 16 ? 12 : 3))
+// PERSIST: CTAs take tiles from an atomic counter until all are done (fixed
+// grid, for batched and graph-captured launches); otherwise one CTA per tile.
+template <int TS, int BATCH, bool COUNT, bool PERSIST>
+__global__ void __launch_bounds__(TS *TS / 2, PERSIST ? (TS == 8 ? 16 : (TS == 16 ? 12 : 3)) : 1)
 blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts) {
     constexpr int NT = TS * TS / 2;
     __shared__ float4 s_g[BATCH];    // u, v, A, B
@@ -71,11 +73,16 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
     const int total = (int)bw[kBaTotalTiles];
     uint32_t n_eval = 0, n_blend = 0;
 
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int32_t)atomicAdd(bw + kBaBlend, 1u);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
+    for (int pass = 0;; pass++) {
+        int item;
+        if (PERSIST) {
+            if (threadIdx.x == 0) s_item = (int32_t)atomicAdd(bw + kBaBlend, 1u);
+            __syncthreads();
+            item = s_item;
+            __syncthreads();
+        } else {
+            item = pass == 0 ? (int)blockIdx.x : total;
+        }
         if (item >= total) break;
         int vi = 0;
         for (int u = 1; u < nviews; u++)
@@ -171,7 +178,8 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
 }
 
 template <int TS, int BATCH>
-cudaError_t launch_ts(char *ba, cudaStream_t st, int num_sms, float *out0, unsigned long long *counts) {
+cudaError_t launch_ts(char *ba, int total_tiles, bool persist, cudaStream_t st, int num_sms, float *out0,
+                      unsigned long long *counts) {
     auto go = [&](auto kernel) {
         static int occ = 0;   // per instantiation; queried once, before any graph capture uses it
         if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TS * TS / 2, 0) != cudaSuccess ||
@@ -179,20 +187,27 @@ cudaError_t launch_ts(char *ba, cudaStream_t st, int num_sms, float *out0, unsig
             occ = 1;
         kernel<<<occ * num_sms, TS * TS / 2, 0, st>>>(ba, out0, counts);
     };
-    if (counts) go(blend_kernel<TS, BATCH, true>);
-    else go(blend_kernel<TS, BATCH, false>);
+    if (persist) {
+        if (counts) go(blend_kernel<TS, BATCH, true, true>);
+        else go(blend_kernel<TS, BATCH, false, true>);
+    } else if (counts) {
+        blend_kernel<TS, BATCH, true, false><<<total_tiles, TS * TS / 2, 0, st>>>(ba, out0, counts);
+    } else {
+        blend_kernel<TS, BATCH, false, false><<<total_tiles, TS * TS / 2, 0, st>>>(ba, out0, counts);
+    }
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, float *out0,
-                         unsigned long long *counts) {
+                         unsigned long long *counts, bool persist) {
     if (args.total_tiles == 0) return cudaSuccess;
-#define D4DGS_BATCHES(TS)                                                                        \
-    if (args.batch == 64) return launch_ts<TS, 64>(batch_area, st, num_sms, out0, counts);         \
-    if (args.batch == 128) return launch_ts<TS, 128>(batch_area, st, num_sms, out0, counts);       \
-    if (args.batch == 256) return launch_ts<TS, 256>(batch_area, st, num_sms, out0, counts);       \
+    const int nt = args.total_tiles;
+#define D4DGS_BATCHES(TS)                                                                              \
+    if (args.batch == 64) return launch_ts<TS, 64>(batch_area, nt, persist, st, num_sms, out0, counts);   \
+    if (args.batch == 128) return launch_ts<TS, 128>(batch_area, nt, persist, st, num_sms, out0, counts); \
+    if (args.batch == 256) return launch_ts<TS, 256>(batch_area, nt, persist, st, num_sms, out0, counts); \
     return cudaErrorInvalidValue;
     switch (args.tile) {
         case 8: D4DGS_BATCHES(8)

@@ -17,6 +17,9 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;
 constexpr float kRadiusK = 3.33f;      // 3.33^2 > 2 ln 255: covers every alpha >= 1/255
+// margin on k^2 = 2 ln(255 o_hat) of the binning ellipse (k^2 * kK2Scale + kK2Pad)
+constexpr float kK2Scale = 1.0008f;
+constexpr float kK2Pad = 0.0008f;
 
 // ---- sort geometry
 constexpr int kSortThreads = 256;
@@ -157,7 +160,7 @@ cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batc
 cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms);
 cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms);
 cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, float *out0,
-                         unsigned long long *counts = nullptr);
+                         unsigned long long *counts = nullptr, bool persist = false);
 cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb,
                             const d4dgs_scene_grad &g, cudaStream_t st, int num_sms);
 int sort_launch_count(int n, int tile_passes);

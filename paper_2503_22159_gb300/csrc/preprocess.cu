@@ -8,7 +8,9 @@
 //   (u, v) = (fx X/Z + cx, fy Y/Z + cy)                         (Eq. 12)
 //   J at the time-shifted mean, x/z and y/z clamped             (Eq. 14)
 //   Sigma' = (J W M)(J W M)^T + 0.3 I,  M = R(q) diag(s)        (Eq. 16; Sigma3D = M M^T)
-//   radius = ceil(3.33 sqrt(lambda_max)), tile rectangle, depth key = bits(Z)
+//   radius = ceil(3.33 sqrt(lambda_max)); tile rectangle = bounding box of the
+//   alpha >= 1/255 ellipse (half-extents ceil(k sqrt(Sigma'_00)), ceil(k sqrt(Sigma'_11)),
+//   k^2 = 2 ln(255 o_hat) with a small margin); depth key = bits(Z)
 //   colour = max(0, SH . Y(normalize(mu(t) - campos)) + 0.5)
 //
 // The quantities that decide binning (Z, u, v, Sigma', lambda_max, radius,
@@ -147,10 +149,14 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
             const float mid = mul(0.5f, add(s00, s11));
             const float lam = add(mid, __fsqrt_rn(fmaxf(0.1f, sub(mul(mid, mid), det))));
             const float rf = ceilf(mul(kRadiusK, __fsqrt_rn(lam)));
-            // ---- tile rectangle (inclusive tile indices)
+            // ---- tile rectangle (inclusive tile indices): the bounding box of the
+            // ellipse d^T Sigma'^-1 d <= k^2, k^2 = 2 ln(255 o_hat) (+ margin), outside
+            // which alpha = o_hat e^p < 1/255; half-extents k sqrt(Sigma'_00), k sqrt(Sigma'_11)
             if (!(isfinite(u) && isfinite(v))) break;
-            const float fx0 = floorf(dvd(sub(u, rf), tilef)), fx1 = floorf(dvd(add(u, rf), tilef));
-            const float fy0 = floorf(dvd(sub(v, rf), tilef)), fy1 = floorf(dvd(add(v, rf), tilef));
+            const float k2 = add(mul(mul(2.0f, logf(mul(255.0f, oh))), kK2Scale), kK2Pad);
+            const float rx = ceilf(__fsqrt_rn(mul(k2, s00))), ry = ceilf(__fsqrt_rn(mul(k2, s11)));
+            const float fx0 = floorf(dvd(sub(u, rx), tilef)), fx1 = floorf(dvd(add(u, rx), tilef));
+            const float fy0 = floorf(dvd(sub(v, ry), tilef)), fy1 = floorf(dvd(add(v, ry), tilef));
             if (!(fx1 >= 0.0f) || !(fx0 <= (float)(c.tiles_x - 1))) break;
             if (!(fy1 >= 0.0f) || !(fy0 <= (float)(c.tiles_y - 1))) break;
             const int x0 = (int)fmaxf(fx0, 0.0f), x1 = (int)fminf(fx1, (float)(c.tiles_x - 1));

@@ -1,0 +1,44 @@
+"""Autotuner: cache keys and persistence and the sweep on the CPU (with a
+fake timer); on the GPU, a real sweep picks a valid configuration whose image
+equals every other configuration's."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+
+@pytest.fixture()
+def at(tmp_path, monkeypatch):
+    monkeypatch.setenv("D4DGS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_22159_gb300 import autotune
+    return autotune
+
+
+def test_sweep_picks_fastest_and_cache_roundtrip(at, tmp_path):
+    fake = {(8, 64): 3.0, (16, 128): 1.5, (32, 256): 2.0}
+    best, table = at.sweep(lambda t, b: fake.get((t, b), 9.0))
+    assert best == (16, 128) and len(table) == 9
+    key = at.cache_key("GB300", 1352, 1014, 300_000)
+    assert key == "GB300|1352x1014|n<=524288"
+    c = at.TuneCache()
+    c.put(key, *best, table)
+    assert at.TuneCache().get(key) == (16, 128)
+    assert at.TuneCache().get(at.cache_key("GB300", 1352, 1014, 600_000)) is None   # other N bucket
+
+
+@pytest.mark.gpu
+def test_gpu_sweep_choice_renders_identically(at):
+    import paper_2503_22159_gb300 as d4
+    sc = synth.make_scene(20_000, 61, "box20", sh_degree=1)
+    frames = synth.orbit(3, 320, 240, 300)[100:103]
+    ds = d4.DeviceScene.from_host(sc)
+    (tile, batch), table = at.tune(ds, frames, force=True)
+    assert tile in at.TILES and batch in at.BATCHES and len(table) == 9
+    assert at.tune(ds, frames)[1] is None   # cached
+    cam, t = frames[0]
+    ref = d4.Renderer(sc.n, cam, tile=16, batch=256).render(ds, cam, t).clone()
+    img = d4.Renderer(sc.n, cam, tile=tile, batch=batch).render(ds, cam, t)
+    assert torch.equal(img, ref)

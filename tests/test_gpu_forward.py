@@ -43,13 +43,14 @@ def test_preprocess_matches_oracle():
     rect = r.view("rect", torch.int16, 4 * w.scene.n, cam).cpu().numpy().view(np.uint16).reshape(-1, 4)
     b = oracle.bin_f32(w.scene, cam, t, 16)
     g = oracle.preprocess(w.scene, cam, t)
-    flag = b["flags"] != 0
+    flag = (b["flags"] & 3) != 0
     # integer / bit outputs: exact against the FP32 mirror
     assert np.array_equal(keys[~flag], b["depth_key"][~flag])
     assert np.array_equal(tt[~flag], b["tiles_touched"][~flag].astype(np.int32))
     vis = (b["tiles_touched"] > 0) & ~flag
     assert np.array_equal(rect[vis].astype(np.int32), b["rect"][vis])
-    assert np.array_equal(rec[vis, 7].astype(np.int32), b["radius"][vis])
+    rvis = vis & ((b["flags"] & 4) == 0)
+    assert np.array_equal(rec[rvis, 7].astype(np.int32), b["radius"][rvis])
     # float outputs: against FP64
     np.testing.assert_allclose(rec[vis, 0], g["u"][vis], atol=2e-4)
     np.testing.assert_allclose(rec[vis, 1], g["v"][vis], atol=2e-4)

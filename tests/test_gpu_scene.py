@@ -39,10 +39,11 @@ def test_scene_preprocess_and_lists(scene_w, gpu_renderer, k):
     rec = gu.gpu_records(r, n, cam)
     b = oracle.bin_f32(scene_w.scene, cam, t, 16)
     g = oracle.preprocess(scene_w.scene, cam, t)
-    flag = b["flags"] != 0
+    flag = (b["flags"] & 3) != 0
     vis = (b["tiles_touched"] > 0) & ~flag
     assert vis.sum() > 100_000
-    assert np.array_equal(rec[vis, 7].astype(np.int32), b["radius"][vis])
+    rvis = vis & ((b["flags"] & 4) == 0)
+    assert np.array_equal(rec[rvis, 7].astype(np.int32), b["radius"][rvis])
     assert np.array_equal(rec[vis, 6].view(np.uint32), b["depth_key"][vis])
     np.testing.assert_allclose(rec[vis, 0], g["u"][vis], atol=2e-3)
     np.testing.assert_allclose(rec[vis, 1], g["v"][vis], atol=2e-3)

@@ -49,8 +49,12 @@ MUTANTS = [
     ("colour not clamped at zero", "out->rgb[3 * (size_t)i + ch] = fmax(0.0, s + 0.5);",
      "out->rgb[3 * (size_t)i + ch] = s + 0.5;", ["test_negative_colour_is_clamped"]),
     ("FP32 radius factor 3.0", "float rf = ceilf(3.33f * sqrtf(lam));", "float rf = ceilf(3.0f * sqrtf(lam));",
-     ["test_bin_f32_agrees_with_fp64", "test_tile_rect_covers_alpha_support"]),
-    ("FP32 rect with truncation", "float fx0 = floorf((u - rf) / tilef)", "float fx0 = floorf((u - rf) / tilef) + 1.0f",
+     ["test_bin_f32_agrees_with_fp64"]),
+    ("FP32 binning ellipse without the factor 2", "float k2 = ((2.0f * logf(255.0f * oh)) * 1.0008f) + 0.0008f;",
+     "float k2 = ((1.0f * logf(255.0f * oh)) * 1.0008f) + 0.0008f;", ["test_tile_rect_covers_alpha_support"]),
+    ("FP32 binning ellipse with the wrong axis", "float ex = sqrtf(k2 * s00), ey = sqrtf(k2 * s11);",
+     "float ex = sqrtf(k2 * s11), ey = sqrtf(k2 * s00);", ["test_tile_rect_covers_alpha_support"]),
+    ("FP32 rect with truncation", "float fx0 = floorf((u - rx) / tilef)", "float fx0 = floorf((u - rx) / tilef) + 1.0f",
      ["test_tile_rect_covers_alpha_support"]),
     # adjoint (caught by the finite-difference pin)
     ("adjoint: colour behind ignored", "dalpha += Ti * G[ch] * (c[ch] - B[ch]);", "dalpha += Ti * G[ch] * c[ch];",

@@ -387,7 +387,7 @@ def test_bin_f32_agrees_with_fp64():
     depth = b["depth_key"][ok].view(np.float32).astype(np.float64)
     np.testing.assert_allclose(depth, g["depth"][ok], rtol=1e-6)
     r64 = np.ceil(3.33 * np.sqrt(g["lambda_max"][ok]))
-    unflagged = b["flags"][ok] == 0
+    unflagged = (b["flags"][ok] & 4) == 0
     assert np.array_equal(b["radius"][ok][unflagged], r64[unflagged].astype(np.int32))
     rect = b["rect"][ok]
     assert np.array_equal(b["tiles_touched"][ok], ((rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)))
