@@ -115,7 +115,7 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                 const float p2 = fmaf(fmaf(h.x, dy, bx), dy, axx);
                 const float q = p2 + h.y;
                 if (p2 <= 0.0f && q >= kLog2AlphaMin) {
-                    const float raw = exp2f(q);
+                    const float raw = alpha_exp2(q);
                     const float alpha = fminf(kAlphaMax, raw);
                     const float Ti = T / (1.0f - alpha);
                     const float4 c = s_c[k];

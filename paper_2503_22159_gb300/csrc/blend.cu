@@ -34,18 +34,15 @@ struct PixelState {
     bool done;
 };
 
-// One (pixel, Gaussian) step; returns true if the pixel blended it.
-__device__ __forceinline__ bool blend_step(PixelState &px, float p, float L, const float4 *col, uint32_t pos) {
-    if (p > 0.0f) return false;
-    const float q = p + L;
-    if (q < kLog2AlphaMin) return false;
-    const float alpha = fminf(kAlphaMax, exp2f(q));
+// Composite one Gaussian (already known to pass p <= 0 and q >= log2(1/255))
+// into a pixel: stop before blending once T (1 - alpha) < 1e-4.
+__device__ __forceinline__ bool composite(PixelState &px, float q, const float4 &c, uint32_t pos) {
+    const float alpha = fminf(kAlphaMax, alpha_exp2(q));
     const float test = px.T * (1.0f - alpha);
     if (test < kTMin) {
         px.done = true;
         return false;
     }
-    const float4 c = *col;
     const float w = alpha * px.T;
     px.c0 = fmaf(w, c.x, px.c0);
     px.c1 = fmaf(w, c.y, px.c1);
@@ -128,24 +125,31 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
             const int nb = (int)min((uint32_t)BATCH, rg.y - start);
             if (!(a.done && b.done)) {
                 for (int k = 0; k < nb; k++) {
+                    // both pixels' exponents, branch free; most pairs stop here
                     const float4 g = s_g[k];
                     const float2 h = s_h[k];
                     const float dx = g.x - pxf;
                     const float axx = g.z * dx * dx, bx = g.w * dx;
-                    const uint32_t pos = start - rg.x + (uint32_t)k + 1u;
-                    if (!a.done) {
-                        const float dy = g.y - pyf0;
-                        const float p = fmaf(fmaf(h.x, dy, bx), dy, axx);
-                        const bool bl = blend_step(a, p, h.y, &s_c[k], pos);
-                        if (COUNT) { n_eval++; n_blend += bl; }
+                    const float dya = g.y - pyf0, dyb = g.y - pyf1;
+                    const float pa = fmaf(fmaf(h.x, dya, bx), dya, axx);
+                    const float pb = fmaf(fmaf(h.x, dyb, bx), dyb, axx);
+                    const float qa = pa + h.y, qb = pb + h.y;
+                    const bool ea = !a.done && pa <= 0.0f && qa >= kLog2AlphaMin;
+                    const bool eb = !b.done && pb <= 0.0f && qb >= kLog2AlphaMin;
+                    if (COUNT) n_eval += (uint32_t)!a.done + (uint32_t)!b.done;
+                    if (ea || eb) {
+                        const float4 c = s_c[k];
+                        const uint32_t pos = start - rg.x + (uint32_t)k + 1u;
+                        if (ea) {
+                            const bool bl = composite(a, qa, c, pos);
+                            if (COUNT) n_blend += bl;
+                        }
+                        if (eb) {
+                            const bool bl = composite(b, qb, c, pos);
+                            if (COUNT) n_blend += bl;
+                        }
+                        if (a.done && b.done) break;
                     }
-                    if (!b.done) {
-                        const float dy = g.y - pyf1;
-                        const float p = fmaf(fmaf(h.x, dy, bx), dy, axx);
-                        const bool bl = blend_step(b, p, h.y, &s_c[k], pos);
-                        if (COUNT) { n_eval++; n_blend += bl; }
-                    }
-                    if (a.done && b.done) break;
                 }
             }
         }

@@ -74,7 +74,7 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
 // rectangle, adds its rectangle to the view's difference grid, and counts it in
 // the shared depth-digit histogram.
 template <int DEG>
-__device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *hist, uint32_t &nvis) {
+__device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *hist, uint32_t &nvis, int *sgrid) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const CamArgs &c = vw.cam;
     const float t = vw.t;
@@ -165,10 +165,11 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
             tiles = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
             // per-tile pair counts as a 2D difference grid ((tiles_x+1) x (tiles_y+1))
             const int gw = c.tiles_x + 1;
-            atomicAdd(vw.grid + y0 * gw + x0, 1);
-            atomicAdd(vw.grid + y0 * gw + x1 + 1, -1);
-            atomicAdd(vw.grid + (y1 + 1) * gw + x0, -1);
-            atomicAdd(vw.grid + (y1 + 1) * gw + x1 + 1, 1);
+            int *g = sgrid ? sgrid : vw.grid;   // shared-memory copy when the grid is small
+            atomicAdd(g + y0 * gw + x0, 1);
+            atomicAdd(g + y0 * gw + x1 + 1, -1);
+            atomicAdd(g + (y1 + 1) * gw + x0, -1);
+            atomicAdd(g + (y1 + 1) * gw + x1 + 1, 1);
             key = __float_as_uint(Z);
             nvis++;
             // ---- conic (rendering only; ordinary arithmetic from here on)
@@ -219,8 +220,13 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
     }
 }
 
-// Flush a CTA's depth-digit histogram and visible count into view v.
-__device__ __forceinline__ void flush_view(const View &v, uint32_t *hist, uint32_t &nvis) {
+// Cells of the view's difference grid, and whether a CTA keeps its share of
+// the grid in shared memory (small grids, where the corner atomics of all
+// Gaussians would otherwise pile onto few addresses).
+__device__ __forceinline__ int grid_cells(const View &v) { return (v.cam.tiles_x + 1) * (v.cam.tiles_y + 1); }
+
+// Flush a CTA's depth-digit histogram, visible count and shared grid into view v.
+__device__ __forceinline__ void flush_view(const View &v, uint32_t *hist, uint32_t &nvis, int *sgrid) {
     __syncthreads();
     const uint32_t w = __reduce_add_sync(0xFFFFFFFFu, nvis);
     if ((threadIdx.x & 31) == 0 && w) atomicAdd(v.ctl + kCtlNumVisible, w);
@@ -229,13 +235,22 @@ __device__ __forceinline__ void flush_view(const View &v, uint32_t *hist, uint32
         if (hist[i]) atomicAdd(v.ctl + kCtlDepthHist + i, hist[i]);
         hist[i] = 0;
     }
+    if (sgrid) {
+        const int cells = grid_cells(v);
+        for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+            if (sgrid[i]) atomicAdd(v.grid + i, sgrid[i]);
+            sgrid[i] = 0;
+        }
+    }
     __syncthreads();
 }
 
 // Persistent: CTAs take 256-Gaussian chunks of the views' flattened Gaussians.
-__global__ void __launch_bounds__(256) preprocess_kernel(const char *__restrict__ ba) {
+__global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restrict__ ba, int smem_cells) {
     __shared__ uint32_t hist[4 * kRadix];
     __shared__ int32_t s_chunk;
+    extern __shared__ int s_grid[];
+    for (int i = threadIdx.x; i < smem_cells; i += blockDim.x) s_grid[i] = 0;
     const uint32_t *bw = reinterpret_cast<const uint32_t *>(ba);
     const int nviews = (int)bw[kBaNViews];
     const int total = (int)bw[kBaTotalChunks];
@@ -254,20 +269,27 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const char *__restrict_
             if (view_of(ba, u).chunk_base <= chunk) vi = u;
         const View &v = view_of(ba, vi);
         if (vi != cur) {
-            if (cur >= 0) flush_view(view_of(ba, cur), hist, nvis);
+            if (cur >= 0) {
+                const View &pv = view_of(ba, cur);
+                flush_view(pv, hist, nvis, grid_cells(pv) <= smem_cells ? s_grid : nullptr);
+            }
             cur = vi;
         }
+        int *sg = grid_cells(v) <= smem_cells ? s_grid : nullptr;
         const int i = (chunk - v.chunk_base) * kPreChunk + (int)threadIdx.x;
         if (i < v.n) {
             switch (v.sh_degree) {
-                case 0: preprocess_one<0>(v, i, hist, nvis); break;
-                case 1: preprocess_one<1>(v, i, hist, nvis); break;
-                case 2: preprocess_one<2>(v, i, hist, nvis); break;
-                default: preprocess_one<3>(v, i, hist, nvis); break;
+                case 0: preprocess_one<0>(v, i, hist, nvis, sg); break;
+                case 1: preprocess_one<1>(v, i, hist, nvis, sg); break;
+                case 2: preprocess_one<2>(v, i, hist, nvis, sg); break;
+                default: preprocess_one<3>(v, i, hist, nvis, sg); break;
             }
         }
     }
-    if (cur >= 0) flush_view(view_of(ba, cur), hist, nvis);
+    if (cur >= 0) {
+        const View &pv = view_of(ba, cur);
+        flush_view(pv, hist, nvis, grid_cells(pv) <= smem_cells ? s_grid : nullptr);
+    }
 }
 
 // First kernel of a frame or batch: installs the descriptor table (from the
@@ -326,8 +348,10 @@ cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batc
 
 cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms) {
     if (args.total_chunks == 0) return cudaSuccess;
-    // persistent grid: 8 resident CTAs of 256 threads per SM
-    preprocess_kernel<<<num_sms * 8, 256, 0, st>>>(batch_area);
+    // persistent grid: 8 resident CTAs of 256 threads per SM; grids of up to
+    // 6144 cells (e.g. 1352x1014 at 32-px tiles) are aggregated in shared memory
+    constexpr int kSmemCells = 6144;
+    preprocess_kernel<<<num_sms * 8, 256, kSmemCells * sizeof(int), st>>>(batch_area, kSmemCells);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ constexpr unsigned long long kFlagAgg64 = 1ull << 62;
 constexpr unsigned long long kFlagInc64 = 2ull << 62;
 constexpr unsigned long long kFlagMask64 = 3ull << 62;
 constexpr unsigned long long kValMask64 = (1ull << 62) - 1ull;
+constexpr int kLookAhead = 8;   // predecessor entries read per look-back round trip
 
 // Exclusive scan of one value per thread over a 256-thread block; returns the
 // exclusive prefix and writes the block total to *total.
@@ -185,19 +186,34 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
         s_local_start[d] = lstart;
         uint32_t excl = 0;
         if (part > 0) {
+            // decoupled look-back, reading up to kLookAhead predecessors per round trip:
+            // sum aggregates back to the first inclusive prefix; a not-yet-published
+            // entry is polled again (bounded)
             int64_t j = (int64_t)part - 1;
             uint32_t spins = 0;
             while (j >= 0) {
-                const uint32_t val = ld_volatile_u32(lookback + (size_t)j * kRadix + d);
-                const uint32_t flag = val & kFlagMask;
-                if (flag == 0u) {
+                uint32_t val[kLookAhead];
+#pragma unroll
+                for (int a = 0; a < kLookAhead; a++)
+                    val[a] = j - a >= 0 ? ld_volatile_u32(lookback + (size_t)(j - a) * kRadix + d) : kFlagInc;
+                bool done = false, stalled = false;
+                int consumed = 0;   // aggregates summed this round (entries j, j-1, ...)
+#pragma unroll
+                for (int a = 0; a < kLookAhead; a++) {
+                    if (done || stalled) continue;
+                    const uint32_t flag = val[a] & kFlagMask;
+                    if (flag == 0u) { stalled = true; continue; }
+                    if (j - a < 0) { done = true; continue; }
+                    excl += val[a] & kValMask;
+                    if (flag == kFlagInc) done = true;
+                    else ++consumed;
+                }
+                if (done) break;
+                j -= consumed;
+                if (stalled) {
                     if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); break; }
                     if (spins > 32) __nanosleep(64);
-                    continue;
                 }
-                excl += val & kValMask;
-                if (flag == kFlagInc) break;
-                --j;
             }
             st_volatile_u32(lb + d, kFlagInc | ((excl + bcount) & kValMask));
         }
@@ -228,13 +244,22 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
 // Per-tile pair counts from the view's 2D difference grid; ranges; digit
 // histograms of the tile passes; the total K and the capacity check.  One CTA
 // per view.
-__global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba) {
+__global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, int smem_cells) {
     __shared__ unsigned long long s_warp[32];
     __shared__ uint32_t s_hist[3 * kRadix];
+    extern __shared__ int s_grid[];
     const uint32_t *bw = reinterpret_cast<const uint32_t *>(ba);
     if ((int)blockIdx.x >= (int)bw[kBaNViews]) return;
     const View &v = view_of(ba, blockIdx.x);
     int *grid = v.grid;
+    {   // integrate in shared memory when the view's grid fits (one global read and write)
+        const int cells = (v.cam.tiles_x + 1) * (v.cam.tiles_y + 1);
+        if (cells <= smem_cells) {
+            for (int i = threadIdx.x; i < cells; i += blockDim.x) s_grid[i] = v.grid[i];
+            __syncthreads();
+            grid = s_grid;
+        }
+    }
     const int tiles_x = v.cam.tiles_x, tiles_y = v.cam.tiles_y;
     uint2 *ranges = v.ranges;
     uint32_t *ctl = v.ctl;
@@ -341,30 +366,44 @@ __global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba
         s_cnt[tid] = c;
         s_id[tid] = id;
         s_rect[tid] = r;
-        if (tid == 0) {
+        if (warp == 0) {
+            // warp-wide decoupled look-back: lane l reads predecessor j - l; the warp sums
+            // the aggregates of the lanes before the first inclusive prefix (bounded polling)
             unsigned long long excl = 0;
             unsigned long long *lb = v.lb_dup + part;
-            if (part == 0) {
-                st_volatile_u64(lb, kFlagInc64 | (unsigned long long)ptotal);
-            } else {
-                st_volatile_u64(lb, kFlagAgg64 | (unsigned long long)ptotal);
+            if (lane == 0) st_volatile_u64(lb, (part == 0 ? kFlagInc64 : kFlagAgg64) | (unsigned long long)ptotal);
+            if (part > 0) {
                 int64_t j = (int64_t)part - 1;
                 uint32_t spins = 0;
                 while (j >= 0) {
-                    const unsigned long long val = ld_volatile_u64(v.lb_dup + j);
+                    const int64_t jj = j - lane;
+                    const unsigned long long val = jj >= 0 ? ld_volatile_u64(v.lb_dup + jj) : kFlagInc64;
                     const unsigned long long flag = val & kFlagMask64;
-                    if (flag == 0ull) {
-                        if (++spins > kSpinLimit) { atomicOr(v.ctl + kCtlStatus, kStatusTimeout); break; }
+                    const uint32_t inc = __ballot_sync(0xFFFFFFFFu, flag == kFlagInc64);
+                    const uint32_t empty = __ballot_sync(0xFFFFFFFFu, flag == 0ull);
+                    const uint32_t stop = inc | empty;
+                    const int first = stop ? __ffs(stop) - 1 : 32;   // lanes before it hold aggregates
+                    unsigned long long take = 0;
+                    if (lane < first || (lane == first && (inc >> lane) & 1u)) take = val & kValMask64;
+                    if (jj < 0) take = 0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) take += __shfl_xor_sync(0xFFFFFFFFu, take, o);
+                    excl += take;
+                    if (first < 32 && ((inc >> first) & 1u)) break;     // reached an inclusive prefix
+                    if (first < 32) {                                   // an entry not yet published
+                        j -= first;
+                        if (++spins > kSpinLimit) {
+                            if (lane == 0) atomicOr(v.ctl + kCtlStatus, kStatusTimeout);
+                            break;
+                        }
                         if (spins > 32) __nanosleep(64);
-                        continue;
+                    } else {
+                        j -= 32;
                     }
-                    excl += val & kValMask64;
-                    if (flag == kFlagInc64) break;
-                    --j;
                 }
-                st_volatile_u64(lb, kFlagInc64 | ((excl + ptotal) & kValMask64));
+                if (lane == 0) st_volatile_u64(lb, kFlagInc64 | ((excl + ptotal) & kValMask64));
             }
-            s_excl = excl;
+            if (lane == 0) s_excl = excl;
         }
         __syncthreads();
         // ---- emission: warp w writes the pairs of Gaussians w*32 .. w*32+31, one run each
@@ -423,7 +462,15 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
     // ---- 0. per-tile counts, ranges, tile digit histograms (always: ranges are written for every tile)
     // fixed grid (blocks beyond the table's view count return at once), so that a
     // captured launch serves batches of any size
-    tilecount_kernel<<<kMaxViews, 1024, 0, st>>>(batch_area);
+    static int smem_cells = -1;
+    if (smem_cells < 0) {
+        const int bytes = 160 * 1024;   // grids up to 40960 cells (e.g. 2704x2028 at 16-px tiles)
+        smem_cells = cudaFuncSetAttribute(tilecount_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+                             cudaSuccess
+                         ? bytes / 4
+                         : 0;
+    }
+    tilecount_kernel<<<kMaxViews, 1024, (size_t)smem_cells * 4, st>>>(batch_area, smem_cells);
     if (args.max_n == 0) return cudaGetLastError();
     // ---- 1. depth sort (4 passes), ids in dvals[0]
     for (int p = 0; p < 4; p++) {
