@@ -163,11 +163,13 @@ int d4dgs_sort(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void
 int d4dgs_blend(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
                 float *out_rgb, d4dgs_stream_t stream);
 
-/* Profiling variant of d4dgs_blend: the same compositing, plus the totals of
- * (pixel, Gaussian) pairs evaluated (counts[0]) and blended (counts[1]) over
- * the frame, accumulated into `counts` (2 x uint64 DEVICE memory,
- * caller-owned, zeroed by the call).  Slower than d4dgs_blend; used to turn
- * a blend time into an FP32 throughput. */
+/* Profiling variant of d4dgs_blend: the same compositing, plus three totals
+ * over the frame, accumulated into `counts` (3 x uint64 DEVICE memory,
+ * caller-owned, zeroed by the call): counts[0] (pixel, Gaussian) pairs the
+ * kernel evaluated, counts[1] pairs blended, counts[2] the work of the plain
+ * tile algorithm (Sec. III-B-2), the sum over tiles of the tile's in-image
+ * pixels times the list entries walked until its last pixel stopped.  Slower
+ * than d4dgs_blend; used to turn a blend time into an FP32 throughput. */
 int d4dgs_blend_profile(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
                         float *out_rgb, uint64_t *counts, d4dgs_stream_t stream);
 

@@ -97,7 +97,7 @@ def lib():
                                         ctypes.c_int, ctypes.POINTER(_G2D)]
         _lib.orc_render_pixels.argtypes = [ctypes.POINTER(_G2D), ctypes.c_int, ctypes.POINTER(_Camera),
                                            c_double_p, ctypes.c_int64, c_int32_p, c_int32_p, ctypes.c_double,
-                                           c_double_p, c_double_p, c_int32_p, c_double_p]
+                                           c_double_p, c_double_p, c_int32_p, c_double_p, c_double_p]
         _lib.orc_bin_f32.argtypes = [ctypes.POINTER(_SceneF32), ctypes.POINTER(_CameraF32), ctypes.c_float,
                                      ctypes.c_int32, c_uint32_p, c_int32_p, c_int32_p, c_uint32_p, c_int32_p,
                                      c_float_p]
@@ -197,7 +197,7 @@ def render_g2d(g: dict, cam, pixels=None, bg=(0.0, 0.0, 0.0), eps_px=None) -> di
     """Per-pixel brute-force compositing of precomputed FP64 2D Gaussians.
 
     ``pixels`` is None (whole image, row-major) or an (M, 2) int array of (x, y).
-    Returns rgb (H,W,3) or (M,3), T, ncontrib and slack (see oracle.c)."""
+    Returns rgb (H,W,3) or (M,3), T, ncontrib, slack and Tw (see oracle.c)."""
     n = len(g["u"])
     fields = ("u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max")
     gg = {k: _d(g[k]) for k in fields}
@@ -219,14 +219,15 @@ def render_g2d(g: dict, cam, pixels=None, bg=(0.0, 0.0, 0.0), eps_px=None) -> di
     T = np.zeros(shape)
     nc = np.zeros(shape, np.int32)
     slack = np.zeros(shape)
+    Tw = np.zeros(shape)
     bgv = _d(np.asarray(bg, np.float64))
     eps = default_eps_px(cam) if eps_px is None else float(eps_px)
     lib().orc_render_pixels(ctypes.byref(s), n, ctypes.byref(c), _p(bgv, ctypes.c_double), m,
                             _p(px, ctypes.c_int32), _p(py, ctypes.c_int32), eps,
                             _p(rgb, ctypes.c_double), _p(T, ctypes.c_double), _p(nc, ctypes.c_int32),
-                            _p(slack, ctypes.c_double))
+                            _p(slack, ctypes.c_double), _p(Tw, ctypes.c_double))
     del keep
-    return dict(rgb=rgb, T=T, ncontrib=nc, slack=slack)
+    return dict(rgb=rgb, T=T, ncontrib=nc, slack=slack, Tw=Tw)
 
 
 def render(scene, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0), temporal_cull: bool = True,

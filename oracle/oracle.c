@@ -263,8 +263,10 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, double t, int te
  * per-pixel slack: an upper bound on how far an FP32 evaluation of the same
  * definition may legitimately move the colour because a discrete decision
  * (alpha vs 1/255, T(1-alpha) vs 1e-4, p vs 0, the order of two nearly equal
- * depths) sits within FP32 reach of its threshold.  eps_px is the absolute
- * error budget of an FP32 projected mean in pixels.
+ * depths) sits within FP32 reach of its threshold; and Tw, the accumulated
+ * relative error budget of an FP32 T (the sum over blended Gaussians of the
+ * alpha budget times alpha / (1 - alpha), plus 1e-6 per blend).  eps_px is
+ * the absolute error budget of an FP32 projected mean in pixels.
  * ------------------------------------------------------------------------- */
 typedef struct { double depth; int32_t idx; double alpha; double w; int near_alpha; } orc_cand;
 
@@ -277,7 +279,8 @@ static int cand_cmp(const void *pa, const void *pb) {
 
 void orc_render_pixels(const orc_g2d *g, int n, const orc_camera *cam, const double bg[3],
                        int64_t npix, const int32_t *px, const int32_t *py, double eps_px,
-                       double *out_rgb, double *out_T, int32_t *out_ncontrib, double *out_slack) {
+                       double *out_rgb, double *out_T, int32_t *out_ncontrib, double *out_slack,
+                       double *out_Tw) {
     /* compact list of drawn Gaussians */
     int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
     int nd = 0;
@@ -357,6 +360,7 @@ void orc_render_pixels(const orc_g2d *g, int n, const orc_camera *cam, const dou
             if (out_T) out_T[q] = T;
             if (out_ncontrib) out_ncontrib[q] = ncontrib;
             if (out_slack) out_slack[q] = slack;
+            if (out_Tw) out_Tw[q] = wT;
         }
         free(cand);
     }

@@ -120,8 +120,10 @@ def d4dgs_blend(n: int, cam, cfg, ws: torch.Tensor, out: torch.Tensor, stream=No
 
 
 def d4dgs_blend_profile(n: int, cam, cfg, ws: torch.Tensor, out: torch.Tensor, counts: torch.Tensor, stream=None):
-    """Instrumented blend: also totals the evaluated and blended (pixel, Gaussian) pairs into
-    ``counts`` (a 2-element int64 CUDA tensor)."""
+    """Instrumented blend: also totals the evaluated and blended (pixel, Gaussian) pairs and the
+    plain tile algorithm's pair count into ``counts`` (a 3-element int64 CUDA tensor)."""
+    if counts.numel() < 3 or counts.dtype != torch.int64 or not counts.is_cuda:
+        raise ValueError("counts must be a CUDA int64 tensor with at least 3 elements")
     p, nb = _ws(ws)
     _abi.check(_abi.load().d4dgs_blend_profile(int(n), ctypes.byref(camera_struct(cam)), ctypes.byref(cfg), p, nb,
                                                ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(counts.data_ptr()),

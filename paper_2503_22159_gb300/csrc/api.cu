@@ -315,7 +315,7 @@ int d4dgs_blend_profile(int32_t n, const d4dgs_camera *cam, const d4dgs_config *
     char *ba = at<char>(ws, L.batch);
     // the blend's work counter is reset so that the same frame can be blended again
     if (cudaMemsetAsync(ba + 4 * kBaBlend, 0, 4, st) != cudaSuccess) return D4DGS_ERR_CUDA;
-    if (cudaMemsetAsync(counts, 0, 2 * sizeof(uint64_t), st) != cudaSuccess) return D4DGS_ERR_CUDA;
+    if (cudaMemsetAsync(counts, 0, 3 * sizeof(uint64_t), st) != cudaSuccess) return D4DGS_ERR_CUDA;
     return cuda_status(launch_blend(b, ba, st, num_sms_current(), out_rgb, reinterpret_cast<unsigned long long *>(counts)));
 }
 

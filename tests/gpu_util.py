@@ -91,3 +91,26 @@ def compare_image(got, ref, where=""):
         assert strict.max() <= MAX_ABS, f"{where}: unflagged max err {strict.max():.3g}"
     assert err.mean() <= MEAN_ABS, f"{where}: mean abs err {err.mean():.3g}"
     return dict(max=float(err.max()), mean=float(err.mean()), flagged=int(flagged.sum()))
+
+
+def gpu_final_T(r, cam):
+    """Per-pixel transmittance the blend stored for the backward (H x W)."""
+    return r.view("final_T", torch.float32, cam.width * cam.height, cam).cpu().numpy().reshape(cam.height, cam.width)
+
+
+def compare_T(got_T, ref, where=""):
+    """Final transmittance within the oracle's accumulated FP32 budget Tw
+    (twice it, plus 1e-6 relative) on pixels without a near-threshold
+    decision.  A dropped or extra alpha >= 1/255 term moves T by at least
+    0.39% relative, so every pixel whose bound is tighter than that also
+    checks that no such term was lost; require most pixels to be of that kind."""
+    got_T = np.asarray(got_T, np.float64)
+    T = ref["T"]
+    tol = (2.0 * ref["Tw"] + 1e-6) * T + 1e-9
+    strict = ref["slack"] == 0
+    err = np.abs(got_T - T)
+    bad = strict & (err > tol)
+    assert not bad.any(), f"{where}: {int(bad.sum())} pixels with T beyond budget, worst rel {float((err / np.maximum(T, 1e-30))[bad].max()):.3g}"
+    sharp = strict & (tol < (1.0 / 255.0) * T)
+    assert sharp.sum() >= 0.2 * T.size, f"{where}: only {int(sharp.sum())} of {T.size} pixels can see a dropped term"
+    return dict(strict=int(strict.sum()), sharp=int(sharp.sum()))

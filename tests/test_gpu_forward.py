@@ -103,21 +103,23 @@ def test_lists_bit_exact_unpacked_pairs():
 def test_image_parity_tiny():
     w = synth.tiny_workload()
     cam, t = w.frames[0]
-    _, _, img = gu.render(w.scene, cam, t)
+    r, _, img = gu.render(w.scene, cam, t)
     ref = oracle.render(w.scene, cam, t)
     s = gu.compare_image(img.cpu().numpy(), ref, "tiny")
     assert s["flagged"] < 0.02 * cam.width * cam.height
+    gu.compare_T(gu.gpu_final_T(r, cam), ref, "tiny")
 
 
 def test_image_parity_medium_sampled():
     scene, cam, t = medium()
-    _, _, img = gu.render(scene, cam, t)
+    r, _, img = gu.render(scene, cam, t)
     rng = np.random.default_rng(0)
     pix = np.column_stack([rng.integers(0, cam.width, 2500), rng.integers(0, cam.height, 2500)])
     pix = np.concatenate([pix, np.column_stack([np.arange(cam.width), np.full(cam.width, cam.height - 1)])])
     ref = oracle.render(scene, cam, t, pixels=pix)
     got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
     gu.compare_image(got, ref, "medium")
+    gu.compare_T(gu.gpu_final_T(r, cam)[pix[:, 1], pix[:, 0]], ref, "medium")
 
 
 @pytest.mark.parametrize("tile,batch", [(8, 64), (8, 256), (16, 64), (16, 128), (32, 128), (32, 256)])

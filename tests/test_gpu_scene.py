@@ -72,6 +72,7 @@ def test_scene_image_sampled(scene_w, gpu_renderer, k):
     ref = oracle.render(scene_w.scene, cam, t, pixels=pix)
     got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
     s = gu.compare_image(got, ref, f"scene frame {k}")
+    gu.compare_T(gu.gpu_final_T(r, cam)[pix[:, 1], pix[:, 0]], ref, f"scene frame {k}")
     assert float(np.abs(ref["rgb"]).max()) > 0.1
     # the dense scene puts a near-threshold candidate on many pixels; the strict
     # 2e-3 check must still cover a good share of them
