@@ -7,22 +7,28 @@
 //   stop (before blending) once T (1 - alpha) < 1e-4
 //   C += alpha T c;  T *= 1 - alpha;       out = C + T bg
 //
-// One CTA per tile; each warp owns an 8 x 8 pixel block of it and each thread
-// two vertically adjacent pixels of that block, so dx and its products are
-// shared.  The CTA walks the tile's list in batches: each batch of Gaussians is
-// gathered once into shared memory (already scaled to base-2 exponent form)
-// together with a bit mask of the 8 x 8 blocks its alpha >= 1/255 ellipse
-// reaches, and each warp visits only the Gaussians whose mask holds its bit
-// (a ballot per 32 Gaussians, then the set bits in ascending order).  Skipped
-// (block, Gaussian) pairs have alpha < 1/255 at every pixel of the block, so
-// the image is the one the full walk gives.  A warp stops when its 64 pixels
-// have stopped, a CTA when all of its pixels have.
+// One CTA per tile.  Each thread owns a column of PX pixels (4; 2 at 8-px
+// tiles), so dx and its products are shared, and works on them as pixel
+// pairs with Blackwell's packed FP32x2 add/mul/fma (one instruction for both
+// pixels of a pair, each lane rounded as the scalar operation).  Each warp
+// owns an 8 x 4PX block of the tile.  The CTA walks the tile's list in
+// batches: each batch of Gaussians is gathered once into shared memory
+// (already in base-2 exponent form, every scalar stored twice so that a
+// 128-bit broadcast load fills register pairs) together with a bit mask of
+// the blocks its alpha >= 1/255 ellipse reaches, and each warp visits only
+// the Gaussians whose mask holds its bit (a ballot per 32 Gaussians, then the
+// set bits in ascending order).  Skipped (block, Gaussian) pairs have
+// alpha < 1/255 at every pixel of the block, so the image is the one the full
+// walk gives.  When any pixel of a thread passes, all of its pixels take the
+// compositing step, with alpha = 0 for the ones that do not (T and C then
+// stay as they are).  A warp stops when all of its pixels have stopped, a CTA
+// when all of its warps have.
 //
 // Exponent form: with A = -a/2 log2(e), B = -b log2(e), C = -c/2 log2(e) and
 // L = log2(o_hat), q = A dx^2 + B dx dy + C dy^2 + L and alpha = min(0.99, 2^q),
-// so the alpha >= 1/255 test is q >= log2(1/255), taken before the exp: most
-// pairs are rejected with five FMAs and two compares.  No tensor cores:
-// nothing here is a dense contraction; the bound is FP32 issue.
+// so the alpha >= 1/255 test is q >= log2(1/255), taken before the exp.  No
+// tensor cores: nothing here is a dense contraction; the bound is instruction
+// issue.
 #include "blend_mask.cuh"
 #include "d4dgs_internal.cuh"
 
@@ -33,29 +39,50 @@ namespace {
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLog2AlphaMin = -7.9943534368588578f;   // log2(1/255)
 
-struct PixelState {
-    float T, c0, c1, c2;
-    uint32_t last;
-    bool done;
-};
-
-// Composite one Gaussian (already known to pass p <= 0 and q >= log2(1/255))
-// into a pixel: stop before blending once T (1 - alpha) < 1e-4.
-__device__ __forceinline__ bool composite(PixelState &px, float q, const float4 &c, uint32_t pos) {
-    const float alpha = fminf(kAlphaMax, alpha_exp2(q));
-    const float test = px.T * (1.0f - alpha);
-    if (test < kTMin) {
-        px.done = true;
-        return false;
-    }
-    const float w = alpha * px.T;
-    px.c0 = fmaf(w, c.x, px.c0);
-    px.c1 = fmaf(w, c.y, px.c1);
-    px.c2 = fmaf(w, c.z, px.c2);
-    px.T = test;
-    px.last = pos;
-    return true;
+// Packed FP32x2 arithmetic (sm_100 family): both lanes rounded to nearest,
+// no flush to zero, exactly as the scalar operations.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
 }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+template <int TS>
+struct BlendShape {
+    static constexpr int PX = TS == 8 ? 2 : 4;   // pixels per thread (a column)
+    static constexpr int NP = PX / 2;            // pixel pairs
+    static constexpr int BH = 4 * PX;            // warp block: 8 wide, BH tall
+    static constexpr int NT = TS * TS / PX;      // threads per CTA
+    static constexpr int BX = TS / 8, BY = TS / BH;
+    static_assert(NT / 32 == BX * BY, "one warp per block");
+};
 
 // COUNT: instrumented variant for profiling (not used on the render path),
 // which also totals into counts[0..2]: (pixel, Gaussian) pairs the warps
@@ -65,14 +92,15 @@ __device__ __forceinline__ bool composite(PixelState &px, float q, const float4 
 // PERSIST: CTAs take tiles from an atomic counter until all are done (fixed
 // grid, for batched and graph-captured launches); otherwise one CTA per tile.
 template <int TS, int BATCH, bool COUNT, bool PERSIST>
-__global__ void __launch_bounds__(TS *TS / 2, TS == 8 ? 16 : (TS == 16 ? 8 : 2))
+__global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 24 : (TS == 16 ? 10 : 3))
 blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts) {
-    constexpr int NT = TS * TS / 2;
-    constexpr int BX = TS / 8;       // 8 x 8 blocks per tile row; warp w owns block (w % BX, w / BX)
-    static_assert(NT / 32 == BX * BX, "one warp per 8 x 8 block");
-    __shared__ float4 s_g[BATCH];    // u, v, A, B
-    __shared__ float2 s_h[BATCH];    // C, L
-    __shared__ float4 s_c[BATCH];    // r, g, b
+    using S = BlendShape<TS>;
+    constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
+    __shared__ float4 s_ua[BATCH];   // u, u, A, A
+    __shared__ float4 s_bc[BATCH];   // B, B, C, C
+    __shared__ float4 s_vl[BATCH];   // v, v, L, L
+    __shared__ float4 s_rg[BATCH];   // r, r, g, g
+    __shared__ float2 s_bl[BATCH];   // b, b
     __shared__ uint32_t s_m[BATCH];  // blocks the Gaussian's alpha >= 1/255 ellipse reaches
     __shared__ int32_t s_item;
     __shared__ uint32_t s_stop;
@@ -82,6 +110,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
     const int lane = (int)(threadIdx.x & 31u), warp = (int)(threadIdx.x >> 5);
     uint32_t n_eval = 0, n_blend = 0;
     unsigned long long n_work = 0;
+    const float2 one2 = make_float2(1.0f, 1.0f);
 
     for (int pass = 0;; pass++) {
         int item;
@@ -109,20 +138,34 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
 
         const int tx = tile % tiles_x, ty = tile / tiles_x;
         const int x0 = tx * TS, y0 = ty * TS;
-        const int lx = 8 * (warp % BX) + (lane & 7), ly = 8 * (warp / BX) + 2 * (lane >> 3);
-        const int px = x0 + lx, py0 = y0 + ly, py1 = py0 + 1;
-        const bool in0 = px < width && py0 < height, in1 = px < width && py1 < height;
-        const float pxf = (float)px + 0.5f, pyf0 = (float)py0 + 0.5f, pyf1 = (float)py1 + 0.5f;
+        const int px = x0 + 8 * (warp % BX) + (lane & 7);
+        const int py = y0 + BH * (warp / BX) + PX * (lane >> 3);
+        const float pxf = (float)px + 0.5f;
+        const float2 pxf2 = make_float2(pxf, pxf);
+        float2 pyf[NP], T[NP], c0[NP], c1[NP], c2[NP];
+        uint32_t last[PX], stop[PX];
+        bool done[PX];
         uint2 rg = v.ranges[tile];
         rg.y = min(rg.y, cap);   // ranges are written clamped; this keeps every read in bounds regardless
         rg.x = min(rg.x, rg.y);
-
-        PixelState a{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in0};
-        PixelState b{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in1};
-        uint32_t stop_a = rg.y - rg.x, stop_b = stop_a;   // COUNT only
+#pragma unroll
+        for (int j = 0; j < NP; j++) {
+            pyf[j] = make_float2((float)(py + 2 * j) + 0.5f, (float)(py + 2 * j + 1) + 0.5f);
+            T[j] = one2;
+            c0[j] = c1[j] = c2[j] = make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int i = 0; i < PX; i++) {
+            last[i] = 0u;
+            stop[i] = rg.y - rg.x;   // COUNT only
+            done[i] = !(px < width && py + i < height);
+        }
 
         for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-            if (__syncthreads_count(!(a.done && b.done)) == 0) break;
+            bool live = false;
+#pragma unroll
+            for (int i = 0; i < PX; i++) live |= !done[i];
+            if (__syncthreads_count(live) == 0) break;
             for (int k = threadIdx.x; k < BATCH; k += NT) {
                 const uint32_t j = start + (uint32_t)k;
                 if (j < rg.y) {
@@ -132,54 +175,80 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     const float4 r1 = rec[3 * (size_t)id + 1];
                     const float4 r2 = rec[3 * (size_t)id + 2];
                     const float A = -0.5f * kLog2e * r0.z, B = -kLog2e * r0.w, C = -0.5f * kLog2e * r1.x;
-                    s_g[k] = make_float4(r0.x, r0.y, A, B);
-                    s_h[k] = make_float2(C, r2.w);
-                    s_c[k] = r2;
-                    s_m[k] = d4dgs::block_mask<TS>(r0.x, r0.y, A, B, C, r2.w, x0, y0);
+                    s_ua[k] = make_float4(r0.x, r0.x, A, A);
+                    s_bc[k] = make_float4(B, B, C, C);
+                    s_vl[k] = make_float4(r0.y, r0.y, r2.w, r2.w);
+                    s_rg[k] = make_float4(r2.x, r2.x, r2.y, r2.y);
+                    s_bl[k] = make_float2(r2.z, r2.z);
+                    s_m[k] = d4dgs::block_mask<TS, BH>(r0.x, r0.y, A, B, C, r2.w, x0, y0);
                 }
             }
             __syncthreads();
             const int nb = (int)min((uint32_t)BATCH, rg.y - start);
             // warp-uniform from here to the end of the batch
-            if (__any_sync(0xFFFFFFFFu, !(a.done && b.done))) {
+            if (__any_sync(0xFFFFFFFFu, live)) {
                 for (int k0 = 0; k0 < nb; k0 += 32) {
                     const int kl = k0 + lane;
                     uint32_t bits = __ballot_sync(0xFFFFFFFFu, kl < nb && ((s_m[kl] >> warp) & 1u));
                     while (bits) {
                         const int k = k0 + __ffs((int)bits) - 1;
                         bits &= bits - 1u;
-                        // both pixels' exponents, branch free; most pairs stop here
-                        const float4 g = s_g[k];
-                        const float2 h = s_h[k];
-                        const float dx = g.x - pxf;
-                        const float axx = g.z * dx * dx, bx = g.w * dx;
-                        const float dya = g.y - pyf0, dyb = g.y - pyf1;
-                        const float pa = fmaf(fmaf(h.x, dya, bx), dya, axx);
-                        const float pb = fmaf(fmaf(h.x, dyb, bx), dyb, axx);
-                        const float qa = pa + h.y, qb = pb + h.y;
-                        const bool ea = !a.done && pa <= 0.0f && qa >= kLog2AlphaMin;
-                        const bool eb = !b.done && pb <= 0.0f && qb >= kLog2AlphaMin;
-                        if (COUNT) n_eval += (uint32_t)!a.done + (uint32_t)!b.done;
-                        if (ea || eb) {
-                            const float4 c = s_c[k];
+                        const float4 ua = s_ua[k], bc = s_bc[k], vl = s_vl[k];
+                        const float2 dx = f2_sub(make_float2(ua.x, ua.y), pxf2);
+                        const float2 axx = f2_mul(f2_mul(make_float2(ua.z, ua.w), dx), dx);
+                        const float2 bx = f2_mul(make_float2(bc.x, bc.y), dx);
+                        float2 q[NP];
+                        bool e[PX];
+                        bool any = false;
+#pragma unroll
+                        for (int j = 0; j < NP; j++) {
+                            const float2 dy = f2_sub(make_float2(vl.x, vl.y), pyf[j]);
+                            const float2 p = f2_fma(f2_fma(make_float2(bc.z, bc.w), dy, bx), dy, axx);
+                            q[j] = f2_add(p, make_float2(vl.z, vl.w));
+                            e[2 * j] = !done[2 * j] && p.x <= 0.0f && q[j].x >= kLog2AlphaMin;
+                            e[2 * j + 1] = !done[2 * j + 1] && p.y <= 0.0f && q[j].y >= kLog2AlphaMin;
+                            any |= e[2 * j] | e[2 * j + 1];
+                        }
+                        if (COUNT) {
+#pragma unroll
+                            for (int i = 0; i < PX; i++) n_eval += (uint32_t)!done[i];
+                        }
+                        if (any) {
+                            const float4 rgc = s_rg[k];
+                            const float2 bl = s_bl[k];
                             const uint32_t pos = start - rg.x + (uint32_t)k + 1u;
-                            if (ea) {
-                                const bool bl = composite(a, qa, c, pos);
+#pragma unroll
+                            for (int j = 0; j < NP; j++) {
+                                const bool ea = e[2 * j], eb = e[2 * j + 1];
+                                float2 al = make_float2(ea ? fminf(kAlphaMax, alpha_exp2(q[j].x)) : 0.0f,
+                                                        eb ? fminf(kAlphaMax, alpha_exp2(q[j].y)) : 0.0f);
+                                const float2 test = f2_mul(T[j], f2_sub(one2, al));
+                                // a pixel that does not pass keeps T (>= 1e-4), so only passing ones can stop
+                                const bool sa = test.x < kTMin, sb = test.y < kTMin;
+                                done[2 * j] |= sa;
+                                done[2 * j + 1] |= sb;
+                                al.x = sa ? 0.0f : al.x;
+                                al.y = sb ? 0.0f : al.y;
+                                const float2 w = f2_mul(al, T[j]);
+                                T[j].x = sa ? T[j].x : test.x;
+                                T[j].y = sb ? T[j].y : test.y;
+                                c0[j] = f2_fma(w, make_float2(rgc.x, rgc.y), c0[j]);
+                                c1[j] = f2_fma(w, make_float2(rgc.z, rgc.w), c1[j]);
+                                c2[j] = f2_fma(w, bl, c2[j]);
+                                if (ea && !sa) last[2 * j] = pos;
+                                if (eb && !sb) last[2 * j + 1] = pos;
                                 if (COUNT) {
-                                    n_blend += bl;
-                                    if (!bl) stop_a = pos;
-                                }
-                            }
-                            if (eb) {
-                                const bool bl = composite(b, qb, c, pos);
-                                if (COUNT) {
-                                    n_blend += bl;
-                                    if (!bl) stop_b = pos;
+                                    n_blend += (uint32_t)(ea && !sa) + (uint32_t)(eb && !sb);
+                                    if (sa) stop[2 * j] = pos;
+                                    if (sb) stop[2 * j + 1] = pos;
                                 }
                             }
                         }
                     }
-                    if (__all_sync(0xFFFFFFFFu, a.done && b.done)) break;
+                    bool all_done = true;
+#pragma unroll
+                    for (int i = 0; i < PX; i++) all_done &= done[i];
+                    if (__all_sync(0xFFFFFFFFu, all_done)) break;
                 }
             }
         }
@@ -187,7 +256,10 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
             // tile work: in-image pixels x entries up to the tile's last stop
             if (threadIdx.x == 0) s_stop = 0u;
             __syncthreads();
-            const uint32_t st = max(in0 ? stop_a : 0u, in1 ? stop_b : 0u);
+            uint32_t st = 0u;
+#pragma unroll
+            for (int i = 0; i < PX; i++)
+                if (px < width && py + i < height) st = max(st, stop[i]);
             const uint32_t wst = __reduce_max_sync(0xFFFFFFFFu, st);
             if (lane == 0) atomicMax(&s_stop, wst);
             __syncthreads();
@@ -196,21 +268,19 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
             __syncthreads();
         }
         const float bg0 = v.bg[0], bg1 = v.bg[1], bg2 = v.bg[2];
-        if (in0) {
-            const size_t p = (size_t)py0 * width + px;
-            out_rgb[3 * p + 0] = a.c0 + a.T * bg0;
-            out_rgb[3 * p + 1] = a.c1 + a.T * bg1;
-            out_rgb[3 * p + 2] = a.c2 + a.T * bg2;
-            v.final_T[p] = a.T;
-            v.n_contrib[p] = a.last;
-        }
-        if (in1) {
-            const size_t p = (size_t)py1 * width + px;
-            out_rgb[3 * p + 0] = b.c0 + b.T * bg0;
-            out_rgb[3 * p + 1] = b.c1 + b.T * bg1;
-            out_rgb[3 * p + 2] = b.c2 + b.T * bg2;
-            v.final_T[p] = b.T;
-            v.n_contrib[p] = b.last;
+#pragma unroll
+        for (int i = 0; i < PX; i++) {
+            if (px < width && py + i < height) {
+                const int j = i >> 1;
+                const bool hi = (i & 1) != 0;
+                const float Ti = hi ? T[j].y : T[j].x;
+                const size_t p = (size_t)(py + i) * width + px;
+                out_rgb[3 * p + 0] = (hi ? c0[j].y : c0[j].x) + Ti * bg0;
+                out_rgb[3 * p + 1] = (hi ? c1[j].y : c1[j].x) + Ti * bg1;
+                out_rgb[3 * p + 2] = (hi ? c2[j].y : c2[j].x) + Ti * bg2;
+                v.final_T[p] = Ti;
+                v.n_contrib[p] = last[i];
+            }
         }
     }
     if (COUNT) {
@@ -229,18 +299,18 @@ cudaError_t launch_ts(char *ba, int total_tiles, bool persist, cudaStream_t st, 
                       unsigned long long *counts) {
     auto go = [&](auto kernel) {
         static int occ = 0;   // per instantiation; queried once, before any graph capture uses it
-        if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TS * TS / 2, 0) != cudaSuccess ||
+        if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BlendShape<TS>::NT, 0) != cudaSuccess ||
                      occ < 1))
             occ = 1;
-        kernel<<<occ * num_sms, TS * TS / 2, 0, st>>>(ba, out0, counts);
+        kernel<<<occ * num_sms, BlendShape<TS>::NT, 0, st>>>(ba, out0, counts);
     };
     if (persist) {
         if (counts) go(blend_kernel<TS, BATCH, true, true>);
         else go(blend_kernel<TS, BATCH, false, true>);
     } else if (counts) {
-        blend_kernel<TS, BATCH, true, false><<<total_tiles, TS * TS / 2, 0, st>>>(ba, out0, counts);
+        blend_kernel<TS, BATCH, true, false><<<total_tiles, BlendShape<TS>::NT, 0, st>>>(ba, out0, counts);
     } else {
-        blend_kernel<TS, BATCH, false, false><<<total_tiles, TS * TS / 2, 0, st>>>(ba, out0, counts);
+        blend_kernel<TS, BATCH, false, false><<<total_tiles, BlendShape<TS>::NT, 0, st>>>(ba, out0, counts);
     }
     return cudaGetLastError();
 }

@@ -1,4 +1,4 @@
-// blend_mask.cuh -- which 8 x 8 pixel blocks of a tile one Gaussian's
+// blend_mask.cuh -- which 8 x BH pixel blocks of a tile one Gaussian's
 // alpha >= 1/255 region reaches (used by the blend to let each warp skip the
 // Gaussians of its tile list that cannot touch its block).  Self-contained
 // and usable from host code, so its conservativeness can be checked on the
@@ -20,8 +20,9 @@ constexpr float kBlockMarginRel = 1e-3f;           // margins of the test (see b
 constexpr float kBlockMarginAbs = 1e-3f;
 constexpr float kBlockMarginPx = 1.0f / 64.0f;
 
-// Bit set of the 8 x 8 pixel blocks of a TS x TS tile (row-major, bit
-// r * (TS/8) + c) that the ellipse {q >= log2(1/255)} of one Gaussian reaches.
+// Bit set of the 8 x BH pixel blocks (8 wide, BH tall) of a TS x TS tile
+// (row-major, bit r * (TS/8) + c) that the ellipse {q >= log2(1/255)} of one
+// Gaussian reaches.
 // With dx = u - x, dy = v - y the ellipse is al dx^2 + be dx dy + ga dy^2 <= K
 // (al = -A, be = -B, ga = -C, K = L + log2 255).  For a band of pixel rows
 // the reachable dx form one interval: for fixed dy they are centred at
@@ -34,11 +35,11 @@ constexpr float kBlockMarginPx = 1.0f / 64.0f;
 // rounding of both this test and the per-pixel exponent, so no pixel whose q
 // passes in the blend loop lies in an unmarked block.  Every multiply-add is
 // written as fmaf, so host and device builds compute the same bits.
-template <int TS>
+template <int TS, int BH>
 D4DGS_HD uint32_t block_mask(float u, float v, float A, float B, float C, float L, int x0, int y0) {
-    constexpr int BX = TS / 8;
-    static_assert(BX >= 1 && BX * BX <= 16, "tile of 8, 16 or 32 pixels");
-    constexpr uint32_t kAll = (1u << (BX * BX)) - 1u;
+    constexpr int BX = TS / 8, BY = TS / BH;
+    static_assert(BX >= 1 && BY >= 1 && BX * BY <= 16 && BY * BH == TS, "tile of 8, 16 or 32 pixels");
+    constexpr uint32_t kAll = (1u << (BX * BY)) - 1u;
     const float al = -A, be = -B, ga = -C;
     float K = L + kLog2_255;
     if (!(K >= 0.0f)) return 0u;   // o_hat < 1/255: no pixel passes
@@ -50,8 +51,8 @@ D4DGS_HD uint32_t block_mask(float u, float v, float A, float B, float C, float 
     const float dyR = -0.5f * be * ex / ga;
     uint32_t m = 0u;
 #pragma unroll 1
-    for (int r = 0; r < BX; r++) {
-        const float ylo = (float)(y0 + 8 * r) + 0.5f, yhi = ylo + 7.0f;
+    for (int r = 0; r < BY; r++) {
+        const float ylo = (float)(y0 + BH * r) + 0.5f, yhi = ylo + (float)(BH - 1);
         const float d0 = fmaxf(v - yhi, -ey), d1 = fminf(v - ylo, ey);
         if (d0 > d1) continue;   // the band is outside the ellipse's rows
         const float dA = fminf(fmaxf(dyR, d0), d1), dB = fminf(fmaxf(-dyR, d0), d1);

@@ -1,9 +1,11 @@
-// Conservativeness check of the blend's 8 x 8 block mask (blend_mask.cuh):
+// Conservativeness check of the blend's 8 x BH block mask (blend_mask.cuh):
 // for random 2D Gaussians (rotated, elongated, tiny and huge, opacity down to
-// the 1/255 cut) and tiles of 8, 16 and 32 pixels, every pixel of every block
+// the 1/255 cut), tiles of 8, 16 and 32 pixels and blocks 8 or 16 pixels
+// tall, every pixel of every block
 // whose bit is clear must fail the blend's alpha test, both as the kernel
 // evaluates the exponent in FP32 and in FP64 with a margin.  Prints
-// "pairs set needed failures" per tile size; exit status 1 on any failure.
+// "tile block_height blocks set needed failures" per case; exit status 1 on
+// any failure.
 #include "blend_mask.cuh"
 
 #include <cmath>
@@ -19,9 +21,9 @@ struct Counts {
     long blocks = 0, set = 0, needed = 0, failures = 0;
 };
 
-template <int TS>
+template <int TS, int BH>
 void run(std::mt19937_64 &rng, int trials, Counts &c) {
-    constexpr int BX = TS / 8;
+    constexpr int BX = TS / 8, BY = TS / BH;
     std::uniform_real_distribution<double> U(0.0, 1.0);
     for (int it = 0; it < trials; it++) {
         // covariance: random angle, log-uniform sigmas, +0.3 px^2 dilation
@@ -45,13 +47,13 @@ void run(std::mt19937_64 &rng, int trials, Counts &c) {
         const int x0 = 8 * (int)(U(rng) * 40), y0 = 8 * (int)(U(rng) * 40);
         const float u = (float)(x0 + TS * 0.5 + (U(rng) - 0.5) * (TS + 2.0 * ext));
         const float v = (float)(y0 + TS * 0.5 + (U(rng) - 0.5) * (TS + 2.0 * ext));
-        const uint32_t m = d4dgs::block_mask<TS>(u, v, A, B, C, L, x0, y0);
-        for (int r = 0; r < BX; r++)
+        const uint32_t m = d4dgs::block_mask<TS, BH>(u, v, A, B, C, L, x0, y0);
+        for (int r = 0; r < BY; r++)
             for (int q = 0; q < BX; q++) {
                 bool any32 = false, near64 = false;
-                for (int yy = 0; yy < 8; yy++)
+                for (int yy = 0; yy < BH; yy++)
                     for (int xx = 0; xx < 8; xx++) {
-                        const float pxf = (float)(x0 + 8 * q + xx) + 0.5f, pyf = (float)(y0 + 8 * r + yy) + 0.5f;
+                        const float pxf = (float)(x0 + 8 * q + xx) + 0.5f, pyf = (float)(y0 + BH * r + yy) + 0.5f;
                         const float dx = u - pxf, dy = v - pyf;
                         const float axx = A * dx * dx, bx = B * dx;
                         const float p = std::fma(std::fma(C, dy, bx), dy, axx);
@@ -67,8 +69,8 @@ void run(std::mt19937_64 &rng, int trials, Counts &c) {
                 c.needed += any32;
                 if (!bit && (any32 || near64)) {
                     if (c.failures < 5)
-                        std::printf("FAIL TS=%d u=%.6g v=%.6g A=%.9g B=%.9g C=%.9g L=%.9g tile=(%d,%d) block=(%d,%d)\n",
-                                    TS, u, v, A, B, C, L, x0, y0, q, r);
+                        std::printf("FAIL TS=%d BH=%d u=%.6g v=%.6g A=%.9g B=%.9g C=%.9g L=%.9g tile=(%d,%d) block=(%d,%d)\n",
+                                    TS, BH, u, v, A, B, C, L, x0, y0, q, r);
                     c.failures++;
                 }
             }
@@ -80,14 +82,17 @@ void run(std::mt19937_64 &rng, int trials, Counts &c) {
 int main(int argc, char **argv) {
     const int trials = argc > 1 ? std::atoi(argv[1]) : 20000;
     std::mt19937_64 rng(12345);
-    Counts c8, c16, c32;
-    run<8>(rng, trials, c8);
-    run<16>(rng, trials, c16);
-    run<32>(rng, trials, c32);
+    Counts c[5];
+    run<8, 8>(rng, trials, c[0]);
+    run<16, 8>(rng, trials, c[1]);
+    run<32, 8>(rng, trials, c[2]);
+    run<16, 16>(rng, trials, c[3]);
+    run<32, 16>(rng, trials, c[4]);
+    const int ts[5] = {8, 16, 32, 16, 32}, bh[5] = {8, 8, 8, 16, 16};
     long fails = 0;
-    for (auto [ts, c] : {std::pair<int, Counts>{8, c8}, {16, c16}, {32, c32}}) {
-        std::printf("%d %ld %ld %ld %ld\n", ts, c.blocks, c.set, c.needed, c.failures);
-        fails += c.failures;
+    for (int i = 0; i < 5; i++) {
+        std::printf("%d %d %ld %ld %ld %ld\n", ts[i], bh[i], c[i].blocks, c[i].set, c[i].needed, c[i].failures);
+        fails += c[i].failures;
     }
     return fails ? 1 : 0;
 }

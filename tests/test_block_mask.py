@@ -25,10 +25,10 @@ def test_block_mask_is_conservative_and_tight(checker):
     r = subprocess.run([str(checker), "20000"], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     rows = [list(map(int, line.split())) for line in r.stdout.strip().splitlines()]
-    assert [row[0] for row in rows] == [8, 16, 32]
-    for ts, blocks, marked, needed, failures in rows:
+    assert [(row[0], row[1]) for row in rows] == [(8, 8), (16, 8), (32, 8), (16, 16), (32, 16)]
+    for ts, bh, blocks, marked, needed, failures in rows:
         assert failures == 0
         assert needed <= marked <= blocks
         assert needed > 0
         # few false positives: the interval per 8-row band is exact up to the margins
-        assert marked - needed <= 0.1 * marked, (ts, marked, needed)
+        assert marked - needed <= 0.1 * marked, (ts, bh, marked, needed)
