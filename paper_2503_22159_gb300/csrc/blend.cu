@@ -74,6 +74,25 @@ __device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
     return d;
 }
 
+// A Gaussian takes the fast compositing body when neither the 0.99 clamp nor
+// the p > 0 test can fire for it, so both can be left out with the same bits:
+//  * L = log2(o_hat) <= log2(0.98): q <= L, and ex2.approx is within a few
+//    ulp, so 2^q < 0.99;
+//  * 4 al ga - be^2 > 2^-12 (al + ga)^2: the FP32 exponent p (two products
+//    and two FMAs) is off by at most ~8 u (al + ga) r^2 (u = 2^-24, r the
+//    pixel's distance to the mean) while -p >= lambda_min r^2 with
+//    lambda_min >= det4 / (4 (al + ga)), so the computed p is never > 0
+//    (margin 2^7).
+// Every other Gaussian takes the general body.
+constexpr float kLog2FastOpacity = -0.029146346f;    // log2(0.98)
+constexpr float kFastConditioning = 1.0f / 4096.0f;
+constexpr uint32_t kSlowBit = 1u << 31;             // in the staged block mask
+
+template <bool B>
+struct BoolC {
+    static constexpr bool value = B;
+};
+
 template <int TS>
 struct BlendShape {
     static constexpr int PX = TS == 8 ? 2 : 4;   // pixels per thread (a column)
@@ -180,69 +199,114 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     s_vl[k] = make_float4(r0.y, r0.y, r2.w, r2.w);
                     s_rg[k] = make_float4(r2.x, r2.x, r2.y, r2.y);
                     s_bl[k] = make_float2(r2.z, r2.z);
-                    s_m[k] = d4dgs::block_mask<TS, BH>(r0.x, r0.y, A, B, C, r2.w, x0, y0);
+                    const float det4 = fmaf(4.0f * A, C, -(B * B)), tr = -(A + C);
+                    const bool fast = r2.w <= kLog2FastOpacity && det4 > kFastConditioning * tr * tr;
+                    s_m[k] = d4dgs::block_mask<TS, BH>(r0.x, r0.y, A, B, C, r2.w, x0, y0) | (fast ? 0u : kSlowBit);
                 }
             }
             __syncthreads();
             const int nb = (int)min((uint32_t)BATCH, rg.y - start);
+            // Visit Gaussian k of the batch (warp-uniform).  FAST: no clamp and no
+            // p > 0 test (see kLog2FastOpacity).  In both bodies the stop test
+            // T (1 - alpha) < 1e-4 is taken for all pixels at once, and the
+            // per-pixel selects run only when one of the thread's pixels stops.
+            auto visit = [&](auto fast_c, int k) {
+                constexpr bool FAST = decltype(fast_c)::value;
+                const float4 ua = s_ua[k], bc = s_bc[k], vl = s_vl[k];
+                const float2 dx = f2_sub(make_float2(ua.x, ua.y), pxf2);
+                const float2 axx = f2_mul(f2_mul(make_float2(ua.z, ua.w), dx), dx);
+                const float2 bx = f2_mul(make_float2(bc.x, bc.y), dx);
+                float2 al[NP];
+                bool e[PX];
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    const float2 dy = f2_sub(make_float2(vl.x, vl.y), pyf[j]);
+                    const float2 p = f2_fma(f2_fma(make_float2(bc.z, bc.w), dy, bx), dy, axx);
+                    const float2 q = f2_add(p, make_float2(vl.z, vl.w));
+                    if (FAST) {
+                        e[2 * j] = !done[2 * j] && q.x >= kLog2AlphaMin;
+                        e[2 * j + 1] = !done[2 * j + 1] && q.y >= kLog2AlphaMin;
+                        al[j] = make_float2(e[2 * j] ? alpha_exp2(q.x) : 0.0f, e[2 * j + 1] ? alpha_exp2(q.y) : 0.0f);
+                    } else {
+                        e[2 * j] = !done[2 * j] && p.x <= 0.0f && q.x >= kLog2AlphaMin;
+                        e[2 * j + 1] = !done[2 * j + 1] && p.y <= 0.0f && q.y >= kLog2AlphaMin;
+                        al[j] = make_float2(e[2 * j] ? fminf(kAlphaMax, alpha_exp2(q.x)) : 0.0f,
+                                            e[2 * j + 1] ? fminf(kAlphaMax, alpha_exp2(q.y)) : 0.0f);
+                    }
+                }
+                if (COUNT) {
+#pragma unroll
+                    for (int i = 0; i < PX; i++) n_eval += (uint32_t)!done[i];
+                }
+                // a pixel that does not pass has alpha = 0 and keeps T >= 1e-4, so only passing ones can stop
+                float2 test[NP];
+                bool any_stop = false;
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    test[j] = f2_mul(T[j], f2_sub(one2, al[j]));
+                    any_stop |= (test[j].x < kTMin) | (test[j].y < kTMin);
+                }
+                const float4 rgc = s_rg[k];
+                const float2 bl = s_bl[k];
+                const uint32_t pos = start - rg.x + (uint32_t)k + 1u;
+                if (!any_stop) {
+#pragma unroll
+                    for (int j = 0; j < NP; j++) {
+                        const float2 w = f2_mul(al[j], T[j]);
+                        T[j] = test[j];
+                        c0[j] = f2_fma(w, make_float2(rgc.x, rgc.y), c0[j]);
+                        c1[j] = f2_fma(w, make_float2(rgc.z, rgc.w), c1[j]);
+                        c2[j] = f2_fma(w, bl, c2[j]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < PX; i++) last[i] = e[i] ? pos : last[i];
+                    if (COUNT) {
+#pragma unroll
+                        for (int i = 0; i < PX; i++) n_blend += (uint32_t)e[i];
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NP; j++) {
+                        const bool sa = test[j].x < kTMin, sb = test[j].y < kTMin;
+                        const bool ba = e[2 * j] && !sa, bb = e[2 * j + 1] && !sb;
+                        done[2 * j] |= sa;
+                        done[2 * j + 1] |= sb;
+                        const float2 w = f2_mul(make_float2(sa ? 0.0f : al[j].x, sb ? 0.0f : al[j].y), T[j]);
+                        T[j].x = sa ? T[j].x : test[j].x;
+                        T[j].y = sb ? T[j].y : test[j].y;
+                        c0[j] = f2_fma(w, make_float2(rgc.x, rgc.y), c0[j]);
+                        c1[j] = f2_fma(w, make_float2(rgc.z, rgc.w), c1[j]);
+                        c2[j] = f2_fma(w, bl, c2[j]);
+                        if (ba) last[2 * j] = pos;
+                        if (bb) last[2 * j + 1] = pos;
+                        if (COUNT) {
+                            n_blend += (uint32_t)ba + (uint32_t)bb;
+                            if (sa) stop[2 * j] = pos;
+                            if (sb) stop[2 * j + 1] = pos;
+                        }
+                    }
+                }
+            };
             // warp-uniform from here to the end of the batch
             if (__any_sync(0xFFFFFFFFu, live)) {
+                const uint32_t wbit = 1u << warp;
                 for (int k0 = 0; k0 < nb; k0 += 32) {
                     const int kl = k0 + lane;
-                    uint32_t bits = __ballot_sync(0xFFFFFFFFu, kl < nb && ((s_m[kl] >> warp) & 1u));
-                    while (bits) {
-                        const int k = k0 + __ffs((int)bits) - 1;
-                        bits &= bits - 1u;
-                        const float4 ua = s_ua[k], bc = s_bc[k], vl = s_vl[k];
-                        const float2 dx = f2_sub(make_float2(ua.x, ua.y), pxf2);
-                        const float2 axx = f2_mul(f2_mul(make_float2(ua.z, ua.w), dx), dx);
-                        const float2 bx = f2_mul(make_float2(bc.x, bc.y), dx);
-                        float2 q[NP];
-                        bool e[PX];
-                        bool any = false;
-#pragma unroll
-                        for (int j = 0; j < NP; j++) {
-                            const float2 dy = f2_sub(make_float2(vl.x, vl.y), pyf[j]);
-                            const float2 p = f2_fma(f2_fma(make_float2(bc.z, bc.w), dy, bx), dy, axx);
-                            q[j] = f2_add(p, make_float2(vl.z, vl.w));
-                            e[2 * j] = !done[2 * j] && p.x <= 0.0f && q[j].x >= kLog2AlphaMin;
-                            e[2 * j + 1] = !done[2 * j + 1] && p.y <= 0.0f && q[j].y >= kLog2AlphaMin;
-                            any |= e[2 * j] | e[2 * j + 1];
+                    const uint32_t m = kl < nb ? s_m[kl] : 0u;
+                    uint32_t bits = __ballot_sync(0xFFFFFFFFu, (m & wbit) != 0u);
+                    const uint32_t slow = __ballot_sync(0xFFFFFFFFu, (m & wbit) != 0u && (m & kSlowBit) != 0u);
+                    if (slow == 0u) {
+                        while (bits) {
+                            const int b = __ffs((int)bits) - 1;
+                            bits &= bits - 1u;
+                            visit(BoolC<true>{}, k0 + b);
                         }
-                        if (COUNT) {
-#pragma unroll
-                            for (int i = 0; i < PX; i++) n_eval += (uint32_t)!done[i];
-                        }
-                        if (any) {
-                            const float4 rgc = s_rg[k];
-                            const float2 bl = s_bl[k];
-                            const uint32_t pos = start - rg.x + (uint32_t)k + 1u;
-#pragma unroll
-                            for (int j = 0; j < NP; j++) {
-                                const bool ea = e[2 * j], eb = e[2 * j + 1];
-                                float2 al = make_float2(ea ? fminf(kAlphaMax, alpha_exp2(q[j].x)) : 0.0f,
-                                                        eb ? fminf(kAlphaMax, alpha_exp2(q[j].y)) : 0.0f);
-                                const float2 test = f2_mul(T[j], f2_sub(one2, al));
-                                // a pixel that does not pass keeps T (>= 1e-4), so only passing ones can stop
-                                const bool sa = test.x < kTMin, sb = test.y < kTMin;
-                                done[2 * j] |= sa;
-                                done[2 * j + 1] |= sb;
-                                al.x = sa ? 0.0f : al.x;
-                                al.y = sb ? 0.0f : al.y;
-                                const float2 w = f2_mul(al, T[j]);
-                                T[j].x = sa ? T[j].x : test.x;
-                                T[j].y = sb ? T[j].y : test.y;
-                                c0[j] = f2_fma(w, make_float2(rgc.x, rgc.y), c0[j]);
-                                c1[j] = f2_fma(w, make_float2(rgc.z, rgc.w), c1[j]);
-                                c2[j] = f2_fma(w, bl, c2[j]);
-                                if (ea && !sa) last[2 * j] = pos;
-                                if (eb && !sb) last[2 * j + 1] = pos;
-                                if (COUNT) {
-                                    n_blend += (uint32_t)(ea && !sa) + (uint32_t)(eb && !sb);
-                                    if (sa) stop[2 * j] = pos;
-                                    if (sb) stop[2 * j + 1] = pos;
-                                }
-                            }
+                    } else {
+                        while (bits) {
+                            const int b = __ffs((int)bits) - 1;
+                            bits &= bits - 1u;
+                            if ((slow >> b) & 1u) visit(BoolC<false>{}, k0 + b);
+                            else visit(BoolC<true>{}, k0 + b);
                         }
                     }
                     bool all_done = true;
