@@ -92,9 +92,9 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.id_bits = ceil_log2(n > 1 ? n : 2);
     l.packed = (l.id_bits + l.tile_bits) <= 32;
     l.cap = cap;
-    l.parts_depth = n > 0 ? ((int64_t)n + kSortItems - 1) / kSortItems : 1;
+    l.parts_depth = n > 0 ? ((int64_t)n + kDepthItems - 1) / kDepthItems : 1;
     l.parts_dup = n > 0 ? ((int64_t)n + kDupItems - 1) / kDupItems : 1;
-    l.parts_tile = cap > 0 ? (cap + kSortItems - 1) / kSortItems : 1;
+    l.parts_tile = cap > 0 ? (cap + kTileItems - 1) / kTileItems : 1;
     int64_t off = 0;
     l.control = off; off += align256((int64_t)kCtlWords * 4);
     l.grid = off; off += align256((int64_t)(l.tiles_x + 1) * (l.tiles_y + 1) * 4);

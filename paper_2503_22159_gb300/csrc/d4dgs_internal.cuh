@@ -23,8 +23,10 @@ constexpr float kK2Pad = 0.0008f;
 
 // ---- sort geometry
 constexpr int kSortThreads = 256;
-constexpr int kSortIPT = 15;                              // keys per thread
-constexpr int kSortItems = kSortThreads * kSortIPT;       // 3840 keys per partition
+constexpr int kTileIPT = 15;                              // pair keys per thread (tile passes)
+constexpr int kTileItems = kSortThreads * kTileIPT;       // 3840 pairs per partition
+constexpr int kDepthIPT = 4;                              // depth keys per thread: short partitions, so
+constexpr int kDepthItems = kSortThreads * kDepthIPT;     // the few-key depth passes spread over all SMs
 constexpr int kRadix = 256;                               // digit bins (<= 8 bits per pass)
 constexpr int kDupThreads = 256;
 constexpr int kDupItems = kDupThreads;                    // depth-ordered Gaussians per scan partition

@@ -78,7 +78,7 @@ __device__ __forceinline__ uint32_t pass_bases(const char *ba, int nviews, uint3
             uint32_t parts;
             if (TILE) {
                 const uint32_t k = min(v.ctl[kCtlNumKeys], v.cap);
-                parts = (k + kSortItems - 1) / kSortItems;
+                parts = (k + kTileItems - 1) / kTileItems;
             } else {
                 parts = (uint32_t)v.parts_depth;
             }
@@ -95,11 +95,13 @@ __device__ __forceinline__ uint32_t pass_bases(const char *ba, int nviews, uint3
 // TILE = true: tile pass `pass` of the (tile, id) pairs (count read on the
 // device).  KV: keys carry a separate uint32 value.
 template <bool KV, bool IOTA, bool TILE>
-__global__ void __launch_bounds__(kSortThreads, KV ? 3 : 4)
+__global__ void __launch_bounds__(kSortThreads, TILE ? (KV ? 3 : 4) : 4)
 onesweep_kernel(char *__restrict__ ba, int pass) {
+    constexpr int IPT = TILE ? kTileIPT : kDepthIPT;
+    constexpr int ITEMS = kSortThreads * IPT;
     __shared__ uint32_t s_warp_hist[8][kRadix];
-    __shared__ uint32_t s_keys[kSortItems];
-    __shared__ uint32_t s_vals[KV ? kSortItems : 1];
+    __shared__ uint32_t s_keys[ITEMS];
+    __shared__ uint32_t s_vals[KV ? ITEMS : 1];
     __shared__ uint32_t s_delta[kRadix];   // global_start - local_start of each digit
     __shared__ uint32_t s_local_start[kRadix];
     __shared__ uint32_t s_hist_excl[kRadix];
@@ -141,13 +143,13 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
             s_hist_excl[tid] = block_exclusive_scan_256(hist[tid], s_scan, &tot);
             cur = vi;
         }
-        const uint32_t base = part * kSortItems;
+        const uint32_t base = part * ITEMS;
 
         // ---- load (warp-striped: item k of lane l is base + warp*32*IPT + k*32 + l)
-        uint32_t keys[kSortIPT], vals[KV ? kSortIPT : 1], rank[kSortIPT];
-        const uint32_t wbase = base + warp * 32 * kSortIPT + lane;
+        uint32_t keys[IPT], vals[KV ? IPT : 1], rank[IPT];
+        const uint32_t wbase = base + warp * 32 * IPT + lane;
 #pragma unroll
-        for (int k = 0; k < kSortIPT; k++) {
+        for (int k = 0; k < IPT; k++) {
             const uint32_t idx = wbase + k * 32;
             const bool ok = idx < count;
             keys[k] = ok ? keys_in[idx] : 0xFFFFFFFFu;
@@ -155,7 +157,7 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
         }
         // ---- stable rank within the warp (match-any on the digit)
 #pragma unroll
-        for (int k = 0; k < kSortIPT; k++) {
+        for (int k = 0; k < IPT; k++) {
             const uint32_t d = (keys[k] >> shift) & mask;
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
             const int leader = __ffs(peers) - 1;
@@ -221,7 +223,7 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
         __syncthreads();
         // ---- scatter into shared memory in digit order
 #pragma unroll
-        for (int k = 0; k < kSortIPT; k++) {
+        for (int k = 0; k < IPT; k++) {
             const uint32_t dd = (keys[k] >> shift) & mask;
             const uint32_t pos = s_local_start[dd] + s_warp_hist[warp][dd] + rank[k];
             s_keys[pos] = keys[k];
@@ -229,7 +231,7 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
         }
         __syncthreads();
         // ---- write out: consecutive threads write consecutive positions of a digit run
-        for (int i = tid; i < kSortItems; i += kSortThreads) {
+        for (int i = tid; i < ITEMS; i += kSortThreads) {
             const uint32_t key = s_keys[i];
             const uint32_t dest = (uint32_t)i + s_delta[(key >> shift) & mask];
             if (dest < count) {
