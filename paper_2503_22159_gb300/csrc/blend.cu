@@ -85,6 +85,7 @@ __device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
 //    (margin 2^7).
 // Every other Gaussian takes the general body.
 constexpr float kLog2FastOpacity = -0.029146346f;    // log2(0.98)
+constexpr float kInf = __builtin_huge_valf();
 constexpr float kFastConditioning = 1.0f / 4096.0f;
 constexpr uint32_t kSlowBit = 1u << 31;             // in the staged block mask
 
@@ -123,6 +124,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
     __shared__ uint32_t s_m[BATCH];  // blocks the Gaussian's alpha >= 1/255 ellipse reaches
     __shared__ int32_t s_item;
     __shared__ uint32_t s_stop;
+    grid_dependency_wait();
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
     const int nviews = (int)bw[kBaNViews];
     const int total = (int)bw[kBaTotalTiles];
@@ -163,7 +165,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
         const float2 pxf2 = make_float2(pxf, pxf);
         float2 pyf[NP], T[NP], c0[NP], c1[NP], c2[NP];
         uint32_t last[PX], stop[PX];
-        bool done[PX];
+        float thr[PX];   // per-pixel pass threshold of q: log2(1/255), +inf once the pixel has stopped
         uint2 rg = v.ranges[tile];
         rg.y = min(rg.y, cap);   // ranges are written clamped; this keeps every read in bounds regardless
         rg.x = min(rg.x, rg.y);
@@ -177,13 +179,13 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
         for (int i = 0; i < PX; i++) {
             last[i] = 0u;
             stop[i] = rg.y - rg.x;   // COUNT only
-            done[i] = !(px < width && py + i < height);
+            thr[i] = (px < width && py + i < height) ? kLog2AlphaMin : kInf;
         }
 
         for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
             bool live = false;
 #pragma unroll
-            for (int i = 0; i < PX; i++) live |= !done[i];
+            for (int i = 0; i < PX; i++) live |= thr[i] < kInf;
             if (__syncthreads_count(live) == 0) break;
             for (int k = threadIdx.x; k < BATCH; k += NT) {
                 const uint32_t j = start + (uint32_t)k;
@@ -224,19 +226,19 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     const float2 p = f2_fma(f2_fma(make_float2(bc.z, bc.w), dy, bx), dy, axx);
                     const float2 q = f2_add(p, make_float2(vl.z, vl.w));
                     if (FAST) {
-                        e[2 * j] = !done[2 * j] && q.x >= kLog2AlphaMin;
-                        e[2 * j + 1] = !done[2 * j + 1] && q.y >= kLog2AlphaMin;
+                        e[2 * j] = q.x >= thr[2 * j];
+                        e[2 * j + 1] = q.y >= thr[2 * j + 1];
                         al[j] = make_float2(e[2 * j] ? alpha_exp2(q.x) : 0.0f, e[2 * j + 1] ? alpha_exp2(q.y) : 0.0f);
                     } else {
-                        e[2 * j] = !done[2 * j] && p.x <= 0.0f && q.x >= kLog2AlphaMin;
-                        e[2 * j + 1] = !done[2 * j + 1] && p.y <= 0.0f && q.y >= kLog2AlphaMin;
+                        e[2 * j] = p.x <= 0.0f && q.x >= thr[2 * j];
+                        e[2 * j + 1] = p.y <= 0.0f && q.y >= thr[2 * j + 1];
                         al[j] = make_float2(e[2 * j] ? fminf(kAlphaMax, alpha_exp2(q.x)) : 0.0f,
                                             e[2 * j + 1] ? fminf(kAlphaMax, alpha_exp2(q.y)) : 0.0f);
                     }
                 }
                 if (COUNT) {
 #pragma unroll
-                    for (int i = 0; i < PX; i++) n_eval += (uint32_t)!done[i];
+                    for (int i = 0; i < PX; i++) n_eval += (uint32_t)(thr[i] < kInf);
                 }
                 // a pixel that does not pass has alpha = 0 and keeps T >= 1e-4, so only passing ones can stop
                 float2 test[NP];
@@ -269,8 +271,8 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     for (int j = 0; j < NP; j++) {
                         const bool sa = test[j].x < kTMin, sb = test[j].y < kTMin;
                         const bool ba = e[2 * j] && !sa, bb = e[2 * j + 1] && !sb;
-                        done[2 * j] |= sa;
-                        done[2 * j + 1] |= sb;
+                        if (sa) thr[2 * j] = kInf;
+                        if (sb) thr[2 * j + 1] = kInf;
                         const float2 w = f2_mul(make_float2(sa ? 0.0f : al[j].x, sb ? 0.0f : al[j].y), T[j]);
                         T[j].x = sa ? T[j].x : test[j].x;
                         T[j].y = sb ? T[j].y : test[j].y;
@@ -311,7 +313,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     }
                     bool all_done = true;
 #pragma unroll
-                    for (int i = 0; i < PX; i++) all_done &= done[i];
+                    for (int i = 0; i < PX; i++) all_done &= thr[i] == kInf;
                     if (__all_sync(0xFFFFFFFFu, all_done)) break;
                 }
             }
@@ -366,17 +368,18 @@ cudaError_t launch_ts(char *ba, int total_tiles, bool persist, cudaStream_t st, 
         if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BlendShape<TS>::NT, 0) != cudaSuccess ||
                      occ < 1))
             occ = 1;
-        kernel<<<occ * num_sms, BlendShape<TS>::NT, 0, st>>>(ba, out0, counts);
+        return launch_chained(kernel, occ * num_sms, BlendShape<TS>::NT, 0, st, ba, out0, counts);
     };
     if (persist) {
-        if (counts) go(blend_kernel<TS, BATCH, true, true>);
-        else go(blend_kernel<TS, BATCH, false, true>);
+        if (counts) return go(blend_kernel<TS, BATCH, true, true>);
+        return go(blend_kernel<TS, BATCH, false, true>);
     } else if (counts) {
-        blend_kernel<TS, BATCH, true, false><<<total_tiles, BlendShape<TS>::NT, 0, st>>>(ba, out0, counts);
+        return launch_chained(blend_kernel<TS, BATCH, true, false>, total_tiles, BlendShape<TS>::NT, 0, st, ba, out0,
+                              counts);
     } else {
-        blend_kernel<TS, BATCH, false, false><<<total_tiles, BlendShape<TS>::NT, 0, st>>>(ba, out0, counts);
+        return launch_chained(blend_kernel<TS, BATCH, false, false>, total_tiles, BlendShape<TS>::NT, 0, st, ba, out0,
+                              counts);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace

@@ -202,4 +202,30 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Chained launches (programmatic dependent launch): the forward kernels of a
+// frame are launched with programmatic stream serialisation, so the launch of
+// a kernel overlaps the end of the one before it in the stream.  Every such
+// kernel calls grid_dependency_wait() before its first memory access; it
+// returns once the preceding kernel has completed and its writes are visible
+// (at once for a kernel launched without the attribute).
+constexpr bool kChainedLaunch = true;
+
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                           Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = kChainedLaunch ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 }  // namespace d4dgs

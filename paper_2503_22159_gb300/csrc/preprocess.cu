@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restri
     __shared__ uint32_t hist[4 * kRadix];
     __shared__ int32_t s_chunk;
     extern __shared__ int s_grid[];
+    grid_dependency_wait();
     for (int i = threadIdx.x; i < smem_cells; i += blockDim.x) s_grid[i] = 0;
     const uint32_t *bw = reinterpret_cast<const uint32_t *>(ba);
     const int nviews = (int)bw[kBaNViews];
@@ -297,6 +298,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restri
 // work counters, and clears every view's per-frame region.
 __global__ void __launch_bounds__(256)
 clear_kernel(const __grid_constant__ BatchArgs args, const BatchArgs *args_dev, char *__restrict__ ba) {
+    grid_dependency_wait();
     const BatchArgs *A = args_dev ? args_dev : &args;
     const int nviews = A->nviews;
     if (blockIdx.x == 0) {
@@ -342,7 +344,9 @@ CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile) {
 
 cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batch_area, cudaStream_t st,
                          int num_sms) {
-    clear_kernel<<<num_sms * 2, 256, 0, st>>>(args, static_cast<const BatchArgs *>(args_dev), batch_area);
+    const cudaError_t e = launch_chained(clear_kernel, num_sms * 2, 256, 0, st, args,
+                                         static_cast<const BatchArgs *>(args_dev), batch_area);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -351,7 +355,9 @@ cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cud
     // persistent grid: 8 resident CTAs of 256 threads per SM; grids of up to
     // 6144 cells (e.g. 1352x1014 at 32-px tiles) are aggregated in shared memory
     constexpr int kSmemCells = 6144;
-    preprocess_kernel<<<num_sms * 8, 256, kSmemCells * sizeof(int), st>>>(batch_area, kSmemCells);
+    const cudaError_t e = launch_chained(preprocess_kernel, num_sms * 8, 256, kSmemCells * sizeof(int), st,
+                                         (const char *)batch_area, kSmemCells);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -102,6 +102,7 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
     __shared__ uint32_t s_warp_hist[8][kRadix];
     __shared__ uint32_t s_keys[ITEMS];
     __shared__ uint32_t s_vals[KV ? ITEMS : 1];
+    grid_dependency_wait();
     __shared__ uint32_t s_delta[kRadix];   // global_start - local_start of each digit
     __shared__ uint32_t s_local_start[kRadix];
     __shared__ uint32_t s_hist_excl[kRadix];
@@ -250,6 +251,7 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
     __shared__ unsigned long long s_warp[32];
     __shared__ uint32_t s_hist[3 * kRadix];
     extern __shared__ int s_grid[];
+    grid_dependency_wait();
     const uint32_t *bw = reinterpret_cast<const uint32_t *>(ba);
     if ((int)blockIdx.x >= (int)bw[kBaNViews]) return;
     const View &v = view_of(ba, blockIdx.x);
@@ -329,6 +331,7 @@ __global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba
     __shared__ uint32_t s_off[kDupItems], s_cnt[kDupItems], s_id[kDupItems];
     __shared__ ushort4 s_rect[kDupItems];
     __shared__ uint32_t s_scan[8];
+    grid_dependency_wait();
     __shared__ uint32_t s_part;
     __shared__ unsigned long long s_excl;
 
@@ -472,25 +475,26 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
                          ? bytes / 4
                          : 0;
     }
-    tilecount_kernel<<<kMaxViews, 1024, (size_t)smem_cells * 4, st>>>(batch_area, smem_cells);
-    if (args.max_n == 0) return cudaGetLastError();
+    cudaError_t e = launch_chained(tilecount_kernel, kMaxViews, 1024, (size_t)smem_cells * 4, st, batch_area, smem_cells);
+    if (e != cudaSuccess || args.max_n == 0) return e;
     // ---- 1. depth sort (4 passes), ids in dvals[0]
-    for (int p = 0; p < 4; p++) {
+    for (int p = 0; p < 4 && e == cudaSuccess; p++) {
         if (p == 0)
-            onesweep_kernel<true, true, false><<<occ_iota * num_sms, kSortThreads, 0, st>>>(batch_area, p);
+            e = launch_chained(onesweep_kernel<true, true, false>, occ_iota * num_sms, kSortThreads, 0, st, batch_area, p);
         else
-            onesweep_kernel<true, false, false><<<occ_kv * num_sms, kSortThreads, 0, st>>>(batch_area, p);
+            e = launch_chained(onesweep_kernel<true, false, false>, occ_kv * num_sms, kSortThreads, 0, st, batch_area, p);
     }
+    if (e != cudaSuccess) return e;
     // ---- 2. scan + emission in depth order
-    emit_kernel<<<occ_emit * num_sms, kDupThreads, 0, st>>>(batch_area);
+    e = launch_chained(emit_kernel, occ_emit * num_sms, kDupThreads, 0, st, batch_area);
     // ---- 3. stable sort of the pairs by tile bits
-    for (int p = 0; p < args.tile_passes; p++) {
+    for (int p = 0; p < args.tile_passes && e == cudaSuccess; p++) {
         if (args.packed)
-            onesweep_kernel<false, false, true><<<occ_k * num_sms, kSortThreads, 0, st>>>(batch_area, p);
+            e = launch_chained(onesweep_kernel<false, false, true>, occ_k * num_sms, kSortThreads, 0, st, batch_area, p);
         else
-            onesweep_kernel<true, false, true><<<occ_tkv * num_sms, kSortThreads, 0, st>>>(batch_area, p);
+            e = launch_chained(onesweep_kernel<true, false, true>, occ_tkv * num_sms, kSortThreads, 0, st, batch_area, p);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace d4dgs
