@@ -113,7 +113,7 @@ typedef struct {
     int64_t tile_vals;           /* key_capacity uint32 Gaussian ids when not packed, else -1  */
     int64_t ranges;              /* tiles x 2 uint32: [start, end) of each tile's list        */
     int64_t final_T;             /* H x W float: transmittance after the last blend           */
-    int64_t n_contrib;           /* H x W uint32: list positions walked up to the last blend  */
+    int64_t n_contrib;           /* H x W uint32: list entries walked before the pixel stopped */
     int64_t control;             /* device status word and counters                           */
     int64_t key_capacity;
     int32_t tiles_x, tiles_y;
@@ -158,7 +158,8 @@ int d4dgs_sort(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void
  * list (Eq. 4 with alpha = min(0.99, o_hat exp(p)), p = -1/2 d^T conic d,
  * skip alpha < 1/255, stop before blending once T (1 - alpha) < 1e-4).
  * out_rgb: H x W x 3 float32 device, caller-owned, overwritten with
- * C + T bg; also stores T and the list position of the last blend per pixel
+ * C + T bg; also stores T and, per pixel, the number of list entries walked
+ * before the one at which it stopped (the whole list if it never stopped)
  * in the workspace for the backward pass. */
 int d4dgs_blend(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
                 float *out_rgb, d4dgs_stream_t stream);

@@ -2,7 +2,9 @@
 // splatting", Sec. III-B-2), in two kernels:
 //
 // K7 blend_backward_kernel: one CTA per tile replays the tile's list back to
-//   front from each pixel's last blended position, recovering T_i = T_{i+1} /
+//   front from the last entry each pixel walked before it stopped (the entry
+//   that stopped it is not blended; entries that do not pass the alpha test
+//   are skipped as in the forward), recovering T_i = T_{i+1} /
 //   (1 - alpha_i) from the stored final T (no per-pixel lists are kept), with
 //   G = dL/dC and B = the colour behind (B <- alpha c + (1 - alpha) B):
 //     dL/dc_i = alpha_i T_i G,   dL/dalpha_i = T_i G.(c_i - B)

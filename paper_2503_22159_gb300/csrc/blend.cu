@@ -164,7 +164,9 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
         const float pxf = (float)px + 0.5f;
         const float2 pxf2 = make_float2(pxf, pxf);
         float2 pyf[NP], T[NP], c0[NP], c1[NP], c2[NP];
-        uint32_t last[PX], stop[PX];
+        // walked[i]: list entries the pixel walks before the one at which it stops (the
+        // whole list if it never stops); the backward replays those entries
+        uint32_t walked[PX], stop[PX];
         float thr[PX];   // per-pixel pass threshold of q: log2(1/255), +inf once the pixel has stopped
         uint2 rg = v.ranges[tile];
         rg.y = min(rg.y, cap);   // ranges are written clamped; this keeps every read in bounds regardless
@@ -177,7 +179,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
         }
 #pragma unroll
         for (int i = 0; i < PX; i++) {
-            last[i] = 0u;
+            walked[i] = rg.y - rg.x;
             stop[i] = rg.y - rg.x;   // COUNT only
             thr[i] = (px < width && py + i < height) ? kLog2AlphaMin : kInf;
         }
@@ -260,8 +262,6 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                         c1[j] = f2_fma(w, make_float2(rgc.z, rgc.w), c1[j]);
                         c2[j] = f2_fma(w, bl, c2[j]);
                     }
-#pragma unroll
-                    for (int i = 0; i < PX; i++) last[i] = e[i] ? pos : last[i];
                     if (COUNT) {
 #pragma unroll
                         for (int i = 0; i < PX; i++) n_blend += (uint32_t)e[i];
@@ -271,16 +271,20 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     for (int j = 0; j < NP; j++) {
                         const bool sa = test[j].x < kTMin, sb = test[j].y < kTMin;
                         const bool ba = e[2 * j] && !sa, bb = e[2 * j + 1] && !sb;
-                        if (sa) thr[2 * j] = kInf;
-                        if (sb) thr[2 * j + 1] = kInf;
+                        if (sa) {
+                            thr[2 * j] = kInf;
+                            walked[2 * j] = pos - 1u;
+                        }
+                        if (sb) {
+                            thr[2 * j + 1] = kInf;
+                            walked[2 * j + 1] = pos - 1u;
+                        }
                         const float2 w = f2_mul(make_float2(sa ? 0.0f : al[j].x, sb ? 0.0f : al[j].y), T[j]);
                         T[j].x = sa ? T[j].x : test[j].x;
                         T[j].y = sb ? T[j].y : test[j].y;
                         c0[j] = f2_fma(w, make_float2(rgc.x, rgc.y), c0[j]);
                         c1[j] = f2_fma(w, make_float2(rgc.z, rgc.w), c1[j]);
                         c2[j] = f2_fma(w, bl, c2[j]);
-                        if (ba) last[2 * j] = pos;
-                        if (bb) last[2 * j + 1] = pos;
                         if (COUNT) {
                             n_blend += (uint32_t)ba + (uint32_t)bb;
                             if (sa) stop[2 * j] = pos;
@@ -345,7 +349,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                 out_rgb[3 * p + 1] = (hi ? c1[j].y : c1[j].x) + Ti * bg1;
                 out_rgb[3 * p + 2] = (hi ? c2[j].y : c2[j].x) + Ti * bg2;
                 v.final_T[p] = Ti;
-                v.n_contrib[p] = last[i];
+                v.n_contrib[p] = walked[i];
             }
         }
     }
