@@ -108,8 +108,9 @@ typedef struct {
     int64_t tiles_touched;       /* N uint32                                                 */
     int64_t rect;                /* N x 4 uint16: x0, x1, y0, y1 (inclusive tile indices)    */
     int64_t depth_order;         /* N uint32: Gaussian ids sorted by (depth key, id)         */
-    int64_t tile_keys;           /* key_capacity uint32, sorted by tile: (tile << id_bits) | id
-                                    when packed, else the tile id                               */
+    int64_t tile_keys;           /* key_capacity uint32, sorted by tile: (tile key << id_bits) | id
+                                    when packed, else the tile key; tile key =
+                                    (tile row << col_bits) | tile column                       */
     int64_t tile_vals;           /* key_capacity uint32 Gaussian ids when not packed, else -1  */
     int64_t ranges;              /* tiles x 2 uint32: [start, end) of each tile's list        */
     int64_t final_T;             /* H x W float: transmittance after the last blend           */
@@ -119,7 +120,8 @@ typedef struct {
     int32_t tiles_x, tiles_y;
     int32_t depth_passes, tile_passes;
     int32_t id_bits;             /* ceil(log2 N) */
-    int32_t packed;              /* 1: pairs packed in one uint32 (tile bits + id_bits <= 32) */
+    int32_t packed;              /* 1: pairs packed in one uint32 (tile key bits + id_bits <= 32) */
+    int32_t col_bits;            /* ceil(log2 tiles_x): bits of the column in a tile key      */
 } d4dgs_layout;
 
 /* Bytes of workspace for N Gaussians, this camera and config, and room for
@@ -147,10 +149,10 @@ int d4dgs_preprocess(const d4dgs_scene *scene, const d4dgs_camera *cam, float t,
 
 /* Stage 2 -- binning of the preprocessed frame (the 3DGS fast rasteriser's
  * tile/depth ordering, Sec. III-B-2): onesweep radix sort of the depth keys,
- * exclusive scan of the tile counts in depth order fused with the
- * duplication of one (tile, Gaussian) pair per covered tile, onesweep radix
- * sort of the pairs by tile (stable, so each tile's list stays in
- * (depth, id) order) and per-tile [start, end) ranges. */
+ * the duplication of one (tile, Gaussian) pair per covered tile in depth
+ * order straight into per-tile-column buckets, onesweep radix sort of the
+ * pairs by tile row (stable, so each tile's list stays in (depth, id) order)
+ * and per-tile [start, end) ranges.  Widths up to 2048 tiles. */
 int d4dgs_sort(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
                d4dgs_stream_t stream);
 

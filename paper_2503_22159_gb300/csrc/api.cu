@@ -78,11 +78,17 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.ntiles = l.tiles_x * l.tiles_y;
     l.pixels = (int64_t)cam->width * cam->height;
     l.depth_passes = 4;
-    l.tile_bits = ceil_log2(l.ntiles);
-    // at least two passes, so frames of different sizes (up to 65536 tiles) can share a batched launch
-    l.tile_passes = (l.tile_bits + 7) / 8 < 2 ? 2 : (l.tile_bits + 7) / 8;
-    int sh = 0;
-    for (int p = 0; p < l.tile_passes; p++) {
+    if (l.tiles_x > kMaxCols) return false;
+    l.col_bits = ceil_log2(l.tiles_x);
+    l.row_bits = ceil_log2(l.tiles_y);
+    l.tile_bits = l.col_bits + l.row_bits;
+    // pass 0: column buckets (emission); then >= 1 radix pass over the row bits
+    const int row_passes = (l.row_bits + 7) / 8 < 1 ? 1 : (l.row_bits + 7) / 8;
+    l.tile_passes = 1 + row_passes;
+    l.tile_shift[0] = 0;
+    l.tile_pass_bits[0] = l.col_bits;
+    int sh = l.col_bits;
+    for (int p = 1; p < l.tile_passes; p++) {
         const int left = l.tile_bits - sh, passes_left = l.tile_passes - p;
         const int b = (left + passes_left - 1) / passes_left;
         l.tile_shift[p] = sh;
@@ -99,9 +105,10 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.control = off; off += align256((int64_t)kCtlWords * 4);
     l.grid = off; off += align256((int64_t)(l.tiles_x + 1) * (l.tiles_y + 1) * 4);
     l.lb_depth = off; off += align256((int64_t)l.depth_passes * l.parts_depth * kRadix * 4);
-    l.lb_dup = off; off += align256(l.parts_dup * 8);
-    l.lb_tile = off; off += align256((int64_t)(l.tile_passes > 0 ? l.tile_passes : 1) * l.parts_tile * kRadix * 4);
+    l.lb_col = off; off += align256(l.parts_dup * l.tiles_x * 4);
+    l.lb_tile = off; off += align256((int64_t)(l.tile_passes - 1) * l.parts_tile * kRadix * 4);
     l.zero_end = off;
+    l.colbase = off; off += align256((int64_t)l.tiles_x * 4);
     l.batch = off; off += align256(kBatchAreaBytes);
     l.ranges = off; off += align256((int64_t)l.ntiles * 8);
     l.records = off; off += align256((int64_t)n * 48);
@@ -164,9 +171,11 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     x.grad2d = at<float>(ws, L.grad2d);
     x.lb_depth = at<uint32_t>(ws, L.lb_depth);
     x.lb_tile = at<uint32_t>(ws, L.lb_tile);
-    x.lb_dup = at<unsigned long long>(ws, L.lb_dup);
+    x.lb_col = at<uint32_t>(ws, L.lb_col);
+    x.colbase = at<uint32_t>(ws, L.colbase);
     x.cap = (uint32_t)L.cap;
     x.id_bits = L.id_bits;
+    x.col_bits = L.col_bits;
     x.packed = L.packed ? 1 : 0;
     x.tile_passes = L.tile_passes;
     x.ntiles = L.ntiles;
@@ -242,6 +251,7 @@ int d4dgs_workspace_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_confi
     out->tile_passes = L.tile_passes;
     out->id_bits = L.id_bits;
     out->packed = L.packed ? 1 : 0;
+    out->col_bits = L.col_bits;
     return D4DGS_OK;
 }
 

@@ -25,6 +25,7 @@ constexpr float kK2Pad = 0.0008f;
 constexpr int kSortThreads = 256;
 constexpr int kTileIPT = 15;                              // pair keys per thread (tile passes)
 constexpr int kTileItems = kSortThreads * kTileIPT;       // 3840 pairs per partition
+constexpr int kMaxCols = 2048;                            // tile columns of a view (16384 px at 8-px tiles)
 constexpr int kDepthIPT = 4;                              // depth keys per thread: short partitions, so
 constexpr int kDepthItems = kSortThreads * kDepthIPT;     // the few-key depth passes spread over all SMs
 constexpr int kRadix = 256;                               // digit bins (<= 8 bits per pass)
@@ -51,18 +52,20 @@ struct Layout {
     int32_t n = 0, width = 0, height = 0, tile = 0, tiles_x = 0, tiles_y = 0, ntiles = 0;
     int64_t pixels = 0;
     int32_t depth_passes = 4;
-    int32_t tile_bits = 0, tile_passes = 0;
+    // tile key = (row << col_bits) | column; pass 0 of the tile sort is the
+    // column bucketing done by the emission, passes 1.. sort by row bits
+    int32_t col_bits = 0, row_bits = 0, tile_bits = 0, tile_passes = 0;
     int32_t tile_shift[3] = {0, 0, 0}, tile_pass_bits[3] = {0, 0, 0};
-    // pairs are packed as (tile << id_bits | id) in one uint32 when they fit,
-    // else kept as a tile key plus a separate Gaussian-id value
+    // pairs are packed as (tile key << id_bits | id) in one uint32 when they
+    // fit, else kept as a tile key plus a separate Gaussian-id value
     int32_t id_bits = 0;
     bool packed = true;
     int64_t cap = 0;
     int64_t parts_depth = 0, parts_dup = 0, parts_tile = 0;
     // zero-initialised region [0, zero_end)
-    int64_t control = 0, grid = 0, lb_depth = 0, lb_dup = 0, lb_tile = 0, zero_end = 0;
+    int64_t control = 0, grid = 0, lb_depth = 0, lb_col = 0, lb_tile = 0, zero_end = 0;
     // the rest
-    int64_t ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
+    int64_t colbase = 0, ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
     int64_t final_T = 0, n_contrib = 0, grad2d = 0, batch = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
     int64_t total = 0;
     int32_t grid_w() const { return tiles_x + 1; }
@@ -112,10 +115,10 @@ struct View {
     uint32_t *n_contrib;
     float *grad2d;
     uint32_t *tkeys[2], *tvals[2];
-    uint32_t *lb_depth, *lb_tile;
-    unsigned long long *lb_dup;
+    uint32_t *lb_depth, *lb_tile, *lb_col;
+    uint32_t *colbase;               // first position of each tile column's bucket (clamped to cap)
     uint32_t cap;
-    int32_t id_bits, packed, tile_passes, ntiles;
+    int32_t id_bits, col_bits, packed, tile_passes, ntiles;
     int32_t tile_shift[3];
     uint32_t tile_mask[3];
     int32_t parts_depth, parts_dup, parts_tile;

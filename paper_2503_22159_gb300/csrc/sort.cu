@@ -1,24 +1,27 @@
 // sort.cu -- binning of the preprocessed frame into per-tile, depth-ordered
-// lists (the 3DGS fast rasteriser's (tile | depth) ordering, Sec. III-B-2):
+// lists (the 3DGS fast rasteriser's (tile | depth) ordering, Sec. III-B-2).
+// A tile is keyed (row << col_bits) | column, which orders tiles row-major.
 //
 //   0. tilecount: the per-tile pair counts, accumulated by the preprocess as a
 //      2D difference grid (4 atomics per Gaussian rectangle), are integrated
 //      into counts, exclusive-scanned into each tile's [start, end) range and
-//      reduced into the digit histograms of every tile-sort pass; no pass over
-//      the pairs is needed for either;
+//      into the first position of each tile column's bucket, and reduced into
+//      the digit histograms of the row passes; no pass over the pairs is
+//      needed for any of them;
 //   1. onesweep LSD radix sort of the N depth keys (4 passes of 8 bits; the
 //      first pass generates the Gaussian ids as values): Gaussians in
 //      (depth, id) order;
-//   2. emit: exclusive scan of the tile counts in that order (chained scan with
-//      decoupled look-back over 256-Gaussian partitions) fused with the
-//      emission of one pair per covered tile, a warp per Gaussian writing its
-//      pairs as one coalesced run.  A pair is packed as (tile << id_bits | id)
-//      in one uint32 when it fits (otherwise tile key + id value);
-//   3. onesweep LSD radix sort of the pairs by their tile bits
-//      (ceil(log2 tiles) bits in <= 8-bit passes).  The sort is stable, so
-//      every tile's list stays in (depth, id) order -- the order a
-//      (tile << 32 | depth) sort gives, with 4-byte instead of 12-byte records
-//      and 2 passes instead of 6 at 1352x1014 / 16 px.
+//   2. emit: one pair per covered tile, written in that order straight into
+//      its tile column's bucket (per-column prefixes over 256-Gaussian
+//      partitions with decoupled look-back), which is the first, column, pass
+//      of an LSD sort by tile key.  A pair is packed as
+//      (tile key << id_bits | id) in one uint32 when it fits (otherwise tile
+//      key + id value);
+//   3. onesweep LSD radix sort of the pairs by the row bits of their tile key
+//      (one 8-bit pass up to 256 tile rows).  Every step is stable, so each
+//      tile's list ends in (depth, id) order -- the order a
+//      (tile << 32 | depth) sort gives, with 4-byte records and one pass over
+//      the pairs instead of six.
 //
 // Each onesweep pass is one persistent launch: CTAs take partitions in launch
 // order from an atomic counter, rank their keys with warp match-any, publish
@@ -36,10 +39,6 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1u;
-constexpr unsigned long long kFlagAgg64 = 1ull << 62;
-constexpr unsigned long long kFlagInc64 = 2ull << 62;
-constexpr unsigned long long kFlagMask64 = 3ull << 62;
-constexpr unsigned long long kValMask64 = (1ull << 62) - 1ull;
 constexpr int kLookAhead = 8;   // predecessor entries read per look-back round trip
 
 // Exclusive scan of one value per thread over a 256-thread block; returns the
@@ -135,7 +134,7 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
         const uint32_t count = TILE ? min(v.ctl[kCtlNumKeys], v.cap) : (uint32_t)v.n;
         const int shift = TILE ? (v.packed ? v.id_bits : 0) + v.tile_shift[pass] : 8 * pass;
         const uint32_t mask = TILE ? v.tile_mask[pass] : 0xFFu;
-        uint32_t *lookback = TILE ? v.lb_tile + (size_t)pass * v.parts_tile * kRadix
+        uint32_t *lookback = TILE ? v.lb_tile + (size_t)(pass - 1) * v.parts_tile * kRadix
                                   : v.lb_depth + (size_t)pass * v.parts_depth * kRadix;
         uint32_t *status = v.ctl + kCtlStatus;
         if (vi != cur) {   // exclusive digit offsets of this view's pass
@@ -244,9 +243,9 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
     }
 }
 
-// Per-tile pair counts from the view's 2D difference grid; ranges; digit
-// histograms of the tile passes; the total K and the capacity check.  One CTA
-// per view.
+// Per-tile pair counts from the view's 2D difference grid; ranges; the first
+// position of every tile column's bucket; digit histograms of the row passes;
+// the total K and the capacity check.  One CTA per view.
 __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, int smem_cells) {
     __shared__ unsigned long long s_warp[32];
     __shared__ uint32_t s_hist[3 * kRadix];
@@ -268,9 +267,9 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
     uint2 *ranges = v.ranges;
     uint32_t *ctl = v.ctl;
     const uint32_t cap = v.cap;
-    const int tile_passes = v.tile_passes;
-    const int sh0 = v.tile_shift[0], sh1 = v.tile_shift[1], sh2 = v.tile_shift[2];
-    const uint32_t mk0 = v.tile_mask[0], mk1 = v.tile_mask[1], mk2 = v.tile_mask[2];
+    const int tile_passes = v.tile_passes, col_bits = v.col_bits;
+    const int sh1 = v.tile_shift[1], sh2 = v.tile_shift[2];
+    const uint32_t mk1 = v.tile_mask[1], mk2 = v.tile_mask[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     const int gw = tiles_x + 1, gh = tiles_y + 1;
     for (int i = tid; i < 3 * kRadix; i += nt) s_hist[i] = 0;
@@ -284,57 +283,129 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
         for (int y = 0; y < gh; y++) { acc += grid[y * gw + c]; grid[y * gw + c] = acc; }
     }
     __syncthreads();
+
+    // block-wide exclusive scan of one 64-bit value per thread; returns (prefix, total)
+    auto block_scan = [&](unsigned long long mine, unsigned long long *total) {
+        unsigned long long x = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        unsigned long long before = 0, all = 0;
+        for (int w = 0; w < nt / 32; w++) {
+            if (w < warp) before += s_warp[w];
+            all += s_warp[w];
+        }
+        __syncthreads();
+        *total = all;
+        return before + x - mine;
+    };
+
     // exclusive scan over tiles in row-major order, one contiguous chunk per thread
     const int ntiles = tiles_x * tiles_y;
     const int chunk = (ntiles + nt - 1) / nt;
     const int t0 = min(tid * chunk, ntiles), t1 = min(t0 + chunk, ntiles);
     unsigned long long sum = 0;
     for (int t = t0; t < t1; t++) sum += (unsigned)grid[(t / tiles_x) * gw + (t % tiles_x)];
-    unsigned long long x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    unsigned long long before = 0, all = 0;
-    for (int w = 0; w < nt / 32; w++) {
-        if (w < warp) before += s_warp[w];
-        all += s_warp[w];
-    }
-    unsigned long long run = before + x - sum;
+    unsigned long long all;
+    unsigned long long run = block_scan(sum, &all);
     for (int t = t0; t < t1; t++) {
-        const uint32_t c = (uint32_t)grid[(t / tiles_x) * gw + (t % tiles_x)];
-        const unsigned long long a = run < cap ? run : cap, b = run + c < cap ? run + c : cap;
+        const int r = t / tiles_x, c = t % tiles_x;
+        const uint32_t cnt = (uint32_t)grid[r * gw + c];
+        const unsigned long long a = run < cap ? run : cap, b = run + cnt < cap ? run + cnt : cap;
         ranges[t] = make_uint2((uint32_t)a, (uint32_t)b);
-        // digit counts of the pairs that fit in the capacity (the ones that get sorted)
-        const uint32_t kept = (uint32_t)(b - a);
-        if (kept) {
-            atomicAdd(&s_hist[(t >> sh0) & mk0], kept);
-            if (tile_passes > 1) atomicAdd(&s_hist[kRadix + ((t >> sh1) & mk1)], kept);
-            if (tile_passes > 2) atomicAdd(&s_hist[2 * kRadix + ((t >> sh2) & mk2)], kept);
+        // digit counts of the row passes (keys (row << col_bits) | column)
+        if (cnt) {
+            const uint32_t tk = ((uint32_t)r << col_bits) | (uint32_t)c;
+            atomicAdd(&s_hist[kRadix + ((tk >> sh1) & mk1)], cnt);
+            if (tile_passes > 2) atomicAdd(&s_hist[2 * kRadix + ((tk >> sh2) & mk2)], cnt);
         }
-        run += c;
+        run += cnt;
+    }
+    // column buckets: exclusive scan of the column totals, two columns per thread
+    unsigned long long csum[2] = {0, 0};
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int c = 2 * tid + k;
+        if (c < tiles_x)
+            for (int r = 0; r < tiles_y; r++) csum[k] += (unsigned)grid[r * gw + c];
+    }
+    unsigned long long call;
+    const unsigned long long cbase = block_scan(csum[0] + csum[1], &call);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int c = 2 * tid + k;
+        const unsigned long long b = cbase + (k ? csum[0] : 0ull);
+        if (c < tiles_x) v.colbase[c] = (uint32_t)(b < cap ? b : cap);
     }
     __syncthreads();
-    for (int i = tid; i < tile_passes * kRadix; i += nt) ctl[kCtlTileHist + i] = s_hist[i];
+    for (int i = kRadix + tid; i < tile_passes * kRadix; i += nt) ctl[kCtlTileHist + i] = s_hist[i];
     if (tid == 0) {
         ctl[kCtlNumKeys] = all > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)all;
         if (all > cap) atomicOr(ctl + kCtlStatus, kStatusCapacity);
     }
 }
 
-// Scan of the tile counts in depth order fused with the pair emission, over
-// 256-Gaussian partitions of every view of the launch.
-__global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba) {
-    __shared__ uint32_t s_off[kDupItems], s_cnt[kDupItems], s_id[kDupItems];
-    __shared__ ushort4 s_rect[kDupItems];
-    __shared__ uint32_t s_scan[8];
-    grid_dependency_wait();
-    __shared__ uint32_t s_part;
-    __shared__ unsigned long long s_excl;
+// Decoupled look-back by one thread over entries base[j * stride], j = from,
+// from - 1, ...: sums aggregates back to the first inclusive prefix, reading
+// kLookAhead entries per round trip; an entry not yet published is polled
+// again (bounded: on timeout the status word is latched and 0 is returned).
+__device__ __forceinline__ uint32_t lookback_serial(const uint32_t *base, size_t stride, int64_t from,
+                                                    uint32_t *status) {
+    uint32_t excl = 0, spins = 0;
+    int64_t j = from;
+    while (j >= 0) {
+        uint32_t val[kLookAhead];
+#pragma unroll
+        for (int a = 0; a < kLookAhead; a++) val[a] = j - a >= 0 ? ld_volatile_u32(base + (size_t)(j - a) * stride) : kFlagInc;
+        bool done = false, stalled = false;
+        int consumed = 0;
+#pragma unroll
+        for (int a = 0; a < kLookAhead; a++) {
+            if (done || stalled) continue;
+            const uint32_t flag = val[a] & kFlagMask;
+            if (flag == 0u) { stalled = true; continue; }
+            if (j - a < 0) { done = true; continue; }
+            excl += val[a] & kValMask;
+            if (flag == kFlagInc) done = true;
+            else ++consumed;
+        }
+        if (done) break;
+        j -= consumed;
+        if (stalled) {
+            if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); return 0u; }
+            if (spins > 32) __nanosleep(64);
+        }
+    }
+    return excl;
+}
 
+// Pair emission in depth order straight into per-tile-column buckets (pass 0
+// of the tile sort), over 256-Gaussian partitions of every view of the launch:
+//   1. per warp (32 consecutive Gaussians of the depth order) and tile column,
+//      the pairs the warp's Gaussians put in that column;
+//   2. per column: exclusive prefix over the warps, the partition's total, and
+//      the partition's offset within the column's bucket by decoupled
+//      look-back over the preceding partitions;
+//   3. each warp writes its Gaussians' pairs in order: the pairs of Gaussian g
+//      in column c go to colbase[c] + (pairs of c from earlier partitions,
+//      warps and Gaussians) + (row - y0), so each column bucket holds its
+//      pairs in (depth, id) order and, within one Gaussian, by row; a
+//      Gaussian's pairs of one column are consecutive positions written by
+//      consecutive lanes.
+// The stable row passes that follow leave every tile's list in (depth, id)
+// order.
+__global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba) {
+    static_assert(kDupThreads == 256 && kDupItems == 256, "8 warps of 32 Gaussians per partition");
+    extern __shared__ uint32_t s_dyn[];   // [8][kMaxCols] per-warp column counts, then [kMaxCols] bases
+    __shared__ uint32_t s_id[kDupItems];
+    __shared__ ushort4 s_rect[kDupItems];
+    __shared__ uint32_t s_part;
+    grid_dependency_wait();
+    uint32_t *s_base = s_dyn + 8 * kMaxCols;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
     const int nviews = (int)bw[kBaNViews];
@@ -351,109 +422,105 @@ __global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba
             if ((uint32_t)view_of(ba, u).dup_part_base <= g) vi = u;
         const View &v = view_of(ba, vi);
         const uint32_t part = g - (uint32_t)v.dup_part_base;
-        const uint32_t n = (uint32_t)v.n;
+        const uint32_t n = (uint32_t)v.n, cap = v.cap;
+        const int ncols = v.cam.tiles_x;
         const uint32_t *order = v.dvals[0];   // after the 4 depth passes
         const uint32_t pos = part * kDupItems + tid;
-        uint32_t id = 0, c = 0;
-        ushort4 r = make_ushort4(0, 0, 0, 0);
+        uint32_t id = 0;
+        ushort4 r = make_ushort4(1, 0, 0, 0);   // empty: x0 > x1
         if (pos < n) {
             id = order[pos];
             if (id < n) {   // always true unless an earlier pass gave up on a spin-wait
-                c = v.tiles_touched[id];
-                if (c) r = v.rect[id];
+                if (v.tiles_touched[id]) r = v.rect[id];
             } else {
                 id = 0;
             }
         }
-        uint32_t ptotal;
-        const uint32_t local = block_exclusive_scan_256(c, s_scan, &ptotal);
-        s_off[tid] = local;
-        s_cnt[tid] = c;
+        // rectangles are clamped to the grid by the preprocess; clamp again for shared-memory indices
+        r.y = (unsigned short)min((int)r.y, ncols - 1);
+        r.w = (unsigned short)min((int)r.w, v.cam.tiles_y - 1);
         s_id[tid] = id;
         s_rect[tid] = r;
-        if (warp == 0) {
-            // warp-wide decoupled look-back: lane l reads predecessor j - l; the warp sums
-            // the aggregates of the lanes before the first inclusive prefix (bounded polling)
-            unsigned long long excl = 0;
-            unsigned long long *lb = v.lb_dup + part;
-            if (lane == 0) st_volatile_u64(lb, (part == 0 ? kFlagInc64 : kFlagAgg64) | (unsigned long long)ptotal);
-            if (part > 0) {
-                int64_t j = (int64_t)part - 1;
-                uint32_t spins = 0;
-                while (j >= 0) {
-                    const int64_t jj = j - lane;
-                    const unsigned long long val = jj >= 0 ? ld_volatile_u64(v.lb_dup + jj) : kFlagInc64;
-                    const unsigned long long flag = val & kFlagMask64;
-                    const uint32_t inc = __ballot_sync(0xFFFFFFFFu, flag == kFlagInc64);
-                    const uint32_t empty = __ballot_sync(0xFFFFFFFFu, flag == 0ull);
-                    const uint32_t stop = inc | empty;
-                    const int first = stop ? __ffs(stop) - 1 : 32;   // lanes before it hold aggregates
-                    unsigned long long take = 0;
-                    if (lane < first || (lane == first && (inc >> lane) & 1u)) take = val & kValMask64;
-                    if (jj < 0) take = 0;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) take += __shfl_xor_sync(0xFFFFFFFFu, take, o);
-                    excl += take;
-                    if (first < 32 && ((inc >> first) & 1u)) break;     // reached an inclusive prefix
-                    if (first < 32) {                                   // an entry not yet published
-                        j -= first;
-                        if (++spins > kSpinLimit) {
-                            if (lane == 0) atomicOr(v.ctl + kCtlStatus, kStatusTimeout);
-                            break;
-                        }
-                        if (spins > 32) __nanosleep(64);
-                    } else {
-                        j -= 32;
-                    }
-                }
-                if (lane == 0) st_volatile_u64(lb, kFlagInc64 | ((excl + ptotal) & kValMask64));
-            }
-            if (lane == 0) s_excl = excl;
+        for (int w = 0; w < 8; w++)
+            for (int c = tid; c < ncols; c += kDupThreads) s_dyn[w * kMaxCols + c] = 0u;
+        __syncthreads();
+        // ---- 1. per-warp column counts
+        if (r.x <= r.y) {
+            const uint32_t h = (uint32_t)r.w - (uint32_t)r.z + 1u;
+            for (int c = r.x; c <= r.y; c++) atomicAdd(&s_dyn[warp * kMaxCols + c], h);
         }
         __syncthreads();
-        // ---- emission: warp w writes the pairs of Gaussians w*32 .. w*32+31, one run each
-        const unsigned long long gexcl = s_excl;
-        const int tiles_x = v.cam.tiles_x, id_bits = v.id_bits;
+        // ---- 2. warp prefixes, partition totals, look-back per column
+        for (int c = tid; c < ncols; c += kDupThreads) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                const uint32_t x = s_dyn[w * kMaxCols + c];
+                s_dyn[w * kMaxCols + c] = run;
+                run += x;
+            }
+            uint32_t *lb = v.lb_col + (size_t)part * ncols + c;
+            st_volatile_u32(lb, (part == 0 ? kFlagInc : kFlagAgg) | (run & kValMask));
+            uint32_t excl = 0;
+            if (part > 0) {
+                excl = lookback_serial(v.lb_col + c, (size_t)ncols, (int64_t)part - 1, v.ctl + kCtlStatus);
+                st_volatile_u32(lb, kFlagInc | ((excl + run) & kValMask));
+            }
+            const unsigned long long b = (unsigned long long)v.colbase[c] + excl;
+            s_base[c] = (uint32_t)(b < cap ? b : cap);
+        }
+        __syncthreads();
+        // ---- 3. emission, warp w: Gaussians w*32 .. w*32+31 in order
+        const int id_bits = v.id_bits, col_bits = v.col_bits;
         const bool packed = v.packed != 0;
-        const unsigned long long cap = v.cap;
-        uint32_t *keys_out = v.tkeys[0], *vals_out = v.tvals[0];
+        uint32_t *keys_out = v.tkeys[1], *vals_out = v.tvals[1];
+        uint32_t *wcnt = s_dyn + warp * kMaxCols;
         for (int q = warp * 32; q < warp * 32 + 32; q++) {
-            const uint32_t cq = s_cnt[q];
-            if (!cq) continue;
             const ushort4 rq = s_rect[q];
+            if (rq.x > rq.y) continue;
             const uint32_t gid = s_id[q];
-            const int wdt = (int)rq.y - (int)rq.x + 1;
-            const float inv_w = 1.0f / (float)wdt;
-            const unsigned long long off = gexcl + s_off[q];
-            for (uint32_t j = lane; j < cq; j += 32) {
-                int ty = __float2int_rz((float)j * inv_w);
-                int tx = (int)j - ty * wdt;
-                if (tx < 0) { ty--; tx += wdt; } else if (tx >= wdt) { ty++; tx -= wdt; }
-                const uint32_t tile = (uint32_t)(((int)rq.z + ty) * tiles_x + (int)rq.x + tx);
-                const unsigned long long o = off + j;
+            const int wdt = (int)rq.y - (int)rq.x + 1, hgt = (int)rq.w - (int)rq.z + 1;
+            const int cnt = wdt * hgt;
+            const float inv_h = 1.0f / (float)hgt;
+            for (int j = lane; j < cnt; j += 32) {
+                int cc = __float2int_rz((float)j * inv_h);
+                int rr = j - cc * hgt;
+                if (rr < 0) { cc--; rr += hgt; } else if (rr >= hgt) { cc++; rr -= hgt; }
+                const int c = (int)rq.x + cc;
+                const uint32_t o = s_base[c] + wcnt[c] + (uint32_t)rr;
                 if (o < cap) {
+                    const uint32_t tk = ((uint32_t)((int)rq.z + rr) << col_bits) | (uint32_t)c;
                     if (packed) {
-                        keys_out[o] = (tile << id_bits) | gid;
+                        keys_out[o] = (tk << id_bits) | gid;
                     } else {
-                        keys_out[o] = tile;
+                        keys_out[o] = tk;
                         vals_out[o] = gid;
                     }
                 }
             }
+            __syncwarp();
+            for (int c = (int)rq.x + lane; c <= (int)rq.y; c += 32) wcnt[c] += (uint32_t)hgt;
+            __syncwarp();
         }
         __syncthreads();
     }
 }
 
-int occupancy_blocks(const void *fn, int threads) {
+}  // namespace
+
+namespace {
+
+int occupancy_blocks(const void *fn, int threads, size_t smem = 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem) != cudaSuccess || b < 1) b = 1;
     return b;
 }
 
 }  // namespace
 
-int sort_launch_count(int n, int tile_passes) { return n == 0 ? 1 : 1 + 4 + 1 + tile_passes; }
+constexpr size_t kEmitSmem = (size_t)9 * kMaxCols * sizeof(uint32_t);
+
+int sort_launch_count(int n, int tile_passes) { return n == 0 ? 1 : 1 + 4 + 1 + (tile_passes - 1); }
 
 cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
     static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0, occ_emit = 0;
@@ -462,7 +529,8 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
         occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false, false>, kSortThreads);
         occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false, true>, kSortThreads);
         occ_tkv = occupancy_blocks((const void *)onesweep_kernel<true, false, true>, kSortThreads);
-        occ_emit = occupancy_blocks((const void *)emit_kernel, kDupThreads);
+        cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmitSmem);
+        occ_emit = occupancy_blocks((const void *)emit_kernel, kDupThreads, kEmitSmem);
     }
     // ---- 0. per-tile counts, ranges, tile digit histograms (always: ranges are written for every tile)
     // fixed grid (blocks beyond the table's view count return at once), so that a
@@ -485,10 +553,10 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
             e = launch_chained(onesweep_kernel<true, false, false>, occ_kv * num_sms, kSortThreads, 0, st, batch_area, p);
     }
     if (e != cudaSuccess) return e;
-    // ---- 2. scan + emission in depth order
-    e = launch_chained(emit_kernel, occ_emit * num_sms, kDupThreads, 0, st, batch_area);
-    // ---- 3. stable sort of the pairs by tile bits
-    for (int p = 0; p < args.tile_passes && e == cudaSuccess; p++) {
+    // ---- 2. emission in depth order into tile-column buckets (tile pass 0)
+    e = launch_chained(emit_kernel, occ_emit * num_sms, kDupThreads, kEmitSmem, st, batch_area);
+    // ---- 3. stable sort of the pairs by tile-row bits (tile passes 1..)
+    for (int p = 1; p < args.tile_passes && e == cudaSuccess; p++) {
         if (args.packed)
             e = launch_chained(onesweep_kernel<false, false, true>, occ_k * num_sms, kSortThreads, 0, st, batch_area, p);
         else

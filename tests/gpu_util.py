@@ -44,11 +44,13 @@ def gpu_lists(r, cam):
     ntiles = L["tiles_x"] * L["tiles_y"]
     keys = _u32(r, "tile_keys", k, cam)
     if L["packed"]:
-        tiles = keys >> np.uint32(L["id_bits"])
+        tkey = keys >> np.uint32(L["id_bits"])
         ids = keys & np.uint32((1 << L["id_bits"]) - 1)
     else:
-        tiles = keys
+        tkey = keys
         ids = _u32(r, "tile_vals", k, cam)
+    # tile key = (row << col_bits) | column
+    tiles = (tkey >> np.uint32(L["col_bits"])) * np.uint32(L["tiles_x"]) + (tkey & np.uint32((1 << L["col_bits"]) - 1))
     ranges = _u32(r, "ranges", 2 * ntiles, cam).reshape(ntiles, 2)
     return dict(tile=tiles, id=ids, ranges=ranges, stats=st, packed=bool(L["packed"]))
 

@@ -66,15 +66,18 @@ def test_workspace_bytes_monotone_and_layout(d4):
         d4.d4dgs_workspace_layout(300_000, cam, cfg, b0 - 1)
 
 
-@pytest.mark.parametrize("w,h,tile,passes", [(128, 128, 16, 2), (1352, 1014, 16, 2), (2704, 2028, 8, 3),
-                                             (16, 16, 16, 2), (7, 5, 32, 2), (4096, 4096, 8, 3)])
+@pytest.mark.parametrize("w,h,tile,passes", [(128, 128, 16, 2), (1352, 1014, 16, 2), (2704, 2028, 8, 2),
+                                             (16, 16, 16, 2), (7, 5, 32, 2), (4096, 4096, 8, 3),
+                                             (16384, 2048, 8, 2)])
 def test_tile_pass_count(d4, w, h, tile, passes):
+    """Pass 0 buckets the pairs by tile column; 8-bit passes over the row bits follow (at least one)."""
     cam = synth.pinhole(w, h)
     cfg = d4.config_struct(tile, 64)
     L = d4.d4dgs_workspace_layout(10, cam, cfg, d4.d4dgs_workspace_bytes(10, cam, cfg, 100))
-    ntiles = math.ceil(w / tile) * math.ceil(h / tile)
+    cols, rows = math.ceil(w / tile), math.ceil(h / tile)
     assert L["tile_passes"] == passes
-    assert 2 ** (8 * passes) >= ntiles
+    assert 2 ** (8 * (passes - 1)) >= rows
+    assert 2 ** L["col_bits"] >= cols > 2 ** (L["col_bits"] - 1) or cols == 1
 
 
 def test_invalid_arguments_rejected_on_host(d4):
@@ -111,15 +114,16 @@ def test_invalid_arguments_rejected_on_host(d4):
 def test_launch_count(d4):
     cam = synth.pinhole(1352, 1014)
     cfg = d4.config_struct(16, 256)
-    # clear + preprocess + tile counts + 4 depth passes + scan/emit + 2 tile passes + blend
-    assert d4.d4dgs_launches_per_frame(300_000, cam, cfg) == 11
+    # clear + preprocess + tile counts + 4 depth passes + column emit + 1 row pass + blend
+    assert d4.d4dgs_launches_per_frame(300_000, cam, cfg) == 10
 
 
 def test_packing_decision(d4):
     cfg8 = d4.config_struct(8, 64)
     cam = synth.pinhole(2560, 2048)
     L = d4.d4dgs_workspace_layout(40_000, cam, cfg8, d4.d4dgs_workspace_bytes(40_000, cam, cfg8, 1000))
-    assert L["id_bits"] == 16 and L["packed"] == 0 and L["tile_vals"] > 0 and L["tile_passes"] == 3
+    assert L["id_bits"] == 16 and L["packed"] == 0 and L["tile_vals"] > 0 and L["tile_passes"] == 2
+    assert L["col_bits"] == 9   # 320 tile columns, 256 rows: 9 + 8 + 16 bits do not fit 32
     L = d4.d4dgs_workspace_layout(20_000, cam, cfg8, d4.d4dgs_workspace_bytes(20_000, cam, cfg8, 1000))
     assert L["id_bits"] == 15 and L["packed"] == 1
 
