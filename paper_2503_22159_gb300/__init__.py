@@ -261,9 +261,9 @@ class BatchRenderer:
 
     @staticmethod
     def _class_key(host: torch.Tensor):
-        # nviews, tile, batch, packed, tile_passes (leading int32 fields of the encoded batch)
-        head = host[:20].view(torch.int32).tolist()
-        return (head[1], head[2], head[3], head[4])
+        # nviews, tile, batch, packed, tile_passes, column capacity (leading int32 fields of the encoded batch)
+        head = host[:24].view(torch.int32).tolist()
+        return (head[1], head[2], head[3], head[4], head[5])
 
 
 class Renderer:

@@ -193,6 +193,7 @@ bool finish_batch(BatchArgs *b) {
     if (b->nviews < 1 || b->nviews > kMaxViews) return false;
     int64_t chunks = 0, dparts = 0, uparts = 0, tiles = 0;
     b->max_n = 0;
+    b->col_cap = 32;
     b->packed = b->v[0].packed;
     b->tile_passes = b->v[0].tile_passes;
     for (int i = 0; i < b->nviews; i++) {
@@ -207,6 +208,7 @@ bool finish_batch(BatchArgs *b) {
         uparts += v.parts_dup;
         tiles += v.ntiles;
         if (v.n > b->max_n) b->max_n = v.n;
+        while (b->col_cap < v.cam.tiles_x) b->col_cap *= 2;
     }
     if (chunks > INT32_MAX || tiles > INT32_MAX) return false;
     b->total_chunks = (int32_t)chunks;

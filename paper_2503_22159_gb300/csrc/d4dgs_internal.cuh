@@ -131,6 +131,7 @@ struct View {
 struct BatchArgs {
     int32_t nviews;
     int32_t tile, batch, packed, tile_passes;   // shared by every view of a launch
+    int32_t col_cap;                            // power of two >= every view's tile columns
     int32_t total_chunks, total_depth_parts, total_dup_parts, total_tiles;
     int32_t max_n;
     View v[kMaxViews];

@@ -39,7 +39,6 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kFlagMask = 3u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1u;
-constexpr int kLookAhead = 8;   // predecessor entries read per look-back round trip
 
 // Exclusive scan of one value per thread over a 256-thread block; returns the
 // exclusive prefix and writes the block total to *total.
@@ -63,6 +62,61 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
     *total = all;
     __syncthreads();
     return wsum + x - v;
+}
+
+// One round of a decoupled look-back by one thread: reads R entries
+// base[(j - a) * stride] at once, adds aggregates up to the first inclusive
+// prefix (or the start), and moves j past the aggregates it consumed.
+// Returns true when the prefix is complete; *stalled when an entry was not
+// yet published (the next round reads it again).
+template <int R>
+__device__ __forceinline__ bool lookback_round(const uint32_t *base, size_t stride, int64_t &j, uint32_t &excl,
+                                               bool &stalled) {
+    uint32_t val[R];
+#pragma unroll
+    for (int a = 0; a < R; a++) val[a] = j - a >= 0 ? ld_volatile_u32(base + (size_t)(j - a) * stride) : kFlagInc;
+    bool done = false;
+    int consumed = 0;
+    stalled = false;
+#pragma unroll
+    for (int a = 0; a < R; a++) {
+        if (done || stalled) continue;
+        const uint32_t flag = val[a] & kFlagMask;
+        if (flag == 0u) { stalled = true; continue; }
+        if (j - a < 0) { done = true; continue; }
+        excl += val[a] & kValMask;
+        if (flag == kFlagInc) done = true;
+        else ++consumed;
+    }
+    j -= consumed;
+    return done;
+}
+
+// Decoupled look-back by one thread over entries base[j * stride], j = from,
+// from - 1, ...: the exclusive prefix of the entry after `from`.  The first
+// round reads FIRST entries (usually enough: the predecessor has its
+// inclusive prefix), later rounds MORE at a time, so long chains of
+// aggregates -- partitions that all reach the look-back at once -- take few
+// round trips.  An unpublished entry is polled again (bounded: on timeout
+// the status word is latched and 0 is returned).
+template <int FIRST, int MORE>
+__device__ __forceinline__ uint32_t lookback_serial(const uint32_t *base, size_t stride, int64_t from,
+                                                    uint32_t *status) {
+    uint32_t excl = 0, spins = 0;
+    int64_t j = from;
+    if (j < 0) return 0u;
+    bool stalled;
+    if (lookback_round<FIRST>(base, stride, j, excl, stalled)) return excl;
+    for (;;) {
+        if (stalled) {
+            if (++spins > kSpinLimit) {
+                atomicOr(status, kStatusTimeout);
+                return 0u;
+            }
+            if (spins > 32) __nanosleep(64);
+        }
+        if (lookback_round<MORE>(base, stride, j, excl, stalled)) return excl;
+    }
 }
 
 // Partition bases of a pass over the views of a launch (prefix sums of each
@@ -188,35 +242,7 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
         s_local_start[d] = lstart;
         uint32_t excl = 0;
         if (part > 0) {
-            // decoupled look-back, reading up to kLookAhead predecessors per round trip:
-            // sum aggregates back to the first inclusive prefix; a not-yet-published
-            // entry is polled again (bounded)
-            int64_t j = (int64_t)part - 1;
-            uint32_t spins = 0;
-            while (j >= 0) {
-                uint32_t val[kLookAhead];
-#pragma unroll
-                for (int a = 0; a < kLookAhead; a++)
-                    val[a] = j - a >= 0 ? ld_volatile_u32(lookback + (size_t)(j - a) * kRadix + d) : kFlagInc;
-                bool done = false, stalled = false;
-                int consumed = 0;   // aggregates summed this round (entries j, j-1, ...)
-#pragma unroll
-                for (int a = 0; a < kLookAhead; a++) {
-                    if (done || stalled) continue;
-                    const uint32_t flag = val[a] & kFlagMask;
-                    if (flag == 0u) { stalled = true; continue; }
-                    if (j - a < 0) { done = true; continue; }
-                    excl += val[a] & kValMask;
-                    if (flag == kFlagInc) done = true;
-                    else ++consumed;
-                }
-                if (done) break;
-                j -= consumed;
-                if (stalled) {
-                    if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); break; }
-                    if (spins > 32) __nanosleep(64);
-                }
-            }
+            excl = lookback_serial<8, 8>(lookback + d, kRadix, (int64_t)part - 1, status);
             st_volatile_u32(lb + d, kFlagInc | ((excl + bcount) & kValMask));
         }
         s_delta[d] = s_hist_excl[d] + excl - lstart;
@@ -349,40 +375,6 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
     }
 }
 
-// Decoupled look-back by one thread over entries base[j * stride], j = from,
-// from - 1, ...: sums aggregates back to the first inclusive prefix, reading
-// kLookAhead entries per round trip; an entry not yet published is polled
-// again (bounded: on timeout the status word is latched and 0 is returned).
-__device__ __forceinline__ uint32_t lookback_serial(const uint32_t *base, size_t stride, int64_t from,
-                                                    uint32_t *status) {
-    uint32_t excl = 0, spins = 0;
-    int64_t j = from;
-    while (j >= 0) {
-        uint32_t val[kLookAhead];
-#pragma unroll
-        for (int a = 0; a < kLookAhead; a++) val[a] = j - a >= 0 ? ld_volatile_u32(base + (size_t)(j - a) * stride) : kFlagInc;
-        bool done = false, stalled = false;
-        int consumed = 0;
-#pragma unroll
-        for (int a = 0; a < kLookAhead; a++) {
-            if (done || stalled) continue;
-            const uint32_t flag = val[a] & kFlagMask;
-            if (flag == 0u) { stalled = true; continue; }
-            if (j - a < 0) { done = true; continue; }
-            excl += val[a] & kValMask;
-            if (flag == kFlagInc) done = true;
-            else ++consumed;
-        }
-        if (done) break;
-        j -= consumed;
-        if (stalled) {
-            if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); return 0u; }
-            if (spins > 32) __nanosleep(64);
-        }
-    }
-    return excl;
-}
-
 // Pair emission in depth order straight into per-tile-column buckets (pass 0
 // of the tile sort), over 256-Gaussian partitions of every view of the launch:
 //   1. per warp (32 consecutive Gaussians of the depth order) and tile column,
@@ -398,14 +390,14 @@ __device__ __forceinline__ uint32_t lookback_serial(const uint32_t *base, size_t
 //      consecutive lanes.
 // The stable row passes that follow leave every tile's list in (depth, id)
 // order.
-__global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba) {
+__global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__ ba, int col_cap) {
     static_assert(kDupThreads == 256 && kDupItems == 256, "8 warps of 32 Gaussians per partition");
-    extern __shared__ uint32_t s_dyn[];   // [8][kMaxCols] per-warp column counts, then [kMaxCols] bases
+    extern __shared__ uint32_t s_dyn[];   // [8][col_cap] per-warp column counts, then [col_cap] bases
     __shared__ uint32_t s_id[kDupItems];
     __shared__ ushort4 s_rect[kDupItems];
     __shared__ uint32_t s_part;
     grid_dependency_wait();
-    uint32_t *s_base = s_dyn + 8 * kMaxCols;
+    uint32_t *s_base = s_dyn + 8 * col_cap;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
     const int nviews = (int)bw[kBaNViews];
@@ -424,6 +416,11 @@ __global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba
         const uint32_t part = g - (uint32_t)v.dup_part_base;
         const uint32_t n = (uint32_t)v.n, cap = v.cap;
         const int ncols = v.cam.tiles_x;
+        if (ncols > col_cap) {   // a table with wider views than this launch was sized for
+            if (tid == 0) atomicOr(v.ctl + kCtlStatus, kStatusCapacity);
+            __syncthreads();
+            continue;
+        }
         const uint32_t *order = v.dvals[0];   // after the 4 depth passes
         const uint32_t pos = part * kDupItems + tid;
         uint32_t id = 0;
@@ -442,12 +439,12 @@ __global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba
         s_id[tid] = id;
         s_rect[tid] = r;
         for (int w = 0; w < 8; w++)
-            for (int c = tid; c < ncols; c += kDupThreads) s_dyn[w * kMaxCols + c] = 0u;
+            for (int c = tid; c < ncols; c += kDupThreads) s_dyn[w * col_cap + c] = 0u;
         __syncthreads();
         // ---- 1. per-warp column counts
         if (r.x <= r.y) {
             const uint32_t h = (uint32_t)r.w - (uint32_t)r.z + 1u;
-            for (int c = r.x; c <= r.y; c++) atomicAdd(&s_dyn[warp * kMaxCols + c], h);
+            for (int c = r.x; c <= r.y; c++) atomicAdd(&s_dyn[warp * col_cap + c], h);
         }
         __syncthreads();
         // ---- 2. warp prefixes, partition totals, look-back per column
@@ -455,15 +452,15 @@ __global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba
             uint32_t run = 0;
 #pragma unroll
             for (int w = 0; w < 8; w++) {
-                const uint32_t x = s_dyn[w * kMaxCols + c];
-                s_dyn[w * kMaxCols + c] = run;
+                const uint32_t x = s_dyn[w * col_cap + c];
+                s_dyn[w * col_cap + c] = run;
                 run += x;
             }
             uint32_t *lb = v.lb_col + (size_t)part * ncols + c;
             st_volatile_u32(lb, (part == 0 ? kFlagInc : kFlagAgg) | (run & kValMask));
             uint32_t excl = 0;
             if (part > 0) {
-                excl = lookback_serial(v.lb_col + c, (size_t)ncols, (int64_t)part - 1, v.ctl + kCtlStatus);
+                excl = lookback_serial<8, 8>(v.lb_col + c, (size_t)ncols, (int64_t)part - 1, v.ctl + kCtlStatus);
                 st_volatile_u32(lb, kFlagInc | ((excl + run) & kValMask));
             }
             const unsigned long long b = (unsigned long long)v.colbase[c] + excl;
@@ -474,7 +471,7 @@ __global__ void __launch_bounds__(kDupThreads) emit_kernel(char *__restrict__ ba
         const int id_bits = v.id_bits, col_bits = v.col_bits;
         const bool packed = v.packed != 0;
         uint32_t *keys_out = v.tkeys[1], *vals_out = v.tvals[1];
-        uint32_t *wcnt = s_dyn + warp * kMaxCols;
+        uint32_t *wcnt = s_dyn + warp * col_cap;
         for (int q = warp * 32; q < warp * 32 + 32; q++) {
             const ushort4 rq = s_rect[q];
             if (rq.x > rq.y) continue;
@@ -518,19 +515,20 @@ int occupancy_blocks(const void *fn, int threads, size_t smem = 0) {
 
 }  // namespace
 
-constexpr size_t kEmitSmem = (size_t)9 * kMaxCols * sizeof(uint32_t);
+// dynamic shared memory of the emission for a launch's column capacity
+constexpr size_t emit_smem(int col_cap) { return (size_t)9 * col_cap * sizeof(uint32_t); }
 
 int sort_launch_count(int n, int tile_passes) { return n == 0 ? 1 : 1 + 4 + 1 + (tile_passes - 1); }
 
 cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
-    static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0, occ_emit = 0;
+    static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0;
+    static int occ_emit[16] = {0};   // by log2 of the column capacity
     if (!occ_kv) {
         occ_iota = occupancy_blocks((const void *)onesweep_kernel<true, true, false>, kSortThreads);
         occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false, false>, kSortThreads);
         occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false, true>, kSortThreads);
         occ_tkv = occupancy_blocks((const void *)onesweep_kernel<true, false, true>, kSortThreads);
-        cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmitSmem);
-        occ_emit = occupancy_blocks((const void *)emit_kernel, kDupThreads, kEmitSmem);
+        cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
     }
     // ---- 0. per-tile counts, ranges, tile digit histograms (always: ranges are written for every tile)
     // fixed grid (blocks beyond the table's view count return at once), so that a
@@ -554,7 +552,12 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
     }
     if (e != cudaSuccess) return e;
     // ---- 2. emission in depth order into tile-column buckets (tile pass 0)
-    e = launch_chained(emit_kernel, occ_emit * num_sms, kDupThreads, kEmitSmem, st, batch_area);
+    int lc = 0;
+    while ((1 << lc) < args.col_cap) lc++;
+    if (args.col_cap > kMaxCols || lc >= 16) return cudaErrorInvalidValue;
+    if (!occ_emit[lc]) occ_emit[lc] = occupancy_blocks((const void *)emit_kernel, kDupThreads, emit_smem(args.col_cap));
+    e = launch_chained(emit_kernel, occ_emit[lc] * num_sms, kDupThreads, emit_smem(args.col_cap), st, batch_area,
+                       (int)args.col_cap);
     // ---- 3. stable sort of the pairs by tile-row bits (tile passes 1..)
     for (int p = 1; p < args.tile_passes && e == cudaSuccess; p++) {
         if (args.packed)
