@@ -285,6 +285,68 @@ def run_serving(args, dev, d4):
     return out
 
 
+def run_time_groups(args, dev, d4, w, scene, cfg, cap, peaks):
+    """Fixed viewpoint, several timestamps: one camera of the orbit rendered at B = 4 times as one
+    batch (a time group: the preprocess reads each Gaussian once for the 4 views) against the same 4
+    views rendered one by one.  Device time per frame of the preprocess stage and of whole frames,
+    L2 flushed before every repetition."""
+    import numpy as np
+    import torch
+    B, reps = 4, 20
+    stream = torch.cuda.current_stream(dev)
+    k0 = len(w.frames) // 2
+    cam = w.frames[k0][0]
+    times = [w.frames[k0 + j][1] for j in range(B)]
+    views = []
+    for t in times:
+        ws = torch.empty(d4.d4dgs_workspace_bytes(scene.n, cam, cfg, cap), dtype=torch.uint8, device=dev)
+        views.append((scene, cam, t, ws, torch.empty((cam.height, cam.width, 3), device=dev)))
+    br = d4.BatchRenderer(cfg, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        ms = []
+        for k in range(reps + 3):
+            torch.cuda._sleep(1_000_000)
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ms.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        return float(np.mean([a.elapsed_time(b) for a, b in ms[3:]]))
+
+    def single_pre():
+        for sc, c, t, ws, out in views:
+            d4.d4dgs_preprocess(sc, c, t, cfg, ws, stream)
+
+    def single_all():
+        for sc, c, t, ws, out in views:
+            d4.d4dgs_render(sc, c, t, cfg, ws, out, stream)
+
+    pre_group = timed(lambda: br.render_stages(views, 1, stream)) / B
+    pre_single = timed(single_pre) / B
+    all_group = timed(lambda: br.render(views, stream)) / B
+    all_single = timed(single_all) / B
+    for sc, c, t, ws, out in views:
+        if d4.d4dgs_read_stats(sc.n, c, cfg, ws)["status"] != 0:
+            raise RuntimeError("time-group frame reported an error")
+    n = scene.n
+    sh_bytes = 4 * 3 * (w.scene.sh_degree + 1) ** 2
+    read_b, write_b = n * (64 + sh_bytes), n * 64
+    gbs = lambda byts, ms: byts / (ms * 1e-3) / 1e9
+    return {"views": B, "camera_frame": k0, "times": [float(t) for t in times],
+            "preprocess_us_per_frame": {"group": 1e3 * pre_group, "single": 1e3 * pre_single},
+            "frame_us": {"group": 1e3 * all_group, "single": 1e3 * all_single},
+            "frames_per_s": {"group": 1e3 / all_group, "single": 1e3 / all_single},
+            "preprocess_roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                                    "bytes_per_frame_group": read_b / B + write_b,
+                                    "bytes_per_frame_single": read_b + write_b,
+                                    "achieved_group": gbs(read_b / B + write_b, pre_group),
+                                    "achieved_single": gbs(read_b + write_b, pre_single)}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -443,6 +505,10 @@ def run_ours(args):
         e2e = {"value": world * E / te, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": E, "api": "d4dgs_render_host"}
 
+    groups_out = None
+    if not args.no_serving and world == 1:
+        groups_out = run_time_groups(args, dev, d4, w, scene, cfg, r.key_capacity, peaks)
+
     serving_out = None
     if not args.no_serving and world == 1:
         serving_out = run_serving(args, dev, d4)
@@ -461,7 +527,7 @@ def run_ours(args):
         "keys_per_frame": {"mean": float(np.mean(nkeys)), "max": int(np.max(nkeys))},
         "gpu_launches": int(launches * K), "launches_per_frame": launches,
         "wall_s_timed_region": t_wall, "peaks": peak_kind,
-        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out,
+        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out, "time_groups": groups_out,
         "autotune": {"chosen": f"{args.tile}/{args.batch}", "ms_per_frame": tune_table} if tune_table else None,
     }
     print(json.dumps(line), flush=True)

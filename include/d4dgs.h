@@ -202,7 +202,13 @@ int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, flo
  * sequence of d4dgs_render_batch does not depend on the batch's contents and
  * can be captured once as a CUDA graph; with args_dev the first kernel reads
  * the descriptors from device memory, which the caller refreshes (e.g. by a
- * captured host-to-device copy) before each replay. */
+ * captured host-to-device copy) before each replay.
+ * Time groups: consecutive views (up to 4) with the same scene arrays and the
+ * same camera -- the paper's fixed-viewpoint multi-timestamp case (Alg. 1
+ * caches the camera-dependent terms; Sec. IV-C renders such frames in
+ * parallel) -- are preprocessed together: each Gaussian's parameters are read
+ * from DRAM once for all times of the group.  Every view's outputs are the
+ * same, bit for bit, as when it is rendered alone. */
 typedef struct {
     const d4dgs_scene *scene;    /* host struct of device arrays                     */
     d4dgs_camera cam;
@@ -229,6 +235,11 @@ int d4dgs_batch_encode(int32_t nviews, const d4dgs_view *views, const d4dgs_conf
  * d4dgs_read_stats on each view's workspace. */
 int d4dgs_render_batch(const void *args_host, const void *args_dev, void *batch_area, size_t batch_area_bytes,
                        d4dgs_stream_t stream);
+/* The stages of d4dgs_render_batch one at a time (profiling hook): stages is
+ * a bit set, 1 = clear + preprocess, 2 = binning, 4 = blend; a batch's stages
+ * must be launched in that order on one stream and batch_area. */
+int d4dgs_render_batch_stages(const void *args_host, const void *args_dev, void *batch_area,
+                              size_t batch_area_bytes, int32_t stages, d4dgs_stream_t stream);
 
 /* Synchronises `stream`, then copies the status word and counters of the
  * last frame rendered in `ws` into *out (host).  Returns out->status. */

@@ -220,6 +220,19 @@ class BatchRenderer:
         _abi.check(_abi.load().d4dgs_batch_encode(n, arr, ctypes.byref(self.cfg), ctypes.c_void_p(host.data_ptr()),
                                                   self.args_bytes), "d4dgs_batch_encode")
 
+    def render_stages(self, views, stages: int, stream=None):
+        """Launch some stages of an eager batch render (1 = preprocess, 2 = binning, 4 = blend; in that
+        order, on one stream): a profiling hook."""
+        stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        slot = self._slot(stream)
+        host = slot.setdefault("stage_host", torch.empty(self.args_bytes, dtype=torch.uint8))
+        if stages & 1:
+            self.encode(views, host)
+        _abi.check(_abi.load().d4dgs_render_batch_stages(ctypes.c_void_p(host.data_ptr()), None,
+                                                         ctypes.c_void_p(slot["area"].data_ptr()), self.area_bytes,
+                                                         int(stages), _stream_handle(stream)),
+                   "d4dgs_render_batch_stages")
+
     def render(self, views, stream=None, graph: bool = False):
         stream = torch.cuda.current_stream(self.device) if stream is None else stream
         slot = self._slot(stream)

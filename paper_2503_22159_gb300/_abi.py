@@ -90,6 +90,7 @@ PROTOTYPES = {
     "d4dgs_batch_area_bytes": (ctypes.c_size_t, []),
     "d4dgs_batch_encode": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_view), _P(d4dgs_config), _vp, ctypes.c_size_t]),
     "d4dgs_render_batch": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "d4dgs_render_batch_stages": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, ctypes.c_int32, _vp]),
     "d4dgs_launches_per_frame": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_camera), _P(d4dgs_config)]),
     "d4dgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -189,6 +189,14 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     *v = x;
 }
 
+// Same scene arrays and camera (the time may differ): views that can share one
+// read of each Gaussian in the preprocess.
+static bool same_scene_and_camera(const View &a, const View &b) {
+    return a.means == b.means && a.t_mean == b.t_mean && a.velocity == b.velocity && a.log_scales == b.log_scales &&
+           a.log_t_scale == b.log_t_scale && a.quats == b.quats && a.opacity_logit == b.opacity_logit &&
+           a.sh == b.sh && a.n == b.n && a.sh_degree == b.sh_degree && memcmp(&a.cam, &b.cam, sizeof(CamArgs)) == 0;
+}
+
 bool finish_batch(BatchArgs *b) {
     if (b->nviews < 1 || b->nviews > kMaxViews) return false;
     int64_t chunks = 0, dparts = 0, uparts = 0, tiles = 0;
@@ -196,14 +204,24 @@ bool finish_batch(BatchArgs *b) {
     b->col_cap = 32;
     b->packed = b->v[0].packed;
     b->tile_passes = b->v[0].tile_passes;
+    int lead = -1;
     for (int i = 0; i < b->nviews; i++) {
         View &v = b->v[i];
         if (v.packed != b->packed || v.tile_passes != b->tile_passes || v.cam.tile != b->tile) return false;
-        v.chunk_base = (int32_t)chunks;
+        // time groups: a view joins the group of the view before it when it shares its scene and camera
+        if (lead >= 0 && b->v[lead].group_size < kMaxGroup && same_scene_and_camera(b->v[lead], v)) {
+            b->v[lead].group_size++;
+            v.group_size = 0;
+            v.chunk_base = b->v[lead].chunk_base;
+        } else {
+            lead = i;
+            v.group_size = 1;
+            v.chunk_base = (int32_t)chunks;
+            chunks += (v.n + kPreChunk - 1) / kPreChunk;
+        }
         v.depth_part_base = (int32_t)dparts;
         v.dup_part_base = (int32_t)uparts;
         v.tile_base = (int32_t)tiles;
-        chunks += (v.n + kPreChunk - 1) / kPreChunk;
         dparts += v.parts_depth;
         uparts += v.parts_dup;
         tiles += v.ntiles;
@@ -394,9 +412,10 @@ int d4dgs_batch_encode(int32_t nviews, const d4dgs_view *views, const d4dgs_conf
     return finish_batch(b) ? D4DGS_OK : D4DGS_ERR_INVALID_ARG;
 }
 
-int d4dgs_render_batch(const void *args_host, const void *args_dev, void *batch_area, size_t batch_area_bytes,
-                       d4dgs_stream_t stream) {
-    if (!args_host || !batch_area || !aligned(batch_area, 256) || batch_area_bytes < (size_t)kBatchAreaBytes)
+int d4dgs_render_batch_stages(const void *args_host, const void *args_dev, void *batch_area,
+                              size_t batch_area_bytes, int32_t stages, d4dgs_stream_t stream) {
+    if (!args_host || !batch_area || !aligned(batch_area, 256) || batch_area_bytes < (size_t)kBatchAreaBytes ||
+        stages < 0 || stages > 7)
         return D4DGS_ERR_INVALID_ARG;
     if (args_dev && !aligned(args_dev, 16)) return D4DGS_ERR_INVALID_ARG;
     const BatchArgs &b = *static_cast<const BatchArgs *>(args_host);
@@ -404,11 +423,17 @@ int d4dgs_render_batch(const void *args_host, const void *args_dev, void *batch_
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char *ba = static_cast<char *>(batch_area);
     const int sms = num_sms_current();
-    cudaError_t e = launch_clear(b, args_dev, ba, st, sms);
-    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
-    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
-    if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr, nullptr, /*persist=*/true);
+    cudaError_t e = cudaSuccess;
+    if (stages & 1) e = launch_clear(b, args_dev, ba, st, sms);
+    if (e == cudaSuccess && (stages & 1)) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess && (stages & 2)) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess && (stages & 4)) e = launch_blend(b, ba, st, sms, nullptr, nullptr, /*persist=*/true);
     return cuda_status(e);
+}
+
+int d4dgs_render_batch(const void *args_host, const void *args_dev, void *batch_area, size_t batch_area_bytes,
+                       d4dgs_stream_t stream) {
+    return d4dgs_render_batch_stages(args_host, args_dev, batch_area, batch_area_bytes, 7, stream);
 }
 
 int d4dgs_read_stats(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, const void *ws, size_t ws_bytes,

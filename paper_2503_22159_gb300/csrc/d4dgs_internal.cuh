@@ -96,6 +96,7 @@ CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile);
 // and the absolute addresses of its workspace buffers).  A launch processes a
 // table of up to kMaxViews of them; a single frame is a table of one.
 constexpr int kMaxViews = 32;
+constexpr int kMaxGroup = 4;     // views per time group
 struct View {
     const float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
     int32_t n, sh_degree;
@@ -122,6 +123,10 @@ struct View {
     int32_t tile_shift[3];
     uint32_t tile_mask[3];
     int32_t parts_depth, parts_dup, parts_tile;
+    // time group: consecutive views of one scene seen by one camera (times may
+    // differ) are preprocessed together, reading each Gaussian once; the
+    // group's first view carries group_size (others 0) and the chunk base
+    int32_t group_size;
     // first flattened work item of this view within its table
     int32_t chunk_base, depth_part_base, dup_part_base, tile_base;
 };

@@ -245,9 +245,15 @@ __device__ __forceinline__ void flush_view(const View &v, uint32_t *hist, uint32
     __syncthreads();
 }
 
-// Persistent: CTAs take 256-Gaussian chunks of the views' flattened Gaussians.
+// Persistent: CTAs take 256-Gaussian chunks of the time groups' flattened
+// Gaussians.  For a chunk of a group of B views (one scene and camera, B
+// times) each thread takes its Gaussian through the B views in turn, so its
+// parameters come from DRAM once and from cache for the other views; every
+// view keeps its own shared-memory depth histogram, visible count and, when B
+// of them fit, tile-count grid.  The per-view arithmetic is the same as for a
+// view alone, so a grouped view's outputs equal the ungrouped ones bit for bit.
 __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restrict__ ba, int smem_cells) {
-    __shared__ uint32_t hist[4 * kRadix];
+    __shared__ uint32_t hist[kMaxGroup][4 * kRadix];
     __shared__ int32_t s_chunk;
     extern __shared__ int s_grid[];
     grid_dependency_wait();
@@ -256,41 +262,53 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restri
     const int nviews = (int)bw[kBaNViews];
     const int total = (int)bw[kBaTotalChunks];
     uint32_t *counter = const_cast<uint32_t *>(bw) + kBaChunk;
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) hist[i] = 0;
-    uint32_t nvis = 0;
-    int cur = -1;
+    for (int i = threadIdx.x; i < kMaxGroup * 4 * kRadix; i += blockDim.x) (&hist[0][0])[i] = 0;
+    uint32_t nvis[kMaxGroup];
+#pragma unroll
+    for (int b = 0; b < kMaxGroup; b++) nvis[b] = 0;
+    int cur = -1;   // first view of the group whose sums the CTA holds
+    // shared-memory grid of slot b of group `lead` (null: the group's grids go to global memory)
+    auto slot_grid = [&](int lead, int b) -> int * {
+        const View &l = view_of(ba, lead);
+        const int cells = grid_cells(l);
+        return cells * l.group_size <= smem_cells ? s_grid + b * cells : nullptr;
+    };
+    auto flush_group = [&](int lead) {
+        const int gs = view_of(ba, lead).group_size;
+        for (int b = 0; b < gs; b++) flush_view(view_of(ba, lead + b), hist[b], nvis[b], slot_grid(lead, b));
+    };
     for (;;) {
         if (threadIdx.x == 0) s_chunk = (int32_t)atomicAdd(counter, 1u);
         __syncthreads();
         const int chunk = s_chunk;
         __syncthreads();
         if (chunk >= total) break;
-        int vi = 0;
-        for (int u = 1; u < nviews; u++)
-            if (view_of(ba, u).chunk_base <= chunk) vi = u;
-        const View &v = view_of(ba, vi);
-        if (vi != cur) {
-            if (cur >= 0) {
-                const View &pv = view_of(ba, cur);
-                flush_view(pv, hist, nvis, grid_cells(pv) <= smem_cells ? s_grid : nullptr);
-            }
-            cur = vi;
+        int lead = 0;
+        for (int u = 1; u < nviews; u++) {
+            const View &w = view_of(ba, u);
+            if (w.group_size > 0 && w.chunk_base <= chunk) lead = u;
         }
-        int *sg = grid_cells(v) <= smem_cells ? s_grid : nullptr;
-        const int i = (chunk - v.chunk_base) * kPreChunk + (int)threadIdx.x;
-        if (i < v.n) {
-            switch (v.sh_degree) {
-                case 0: preprocess_one<0>(v, i, hist, nvis, sg); break;
-                case 1: preprocess_one<1>(v, i, hist, nvis, sg); break;
-                case 2: preprocess_one<2>(v, i, hist, nvis, sg); break;
-                default: preprocess_one<3>(v, i, hist, nvis, sg); break;
+        if (lead != cur) {
+            if (cur >= 0) flush_group(cur);
+            cur = lead;
+        }
+        const View &l = view_of(ba, lead);
+        const int i = (chunk - l.chunk_base) * kPreChunk + (int)threadIdx.x;
+        const int gs = l.group_size;
+        for (int b = 0; b < gs; b++) {
+            const View &v = view_of(ba, lead + b);
+            int *sg = slot_grid(lead, b);
+            if (i < v.n) {
+                switch (v.sh_degree) {
+                    case 0: preprocess_one<0>(v, i, hist[b], nvis[b], sg); break;
+                    case 1: preprocess_one<1>(v, i, hist[b], nvis[b], sg); break;
+                    case 2: preprocess_one<2>(v, i, hist[b], nvis[b], sg); break;
+                    default: preprocess_one<3>(v, i, hist[b], nvis[b], sg); break;
+                }
             }
         }
     }
-    if (cur >= 0) {
-        const View &pv = view_of(ba, cur);
-        flush_view(pv, hist, nvis, grid_cells(pv) <= smem_cells ? s_grid : nullptr);
-    }
+    if (cur >= 0) flush_group(cur);
 }
 
 // First kernel of a frame or batch: installs the descriptor table (from the

@@ -58,6 +58,38 @@ def test_mixed_batch_equals_each_view_alone(graph):
             assert torch.equal(out, solo(sc, cam, t, cfg)), (name, cam.width, cam.height)
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_time_groups_equal_each_time_alone(graph):
+    """Consecutive views of one scene and camera at different times form time groups (up to 4 views,
+    preprocessed together, each Gaussian read once); a view of another camera splits them.  Every
+    view's image and tile lists equal, bit for bit, those of the view rendered alone."""
+    m = gu.d4()
+    scenes = scenes_small()
+    cfg = m.config_struct(16, 256)
+    cam_a, _ = synth.orbit(7, 320, 240, 300)[40]
+    cam_b, _ = synth.orbit(8, 200, 160, 300)[200]
+    spec = [("A", cam_a, 0.05), ("A", cam_a, 0.3), ("A", cam_a, 0.55), ("A", cam_a, 0.8), ("A", cam_a, 0.95),
+            ("B", cam_b, 0.5), ("A", cam_a, 0.42), ("A", cam_a, 0.43)]
+    views = []
+    for name, cam, t in spec:
+        sc = scenes[name]
+        ws = torch.empty(m.d4dgs_workspace_bytes(sc.n, cam, cfg, 40 * sc.n), dtype=torch.uint8, device="cuda")
+        views.append((sc, cam, float(np.float32(t)), ws, torch.full((cam.height, cam.width, 3), -1.0, device="cuda")))
+    m.BatchRenderer(cfg).render(views, graph=graph)
+    torch.cuda.synchronize()
+    for (name, cam, t), (sc, _, tt, ws, out) in zip(spec, views):
+        assert m.d4dgs_read_stats(sc.n, cam, cfg, ws)["status"] == 0
+        r = m.Renderer(sc.n, cam, tile=cfg.tile, batch=cfg.batch, key_capacity=40 * sc.n)
+        alone = r.render(sc, cam, tt).clone()
+        assert torch.equal(out, alone), (name, t)
+        L = m.d4dgs_workspace_layout(sc.n, cam, cfg, ws.numel())
+        k = m.d4dgs_read_stats(sc.n, cam, cfg, ws)["n_keys"]
+        La = r.layout(cam)
+        got = ws[L["tile_keys"]: L["tile_keys"] + 4 * k]
+        ref = r.ws[La["tile_keys"]: La["tile_keys"] + 4 * k]
+        assert k == r.stats(cam)["n_keys"] and torch.equal(got, ref), (name, t)
+
+
 def test_batch_rejects_mixed_layout_classes():
     m = gu.d4()
     cfg = m.config_struct(16, 256)
