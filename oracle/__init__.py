@@ -313,3 +313,66 @@ def fingerprint(scene, cam, t: float) -> np.ndarray:
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+# ---------------------------------------------------------------------------
+# Slicing-first 4D Gaussians (Eq. 5-7), FP64.  The 4D rotation is the
+# isoclinic pair of unit quaternions acting as p -> q_l p q_r on
+# p = t + x i + y j + z k (the paper does not fix the 4D rotation's
+# parameterisation; q_r = conj(q_l) is the 3D rotation of q_l with time fixed).
+
+def _hamilton(a, b):
+    """Quaternion products a b for (..., 4) arrays in (w, x, y, z) order."""
+    aw, ax, ay, az = np.moveaxis(a, -1, 0)
+    bw, bx, by, bz = np.moveaxis(b, -1, 0)
+    return np.stack([aw * bw - ax * bx - ay * by - az * bz,
+                     aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw], axis=-1)
+
+
+def rot4(quat_l, quat_r) -> np.ndarray:
+    """(N, 4, 4) rotation matrices in (x, y, z, t) order of p -> q_l p q_r (both normalised)."""
+    ql = _d(quat_l).reshape(-1, 4)
+    qr = _d(quat_r).reshape(-1, 4)
+    ql = ql / np.linalg.norm(ql, axis=1, keepdims=True)
+    qr = qr / np.linalg.norm(qr, axis=1, keepdims=True)
+    n = len(ql)
+    R = np.zeros((n, 4, 4))
+    # basis vectors x, y, z, t as quaternions i, j, k, 1
+    basis = np.array([[0.0, 1, 0, 0], [0.0, 0, 1, 0], [0.0, 0, 0, 1], [1.0, 0, 0, 0]])
+    for c in range(4):
+        img = _hamilton(_hamilton(ql, np.broadcast_to(basis[c], (n, 4))), qr)
+        R[:, :, c] = img[:, [1, 2, 3, 0]]
+    return R
+
+
+def slice4d(scene4d, t: float):
+    """The slicing-first step at time t (Eq. 5-7): Sigma4D = R4 diag(s4^2) R4^T = [[U, V], [V^T, W]],
+    Sigma3D = U - V V^T / W, mean mu_xyz + (t - mu_t) V / W and opacity times
+    exp(-(t - mu_t)^2 / (2 W)).  Returns (a static FP64 scene at t, its 3D covariances as N x 6)."""
+    import synth
+    m4 = _d(scene4d.means4).reshape(-1, 4)
+    s4 = np.exp(_d(scene4d.log_scales4).reshape(-1, 4))
+    R = rot4(scene4d.quat_l, scene4d.quat_r)
+    S4 = np.einsum("nik,nk,njk->nij", R, s4 * s4, R)
+    U, V, W = S4[:, :3, :3], S4[:, :3, 3], S4[:, 3, 3]
+    S3 = U - np.einsum("ni,nj->nij", V, V) / W[:, None, None]
+    tau = t - m4[:, 3]
+    mean_t = m4[:, :3] + tau[:, None] * V / W[:, None]
+    op = 1.0 / (1.0 + np.exp(-_d(scene4d.opacity_logit))) * np.exp(-0.5 * tau * tau / W)
+    with np.errstate(divide="ignore"):
+        logit = np.where(op >= 1.0, 60.0, np.log(op / (1.0 - op)))
+    n = len(m4)
+    static = synth.Scene(means=mean_t, t_mean=np.full(n, float(t)), velocity=np.zeros((n, 3)),
+                         log_scales=np.zeros((n, 3)), log_t_scale=np.zeros(n),
+                         quats=np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)), opacity_logit=logit,
+                         sh=_d(scene4d.sh), sh_degree=scene4d.sh_degree)
+    cov6 = S3[:, [0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]
+    return static, cov6
+
+
+def render_slicing(scene4d, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0), eps_px=None) -> dict:
+    """Slice every 4D Gaussian at t (Eq. 5-7), then render the static 3D result in FP64."""
+    static, cov6 = slice4d(scene4d, t)
+    return render(static, cam, t, pixels=pixels, bg=bg, cov3d=cov6, eps_px=eps_px)

@@ -69,6 +69,33 @@ class Scene:
 
 
 @dataclass
+class Scene4D:
+    """Raw parameters of N 4D Gaussians in the slicing-first form (Eq. 5: a 4D
+    mean, 4D scales and a 4D rotation), float32, SoA.
+
+    means4 (N,4) as (x,y,z,t), log_scales4 (N,4), quat_l and quat_r (N,4) in
+    (w,x,y,z) order and not necessarily unit -- the left and right quaternions
+    of the rotation -- opacity_logit (N,), sh (N, (deg+1)^2, 3).
+    """
+
+    means4: np.ndarray
+    log_scales4: np.ndarray
+    quat_l: np.ndarray
+    quat_r: np.ndarray
+    opacity_logit: np.ndarray
+    sh: np.ndarray
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means4.shape[0])
+
+    def arrays(self):
+        return dict(means4=self.means4, log_scales4=self.log_scales4, quat_l=self.quat_l, quat_r=self.quat_r,
+                    opacity_logit=self.opacity_logit, sh=self.sh)
+
+
+@dataclass
 class Camera:
     """Pinhole camera. World->camera: X_cam = R @ X_world + T (row-major R).
 
@@ -156,6 +183,39 @@ def make_scene(n: int, seed: int, kind: str = "tiny", sh_degree: int | None = No
                  log_scales=f32(log_scales), log_t_scale=f32(log_t_scale),
                  quats=f32(quats), opacity_logit=f32(opacity_logit), sh=f32(sh),
                  sh_degree=deg)
+
+
+def make_scene4d(n: int, seed: int, kind: str = "box20", sh_degree: int | None = None, mix: float = 0.12) -> Scene4D:
+    """Draw a seeded slicing-first scene shaped like ``make_scene``: means in the box,
+    t_mean ~ U[0,1], spatial log-scales as make_scene's, temporal log-scale N(-1.5, 0.3);
+    quat_l = q + noise and quat_r = conj(q) + noise for a random unit q, noise N(0, mix)
+    per component (q with its conjugate alone leaves time untouched; the noise mixes
+    space and time)."""
+    rng = np.random.default_rng(seed)
+    if kind == "tiny":
+        deg = 0 if sh_degree is None else sh_degree
+        xyz = np.concatenate([rng.uniform(-1.0, 1.0, (n, 2)), rng.uniform(2.0, 6.0, (n, 1))], axis=1)
+        ls_xyz = rng.normal(-3.0, 0.5, (n, 3))
+    elif kind == "box20":
+        deg = 3 if sh_degree is None else sh_degree
+        xyz = rng.uniform(-10.0, 10.0, (n, 3))
+        ls_xyz = rng.normal(-3.0 + math.log(10.0), 0.5, (n, 3))
+    else:
+        raise ValueError(kind)
+    t_mean = rng.uniform(0.0, 1.0, (n, 1))
+    ls_t = rng.normal(-1.5, 0.3, (n, 1))
+    q = _unit_quats(rng, n)
+    ql = q + rng.normal(0.0, mix, (n, 4))
+    qr = q * np.array([1.0, -1.0, -1.0, -1.0]) + rng.normal(0.0, mix, (n, 4))
+    opacity_logit = rng.normal(0.0, 1.0, n)
+    ncoef = (deg + 1) ** 2
+    if deg == 0:
+        sh = ((rng.uniform(0.0, 1.0, (n, 3)) - 0.5) / SH_C0).reshape(n, 1, 3)
+    else:
+        sh = rng.normal(0.0, 0.2, (n, ncoef, 3))
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return Scene4D(means4=f32(np.concatenate([xyz, t_mean], 1)), log_scales4=f32(np.concatenate([ls_xyz, ls_t], 1)),
+                   quat_l=f32(ql), quat_r=f32(qr), opacity_logit=f32(opacity_logit), sh=f32(sh), sh_degree=deg)
 
 
 def orbit(seed: int, width: int, height: int, n_frames: int = 300, radius: float = 30.0):

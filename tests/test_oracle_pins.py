@@ -432,3 +432,83 @@ def test_tile_list_sorted_and_ranges():
     assert np.all(r[1:, 0] == r[:-1, 1])
     for tid in range(len(r)):
         assert np.all(L["tile"][r[tid, 0]:r[tid, 1]] == tid)
+
+
+# ---------------------------------------------------------------------------
+# slicing-first form (Eq. 5-7 with the 4D rotation p -> q_l p q_r)
+
+def test_rot4_conjugate_pair_is_the_3d_rotation():
+    """q_r = conj(q_l): time is untouched and space turns by the 3D rotation of q_l."""
+    rng = np.random.default_rng(21)
+    q = rng.standard_normal((8, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)   # quat_to_rot takes unit quaternions
+    R = oracle.rot4(q, q * np.array([1.0, -1, -1, -1]))
+    for k in range(8):
+        expect = np.eye(4)
+        expect[:3, :3] = oracle.quat_to_rot(q[k])
+        np.testing.assert_allclose(R[k], expect, atol=1e-14)
+
+
+def test_rot4_equal_pair_turns_one_space_time_plane():
+    """q_l = q_r = cos(phi/2) + u sin(phi/2): rotation by phi in the plane of t and u, identity on u's
+    orthogonal complement in space."""
+    rng = np.random.default_rng(22)
+    for _ in range(5):
+        u = rng.standard_normal(3)
+        u /= np.linalg.norm(u)
+        phi = rng.uniform(-2, 2)
+        q = np.append(math.cos(phi / 2), math.sin(phi / 2) * u)
+        R = oracle.rot4(q, q)[0]
+        et = np.array([0, 0, 0, 1.0])
+        eu = np.append(u, 0.0)
+        np.testing.assert_allclose(R @ et, math.cos(phi) * et + math.sin(phi) * eu, atol=1e-14)
+        np.testing.assert_allclose(R @ eu, math.cos(phi) * eu - math.sin(phi) * et, atol=1e-14)
+        w = np.cross(u, rng.standard_normal(3))
+        w = np.append(w / np.linalg.norm(w), 0.0)
+        np.testing.assert_allclose(R @ w, w, atol=1e-14)
+
+
+def test_rot4_is_a_rotation():
+    rng = np.random.default_rng(23)
+    R = oracle.rot4(rng.standard_normal((50, 4)), rng.standard_normal((50, 4)))
+    np.testing.assert_allclose(np.einsum("nij,nkj->nik", R, R), np.broadcast_to(np.eye(4), R.shape), atol=1e-14)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-13)
+
+
+def test_slice4d_is_the_conditional_gaussian():
+    """Sigma3D and the mean at t equal the conditional of the 4D Gaussian computed from the
+    precision matrix (inverse of the spatial block of Sigma4D^-1; mean mu - P_xx^-1 P_xt (t - mu_t)),
+    and the opacity factor is the temporal marginal exp(-(t - mu_t)^2 / (2 Sigma4D_tt))."""
+    sc = synth.make_scene4d(40, 24, "tiny", mix=0.4)
+    t = 0.37
+    static, cov6 = oracle.slice4d(sc, t)
+    R = oracle.rot4(sc.quat_l, sc.quat_r)
+    s4 = np.exp(sc.log_scales4.astype(np.float64))
+    for k in range(sc.n):
+        S4 = R[k] @ np.diag(s4[k] ** 2) @ R[k].T
+        P = np.linalg.inv(S4)
+        S3 = np.linalg.inv(P[:3, :3])
+        m4 = sc.means4[k].astype(np.float64)
+        mean = m4[:3] - S3 @ P[:3, 3] * (t - m4[3])
+        np.testing.assert_allclose(cov6[k], S3[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]], rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(static.means[k], mean, rtol=1e-10, atol=1e-12)
+        o = 1 / (1 + np.exp(-float(sc.opacity_logit[k]))) * np.exp(-0.5 * (t - m4[3]) ** 2 / S4[3, 3])
+        assert 1 / (1 + np.exp(-static.opacity_logit[k])) == pytest.approx(o, rel=1e-12)
+
+
+def test_slicing_without_space_time_mixing_equals_the_disentangled_render():
+    """Identity rotations: Sigma4D is diagonal, V = 0, so slicing-first equals the disentangled render
+    with zero velocity, the same spatial scales and s_t = the fourth scale."""
+    sc = synth.make_scene4d(80, 25, "tiny")
+    n = sc.n
+    ident = np.tile([1.0, 0.0, 0.0, 0.0], (n, 1))
+    sc.quat_l, sc.quat_r = ident.astype(np.float32), ident.astype(np.float32)
+    dis = synth.Scene(means=sc.means4[:, :3], t_mean=sc.means4[:, 3], velocity=np.zeros((n, 3), np.float32),
+                      log_scales=sc.log_scales4[:, :3], log_t_scale=sc.log_scales4[:, 3], quats=ident,
+                      opacity_logit=sc.opacity_logit, sh=sc.sh, sh_degree=sc.sh_degree)
+    cam = camera(width=48, height=40, fx=40.0, fy=40.0)
+    for t in (0.2, 0.6):
+        a = oracle.render_slicing(sc, cam, t)
+        b = oracle.render(dis, cam, t)
+        np.testing.assert_allclose(a["rgb"], b["rgb"], atol=1e-12)
+        assert np.abs(a["rgb"]).max() > 0.05
