@@ -347,6 +347,64 @@ def run_time_groups(args, dev, d4, w, scene, cfg, cap, peaks):
                                     "achieved_single": gbs(read_b + write_b, pre_single)}}
 
 
+def run_slicing_first(args, dev, d4):
+    """The slicing-first baseline (the 4D form sliced at every frame, Eq. 5-7) against the
+    disentangled form on the same scenes (converted on the host), at 100k Gaussians (the count of
+    the paper's rendering-time comparison) and 300k: device time per frame of the preprocess and of
+    whole frames over the same orbit poses, L2 flushed before every frame."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2503_22159_gb300 import convert
+    stream = torch.cuda.current_stream(dev)
+    cfg = d4.config_struct(args.tile, args.batch)
+    frames = synth.orbit(1, 1352, 1014, 300)[::10]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for n in (100_000, 300_000):
+        sc4 = synth.make_scene4d(n, 0, "box20")
+        ds4 = d4.DeviceScene4D.from_host(sc4, dev)
+        dsd = d4.DeviceScene.from_host(convert.disentangle(sc4), dev)
+        r = d4.Renderer(n, frames[0][0], tile=args.tile, batch=args.batch, device=dev)
+        for cam, t in frames:
+            r.render(dsd, cam, t)
+        r._alloc(int(r.key_capacity * 1.1) + 4096)
+        img = torch.empty((frames[0][0].height, frames[0][0].width, 3), device=dev)
+        pre = {"disentangled": lambda c, t: d4.d4dgs_preprocess(dsd, c, t, cfg, r.ws, stream),
+               "slicing_first": lambda c, t: d4.d4dgs_preprocess_slicing(ds4, c, t, cfg, r.ws, stream)}
+        full = {"disentangled": lambda c, t: d4.d4dgs_render(dsd, c, t, cfg, r.ws, img, stream),
+                "slicing_first": lambda c, t: d4.d4dgs_render_slicing(ds4, c, t, cfg, r.ws, img, stream)}
+
+        def timed(fn):
+            evs = []
+            for rep in range(2):
+                for k, (cam, t) in enumerate(frames):
+                    torch.cuda._sleep(1_000_000)
+                    flush.fill_(k & 255)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn(cam, t)
+                    e1.record(stream)
+                    if rep:
+                        evs.append((e0, e1))
+            torch.cuda.synchronize(dev)
+            return 1e3 * float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+        res = {"preprocess_us": {k: timed(f) for k, f in pre.items()},
+               "frame_us": {k: timed(f) for k, f in full.items()}}
+        for cam, t in frames[:3]:
+            d4.d4dgs_render_slicing(ds4, cam, t, cfg, r.ws, img, stream)
+            if r.stats(cam)["status"] != 0:
+                raise RuntimeError("slicing-first frame reported an error")
+        res["speedup"] = {"preprocess": res["preprocess_us"]["slicing_first"] / res["preprocess_us"]["disentangled"],
+                          "frame": res["frame_us"]["slicing_first"] / res["frame_us"]["disentangled"]}
+        out[f"n={n}"] = res
+    out["frames"] = len(frames)
+    out["paper"] = "Tab. 5 (RTX 3090, 100k Gaussians): 0.94 ms slicing-first (Rotor4DGS) vs 0.69 ms disentangled"
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -505,9 +563,10 @@ def run_ours(args):
         e2e = {"value": world * E / te, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": E, "api": "d4dgs_render_host"}
 
-    groups_out = None
+    groups_out = slicing_out = None
     if not args.no_serving and world == 1:
         groups_out = run_time_groups(args, dev, d4, w, scene, cfg, r.key_capacity, peaks)
+        slicing_out = run_slicing_first(args, dev, d4)
 
     serving_out = None
     if not args.no_serving and world == 1:
@@ -528,6 +587,7 @@ def run_ours(args):
         "gpu_launches": int(launches * K), "launches_per_frame": launches,
         "wall_s_timed_region": t_wall, "peaks": peak_kind,
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out, "time_groups": groups_out,
+        "slicing_first": slicing_out,
         "autotune": {"chosen": f"{args.tile}/{args.batch}", "ms_per_frame": tune_table} if tune_table else None,
     }
     print(json.dumps(line), flush=True)

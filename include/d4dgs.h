@@ -191,6 +191,34 @@ int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, flo
                           void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
                           d4dgs_stream_t stream);
 
+/* ---- slicing-first baseline (comparison, Eq. 5-7) --------------------------
+ * The 4D Gaussian form the paper compares against: a 4D mean, 4D scales and
+ * a 4D rotation, sliced at every frame into a 3D Gaussian before projection.
+ * The rotation is the pair of unit quaternions (q_l, q_r) acting as
+ * p -> q_l p q_r on p = t + x i + y j + z k (one reading of the 4D rotations
+ * the paper cites; q_r = conj(q_l) is the 3D rotation of q_l).  Per Gaussian
+ * and frame: Sigma4D = R4 S4^2 R4^T = [[U, V], [V^T, W]] (Eq. 5),
+ * Sigma3D = U - V V^T / W, mean mu + (t - mu_t) V / W, opacity times
+ * exp(-(t - mu_t)^2 / (2 W)) (Eq. 6-7); then the same projection, binning and
+ * blending as the disentangled path (same workspace, d4dgs_sort and
+ * d4dgs_blend apply).  All arrays device, caller-owned, read-only. */
+typedef struct {
+    const float *means4;         /* N x 4: x, y, z, t                                */
+    const float *log_scales4;    /* N x 4                                            */
+    const float *quat_l;         /* N x 4 (w, x, y, z), any norm, 16-byte aligned    */
+    const float *quat_r;         /* N x 4 (w, x, y, z), any norm, 16-byte aligned    */
+    const float *opacity_logit;  /* N                                                */
+    const float *sh;             /* N x (deg+1)^2 x 3                                */
+    int32_t n, sh_degree;
+} d4dgs_scene4d;
+
+/* Stage 1 for a slicing-first scene (then d4dgs_sort and d4dgs_blend). */
+int d4dgs_preprocess_slicing(const d4dgs_scene4d *scene, const d4dgs_camera *cam, float t,
+                             const d4dgs_config *cfg, void *ws, size_t ws_bytes, d4dgs_stream_t stream);
+/* Stages 1-3 for a slicing-first scene. */
+int d4dgs_render_slicing(const d4dgs_scene4d *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                         void *ws, size_t ws_bytes, float *out_rgb, d4dgs_stream_t stream);
+
 /* ---- batched multi-view rendering (serving) -------------------------------
  * V <= 32 frames rendered by ONE launch of each kernel (preprocess, sort
  * passes, blend), each frame with its own scene, camera, time, resolution,

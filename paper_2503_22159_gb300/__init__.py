@@ -26,6 +26,7 @@ SCENE_FIELDS = ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "qua
 
 __all__ = ["DeviceScene", "Renderer", "BatchRenderer", "camera_struct", "config_struct", "d4dgs_workspace_bytes",
            "d4dgs_workspace_layout", "d4dgs_preprocess", "d4dgs_sort", "d4dgs_blend", "d4dgs_blend_profile",
+           "DeviceScene4D", "d4dgs_preprocess_slicing", "d4dgs_render_slicing",
            "d4dgs_render",
            "d4dgs_render_backward", "d4dgs_read_stats", "d4dgs_render_host", "d4dgs_launches_per_frame",
            "D4DGSError", "D4DGS_OK", "D4DGS_ERR_CAPACITY", "D4DGS_ERR_TIMEOUT", "D4DGS_ERR_INVALID_ARG",
@@ -61,6 +62,44 @@ class DeviceScene:
 
     def zeros_like_grad(self) -> dict:
         return {k: torch.zeros_like(v) for k, v in self.t.items()}
+
+
+SCENE4D_FIELDS = ("means4", "log_scales4", "quat_l", "quat_r", "opacity_logit", "sh")
+
+
+class DeviceScene4D:
+    """A slicing-first scene (4D means, 4D log-scales, rotation quaternion pair) on the device."""
+
+    def __init__(self, tensors: dict, sh_degree: int):
+        self.t = {k: tensors[k] for k in SCENE4D_FIELDS}
+        self.sh_degree = int(sh_degree)
+        self.n = int(self.t["means4"].shape[0])
+        for k, v in self.t.items():
+            if v.dtype != torch.float32 or not v.is_contiguous() or not v.is_cuda:
+                raise ValueError(f"scene field {k} must be a contiguous float32 CUDA tensor")
+
+    @classmethod
+    def from_host(cls, scene, device="cuda") -> "DeviceScene4D":
+        t = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), dtype=np.float32)).to(device)
+             for k in SCENE4D_FIELDS}
+        return cls(t, scene.sh_degree)
+
+    def struct(self) -> _abi.d4dgs_scene4d:
+        return _abi.d4dgs_scene4d(*[self.t[k].data_ptr() for k in SCENE4D_FIELDS], self.n, self.sh_degree)
+
+
+def d4dgs_preprocess_slicing(scene: DeviceScene4D, cam, t: float, cfg, ws: torch.Tensor, stream=None):
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_preprocess_slicing(ctypes.byref(scene.struct()), ctypes.byref(camera_struct(cam)),
+                                                    float(t), ctypes.byref(cfg), p, nb, _stream_handle(stream)),
+               "d4dgs_preprocess_slicing")
+
+
+def d4dgs_render_slicing(scene: DeviceScene4D, cam, t: float, cfg, ws: torch.Tensor, out: torch.Tensor, stream=None):
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_render_slicing(ctypes.byref(scene.struct()), ctypes.byref(camera_struct(cam)),
+                                                float(t), ctypes.byref(cfg), p, nb, ctypes.c_void_p(out.data_ptr()),
+                                                _stream_handle(stream)), "d4dgs_render_slicing")
 
 
 def camera_struct(cam) -> _abi.d4dgs_camera:

@@ -27,6 +27,11 @@ class d4dgs_scene(ctypes.Structure):
         ("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
 
 
+class d4dgs_scene4d(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("means4", "log_scales4", "quat_l", "quat_r", "opacity_logit",
+                                                "sh")] + [("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
+
+
 class d4dgs_scene_grad(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
                                                 "quats", "opacity_logit", "sh")]
@@ -90,6 +95,10 @@ PROTOTYPES = {
     "d4dgs_batch_area_bytes": (ctypes.c_size_t, []),
     "d4dgs_batch_encode": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_view), _P(d4dgs_config), _vp, ctypes.c_size_t]),
     "d4dgs_render_batch": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "d4dgs_preprocess_slicing": (ctypes.c_int, [_P(d4dgs_scene4d), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),
+                                                _vp, ctypes.c_size_t, _vp]),
+    "d4dgs_render_slicing": (ctypes.c_int, [_P(d4dgs_scene4d), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),
+                                            _vp, ctypes.c_size_t, _vp, _vp]),
     "d4dgs_render_batch_stages": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, ctypes.c_int32, _vp]),
     "d4dgs_launches_per_frame": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_camera), _P(d4dgs_config)]),
     "d4dgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),

@@ -51,6 +51,17 @@ int check_scene(const d4dgs_scene *s) {
     return D4DGS_OK;
 }
 
+int check_scene4d(const d4dgs_scene4d *s) {
+    if (!s || s->n < 0 || s->sh_degree < 0 || s->sh_degree > 3) return D4DGS_ERR_INVALID_ARG;
+    if (s->n == 0) return D4DGS_OK;
+    const void *ps[] = {s->means4, s->log_scales4, s->quat_l, s->quat_r};
+    for (const void *p : ps)
+        if (!p || !aligned(p, 16)) return D4DGS_ERR_INVALID_ARG;
+    if (!s->opacity_logit || !aligned(s->opacity_logit, 4) || !s->sh || !aligned(s->sh, 4)) return D4DGS_ERR_INVALID_ARG;
+    if ((s->sh_degree == 1 || s->sh_degree == 3) && !aligned(s->sh, 16)) return D4DGS_ERR_INVALID_ARG;
+    return D4DGS_OK;
+}
+
 int num_sms_current() {
     static int cache[64] = {0};
     int dev = 0;
@@ -192,9 +203,11 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
 // Same scene arrays and camera (the time may differ): views that can share one
 // read of each Gaussian in the preprocess.
 static bool same_scene_and_camera(const View &a, const View &b) {
-    return a.means == b.means && a.t_mean == b.t_mean && a.velocity == b.velocity && a.log_scales == b.log_scales &&
-           a.log_t_scale == b.log_t_scale && a.quats == b.quats && a.opacity_logit == b.opacity_logit &&
-           a.sh == b.sh && a.n == b.n && a.sh_degree == b.sh_degree && memcmp(&a.cam, &b.cam, sizeof(CamArgs)) == 0;
+    return a.kind == b.kind && a.means == b.means && a.t_mean == b.t_mean && a.velocity == b.velocity &&
+           a.log_scales == b.log_scales && a.log_t_scale == b.log_t_scale && a.quats == b.quats &&
+           a.means4 == b.means4 && a.log_scales4 == b.log_scales4 && a.quat_l == b.quat_l && a.quat_r == b.quat_r &&
+           a.opacity_logit == b.opacity_logit && a.sh == b.sh && a.n == b.n && a.sh_degree == b.sh_degree &&
+           memcmp(&a.cam, &b.cam, sizeof(CamArgs)) == 0;
 }
 
 bool finish_batch(BatchArgs *b) {
@@ -358,6 +371,52 @@ int d4dgs_render(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, con
     static thread_local BatchArgs b;
     Layout L;
     if ((rc = single(scene, scene->n, cam, t, cfg, ws, ws_bytes, out_rgb, &b, &L))) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ba = at<char>(ws, L.batch);
+    const int sms = num_sms_current();
+    cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
+    return cuda_status(e);
+}
+
+// A slicing-first frame as a batch of one view.
+static int single4d(const d4dgs_scene4d *s, const d4dgs_camera *cam, float t, const d4dgs_config *cfg, void *ws,
+                    size_t ws_bytes, float *out_rgb, BatchArgs *b, Layout *L) {
+    int rc = check_scene4d(s);
+    if (rc) return rc;
+    if (!isfinite(t)) return D4DGS_ERR_INVALID_ARG;
+    if ((rc = single(nullptr, s->n, cam, t, cfg, ws, ws_bytes, out_rgb, b, L))) return rc;
+    View &v = b->v[0];
+    v.kind = 1;
+    v.means4 = s->means4; v.log_scales4 = s->log_scales4; v.quat_l = s->quat_l; v.quat_r = s->quat_r;
+    v.opacity_logit = s->opacity_logit; v.sh = s->sh;
+    v.sh_degree = s->sh_degree;
+    return D4DGS_OK;
+}
+
+int d4dgs_preprocess_slicing(const d4dgs_scene4d *scene, const d4dgs_camera *cam, float t,
+                             const d4dgs_config *cfg, void *ws, size_t ws_bytes, d4dgs_stream_t stream) {
+    static thread_local BatchArgs b;
+    Layout L;
+    int rc = single4d(scene, cam, t, cfg, ws, ws_bytes, nullptr, &b, &L);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ba = at<char>(ws, L.batch);
+    const int sms = num_sms_current();
+    cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    return cuda_status(e);
+}
+
+int d4dgs_render_slicing(const d4dgs_scene4d *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                         void *ws, size_t ws_bytes, float *out_rgb, d4dgs_stream_t stream) {
+    if (!out_rgb || !aligned(out_rgb, 4)) return D4DGS_ERR_INVALID_ARG;
+    static thread_local BatchArgs b;
+    Layout L;
+    int rc = single4d(scene, cam, t, cfg, ws, ws_bytes, out_rgb, &b, &L);
+    if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char *ba = at<char>(ws, L.batch);
     const int sms = num_sms_current();

@@ -99,6 +99,9 @@ constexpr int kMaxViews = 32;
 constexpr int kMaxGroup = 4;     // views per time group
 struct View {
     const float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
+    // slicing-first scenes (kind 1): 4D means, 4D log-scales, rotation quaternion pair
+    const float *means4, *log_scales4, *quat_l, *quat_r;
+    int32_t kind;                    // 0: disentangled, 1: slicing-first
     int32_t n, sh_degree;
     float t;
     float bg[3];

@@ -70,6 +70,163 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
     }
 }
 
+// 2D footprint of one Gaussian at the view's time, before the shared tail.
+struct Footprint {
+    float m0, m1, m2;     // world-space mean at t (SH view direction)
+    float Z, u, v, oh;    // camera depth, pixel mean, opacity at t
+    float s00, s01, s11;  // Sigma' (with the 0.3 px^2 dilation)
+};
+
+// Disentangled form (Algorithm 1): the deferred temporal slice of the mean
+// and opacity, then the projection of the static 3D covariance R S S^T R^T.
+// FP32 in the documented binning operation order.  False: not drawn.
+__device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Footprint &f) {
+    const CamArgs &c = vw.cam;
+    const float t = vw.t;
+    const float limx = mul(kJacClamp, dvd(mul(0.5f, (float)c.width), c.fx));
+    const float limy = mul(kJacClamp, dvd(mul(0.5f, (float)c.height), c.fy));
+    do {
+        // ---- deferred temporal slice and camera transform (binning order)
+        const float tau = sub(t, __ldg(vw.t_mean + i));
+        const float m0 = add(__ldg(vw.means + 3 * i + 0), mul(tau, __ldg(vw.velocity + 3 * i + 0)));
+        const float m1 = add(__ldg(vw.means + 3 * i + 1), mul(tau, __ldg(vw.velocity + 3 * i + 1)));
+        const float m2 = add(__ldg(vw.means + 3 * i + 2), mul(tau, __ldg(vw.velocity + 3 * i + 2)));
+        const float *R = c.R;
+        const float X = add(add(add(mul(R[0], m0), mul(R[1], m1)), mul(R[2], m2)), c.T[0]);
+        const float Y = add(add(add(mul(R[3], m0), mul(R[4], m1)), mul(R[5], m2)), c.T[1]);
+        const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
+        if (!(Z > kNear)) break;
+        // ---- temporal opacity
+        const float o = dvd(1.0f, add(1.0f, expf(-__ldg(vw.opacity_logit + i))));
+        const float st = expf(__ldg(vw.log_t_scale + i));
+        const float oh = mul(o, expf(dvd(mul(-0.5f, mul(tau, tau)), mul(st, st))));
+        if (!(oh >= kAlphaMin)) break;
+        // ---- projection of the mean and the Jacobian at the shifted mean
+        const float xz = dvd(X, Z), yz = dvd(Y, Z);
+        const float u = add(mul(c.fx, xz), c.cx), v = add(mul(c.fy, yz), c.cy);
+        const float xzc = fminf(limx, fmaxf(-limx, xz)), yzc = fminf(limy, fmaxf(-limy, yz));
+        const float J00 = dvd(c.fx, Z), J02 = dvd(-mul(c.fx, xzc), Z);
+        const float J11 = dvd(c.fy, Z), J12 = dvd(-mul(c.fy, yzc), Z);
+        // ---- 3D covariance factor M = R(q) diag(s)
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(vw.quats) + i);
+        const float qn = __fsqrt_rn(add(add(add(mul(q.x, q.x), mul(q.y, q.y)), mul(q.z, q.z)), mul(q.w, q.w)));
+        const float qw = dvd(q.x, qn), qx = dvd(q.y, qn), qy = dvd(q.z, qn), qz = dvd(q.w, qn);
+        float Rq[9];
+        Rq[0] = sub(1.0f, mul(2.0f, add(mul(qy, qy), mul(qz, qz))));
+        Rq[1] = mul(2.0f, sub(mul(qx, qy), mul(qw, qz)));
+        Rq[2] = mul(2.0f, add(mul(qx, qz), mul(qw, qy)));
+        Rq[3] = mul(2.0f, add(mul(qx, qy), mul(qw, qz)));
+        Rq[4] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qz, qz))));
+        Rq[5] = mul(2.0f, sub(mul(qy, qz), mul(qw, qx)));
+        Rq[6] = mul(2.0f, sub(mul(qx, qz), mul(qw, qy)));
+        Rq[7] = mul(2.0f, add(mul(qy, qz), mul(qw, qx)));
+        Rq[8] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qy, qy))));
+        const float sc[3] = {expf(__ldg(vw.log_scales + 3 * i + 0)), expf(__ldg(vw.log_scales + 3 * i + 1)),
+                         expf(__ldg(vw.log_scales + 3 * i + 2))};
+        float M[9];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) M[3 * r + k] = mul(Rq[3 * r + k], sc[k]);
+        // ---- T = J W (2x3), TM = T M, Sigma' = TM TM^T + 0.3 I
+        float Tm[6];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            Tm[j] = add(mul(J00, R[j]), mul(J02, R[6 + j]));
+            Tm[3 + j] = add(mul(J11, R[3 + j]), mul(J12, R[6 + j]));
+        }
+        float TM[6];
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                TM[3 * r + k] = add(add(mul(Tm[3 * r + 0], M[k]), mul(Tm[3 * r + 1], M[3 + k])), mul(Tm[3 * r + 2], M[6 + k]));
+        const float s00 = add(add(add(mul(TM[0], TM[0]), mul(TM[1], TM[1])), mul(TM[2], TM[2])), kDilation);
+        const float s01 = add(add(mul(TM[0], TM[3]), mul(TM[1], TM[4])), mul(TM[2], TM[5]));
+        const float s11 = add(add(add(mul(TM[3], TM[3]), mul(TM[4], TM[4])), mul(TM[5], TM[5])), kDilation);
+        f.m0 = m0; f.m1 = m1; f.m2 = m2;
+        f.Z = Z; f.u = u; f.v = v; f.oh = oh;
+        f.s00 = s00; f.s01 = s01; f.s11 = s11;
+        return true;
+    } while (0);
+    return false;
+}
+
+// Slicing-first form (Eq. 5-7, the comparison baseline): every frame builds
+// the 4D rotation from its quaternion pair (p -> q_l p q_r on p = t + x i +
+// y j + z k), Sigma4D = R4 S4^2 R4^T = [[U, V], [V^T, W]], and slices it at t:
+// Sigma3D = U - V V^T / W, mean mu + (t - mu_t) V / W, opacity times
+// exp(-(t - mu_t)^2 / (2 W)); then the same projection.  Ordinary FP32.
+__device__ __forceinline__ bool footprint_slicing(const View &vw, int i, Footprint &f) {
+    const CamArgs &c = vw.cam;
+    const float4 m4 = __ldg(reinterpret_cast<const float4 *>(vw.means4) + i);
+    const float4 l4 = __ldg(reinterpret_cast<const float4 *>(vw.log_scales4) + i);
+    float4 a = __ldg(reinterpret_cast<const float4 *>(vw.quat_l) + i);
+    float4 b = __ldg(reinterpret_cast<const float4 *>(vw.quat_r) + i);
+    const float ia = rsqrtf(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
+    const float ib = rsqrtf(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
+    a = make_float4(a.x * ia, a.y * ia, a.z * ia, a.w * ia);
+    b = make_float4(b.x * ib, b.y * ib, b.z * ib, b.w * ib);
+    // left- and right-multiplication matrices in the quaternion basis (1, i, j, k)
+    const float La[16] = {a.x, -a.y, -a.z, -a.w, a.y, a.x, -a.w, a.z, a.z, a.w, a.x, -a.y, a.w, -a.z, a.y, a.x};
+    const float Rb[16] = {b.x, -b.y, -b.z, -b.w, b.y, b.x, b.w, -b.z, b.z, -b.w, b.x, b.y, b.w, b.z, -b.y, b.x};
+    // R4 in (x, y, z, t) order: quaternion components (i, j, k, 1) = indices (1, 2, 3, 0)
+    const int perm[4] = {1, 2, 3, 0};
+    const float s4[4] = {__expf(l4.x), __expf(l4.y), __expf(l4.z), __expf(l4.w)};
+    float M[16];   // M = R4 diag(s4)
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int pr = perm[r], pk = perm[k];
+            float acc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc += La[4 * pr + j] * Rb[4 * j + pk];
+            M[4 * r + k] = acc * s4[k];
+        }
+    auto sig = [&](int r, int q) {
+        return M[4 * r] * M[4 * q] + M[4 * r + 1] * M[4 * q + 1] + M[4 * r + 2] * M[4 * q + 2] + M[4 * r + 3] * M[4 * q + 3];
+    };
+    const float W = sig(3, 3);
+    const float V0 = sig(0, 3), V1 = sig(1, 3), V2 = sig(2, 3);
+    const float iW = 1.0f / W;
+    const float S00 = sig(0, 0) - V0 * V0 * iW, S01 = sig(0, 1) - V0 * V1 * iW, S02 = sig(0, 2) - V0 * V2 * iW;
+    const float S11 = sig(1, 1) - V1 * V1 * iW, S12 = sig(1, 2) - V1 * V2 * iW, S22 = sig(2, 2) - V2 * V2 * iW;
+    const float tau = vw.t - m4.w;
+    const float m0 = m4.x + tau * V0 * iW, m1 = m4.y + tau * V1 * iW, m2 = m4.z + tau * V2 * iW;
+    const float *R = c.R;
+    const float X = R[0] * m0 + R[1] * m1 + R[2] * m2 + c.T[0];
+    const float Y = R[3] * m0 + R[4] * m1 + R[5] * m2 + c.T[1];
+    const float Z = R[6] * m0 + R[7] * m1 + R[8] * m2 + c.T[2];
+    if (!(Z > kNear)) return false;
+    const float o = 1.0f / (1.0f + __expf(-__ldg(vw.opacity_logit + i)));
+    const float oh = o * __expf(-0.5f * tau * tau * iW);
+    if (!(oh >= kAlphaMin)) return false;
+    const float iZ = 1.0f / Z;
+    const float xz = X * iZ, yz = Y * iZ;
+    const float limx = kJacClamp * 0.5f * (float)c.width / c.fx, limy = kJacClamp * 0.5f * (float)c.height / c.fy;
+    const float xzc = fminf(limx, fmaxf(-limx, xz)), yzc = fminf(limy, fmaxf(-limy, yz));
+    const float J00 = c.fx * iZ, J02 = -c.fx * xzc * iZ, J11 = c.fy * iZ, J12 = -c.fy * yzc * iZ;
+    float Tm[6];   // J W (2 x 3)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        Tm[j] = J00 * R[j] + J02 * R[6 + j];
+        Tm[3 + j] = J11 * R[3 + j] + J12 * R[6 + j];
+    }
+    const float S3[9] = {S00, S01, S02, S01, S11, S12, S02, S12, S22};
+    float TS[6];   // (J W) Sigma3D
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) TS[3 * r + k] = Tm[3 * r] * S3[k] + Tm[3 * r + 1] * S3[3 + k] + Tm[3 * r + 2] * S3[6 + k];
+    f.m0 = m0; f.m1 = m1; f.m2 = m2;
+    f.Z = Z; f.u = c.fx * xz + c.cx; f.v = c.fy * yz + c.cy; f.oh = oh;
+    f.s00 = TS[0] * Tm[0] + TS[1] * Tm[1] + TS[2] * Tm[2] + kDilation;
+    f.s01 = TS[0] * Tm[3] + TS[1] * Tm[4] + TS[2] * Tm[5];
+    f.s11 = TS[3] * Tm[3] + TS[4] * Tm[4] + TS[5] * Tm[5] + kDilation;
+    return true;
+}
+
 // One Gaussian of view v: writes its 2D record, depth key, tile count and
 // rectangle, adds its rectangle to the view's difference grid, and counts it in
 // the shared depth-digit histogram.
@@ -77,73 +234,16 @@ template <int DEG>
 __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *hist, uint32_t &nvis, int *sgrid) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const CamArgs &c = vw.cam;
-    const float t = vw.t;
-    const float limx = mul(kJacClamp, dvd(mul(0.5f, (float)c.width), c.fx));
-    const float limy = mul(kJacClamp, dvd(mul(0.5f, (float)c.height), c.fy));
     const float tilef = (float)c.tile;
     {
         uint32_t key = 0xFFFFFFFFu, tiles = 0;
         ushort4 rc = make_ushort4(0, 0, 0, 0);
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         do {
-            // ---- deferred temporal slice and camera transform (binning order)
-            const float tau = sub(t, __ldg(vw.t_mean + i));
-            const float m0 = add(__ldg(vw.means + 3 * i + 0), mul(tau, __ldg(vw.velocity + 3 * i + 0)));
-            const float m1 = add(__ldg(vw.means + 3 * i + 1), mul(tau, __ldg(vw.velocity + 3 * i + 1)));
-            const float m2 = add(__ldg(vw.means + 3 * i + 2), mul(tau, __ldg(vw.velocity + 3 * i + 2)));
-            const float *R = c.R;
-            const float X = add(add(add(mul(R[0], m0), mul(R[1], m1)), mul(R[2], m2)), c.T[0]);
-            const float Y = add(add(add(mul(R[3], m0), mul(R[4], m1)), mul(R[5], m2)), c.T[1]);
-            const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
-            if (!(Z > kNear)) break;
-            // ---- temporal opacity
-            const float o = dvd(1.0f, add(1.0f, expf(-__ldg(vw.opacity_logit + i))));
-            const float st = expf(__ldg(vw.log_t_scale + i));
-            const float oh = mul(o, expf(dvd(mul(-0.5f, mul(tau, tau)), mul(st, st))));
-            if (!(oh >= kAlphaMin)) break;
-            // ---- projection of the mean and the Jacobian at the shifted mean
-            const float xz = dvd(X, Z), yz = dvd(Y, Z);
-            const float u = add(mul(c.fx, xz), c.cx), v = add(mul(c.fy, yz), c.cy);
-            const float xzc = fminf(limx, fmaxf(-limx, xz)), yzc = fminf(limy, fmaxf(-limy, yz));
-            const float J00 = dvd(c.fx, Z), J02 = dvd(-mul(c.fx, xzc), Z);
-            const float J11 = dvd(c.fy, Z), J12 = dvd(-mul(c.fy, yzc), Z);
-            // ---- 3D covariance factor M = R(q) diag(s)
-            const float4 q = __ldg(reinterpret_cast<const float4 *>(vw.quats) + i);
-            const float qn = __fsqrt_rn(add(add(add(mul(q.x, q.x), mul(q.y, q.y)), mul(q.z, q.z)), mul(q.w, q.w)));
-            const float qw = dvd(q.x, qn), qx = dvd(q.y, qn), qy = dvd(q.z, qn), qz = dvd(q.w, qn);
-            float Rq[9];
-            Rq[0] = sub(1.0f, mul(2.0f, add(mul(qy, qy), mul(qz, qz))));
-            Rq[1] = mul(2.0f, sub(mul(qx, qy), mul(qw, qz)));
-            Rq[2] = mul(2.0f, add(mul(qx, qz), mul(qw, qy)));
-            Rq[3] = mul(2.0f, add(mul(qx, qy), mul(qw, qz)));
-            Rq[4] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qz, qz))));
-            Rq[5] = mul(2.0f, sub(mul(qy, qz), mul(qw, qx)));
-            Rq[6] = mul(2.0f, sub(mul(qx, qz), mul(qw, qy)));
-            Rq[7] = mul(2.0f, add(mul(qy, qz), mul(qw, qx)));
-            Rq[8] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qy, qy))));
-            const float sc[3] = {expf(__ldg(vw.log_scales + 3 * i + 0)), expf(__ldg(vw.log_scales + 3 * i + 1)),
-                                 expf(__ldg(vw.log_scales + 3 * i + 2))};
-            float M[9];
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int k = 0; k < 3; k++) M[3 * r + k] = mul(Rq[3 * r + k], sc[k]);
-            // ---- T = J W (2x3), TM = T M, Sigma' = TM TM^T + 0.3 I
-            float Tm[6];
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                Tm[j] = add(mul(J00, R[j]), mul(J02, R[6 + j]));
-                Tm[3 + j] = add(mul(J11, R[3 + j]), mul(J12, R[6 + j]));
-            }
-            float TM[6];
-#pragma unroll
-            for (int r = 0; r < 2; r++)
-#pragma unroll
-                for (int k = 0; k < 3; k++)
-                    TM[3 * r + k] = add(add(mul(Tm[3 * r + 0], M[k]), mul(Tm[3 * r + 1], M[3 + k])), mul(Tm[3 * r + 2], M[6 + k]));
-            const float s00 = add(add(add(mul(TM[0], TM[0]), mul(TM[1], TM[1])), mul(TM[2], TM[2])), kDilation);
-            const float s01 = add(add(mul(TM[0], TM[3]), mul(TM[1], TM[4])), mul(TM[2], TM[5]));
-            const float s11 = add(add(add(mul(TM[3], TM[3]), mul(TM[4], TM[4])), mul(TM[5], TM[5])), kDilation);
+            Footprint f;
+            if (!(vw.kind == 0 ? footprint_disentangled(vw, i, f) : footprint_slicing(vw, i, f))) break;
+            const float m0 = f.m0, m1 = f.m1, m2 = f.m2, Z = f.Z, u = f.u, v = f.v, oh = f.oh;
+            const float s00 = f.s00, s01 = f.s01, s11 = f.s11;
             const float det = sub(mul(s00, s11), mul(s01, s01));
             if (!(det > 0.0f)) break;
             const float mid = mul(0.5f, add(s00, s11));
