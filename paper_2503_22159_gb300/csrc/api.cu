@@ -220,7 +220,9 @@ bool finish_batch(BatchArgs *b) {
     int lead = -1;
     for (int i = 0; i < b->nviews; i++) {
         View &v = b->v[i];
-        if (v.packed != b->packed || v.tile_passes != b->tile_passes || v.cam.tile != b->tile) return false;
+        if (v.packed != b->packed || v.tile_passes != b->tile_passes || v.cam.tile != b->tile ||
+            v.kind != b->v[0].kind)
+            return false;
         // time groups: a view joins the group of the view before it when it shares its scene and camera
         if (lead >= 0 && b->v[lead].group_size < kMaxGroup && same_scene_and_camera(b->v[lead], v)) {
             b->v[lead].group_size++;

@@ -156,81 +156,86 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
 // the 4D rotation from its quaternion pair (p -> q_l p q_r on p = t + x i +
 // y j + z k), Sigma4D = R4 S4^2 R4^T = [[U, V], [V^T, W]], and slices it at t:
 // Sigma3D = U - V V^T / W, mean mu + (t - mu_t) V / W, opacity times
-// exp(-(t - mu_t)^2 / (2 W)); then the same projection.  Ordinary FP32.
+// exp(-(t - mu_t)^2 / (2 W)); then the same projection.  Same arithmetic
+// rules as the disentangled form (separately rounded products and sums,
+// IEEE division and square root, full-precision exp), so the two are timed
+// like for like.
 __device__ __forceinline__ bool footprint_slicing(const View &vw, int i, Footprint &f) {
     const CamArgs &c = vw.cam;
+    const float limx = mul(kJacClamp, dvd(mul(0.5f, (float)c.width), c.fx));
+    const float limy = mul(kJacClamp, dvd(mul(0.5f, (float)c.height), c.fy));
     const float4 m4 = __ldg(reinterpret_cast<const float4 *>(vw.means4) + i);
     const float4 l4 = __ldg(reinterpret_cast<const float4 *>(vw.log_scales4) + i);
     float4 a = __ldg(reinterpret_cast<const float4 *>(vw.quat_l) + i);
     float4 b = __ldg(reinterpret_cast<const float4 *>(vw.quat_r) + i);
-    const float ia = rsqrtf(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
-    const float ib = rsqrtf(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
-    a = make_float4(a.x * ia, a.y * ia, a.z * ia, a.w * ia);
-    b = make_float4(b.x * ib, b.y * ib, b.z * ib, b.w * ib);
+    const float na = __fsqrt_rn(add(add(add(mul(a.x, a.x), mul(a.y, a.y)), mul(a.z, a.z)), mul(a.w, a.w)));
+    const float nb = __fsqrt_rn(add(add(add(mul(b.x, b.x), mul(b.y, b.y)), mul(b.z, b.z)), mul(b.w, b.w)));
+    a = make_float4(dvd(a.x, na), dvd(a.y, na), dvd(a.z, na), dvd(a.w, na));
+    b = make_float4(dvd(b.x, nb), dvd(b.y, nb), dvd(b.z, nb), dvd(b.w, nb));
     // left- and right-multiplication matrices in the quaternion basis (1, i, j, k)
     const float La[16] = {a.x, -a.y, -a.z, -a.w, a.y, a.x, -a.w, a.z, a.z, a.w, a.x, -a.y, a.w, -a.z, a.y, a.x};
     const float Rb[16] = {b.x, -b.y, -b.z, -b.w, b.y, b.x, b.w, -b.z, b.z, -b.w, b.x, b.y, b.w, b.z, -b.y, b.x};
     // R4 in (x, y, z, t) order: quaternion components (i, j, k, 1) = indices (1, 2, 3, 0)
     const int perm[4] = {1, 2, 3, 0};
-    const float s4[4] = {__expf(l4.x), __expf(l4.y), __expf(l4.z), __expf(l4.w)};
+    const float s4[4] = {expf(l4.x), expf(l4.y), expf(l4.z), expf(l4.w)};
     float M[16];   // M = R4 diag(s4)
 #pragma unroll
     for (int r = 0; r < 4; r++)
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const int pr = perm[r], pk = perm[k];
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 4; j++) acc += La[4 * pr + j] * Rb[4 * j + pk];
-            M[4 * r + k] = acc * s4[k];
+            const float acc = add(add(add(mul(La[4 * pr], Rb[pk]), mul(La[4 * pr + 1], Rb[4 + pk])),
+                                      mul(La[4 * pr + 2], Rb[8 + pk])), mul(La[4 * pr + 3], Rb[12 + pk]));
+            M[4 * r + k] = mul(acc, s4[k]);
         }
     auto sig = [&](int r, int q) {
-        return M[4 * r] * M[4 * q] + M[4 * r + 1] * M[4 * q + 1] + M[4 * r + 2] * M[4 * q + 2] + M[4 * r + 3] * M[4 * q + 3];
+        return add(add(add(mul(M[4 * r], M[4 * q]), mul(M[4 * r + 1], M[4 * q + 1])), mul(M[4 * r + 2], M[4 * q + 2])),
+                   mul(M[4 * r + 3], M[4 * q + 3]));
     };
     const float W = sig(3, 3);
     const float V0 = sig(0, 3), V1 = sig(1, 3), V2 = sig(2, 3);
-    const float iW = 1.0f / W;
-    const float S00 = sig(0, 0) - V0 * V0 * iW, S01 = sig(0, 1) - V0 * V1 * iW, S02 = sig(0, 2) - V0 * V2 * iW;
-    const float S11 = sig(1, 1) - V1 * V1 * iW, S12 = sig(1, 2) - V1 * V2 * iW, S22 = sig(2, 2) - V2 * V2 * iW;
-    const float tau = vw.t - m4.w;
-    const float m0 = m4.x + tau * V0 * iW, m1 = m4.y + tau * V1 * iW, m2 = m4.z + tau * V2 * iW;
+    const float v0 = dvd(V0, W), v1 = dvd(V1, W), v2 = dvd(V2, W);   // V / W
+    const float S00 = sub(sig(0, 0), mul(V0, v0)), S01 = sub(sig(0, 1), mul(V0, v1)), S02 = sub(sig(0, 2), mul(V0, v2));
+    const float S11 = sub(sig(1, 1), mul(V1, v1)), S12 = sub(sig(1, 2), mul(V1, v2)), S22 = sub(sig(2, 2), mul(V2, v2));
+    const float tau = sub(vw.t, m4.w);
+    const float m0 = add(m4.x, mul(tau, v0)), m1 = add(m4.y, mul(tau, v1)), m2 = add(m4.z, mul(tau, v2));
     const float *R = c.R;
-    const float X = R[0] * m0 + R[1] * m1 + R[2] * m2 + c.T[0];
-    const float Y = R[3] * m0 + R[4] * m1 + R[5] * m2 + c.T[1];
-    const float Z = R[6] * m0 + R[7] * m1 + R[8] * m2 + c.T[2];
+    const float X = add(add(add(mul(R[0], m0), mul(R[1], m1)), mul(R[2], m2)), c.T[0]);
+    const float Y = add(add(add(mul(R[3], m0), mul(R[4], m1)), mul(R[5], m2)), c.T[1]);
+    const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
     if (!(Z > kNear)) return false;
-    const float o = 1.0f / (1.0f + __expf(-__ldg(vw.opacity_logit + i)));
-    const float oh = o * __expf(-0.5f * tau * tau * iW);
+    const float o = dvd(1.0f, add(1.0f, expf(-__ldg(vw.opacity_logit + i))));
+    const float oh = mul(o, expf(dvd(mul(-0.5f, mul(tau, tau)), W)));
     if (!(oh >= kAlphaMin)) return false;
-    const float iZ = 1.0f / Z;
-    const float xz = X * iZ, yz = Y * iZ;
-    const float limx = kJacClamp * 0.5f * (float)c.width / c.fx, limy = kJacClamp * 0.5f * (float)c.height / c.fy;
+    const float xz = dvd(X, Z), yz = dvd(Y, Z);
     const float xzc = fminf(limx, fmaxf(-limx, xz)), yzc = fminf(limy, fmaxf(-limy, yz));
-    const float J00 = c.fx * iZ, J02 = -c.fx * xzc * iZ, J11 = c.fy * iZ, J12 = -c.fy * yzc * iZ;
+    const float J00 = dvd(c.fx, Z), J02 = dvd(-mul(c.fx, xzc), Z);
+    const float J11 = dvd(c.fy, Z), J12 = dvd(-mul(c.fy, yzc), Z);
     float Tm[6];   // J W (2 x 3)
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        Tm[j] = J00 * R[j] + J02 * R[6 + j];
-        Tm[3 + j] = J11 * R[3 + j] + J12 * R[6 + j];
+        Tm[j] = add(mul(J00, R[j]), mul(J02, R[6 + j]));
+        Tm[3 + j] = add(mul(J11, R[3 + j]), mul(J12, R[6 + j]));
     }
     const float S3[9] = {S00, S01, S02, S01, S11, S12, S02, S12, S22};
     float TS[6];   // (J W) Sigma3D
 #pragma unroll
     for (int r = 0; r < 2; r++)
 #pragma unroll
-        for (int k = 0; k < 3; k++) TS[3 * r + k] = Tm[3 * r] * S3[k] + Tm[3 * r + 1] * S3[3 + k] + Tm[3 * r + 2] * S3[6 + k];
+        for (int k = 0; k < 3; k++)
+            TS[3 * r + k] = add(add(mul(Tm[3 * r], S3[k]), mul(Tm[3 * r + 1], S3[3 + k])), mul(Tm[3 * r + 2], S3[6 + k]));
     f.m0 = m0; f.m1 = m1; f.m2 = m2;
-    f.Z = Z; f.u = c.fx * xz + c.cx; f.v = c.fy * yz + c.cy; f.oh = oh;
-    f.s00 = TS[0] * Tm[0] + TS[1] * Tm[1] + TS[2] * Tm[2] + kDilation;
-    f.s01 = TS[0] * Tm[3] + TS[1] * Tm[4] + TS[2] * Tm[5];
-    f.s11 = TS[3] * Tm[3] + TS[4] * Tm[4] + TS[5] * Tm[5] + kDilation;
+    f.Z = Z; f.u = add(mul(c.fx, xz), c.cx); f.v = add(mul(c.fy, yz), c.cy); f.oh = oh;
+    f.s00 = add(add(add(mul(TS[0], Tm[0]), mul(TS[1], Tm[1])), mul(TS[2], Tm[2])), kDilation);
+    f.s01 = add(add(mul(TS[0], Tm[3]), mul(TS[1], Tm[4])), mul(TS[2], Tm[5]));
+    f.s11 = add(add(add(mul(TS[3], Tm[3]), mul(TS[4], Tm[4])), mul(TS[5], Tm[5])), kDilation);
     return true;
 }
 
 // One Gaussian of view v: writes its 2D record, depth key, tile count and
 // rectangle, adds its rectangle to the view's difference grid, and counts it in
 // the shared depth-digit histogram.
-template <int DEG>
+template <int DEG, int KIND>
 __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *hist, uint32_t &nvis, int *sgrid) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const CamArgs &c = vw.cam;
@@ -241,7 +246,7 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         do {
             Footprint f;
-            if (!(vw.kind == 0 ? footprint_disentangled(vw, i, f) : footprint_slicing(vw, i, f))) break;
+            if (!(KIND == 0 ? footprint_disentangled(vw, i, f) : footprint_slicing(vw, i, f))) break;
             const float m0 = f.m0, m1 = f.m1, m2 = f.m2, Z = f.Z, u = f.u, v = f.v, oh = f.oh;
             const float s00 = f.s00, s01 = f.s01, s11 = f.s11;
             const float det = sub(mul(s00, s11), mul(s01, s01));
@@ -352,6 +357,8 @@ __device__ __forceinline__ void flush_view(const View &v, uint32_t *hist, uint32
 // view keeps its own shared-memory depth histogram, visible count and, when B
 // of them fit, tile-count grid.  The per-view arithmetic is the same as for a
 // view alone, so a grouped view's outputs equal the ungrouped ones bit for bit.
+// KIND: 0 disentangled, 1 slicing-first (every view of a launch has the same kind).
+template <int KIND>
 __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restrict__ ba, int smem_cells) {
     __shared__ uint32_t hist[kMaxGroup][4 * kRadix];
     __shared__ int32_t s_chunk;
@@ -400,10 +407,10 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restri
             int *sg = slot_grid(lead, b);
             if (i < v.n) {
                 switch (v.sh_degree) {
-                    case 0: preprocess_one<0>(v, i, hist[b], nvis[b], sg); break;
-                    case 1: preprocess_one<1>(v, i, hist[b], nvis[b], sg); break;
-                    case 2: preprocess_one<2>(v, i, hist[b], nvis[b], sg); break;
-                    default: preprocess_one<3>(v, i, hist[b], nvis[b], sg); break;
+                    case 0: preprocess_one<0, KIND>(v, i, hist[b], nvis[b], sg); break;
+                    case 1: preprocess_one<1, KIND>(v, i, hist[b], nvis[b], sg); break;
+                    case 2: preprocess_one<2, KIND>(v, i, hist[b], nvis[b], sg); break;
+                    default: preprocess_one<3, KIND>(v, i, hist[b], nvis[b], sg); break;
                 }
             }
         }
@@ -473,8 +480,12 @@ cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cud
     // persistent grid: 8 resident CTAs of 256 threads per SM; grids of up to
     // 6144 cells (e.g. 1352x1014 at 32-px tiles) are aggregated in shared memory
     constexpr int kSmemCells = 6144;
-    const cudaError_t e = launch_chained(preprocess_kernel, num_sms * 8, 256, kSmemCells * sizeof(int), st,
-                                         (const char *)batch_area, kSmemCells);
+    const cudaError_t e =
+        args.v[0].kind == 0
+            ? launch_chained(preprocess_kernel<0>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
+                             (const char *)batch_area, kSmemCells)
+            : launch_chained(preprocess_kernel<1>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
+                             (const char *)batch_area, kSmemCells);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
