@@ -405,6 +405,45 @@ def run_slicing_first(args, dev, d4):
     return out
 
 
+def run_backward(args, dev, d4, w, scene, cfg, cap):
+    """Backward pass (K7 tile replay + K8 preprocess adjoint) after each forward frame of the workload,
+    with a fixed seeded dL/dC: device time per frame of d4dgs_render_backward, L2 flushed between the
+    forward and the backward.  K8's algorithmic bytes: the raw parameters read (256 B at SH3), the 2D
+    gradient sums read (48 B) and the raw gradients written (256 B) per Gaussian."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    frames = [w.frames[k] for k in range(0, len(w.frames), 15)]
+    cam0 = frames[0][0]
+    ws = torch.empty(d4.d4dgs_workspace_bytes(scene.n, cam0, cfg, cap), dtype=torch.uint8, device=dev)
+    out = torch.empty((cam0.height, cam0.width, 3), device=dev)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    dl = torch.randn((cam0.height, cam0.width, 3), generator=g).to(dev)
+    grads = scene.zeros_like_grad()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    evs = []
+    for rep in range(2):
+        for k, (cam, t) in enumerate(frames):
+            d4.d4dgs_render(scene, cam, t, cfg, ws, out, stream)
+            torch.cuda._sleep(1_000_000)
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d4.d4dgs_render_backward(scene, cam, t, cfg, ws, dl, grads, stream)
+            e1.record(stream)
+            if rep:
+                evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    if d4.d4dgs_read_stats(scene.n, cam0, cfg, ws)["status"] != 0:
+        raise RuntimeError("backward frame reported an error")
+    if not all(bool(torch.isfinite(v).all()) for v in grads.values()):
+        raise RuntimeError("non-finite gradients")
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    sh_bytes = 4 * 3 * (w.scene.sh_degree + 1) ** 2
+    return {"ms_per_frame": ms, "frames": len(frames), "frames_per_s": 1e3 / ms,
+            "k8_bytes_per_frame": scene.n * (64 + sh_bytes + 48 + 64 + sh_bytes)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -564,6 +603,7 @@ def run_ours(args):
                "steps": E, "api": "d4dgs_render_host"}
 
     groups_out = slicing_out = None
+    backward_out = run_backward(args, dev, d4, w, scene, cfg, r.key_capacity) if world == 1 else None
     if not args.no_serving and world == 1:
         groups_out = run_time_groups(args, dev, d4, w, scene, cfg, r.key_capacity, peaks)
         slicing_out = run_slicing_first(args, dev, d4)
@@ -587,7 +627,7 @@ def run_ours(args):
         "gpu_launches": int(launches * K), "launches_per_frame": launches,
         "wall_s_timed_region": t_wall, "peaks": peak_kind,
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out, "time_groups": groups_out,
-        "slicing_first": slicing_out,
+        "slicing_first": slicing_out, "backward": backward_out,
         "autotune": {"chosen": f"{args.tile}/{args.batch}", "ms_per_frame": tune_table} if tune_table else None,
     }
     print(json.dumps(line), flush=True)

@@ -19,14 +19,14 @@
 //   the preprocess in reverse (conic -> Sigma' -> J W M -> J(X), R(q), scales;
 //   (u, v)(X); SH colour and its view direction; X(mu(t)); mu(t) = mu + tau V;
 //   o_hat(logit, tau, log s_t); tau = t - mu_t), writing every raw gradient.
+#include "blend_common.cuh"
+#include "blend_mask.cuh"
 #include "d4dgs_internal.cuh"
 
 namespace d4dgs {
 
 namespace {
 
-constexpr float kLog2e = 1.4426950408889634f;
-constexpr float kLog2AlphaMin = -7.9943534368588578f;   // log2(1/255)
 constexpr int kG2 = 12;   // floats per Gaussian in the 2D gradient buffer (9 used)
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -35,58 +35,84 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// K7: one CTA per tile, the forward's pixel layout (a column of PX pixels per
+// thread, a warp per 8 x 4PX block).  The tile's list is staged in batches
+// from the back (with the forward's per-block masks); each warp walks its
+// Gaussians from the highest position down, skipping those whose
+// alpha >= 1/255 ellipse misses its block or that lie past every pixel's
+// walked range.  Per pixel the exponent is the forward's, so the same pairs
+// pass and alpha has the same bits.  A thread sums its pixels' gradients;
+// a warp reduces them once per Gaussian and adds them into shared memory;
+// each batch is flushed to the global 2D-gradient sums once per Gaussian.
 template <int TS, int BATCH>
-__global__ void __launch_bounds__(TS *TS)
+__global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 16 : (TS == 16 ? 8 : 2))
 blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_drgb) {
+    using S = BlendShape<TS>;
+    constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
     const View &v = view_of(ba, 0);
-    const uint2 *ranges = v.ranges;
     const uint32_t id_mask = v.packed ? (uint32_t)((1ull << v.id_bits) - 1ull) : 0xFFFFFFFFu;
     const uint32_t *ids = v.packed ? v.tkeys[v.tile_passes & 1] : v.tvals[v.tile_passes & 1];
     const float4 *rec = v.rec;
     const uint32_t n = (uint32_t)v.n, cap = v.cap;
     const int width = v.cam.width, height = v.cam.height, tiles_x = v.cam.tiles_x;
-    const float bg0 = v.bg[0], bg1 = v.bg[1], bg2 = v.bg[2];
-    const float *final_T = v.final_T;
-    const uint32_t *n_contrib = v.n_contrib;
     float *g2 = v.grad2d;
-    constexpr int NT = TS * TS;
-    constexpr int NW = NT / 32;
-    __shared__ float4 s_g[BATCH];     // u, v, A, B      (forward exponent form)
-    __shared__ float2 s_h[BATCH];     // C, L
+    __shared__ float4 s_ua[BATCH];    // u, u, A, A (forward exponent form, pairs)
+    __shared__ float4 s_bc[BATCH];    // B, B, C, C
+    __shared__ float4 s_vl[BATCH];    // v, v, L, L
     __shared__ float4 s_c[BATCH];     // r, g, b
-    __shared__ float4 s_k[BATCH];     // a, b, c, o_hat  (natural conic)
+    __shared__ float4 s_k[BATCH];     // a, b, c, o_hat (natural conic)
+    __shared__ uint32_t s_m[BATCH];   // blocks the alpha >= 1/255 ellipse reaches
     __shared__ uint32_t s_id[BATCH];
     __shared__ float s_acc[BATCH][9];
-    __shared__ uint32_t s_maxlast;
+    __shared__ uint32_t s_maxw;
 
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int lane = threadIdx.x & 31;
-    const int px = tx * TS + (int)(threadIdx.x % TS), py = ty * TS + (int)(threadIdx.x / TS);
-    const bool inside = px < width && py < height;
-    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    uint2 rg = ranges[tile];
+    const int x0 = tx * TS, y0 = ty * TS;
+    const int lane = (int)(threadIdx.x & 31u), warp = (int)(threadIdx.x >> 5);
+    const int px = x0 + 8 * (warp % BX) + (lane & 7);
+    const int py = y0 + BH * (warp / BX) + PX * (lane >> 3);
+    const float pxf = (float)px + 0.5f;
+    const float2 pxf2 = make_float2(pxf, pxf);
+    uint2 rg = v.ranges[tile];
     rg.y = min(rg.y, cap);
     rg.x = min(rg.x, rg.y);
+    const uint32_t len = rg.y - rg.x;
 
-    float T = 1.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f, B0 = bg0, B1 = bg1, B2 = bg2;
-    uint32_t last = 0;
-    if (inside) {
-        const size_t p = (size_t)py * width + px;
-        T = final_T[p];
-        last = min(n_contrib[p], rg.y - rg.x);
-        G0 = dl_drgb[3 * p + 0];
-        G1 = dl_drgb[3 * p + 1];
-        G2 = dl_drgb[3 * p + 2];
+    float2 pyf[NP];
+    float T[PX], G[PX][3], Bc[PX][3];
+    uint32_t walked[PX];
+    uint32_t tmax = 0;
+#pragma unroll
+    for (int j = 0; j < NP; j++) pyf[j] = make_float2((float)(py + 2 * j) + 0.5f, (float)(py + 2 * j + 1) + 0.5f);
+#pragma unroll
+    for (int i = 0; i < PX; i++) {
+        T[i] = 1.0f;
+        walked[i] = 0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            G[i][c] = 0.0f;
+            Bc[i][c] = v.bg[c];
+        }
+        if (px < width && py + i < height) {
+            const size_t p = (size_t)(py + i) * width + px;
+            T[i] = v.final_T[p];
+            walked[i] = min(v.n_contrib[p], len);
+#pragma unroll
+            for (int c = 0; c < 3; c++) G[i][c] = dl_drgb[3 * p + c];
+        }
+        tmax = max(tmax, walked[i]);
     }
-    if (threadIdx.x == 0) s_maxlast = 0;
+    const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, tmax);
+    if (threadIdx.x == 0) s_maxw = 0;
     __syncthreads();
-    atomicMax(&s_maxlast, last);
+    if (lane == 0) atomicMax(&s_maxw, wmax);
     __syncthreads();
-    const uint32_t maxlast = s_maxlast;
+    const uint32_t maxw = s_maxw;
+    const uint32_t wbit = 1u << warp;
 
-    // positions are 1-based: list entry rg.x + pos - 1; walk pos = maxlast .. 1 in batches
-    for (int32_t hi = (int32_t)maxlast; hi > 0; hi -= BATCH) {
+    // positions are 1-based: list entry rg.x + pos - 1; walk pos = maxw .. 1 in batches
+    for (int32_t hi = (int32_t)maxw; hi > 0; hi -= BATCH) {
         const int32_t lo = max(hi - BATCH, 0);   // this batch covers positions lo+1 .. hi
         const int nb = hi - lo;
         for (int k = threadIdx.x; k < nb; k += NT) {
@@ -95,72 +121,102 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
             const float4 r0 = rec[3 * (size_t)id + 0];
             const float4 r1 = rec[3 * (size_t)id + 1];
             const float4 r2 = rec[3 * (size_t)id + 2];
-            s_g[k] = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
-            s_h[k] = make_float2(-0.5f * kLog2e * r1.x, r2.w);
+            const float A = -0.5f * kLog2e * r0.z, B = -kLog2e * r0.w, C = -0.5f * kLog2e * r1.x;
+            s_ua[k] = make_float4(r0.x, r0.x, A, A);
+            s_bc[k] = make_float4(B, B, C, C);
+            s_vl[k] = make_float4(r0.y, r0.y, r2.w, r2.w);
             s_c[k] = r2;
             s_k[k] = make_float4(r0.z, r0.w, r1.x, r1.y);
+            s_m[k] = d4dgs::block_mask<TS, BH>(r0.x, r0.y, A, B, C, r2.w, x0, y0);
             s_id[k] = id;
 #pragma unroll
             for (int j = 0; j < 9; j++) s_acc[k][j] = 0.0f;
         }
         __syncthreads();
-        for (int k = nb - 1; k >= 0; k--) {
-            const uint32_t pos = (uint32_t)(lo + k + 1);
-            float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
-            bool contrib = false;
-            if (pos <= last) {
-                const float4 g = s_g[k];
-                const float2 h = s_h[k];
-                const float dx = g.x - pxf;
-                const float axx = g.z * dx * dx, bx = g.w * dx;
-                const float dy = g.y - pyf;
-                const float p2 = fmaf(fmaf(h.x, dy, bx), dy, axx);
-                const float q = p2 + h.y;
-                if (p2 <= 0.0f && q >= kLog2AlphaMin) {
-                    const float raw = alpha_exp2(q);
-                    const float alpha = fminf(kAlphaMax, raw);
-                    const float Ti = T / (1.0f - alpha);
-                    const float4 c = s_c[k];
-                    const float w = alpha * Ti;
-                    gr = w * G0;
-                    gg = w * G1;
-                    gbl = w * G2;
-                    const float dalpha = Ti * (G0 * (c.x - B0) + G1 * (c.y - B1) + G2 * (c.z - B2));
-                    B0 = alpha * c.x + (1.0f - alpha) * B0;
-                    B1 = alpha * c.y + (1.0f - alpha) * B1;
-                    B2 = alpha * c.z + (1.0f - alpha) * B2;
-                    T = Ti;
-                    if (raw <= kAlphaMax) {
-                        const float4 kk = s_k[k];
-                        const float dp = dalpha * alpha;
-                        go = dp / kk.w;
-                        gu = -dp * (kk.x * dx + kk.y * dy);
-                        gv = -dp * (kk.y * dx + kk.z * dy);
-                        ga = -0.5f * dp * dx * dx;
-                        gb = -dp * dx * dy;
-                        gc = -0.5f * dp * dy * dy;
+        if ((uint32_t)lo < wmax) {
+            // chunks of 32 from the top of the batch; within a chunk, set bits from the highest
+            for (int k0 = ((nb - 1) / 32) * 32; k0 >= 0; k0 -= 32) {
+                const int kl = k0 + lane;
+                const bool want = kl < nb && (s_m[kl] & wbit) != 0u && (uint32_t)(lo + kl) < wmax;
+                uint32_t bits = __ballot_sync(0xFFFFFFFFu, want);
+                while (bits) {
+                    const int b = 31 - __clz((int)bits);
+                    bits &= ~(1u << b);
+                    const int k = k0 + b;
+                    const uint32_t pos = (uint32_t)(lo + k + 1);
+                    const float4 ua = s_ua[k], bc = s_bc[k], vl = s_vl[k];
+                    const float2 dx2 = f2_sub(make_float2(ua.x, ua.y), pxf2);
+                    const float2 axx = f2_mul(f2_mul(make_float2(ua.z, ua.w), dx2), dx2);
+                    const float2 bx = f2_mul(make_float2(bc.x, bc.y), dx2);
+                    float q[PX], p[PX], dy[PX];
+                    bool e[PX];
+                    bool any = false;
+#pragma unroll
+                    for (int j = 0; j < NP; j++) {
+                        const float2 d = f2_sub(make_float2(vl.x, vl.y), pyf[j]);
+                        const float2 pp = f2_fma(f2_fma(make_float2(bc.z, bc.w), d, bx), d, axx);
+                        const float2 qq = f2_add(pp, make_float2(vl.z, vl.w));
+                        p[2 * j] = pp.x; p[2 * j + 1] = pp.y;
+                        q[2 * j] = qq.x; q[2 * j + 1] = qq.y;
+                        dy[2 * j] = d.x; dy[2 * j + 1] = d.y;
                     }
-                    contrib = true;
-                }
-            }
-            if (__any_sync(0xFFFFFFFFu, contrib)) {
-                gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga); gb = warp_sum(gb); gc = warp_sum(gc);
-                go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl);
-                if (lane == 0) {
-                    float *acc = s_acc[k];
-                    atomicAdd(acc + 0, gu); atomicAdd(acc + 1, gv); atomicAdd(acc + 2, ga);
-                    atomicAdd(acc + 3, gb); atomicAdd(acc + 4, gc); atomicAdd(acc + 5, go);
-                    atomicAdd(acc + 6, gr); atomicAdd(acc + 7, gg); atomicAdd(acc + 8, gbl);
+#pragma unroll
+                    for (int i = 0; i < PX; i++) {
+                        e[i] = pos <= walked[i] && p[i] <= 0.0f && q[i] >= kLog2AlphaMin;
+                        any |= e[i];
+                    }
+                    float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
+                    if (any) {
+                        const float4 c = s_c[k];
+                        const float4 kk = s_k[k];
+                        const float dx = dx2.x;
+#pragma unroll
+                        for (int i = 0; i < PX; i++) {
+                            if (!e[i]) continue;
+                            const float raw = alpha_exp2(q[i]);
+                            const float alpha = fminf(kAlphaMax, raw);
+                            const float Ti = T[i] / (1.0f - alpha);
+                            const float w = alpha * Ti;
+                            gr += w * G[i][0];
+                            gg += w * G[i][1];
+                            gbl += w * G[i][2];
+                            const float dalpha =
+                                Ti * (G[i][0] * (c.x - Bc[i][0]) + G[i][1] * (c.y - Bc[i][1]) + G[i][2] * (c.z - Bc[i][2]));
+                            Bc[i][0] = alpha * c.x + (1.0f - alpha) * Bc[i][0];
+                            Bc[i][1] = alpha * c.y + (1.0f - alpha) * Bc[i][1];
+                            Bc[i][2] = alpha * c.z + (1.0f - alpha) * Bc[i][2];
+                            T[i] = Ti;
+                            if (raw <= kAlphaMax) {
+                                const float dp = dalpha * alpha, ddy = dy[i];
+                                go += dp / kk.w;
+                                gu += -dp * (kk.x * dx + kk.y * ddy);
+                                gv += -dp * (kk.y * dx + kk.z * ddy);
+                                ga += -0.5f * dp * dx * dx;
+                                gb += -dp * dx * ddy;
+                                gc += -0.5f * dp * ddy * ddy;
+                            }
+                        }
+                    }
+                    if (__any_sync(0xFFFFFFFFu, any)) {
+                        gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga); gb = warp_sum(gb); gc = warp_sum(gc);
+                        go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl);
+                        if (lane == 0) {
+                            float *acc = s_acc[k];
+                            atomicAdd(acc + 0, gu); atomicAdd(acc + 1, gv); atomicAdd(acc + 2, ga);
+                            atomicAdd(acc + 3, gb); atomicAdd(acc + 4, gc); atomicAdd(acc + 5, go);
+                            atomicAdd(acc + 6, gr); atomicAdd(acc + 7, gg); atomicAdd(acc + 8, gbl);
+                        }
+                    }
                 }
             }
         }
         __syncthreads();
         // flush: one set of global atomics per (tile, Gaussian) that received anything
         for (int k = threadIdx.x; k < nb; k += NT) {
-            bool any = false;
+            bool anyg = false;
 #pragma unroll
-            for (int j = 0; j < 9; j++) any |= s_acc[k][j] != 0.0f;
-            if (any) {
+            for (int j = 0; j < 9; j++) anyg |= s_acc[k][j] != 0.0f;
+            if (anyg) {
                 float *dst = g2 + (size_t)s_id[k] * kG2;
 #pragma unroll
                 for (int j = 0; j < 9; j++)
@@ -169,7 +225,6 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
         }
         __syncthreads();
     }
-    (void)NW;
 }
 
 // ---------------------------------------------------------------------------
@@ -403,7 +458,7 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
 
 template <int TS, int BATCH>
 void launch_bb(const char *ba, int ntiles, const float *dl, cudaStream_t st) {
-    blend_backward_kernel<TS, BATCH><<<ntiles, TS * TS, 0, st>>>(ba, dl);
+    blend_backward_kernel<TS, BATCH><<<ntiles, BlendShape<TS>::NT, 0, st>>>(ba, dl);
 }
 
 }  // namespace
