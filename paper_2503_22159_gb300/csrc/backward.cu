@@ -35,6 +35,30 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Warp sums of 8 values at once: three exchange steps (offsets 16, 8, 4) each
+// hand half of a lane's remaining values to its partner and keep the sums of
+// the other half, then two plain steps (offsets 2, 1) finish a single value.
+// 9 shuffles instead of 40; afterwards lane L holds the total of value
+// ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).
+__device__ __forceinline__ float warp_sum8(const float (&x)[8], int lane) {
+    float v4[4], v2[2];
+    const bool h16 = (lane >> 4) & 1, h8 = (lane >> 3) & 1, h4 = (lane >> 2) & 1;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const float send = h16 ? x[j] : x[j + 4], keep = h16 ? x[j + 4] : x[j];
+        v4[j] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        const float send = h8 ? v4[j] : v4[j + 2], keep = h8 ? v4[j + 2] : v4[j];
+        v2[j] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+    }
+    float v = (h4 ? v2[1] : v2[0]) + __shfl_xor_sync(0xFFFFFFFFu, h4 ? v2[0] : v2[1], 4);
+    v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+    v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+    return v;
+}
+
 // K7: one CTA per tile, the forward's pixel layout (a column of PX pixels per
 // thread, a warp per 8 x 4PX block).  The tile's list is staged in batches
 // from the back (with the forward's per-block masks); each warp walks its
@@ -175,7 +199,7 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                             if (!e[i]) continue;
                             const float raw = alpha_exp2(q[i]);
                             const float alpha = fminf(kAlphaMax, raw);
-                            const float Ti = T[i] / (1.0f - alpha);
+                            const float Ti = __fdividef(T[i], 1.0f - alpha);
                             const float w = alpha * Ti;
                             gr += w * G[i][0];
                             gg += w * G[i][1];
@@ -188,7 +212,7 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                             T[i] = Ti;
                             if (raw <= kAlphaMax) {
                                 const float dp = dalpha * alpha, ddy = dy[i];
-                                go += dp / kk.w;
+                                go += __fdividef(dp, kk.w);
                                 gu += -dp * (kk.x * dx + kk.y * ddy);
                                 gv += -dp * (kk.y * dx + kk.z * ddy);
                                 ga += -0.5f * dp * dx * dx;
@@ -198,14 +222,14 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                         }
                     }
                     if (__any_sync(0xFFFFFFFFu, any)) {
-                        gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga); gb = warp_sum(gb); gc = warp_sum(gc);
-                        go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl);
-                        if (lane == 0) {
-                            float *acc = s_acc[k];
-                            atomicAdd(acc + 0, gu); atomicAdd(acc + 1, gv); atomicAdd(acc + 2, ga);
-                            atomicAdd(acc + 3, gb); atomicAdd(acc + 4, gc); atomicAdd(acc + 5, go);
-                            atomicAdd(acc + 6, gr); atomicAdd(acc + 7, gg); atomicAdd(acc + 8, gbl);
+                        const float x8[8] = {gu, gv, ga, gb, gc, gr, gg, gbl};
+                        const float tot = warp_sum8(x8, lane);
+                        const float tgo = warp_sum(go);
+                        if ((lane & 3) == 0) {   // lanes 0, 4, .., 28 hold values 0..7
+                            const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                            atomicAdd(&s_acc[k][idx < 5 ? idx : idx + 1], tot);
                         }
+                        if (lane == 0) atomicAdd(&s_acc[k][5], tgo);
                     }
                 }
             }
