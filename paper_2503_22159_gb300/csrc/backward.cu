@@ -69,7 +69,7 @@ __device__ __forceinline__ float warp_sum8(const float (&x)[8], int lane) {
 // a warp reduces them once per Gaussian and adds them into shared memory;
 // each batch is flushed to the global 2D-gradient sums once per Gaussian.
 template <int TS, int BATCH>
-__global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 16 : (TS == 16 ? 8 : 2))
+__global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 16 : (TS == 16 ? 8 : 3))
 blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_drgb) {
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
