@@ -49,11 +49,9 @@ __global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 24 : (TS == 16 ?
 blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts) {
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
-    __shared__ float4 s_ua[BATCH];   // u, u, A, A
-    __shared__ float4 s_bc[BATCH];   // B, B, C, C
-    __shared__ float4 s_vl[BATCH];   // v, v, L, L
-    __shared__ float4 s_rg[BATCH];   // r, r, g, g
-    __shared__ float2 s_bl[BATCH];   // b, b
+    // one 128-byte record per staged Gaussian (one address for all of its loads):
+    // [0] u, u, A, A  [1] B, B, C, C  [2] v, v, L, L  [3] r, r, g, g  [4] b, b
+    __shared__ float4 s_rec[BATCH][8];
     __shared__ uint32_t s_m[BATCH];  // blocks the Gaussian's alpha >= 1/255 ellipse reaches
     __shared__ int32_t s_item;
     __shared__ uint32_t s_stop;
@@ -131,11 +129,11 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     const float4 r1 = rec[3 * (size_t)id + 1];
                     const float4 r2 = rec[3 * (size_t)id + 2];
                     const float A = -0.5f * kLog2e * r0.z, B = -kLog2e * r0.w, C = -0.5f * kLog2e * r1.x;
-                    s_ua[k] = make_float4(r0.x, r0.x, A, A);
-                    s_bc[k] = make_float4(B, B, C, C);
-                    s_vl[k] = make_float4(r0.y, r0.y, r2.w, r2.w);
-                    s_rg[k] = make_float4(r2.x, r2.x, r2.y, r2.y);
-                    s_bl[k] = make_float2(r2.z, r2.z);
+                    s_rec[k][0] = make_float4(r0.x, r0.x, A, A);
+                    s_rec[k][1] = make_float4(B, B, C, C);
+                    s_rec[k][2] = make_float4(r0.y, r0.y, r2.w, r2.w);
+                    s_rec[k][3] = make_float4(r2.x, r2.x, r2.y, r2.y);
+                    s_rec[k][4] = make_float4(r2.z, r2.z, 0.0f, 0.0f);
                     const float det4 = fmaf(4.0f * A, C, -(B * B)), tr = -(A + C);
                     const bool fast = r2.w <= kLog2FastOpacity && det4 > kFastConditioning * tr * tr;
                     s_m[k] = d4dgs::block_mask<TS, BH>(r0.x, r0.y, A, B, C, r2.w, x0, y0) | (fast ? 0u : kSlowBit);
@@ -149,7 +147,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
             // per-pixel selects run only when one of the thread's pixels stops.
             auto visit = [&](auto fast_c, int k) {
                 constexpr bool FAST = decltype(fast_c)::value;
-                const float4 ua = s_ua[k], bc = s_bc[k], vl = s_vl[k];
+                const float4 ua = s_rec[k][0], bc = s_rec[k][1], vl = s_rec[k][2];
                 const float2 dx = f2_sub(make_float2(ua.x, ua.y), pxf2);
                 const float2 axx = f2_mul(f2_mul(make_float2(ua.z, ua.w), dx), dx);
                 const float2 bx = f2_mul(make_float2(bc.x, bc.y), dx);
@@ -183,10 +181,10 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     test[j] = f2_mul(T[j], f2_sub(one2, al[j]));
                     any_stop |= (test[j].x < kTMin) | (test[j].y < kTMin);
                 }
-                const float4 rgc = s_rg[k];
-                const float2 bl = s_bl[k];
+                const float4 rgc = s_rec[k][3];
+                const float2 bl = make_float2(s_rec[k][4].x, s_rec[k][4].y);
                 const uint32_t pos = start - rg.x + (uint32_t)k + 1u;
-                if (!any_stop) {
+                if (!__any_sync(0xFFFFFFFFu, any_stop)) {   // warp-uniform: no pixel of the warp stops here
 #pragma unroll
                     for (int j = 0; j < NP; j++) {
                         const float2 w = f2_mul(al[j], T[j]);
