@@ -376,3 +376,64 @@ def render_slicing(scene4d, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0), eps_
     """Slice every 4D Gaussian at t (Eq. 5-7), then render the static 3D result in FP64."""
     static, cov6 = slice4d(scene4d, t)
     return render(static, cam, t, pixels=pixels, bg=bg, cov3d=cov6, eps_px=eps_px)
+
+
+# ---------------------------------------------------------------------------
+# Optical-flow channel and the flow-gradient consistency loss (Sec. III-C,
+# Eq. 13, 17-18), FP64.  Readings: a Gaussian's flow is its ray-space velocity
+# (Eq. 13) in pixels, (fx V_x / Z, fy V_y / Z) with V the camera-frame velocity
+# and Z the depth of the time-shifted mean; it is blended with the colour
+# weights (alpha_i T_i, background 0).  Gradients use the 3x3 Sobel operator
+# with replicated borders; the flow-magnitude gradient is divided by the
+# kernel weight 8; the image-gradient magnitude (over the three channels) is
+# divided by its maximum over the image and held fixed as a guide.
+
+def flow_g2d(scene, cam, t: float) -> np.ndarray:
+    """(N, 2) screen velocity in pixels per unit time of every Gaussian at t."""
+    m = _d(scene.means).reshape(-1, 3) + (t - _d(scene.t_mean))[:, None] * _d(scene.velocity).reshape(-1, 3)
+    R, T = _d(cam.R).reshape(3, 3), _d(cam.T).reshape(3)
+    X = m @ R.T + T
+    Vc = _d(scene.velocity).reshape(-1, 3) @ R.T
+    return np.stack([cam.fx * Vc[:, 0] / X[:, 2], cam.fy * Vc[:, 1] / X[:, 2]], axis=1)
+
+
+def render_flow(scene, cam, t: float, pixels=None, eps_px=None) -> dict:
+    """The blended flow image (H, W, 2) (or (M, 2) at `pixels`), composited with the colour
+    weights; the slack is the per-pixel bound of `render` with the flow as colour."""
+    g = preprocess(scene, cam, t)
+    f = flow_g2d(scene, cam, t)
+    gf = dict(g)
+    gf["rgb"] = np.column_stack([f, np.zeros(len(f))])
+    out = render_g2d(gf, cam, pixels=pixels, bg=(0.0, 0.0, 0.0), eps_px=eps_px)
+    return dict(flow=out["rgb"][..., :2], slack=out["slack"], T=out["T"])
+
+
+def _sobel(img: np.ndarray):
+    """Sobel x / y responses of an (H, W) image with replicated borders (kernel weights 1, 2, 1)."""
+    p = np.pad(img, 1, mode="edge")
+    H, W = img.shape
+    s = lambda dy, dx: p[1 + dy:1 + dy + H, 1 + dx:1 + dx + W]
+    gx = (s(-1, 1) + 2 * s(0, 1) + s(1, 1)) - (s(-1, -1) + 2 * s(0, -1) + s(1, -1))
+    gy = (s(1, -1) + 2 * s(1, 0) + s(1, 1)) - (s(-1, -1) + 2 * s(-1, 0) + s(-1, 1))
+    return gx, gy
+
+
+def image_edge_weight(rgb: np.ndarray) -> np.ndarray:
+    """1 - |grad I| / max |grad I| (the fixed guide of Eq. 18); 1 where the image is flat."""
+    rgb = _d(rgb)
+    g2 = np.zeros(rgb.shape[:2])
+    for c in range(3):
+        gx, gy = _sobel(rgb[..., c])
+        g2 += gx * gx + gy * gy
+    g = np.sqrt(g2)
+    mx = g.max()
+    return 1.0 - (g / mx if mx > 0 else np.zeros_like(g))
+
+
+def flow_gradient_loss(flow: np.ndarray, weight: np.ndarray, lam: float = 1.0, eps: float = 1e-6) -> float:
+    """Eq. 17-18: lambda / N * sum |grad M| * weight with M = sqrt(u^2 + v^2 + eps)."""
+    flow = _d(flow)
+    M = np.sqrt(flow[..., 0] ** 2 + flow[..., 1] ** 2 + eps)
+    gx, gy = _sobel(M)
+    nrm = np.sqrt(gx * gx + gy * gy) / 8.0
+    return float(lam * np.mean(nrm * _d(weight)))

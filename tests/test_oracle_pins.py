@@ -512,3 +512,61 @@ def test_slicing_without_space_time_mixing_equals_the_disentangled_render():
         b = oracle.render(dis, cam, t)
         np.testing.assert_allclose(a["rgb"], b["rgb"], atol=1e-12)
         assert np.abs(a["rgb"]).max() > 0.05
+
+
+# ---------------------------------------------------------------------------
+# optical-flow channel and flow-gradient loss (Eq. 13, 17-18)
+
+def test_flow_single_gaussian_closed_form():
+    """One Gaussian on the optical axis moving along x: its flow is fx V_x / Z (Eq. 13 in pixels), and
+    the blended flow at a pixel is alpha times that (a single contributor, background 0)."""
+    Z, vx, fx = 4.0, 0.3, 60.0
+    sc = scene64([[0.0, 0.0, Z]], velocity=[[vx, 0.0, 0.0]], t_mean=[0.5], opacity=[0.8],
+                 log_scales=[[math.log(0.05)] * 3])
+    cam = camera(width=32, height=24, fx=fx, fy=fx)
+    f = oracle.flow_g2d(sc, cam, 0.5)
+    assert f[0, 0] == pytest.approx(fx * vx / Z, rel=1e-14) and f[0, 1] == 0.0
+    out = oracle.render_flow(sc, cam, 0.5)
+    img = oracle.render(sc, cam, 0.5)
+    alpha = 1.0 - img["T"]            # one Gaussian: T = 1 - alpha where it is blended
+    np.testing.assert_allclose(out["flow"][..., 0], alpha * fx * vx / Z, atol=1e-14)
+    assert np.abs(out["flow"][..., 1]).max() == 0.0 and alpha.max() > 0.3
+
+
+def test_flow_of_a_moving_mean_matches_the_finite_difference_of_its_projection():
+    """d u / dt of the projected time-shifted mean, minus the depth-change term that Eq. 13 leaves out,
+    equals the flow: (u(t+h) - u(t-h)) / 2h = fx V_x / Z - fx X V_z / Z^2."""
+    rng = np.random.default_rng(26)
+    sc = scene64(rng.uniform(-0.5, 0.5, (5, 3)) + [0, 0, 3.0], velocity=rng.normal(0, 0.4, (5, 3)),
+                 t_mean=rng.uniform(0, 1, 5))
+    cam = camera(width=40, height=30, fx=50.0, fy=45.0)
+    t, h = 0.4, 1e-6
+    f = oracle.flow_g2d(sc, cam, t)
+    gp, gm = oracle.preprocess(sc, cam, t + h, temporal_cull=False), oracle.preprocess(sc, cam, t - h, temporal_cull=False)
+    du = (gp["u"] - gm["u"]) / (2 * h)
+    m = sc.means + (t - sc.t_mean)[:, None] * sc.velocity
+    Z = m[:, 2]
+    np.testing.assert_allclose(du, f[:, 0] - cam.fx * m[:, 0] * sc.velocity[:, 2] / Z ** 2, rtol=1e-6, atol=1e-6)
+
+
+def test_flow_gradient_loss_closed_forms():
+    """A constant flow gives 0; a flow ramp u = a x + b on a flat image gives lambda a (W - 1) / W with
+    replicated borders (the two border columns see half the ramp)."""
+    H, W = 12, 17
+    flat = np.full((H, W, 3), 0.4)
+    wgt = oracle.image_edge_weight(flat)
+    assert np.all(wgt == 1.0)
+    const = np.zeros((H, W, 2)); const[..., 0] = 3.0
+    assert oracle.flow_gradient_loss(const, wgt, lam=2.0) == pytest.approx(0.0, abs=1e-12)
+    a, b = 0.25, 50.0
+    ramp = np.zeros((H, W, 2)); ramp[..., 0] = a * np.arange(W)[None, :] + b
+    L = oracle.flow_gradient_loss(ramp, wgt, lam=2.0, eps=0.0)
+    assert L == pytest.approx(2.0 * a * (W - 1) / W, rel=1e-12)
+
+
+def test_image_edge_weight_is_one_minus_normalised_sobel():
+    """A vertical step edge: the weight is 0 on the two columns next to the step, 1 elsewhere."""
+    img = np.zeros((8, 10, 3)); img[:, 5:, :] = 1.0
+    w = oracle.image_edge_weight(img)
+    np.testing.assert_allclose(w[:, [4, 5]], 0.0, atol=1e-15)
+    np.testing.assert_allclose(np.delete(w, [4, 5], axis=1), 1.0)
