@@ -191,6 +191,35 @@ int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, flo
                           void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
                           d4dgs_stream_t stream);
 
+/* ---- optical-flow channel and flow-gradient consistency loss (Sec. III-C) -
+ * A Gaussian's screen flow is its ray-space velocity (Eq. 13) in pixels per
+ * unit time, (fx V_x / Z, fy V_y / Z) with V the camera-frame velocity and Z
+ * the depth of the time-shifted mean; the flow image composites it with the
+ * colour weights (background 0).
+ * out_flow: H x W x 2 float32 device, caller-owned, overwritten.  Otherwise
+ * as d4dgs_render, whose outputs (image, T, walked entries) it also writes. */
+int d4dgs_render_flow(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                      void *ws, size_t ws_bytes, float *out_rgb, float *out_flow, d4dgs_stream_t stream);
+/* Backward of d4dgs_render_flow: as d4dgs_render_backward, with dL/dF
+ * (H x W x 2 float32 device) of the flow image as well; the workspace must
+ * hold the d4dgs_render_flow frame with the same arguments. */
+int d4dgs_render_backward_flow(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                               void *ws, size_t ws_bytes, const float *dl_drgb, const float *dl_dflow,
+                               d4dgs_scene_grad *grad, d4dgs_stream_t stream);
+/* Scratch bytes of d4dgs_flow_loss for a W x H image (0 on bad sizes). */
+size_t d4dgs_flow_loss_scratch_bytes(int32_t width, int32_t height);
+/* The flow-gradient consistency loss (Eq. 17-18) of an image I (H x W x 3)
+ * and a flow F (H x W x 2), all float32 device:
+ *   M = sqrt(u^2 + v^2 + eps),
+ *   L = lambda / (W H) * sum |grad M| * (1 - |grad I| / max |grad I|),
+ * with 3x3 Sobel gradients on replicated borders, |grad M| divided by the
+ * kernel weight 8, |grad I| over the three channels and its guide held fixed
+ * (1 where the image is flat).  Writes L to *loss (one float, device) and,
+ * when dl_dflow is not null, dL/dF (H x W x 2) there.  scratch: device,
+ * 256-byte aligned, >= d4dgs_flow_loss_scratch_bytes. */
+int d4dgs_flow_loss(const float *rgb, const float *flow, int32_t width, int32_t height, float lambda, float eps,
+                    void *scratch, size_t scratch_bytes, float *loss, float *dl_dflow, d4dgs_stream_t stream);
+
 /* ---- slicing-first baseline (comparison, Eq. 5-7) --------------------------
  * The 4D Gaussian form the paper compares against: a 4D mean, 4D scales and
  * a 4D rotation, sliced at every frame into a 3D Gaussian before projection.

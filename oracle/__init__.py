@@ -405,7 +405,10 @@ def render_flow(scene, cam, t: float, pixels=None, eps_px=None) -> dict:
     gf = dict(g)
     gf["rgb"] = np.column_stack([f, np.zeros(len(f))])
     out = render_g2d(gf, cam, pixels=pixels, bg=(0.0, 0.0, 0.0), eps_px=eps_px)
-    return dict(flow=out["rgb"][..., :2], slack=out["slack"], T=out["T"])
+    # the slack bound takes non-negative values: evaluate it on |flow|
+    gf["rgb"] = np.abs(gf["rgb"])
+    mag = render_g2d(gf, cam, pixels=pixels, bg=(0.0, 0.0, 0.0), eps_px=eps_px)
+    return dict(flow=out["rgb"][..., :2], slack=mag["slack"], T=out["T"])
 
 
 def _sobel(img: np.ndarray):

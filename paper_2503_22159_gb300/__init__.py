@@ -27,6 +27,7 @@ SCENE_FIELDS = ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "qua
 __all__ = ["DeviceScene", "Renderer", "BatchRenderer", "camera_struct", "config_struct", "d4dgs_workspace_bytes",
            "d4dgs_workspace_layout", "d4dgs_preprocess", "d4dgs_sort", "d4dgs_blend", "d4dgs_blend_profile",
            "DeviceScene4D", "d4dgs_preprocess_slicing", "d4dgs_render_slicing",
+           "d4dgs_render_flow", "d4dgs_render_backward_flow", "d4dgs_flow_loss",
            "d4dgs_render",
            "d4dgs_render_backward", "d4dgs_read_stats", "d4dgs_render_host", "d4dgs_launches_per_frame",
            "D4DGSError", "D4DGS_OK", "D4DGS_ERR_CAPACITY", "D4DGS_ERR_TIMEOUT", "D4DGS_ERR_INVALID_ARG",
@@ -184,6 +185,42 @@ def d4dgs_render_backward(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tens
                                                  float(t), ctypes.byref(cfg), p, nb,
                                                  ctypes.c_void_p(dl_drgb.data_ptr()), ctypes.byref(g),
                                                  _stream_handle(stream)), "d4dgs_render_backward")
+
+
+def d4dgs_render_flow(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tensor, out: torch.Tensor,
+                      out_flow: torch.Tensor, stream=None):
+    """Render the image and the optical-flow channel (H x W x 2, pixels per unit time)."""
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_render_flow(ctypes.byref(scene.struct()), ctypes.byref(camera_struct(cam)), float(t),
+                                             ctypes.byref(cfg), p, nb, ctypes.c_void_p(out.data_ptr()),
+                                             ctypes.c_void_p(out_flow.data_ptr()), _stream_handle(stream)),
+               "d4dgs_render_flow")
+
+
+def d4dgs_render_backward_flow(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tensor, dl_drgb: torch.Tensor,
+                               dl_dflow: torch.Tensor, grads: dict, stream=None):
+    p, nb = _ws(ws)
+    g = _abi.d4dgs_scene_grad(*[grads[k].data_ptr() for k in SCENE_FIELDS])
+    _abi.check(_abi.load().d4dgs_render_backward_flow(ctypes.byref(scene.struct()), ctypes.byref(camera_struct(cam)),
+                                                      float(t), ctypes.byref(cfg), p, nb,
+                                                      ctypes.c_void_p(dl_drgb.data_ptr()),
+                                                      ctypes.c_void_p(dl_dflow.data_ptr()), ctypes.byref(g),
+                                                      _stream_handle(stream)), "d4dgs_render_backward_flow")
+
+
+def d4dgs_flow_loss(rgb: torch.Tensor, flow: torch.Tensor, lam: float = 1.0, eps: float = 1e-6,
+                    dl_dflow: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Flow-gradient consistency loss (a 1-element device tensor); fills dl_dflow when given."""
+    H, W = int(rgb.shape[0]), int(rgb.shape[1])
+    lib = _abi.load()
+    scratch = torch.empty(int(lib.d4dgs_flow_loss_scratch_bytes(W, H)), dtype=torch.uint8, device=rgb.device)
+    loss = torch.empty(1, dtype=torch.float32, device=rgb.device)
+    _abi.check(lib.d4dgs_flow_loss(ctypes.c_void_p(rgb.data_ptr()), ctypes.c_void_p(flow.data_ptr()), W, H,
+                                   float(lam), float(eps), ctypes.c_void_p(scratch.data_ptr()), scratch.numel(),
+                                   ctypes.c_void_p(loss.data_ptr()),
+                                   ctypes.c_void_p(dl_dflow.data_ptr()) if dl_dflow is not None else None,
+                                   _stream_handle(stream)), "d4dgs_flow_loss")
+    return loss
 
 
 def d4dgs_read_stats(n: int, cam, cfg, ws: torch.Tensor, stream=None) -> dict:

@@ -95,6 +95,13 @@ PROTOTYPES = {
     "d4dgs_batch_area_bytes": (ctypes.c_size_t, []),
     "d4dgs_batch_encode": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_view), _P(d4dgs_config), _vp, ctypes.c_size_t]),
     "d4dgs_render_batch": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "d4dgs_render_flow": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config), _vp,
+                                         ctypes.c_size_t, _vp, _vp, _vp]),
+    "d4dgs_render_backward_flow": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),
+                                                  _vp, ctypes.c_size_t, _vp, _vp, _P(d4dgs_scene_grad), _vp]),
+    "d4dgs_flow_loss_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "d4dgs_flow_loss": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _vp,
+                                       ctypes.c_size_t, _vp, _vp, _vp]),
     "d4dgs_preprocess_slicing": (ctypes.c_int, [_P(d4dgs_scene4d), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),
                                                 _vp, ctypes.c_size_t, _vp]),
     "d4dgs_render_slicing": (ctypes.c_int, [_P(d4dgs_scene4d), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),

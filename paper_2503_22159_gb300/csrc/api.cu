@@ -130,6 +130,7 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.final_T = off; off += align256(l.pixels * 4);
     l.n_contrib = off; off += align256(l.pixels * 4);
     l.grad2d = off; off += align256((int64_t)n * 48);
+    l.flow2d = off; off += align256((int64_t)n * 8);
     for (int b = 0; b < 2; b++) { l.tile_keys[b] = off; off += align256(cap * 4); }
     if (!l.packed)
         for (int b = 0; b < 2; b++) { l.tile_vals[b] = off; off += align256(cap * 4); }
@@ -180,6 +181,7 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     x.final_T = at<float>(ws, L.final_T);
     x.n_contrib = at<uint32_t>(ws, L.n_contrib);
     x.grad2d = at<float>(ws, L.grad2d);
+    x.flow2d = at<float2>(ws, L.flow2d);
     x.lb_depth = at<uint32_t>(ws, L.lb_depth);
     x.lb_tile = at<uint32_t>(ws, L.lb_tile);
     x.lb_col = at<uint32_t>(ws, L.lb_col);
@@ -444,8 +446,47 @@ int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, flo
     static thread_local BatchArgs b;
     Layout L;
     if ((rc = single(scene, scene->n, cam, t, cfg, ws, ws_bytes, nullptr, &b, &L))) return rc;
-    return cuda_status(launch_backward(b, at<char>(ws, L.batch), dl_drgb, *grad, reinterpret_cast<cudaStream_t>(stream),
-                                       num_sms_current()));
+    return cuda_status(launch_backward(b, at<char>(ws, L.batch), dl_drgb, nullptr, *grad,
+                                       reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
+}
+
+int d4dgs_render_flow(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg, void *ws,
+                      size_t ws_bytes, float *out_rgb, float *out_flow, d4dgs_stream_t stream) {
+    if (!out_rgb || !aligned(out_rgb, 4) || !out_flow || !aligned(out_flow, 4)) return D4DGS_ERR_INVALID_ARG;
+    int rc = check_scene(scene);
+    if (rc) return rc;
+    if (!isfinite(t)) return D4DGS_ERR_INVALID_ARG;
+    static thread_local BatchArgs b;
+    Layout L;
+    if ((rc = single(scene, scene->n, cam, t, cfg, ws, ws_bytes, out_rgb, &b, &L))) return rc;
+    b.v[0].out_flow = out_flow;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ba = at<char>(ws, L.batch);
+    const int sms = num_sms_current();
+    cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
+    return cuda_status(e);
+}
+
+int d4dgs_render_backward_flow(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                               void *ws, size_t ws_bytes, const float *dl_drgb, const float *dl_dflow,
+                               d4dgs_scene_grad *grad, d4dgs_stream_t stream) {
+    int rc = check_scene(scene);
+    if (rc) return rc;
+    if (!isfinite(t) || !dl_drgb || !dl_dflow || !grad) return D4DGS_ERR_INVALID_ARG;
+    if (scene->n > 0) {
+        float *gp[] = {grad->means, grad->t_mean, grad->velocity, grad->log_scales, grad->log_t_scale, grad->quats,
+                       grad->opacity_logit, grad->sh};
+        for (float *p : gp)
+            if (!p || !aligned(p, 4)) return D4DGS_ERR_INVALID_ARG;
+    }
+    static thread_local BatchArgs b;
+    Layout L;
+    if ((rc = single(scene, scene->n, cam, t, cfg, ws, ws_bytes, nullptr, &b, &L))) return rc;
+    return cuda_status(launch_backward(b, at<char>(ws, L.batch), dl_drgb, dl_dflow, *grad,
+                                       reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
 }
 
 size_t d4dgs_batch_args_bytes(void) { return sizeof(BatchArgs); }

@@ -68,9 +68,12 @@ __device__ __forceinline__ float warp_sum8(const float (&x)[8], int lane) {
 // pass and alpha has the same bits.  A thread sums its pixels' gradients;
 // a warp reduces them once per Gaussian and adds them into shared memory;
 // each batch is flushed to the global 2D-gradient sums once per Gaussian.
-template <int TS, int BATCH>
+// FLOW: the forward also composited the screen flow; dl_dflow (H x W x 2)
+// adds its terms to dL/dalpha and gives dL/d(flow) of every Gaussian.
+template <int TS, int BATCH, bool FLOW = false>
 __global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 16 : (TS == 16 ? 8 : 3))
-blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_drgb) {
+blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_drgb,
+                      const float *__restrict__ dl_dflow) {
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
     const View &v = view_of(ba, 0);
@@ -87,7 +90,8 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
     __shared__ float4 s_k[BATCH];     // a, b, c, o_hat (natural conic)
     __shared__ uint32_t s_m[BATCH];   // blocks the alpha >= 1/255 ellipse reaches
     __shared__ uint32_t s_id[BATCH];
-    __shared__ float s_acc[BATCH][9];
+    __shared__ float2 s_f[FLOW ? BATCH : 1];   // screen flow
+    __shared__ float s_acc[BATCH][FLOW ? 11 : 9];
     __shared__ uint32_t s_maxw;
 
     const int tile = blockIdx.x;
@@ -104,7 +108,7 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
     const uint32_t len = rg.y - rg.x;
 
     float2 pyf[NP];
-    float T[PX], G[PX][3], Bc[PX][3];
+    float T[PX], G[PX][3], Bc[PX][3], GF[FLOW ? PX : 1][2], BF[FLOW ? PX : 1][2];
     uint32_t walked[PX];
     uint32_t tmax = 0;
 #pragma unroll
@@ -118,12 +122,17 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
             G[i][c] = 0.0f;
             Bc[i][c] = v.bg[c];
         }
+        if (FLOW) GF[FLOW ? i : 0][0] = GF[FLOW ? i : 0][1] = BF[FLOW ? i : 0][0] = BF[FLOW ? i : 0][1] = 0.0f;
         if (px < width && py + i < height) {
             const size_t p = (size_t)(py + i) * width + px;
             T[i] = v.final_T[p];
             walked[i] = min(v.n_contrib[p], len);
 #pragma unroll
             for (int c = 0; c < 3; c++) G[i][c] = dl_drgb[3 * p + c];
+            if (FLOW) {
+                GF[FLOW ? i : 0][0] = dl_dflow[2 * p];
+                GF[FLOW ? i : 0][1] = dl_dflow[2 * p + 1];
+            }
         }
         tmax = max(tmax, walked[i]);
     }
@@ -153,8 +162,9 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
             s_k[k] = make_float4(r0.z, r0.w, r1.x, r1.y);
             s_m[k] = d4dgs::block_mask<TS, BH>(r0.x, r0.y, A, B, C, r2.w, x0, y0);
             s_id[k] = id;
+            if (FLOW) s_f[FLOW ? k : 0] = v.flow2d[id];
 #pragma unroll
-            for (int j = 0; j < 9; j++) s_acc[k][j] = 0.0f;
+            for (int j = 0; j < (FLOW ? 11 : 9); j++) s_acc[k][j] = 0.0f;
         }
         __syncthreads();
         if ((uint32_t)lo < wmax) {
@@ -190,9 +200,11 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                         any |= e[i];
                     }
                     float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
+                    float gfu = 0.f, gfv = 0.f;
                     if (any) {
                         const float4 c = s_c[k];
                         const float4 kk = s_k[k];
+                        const float2 fl = FLOW ? s_f[FLOW ? k : 0] : make_float2(0.0f, 0.0f);
                         const float dx = dx2.x;
 #pragma unroll
                         for (int i = 0; i < PX; i++) {
@@ -204,11 +216,19 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                             gr += w * G[i][0];
                             gg += w * G[i][1];
                             gbl += w * G[i][2];
-                            const float dalpha =
+                            float dalpha =
                                 Ti * (G[i][0] * (c.x - Bc[i][0]) + G[i][1] * (c.y - Bc[i][1]) + G[i][2] * (c.z - Bc[i][2]));
                             Bc[i][0] = alpha * c.x + (1.0f - alpha) * Bc[i][0];
                             Bc[i][1] = alpha * c.y + (1.0f - alpha) * Bc[i][1];
                             Bc[i][2] = alpha * c.z + (1.0f - alpha) * Bc[i][2];
+                            if (FLOW) {
+                                const int fi = FLOW ? i : 0;
+                                gfu += w * GF[fi][0];
+                                gfv += w * GF[fi][1];
+                                dalpha += Ti * (GF[fi][0] * (fl.x - BF[fi][0]) + GF[fi][1] * (fl.y - BF[fi][1]));
+                                BF[fi][0] = alpha * fl.x + (1.0f - alpha) * BF[fi][0];
+                                BF[fi][1] = alpha * fl.y + (1.0f - alpha) * BF[fi][1];
+                            }
                             T[i] = Ti;
                             if (raw <= kAlphaMax) {
                                 const float dp = dalpha * alpha, ddy = dy[i];
@@ -230,6 +250,13 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                             atomicAdd(&s_acc[k][idx < 5 ? idx : idx + 1], tot);
                         }
                         if (lane == 0) atomicAdd(&s_acc[k][5], tgo);
+                        if (FLOW) {
+                            const float tfu = warp_sum(gfu), tfv = warp_sum(gfv);
+                            if (lane == 0) {
+                                atomicAdd(&s_acc[k][FLOW ? 9 : 0], tfu);
+                                atomicAdd(&s_acc[k][FLOW ? 10 : 0], tfv);
+                            }
+                        }
                     }
                 }
             }
@@ -237,13 +264,14 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
         __syncthreads();
         // flush: one set of global atomics per (tile, Gaussian) that received anything
         for (int k = threadIdx.x; k < nb; k += NT) {
+            constexpr int NA = FLOW ? 11 : 9;
             bool anyg = false;
 #pragma unroll
-            for (int j = 0; j < 9; j++) anyg |= s_acc[k][j] != 0.0f;
+            for (int j = 0; j < NA; j++) anyg |= s_acc[k][j] != 0.0f;
             if (anyg) {
                 float *dst = g2 + (size_t)s_id[k] * kG2;
 #pragma unroll
-                for (int j = 0; j < 9; j++)
+                for (int j = 0; j < NA; j++)
                     if (s_acc[k][j] != 0.0f) atomicAdd(dst + j, s_acc[k][j]);
             }
         }
@@ -334,6 +362,7 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
     const float *G = g2 + (size_t)i * kG2;
     const float gU = G[0], gV = G[1], gA = G[2], gB = G[3], gCc = G[4], gO = G[5];
     const float gcol[3] = {G[6], G[7], G[8]};
+    const float gFu = G[9], gFv = G[10];   // screen flow (zero unless the frame had a flow channel)
     // ---- forward quantities (the decisions use the forward's rounded operations)
     const float tau = __fsub_rn(t, s.t_mean[i]);
     const float vel[3] = {s.velocity[3 * i], s.velocity[3 * i + 1], s.velocity[3 * i + 2]};
@@ -419,6 +448,10 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
     dX[2] += -gU * c.fx * Xc[0] * iz2;
     dX[1] += gV * c.fy * iz;
     dX[2] += -gV * c.fy * Xc[1] * iz2;
+    // ---- screen flow f = (fx Vc_x / Z, fy Vc_y / Z), Vc = R V: depth and camera-frame velocity
+    const float Vcx = R[0] * vel[0] + R[1] * vel[1] + R[2] * vel[2], Vcy = R[3] * vel[0] + R[4] * vel[1] + R[5] * vel[2];
+    dX[2] += -(gFu * c.fx * Vcx + gFv * c.fy * Vcy) * iz2;
+    const float dVc0 = gFu * c.fx * iz, dVc1 = gFv * c.fy * iz;
     // ---- M = R(qn) diag(s) -> quaternion, log-scales
     float dR[9];
 #pragma unroll
@@ -468,7 +501,7 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         o.means[3 * i + j] = dm[j];
-        o.velocity[3 * i + j] = tau * dm[j];
+        o.velocity[3 * i + j] = tau * dm[j] + R[j] * dVc0 + R[3 + j] * dVc1;
         dtau += vel[j] * dm[j];
     }
     const float oh = rec[3 * (size_t)i + 1].y;
@@ -481,13 +514,14 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
 }
 
 template <int TS, int BATCH>
-void launch_bb(const char *ba, int ntiles, const float *dl, cudaStream_t st) {
-    blend_backward_kernel<TS, BATCH><<<ntiles, BlendShape<TS>::NT, 0, st>>>(ba, dl);
+void launch_bb(const char *ba, int ntiles, const float *dl, const float *dlf, cudaStream_t st) {
+    if (dlf) blend_backward_kernel<TS, BATCH, true><<<ntiles, BlendShape<TS>::NT, 0, st>>>(ba, dl, dlf);
+    else blend_backward_kernel<TS, BATCH, false><<<ntiles, BlendShape<TS>::NT, 0, st>>>(ba, dl, nullptr);
 }
 
 }  // namespace
 
-cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb,
+cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb, const float *dl_dflow,
                             const d4dgs_scene_grad &g, cudaStream_t st, int num_sms) {
     (void)num_sms;
     const View &v = args.v[0];
@@ -495,9 +529,9 @@ cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float
     cudaError_t e = cudaMemsetAsync(v.grad2d, 0, (size_t)v.n * kG2 * sizeof(float), st);
     if (e != cudaSuccess) return e;
     switch (args.tile) {   // the staging depth of the backward follows the tile size
-        case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, st); break;
-        case 16: launch_bb<16, 128>(batch_area, v.ntiles, dl_drgb, st); break;
-        default: launch_bb<32, 128>(batch_area, v.ntiles, dl_drgb, st); break;
+        case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
+        case 16: launch_bb<16, 128>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
+        default: launch_bb<32, 128>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
     }
     GradArgs o{g.means, g.t_mean, g.velocity, g.log_scales, g.log_t_scale, g.quats, g.opacity_logit, g.sh};
     const int blocks = (v.n + 255) / 256;

@@ -44,13 +44,16 @@ namespace {
 // last pixel stopped, or the whole list).
 // PERSIST: CTAs take tiles from an atomic counter until all are done (fixed
 // grid, for batched and graph-captured launches); otherwise one CTA per tile.
-template <int TS, int BATCH, bool COUNT, bool PERSIST>
+// FLOW: also composites the per-Gaussian screen flow into the view's flow
+// output (two channels, background 0) with the same weights.
+template <int TS, int BATCH, bool COUNT, bool PERSIST, bool FLOW = false>
 __global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 24 : (TS == 16 ? 10 : 3))
 blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts) {
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
     // one 128-byte record per staged Gaussian (one address for all of its loads):
     // [0] u, u, A, A  [1] B, B, C, C  [2] v, v, L, L  [3] r, r, g, g  [4] b, b
+    // [5] flow u, u, v, v (FLOW)
     __shared__ float4 s_rec[BATCH][8];
     __shared__ uint32_t s_m[BATCH];  // blocks the Gaussian's alpha >= 1/255 ellipse reaches
     __shared__ int32_t s_item;
@@ -94,7 +97,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
         const int py = y0 + BH * (warp / BX) + PX * (lane >> 3);
         const float pxf = (float)px + 0.5f;
         const float2 pxf2 = make_float2(pxf, pxf);
-        float2 pyf[NP], T[NP], c0[NP], c1[NP], c2[NP];
+        float2 pyf[NP], T[NP], c0[NP], c1[NP], c2[NP], fa[NP], fb[NP];
         // walked[i]: list entries the pixel walks before the one at which it stops (the
         // whole list if it never stops); the backward replays those entries
         uint32_t walked[PX], stop[PX];
@@ -107,6 +110,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
             pyf[j] = make_float2((float)(py + 2 * j) + 0.5f, (float)(py + 2 * j + 1) + 0.5f);
             T[j] = one2;
             c0[j] = c1[j] = c2[j] = make_float2(0.0f, 0.0f);
+            fa[j] = fb[j] = make_float2(0.0f, 0.0f);
         }
 #pragma unroll
         for (int i = 0; i < PX; i++) {
@@ -134,6 +138,10 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                     s_rec[k][2] = make_float4(r0.y, r0.y, r2.w, r2.w);
                     s_rec[k][3] = make_float4(r2.x, r2.x, r2.y, r2.y);
                     s_rec[k][4] = make_float4(r2.z, r2.z, 0.0f, 0.0f);
+                    if (FLOW) {
+                        const float2 fl = v.flow2d[id];
+                        s_rec[k][5] = make_float4(fl.x, fl.x, fl.y, fl.y);
+                    }
                     const float det4 = fmaf(4.0f * A, C, -(B * B)), tr = -(A + C);
                     const bool fast = r2.w <= kLog2FastOpacity && det4 > kFastConditioning * tr * tr;
                     s_m[k] = d4dgs::block_mask<TS, BH>(r0.x, r0.y, A, B, C, r2.w, x0, y0) | (fast ? 0u : kSlowBit);
@@ -192,6 +200,11 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                         c0[j] = f2_fma(w, make_float2(rgc.x, rgc.y), c0[j]);
                         c1[j] = f2_fma(w, make_float2(rgc.z, rgc.w), c1[j]);
                         c2[j] = f2_fma(w, bl, c2[j]);
+                        if (FLOW) {
+                            const float4 fr = s_rec[k][5];
+                            fa[j] = f2_fma(w, make_float2(fr.x, fr.y), fa[j]);
+                            fb[j] = f2_fma(w, make_float2(fr.z, fr.w), fb[j]);
+                        }
                     }
                     if (COUNT) {
 #pragma unroll
@@ -281,6 +294,10 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
                 out_rgb[3 * p + 2] = (hi ? c2[j].y : c2[j].x) + Ti * bg2;
                 v.final_T[p] = Ti;
                 v.n_contrib[p] = walked[i];
+                if (FLOW) {
+                    v.out_flow[2 * p + 0] = hi ? fa[j].y : fa[j].x;
+                    v.out_flow[2 * p + 1] = hi ? fb[j].y : fb[j].x;
+                }
             }
         }
     }
@@ -297,7 +314,10 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
 
 template <int TS, int BATCH>
 cudaError_t launch_ts(char *ba, int total_tiles, bool persist, cudaStream_t st, int num_sms, float *out0,
-                      unsigned long long *counts) {
+                      unsigned long long *counts, bool flow) {
+    if (flow)   // single frames only
+        return launch_chained(blend_kernel<TS, BATCH, false, false, true>, total_tiles, BlendShape<TS>::NT, 0, st, ba,
+                              out0, counts);
     auto go = [&](auto kernel) {
         static int occ = 0;   // per instantiation; queried once, before any graph capture uses it
         if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BlendShape<TS>::NT, 0) != cudaSuccess ||
@@ -323,10 +343,11 @@ cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t s
                          unsigned long long *counts, bool persist) {
     if (args.total_tiles == 0) return cudaSuccess;
     const int nt = args.total_tiles;
-#define D4DGS_BATCHES(TS)                                                                              \
-    if (args.batch == 64) return launch_ts<TS, 64>(batch_area, nt, persist, st, num_sms, out0, counts);   \
-    if (args.batch == 128) return launch_ts<TS, 128>(batch_area, nt, persist, st, num_sms, out0, counts); \
-    if (args.batch == 256) return launch_ts<TS, 256>(batch_area, nt, persist, st, num_sms, out0, counts); \
+    const bool flow = args.nviews == 1 && args.v[0].out_flow != nullptr && !counts && !persist;
+#define D4DGS_BATCHES(TS)                                                                                    \
+    if (args.batch == 64) return launch_ts<TS, 64>(batch_area, nt, persist, st, num_sms, out0, counts, flow);   \
+    if (args.batch == 128) return launch_ts<TS, 128>(batch_area, nt, persist, st, num_sms, out0, counts, flow); \
+    if (args.batch == 256) return launch_ts<TS, 256>(batch_area, nt, persist, st, num_sms, out0, counts, flow); \
     return cudaErrorInvalidValue;
     switch (args.tile) {
         case 8: D4DGS_BATCHES(8)

@@ -66,7 +66,7 @@ struct Layout {
     int64_t control = 0, grid = 0, lb_depth = 0, lb_col = 0, lb_tile = 0, zero_end = 0;
     // the rest
     int64_t colbase = 0, ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
-    int64_t final_T = 0, n_contrib = 0, grad2d = 0, batch = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
+    int64_t final_T = 0, n_contrib = 0, grad2d = 0, flow2d = 0, batch = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
     int64_t total = 0;
     int32_t grid_w() const { return tiles_x + 1; }
     // index of the final sorted pair buffer
@@ -118,6 +118,8 @@ struct View {
     float *final_T;
     uint32_t *n_contrib;
     float *grad2d;
+    float2 *flow2d;                  // per-Gaussian screen flow (pixels per unit time), flow frames only
+    float *out_flow;                 // H x W x 2 blended flow output, or null (no flow channel)
     uint32_t *tkeys[2], *tvals[2];
     uint32_t *lb_depth, *lb_tile, *lb_col;
     uint32_t *colbase;               // first position of each tile column's bucket (clamped to cap)
@@ -175,7 +177,7 @@ cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cud
 cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms);
 cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, float *out0,
                          unsigned long long *counts = nullptr, bool persist = false);
-cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb,
+cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb, const float *dl_dflow,
                             const d4dgs_scene_grad &g, cudaStream_t st, int num_sms);
 int sort_launch_count(int n, int tile_passes);
 

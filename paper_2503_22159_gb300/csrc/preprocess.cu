@@ -75,7 +75,17 @@ struct Footprint {
     float m0, m1, m2;     // world-space mean at t (SH view direction)
     float Z, u, v, oh;    // camera depth, pixel mean, opacity at t
     float s00, s01, s11;  // Sigma' (with the 0.3 px^2 dilation)
+    float fu, fv;         // screen flow (flow frames only)
 };
+
+// Screen flow of a Gaussian (Eq. 13 in pixels): the ray-space velocity of the
+// mean, (fx V_x / Z, fy V_y / Z), V the camera-frame velocity.
+__device__ __forceinline__ void screen_flow(const CamArgs &c, float v0, float v1, float v2, float Z, Footprint &f) {
+    const float *R = c.R;
+    const float Vx = R[0] * v0 + R[1] * v1 + R[2] * v2, Vy = R[3] * v0 + R[4] * v1 + R[5] * v2;
+    f.fu = c.fx * Vx / Z;
+    f.fv = c.fy * Vy / Z;
+}
 
 // Disentangled form (Algorithm 1): the deferred temporal slice of the mean
 // and opacity, then the projection of the static 3D covariance R S S^T R^T.
@@ -147,6 +157,8 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
         f.m0 = m0; f.m1 = m1; f.m2 = m2;
         f.Z = Z; f.u = u; f.v = v; f.oh = oh;
         f.s00 = s00; f.s01 = s01; f.s11 = s11;
+        if (vw.out_flow)
+            screen_flow(c, __ldg(vw.velocity + 3 * i), __ldg(vw.velocity + 3 * i + 1), __ldg(vw.velocity + 3 * i + 2), Z, f);
         return true;
     } while (0);
     return false;
@@ -229,6 +241,7 @@ __device__ __forceinline__ bool footprint_slicing(const View &vw, int i, Footpri
     f.s00 = add(add(add(mul(TS[0], Tm[0]), mul(TS[1], Tm[1])), mul(TS[2], Tm[2])), kDilation);
     f.s01 = add(add(mul(TS[0], Tm[3]), mul(TS[1], Tm[4])), mul(TS[2], Tm[5]));
     f.s11 = add(add(add(mul(TS[3], Tm[3]), mul(TS[4], Tm[4])), mul(TS[5], Tm[5])), kDilation);
+    if (vw.out_flow) screen_flow(c, v0, v1, v2, Z, f);
     return true;
 }
 
@@ -244,11 +257,16 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
         uint32_t key = 0xFFFFFFFFu, tiles = 0;
         ushort4 rc = make_ushort4(0, 0, 0, 0);
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+        float flu = 0.0f, flv = 0.0f;
         do {
             Footprint f;
             if (!(KIND == 0 ? footprint_disentangled(vw, i, f) : footprint_slicing(vw, i, f))) break;
             const float m0 = f.m0, m1 = f.m1, m2 = f.m2, Z = f.Z, u = f.u, v = f.v, oh = f.oh;
             const float s00 = f.s00, s01 = f.s01, s11 = f.s11;
+            if (vw.out_flow) {
+                flu = f.fu;
+                flv = f.fv;
+            }
             const float det = sub(mul(s00, s11), mul(s01, s01));
             if (!(det > 0.0f)) break;
             const float mid = mul(0.5f, add(s00, s11));
@@ -317,6 +335,7 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
         vw.rec[3 * (size_t)i + 0] = r0;
         vw.rec[3 * (size_t)i + 1] = r1;
         vw.rec[3 * (size_t)i + 2] = r2;
+        if (vw.out_flow) vw.flow2d[i] = key == 0xFFFFFFFFu ? make_float2(0.0f, 0.0f) : make_float2(flu, flv);
         vw.dkeys[0][i] = key;
         vw.tiles_touched[i] = tiles;
         vw.rect[i] = rc;
