@@ -440,8 +440,42 @@ def run_backward(args, dev, d4, w, scene, cfg, cap):
         raise RuntimeError("non-finite gradients")
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     sh_bytes = 4 * 3 * (w.scene.sh_degree + 1) ** 2
+
+    # the optical-flow channel (Eq. 13) and the flow-gradient loss (Eq. 17-18): forward with flow,
+    # loss with dL/dF, backward through both channels; device time per frame of each
+    flow = torch.empty((cam0.height, cam0.width, 2), device=dev)
+    dlf = torch.empty_like(flow)
+    zero_rgb = torch.zeros_like(out)
+    tev = {"render": [], "render_flow": [], "loss": [], "backward_flow": []}
+    for rep in range(2):
+        for k, (cam, t) in enumerate(frames):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            torch.cuda._sleep(1_000_000)
+            flush.fill_(k & 255)
+            e[0].record(stream)
+            d4.d4dgs_render(scene, cam, t, cfg, ws, out, stream)
+            e[1].record(stream)
+            torch.cuda._sleep(1_000_000)
+            flush.fill_(k & 255)
+            e[2].record(stream)
+            d4.d4dgs_render_flow(scene, cam, t, cfg, ws, out, flow, stream)
+            e[3].record(stream)
+            d4.d4dgs_flow_loss(out, flow, 1.0, 1e-6, dlf, stream)
+            e[4].record(stream)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            d4.d4dgs_render_backward_flow(scene, cam, t, cfg, ws, zero_rgb, dlf, grads, stream)
+            f1.record(stream)
+            if rep:
+                tev["render"].append((e[0], e[1]))
+                tev["render_flow"].append((e[2], e[3]))
+                tev["loss"].append((e[3], e[4]))
+                tev["backward_flow"].append((f0, f1))
+    torch.cuda.synchronize(dev)
+    flow_ms = {k: float(np.mean([a.elapsed_time(b) for a, b in v])) for k, v in tev.items()}
     return {"ms_per_frame": ms, "frames": len(frames), "frames_per_s": 1e3 / ms,
-            "k8_bytes_per_frame": scene.n * (64 + sh_bytes + 48 + 64 + sh_bytes)}
+            "k8_bytes_per_frame": scene.n * (64 + sh_bytes + 48 + 64 + sh_bytes),
+            "flow_ms_per_frame": flow_ms}
 
 
 def run_ours(args):
