@@ -297,6 +297,10 @@ def run_time_groups(args, dev, d4, w, scene, cfg, cap, peaks):
     k0 = len(w.frames) // 2
     cam = w.frames[k0][0]
     times = [w.frames[k0 + j][1] for j in range(B)]
+    rr = d4.Renderer(scene.n, cam, tile=cfg.tile, batch=cfg.batch, key_capacity=cap, device=dev)
+    for t in times:         # grows the key capacity to these frames
+        rr.render(scene, cam, t)
+    cap = rr.key_capacity
     views = []
     for t in times:
         ws = torch.empty(d4.d4dgs_workspace_bytes(scene.n, cam, cfg, cap), dtype=torch.uint8, device=dev)
@@ -415,7 +419,10 @@ def run_backward(args, dev, d4, w, scene, cfg, cap):
     stream = torch.cuda.current_stream(dev)
     frames = [w.frames[k] for k in range(0, len(w.frames), 15)]
     cam0 = frames[0][0]
-    ws = torch.empty(d4.d4dgs_workspace_bytes(scene.n, cam0, cfg, cap), dtype=torch.uint8, device=dev)
+    rr = d4.Renderer(scene.n, cam0, tile=cfg.tile, batch=cfg.batch, key_capacity=cap, device=dev)
+    for cam, t in frames:   # grows the key capacity to these frames
+        rr.render(scene, cam, t)
+    ws = rr.ws
     out = torch.empty((cam0.height, cam0.width, 3), device=dev)
     g = torch.Generator(device="cpu").manual_seed(5)
     dl = torch.randn((cam0.height, cam0.width, 3), generator=g).to(dev)
