@@ -220,6 +220,34 @@ size_t d4dgs_flow_loss_scratch_bytes(int32_t width, int32_t height);
 int d4dgs_flow_loss(const float *rgb, const float *flow, int32_t width, int32_t height, float lambda, float eps,
                     void *scratch, size_t scratch_bytes, float *loss, float *dl_dflow, d4dgs_stream_t stream);
 
+/* ---- temporal and spatial splitting (Sec. III-C) ----------------------------
+ * Training-side densification: time-domain splitting guided by the gradient
+ * of t, spatial splitting by the gradients of xyz, the two scales split
+ * independently.  d4dgs_split_accumulate adds |dL/d mean| (3-vector norm),
+ * |dL/d t_mean| and 1 to stats (N x 3 float32 device, caller-owned, zeroed by
+ * the caller before the first step) for every Gaussian with a nonzero mean or
+ * t_mean gradient.  d4dgs_split decides, from the float32 averages
+ * g = sum / max(count, 1): in space when g_xyz > tau_xyz and the largest
+ * log-scale > log_min_xyz; in time when g_t > tau_t and log s_t > log_min_t.
+ * A split Gaussian becomes two: child 1 keeps its index, child 2 is appended
+ * after the first N in index order; means mu +- R(q) diag(s) n_xyz and spatial
+ * log-scales - log(factor) for a spatial split, t_mean +- s_t n_t and
+ * log s_t - log(factor) for a temporal one, the other fields copied.
+ * normals: N x 4 standard normal samples (three spatial, one temporal),
+ * device.  out: arrays of capacity >= 2N Gaussians (device, caller-owned);
+ * *out_n (device int32) receives the new count.  scratch: device,
+ * >= d4dgs_split_scratch_bytes(N). */
+typedef struct {
+    float tau_xyz, tau_t;            /* thresholds on the average gradient norms */
+    float log_min_xyz, log_min_t;    /* thresholds on the log-scales              */
+    float factor;                    /* scale divisor of a split (> 1, e.g. 1.6)  */
+} d4dgs_split_params;
+int d4dgs_split_accumulate(const d4dgs_scene_grad *grad, int32_t n, float *stats, d4dgs_stream_t stream);
+size_t d4dgs_split_scratch_bytes(int32_t n);
+int d4dgs_split(const d4dgs_scene *scene, const float *stats, const float *normals, const d4dgs_split_params *params,
+                const d4dgs_scene_grad *out, int32_t capacity, int32_t *out_n, void *scratch, size_t scratch_bytes,
+                d4dgs_stream_t stream);
+
 /* ---- slicing-first baseline (comparison, Eq. 5-7) --------------------------
  * The 4D Gaussian form the paper compares against: a 4D mean, 4D scales and
  * a 4D rotation, sliced at every frame into a 3D Gaussian before projection.

@@ -23,6 +23,7 @@ Parity status of each function (see the pin tests in ``tests/test_oracle_*``):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import sys
@@ -440,3 +441,54 @@ def flow_gradient_loss(flow: np.ndarray, weight: np.ndarray, lam: float = 1.0, e
     gx, gy = _sobel(M)
     nrm = np.sqrt(gx * gx + gy * gy) / 8.0
     return float(lam * np.mean(nrm * _d(weight)))
+
+
+# ---------------------------------------------------------------------------
+# Temporal / spatial splitting (Sec. III-C), plain numpy.  Readings: per
+# Gaussian the training loop accumulates |dL/d mean| (the 3-vector norm) and
+# |dL/d t_mean| over the steps that gave it a nonzero gradient; the averages
+# decide, in float32 (the same rounded operations as the device), whether it
+# splits in space (g_xyz > tau_xyz and max log-scale > log_min_xyz) and / or in
+# time (g_t > tau_t and log s_t > log_min_t).  A split Gaussian becomes two:
+# child 1 keeps its index, child 2 is appended after the kept ones in index
+# order; the children's means are mu +- R(q) diag(s) n_xyz (a draw of
+# N(mu, Sigma3D) and its mirror) and their spatial log-scales drop by
+# log(factor) when splitting in space; t_mean +- s_t n_t and log s_t -
+# log(factor) when splitting in time; everything else is copied.  n are
+# standard normal samples passed in (N x 4: three spatial, one temporal).
+
+def split_decisions(stats, log_scales, log_t_scale, tau_xyz, tau_t, log_min_xyz, log_min_t):
+    """(split_space, split_time) boolean arrays; stats (N, 3) = (sum |dL/dmu|, sum |dL/dmu_t|, count)."""
+    st = np.asarray(stats, np.float32).reshape(-1, 3)
+    cnt = np.maximum(st[:, 2], np.float32(1.0))
+    g_xyz = st[:, 0] / cnt
+    g_t = st[:, 1] / cnt
+    ls = np.asarray(log_scales, np.float32).reshape(-1, 3)
+    ss = (g_xyz > np.float32(tau_xyz)) & (ls.max(axis=1) > np.float32(log_min_xyz))
+    tt = (g_t > np.float32(tau_t)) & (np.asarray(log_t_scale, np.float32) > np.float32(log_min_t))
+    return ss, tt
+
+
+def split_scene(scene, stats, normals, tau_xyz, tau_t, log_min_xyz, log_min_t, factor=1.6):
+    """The scene after splitting (FP64 arrays), and the two decision masks."""
+    import synth
+    ss, tt = split_decisions(stats, scene.log_scales, scene.log_t_scale, tau_xyz, tau_t, log_min_xyz, log_min_t)
+    a = {k: _d(v).copy() for k, v in scene.arrays().items()}
+    n = scene.n
+    nrm = _d(normals).reshape(n, 4)
+    q = a["quats"].reshape(n, 4)
+    Rm = np.array([quat_to_rot(x / np.linalg.norm(x)) for x in q])
+    d = np.einsum("nij,nj->ni", Rm, np.exp(a["log_scales"].reshape(n, 3)) * nrm[:, :3]) * ss[:, None]
+    dt = np.exp(a["log_t_scale"]) * nrm[:, 3] * tt
+    lf = math.log(factor)
+    child1, child2 = dict(a), {k: v.copy() for k, v in a.items()}
+    child1["means"] = a["means"].reshape(n, 3) + d
+    child2["means"] = a["means"].reshape(n, 3) - d
+    child1["t_mean"] = a["t_mean"] + dt
+    child2["t_mean"] = a["t_mean"] - dt
+    for c in (child1, child2):
+        c["log_scales"] = a["log_scales"].reshape(n, 3) - lf * ss[:, None]
+        c["log_t_scale"] = a["log_t_scale"] - lf * tt
+    extra = ss | tt
+    out = {k: np.concatenate([child1[k], child2[k][extra]], axis=0) for k in a}
+    return synth.Scene(**out, sh_degree=scene.sh_degree), ss, tt

@@ -27,7 +27,8 @@ SCENE_FIELDS = ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "qua
 __all__ = ["DeviceScene", "Renderer", "BatchRenderer", "camera_struct", "config_struct", "d4dgs_workspace_bytes",
            "d4dgs_workspace_layout", "d4dgs_preprocess", "d4dgs_sort", "d4dgs_blend", "d4dgs_blend_profile",
            "DeviceScene4D", "d4dgs_preprocess_slicing", "d4dgs_render_slicing",
-           "d4dgs_render_flow", "d4dgs_render_backward_flow", "d4dgs_flow_loss",
+           "d4dgs_render_flow", "d4dgs_render_backward_flow", "d4dgs_flow_loss", "d4dgs_split_accumulate",
+           "d4dgs_split",
            "d4dgs_render",
            "d4dgs_render_backward", "d4dgs_read_stats", "d4dgs_render_host", "d4dgs_launches_per_frame",
            "D4DGSError", "D4DGS_OK", "D4DGS_ERR_CAPACITY", "D4DGS_ERR_TIMEOUT", "D4DGS_ERR_INVALID_ARG",
@@ -221,6 +222,37 @@ def d4dgs_flow_loss(rgb: torch.Tensor, flow: torch.Tensor, lam: float = 1.0, eps
                                    ctypes.c_void_p(dl_dflow.data_ptr()) if dl_dflow is not None else None,
                                    _stream_handle(stream)), "d4dgs_flow_loss")
     return loss
+
+
+def d4dgs_split_accumulate(grads: dict, stats: torch.Tensor, stream=None):
+    """Add |dL/d mean|, |dL/d t_mean| and 1 to stats (N x 3) for Gaussians with a nonzero gradient."""
+    n = int(grads["means"].shape[0])
+    g = _abi.d4dgs_scene_grad(*[grads[k].data_ptr() for k in SCENE_FIELDS])
+    _abi.check(_abi.load().d4dgs_split_accumulate(ctypes.byref(g), n, ctypes.c_void_p(stats.data_ptr()),
+                                                  _stream_handle(stream)), "d4dgs_split_accumulate")
+
+
+def d4dgs_split(scene: DeviceScene, stats: torch.Tensor, normals: torch.Tensor, tau_xyz: float, tau_t: float,
+                log_min_xyz: float, log_min_t: float, factor: float = 1.6, stream=None):
+    """Temporal / spatial splitting: returns (the new scene, its Gaussian count) -- the scene's tensors
+    have room for 2N Gaussians, the first `count` are valid (the count is read back)."""
+    n, dev = scene.n, scene.t["means"].device
+    cap = max(2 * n, 1)
+    K = (scene.sh_degree + 1) ** 2
+    shapes = {"means": (cap, 3), "t_mean": (cap,), "velocity": (cap, 3), "log_scales": (cap, 3),
+              "log_t_scale": (cap,), "quats": (cap, 4), "opacity_logit": (cap,), "sh": (cap, K, 3)}
+    out = {k: torch.empty(v, dtype=torch.float32, device=dev) for k, v in shapes.items()}
+    g = _abi.d4dgs_scene_grad(*[out[k].data_ptr() for k in SCENE_FIELDS])
+    lib = _abi.load()
+    scratch = torch.empty(max(int(lib.d4dgs_split_scratch_bytes(n)), 4), dtype=torch.uint8, device=dev)
+    out_n = torch.zeros(1, dtype=torch.int32, device=dev)
+    prm = _abi.d4dgs_split_params(float(tau_xyz), float(tau_t), float(log_min_xyz), float(log_min_t), float(factor))
+    _abi.check(lib.d4dgs_split(ctypes.byref(scene.struct()), ctypes.c_void_p(stats.data_ptr()),
+                               ctypes.c_void_p(normals.data_ptr()), ctypes.byref(prm), ctypes.byref(g), cap,
+                               ctypes.c_void_p(out_n.data_ptr()), ctypes.c_void_p(scratch.data_ptr()), scratch.numel(),
+                               _stream_handle(stream)), "d4dgs_split")
+    m = int(out_n.item())
+    return DeviceScene({k: v[:m] for k, v in out.items()}, scene.sh_degree), m
 
 
 def d4dgs_read_stats(n: int, cam, cfg, ws: torch.Tensor, stream=None) -> dict:

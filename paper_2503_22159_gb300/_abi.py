@@ -32,6 +32,10 @@ class d4dgs_scene4d(ctypes.Structure):
                                                 "sh")] + [("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
 
 
+class d4dgs_split_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("tau_xyz", "tau_t", "log_min_xyz", "log_min_t", "factor")]
+
+
 class d4dgs_scene_grad(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
                                                 "quats", "opacity_logit", "sh")]
@@ -95,6 +99,10 @@ PROTOTYPES = {
     "d4dgs_batch_area_bytes": (ctypes.c_size_t, []),
     "d4dgs_batch_encode": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_view), _P(d4dgs_config), _vp, ctypes.c_size_t]),
     "d4dgs_render_batch": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "d4dgs_split_accumulate": (ctypes.c_int, [_P(d4dgs_scene_grad), ctypes.c_int32, _vp, _vp]),
+    "d4dgs_split_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
+    "d4dgs_split": (ctypes.c_int, [_P(d4dgs_scene), _vp, _vp, _P(d4dgs_split_params), _P(d4dgs_scene_grad),
+                                   ctypes.c_int32, _vp, _vp, ctypes.c_size_t, _vp]),
     "d4dgs_render_flow": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config), _vp,
                                          ctypes.c_size_t, _vp, _vp, _vp]),
     "d4dgs_render_backward_flow": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),

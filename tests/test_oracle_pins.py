@@ -570,3 +570,45 @@ def test_image_edge_weight_is_one_minus_normalised_sobel():
     w = oracle.image_edge_weight(img)
     np.testing.assert_allclose(w[:, [4, 5]], 0.0, atol=1e-15)
     np.testing.assert_allclose(np.delete(w, [4, 5], axis=1), 1.0)
+
+
+# ---------------------------------------------------------------------------
+# temporal / spatial splitting (Sec. III-C)
+
+def test_split_children_straddle_the_parent():
+    """The two children of a spatial split lie at mu +- R diag(s) n, so their midpoint is the parent's
+    mean, their offset has Mahalanobis length |n| under the parent's Sigma3D, and their scales are the
+    parent's divided by the factor; a temporal split does the same along t with s_t."""
+    sc = synth.make_scene(50, 71, "tiny")
+    rng = np.random.default_rng(72)
+    normals = rng.standard_normal((50, 4))
+    stats = np.column_stack([rng.uniform(0, 2, 50), rng.uniform(0, 2, 50), np.full(50, 2.0)])
+    out, ss, tt = oracle.split_scene(sc, stats, normals, tau_xyz=0.5, tau_t=0.5, log_min_xyz=-10, log_min_t=-10)
+    assert 0 < ss.sum() < 50 and 0 < tt.sum() < 50
+    extra = np.nonzero(ss | tt)[0]
+    assert out.n == 50 + len(extra)
+    m64 = sc.means.astype(np.float64)
+    for j, i in enumerate(extra):
+        c1, c2 = out.means[i], out.means[50 + j]
+        np.testing.assert_allclose((c1 + c2) / 2, m64[i], atol=1e-12)
+        if ss[i]:
+            q = sc.quats[i].astype(np.float64)
+            R = oracle.quat_to_rot(q / np.linalg.norm(q))
+            S2 = R @ np.diag(np.exp(2 * sc.log_scales[i].astype(np.float64))) @ R.T
+            dv = c1 - m64[i]
+            assert dv @ np.linalg.solve(S2, dv) == pytest.approx(np.sum(normals[i, :3] ** 2), rel=1e-9)
+            np.testing.assert_allclose(np.exp(out.log_scales[i]), np.exp(sc.log_scales[i].astype(np.float64)) / 1.6, rtol=1e-12)
+        else:
+            np.testing.assert_allclose(c1, m64[i], atol=0)
+        if tt[i]:
+            st = math.exp(float(sc.log_t_scale[i]))
+            assert out.t_mean[i] - sc.t_mean[i] == pytest.approx(st * normals[i, 3], rel=1e-9)
+            assert out.t_mean[50 + j] - sc.t_mean[i] == pytest.approx(-st * normals[i, 3], rel=1e-9)
+
+
+def test_split_nothing_below_thresholds():
+    sc = synth.make_scene(30, 73, "tiny")
+    stats = np.column_stack([np.full(30, 0.1), np.full(30, 0.1), np.ones(30)])
+    out, ss, tt = oracle.split_scene(sc, stats, np.zeros((30, 4)), 0.5, 0.5, -10, -10)
+    assert not ss.any() and not tt.any() and out.n == 30
+    np.testing.assert_array_equal(out.means, sc.means.astype(np.float64))
