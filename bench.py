@@ -480,9 +480,29 @@ def run_backward(args, dev, d4, w, scene, cfg, cap):
                 tev["backward_flow"].append((f0, f1))
     torch.cuda.synchronize(dev)
     flow_ms = {k: float(np.mean([a.elapsed_time(b) for a, b in v])) for k, v in tev.items()}
+
+    # temporal / spatial splitting (Sec. III-C) of the whole scene from the statistics of these steps
+    stats = torch.zeros((scene.n, 3), device=dev)
+    for cam, t in frames:
+        d4.d4dgs_render(scene, cam, t, cfg, ws, out, stream)
+        d4.d4dgs_render_backward(scene, cam, t, cfg, ws, dl, grads, stream)
+        d4.d4dgs_split_accumulate(grads, stats, stream)
+    avg = stats[:, :2] / stats[:, 2:].clamp(min=1.0)
+    tau_xyz, tau_t = float(avg[:, 0].quantile(0.9)), float(avg[:, 1].quantile(0.9))   # ~10% split per kind
+    normals = torch.randn((scene.n, 4), generator=torch.Generator(device="cpu").manual_seed(6)).to(dev)
+    sp_ms = []
+    for rep in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        new_scene, new_n = d4.d4dgs_split(scene, stats, normals, tau_xyz, tau_t, -10.0, -10.0, 1.6, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sp_ms.append(e0.elapsed_time(e1))
+    split = {"ms": float(np.median(sp_ms)), "n_before": scene.n, "n_after": new_n,
+             "note": "median of 5 calls, the new count read back inside the call"}
     return {"ms_per_frame": ms, "frames": len(frames), "frames_per_s": 1e3 / ms,
             "k8_bytes_per_frame": scene.n * (64 + sh_bytes + 48 + 64 + sh_bytes),
-            "flow_ms_per_frame": flow_ms}
+            "flow_ms_per_frame": flow_ms, "split": split}
 
 
 def run_ours(args):
