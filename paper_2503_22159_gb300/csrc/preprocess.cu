@@ -95,20 +95,30 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
     const float t = vw.t;
     const float limx = mul(kJacClamp, dvd(mul(0.5f, (float)c.width), c.fx));
     const float limy = mul(kJacClamp, dvd(mul(0.5f, (float)c.height), c.fy));
+    // every geometric parameter is loaded before the first cull test, so a Gaussian
+    // costs one DRAM round trip instead of one per test
+    const float p_tm = __ldg(vw.t_mean + i);
+    const float p_m0 = __ldg(vw.means + 3 * i + 0), p_m1 = __ldg(vw.means + 3 * i + 1), p_m2 = __ldg(vw.means + 3 * i + 2);
+    const float p_v0 = __ldg(vw.velocity + 3 * i + 0), p_v1 = __ldg(vw.velocity + 3 * i + 1);
+    const float p_v2 = __ldg(vw.velocity + 3 * i + 2);
+    const float p_lg = __ldg(vw.opacity_logit + i), p_lt = __ldg(vw.log_t_scale + i);
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(vw.quats) + i);
+    const float p_s0 = __ldg(vw.log_scales + 3 * i + 0), p_s1 = __ldg(vw.log_scales + 3 * i + 1);
+    const float p_s2 = __ldg(vw.log_scales + 3 * i + 2);
     do {
         // ---- deferred temporal slice and camera transform (binning order)
-        const float tau = sub(t, __ldg(vw.t_mean + i));
-        const float m0 = add(__ldg(vw.means + 3 * i + 0), mul(tau, __ldg(vw.velocity + 3 * i + 0)));
-        const float m1 = add(__ldg(vw.means + 3 * i + 1), mul(tau, __ldg(vw.velocity + 3 * i + 1)));
-        const float m2 = add(__ldg(vw.means + 3 * i + 2), mul(tau, __ldg(vw.velocity + 3 * i + 2)));
+        const float tau = sub(t, p_tm);
+        const float m0 = add(p_m0, mul(tau, p_v0));
+        const float m1 = add(p_m1, mul(tau, p_v1));
+        const float m2 = add(p_m2, mul(tau, p_v2));
         const float *R = c.R;
         const float X = add(add(add(mul(R[0], m0), mul(R[1], m1)), mul(R[2], m2)), c.T[0]);
         const float Y = add(add(add(mul(R[3], m0), mul(R[4], m1)), mul(R[5], m2)), c.T[1]);
         const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
         if (!(Z > kNear)) break;
         // ---- temporal opacity
-        const float o = dvd(1.0f, add(1.0f, expf(-__ldg(vw.opacity_logit + i))));
-        const float st = expf(__ldg(vw.log_t_scale + i));
+        const float o = dvd(1.0f, add(1.0f, expf(-p_lg)));
+        const float st = expf(p_lt);
         const float oh = mul(o, expf(dvd(mul(-0.5f, mul(tau, tau)), mul(st, st))));
         if (!(oh >= kAlphaMin)) break;
         // ---- projection of the mean and the Jacobian at the shifted mean
@@ -118,7 +128,6 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
         const float J00 = dvd(c.fx, Z), J02 = dvd(-mul(c.fx, xzc), Z);
         const float J11 = dvd(c.fy, Z), J12 = dvd(-mul(c.fy, yzc), Z);
         // ---- 3D covariance factor M = R(q) diag(s)
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(vw.quats) + i);
         const float qn = __fsqrt_rn(add(add(add(mul(q.x, q.x), mul(q.y, q.y)), mul(q.z, q.z)), mul(q.w, q.w)));
         const float qw = dvd(q.x, qn), qx = dvd(q.y, qn), qy = dvd(q.z, qn), qz = dvd(q.w, qn);
         float Rq[9];
@@ -131,8 +140,7 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
         Rq[6] = mul(2.0f, sub(mul(qx, qz), mul(qw, qy)));
         Rq[7] = mul(2.0f, add(mul(qy, qz), mul(qw, qx)));
         Rq[8] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qy, qy))));
-        const float sc[3] = {expf(__ldg(vw.log_scales + 3 * i + 0)), expf(__ldg(vw.log_scales + 3 * i + 1)),
-                         expf(__ldg(vw.log_scales + 3 * i + 2))};
+        const float sc[3] = {expf(p_s0), expf(p_s1), expf(p_s2)};
         float M[9];
 #pragma unroll
         for (int r = 0; r < 3; r++)
@@ -157,8 +165,7 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
         f.m0 = m0; f.m1 = m1; f.m2 = m2;
         f.Z = Z; f.u = u; f.v = v; f.oh = oh;
         f.s00 = s00; f.s01 = s01; f.s11 = s11;
-        if (vw.out_flow)
-            screen_flow(c, __ldg(vw.velocity + 3 * i), __ldg(vw.velocity + 3 * i + 1), __ldg(vw.velocity + 3 * i + 2), Z, f);
+        if (vw.out_flow) screen_flow(c, p_v0, p_v1, p_v2, Z, f);
         return true;
     } while (0);
     return false;
