@@ -340,6 +340,18 @@ size_t d4dgs_scene_bytes(int32_t n, int32_t sh_degree);
 int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
                       void *dev_scene_buf, size_t dev_scene_bytes, void *ws, size_t ws_bytes,
                       void *dev_rgb, float *out_rgb_host, d4dgs_stream_t stream);
+/* d4dgs_render_host without the final wait: the copies and the frame are
+ * queued on `stream` and the image is in out_rgb_host once the stream has
+ * reached this point (cudaStreamSynchronize, or an event recorded after the
+ * call).  Until then the host scene arrays, out_rgb_host, dev_scene_buf, ws
+ * and dev_rgb belong to the call.  Callers that give consecutive frames
+ * their own slot (staging buffer, workspace, device image, stream) overlap
+ * one frame's copies with another's kernels.  Same arguments, checks and
+ * return codes as d4dgs_render_host (CUDA errors of the queued work surface
+ * at the wait). */
+int d4dgs_render_host_async(const d4dgs_scene *host_scene, const d4dgs_camera *cam, float t,
+                            const d4dgs_config *cfg, void *dev_scene_buf, size_t dev_scene_bytes, void *ws,
+                            size_t ws_bytes, void *dev_rgb, float *out_rgb_host, d4dgs_stream_t stream);
 
 /* d4dgs_render for callers that cannot allocate device memory when they
  * render (the paper has no counterpart; this is a library convenience).  The

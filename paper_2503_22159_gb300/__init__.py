@@ -30,7 +30,8 @@ __all__ = ["DeviceScene", "Renderer", "BatchRenderer", "camera_struct", "config_
            "d4dgs_render_flow", "d4dgs_render_backward_flow", "d4dgs_flow_loss", "d4dgs_split_accumulate",
            "d4dgs_split",
            "d4dgs_render",
-           "d4dgs_render_backward", "d4dgs_read_stats", "d4dgs_render_host", "d4dgs_launches_per_frame",
+           "d4dgs_render_backward", "d4dgs_read_stats", "d4dgs_render_host", "d4dgs_render_host_async",
+           "d4dgs_launches_per_frame",
            "D4DGSError", "D4DGS_OK", "D4DGS_ERR_CAPACITY", "D4DGS_ERR_TIMEOUT", "D4DGS_ERR_INVALID_ARG",
            "D4DGS_ERR_WORKSPACE_TOO_SMALL", "D4DGS_ERR_CUDA"]
 
@@ -279,6 +280,20 @@ def d4dgs_render_host(host_scene, cam, t: float, cfg, dev_scene_buf: torch.Tenso
                                              dev_scene_buf.numel(), p, nb, ctypes.c_void_p(dev_rgb.data_ptr()),
                                              ctypes.c_void_p(out_host.data_ptr()), _stream_handle(stream)),
                "d4dgs_render_host")
+
+
+def d4dgs_render_host_async(host_scene, cam, t: float, cfg, dev_scene_buf: torch.Tensor, ws: torch.Tensor,
+                            dev_rgb: torch.Tensor, out_host: torch.Tensor, stream=None):
+    """d4dgs_render_host queued on `stream` without waiting: out_host holds the image once the
+    stream has passed this point; the host and device buffers belong to the call until then."""
+    s = _abi.d4dgs_scene(*[host_scene[k].data_ptr() for k in SCENE_FIELDS], int(host_scene["means"].shape[0]),
+                         int(host_scene["sh_degree"]))
+    p, nb = _ws(ws)
+    _abi.check(_abi.load().d4dgs_render_host_async(ctypes.byref(s), ctypes.byref(camera_struct(cam)), float(t),
+                                                   ctypes.byref(cfg), ctypes.c_void_p(dev_scene_buf.data_ptr()),
+                                                   dev_scene_buf.numel(), p, nb, ctypes.c_void_p(dev_rgb.data_ptr()),
+                                                   ctypes.c_void_p(out_host.data_ptr()), _stream_handle(stream)),
+               "d4dgs_render_host_async")
 
 
 def d4dgs_launches_per_frame(n: int, cam, cfg) -> int:

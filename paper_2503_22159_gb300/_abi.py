@@ -93,6 +93,8 @@ PROTOTYPES = {
     "d4dgs_scene_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
     "d4dgs_render_host": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config), _vp,
                                          ctypes.c_size_t, _vp, ctypes.c_size_t, _vp, _vp, _vp]),
+    "d4dgs_render_host_async": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config), _vp,
+                                         ctypes.c_size_t, _vp, ctypes.c_size_t, _vp, _vp, _vp]),
     "d4dgs_render_static": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),
                                            _vp, _P(d4dgs_stats), _vp]),
     "d4dgs_batch_args_bytes": (ctypes.c_size_t, []),

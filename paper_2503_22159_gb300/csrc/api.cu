@@ -567,9 +567,10 @@ size_t d4dgs_scene_bytes(int32_t n, int32_t sh_degree) {
     return (size_t)off;
 }
 
-int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
-                      void *dev_scene_buf, size_t dev_scene_bytes, void *ws, size_t ws_bytes, void *dev_rgb,
-                      float *out_rgb_host, d4dgs_stream_t stream) {
+// Copies in, frame, copy out, all on `stream`; waits for the stream when `sync`.
+static int render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                       void *dev_scene_buf, size_t dev_scene_bytes, void *ws, size_t ws_bytes, void *dev_rgb,
+                       float *out_rgb_host, d4dgs_stream_t stream, bool sync) {
     if (!host_scene || host_scene->n < 0 || host_scene->sh_degree < 0 || host_scene->sh_degree > 3)
         return D4DGS_ERR_INVALID_ARG;
     if (!dev_scene_buf || !aligned(dev_scene_buf, 256) || !dev_rgb || !out_rgb_host || !valid_camera(cam))
@@ -597,8 +598,22 @@ int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, fl
     if (rc) return rc;
     const size_t img = (size_t)cam->width * cam->height * 3 * sizeof(float);
     if (cudaMemcpyAsync(out_rgb_host, dev_rgb, img, cudaMemcpyDeviceToHost, st) != cudaSuccess) return D4DGS_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return D4DGS_ERR_CUDA;
+    if (sync && cudaStreamSynchronize(st) != cudaSuccess) return D4DGS_ERR_CUDA;
     return D4DGS_OK;
+}
+
+int d4dgs_render_host(const d4dgs_scene *host_scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                      void *dev_scene_buf, size_t dev_scene_bytes, void *ws, size_t ws_bytes, void *dev_rgb,
+                      float *out_rgb_host, d4dgs_stream_t stream) {
+    return render_host(host_scene, cam, t, cfg, dev_scene_buf, dev_scene_bytes, ws, ws_bytes, dev_rgb, out_rgb_host,
+                       stream, true);
+}
+
+int d4dgs_render_host_async(const d4dgs_scene *host_scene, const d4dgs_camera *cam, float t,
+                            const d4dgs_config *cfg, void *dev_scene_buf, size_t dev_scene_bytes, void *ws,
+                            size_t ws_bytes, void *dev_rgb, float *out_rgb_host, d4dgs_stream_t stream) {
+    return render_host(host_scene, cam, t, cfg, dev_scene_buf, dev_scene_bytes, ws, ws_bytes, dev_rgb, out_rgb_host,
+                       stream, false);
 }
 
 int d4dgs_launches_per_frame(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg) {

@@ -250,3 +250,36 @@ def test_render_host_matches_device_path():
     out = torch.empty(img.shape, dtype=torch.float32).pin_memory()
     m.d4dgs_render_host(host, cam, t, r.cfg, buf, r.ws, dev_rgb, out)
     assert torch.equal(out, img.cpu())
+
+
+def test_render_host_async_two_slots_match_device_path():
+    """Frames queued alternately on two slots (staging buffer, workspace, device image, stream)
+    overlap on the device; after each slot's wait its host image equals the device-path render."""
+    w = synth.tiny_workload()
+    m = gu.d4()
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).pin_memory() for k in m.SCENE_FIELDS}
+    host["sh_degree"] = w.scene.sh_degree
+    frames = [(w.frames[0][0], t) for t in (0.5, 0.1, 0.9, 0.3)]
+    refs = [gu.render(w.scene, cam, t)[2].cpu() for cam, t in frames]
+    cam0 = frames[0][0]
+    slots = []
+    for _ in range(2):
+        r = m.Renderer(w.scene.n, cam0)
+        slots.append(dict(r=r, buf=torch.empty(m.d4dgs_scene_bytes(w.scene.n, w.scene.sh_degree), dtype=torch.uint8,
+                                               device="cuda"),
+                          rgb=torch.empty((cam0.height, cam0.width, 3), device="cuda"),
+                          out=torch.empty((cam0.height, cam0.width, 3)).pin_memory(), st=torch.cuda.Stream()))
+    got = [None] * len(frames)
+    pending = [None, None]
+    for k, (cam, t) in enumerate(frames):
+        s = slots[k % 2]
+        if pending[k % 2] is not None:
+            s["st"].synchronize()
+            got[pending[k % 2]] = s["out"].clone()
+        m.d4dgs_render_host_async(host, cam, t, s["r"].cfg, s["buf"], s["r"].ws, s["rgb"], s["out"], s["st"])
+        pending[k % 2] = k
+    for j in range(2):
+        slots[j]["st"].synchronize()
+        got[pending[j]] = slots[j]["out"].clone()
+    for a, b in zip(got, refs):
+        assert torch.equal(a, b)
