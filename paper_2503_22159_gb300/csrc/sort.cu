@@ -238,13 +238,16 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
             run += c;
         }
         const uint32_t bcount = run;
+        // only digits the pass can produce take part in the look-back (a row
+        // pass over 5 bits has 32 of them; padding keys take the top digit)
+        const bool live = d <= mask;
         uint32_t *lb = lookback + (size_t)part * kRadix;
-        st_volatile_u32(lb + d, (part == 0 ? kFlagInc : kFlagAgg) | bcount);
+        if (live) st_volatile_u32(lb + d, (part == 0 ? kFlagInc : kFlagAgg) | bcount);
         uint32_t btot;
         const uint32_t lstart = block_exclusive_scan_256(bcount, s_scan, &btot);
         s_local_start[d] = lstart;
         uint32_t excl = 0;
-        if (part > 0) {
+        if (part > 0 && live) {
             excl = lookback_serial<4, 4>(lookback + d, kRadix, (int64_t)part - 1, status);
             st_volatile_u32(lb + d, kFlagInc | ((excl + bcount) & kValMask));
         }
