@@ -433,6 +433,8 @@ class Renderer:
                 return out
             st = d4dgs_read_stats(self.n, cam, self.cfg, self.ws, stream)
             if st["status"] == D4DGS_ERR_CAPACITY:
+                if self.key_capacity >= (1 << 30) - 1:   # the largest capacity the workspace format allows
+                    break
                 self._alloc(int(st["n_keys"] * 1.25) + 1024)
                 continue
             if st["status"] != D4DGS_OK:

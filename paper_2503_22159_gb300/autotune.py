@@ -57,25 +57,36 @@ class TuneCache:
 
 
 def sweep(time_config, tiles=TILES, batches=BATCHES):
-    """time_config(tile, batch) -> ms per frame; returns (best (tile, batch), {"tile/batch": ms})."""
+    """time_config(tile, batch) -> ms per frame, or None when the configuration cannot render
+    these frames; returns (best (tile, batch), {"tile/batch": ms or None})."""
     table = {}
     for t in tiles:
         for b in batches:
-            table[f"{t}/{b}"] = float(time_config(t, b))
-    best = min(table, key=table.get)
+            ms = time_config(t, b)
+            table[f"{t}/{b}"] = None if ms is None else float(ms)
+    feasible = {k: v for k, v in table.items() if v is not None}
+    if not feasible:
+        raise RuntimeError("no tile / batch configuration can render these frames")
+    best = min(feasible, key=feasible.get)
     t, b = best.split("/")
     return (int(t), int(b)), table
 
 
 def time_frames(scene, frames, tile: int, batch: int, warmup: int = 2, reps: int = 1, device="cuda") -> float:
-    """Mean ms per frame of d4dgs_render for one (tile, batch) over `frames` [(camera, t)]."""
+    """Mean ms per frame of d4dgs_render for one (tile, batch) over `frames` [(camera, t)];
+    None when a frame has more (tile, Gaussian) pairs than a workspace can hold at this tile size."""
     import torch
 
-    from . import Renderer, config_struct, d4dgs_render, d4dgs_workspace_bytes
+    from . import D4DGS_ERR_CAPACITY, D4DGSError, Renderer, d4dgs_render
     cam0 = frames[0][0]
     r = Renderer(scene.n, cam0, tile=tile, batch=batch, device=device)
-    for cam, t in frames:                      # size the workspace for these frames
-        r.render(scene, cam, t)
+    try:
+        for cam, t in frames:                  # size the workspace for these frames
+            r.render(scene, cam, t)
+    except D4DGSError as e:
+        if e.code != D4DGS_ERR_CAPACITY:
+            raise
+        return None
     out = torch.empty((cam0.height, cam0.width, 3), dtype=torch.float32, device=device)
     stream = torch.cuda.current_stream(device)
     for k in range(warmup):

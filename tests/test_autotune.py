@@ -29,6 +29,15 @@ def test_sweep_picks_fastest_and_cache_roundtrip(at, tmp_path):
     assert at.TuneCache().get(at.cache_key("GB300", 1352, 1014, 600_000)) is None   # other N bucket
 
 
+def test_sweep_skips_configurations_that_cannot_render(at):
+    """A tile size whose frames need more pairs than a workspace can hold is reported as None."""
+    best, table = at.sweep(lambda t, b: None if t == 8 else float(t + b / 1000))
+    assert best == (16, 64)
+    assert all(table[f"8/{b}"] is None for b in at.BATCHES)
+    with pytest.raises(RuntimeError):
+        at.sweep(lambda t, b: None)
+
+
 @pytest.mark.gpu
 def test_gpu_sweep_choice_renders_identically(at):
     import paper_2503_22159_gb300 as d4
