@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--workload", choices=["scene", "tiny", "large"], default="scene")
     p.add_argument("--tile", default="auto", help="8, 16, 32 or auto (autotuner sweep)")
     p.add_argument("--batch", type=int, default=256)
+    p.add_argument("--trim", action="store_true", help="cut binning rectangles per column (--tile auto decides)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-e2e", action="store_true")
@@ -252,6 +253,7 @@ def config_dict(w, args):
     cam, _ = w.frames[0]
     return {"workload": w.name, "gaussians": w.scene.n, "sh_degree": w.scene.sh_degree, "width": cam.width,
             "height": cam.height, "timestamps": len(w.frames), "tile": args.tile, "batch": args.batch,
+            "column_cuts": bool(getattr(args, "trim", False)),
             "l2": "flushed before every frame (256 MiB write, outside the timed events)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -419,7 +421,7 @@ def run_backward(args, dev, d4, w, scene, cfg, cap):
     stream = torch.cuda.current_stream(dev)
     frames = [w.frames[k] for k in range(0, len(w.frames), 15)]
     cam0 = frames[0][0]
-    rr = d4.Renderer(scene.n, cam0, tile=cfg.tile, batch=cfg.batch, key_capacity=cap, device=dev)
+    rr = d4.Renderer(scene.n, cam0, tile=cfg.tile, batch=cfg.batch, key_capacity=cap, device=dev, trim=bool(cfg.trim))
     for cam, t in frames:   # grows the key capacity to these frames
         rr.render(scene, cam, t)
     ws = rr.ws
@@ -533,16 +535,17 @@ def run_ours(args):
     if args.tile == "auto":
         from paper_2503_22159_gb300 import autotune
         probe = [w.frames[k] for k in (0, nf // 2, nf - 1)]
-        (tile, batch), tune_table = autotune.tune(scene, probe, device=dev, force=True)
-        args.tile, args.batch = tile, batch
+        (tile, batch, trim), tune_table = autotune.tune(scene, probe, device=dev, force=True)
+        args.tile, args.batch, args.trim = tile, batch, trim
     args.tile = int(args.tile)
-    cfg = d4.config_struct(args.tile, args.batch)
+    cfg = d4.config_struct(args.tile, args.batch, trim=args.trim)
     cam0 = w.frames[0][0]
     K, W = args.steps, args.warmup
     order = rank_frames(rank, world, nf, W + K)
 
     # size the key capacity on this rank's frames (untimed)
-    r = d4.Renderer(scene.n, cam0, tile=args.tile, batch=args.batch, key_capacity=160 * scene.n, device=dev)
+    r = d4.Renderer(scene.n, cam0, tile=args.tile, batch=args.batch, key_capacity=160 * scene.n, device=dev,
+                    trim=args.trim)
     max_keys = 0
     for fi in sorted(set(order)):
         cam, t = w.frames[fi]
@@ -655,7 +658,7 @@ def run_ours(args):
         slots = []
         for j in range(2):
             rj = r if j == 0 else d4.Renderer(n, cam0, tile=int(cfg.tile), batch=int(cfg.batch),
-                                              key_capacity=r.key_capacity, device=dev)
+                                              key_capacity=r.key_capacity, device=dev, trim=bool(cfg.trim))
             slots.append(dict(r=rj, st=stream if j == 0 else torch.cuda.Stream(device=dev),
                               buf=torch.empty(d4.d4dgs_scene_bytes(n, w.scene.sh_degree), dtype=torch.uint8,
                                               device=dev),
@@ -716,7 +719,8 @@ def run_ours(args):
         "wall_s_timed_region": t_wall, "peaks": peak_kind,
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out, "time_groups": groups_out,
         "slicing_first": slicing_out, "backward": backward_out,
-        "autotune": {"chosen": f"{args.tile}/{args.batch}", "ms_per_frame": tune_table} if tune_table else None,
+        "autotune": {"chosen": f"{args.tile}/{args.batch}" + ("/cut" if args.trim else ""),
+                     "ms_per_frame": tune_table} if tune_table else None,
     }
     print(json.dumps(line), flush=True)
     if pg:

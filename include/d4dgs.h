@@ -85,11 +85,16 @@ typedef struct {
 
 /* Rasteriser settings.  tile: 8, 16 or 32 pixels; batch: Gaussians staged
  * per shared-memory batch in the blend, 64, 128 or 256 (<= tile*tile);
- * bg: background colour added with the final transmittance. */
+ * bg: background colour added with the final transmittance; trim: 0 bins
+ * each Gaussian into its whole tile rectangle, 1 cuts the rectangle's first
+ * 8 columns to the tile rows its alpha >= 1/255 ellipse reaches (fewer
+ * pairs, more binning arithmetic: worth it for large splats; the image is
+ * the same either way). */
 typedef struct {
     int32_t tile;
     int32_t batch;
     float bg[3];
+    int32_t trim;
 } d4dgs_config;
 
 /* Counters read back after a frame (host struct). */
@@ -105,7 +110,7 @@ typedef struct {
 typedef struct {
     int64_t records;             /* N x 12 float: (u,v,a,b) (c,o_hat,depth,radius) (r,g,b,log2 o_hat) */
     int64_t depth_keys;          /* N uint32: float bits of camera z, 0xFFFFFFFF if culled   */
-    int64_t tiles_touched;       /* N uint32                                                 */
+    int64_t tiles_touched;       /* N uint32: tiles kept of the trimmed rectangle, 0 if culled */
     int64_t rect;                /* N x 4 uint16: x0, x1, y0, y1 (inclusive tile indices)    */
     int64_t depth_order;         /* N uint32: Gaussian ids sorted by (depth key, id)         */
     int64_t tile_keys;           /* key_capacity uint32, sorted by tile: (tile key << id_bits) | id
@@ -122,6 +127,11 @@ typedef struct {
     int32_t id_bits;             /* ceil(log2 N) */
     int32_t packed;              /* 1: pairs packed in one uint32 (tile key bits + id_bits <= 32) */
     int32_t col_bits;            /* ceil(log2 tiles_x): bits of the column in a tile key      */
+    int64_t trims;               /* N uint64: per-column trims of the rectangle (config trim = 1,
+                                    else 0); byte j (column x0 + j, j < 8) = rows cut at the
+                                    top | rows cut at the bottom << 4 (0..15 each); the
+                                    Gaussian's tiles are the rectangle minus these cuts,
+                                    tiles_touched of them                                    */
 } d4dgs_layout;
 
 /* Bytes of workspace for N Gaussians, this camera and config, and room for

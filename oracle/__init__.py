@@ -99,12 +99,13 @@ def lib():
         _lib.orc_render_pixels.argtypes = [ctypes.POINTER(_G2D), ctypes.c_int, ctypes.POINTER(_Camera),
                                            c_double_p, ctypes.c_int64, c_int32_p, c_int32_p, ctypes.c_double,
                                            c_double_p, c_double_p, c_int32_p, c_double_p, c_double_p]
+        c_uint64_p = ctypes.POINTER(ctypes.c_uint64)
         _lib.orc_bin_f32.argtypes = [ctypes.POINTER(_SceneF32), ctypes.POINTER(_CameraF32), ctypes.c_float,
-                                     ctypes.c_int32, c_uint32_p, c_int32_p, c_int32_p, c_uint32_p, c_int32_p,
-                                     c_float_p]
+                                     ctypes.c_int32, ctypes.c_int32, c_uint32_p, c_int32_p, c_int32_p, c_uint32_p, c_uint64_p,
+                                     c_int32_p, c_float_p]
         _lib.orc_emit_keys.restype = ctypes.c_int64
-        _lib.orc_emit_keys.argtypes = [ctypes.c_int32, c_uint32_p, c_int32_p, c_uint32_p, ctypes.c_int32,
-                                       ctypes.c_int64, c_uint32_p, c_uint32_p, c_uint32_p]
+        _lib.orc_emit_keys.argtypes = [ctypes.c_int32, c_uint32_p, c_int32_p, c_uint64_p, c_uint32_p,
+                                       ctypes.c_int32, ctypes.c_int64, c_uint32_p, c_uint32_p, c_uint32_p]
         _lib.orc_sh_basis.argtypes = [c_double_p, ctypes.c_int, c_double_p]
         _lib.orc_quat_to_rot.argtypes = [c_double_p, c_double_p]
         _lib.orc_backward.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
@@ -240,8 +241,9 @@ def render(scene, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0), temporal_cull:
     return out
 
 
-def bin_f32(scene, cam, t: float, tile: int) -> dict:
-    """FP32 binning mirror: depth key bits, radius, rect, tile count, flags, uv."""
+def bin_f32(scene, cam, t: float, tile: int, trim: bool = False) -> dict:
+    """FP32 binning mirror: depth key bits, radius, rect, column trims (``trim``: the renderer's
+    config trim; all zero otherwise), tile count, flags, uv."""
     n = scene.n
     f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     arrs = {k: f(getattr(scene, k)) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
@@ -254,11 +256,12 @@ def bin_f32(scene, cam, t: float, tile: int) -> dict:
     c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
     c.width, c.height = int(cam.width), int(cam.height)
     out = dict(depth_key=np.zeros(n, np.uint32), radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
-               tiles_touched=np.zeros(n, np.uint32), flags=np.zeros(n, np.int32), uv=np.zeros((n, 2), np.float32))
-    lib().orc_bin_f32(ctypes.byref(s), ctypes.byref(c), ctypes.c_float(t), int(tile),
+               tiles_touched=np.zeros(n, np.uint32), trims=np.zeros(n, np.uint64), flags=np.zeros(n, np.int32),
+               uv=np.zeros((n, 2), np.float32))
+    lib().orc_bin_f32(ctypes.byref(s), ctypes.byref(c), ctypes.c_float(t), int(tile), 1 if trim else 0,
                       _p(out["depth_key"], ctypes.c_uint32), _p(out["radius"], ctypes.c_int32),
                       _p(out["rect"], ctypes.c_int32), _p(out["tiles_touched"], ctypes.c_uint32),
-                      _p(out["flags"], ctypes.c_int32), _p(out["uv"], ctypes.c_float))
+                      _p(out["trims"], ctypes.c_uint64), _p(out["flags"], ctypes.c_int32), _p(out["uv"], ctypes.c_float))
     out["tiles_x"] = (cam.width + tile - 1) // tile
     out["tiles_y"] = (cam.height + tile - 1) // tile
     return out
@@ -273,6 +276,7 @@ def tile_list(b: dict) -> dict:
     depth = np.zeros(total, np.uint32)
     ids = np.zeros(total, np.uint32)
     k = lib().orc_emit_keys(n, _p(b["depth_key"], ctypes.c_uint32), _p(np.ascontiguousarray(b["rect"]), ctypes.c_int32),
+                            _p(np.ascontiguousarray(b["trims"]), ctypes.c_uint64),
                             _p(b["tiles_touched"], ctypes.c_uint32), int(b["tiles_x"]), total,
                             _p(tile, ctypes.c_uint32), _p(depth, ctypes.c_uint32), _p(ids, ctypes.c_uint32))
     assert k == total

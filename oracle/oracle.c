@@ -397,11 +397,27 @@ void orc_render_pixels(const orc_g2d *g, int n, const orc_camera *cam, const dou
  *   (bounding box of d^T Sigma'^-1 d <= k2: outside it o_hat e^p < 1/255)
  *   x0 = floorf((u - rx)/tile), x1 = floorf((u + rx)/tile),
  *   cull if x1 < 0 or x0 > tiles_x - 1, then clamp to [0, tiles_x-1] (same in y with ry)
- *   tiles = (x1 - x0 + 1)(y1 - y0 + 1); depth key = bits of Z
+ *   column cuts (only when `trim` is set; otherwise every column keeps its h
+ *   rows), for rectangle columns c = x0 + j, j < 8 (ex = sqrtf(k2*s00),
+ *   ey = sqrtf(k2*s11), q2 = k2*s00, xl = (s01*ey)/s11, tl = tile - 0.5):
+ *     a = max(((c*tile) + 0.5) - u, -ex);  b = min(min((c*tile) + tl, W - 0.5) - u, ex)
+ *     a > b (the column's pixel centres miss the ellipse): cut_t = min(h, 15),
+ *       cut_b = min(h - cut_t, 15)
+ *     else xt = min(max(-xl, a), b), xb = min(max(xl, a), b), i00 = 1/s00
+ *       lo = ((v + ((s01*xt) - sqrtf(max(0, det*(q2 - xt*xt))))*i00) - 1/64) - tl
+ *       hi = ((v + ((s01*xb) + sqrtf(max(0, det*(q2 - xb*xb))))*i00) + 1/64) - 0.5
+ *       cut_t = clamp(ceilf(lo/tile) - y0, 0, 15), cut_b = clamp(y1 - floorf(hi/tile), 0, 15)
+ *     (xt, xb: abscissae of the ellipse's top and bottom points clamped to the
+ *     column; the column keeps the tile rows whose pixel-centre rows meet
+ *     [lo + tl, hi + 0.5]); trims byte j = cut_t | cut_b << 4
+ *   tiles = sum over columns of max(0, h - cut_t - cut_b) (columns from the
+ *   9th on keep all h rows); culled if 0; depth key = bits of Z
  * Flags: bit 0 -- sqrt(k2 s00) or sqrt(k2 s11) within 3e-6 relative of an
  * integer (rectangle); bit 1 -- o_hat within 3e-6 relative of 1/255 (cull);
  * bit 2 -- 3.33 sqrt(lambda_max) within 3e-6 of an integer (the radius field
- * only: it does not take part in binning).
+ * only: it does not take part in binning); bit 3 -- a column-cut decision
+ * (a against b through ex, lo/tile or hi/tile against an integer) within
+ * reach of the same ulp differences.
  * Every operation above is correctly rounded and reproducible on any IEEE
  * machine except expf and logf, whose FP32 results may differ by one or two
  * ulps between math libraries; through the chains (s -> Sigma' -> radii, three
@@ -418,9 +434,9 @@ typedef struct {
 
 typedef struct { float R[9], T[3], fx, fy, cx, cy; int32_t width, height; } orc_camera_f32;
 
-void orc_bin_f32(const orc_scene_f32 *sc, const orc_camera_f32 *cam, float t, int32_t tile,
+void orc_bin_f32(const orc_scene_f32 *sc, const orc_camera_f32 *cam, float t, int32_t tile, int32_t trim,
                  uint32_t *depth_key, int32_t *radius, int32_t *rect /* N x 4: x0,x1,y0,y1 */,
-                 uint32_t *tiles_touched, int32_t *flags, float *uv /* N x 2, may be NULL */) {
+                 uint32_t *tiles_touched, uint64_t *trims, int32_t *flags, float *uv /* N x 2, may be NULL */) {
     const int n = sc->n;
     const int32_t tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
     const float limx = 1.3f * ((0.5f * (float)cam->width) / cam->fx);
@@ -433,6 +449,7 @@ void orc_bin_f32(const orc_scene_f32 *sc, const orc_camera_f32 *cam, float t, in
         radius[i] = 0;
         rect[4 * (size_t)i + 0] = rect[4 * (size_t)i + 1] = rect[4 * (size_t)i + 2] = rect[4 * (size_t)i + 3] = 0;
         tiles_touched[i] = 0;
+        trims[i] = 0;
         flags[i] = 0;
         if (uv) { uv[2 * (size_t)i] = 0.f; uv[2 * (size_t)i + 1] = 0.f; }
         const float *mu = sc->means + 3 * (size_t)i, *vel = sc->velocity + 3 * (size_t)i;
@@ -500,26 +517,72 @@ void orc_bin_f32(const orc_scene_f32 *sc, const orc_camera_f32 *cam, float t, in
         if (!(fy1 >= 0.0f) || !(fy0 <= (float)(tiles_y - 1))) continue;
         int32_t x0 = (int32_t)fmaxf(fx0, 0.0f), x1 = (int32_t)fminf(fx1, (float)(tiles_x - 1));
         int32_t y0 = (int32_t)fmaxf(fy0, 0.0f), y1 = (int32_t)fminf(fy1, (float)(tiles_y - 1));
+        /* column cuts */
+        const int32_t h = y1 - y0 + 1;
+        const float q2 = k2 * s00, xl = (s01 * ey) / s11, i00 = 1.0f / s00;
+        const float tl = tilef - 0.5f, wl = (float)cam->width - 0.5f;
+        /* ulp differences in expf / logf move k2 and Sigma' by <= ~1.5e-6 relative and
+         * the row extents (|offset| <= ey) with them; u, v are the same bits everywhere */
+        const double reach = 3e-6 * ((double)ey / tilef);
+        uint64_t tw = 0;
+        int64_t kept = 0;
+        for (int32_t c = x0; c <= x1; c++) {
+            const int32_t j = c - x0;
+            int32_t cut_t = 0, cut_b = 0;
+            if (trim && j < 8) {
+                const float left = ((float)c * tilef + 0.5f) - u;
+                const float right = fminf((float)c * tilef + tl, wl) - u;
+                if (fabs((double)left - ex) <= 3e-6 * ex || fabs((double)right + ex) <= 3e-6 * ex) flags[i] |= 8;
+                const float a = fmaxf(left, -ex), b = fminf(right, ex);
+                if (!(a <= b)) {
+                    cut_t = h < 15 ? h : 15;
+                    cut_b = h - cut_t < 15 ? h - cut_t : 15;
+                } else {
+                    const float xt = fminf(fmaxf(-xl, a), b), xb = fminf(fmaxf(xl, a), b);
+                    const float lo = ((v + ((s01 * xt) - sqrtf(fmaxf(0.0f, det * (q2 - xt * xt)))) * i00) - 0.015625f) - tl;
+                    const float hi = ((v + ((s01 * xb) + sqrtf(fmaxf(0.0f, det * (q2 - xb * xb)))) * i00) + 0.015625f) - 0.5f;
+                    const float flo = lo / tilef, fhi = hi / tilef;
+                    if (fabs((double)flo - nearbyint((double)flo)) <= reach + 2e-7 * (fabs((double)flo) + 1.0) ||
+                        fabs((double)fhi - nearbyint((double)fhi)) <= reach + 2e-7 * (fabs((double)fhi) + 1.0))
+                        flags[i] |= 8;
+                    cut_t = (int32_t)fminf(fmaxf(ceilf(flo) - (float)y0, 0.0f), 15.0f);
+                    cut_b = (int32_t)fminf(fmaxf((float)y1 - floorf(fhi), 0.0f), 15.0f);
+                }
+                tw |= (uint64_t)(uint32_t)(cut_t | (cut_b << 4)) << (8 * j);
+            }
+            if (h - cut_t - cut_b > 0) kept += h - cut_t - cut_b;
+        }
+        if (kept == 0) continue;
         uint32_t bits;
         memcpy(&bits, &Z, 4);
         depth_key[i] = bits;
         radius[i] = (int32_t)rf;
         rect[4 * (size_t)i + 0] = x0; rect[4 * (size_t)i + 1] = x1;
         rect[4 * (size_t)i + 2] = y0; rect[4 * (size_t)i + 3] = y1;
-        tiles_touched[i] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+        tiles_touched[i] = (uint32_t)kept;
+        trims[i] = tw;
         if (uv) { uv[2 * (size_t)i] = u; uv[2 * (size_t)i + 1] = v; }
     }
 }
 
 /* Emit the unsorted (tile, depth_bits, id) triples of all binned Gaussians in
- * index order, tiles of one Gaussian row-major; returns the count written. */
-int64_t orc_emit_keys(int32_t n, const uint32_t *depth_key, const int32_t *rect, const uint32_t *tiles_touched,
-                      int32_t tiles_x, int64_t cap, uint32_t *tile_out, uint32_t *depth_out, uint32_t *id_out) {
+ * index order, tiles of one Gaussian row-major (the rectangle less the column
+ * cuts of orc_bin_f32); returns the count written. */
+int64_t orc_emit_keys(int32_t n, const uint32_t *depth_key, const int32_t *rect, const uint64_t *trims,
+                      const uint32_t *tiles_touched, int32_t tiles_x, int64_t cap, uint32_t *tile_out,
+                      uint32_t *depth_out, uint32_t *id_out) {
     int64_t k = 0;
     for (int32_t i = 0; i < n; i++) {
         if (!tiles_touched[i]) continue;
         for (int32_t ty = rect[4 * (size_t)i + 2]; ty <= rect[4 * (size_t)i + 3]; ty++)
             for (int32_t tx = rect[4 * (size_t)i + 0]; tx <= rect[4 * (size_t)i + 1]; tx++) {
+                const int32_t j = tx - rect[4 * (size_t)i + 0];
+                if (j < 8) {
+                    const uint32_t byte = (uint32_t)(trims[i] >> (8 * j)) & 0xFFu;
+                    if (ty < rect[4 * (size_t)i + 2] + (int32_t)(byte & 15u) ||
+                        ty > rect[4 * (size_t)i + 3] - (int32_t)(byte >> 4))
+                        continue;
+                }
                 if (k < cap) {
                     tile_out[k] = (uint32_t)(ty * tiles_x + tx);
                     depth_out[k] = depth_key[i];

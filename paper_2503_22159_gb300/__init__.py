@@ -114,10 +114,11 @@ def camera_struct(cam) -> _abi.d4dgs_camera:
     return c
 
 
-def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0)) -> _abi.d4dgs_config:
+def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0), trim: bool = False) -> _abi.d4dgs_config:
     g = _abi.d4dgs_config()
     g.tile, g.batch = int(tile), int(batch)
     g.bg[:] = [float(x) for x in bg]
+    g.trim = 1 if trim else 0
     return g
 
 
@@ -397,9 +398,9 @@ class BatchRenderer:
 
     @staticmethod
     def _class_key(host: torch.Tensor):
-        # nviews, tile, batch, packed, tile_passes, column capacity (leading int32 fields of the encoded batch)
-        head = host[:24].view(torch.int32).tolist()
-        return (head[1], head[2], head[3], head[4], head[5])
+        # nviews, tile, batch, packed, tile_passes, column capacity, trim (leading int32 fields of the encoded batch)
+        head = host[:28].view(torch.int32).tolist()
+        return (head[1], head[2], head[3], head[4], head[5], head[6])
 
 
 class Renderer:
@@ -407,9 +408,9 @@ class Renderer:
     capacity when a frame reports D4DGS_ERR_CAPACITY."""
 
     def __init__(self, n: int, cam, tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0),
-                 key_capacity: int | None = None, device="cuda"):
+                 key_capacity: int | None = None, device="cuda", trim: bool = False):
         self.n, self.device = int(n), torch.device(device)
-        self.cfg = config_struct(tile, batch, bg)
+        self.cfg = config_struct(tile, batch, bg, trim)
         self.width, self.height = int(cam.width), int(cam.height)
         self.cam0 = cam
         cap = key_capacity if key_capacity is not None else max(1 << 16, 16 * self.n)

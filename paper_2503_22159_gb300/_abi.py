@@ -48,7 +48,8 @@ class d4dgs_camera(ctypes.Structure):
 
 
 class d4dgs_config(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("bg", ctypes.c_float * 3)]
+    _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("bg", ctypes.c_float * 3),
+                ("trim", ctypes.c_int32)]
 
 
 class d4dgs_view(ctypes.Structure):
@@ -67,7 +68,7 @@ class d4dgs_layout(ctypes.Structure):
                                                "control", "key_capacity")] + [
         ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("depth_passes", ctypes.c_int32),
         ("tile_passes", ctypes.c_int32), ("id_bits", ctypes.c_int32), ("packed", ctypes.c_int32),
-        ("col_bits", ctypes.c_int32)]
+        ("col_bits", ctypes.c_int32), ("trims", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); the exported symbols of include/d4dgs.h

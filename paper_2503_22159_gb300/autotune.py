@@ -1,11 +1,12 @@
-"""Tile-size / blend-batch autotuner.
+"""Tile-size / blend-batch / column-cut autotuner.
 
 For a resolution and scene size it times whole frames (preprocess + binning +
-blend, CUDA events, after warm-up) for every tile size in {8, 16, 32} and
-blend staging depth in {64, 128, 256} on a few representative frames, keeps
-the fastest, and caches the choice per (GPU name, width, height, N bucket) in
-a JSON file.  The image does not depend on the choice: every pixel walks the
-same depth-ordered Gaussians with the same operations whatever the tiling.
+blend, CUDA events, after warm-up) for every tile size in {8, 16, 32}, blend
+staging depth in {64, 128, 256} and binning with or without the per-column
+cuts of the rectangles, on a few representative frames, keeps the fastest,
+and caches the choice per (GPU name, width, height, N bucket) in a JSON file.
+The image does not depend on the choice: every pixel walks the same
+depth-ordered Gaussians with the same operations whatever the tiling.
 """
 from __future__ import annotations
 
@@ -16,6 +17,7 @@ from pathlib import Path
 
 TILES = (8, 16, 32)
 BATCHES = (64, 128, 256)
+TRIMS = (False, True)
 
 
 def default_cache_path() -> Path:
@@ -46,40 +48,46 @@ class TuneCache:
 
     def get(self, key: str):
         e = self.data.get(key)
-        return (int(e["tile"]), int(e["batch"])) if e else None
+        return (int(e["tile"]), int(e["batch"]), bool(e.get("trim", False))) if e else None
 
-    def put(self, key: str, tile: int, batch: int, table: dict):
-        self.data[key] = {"tile": tile, "batch": batch, "ms": table}
+    def put(self, key: str, tile: int, batch: int, trim: bool, table: dict):
+        self.data[key] = {"tile": tile, "batch": batch, "trim": bool(trim), "ms": table}
         self.path.parent.mkdir(parents=True, exist_ok=True)
         tmp = self.path.with_suffix(f".{os.getpid()}.tmp")
         tmp.write_text(json.dumps(self.data, indent=1, sort_keys=True))
         os.replace(tmp, self.path)
 
 
-def sweep(time_config, tiles=TILES, batches=BATCHES):
-    """time_config(tile, batch) -> ms per frame, or None when the configuration cannot render
-    these frames; returns (best (tile, batch), {"tile/batch": ms or None})."""
-    table = {}
+def config_name(tile: int, batch: int, trim: bool) -> str:
+    return f"{tile}/{batch}" + ("/cut" if trim else "")
+
+
+def sweep(time_config, tiles=TILES, batches=BATCHES, trims=TRIMS):
+    """time_config(tile, batch, trim) -> ms per frame, or None when the configuration cannot
+    render these frames; returns (best (tile, batch, trim), {config_name: ms or None})."""
+    table, cfgs = {}, {}
     for t in tiles:
         for b in batches:
-            ms = time_config(t, b)
-            table[f"{t}/{b}"] = None if ms is None else float(ms)
+            for c in trims:
+                ms = time_config(t, b, c)
+                name = config_name(t, b, c)
+                table[name] = None if ms is None else float(ms)
+                cfgs[name] = (int(t), int(b), bool(c))
     feasible = {k: v for k, v in table.items() if v is not None}
     if not feasible:
         raise RuntimeError("no tile / batch configuration can render these frames")
-    best = min(feasible, key=feasible.get)
-    t, b = best.split("/")
-    return (int(t), int(b)), table
+    return cfgs[min(feasible, key=feasible.get)], table
 
 
-def time_frames(scene, frames, tile: int, batch: int, warmup: int = 2, reps: int = 1, device="cuda") -> float:
+def time_frames(scene, frames, tile: int, batch: int, trim: bool = False, warmup: int = 2, reps: int = 1,
+                device="cuda") -> float:
     """Mean ms per frame of d4dgs_render for one (tile, batch) over `frames` [(camera, t)];
     None when a frame has more (tile, Gaussian) pairs than a workspace can hold at this tile size."""
     import torch
 
     from . import D4DGS_ERR_CAPACITY, D4DGSError, Renderer, d4dgs_render
     cam0 = frames[0][0]
-    r = Renderer(scene.n, cam0, tile=tile, batch=batch, device=device)
+    r = Renderer(scene.n, cam0, tile=tile, batch=batch, device=device, trim=trim)
     try:
         for cam, t in frames:                  # size the workspace for these frames
             r.render(scene, cam, t)
@@ -103,7 +111,7 @@ def time_frames(scene, frames, tile: int, batch: int, warmup: int = 2, reps: int
 
 
 def tune(scene, frames, cache: TuneCache | None = None, device="cuda", force: bool = False):
-    """Best (tile, batch) for this scene size and the frames' resolution (cached)."""
+    """Best (tile, batch, trim) for this scene size and the frames' resolution (cached)."""
     import torch
     cam = frames[0][0]
     gpu = torch.cuda.get_device_name(device)
@@ -112,6 +120,6 @@ def tune(scene, frames, cache: TuneCache | None = None, device="cuda", force: bo
     hit = cache.get(key)
     if hit and not force:
         return hit, None
-    best, table = sweep(lambda t, b: time_frames(scene, frames, t, b, device=device))
-    cache.put(key, best[0], best[1], table)
+    best, table = sweep(lambda t, b, c: time_frames(scene, frames, t, b, c, device=device))
+    cache.put(key, best[0], best[1], best[2], table)
     return best, table

@@ -33,6 +33,7 @@ bool valid_config(const d4dgs_config *g) {
     if (!g) return false;
     if (g->tile != 8 && g->tile != 16 && g->tile != 32) return false;
     if (g->batch != 64 && g->batch != 128 && g->batch != 256) return false;
+    if (g->trim != 0 && g->trim != 1) return false;
     for (int i = 0; i < 3; i++)
         if (!isfinite(g->bg[i])) return false;
     return true;
@@ -108,6 +109,7 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     }
     l.id_bits = ceil_log2(n > 1 ? n : 2);
     l.packed = (l.id_bits + l.tile_bits) <= 32;
+    l.trim_on = cfg->trim;
     l.cap = cap;
     l.parts_depth = n > 0 ? ((int64_t)n + kDepthItems - 1) / kDepthItems : 1;
     l.parts_dup = n > 0 ? ((int64_t)n + kDupItems - 1) / kDupItems : 1;
@@ -127,6 +129,7 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     for (int b = 0; b < 2; b++) { l.depth_vals[b] = off; off += align256((int64_t)n * 4); }
     l.tiles_touched = off; off += align256((int64_t)n * 4);
     l.rect = off; off += align256((int64_t)n * 8);
+    l.trim = off; off += align256((int64_t)n * 8);
     l.final_T = off; off += align256(l.pixels * 4);
     l.n_contrib = off; off += align256(l.pixels * 4);
     l.grad2d = off; off += align256((int64_t)n * 48);
@@ -177,6 +180,7 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     }
     x.tiles_touched = at<uint32_t>(ws, L.tiles_touched);
     x.rect = at<ushort4>(ws, L.rect);
+    x.trim = at<unsigned long long>(ws, L.trim);
     x.ranges = at<uint2>(ws, L.ranges);
     x.final_T = at<float>(ws, L.final_T);
     x.n_contrib = at<uint32_t>(ws, L.n_contrib);
@@ -191,6 +195,7 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     x.col_bits = L.col_bits;
     x.packed = L.packed ? 1 : 0;
     x.tile_passes = L.tile_passes;
+    x.trim_on = L.trim_on;
     x.ntiles = L.ntiles;
     for (int p = 0; p < 3; p++) {
         x.tile_shift[p] = L.tile_shift[p];
@@ -219,10 +224,11 @@ bool finish_batch(BatchArgs *b) {
     b->col_cap = 32;
     b->packed = b->v[0].packed;
     b->tile_passes = b->v[0].tile_passes;
+    b->trim_on = b->v[0].trim_on;
     int lead = -1;
     for (int i = 0; i < b->nviews; i++) {
         View &v = b->v[i];
-        if (v.packed != b->packed || v.tile_passes != b->tile_passes || v.cam.tile != b->tile ||
+        if (v.packed != b->packed || v.tile_passes != b->tile_passes || v.cam.tile != b->tile || v.trim_on != b->trim_on ||
             v.kind != b->v[0].kind)
             return false;
         // time groups: a view joins the group of the view before it when it shares its scene and camera
@@ -274,6 +280,7 @@ int d4dgs_workspace_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_confi
     out->depth_keys = L.depth_keys[0];
     out->tiles_touched = L.tiles_touched;
     out->rect = L.rect;
+    out->trims = L.trim;
     out->depth_order = L.depth_vals[L.depth_passes & 1];
     out->tile_keys = L.tile_keys[L.final_buf()];
     out->tile_vals = L.packed ? -1 : L.tile_vals[L.final_buf()];

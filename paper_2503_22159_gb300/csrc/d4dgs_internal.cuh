@@ -60,12 +60,14 @@ struct Layout {
     // fit, else kept as a tile key plus a separate Gaussian-id value
     int32_t id_bits = 0;
     bool packed = true;
+    int32_t trim_on = 0;   // config trim: 1 rectangles cut per column (tile_trim.cuh), 0 whole
     int64_t cap = 0;
     int64_t parts_depth = 0, parts_dup = 0, parts_tile = 0;
     // zero-initialised region [0, zero_end)
     int64_t control = 0, grid = 0, lb_depth = 0, lb_col = 0, lb_tile = 0, zero_end = 0;
     // the rest
     int64_t colbase = 0, ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
+    int64_t trim = 0;   // per-Gaussian column trims of the rectangle (tile_trim.cuh)
     int64_t final_T = 0, n_contrib = 0, grad2d = 0, flow2d = 0, batch = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
     int64_t total = 0;
     int32_t grid_w() const { return tiles_x + 1; }
@@ -114,6 +116,7 @@ struct View {
     float4 *rec;
     uint32_t *dkeys[2], *dvals[2], *tiles_touched;
     ushort4 *rect;
+    unsigned long long *trim;        // column trims of each rectangle (tile_trim.cuh)
     uint2 *ranges;
     float *final_T;
     uint32_t *n_contrib;
@@ -125,6 +128,7 @@ struct View {
     uint32_t *colbase;               // first position of each tile column's bucket (clamped to cap)
     uint32_t cap;
     int32_t id_bits, col_bits, packed, tile_passes, ntiles;
+    int32_t trim_on;                 // config trim: 1 rectangles cut per column
     int32_t tile_shift[3];
     uint32_t tile_mask[3];
     int32_t parts_depth, parts_dup, parts_tile;
@@ -142,6 +146,7 @@ struct BatchArgs {
     int32_t nviews;
     int32_t tile, batch, packed, tile_passes;   // shared by every view of a launch
     int32_t col_cap;                            // power of two >= every view's tile columns
+    int32_t trim_on;                            // config trim, shared by every view of a launch
     int32_t total_chunks, total_depth_parts, total_dup_parts, total_tiles;
     int32_t max_n;
     View v[kMaxViews];

@@ -20,6 +20,7 @@
 // for bit; only exp() of the scales and of the opacity terms may differ by an
 // ulp between math libraries.
 #include "d4dgs_internal.cuh"
+#include "tile_trim.cuh"
 
 namespace d4dgs {
 
@@ -252,9 +253,11 @@ __device__ __forceinline__ bool footprint_slicing(const View &vw, int i, Footpri
     return true;
 }
 
-// One Gaussian of view v: writes its 2D record, depth key, tile count and
-// rectangle, adds its rectangle to the view's difference grid, and counts it in
-// the shared depth-digit histogram.
+// One Gaussian of view v: writes its 2D record, depth key, tile count,
+// rectangle and (config trim) column cuts, adds its tiles to the view's
+// difference grid (2D differences of the rectangle, or per-column
+// differences of the cut columns), and counts it in the shared depth-digit
+// histogram.
 template <int DEG, int KIND>
 __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *hist, uint32_t &nvis, int *sgrid) {
     constexpr int K = (DEG + 1) * (DEG + 1);
@@ -263,6 +266,7 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
     {
         uint32_t key = 0xFFFFFFFFu, tiles = 0;
         ushort4 rc = make_ushort4(0, 0, 0, 0);
+        uint64_t tw = 0;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         float flu = 0.0f, flv = 0.0f;
         do {
@@ -284,22 +288,42 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
             // which alpha = o_hat e^p < 1/255; half-extents k sqrt(Sigma'_00), k sqrt(Sigma'_11)
             if (!(isfinite(u) && isfinite(v))) break;
             const float k2 = add(mul(mul(2.0f, logf(mul(255.0f, oh))), kK2Scale), kK2Pad);
-            const float rx = ceilf(__fsqrt_rn(mul(k2, s00))), ry = ceilf(__fsqrt_rn(mul(k2, s11)));
+            const float ex = __fsqrt_rn(mul(k2, s00)), ey = __fsqrt_rn(mul(k2, s11));
+            const float rx = ceilf(ex), ry = ceilf(ey);
             const float fx0 = floorf(dvd(sub(u, rx), tilef)), fx1 = floorf(dvd(add(u, rx), tilef));
             const float fy0 = floorf(dvd(sub(v, ry), tilef)), fy1 = floorf(dvd(add(v, ry), tilef));
             if (!(fx1 >= 0.0f) || !(fx0 <= (float)(c.tiles_x - 1))) break;
             if (!(fy1 >= 0.0f) || !(fy0 <= (float)(c.tiles_y - 1))) break;
             const int x0 = (int)fmaxf(fx0, 0.0f), x1 = (int)fminf(fx1, (float)(c.tiles_x - 1));
             const int y0 = (int)fmaxf(fy0, 0.0f), y1 = (int)fminf(fy1, (float)(c.tiles_y - 1));
-            rc = make_ushort4((unsigned short)x0, (unsigned short)x1, (unsigned short)y0, (unsigned short)y1);
-            tiles = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-            // per-tile pair counts as a 2D difference grid ((tiles_x+1) x (tiles_y+1))
             const int gw = c.tiles_x + 1;
             int *g = sgrid ? sgrid : vw.grid;   // shared-memory copy when the grid is small
-            atomicAdd(g + y0 * gw + x0, 1);
-            atomicAdd(g + y0 * gw + x1 + 1, -1);
-            atomicAdd(g + (y1 + 1) * gw + x0, -1);
-            atomicAdd(g + (y1 + 1) * gw + x1 + 1, 1);
+            if (vw.trim_on) {
+                // ---- the rectangle's leading columns cut to the rows the ellipse reaches
+                tw = tile_trims(u, v, s00, s01, s11, det, k2, ex, ey, x0, x1, y0, y1, tilef, (float)c.width);
+                const int h = y1 - y0 + 1;
+                for (int j = 0; j <= x1 - x0; j++) tiles += (uint32_t)trim_count(tw, j, h);
+                if (tiles == 0) {   // no pixel centre within reach: culled
+                    tw = 0;
+                    break;
+                }
+                // per-tile pair counts as per-column differences on the ((tiles_x+1) x (tiles_y+1))
+                // grid: +1 at a column's first kept row, -1 below its last
+                for (int j = 0; j <= x1 - x0; j++) {
+                    const int ra = y0 + trim_top(tw, j), rb = y1 - trim_bot(tw, j);
+                    if (ra > rb) continue;
+                    atomicAdd(g + ra * gw + x0 + j, 1);
+                    atomicAdd(g + (rb + 1) * gw + x0 + j, -1);
+                }
+            } else {
+                // whole rectangle: per-tile pair counts as a 2D difference grid
+                tiles = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+                atomicAdd(g + y0 * gw + x0, 1);
+                atomicAdd(g + y0 * gw + x1 + 1, -1);
+                atomicAdd(g + (y1 + 1) * gw + x0, -1);
+                atomicAdd(g + (y1 + 1) * gw + x1 + 1, 1);
+            }
+            rc = make_ushort4((unsigned short)x0, (unsigned short)x1, (unsigned short)y0, (unsigned short)y1);
             key = __float_as_uint(Z);
             nvis++;
             // ---- conic (rendering only; ordinary arithmetic from here on)
@@ -346,6 +370,7 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
         vw.dkeys[0][i] = key;
         vw.tiles_touched[i] = tiles;
         vw.rect[i] = rc;
+        vw.trim[i] = tw;
 #pragma unroll
         for (int p = 0; p < 4; p++) atomicAdd(&hist[p * kRadix + ((key >> (8 * p)) & 0xFFu)], 1u);
     }

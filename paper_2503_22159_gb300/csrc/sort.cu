@@ -30,6 +30,7 @@
 // and the pass completes without hanging), and scatter through shared memory
 // so that global writes are runs of consecutive addresses.
 #include "d4dgs_internal.cuh"
+#include "tile_trim.cuh"
 
 namespace d4dgs {
 
@@ -275,9 +276,11 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
     }
 }
 
-// Per-tile pair counts from the view's 2D difference grid; ranges; the first
-// position of every tile column's bucket; digit histograms of the row passes;
-// the total K and the capacity check.  One CTA per view.
+// Per-tile pair counts from the view's difference grid (2D differences of the
+// rectangles, or, config trim, per-column differences: +1 at a column's first
+// kept row, -1 below its last); ranges; the first position
+// of every tile column's bucket; digit histograms of the row passes; the
+// total K and the capacity check.  One CTA per view.
 __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, int smem_cells) {
     __shared__ unsigned long long s_warp[32];
     __shared__ uint32_t s_hist[3 * kRadix];
@@ -305,11 +308,13 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     const int gw = tiles_x + 1, gh = tiles_y + 1;
     for (int i = tid; i < 3 * kRadix; i += nt) s_hist[i] = 0;
-    for (int r = tid; r < gh; r += nt) {          // integrate along x
-        int acc = 0;
-        for (int x = 0; x < gw; x++) { acc += grid[r * gw + x]; grid[r * gw + x] = acc; }
+    if (!v.trim_on) {                                // 2D differences: integrate along x first
+        for (int r = tid; r < gh; r += nt) {
+            int acc = 0;
+            for (int x = 0; x < gw; x++) { acc += grid[r * gw + x]; grid[r * gw + x] = acc; }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int c = tid; c < gw; c += nt) {          // then along y
         int acc = 0;
         for (int y = 0; y < gh; y++) { acc += grid[y * gw + c]; grid[y * gw + c] = acc; }
@@ -384,23 +389,28 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
 // Pair emission in depth order straight into per-tile-column buckets (pass 0
 // of the tile sort), over 256-Gaussian partitions of every view of the launch:
 //   1. per warp (32 consecutive Gaussians of the depth order) and tile column,
-//      the pairs the warp's Gaussians put in that column;
+//      the pairs the warp's Gaussians put in that column (the rectangle's
+//      rows less the column's trims);
 //   2. per column: exclusive prefix over the warps, the partition's total, and
 //      the partition's offset within the column's bucket by decoupled
 //      look-back over the preceding partitions;
 //   3. each warp writes its Gaussians' pairs in order: the pairs of Gaussian g
 //      in column c go to colbase[c] + (pairs of c from earlier partitions,
-//      warps and Gaussians) + (row - y0), so each column bucket holds its
+//      warps and Gaussians) + (row - first kept row of the column), so each
+//      column bucket holds its
 //      pairs in (depth, id) order and, within one Gaussian, by row; a
 //      Gaussian's pairs of one column are consecutive positions written by
 //      consecutive lanes.
 // The stable row passes that follow leave every tile's list in (depth, id)
 // order.
+// TRIM: the launch's views cut their rectangles per column (config trim).
+template <bool TRIM>
 __global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__ ba, int col_cap) {
     static_assert(kDupThreads == 256 && kDupItems == 256, "8 warps of 32 Gaussians per partition");
     extern __shared__ uint32_t s_dyn[];   // [8][col_cap] per-warp column counts, then [col_cap] bases
     __shared__ uint32_t s_id[kDupItems];
     __shared__ ushort4 s_rect[kDupItems];
+    __shared__ unsigned long long s_trim[TRIM ? kDupItems : 1];
     __shared__ uint32_t s_part;
     grid_dependency_wait();
     uint32_t *s_base = s_dyn + 8 * col_cap;
@@ -431,10 +441,14 @@ __global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__
         const uint32_t pos = part * kDupItems + tid;
         uint32_t id = 0;
         ushort4 r = make_ushort4(1, 0, 0, 0);   // empty: x0 > x1
+        unsigned long long tw = 0;
         if (pos < n) {
             id = order[pos];
             if (id < n) {   // always true unless an earlier pass gave up on a spin-wait
-                if (v.tiles_touched[id]) r = v.rect[id];
+                if (v.tiles_touched[id]) {
+                    r = v.rect[id];
+                    if (TRIM) tw = v.trim[id];
+                }
             } else {
                 id = 0;
             }
@@ -444,13 +458,17 @@ __global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__
         r.w = (unsigned short)min((int)r.w, v.cam.tiles_y - 1);
         s_id[tid] = id;
         s_rect[tid] = r;
+        if (TRIM) s_trim[TRIM ? tid : 0] = tw;
         for (int w = 0; w < 8; w++)
             for (int c = tid; c < ncols; c += kDupThreads) s_dyn[w * col_cap + c] = 0u;
         __syncthreads();
-        // ---- 1. per-warp column counts
+        // ---- 1. per-warp column counts (the rectangle's rows less the column's trims)
         if (r.x <= r.y) {
-            const uint32_t h = (uint32_t)r.w - (uint32_t)r.z + 1u;
-            for (int c = r.x; c <= r.y; c++) atomicAdd(&s_dyn[warp * col_cap + c], h);
+            const int h = (int)r.w - (int)r.z + 1;
+            for (int c = r.x; c <= r.y; c++) {
+                const int k = TRIM ? trim_count(tw, c - (int)r.x, h) : h;
+                if (k) atomicAdd(&s_dyn[warp * col_cap + c], (uint32_t)k);
+            }
         }
         __syncthreads();
         // ---- 2. warp prefixes, partition totals, look-back per column
@@ -482,6 +500,7 @@ __global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__
             const ushort4 rq = s_rect[q];
             if (rq.x > rq.y) continue;
             const uint32_t gid = s_id[q];
+            const unsigned long long tq = TRIM ? s_trim[TRIM ? q : 0] : 0ull;
             const int wdt = (int)rq.y - (int)rq.x + 1, hgt = (int)rq.w - (int)rq.z + 1;
             const int cnt = wdt * hgt;
             const float inv_h = 1.0f / (float)hgt;
@@ -489,8 +508,10 @@ __global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__
                 int cc = __float2int_rz((float)j * inv_h);
                 int rr = j - cc * hgt;
                 if (rr < 0) { cc--; rr += hgt; } else if (rr >= hgt) { cc++; rr -= hgt; }
+                const int top = TRIM ? trim_top(tq, cc) : 0;
+                if (TRIM && (rr < top || rr >= hgt - trim_bot(tq, cc))) continue;   // cut away
                 const int c = (int)rq.x + cc;
-                const uint32_t o = s_base[c] + wcnt[c] + (uint32_t)rr;
+                const uint32_t o = s_base[c] + wcnt[c] + (uint32_t)(rr - top);
                 if (o < cap) {
                     const uint32_t tk = ((uint32_t)((int)rq.z + rr) << col_bits) | (uint32_t)c;
                     if (packed) {
@@ -502,7 +523,8 @@ __global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__
                 }
             }
             __syncwarp();
-            for (int c = (int)rq.x + lane; c <= (int)rq.y; c += 32) wcnt[c] += (uint32_t)hgt;
+            for (int c = (int)rq.x + lane; c <= (int)rq.y; c += 32)
+                wcnt[c] += (uint32_t)(TRIM ? trim_count(tq, c - (int)rq.x, hgt) : hgt);
             __syncwarp();
         }
         __syncthreads();
@@ -528,13 +550,14 @@ int sort_launch_count(int n, int tile_passes) { return n == 0 ? 1 : 1 + 4 + 1 + 
 
 cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
     static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0;
-    static int occ_emit[16] = {0};   // by log2 of the column capacity
+    static int occ_emit[2][16] = {};   // by trim and log2 of the column capacity
     if (!occ_kv) {
         occ_iota = occupancy_blocks((const void *)onesweep_kernel<true, true, false>, kSortThreads);
         occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false, false>, kSortThreads);
         occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false, true>, kSortThreads);
         occ_tkv = occupancy_blocks((const void *)onesweep_kernel<true, false, true>, kSortThreads);
-        cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
+        cudaFuncSetAttribute(emit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
+        cudaFuncSetAttribute(emit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
     }
     // ---- 0. per-tile counts, ranges, tile digit histograms (always: ranges are written for every tile)
     // fixed grid (blocks beyond the table's view count return at once), so that a
@@ -561,9 +584,13 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
     int lc = 0;
     while ((1 << lc) < args.col_cap) lc++;
     if (args.col_cap > kMaxCols || lc >= 16) return cudaErrorInvalidValue;
-    if (!occ_emit[lc]) occ_emit[lc] = occupancy_blocks((const void *)emit_kernel, kDupThreads, emit_smem(args.col_cap));
-    e = launch_chained(emit_kernel, occ_emit[lc] * num_sms, kDupThreads, emit_smem(args.col_cap), st, batch_area,
-                       (int)args.col_cap);
+    const int ti = args.trim_on ? 1 : 0;
+    const void *emit_fn = args.trim_on ? (const void *)emit_kernel<true> : (const void *)emit_kernel<false>;
+    if (!occ_emit[ti][lc]) occ_emit[ti][lc] = occupancy_blocks(emit_fn, kDupThreads, emit_smem(args.col_cap));
+    e = args.trim_on ? launch_chained(emit_kernel<true>, occ_emit[ti][lc] * num_sms, kDupThreads, emit_smem(args.col_cap), st,
+                                   batch_area, (int)args.col_cap)
+                  : launch_chained(emit_kernel<false>, occ_emit[ti][lc] * num_sms, kDupThreads, emit_smem(args.col_cap), st,
+                                   batch_area, (int)args.col_cap);
     // ---- 3. stable sort of the pairs by tile-row bits (tile passes 1..)
     for (int p = 1; p < args.tile_passes && e == cudaSuccess; p++) {
         if (args.packed)

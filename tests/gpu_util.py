@@ -18,10 +18,10 @@ def d4():
     return m
 
 
-def render(scene, cam, t, tile=16, batch=256, bg=(0.0, 0.0, 0.0), cap=None):
+def render(scene, cam, t, tile=16, batch=256, bg=(0.0, 0.0, 0.0), cap=None, trim=False):
     m = d4()
     ds = m.DeviceScene.from_host(scene)
-    r = m.Renderer(scene.n, cam, tile=tile, batch=batch, bg=bg, key_capacity=cap)
+    r = m.Renderer(scene.n, cam, tile=tile, batch=batch, bg=bg, key_capacity=cap, trim=trim)
     img = r.render(ds, cam, t)
     torch.cuda.synchronize()
     return r, ds, img
@@ -55,15 +55,15 @@ def gpu_lists(r, cam):
     return dict(tile=tiles, id=ids, ranges=ranges, stats=st, packed=bool(L["packed"]))
 
 
-def expected_lists(scene, cam, t, tile):
-    b = oracle.bin_f32(scene, cam, t, tile)
+def expected_lists(scene, cam, t, tile, trim=False):
+    b = oracle.bin_f32(scene, cam, t, tile, trim=trim)
     return b, oracle.tile_list(b)
 
 
 def compare_lists(got, b, exp):
     """Bit-exact (tile, id) sequence after removing the Gaussians the mirror
     flags (decisions through expf within 3e-6 of a threshold)."""
-    flagged = np.nonzero(b["flags"] & 3)[0]   # rectangle or cull decided near a threshold
+    flagged = np.nonzero(b["flags"] & 11)[0]   # rectangle, cull or column cut decided near a threshold
     keep_g = ~np.isin(got["id"], flagged)
     keep_e = ~np.isin(exp["id"], flagged)
     gt, gi = got["tile"][keep_g], got["id"][keep_g]

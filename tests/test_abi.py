@@ -58,7 +58,7 @@ def test_workspace_bytes_monotone_and_layout(d4):
     assert (L["tiles_x"], L["tiles_y"]) == (85, 64)
     assert L["tile_passes"] == 2 and L["depth_passes"] == 4
     assert L["id_bits"] == 19 and L["packed"] == 1 and L["tile_vals"] == -1
-    offs = [L[k] for k in ("records", "depth_keys", "tiles_touched", "rect", "depth_order", "tile_keys",
+    offs = [L[k] for k in ("records", "depth_keys", "tiles_touched", "rect", "trims", "depth_order", "tile_keys",
                            "ranges", "final_T", "n_contrib", "control")]
     assert all(o % 256 == 0 for o in offs)
     assert max(offs) < b1

@@ -18,24 +18,24 @@ def at(tmp_path, monkeypatch):
 
 
 def test_sweep_picks_fastest_and_cache_roundtrip(at, tmp_path):
-    fake = {(8, 64): 3.0, (16, 128): 1.5, (32, 256): 2.0}
-    best, table = at.sweep(lambda t, b: fake.get((t, b), 9.0))
-    assert best == (16, 128) and len(table) == 9
+    fake = {(8, 64, False): 3.0, (16, 128, True): 1.5, (32, 256, False): 2.0}
+    best, table = at.sweep(lambda t, b, c: fake.get((t, b, c), 9.0))
+    assert best == (16, 128, True) and len(table) == 18 and table["16/128/cut"] == 1.5
     key = at.cache_key("GB300", 1352, 1014, 300_000)
     assert key == "GB300|1352x1014|n<=524288"
     c = at.TuneCache()
     c.put(key, *best, table)
-    assert at.TuneCache().get(key) == (16, 128)
+    assert at.TuneCache().get(key) == (16, 128, True)
     assert at.TuneCache().get(at.cache_key("GB300", 1352, 1014, 600_000)) is None   # other N bucket
 
 
 def test_sweep_skips_configurations_that_cannot_render(at):
     """A tile size whose frames need more pairs than a workspace can hold is reported as None."""
-    best, table = at.sweep(lambda t, b: None if t == 8 else float(t + b / 1000))
-    assert best == (16, 64)
-    assert all(table[f"8/{b}"] is None for b in at.BATCHES)
+    best, table = at.sweep(lambda t, b, c: None if t == 8 else float(t + b / 1000 + c))
+    assert best == (16, 64, False)
+    assert all(table[at.config_name(8, b, c)] is None for b in at.BATCHES for c in at.TRIMS)
     with pytest.raises(RuntimeError):
-        at.sweep(lambda t, b: None)
+        at.sweep(lambda t, b, c: None)
 
 
 @pytest.mark.gpu
@@ -44,10 +44,10 @@ def test_gpu_sweep_choice_renders_identically(at):
     sc = synth.make_scene(20_000, 61, "box20", sh_degree=1)
     frames = synth.orbit(3, 320, 240, 300)[100:103]
     ds = d4.DeviceScene.from_host(sc)
-    (tile, batch), table = at.tune(ds, frames, force=True)
-    assert tile in at.TILES and batch in at.BATCHES and len(table) == 9
+    (tile, batch, trim), table = at.tune(ds, frames, force=True)
+    assert tile in at.TILES and batch in at.BATCHES and len(table) == 18
     assert at.tune(ds, frames)[1] is None   # cached
     cam, t = frames[0]
     ref = d4.Renderer(sc.n, cam, tile=16, batch=256).render(ds, cam, t).clone()
-    img = d4.Renderer(sc.n, cam, tile=tile, batch=batch).render(ds, cam, t)
+    img = d4.Renderer(sc.n, cam, tile=tile, batch=batch, trim=trim).render(ds, cam, t)
     assert torch.equal(img, ref)

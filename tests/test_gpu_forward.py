@@ -28,12 +28,13 @@ def medium(n=20_000, w=333, h=257, seed=5, deg=1, frame=40):
 # stage parity
 # ---------------------------------------------------------------------------
 
-def test_preprocess_matches_oracle():
+@pytest.mark.parametrize("trim", [False, True])
+def test_preprocess_matches_oracle(trim):
     w = synth.tiny_workload()
     cam, t = w.frames[0]
     m = gu.d4()
     ds = m.DeviceScene.from_host(w.scene)
-    r = m.Renderer(w.scene.n, cam)
+    r = m.Renderer(w.scene.n, cam, trim=trim)
     m.d4dgs_preprocess(ds, cam, t, r.cfg, r.ws)
     torch.cuda.synchronize()
     rec = gu.gpu_records(r, w.scene.n, cam)
@@ -41,14 +42,17 @@ def test_preprocess_matches_oracle():
     keys = r.view("depth_keys", torch.int32, w.scene.n, cam).cpu().numpy().view(np.uint32)
     tt = r.view("tiles_touched", torch.int32, w.scene.n, cam).cpu().numpy()
     rect = r.view("rect", torch.int16, 4 * w.scene.n, cam).cpu().numpy().view(np.uint16).reshape(-1, 4)
-    b = oracle.bin_f32(w.scene, cam, t, 16)
+    trims = r.view("trims", torch.int64, w.scene.n, cam).cpu().numpy().view(np.uint64)
+    b = oracle.bin_f32(w.scene, cam, t, 16, trim=trim)
     g = oracle.preprocess(w.scene, cam, t)
-    flag = (b["flags"] & 3) != 0
+    flag = (b["flags"] & 11) != 0
     # integer / bit outputs: exact against the FP32 mirror
     assert np.array_equal(keys[~flag], b["depth_key"][~flag])
     assert np.array_equal(tt[~flag], b["tiles_touched"][~flag].astype(np.int32))
     vis = (b["tiles_touched"] > 0) & ~flag
     assert np.array_equal(rect[vis].astype(np.int32), b["rect"][vis])
+    assert np.array_equal(trims[vis], b["trims"][vis])
+    assert np.any(trims[vis] != 0) == trim
     rvis = vis & ((b["flags"] & 4) == 0)
     assert np.array_equal(rec[rvis, 7].astype(np.int32), b["radius"][rvis])
     # float outputs: against FP64
@@ -62,28 +66,32 @@ def test_preprocess_matches_oracle():
     assert L["key_capacity"] > 0
 
 
+@pytest.mark.parametrize("trim", [False, True])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_lists_bit_exact_tiny(tile):
+def test_lists_bit_exact_tiny(tile, trim):
     w = synth.tiny_workload()
     cam, t = w.frames[0]
-    r, _, _ = gu.render(w.scene, cam, t, tile=tile, batch=64)
+    r, _, _ = gu.render(w.scene, cam, t, tile=tile, batch=64, trim=trim)
     got = gu.gpu_lists(r, cam)
-    b, exp = gu.expected_lists(w.scene, cam, t, tile)
+    b, exp = gu.expected_lists(w.scene, cam, t, tile, trim=trim)
     assert got["stats"]["status"] == 0
     assert got["stats"]["n_keys"] == len(exp["tile"])
     nflag = gu.compare_lists(got, b, exp)
     assert nflag == 0
 
 
+@pytest.mark.parametrize("trim", [False, True])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_lists_bit_exact_medium_ragged(tile):
+def test_lists_bit_exact_medium_ragged(tile, trim):
     scene, cam, t = medium()
-    r, _, _ = gu.render(scene, cam, t, tile=tile, batch=128)
+    r, _, _ = gu.render(scene, cam, t, tile=tile, batch=128, trim=trim)
     got = gu.gpu_lists(r, cam)
-    b, exp = gu.expected_lists(scene, cam, t, tile)
+    b, exp = gu.expected_lists(scene, cam, t, tile, trim=trim)
     assert len(exp["tile"]) > 10 * 3840, "the case should span many sort partitions"
     nflag = gu.compare_lists(got, b, exp)
-    assert nflag <= 5
+    # Gaussians whose rectangle, cull or column-cut decision lies within the reach of an ulp
+    # difference in expf / logf are left out of the bit-exact comparison: a handful in 20,000
+    assert nflag <= 20
 
 
 def test_lists_bit_exact_unpacked_pairs():
@@ -120,6 +128,18 @@ def test_image_parity_medium_sampled():
     got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
     gu.compare_image(got, ref, "medium")
     gu.compare_T(gu.gpu_final_T(r, cam)[pix[:, 1], pix[:, 0]], ref, "medium")
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_image_identical_with_and_without_column_cuts(tile):
+    """The cuts drop only tiles where no pixel passes the alpha test: the image, the final
+    transmittance and the blend's visits are the same bits, with fewer pairs."""
+    scene, cam, t = medium(n=5000, w=200, h=150)
+    r0, _, base = gu.render(scene, cam, t, tile=tile)
+    r1, _, img = gu.render(scene, cam, t, tile=tile, trim=True)
+    assert torch.equal(base, img)
+    assert np.array_equal(gu.gpu_final_T(r0, cam), gu.gpu_final_T(r1, cam))
+    assert r1.stats(cam)["n_keys"] < r0.stats(cam)["n_keys"]
 
 
 @pytest.mark.parametrize("tile,batch", [(8, 64), (8, 256), (16, 64), (16, 128), (32, 128), (32, 256)])

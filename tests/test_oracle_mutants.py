@@ -56,6 +56,12 @@ MUTANTS = [
      "float ex = sqrtf(k2 * s11), ey = sqrtf(k2 * s00);", ["test_tile_rect_covers_alpha_support"]),
     ("FP32 rect with truncation", "float fx0 = floorf((u - rx) / tilef)", "float fx0 = floorf((u - rx) / tilef) + 1.0f",
      ["test_tile_rect_covers_alpha_support"]),
+    ("column cuts on the wrong branch", "((v + ((s01 * xt) - sqrtf(", "((v + ((s01 * xt) + sqrtf(",
+     ["test_column_trims_match_fp64_box_test", "test_tile_rect_covers_alpha_support"]),
+    ("column cuts at the bottom point's abscissa", "const float xt = fminf(fmaxf(-xl, a), b)",
+     "const float xt = fminf(fmaxf(xl, a), b)", ["test_column_trims_match_fp64_box_test"]),
+    ("column cuts counted from the rectangle's last row", "cut_t = (int32_t)fminf(fmaxf(ceilf(flo) - (float)y0",
+     "cut_t = (int32_t)fminf(fmaxf(ceilf(flo) - (float)(y0 + 1)", ["test_column_trims_match_fp64_box_test"]),
     # adjoint (caught by the finite-difference pin)
     ("adjoint: colour behind ignored", "dalpha += Ti * G[ch] * (c[ch] - B[ch]);", "dalpha += Ti * G[ch] * c[ch];",
      ["test_adjoint_matches_central_differences"]),
@@ -69,6 +75,9 @@ MUTANTS = [
 
 ARGSETS = {
     "test_single_gaussian_on_axis_closed_form": [dict(rotated=False), dict(rotated=True)],
+    "test_column_trims_match_fp64_box_test": [dict(tile=16, frame=0), dict(tile=32, frame=150)],
+    "test_tile_rect_covers_alpha_support": [dict(trim=True)],
+    "test_bin_f32_agrees_with_fp64": [dict(trim=False), dict(trim=True)],
     "test_adjoint_matches_central_differences": [dict(deg=0), dict(deg=3)],
 }
 

@@ -374,10 +374,11 @@ def test_transmittance_monotone_in_added_layers():
 # FP32 binning mirror
 # ---------------------------------------------------------------------------
 
-def test_bin_f32_agrees_with_fp64():
+@pytest.mark.parametrize("trim", [False, True])
+def test_bin_f32_agrees_with_fp64(trim):
     w = synth.tiny_workload()
     cam, t = w.frames[0]
-    b = oracle.bin_f32(w.scene, cam, t, 16)
+    b = oracle.bin_f32(w.scene, cam, t, 16, trim=trim)
     g = oracle.preprocess(w.scene, cam, t)
     ok = b["tiles_touched"] > 0
     assert ok.sum() > 900
@@ -390,15 +391,88 @@ def test_bin_f32_agrees_with_fp64():
     unflagged = (b["flags"][ok] & 4) == 0
     assert np.array_equal(b["radius"][ok][unflagged], r64[unflagged].astype(np.int32))
     rect = b["rect"][ok]
-    assert np.array_equal(b["tiles_touched"][ok], ((rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)))
+    area = (rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)
+    kept = np.array([kept_tiles(b, i).sum() for i in np.nonzero(ok)[0]])
+    assert np.array_equal(b["tiles_touched"][ok], kept)
+    if trim:
+        assert np.all(kept <= area) and kept.sum() < area.sum()
+    else:
+        assert np.array_equal(kept, area) and not b["trims"].any()
 
 
-def test_tile_rect_covers_alpha_support():
-    """Every pixel where a Gaussian's FP64 alpha reaches 1/255 lies in a tile of its FP32 rect."""
+def kept_tiles(b, i):
+    """Boolean (rows x columns) mask of the rectangle tiles Gaussian i keeps after its column cuts
+    (trims byte j: rows cut at the top of column x0 + j in the low nibble, at the bottom in the high)."""
+    x0, x1, y0, y1 = (int(z) for z in b["rect"][i])
+    h, w = y1 - y0 + 1, x1 - x0 + 1
+    m = np.ones((h, w), bool)
+    for j in range(min(w, 8)):
+        byte = (int(b["trims"][i]) >> (8 * j)) & 0xFF
+        top, bot = byte & 15, byte >> 4
+        m[:top, j] = False
+        m[h - bot:, j] = False
+    return m
+
+
+def box_min_quadratic(A00, A01, A11, xa, xb, ya, yb):
+    """min of A00 x^2 + 2 A01 x y + A11 y^2 (positive definite) over the box [xa, xb] x [ya, yb]:
+    0 if the origin is inside, else the least of the four edge minima (each a clamped 1D parabola)."""
+    best = np.inf
+    if xa <= 0.0 <= xb and ya <= 0.0 <= yb:
+        return 0.0
+    for x in (xa, xb):
+        y = min(max(-A01 * x / A11, ya), yb)
+        best = min(best, A00 * x * x + 2 * A01 * x * y + A11 * y * y)
+    for y in (ya, yb):
+        x = min(max(-A01 * y / A00, xa), xb)
+        best = min(best, A00 * x * x + 2 * A01 * x * y + A11 * y * y)
+    return best
+
+
+@pytest.mark.parametrize("tile,frame", [(16, 0), (32, 150)])
+def test_column_trims_match_fp64_box_test(tile, frame):
+    """The FP32 column cuts keep exactly the tiles whose pixel-centre box (rows widened by 1/64 px)
+    meets the binning ellipse d^T Sigma'^-1 d <= k2 (k2 = 2 ln(255 o_hat) 1.0008 + 0.0008), decided
+    here independently in FP64 by minimising the quadratic form over each box; tiles within 1e-4
+    relative of the ellipse, cuts saturated at 15 rows and flagged Gaussians are left out."""
+    scene = synth.make_scene(3000, 21, "box20", sh_degree=0)
+    cam, t = synth.orbit(4, 320, 240, 300)[frame]
+    b = oracle.bin_f32(scene, cam, t, tile, trim=True)
+    g = oracle.preprocess(scene, cam, t)
+    checked = cut = 0
+    for i in np.nonzero((b["tiles_touched"] > 0) & (b["flags"] == 0))[0]:
+        s00, s01, s11 = g["cov2d"][i]
+        det = s00 * s11 - s01 * s01
+        A00, A01, A11 = s11 / det, -s01 / det, s00 / det
+        k2 = 2.0 * np.log(255.0 * g["opacity_t"][i]) * 1.0008 + 0.0008
+        u, v = g["u"][i], g["v"][i]
+        x0, x1, y0, y1 = (int(z) for z in b["rect"][i])
+        m = kept_tiles(b, i)
+        for j in range(min(x1 - x0 + 1, 8)):
+            byte = (int(b["trims"][i]) >> (8 * j)) & 0xFF
+            if (byte & 15) == 15 or (byte >> 4) == 15:
+                continue
+            c = x0 + j
+            xa, xb = c * tile + 0.5 - u, min(c * tile + tile - 0.5, cam.width - 0.5) - u
+            for r in range(y0, y1 + 1):
+                ya, yb = r * tile + 0.5 - 1 / 64 - v, r * tile + tile - 0.5 + 1 / 64 - v
+                qmin = box_min_quadratic(A00, A01, A11, xa, xb, ya, yb)
+                if abs(qmin - k2) <= 1e-4 * k2:
+                    continue
+                assert m[r - y0, j] == (qmin <= k2), (i, r, c, qmin, k2)
+                checked += 1
+                cut += qmin > k2
+    assert checked > 2000 and cut > 100, (checked, cut)
+
+
+@pytest.mark.parametrize("trim", [False, True])
+def test_tile_rect_covers_alpha_support(trim):
+    """Every pixel where a Gaussian's FP64 alpha reaches 1/255 lies in a tile its FP32 binning keeps
+    (its rectangle, less the column cuts when they are on)."""
     w = synth.tiny_workload()
     cam, t = w.frames[0]
     tile = 16
-    b = oracle.bin_f32(w.scene, cam, t, tile)
+    b = oracle.bin_f32(w.scene, cam, t, tile, trim=trim)
     g = oracle.preprocess(w.scene, cam, t)
     ys, xs = np.mgrid[0:cam.height, 0:cam.width]
     px, py = xs.ravel() + 0.5, ys.ravel() + 0.5
@@ -415,6 +489,7 @@ def test_tile_rect_covers_alpha_support():
         assert b["tiles_touched"][i] > 0
         x0, x1, y0, y1 = b["rect"][i]
         assert np.all((tx[hit] >= x0) & (tx[hit] <= x1) & (ty[hit] >= y0) & (ty[hit] <= y1)), i
+        assert np.all(kept_tiles(b, i)[ty[hit] - y0, tx[hit] - x0]), i
         checked += 1
     assert checked > 900
 
@@ -422,7 +497,7 @@ def test_tile_rect_covers_alpha_support():
 def test_tile_list_sorted_and_ranges():
     w = synth.tiny_workload()
     cam, t = w.frames[0]
-    b = oracle.bin_f32(w.scene, cam, t, 16)
+    b = oracle.bin_f32(w.scene, cam, t, 16, trim=True)
     L = oracle.tile_list(b)
     key = (L["tile"].astype(np.uint64) << np.uint64(32)) | L["depth"].astype(np.uint64)
     assert np.all(np.diff(key.astype(np.float64)) >= 0) or np.all(key[1:] >= key[:-1])
