@@ -113,9 +113,9 @@ typedef struct {
     int64_t tiles_touched;       /* N uint32: tiles kept of the trimmed rectangle, 0 if culled */
     int64_t rect;                /* N x 4 uint16: x0, x1, y0, y1 (inclusive tile indices)    */
     int64_t depth_order;         /* N uint32: Gaussian ids sorted by (depth key, id)         */
-    int64_t tile_keys;           /* key_capacity uint32, sorted by tile: (tile key << id_bits) | id
-                                    when packed, else the tile key; tile key =
-                                    (tile row << col_bits) | tile column                       */
+    int64_t tile_keys;           /* key_capacity uint32, sorted by tile: (tile row << id_bits) | id
+                                    when packed, else the tile row; a tile's pairs are
+                                    [ranges[t].x, ranges[t].y)                                */
     int64_t tile_vals;           /* key_capacity uint32 Gaussian ids when not packed, else -1  */
     int64_t ranges;              /* tiles x 2 uint32: [start, end) of each tile's list        */
     int64_t final_T;             /* H x W float: transmittance after the last blend           */
@@ -125,8 +125,8 @@ typedef struct {
     int32_t tiles_x, tiles_y;
     int32_t depth_passes, tile_passes;
     int32_t id_bits;             /* ceil(log2 N) */
-    int32_t packed;              /* 1: pairs packed in one uint32 (tile key bits + id_bits <= 32) */
-    int32_t col_bits;            /* ceil(log2 tiles_x): bits of the column in a tile key      */
+    int32_t packed;              /* 1: pairs packed in one uint32 (row bits + id_bits <= 32) */
+    int32_t col_bits;            /* ceil(log2 tiles_x) (the pair keys carry the row only)     */
     int64_t trims;               /* N uint64: per-column trims of the rectangle (config trim = 1,
                                     else 0); byte j (column x0 + j, j < 8) = rows cut at the
                                     top | rows cut at the bottom << 4 (0..15 each); the

@@ -93,13 +93,14 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     if (l.tiles_x > kMaxCols) return false;
     l.col_bits = ceil_log2(l.tiles_x);
     l.row_bits = ceil_log2(l.tiles_y);
-    l.tile_bits = l.col_bits + l.row_bits;
-    // pass 0: column buckets (emission); then >= 1 radix pass over the row bits
+    // a pair's key holds its tile row only: the emission buckets the pairs by
+    // column (pass 0) and the stable row passes keep that order within a row
+    l.tile_bits = l.row_bits;
     const int row_passes = (l.row_bits + 7) / 8 < 1 ? 1 : (l.row_bits + 7) / 8;
     l.tile_passes = 1 + row_passes;
     l.tile_shift[0] = 0;
     l.tile_pass_bits[0] = l.col_bits;
-    int sh = l.col_bits;
+    int sh = 0;
     for (int p = 1; p < l.tile_passes; p++) {
         const int left = l.tile_bits - sh, passes_left = l.tile_passes - p;
         const int b = (left + passes_left - 1) / passes_left;

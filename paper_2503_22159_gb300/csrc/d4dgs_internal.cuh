@@ -52,12 +52,14 @@ struct Layout {
     int32_t n = 0, width = 0, height = 0, tile = 0, tiles_x = 0, tiles_y = 0, ntiles = 0;
     int64_t pixels = 0;
     int32_t depth_passes = 4;
-    // tile key = (row << col_bits) | column; pass 0 of the tile sort is the
-    // column bucketing done by the emission, passes 1.. sort by row bits
+    // pass 0 of the tile sort is the column bucketing done by the emission;
+    // passes 1.. sort stably by the tile row, so a pair's key is its tile row
+    // (tile_bits = row_bits; tile_shift / tile_pass_bits of passes 1.. are
+    // relative to it)
     int32_t col_bits = 0, row_bits = 0, tile_bits = 0, tile_passes = 0;
     int32_t tile_shift[3] = {0, 0, 0}, tile_pass_bits[3] = {0, 0, 0};
-    // pairs are packed as (tile key << id_bits | id) in one uint32 when they
-    // fit, else kept as a tile key plus a separate Gaussian-id value
+    // pairs are packed as (row << id_bits | id) in one uint32 when they fit,
+    // else kept as a row key plus a separate Gaussian-id value
     int32_t id_bits = 0;
     bool packed = true;
     int32_t trim_on = 0;   // config trim: 1 rectangles cut per column (tile_trim.cuh), 0 whole

@@ -1,9 +1,10 @@
 // sort.cu -- binning of the preprocessed frame into per-tile, depth-ordered
 // lists (the 3DGS fast rasteriser's (tile | depth) ordering, Sec. III-B-2).
-// A tile is keyed (row << col_bits) | column, which orders tiles row-major.
+// Tiles are ordered row-major, (row, column).
 //
 //   0. tilecount: the per-tile pair counts, accumulated by the preprocess as a
-//      2D difference grid (4 atomics per Gaussian rectangle), are integrated
+//      difference grid (4 atomics per Gaussian rectangle, or 2 per column of a
+//      rectangle cut per column), are integrated
 //      into counts, exclusive-scanned into each tile's [start, end) range and
 //      into the first position of each tile column's bucket, and reduced into
 //      the digit histograms of the row passes; no pass over the pairs is
@@ -14,11 +15,11 @@
 //   2. emit: one pair per covered tile, written in that order straight into
 //      its tile column's bucket (per-column prefixes over 256-Gaussian
 //      partitions with decoupled look-back), which is the first, column, pass
-//      of an LSD sort by tile key.  A pair is packed as
-//      (tile key << id_bits | id) in one uint32 when it fits (otherwise tile
-//      key + id value);
-//   3. onesweep LSD radix sort of the pairs by the row bits of their tile key
-//      (one 8-bit pass up to 256 tile rows).  Every step is stable, so each
+//      of an LSD sort by (row, column).  Only the row is kept in the pair: a
+//      pair is packed as (tile row << id_bits | id) in one uint32 when it
+//      fits (otherwise row + id value);
+//   3. onesweep LSD radix sort of the pairs by their tile row (one 8-bit pass
+//      up to 256 tile rows).  Every step is stable, so each
 //      tile's list ends in (depth, id) order -- the order a
 //      (tile << 32 | depth) sort gives, with 4-byte records and one pass over
 //      the pairs instead of six.
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
     uint2 *ranges = v.ranges;
     uint32_t *ctl = v.ctl;
     const uint32_t cap = v.cap;
-    const int tile_passes = v.tile_passes, col_bits = v.col_bits;
+    const int tile_passes = v.tile_passes;
     const int sh1 = v.tile_shift[1], sh2 = v.tile_shift[2];
     const uint32_t mk1 = v.tile_mask[1], mk2 = v.tile_mask[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
@@ -354,9 +355,9 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
         const uint32_t cnt = (uint32_t)grid[r * gw + c];
         const unsigned long long a = run < cap ? run : cap, b = run + cnt < cap ? run + cnt : cap;
         ranges[t] = make_uint2((uint32_t)a, (uint32_t)b);
-        // digit counts of the row passes (keys (row << col_bits) | column)
+        // digit counts of the row passes (a pair's key is its tile row)
         if (cnt) {
-            const uint32_t tk = ((uint32_t)r << col_bits) | (uint32_t)c;
+            const uint32_t tk = (uint32_t)r;
             atomicAdd(&s_hist[kRadix + ((tk >> sh1) & mk1)], cnt);
             if (tile_passes > 2) atomicAdd(&s_hist[2 * kRadix + ((tk >> sh2) & mk2)], cnt);
         }
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__
         }
         __syncthreads();
         // ---- 3. emission, warp w: Gaussians w*32 .. w*32+31 in order
-        const int id_bits = v.id_bits, col_bits = v.col_bits;
+        const int id_bits = v.id_bits;
         const bool packed = v.packed != 0;
         uint32_t *keys_out = v.tkeys[1], *vals_out = v.tvals[1];
         uint32_t *wcnt = s_dyn + warp * col_cap;
@@ -513,7 +514,7 @@ __global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__
                 const int c = (int)rq.x + cc;
                 const uint32_t o = s_base[c] + wcnt[c] + (uint32_t)(rr - top);
                 if (o < cap) {
-                    const uint32_t tk = ((uint32_t)((int)rq.z + rr) << col_bits) | (uint32_t)c;
+                    const uint32_t tk = (uint32_t)((int)rq.z + rr);   // the tile row
                     if (packed) {
                         keys_out[o] = (tk << id_bits) | gid;
                     } else {

@@ -44,14 +44,19 @@ def gpu_lists(r, cam):
     ntiles = L["tiles_x"] * L["tiles_y"]
     keys = _u32(r, "tile_keys", k, cam)
     if L["packed"]:
-        tkey = keys >> np.uint32(L["id_bits"])
+        rows = keys >> np.uint32(L["id_bits"])
         ids = keys & np.uint32((1 << L["id_bits"]) - 1)
     else:
-        tkey = keys
+        rows = keys
         ids = _u32(r, "tile_vals", k, cam)
-    # tile key = (row << col_bits) | column
-    tiles = (tkey >> np.uint32(L["col_bits"])) * np.uint32(L["tiles_x"]) + (tkey & np.uint32((1 << L["col_bits"]) - 1))
     ranges = _u32(r, "ranges", 2 * ntiles, cam).reshape(ntiles, 2)
+    # the tile of each position from the ranges; the key carries the tile row
+    starts = ranges[:, 0].astype(np.int64)
+    counts = (ranges[:, 1].astype(np.int64) - starts)
+    assert np.all(counts >= 0) and counts.sum() == k
+    assert np.array_equal(starts[counts > 0], np.concatenate([[0], np.cumsum(counts)[:-1]])[counts > 0])
+    tiles = np.repeat(np.arange(ntiles, dtype=np.uint32), counts)
+    assert np.array_equal(rows, tiles // np.uint32(L["tiles_x"])), "pair keys disagree with the tile ranges"
     return dict(tile=tiles, id=ids, ranges=ranges, stats=st, packed=bool(L["packed"]))
 
 

@@ -119,13 +119,18 @@ def test_launch_count(d4):
 
 
 def test_packing_decision(d4):
+    """A pair's key holds its tile row only (the emission has bucketed the columns): packed into one
+    uint32 with the id whenever row bits + id bits <= 32."""
     cfg8 = d4.config_struct(8, 64)
-    cam = synth.pinhole(2560, 2048)
+    cam = synth.pinhole(2560, 2048)   # 320 tile columns, 256 rows (8 bits)
     L = d4.d4dgs_workspace_layout(40_000, cam, cfg8, d4.d4dgs_workspace_bytes(40_000, cam, cfg8, 1000))
-    assert L["id_bits"] == 16 and L["packed"] == 0 and L["tile_vals"] > 0 and L["tile_passes"] == 2
-    assert L["col_bits"] == 9   # 320 tile columns, 256 rows: 9 + 8 + 16 bits do not fit 32
-    L = d4.d4dgs_workspace_layout(20_000, cam, cfg8, d4.d4dgs_workspace_bytes(20_000, cam, cfg8, 1000))
-    assert L["id_bits"] == 15 and L["packed"] == 1
+    assert L["id_bits"] == 16 and L["packed"] == 1 and L["tile_vals"] == -1 and L["tile_passes"] == 2
+    assert L["col_bits"] == 9
+    tall = synth.pinhole(64, 16384)   # 2048 tile rows (11 bits)
+    for n, ids, packed in ((2 ** 21, 21, 1), (2 ** 21 + 1, 22, 0)):
+        L = d4.d4dgs_workspace_layout(n, tall, cfg8, d4.d4dgs_workspace_bytes(n, tall, cfg8, 1000))
+        assert L["id_bits"] == ids and L["packed"] == packed and (L["tile_vals"] > 0) == (not packed)
+        assert L["tile_passes"] == 3   # 11 row bits: two row passes
 
 
 def test_product_does_not_import_oracle():

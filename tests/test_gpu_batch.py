@@ -93,9 +93,9 @@ def test_time_groups_equal_each_time_alone(graph):
 def test_batch_rejects_mixed_layout_classes():
     m = gu.d4()
     cfg = m.config_struct(16, 256)
-    big = m.DeviceScene.from_host(synth.make_scene(70_000, 3, "tiny"))   # 17 id bits
+    big = m.DeviceScene.from_host(synth.make_scene(70_000, 3, "tiny"))
     small = m.DeviceScene.from_host(synth.make_scene(100, 3, "tiny"))
-    cam_big = synth.pinhole(4096, 4096)   # 16 tile bits: 33 bits with the big scene -> unpacked
+    cam_big = synth.pinhole(256, 8192)   # 512 tile rows: two row passes, against one for the small view
     cam_small = synth.pinhole(64, 64)
     views = []
     for sc, cam in ((big, cam_big), (small, cam_small)):

@@ -94,18 +94,32 @@ def test_lists_bit_exact_medium_ragged(tile, trim):
     assert nflag <= 20
 
 
-def test_lists_bit_exact_unpacked_pairs():
-    """40,000 Gaussians (16 id bits) on 2560x2048 at 8-px tiles (9 + 8 tile-key bits) do not fit a
-    32-bit packed pair: the sort runs on tile keys with separate id values."""
+def test_lists_bit_exact_wide_grid():
+    """40,000 Gaussians on 2560x2048 at 8-px tiles (320 x 256 tiles): the pairs pack as
+    (tile row << 16 | id); the column order comes from the emission's buckets."""
     scene = synth.make_scene(40_000, 8, "box20", sh_degree=0)
     scene.log_scales -= 1.5   # smaller splats keep the pair count moderate
     cam, t = synth.orbit(2, 2560, 2048, 300)[100]
     r, _, _ = gu.render(scene, cam, t, tile=8, batch=64)
     got = gu.gpu_lists(r, cam)
-    assert not got["packed"]
+    assert got["packed"] and r.layout(cam)["tile_passes"] == 2
     b, exp = gu.expected_lists(scene, cam, t, 8)
-    assert r.layout(cam)["tile_passes"] == 2
     gu.compare_lists(got, b, exp)
+
+
+def test_lists_bit_exact_unpacked_pairs():
+    """2^21 + 1 Gaussians (22 id bits) on a 64 x 16384 image at 8-px tiles (2048 tile rows, 11 bits):
+    a pair does not fit 32 bits, so the sort carries row keys and id values separately, with two
+    row passes."""
+    scene = synth.make_scene(2 ** 21 + 1, 12, "tiny", sh_degree=0)
+    cam, t = synth.pinhole(64, 16384), 0.5
+    r, _, _ = gu.render(scene, cam, t, tile=8, batch=64)
+    L = r.layout(cam)
+    assert L["id_bits"] == 22 and not L["packed"] and L["tile_passes"] == 3
+    got = gu.gpu_lists(r, cam)
+    assert got["stats"]["status"] == 0 and got["stats"]["n_keys"] > 1_000_000
+    b, exp = gu.expected_lists(scene, cam, t, 8)
+    assert gu.compare_lists(got, b, exp) <= 1e-3 * scene.n
 
 
 def test_image_parity_tiny():
