@@ -39,7 +39,7 @@ enum : int {
     kCtlNumVisible = 2,    // Gaussians with at least one tile
     kCtlPartBase = 4,      // partition counters: depth passes 4..7, scan+emit 8, tile passes 9..11
     kCtlDepthHist = 64,    // 4 x 256 digit counts of the depth keys
-    kCtlTileHist = 64 + 4 * kRadix,   // 3 x 256 digit counts of the tile keys
+    kCtlTileHist = 64 + 4 * kRadix,   // 3 x 256 digit counts of the pair keys (tile rows)
     kCtlWords = 2048
 };
 constexpr uint32_t kStatusCapacity = 1u;
