@@ -36,11 +36,11 @@ def mixed_views(scenes, seed=0, k=6):
     return out
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_mixed_batch_equals_each_view_alone(graph):
+@pytest.mark.parametrize("graph,tile,trim", [(False, 16, False), (True, 16, False), (True, 32, True)])
+def test_mixed_batch_equals_each_view_alone(graph, tile, trim):
     m = gu.d4()
     scenes = scenes_small()
-    cfg = m.config_struct(16, 256)
+    cfg = m.config_struct(tile, 256, trim=trim)
     br = m.BatchRenderer(cfg)
     for seed in (0, 1):   # two different batches through the same (graph) path
         vs = mixed_views(scenes, seed)
@@ -105,12 +105,12 @@ def test_batch_rejects_mixed_layout_classes():
         m.BatchRenderer(cfg).render(views)
 
 
-@pytest.mark.parametrize("mode", ["batched", "loop"])
-def test_serving_returns_every_request_as_rendered_alone(mode):
+@pytest.mark.parametrize("mode,trim", [("batched", False), ("loop", False), ("batched", True)])
+def test_serving_returns_every_request_as_rendered_alone(mode, trim):
     from paper_2503_22159_gb300 import serving
     m = gu.d4()
     scenes = scenes_small()
-    cfg = m.config_struct(16, 256)
+    cfg = m.config_struct(32 if trim else 16, 256, trim=trim)
     reqs = serving.make_trace(scenes, n_requests=48, rate_hz=2000.0, seed=9,
                               resolutions=((160, 120), (320, 240), (256, 192)))
     caps = serving.calibrate_capacity(scenes, reqs, cfg, "cuda")
