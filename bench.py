@@ -365,6 +365,50 @@ def run_time_groups(args, dev, d4, w, scene, cfg, cap, peaks):
                                     "achieved_single": gbs(read_b + write_b, pre_single)}}
 
 
+def run_batched_orbit(args, dev, d4, w, scene, cfg, cap):
+    """The benchmark orbit through the batched multi-view launch (d4dgs_render_batch, the
+    serving engine's form): consecutive timestamps, each with its own camera and time, B = 8 views
+    per launch sequence, replayed as one CUDA graph; device time per batch with the L2 flushed and
+    the stream backlogged before each, as for the per-frame line."""
+    import numpy as np
+    import torch
+    B, nb = 8, 20
+    stream = torch.cuda.current_stream(dev)
+    frames = w.frames[:B * nb]
+    cam0 = frames[0][0]
+    views = []
+    for j in range(B):
+        ws = torch.empty(d4.d4dgs_workspace_bytes(scene.n, cam0, cfg, cap), dtype=torch.uint8, device=dev)
+        views.append([scene, None, None, ws, torch.empty((cam0.height, cam0.width, 3), device=dev)])
+    br = d4.BatchRenderer(cfg, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def batch(k):
+        for j in range(B):
+            cam, t = frames[(k * B + j) % len(frames)]
+            views[j][1], views[j][2] = cam, t
+        br.render([tuple(v) for v in views], stream, graph=True)
+
+    for k in range(3):
+        batch(k)
+    ev = []
+    for k in range(nb):
+        torch.cuda._sleep(1_000_000)
+        flush.fill_(k & 255)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch(k)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    stats = [d4.d4dgs_read_stats(sc.n, c, cfg, ws) for sc, c, t, ws, out in views]
+    if any(s_["status"] != 0 for s_ in stats):
+        raise RuntimeError(f"batched orbit frame reported an error: {[(s_['status'], s_['n_keys']) for s_ in stats]}")
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    return {"views_per_launch": B, "batches": nb, "frames": B * nb, "api": "d4dgs_render_batch, CUDA graph",
+            "ms_per_frame": float(ms.mean() / B), "frames_per_s": float(1e3 * B / ms.mean())}
+
+
 def run_slicing_first(args, dev, d4):
     """The slicing-first baseline (the 4D form sliced at every frame, Eq. 5-7) against the
     disentangled form on the same scenes (converted on the host), at 100k Gaussians (the count of
@@ -705,10 +749,12 @@ def run_ours(args):
                "steps": E, "api": "d4dgs_render_host_async, two slots",
                "blocking": {"value": world * E / ts, "unit": "frames/s", "api": "d4dgs_render_host"}}
 
-    groups_out = slicing_out = None
+    groups_out = slicing_out = batched_out = None
     backward_out = run_backward(args, dev, d4, w, scene, cfg, r.key_capacity) if world == 1 else None
     if not args.no_serving and world == 1:
         groups_out = run_time_groups(args, dev, d4, w, scene, cfg, r.key_capacity, peaks)
+        # the main workspace was trimmed to this run's frames; the batches cover the first 160
+        batched_out = run_batched_orbit(args, dev, d4, w, scene, cfg, 160 * scene.n)
         slicing_out = run_slicing_first(args, dev, d4)
 
     serving_out = None
@@ -730,6 +776,7 @@ def run_ours(args):
         "gpu_launches": int(launches * K), "launches_per_frame": launches,
         "wall_s_timed_region": t_wall, "peaks": peak_kind,
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out, "time_groups": groups_out,
+        "batched_orbit": batched_out,
         "slicing_first": slicing_out, "backward": backward_out,
         "autotune": {"chosen": f"{args.tile}/{args.batch}" + ("/cut" if args.trim else ""),
                      "ms_per_frame": tune_table} if tune_table else None,
