@@ -628,7 +628,7 @@ int d4dgs_launches_per_frame(int32_t n, const d4dgs_camera *cam, const d4dgs_con
     Layout L;
     if (!make_layout(n, cam, cfg, 0, &L)) return D4DGS_ERR_INVALID_ARG;
     // clear + preprocess + sort stages + blend
-    return 1 + (n > 0 ? 1 : 0) + sort_launch_count(n, L.tile_passes) + 1;
+    return 1 + (n > 0 ? 1 : 0) + sort_launch_count(n, L.tile_passes, (L.tiles_x + 1) * (L.tiles_y + 1)) + 1;
 }
 
 const char *d4dgs_strerror(int code) {

@@ -25,6 +25,8 @@ constexpr float kK2Pad = 0.0008f;
 constexpr int kSortThreads = 256;
 constexpr int kTileIPT = 15;                              // pair keys per thread (tile passes)
 constexpr int kTileItems = kSortThreads * kTileIPT;       // 3840 pairs per partition
+// tile-count grids of at most this many cells ride with the first depth pass
+constexpr int kTileCountCells = 6144;
 constexpr int kMaxCols = 2048;                            // tile columns of a view (16384 px at 8-px tiles)
 constexpr int kDepthIPT = 4;                              // depth keys per thread: short partitions, so
 constexpr int kDepthItems = kSortThreads * kDepthIPT;     // the few-key depth passes spread over all SMs
@@ -186,7 +188,7 @@ cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t s
                          unsigned long long *counts = nullptr, bool persist = false);
 cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb, const float *dl_dflow,
                             const d4dgs_scene_grad &g, cudaStream_t st, int num_sms);
-int sort_launch_count(int n, int tile_passes);
+int sort_launch_count(int n, int tile_passes, int grid_cells);
 
 __device__ __forceinline__ const View &view_of(const char *batch_area, int v) {
     return reinterpret_cast<const View *>(batch_area + kBatchTableOffset)[v];

@@ -152,9 +152,116 @@ __device__ __forceinline__ uint32_t pass_bases(const char *ba, int nviews, uint3
 // `pass` (keys = depth bits, 8-bit digits, values = ids; IOTA generates them);
 // TILE = true: tile pass `pass` of the (tile, id) pairs (count read on the
 // device).  KV: keys carry a separate uint32 value.
+// Per-tile pair counts from the view's difference grid (2D differences of the
+// rectangles, or, config trim, per-column differences: +1 at a column's first
+// kept row, -1 below its last); ranges; the first position
+// of every tile column's bucket; digit histograms of the row passes; the
+// total K and the capacity check.  One CTA per view.
+// The work of one view, by one CTA of any size: s_grid (smem_cells ints of
+// shared memory) holds the view's grid while it is integrated when it fits,
+// else the grid is integrated in place in global memory.
+__device__ __forceinline__ void tile_count_view(const View &v, int *s_grid, int smem_cells, uint32_t *s_hist,
+                                                unsigned long long *s_warp) {
+    int *grid = v.grid;
+    {   // integrate in shared memory when the view's grid fits (one global read and write)
+        const int cells = (v.cam.tiles_x + 1) * (v.cam.tiles_y + 1);
+        if (cells <= smem_cells) {
+            for (int i = threadIdx.x; i < cells; i += blockDim.x) s_grid[i] = v.grid[i];
+            __syncthreads();
+            grid = s_grid;
+        }
+    }
+    const int tiles_x = v.cam.tiles_x, tiles_y = v.cam.tiles_y;
+    uint2 *ranges = v.ranges;
+    uint32_t *ctl = v.ctl;
+    const uint32_t cap = v.cap;
+    const int tile_passes = v.tile_passes;
+    const int sh1 = v.tile_shift[1], sh2 = v.tile_shift[2];
+    const uint32_t mk1 = v.tile_mask[1], mk2 = v.tile_mask[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    const int gw = tiles_x + 1, gh = tiles_y + 1;
+    for (int i = tid; i < 3 * kRadix; i += nt) s_hist[i] = 0;
+    if (!v.trim_on) {                                // 2D differences: integrate along x first
+        for (int r = tid; r < gh; r += nt) {
+            int acc = 0;
+            for (int x = 0; x < gw; x++) { acc += grid[r * gw + x]; grid[r * gw + x] = acc; }
+        }
+        __syncthreads();
+    }
+    for (int c = tid; c < gw; c += nt) {          // then along y
+        int acc = 0;
+        for (int y = 0; y < gh; y++) { acc += grid[y * gw + c]; grid[y * gw + c] = acc; }
+    }
+    __syncthreads();
+
+    // block-wide exclusive scan of one 64-bit value per thread; returns (prefix, total)
+    auto block_scan = [&](unsigned long long mine, unsigned long long *total) {
+        unsigned long long x = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        unsigned long long before = 0, all = 0;
+        for (int w = 0; w < nt / 32; w++) {
+            if (w < warp) before += s_warp[w];
+            all += s_warp[w];
+        }
+        __syncthreads();
+        *total = all;
+        return before + x - mine;
+    };
+
+    // exclusive scan over tiles in row-major order, one contiguous chunk per thread
+    const int ntiles = tiles_x * tiles_y;
+    const int chunk = (ntiles + nt - 1) / nt;
+    const int t0 = min(tid * chunk, ntiles), t1 = min(t0 + chunk, ntiles);
+    unsigned long long sum = 0;
+    for (int t = t0; t < t1; t++) sum += (unsigned)grid[(t / tiles_x) * gw + (t % tiles_x)];
+    unsigned long long all;
+    unsigned long long run = block_scan(sum, &all);
+    for (int t = t0; t < t1; t++) {
+        const int r = t / tiles_x, c = t % tiles_x;
+        const uint32_t cnt = (uint32_t)grid[r * gw + c];
+        const unsigned long long a = run < cap ? run : cap, b = run + cnt < cap ? run + cnt : cap;
+        ranges[t] = make_uint2((uint32_t)a, (uint32_t)b);
+        // digit counts of the row passes (a pair's key is its tile row)
+        if (cnt) {
+            const uint32_t tk = (uint32_t)r;
+            atomicAdd(&s_hist[kRadix + ((tk >> sh1) & mk1)], cnt);
+            if (tile_passes > 2) atomicAdd(&s_hist[2 * kRadix + ((tk >> sh2) & mk2)], cnt);
+        }
+        run += cnt;
+    }
+    // column buckets: exclusive scan of the column totals, one contiguous run of columns per thread
+    const int cchunk = (tiles_x + nt - 1) / nt;
+    const int c0 = min(tid * cchunk, tiles_x), c1 = min(c0 + cchunk, tiles_x);
+    unsigned long long csum = 0;
+    for (int c = c0; c < c1; c++)
+        for (int r = 0; r < tiles_y; r++) csum += (unsigned)grid[r * gw + c];
+    unsigned long long call;
+    unsigned long long cb = block_scan(csum, &call);
+    for (int c = c0; c < c1; c++) {
+        v.colbase[c] = (uint32_t)(cb < cap ? cb : cap);
+        for (int r = 0; r < tiles_y; r++) cb += (unsigned)grid[r * gw + c];
+    }
+    __syncthreads();
+    for (int i = kRadix + tid; i < tile_passes * kRadix; i += nt) ctl[kCtlTileHist + i] = s_hist[i];
+    if (tid == 0) {
+        ctl[kCtlNumKeys] = all > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)all;
+        if (all > cap) atomicOr(ctl + kCtlStatus, kStatusCapacity);
+    }
+}
+
+// tc_cells (first depth pass only): when positive, the launch's first
+// kMaxViews CTAs do the tile counts of the views (tile_count_view, grid in
+// tc_cells ints of dynamic shared memory) instead of sorting, so that work
+// overlaps the pass rather than taking a launch of its own.
 template <bool KV, bool IOTA, bool TILE>
 __global__ void __launch_bounds__(kSortThreads, TILE ? (KV ? 3 : 4) : 4)
-onesweep_kernel(char *__restrict__ ba, int pass) {
+onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells) {
     constexpr int IPT = TILE ? kTileIPT : kDepthIPT;
     constexpr int ITEMS = kSortThreads * IPT;
     __shared__ uint32_t s_warp_hist[8][kRadix];
@@ -171,6 +278,14 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
     const int nviews = (int)bw[kBaNViews];
+    if (IOTA && tc_cells > 0 && (int)blockIdx.x < kMaxViews) {
+        // leading CTAs (dispatched first, so they run beside the sort): tile counts
+        extern __shared__ int s_tc[];   // [3 * kRadix] digit counts, [64] scan words, [tc_cells] grid
+        if ((int)blockIdx.x < nviews)
+            tile_count_view(view_of(ba, blockIdx.x), s_tc + 3 * kRadix + 64, tc_cells,
+                            reinterpret_cast<uint32_t *>(s_tc), reinterpret_cast<unsigned long long *>(s_tc + 3 * kRadix));
+        return;
+    }
     uint32_t *part_counter = bw + (TILE ? kBaTile : kBaDepth) + pass;
     const uint32_t total = pass_bases<TILE>(ba, nviews, s_base);
     int cur = -1;
@@ -277,11 +392,7 @@ onesweep_kernel(char *__restrict__ ba, int pass) {
     }
 }
 
-// Per-tile pair counts from the view's difference grid (2D differences of the
-// rectangles, or, config trim, per-column differences: +1 at a column's first
-// kept row, -1 below its last); ranges; the first position
-// of every tile column's bucket; digit histograms of the row passes; the
-// total K and the capacity check.  One CTA per view.
+// One CTA per view (blocks beyond the table's views return at once).
 __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, int smem_cells) {
     __shared__ unsigned long long s_warp[32];
     __shared__ uint32_t s_hist[3 * kRadix];
@@ -289,102 +400,7 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
     grid_dependency_wait();
     const uint32_t *bw = reinterpret_cast<const uint32_t *>(ba);
     if ((int)blockIdx.x >= (int)bw[kBaNViews]) return;
-    const View &v = view_of(ba, blockIdx.x);
-    int *grid = v.grid;
-    {   // integrate in shared memory when the view's grid fits (one global read and write)
-        const int cells = (v.cam.tiles_x + 1) * (v.cam.tiles_y + 1);
-        if (cells <= smem_cells) {
-            for (int i = threadIdx.x; i < cells; i += blockDim.x) s_grid[i] = v.grid[i];
-            __syncthreads();
-            grid = s_grid;
-        }
-    }
-    const int tiles_x = v.cam.tiles_x, tiles_y = v.cam.tiles_y;
-    uint2 *ranges = v.ranges;
-    uint32_t *ctl = v.ctl;
-    const uint32_t cap = v.cap;
-    const int tile_passes = v.tile_passes;
-    const int sh1 = v.tile_shift[1], sh2 = v.tile_shift[2];
-    const uint32_t mk1 = v.tile_mask[1], mk2 = v.tile_mask[2];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    const int gw = tiles_x + 1, gh = tiles_y + 1;
-    for (int i = tid; i < 3 * kRadix; i += nt) s_hist[i] = 0;
-    if (!v.trim_on) {                                // 2D differences: integrate along x first
-        for (int r = tid; r < gh; r += nt) {
-            int acc = 0;
-            for (int x = 0; x < gw; x++) { acc += grid[r * gw + x]; grid[r * gw + x] = acc; }
-        }
-        __syncthreads();
-    }
-    for (int c = tid; c < gw; c += nt) {          // then along y
-        int acc = 0;
-        for (int y = 0; y < gh; y++) { acc += grid[y * gw + c]; grid[y * gw + c] = acc; }
-    }
-    __syncthreads();
-
-    // block-wide exclusive scan of one 64-bit value per thread; returns (prefix, total)
-    auto block_scan = [&](unsigned long long mine, unsigned long long *total) {
-        unsigned long long x = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        unsigned long long before = 0, all = 0;
-        for (int w = 0; w < nt / 32; w++) {
-            if (w < warp) before += s_warp[w];
-            all += s_warp[w];
-        }
-        __syncthreads();
-        *total = all;
-        return before + x - mine;
-    };
-
-    // exclusive scan over tiles in row-major order, one contiguous chunk per thread
-    const int ntiles = tiles_x * tiles_y;
-    const int chunk = (ntiles + nt - 1) / nt;
-    const int t0 = min(tid * chunk, ntiles), t1 = min(t0 + chunk, ntiles);
-    unsigned long long sum = 0;
-    for (int t = t0; t < t1; t++) sum += (unsigned)grid[(t / tiles_x) * gw + (t % tiles_x)];
-    unsigned long long all;
-    unsigned long long run = block_scan(sum, &all);
-    for (int t = t0; t < t1; t++) {
-        const int r = t / tiles_x, c = t % tiles_x;
-        const uint32_t cnt = (uint32_t)grid[r * gw + c];
-        const unsigned long long a = run < cap ? run : cap, b = run + cnt < cap ? run + cnt : cap;
-        ranges[t] = make_uint2((uint32_t)a, (uint32_t)b);
-        // digit counts of the row passes (a pair's key is its tile row)
-        if (cnt) {
-            const uint32_t tk = (uint32_t)r;
-            atomicAdd(&s_hist[kRadix + ((tk >> sh1) & mk1)], cnt);
-            if (tile_passes > 2) atomicAdd(&s_hist[2 * kRadix + ((tk >> sh2) & mk2)], cnt);
-        }
-        run += cnt;
-    }
-    // column buckets: exclusive scan of the column totals, two columns per thread
-    unsigned long long csum[2] = {0, 0};
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int c = 2 * tid + k;
-        if (c < tiles_x)
-            for (int r = 0; r < tiles_y; r++) csum[k] += (unsigned)grid[r * gw + c];
-    }
-    unsigned long long call;
-    const unsigned long long cbase = block_scan(csum[0] + csum[1], &call);
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int c = 2 * tid + k;
-        const unsigned long long b = cbase + (k ? csum[0] : 0ull);
-        if (c < tiles_x) v.colbase[c] = (uint32_t)(b < cap ? b : cap);
-    }
-    __syncthreads();
-    for (int i = kRadix + tid; i < tile_passes * kRadix; i += nt) ctl[kCtlTileHist + i] = s_hist[i];
-    if (tid == 0) {
-        ctl[kCtlNumKeys] = all > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)all;
-        if (all > cap) atomicOr(ctl + kCtlStatus, kStatusCapacity);
-    }
+    tile_count_view(view_of(ba, blockIdx.x), s_grid, smem_cells, s_hist, s_warp);
 }
 
 // Pair emission in depth order straight into per-tile-column buckets (pass 0
@@ -547,7 +563,10 @@ int occupancy_blocks(const void *fn, int threads, size_t smem = 0) {
 // dynamic shared memory of the emission for a launch's column capacity
 constexpr size_t emit_smem(int col_cap) { return (size_t)9 * col_cap * sizeof(uint32_t); }
 
-int sort_launch_count(int n, int tile_passes) { return n == 0 ? 1 : 1 + 4 + 1 + (tile_passes - 1); }
+int sort_launch_count(int n, int tile_passes, int grid_cells) {
+    // tile counts (own launch unless they ride with the first depth pass) + 4 depth passes + emit + row passes
+    return n == 0 ? 1 : (grid_cells <= kTileCountCells ? 0 : 1) + 4 + 1 + (tile_passes - 1);
+}
 
 cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
     static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0;
@@ -560,25 +579,45 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
         cudaFuncSetAttribute(emit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
         cudaFuncSetAttribute(emit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
     }
-    // ---- 0. per-tile counts, ranges, tile digit histograms (always: ranges are written for every tile)
-    // fixed grid (blocks beyond the table's view count return at once), so that a
-    // captured launch serves batches of any size
-    static int smem_cells = -1;
-    if (smem_cells < 0) {
-        const int bytes = 160 * 1024;   // grids up to 40960 cells (e.g. 2704x2028 at 16-px tiles)
-        smem_cells = cudaFuncSetAttribute(tilecount_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-                             cudaSuccess
-                         ? bytes / 4
-                         : 0;
+    // ---- 0. per-tile counts, ranges, tile digit histograms (always: ranges are written for every tile).
+    // When every view's grid fits kTileCountCells, leading CTAs of the first depth pass do it (in
+    // shared memory sized for the largest grid of the launch); else a launch of its own, one CTA
+    // per view with up to 160 KB of shared memory.  Fixed grids (blocks beyond the table's views
+    // return at once), so that a captured launch serves batches of any size.
+    int tc_cells = 0;
+    if (args.max_n > 0) {
+        for (int i = 0; i < args.nviews; i++) {
+            const int c = (args.v[i].cam.tiles_x + 1) * (args.v[i].cam.tiles_y + 1);
+            tc_cells = c > tc_cells ? c : tc_cells;
+        }
+        tc_cells = tc_cells <= kTileCountCells ? (tc_cells + 255) / 256 * 256 : 0;
     }
-    cudaError_t e = launch_chained(tilecount_kernel, kMaxViews, 1024, (size_t)smem_cells * 4, st, batch_area, smem_cells);
+    cudaError_t e = cudaSuccess;
+    if (tc_cells == 0) {
+        static int smem_cells = -1;
+        if (smem_cells < 0) {
+            const int bytes = 160 * 1024;   // grids up to 40960 cells (e.g. 2704x2028 at 16-px tiles)
+            smem_cells = cudaFuncSetAttribute(tilecount_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+                                 cudaSuccess
+                             ? bytes / 4
+                             : 0;
+        }
+        e = launch_chained(tilecount_kernel, kMaxViews, 1024, (size_t)smem_cells * 4, st, batch_area, smem_cells);
+    }
     if (e != cudaSuccess || args.max_n == 0) return e;
     // ---- 1. depth sort (4 passes), ids in dvals[0]
     for (int p = 0; p < 4 && e == cudaSuccess; p++) {
-        if (p == 0)
-            e = launch_chained(onesweep_kernel<true, true, false>, occ_iota * num_sms, kSortThreads, 0, st, batch_area, p);
-        else
-            e = launch_chained(onesweep_kernel<true, false, false>, occ_kv * num_sms, kSortThreads, 0, st, batch_area, p);
+        if (p == 0) {
+            const size_t tc_smem = tc_cells ? (size_t)(3 * kRadix + 64 + tc_cells) * sizeof(int) : 0;
+            static int occ_tc[kTileCountCells / 256 + 1] = {0};   // by grid cells / 256
+            int &occ = tc_cells ? occ_tc[tc_cells / 256] : occ_iota;
+            if (!occ) occ = occupancy_blocks((const void *)onesweep_kernel<true, true, false>, kSortThreads, tc_smem);
+            e = launch_chained(onesweep_kernel<true, true, false>, occ * num_sms + (tc_cells ? kMaxViews : 0),
+                               kSortThreads, tc_smem, st, batch_area, p, tc_cells);
+        } else {
+            e = launch_chained(onesweep_kernel<true, false, false>, occ_kv * num_sms, kSortThreads, 0, st, batch_area, p,
+                               0);
+        }
     }
     if (e != cudaSuccess) return e;
     // ---- 2. emission in depth order into tile-column buckets (tile pass 0)
@@ -595,9 +634,11 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
     // ---- 3. stable sort of the pairs by tile-row bits (tile passes 1..)
     for (int p = 1; p < args.tile_passes && e == cudaSuccess; p++) {
         if (args.packed)
-            e = launch_chained(onesweep_kernel<false, false, true>, occ_k * num_sms, kSortThreads, 0, st, batch_area, p);
+            e = launch_chained(onesweep_kernel<false, false, true>, occ_k * num_sms, kSortThreads, 0, st, batch_area, p,
+                               0);
         else
-            e = launch_chained(onesweep_kernel<true, false, true>, occ_tkv * num_sms, kSortThreads, 0, st, batch_area, p);
+            e = launch_chained(onesweep_kernel<true, false, true>, occ_tkv * num_sms, kSortThreads, 0, st, batch_area, p,
+                               0);
     }
     return e;
 }

@@ -112,10 +112,12 @@ def test_invalid_arguments_rejected_on_host(d4):
 
 
 def test_launch_count(d4):
-    cam = synth.pinhole(1352, 1014)
     cfg = d4.config_struct(16, 256)
-    # clear + preprocess + tile counts + 4 depth passes + column emit + 1 row pass + blend
-    assert d4.d4dgs_launches_per_frame(300_000, cam, cfg) == 10
+    # clear + preprocess + 4 depth passes (the first also does the tile counts: 86 x 65 grid cells)
+    # + column emit + 1 row pass + blend
+    assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(1352, 1014), cfg) == 9
+    # 2704 x 2028 at 16 px: 171 x 128 grid cells are too many to ride along, tile counts launch alone
+    assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(2704, 2028), cfg) == 10
 
 
 def test_packing_decision(d4):
