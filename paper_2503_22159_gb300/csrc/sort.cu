@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
 // order.
 // TRIM: the launch's views cut their rectangles per column (config trim).
 template <bool TRIM>
-__global__ void __launch_bounds__(kDupThreads, 4) emit_kernel(char *__restrict__ ba, int col_cap) {
+__global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__ ba, int col_cap) {
     static_assert(kDupThreads == 256 && kDupItems == 256, "8 warps of 32 Gaussians per partition");
     extern __shared__ uint32_t s_dyn[];   // [8][col_cap] per-warp column counts, then [col_cap] bases
     __shared__ uint32_t s_id[kDupItems];
