@@ -64,3 +64,15 @@ def test_trace_is_seeded_poisson(serving):
     assert res == {(640, 480), (1352, 1014), (1920, 1080), (2704, 2028)}
     assert {r.scene for r in r1} == {"A", "B"}
     assert all(0.0 <= r.t <= 1.0 for r in r1)
+
+
+def test_trace_at_another_rate_has_the_same_requests(serving):
+    """The saturated replay offers the same requests faster: with the same seed, a different rate
+    changes only the arrival times (all drawn first), by exactly the rate ratio."""
+    scenes = {"A": FakeScene(10), "B": FakeScene(10)}
+    slow = serving.make_trace(scenes, n_requests=500, rate_hz=500.0, seed=4)
+    fast = serving.make_trace(scenes, n_requests=500, rate_hz=20000.0, seed=4)
+    for a, b in zip(slow, fast):
+        assert (a.scene, a.res, a.t) == (b.scene, b.res, b.t)
+        assert np.array_equal(a.cam.R, b.cam.R) and np.array_equal(a.cam.T, b.cam.T)
+        assert b.arrival == pytest.approx(a.arrival * 500.0 / 20000.0, rel=1e-9)
