@@ -58,7 +58,7 @@ def build(force: bool = False) -> Path:
 class _Scene(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)] + [
         (k, c_double_p) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
-                                  "quats", "opacity_logit", "sh", "cov3d")]
+                                  "quats", "opacity_logit", "sh", "cov3d", "in_err")]
 
 
 class _SceneF32(ctypes.Structure):
@@ -84,9 +84,11 @@ class _CameraF32(ctypes.Structure):
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
 
 
+_G2D_FIELDS = ("u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max", "err")
+
+
 class _G2D(ctypes.Structure):
-    _fields_ = [("drawn", c_int32_p)] + [(k, c_double_p) for k in (
-        "u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max")]
+    _fields_ = [("drawn", c_int32_p)] + [(k, c_double_p) for k in _G2D_FIELDS]
 
 
 def lib():
@@ -97,19 +99,25 @@ def lib():
         _lib.orc_preprocess.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
                                         ctypes.c_int, ctypes.POINTER(_G2D)]
         _lib.orc_render_pixels.argtypes = [ctypes.POINTER(_G2D), ctypes.c_int, ctypes.POINTER(_Camera),
-                                           c_double_p, ctypes.c_int64, c_int32_p, c_int32_p, ctypes.c_double,
+                                           c_double_p, ctypes.c_int64, c_int32_p, c_int32_p,
                                            c_double_p, c_double_p, c_int32_p, c_double_p, c_double_p]
+        _lib.orc_pair_windows.argtypes = [ctypes.POINTER(_G2D), ctypes.c_int64, c_int32_p, c_int32_p, c_int32_p,
+                                          c_double_p]
         c_uint64_p = ctypes.POINTER(ctypes.c_uint64)
         _lib.orc_bin_f32.argtypes = [ctypes.POINTER(_SceneF32), ctypes.POINTER(_CameraF32), ctypes.c_float,
                                      ctypes.c_int32, ctypes.c_int32, c_uint32_p, c_int32_p, c_int32_p, c_uint32_p, c_uint64_p,
-                                     c_int32_p, c_float_p]
+                                     c_float_p, c_float_p]
+        _lib.orc_expf.restype = ctypes.c_float
+        _lib.orc_expf.argtypes = [ctypes.c_float]
+        _lib.orc_logf.restype = ctypes.c_float
+        _lib.orc_logf.argtypes = [ctypes.c_float]
         _lib.orc_emit_keys.restype = ctypes.c_int64
         _lib.orc_emit_keys.argtypes = [ctypes.c_int32, c_uint32_p, c_int32_p, c_uint64_p, c_uint32_p,
                                        ctypes.c_int32, ctypes.c_int64, c_uint32_p, c_uint32_p, c_uint32_p]
         _lib.orc_sh_basis.argtypes = [c_double_p, ctypes.c_int, c_double_p]
         _lib.orc_quat_to_rot.argtypes = [c_double_p, c_double_p]
         _lib.orc_backward.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
-                                      c_double_p, c_double_p, ctypes.POINTER(_SceneGrad)]
+                                      c_double_p, c_double_p, ctypes.POINTER(_SceneGrad), ctypes.POINTER(_SceneGrad)]
         _lib.orc_fingerprint.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_double,
                                          ctypes.POINTER(ctypes.c_uint64)]
     return _lib
@@ -117,6 +125,20 @@ def lib():
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def expf32(x) -> np.ndarray:
+    """The binary32 exp of the binning contract (Cody-Waite reduction + Taylor series), elementwise."""
+    x = np.asarray(x, np.float32)
+    f = lib().orc_expf
+    return np.array([f(float(v)) for v in x.ravel()], np.float32).reshape(x.shape)
+
+
+def logf32(x) -> np.ndarray:
+    """The binary32 log of the binning contract (atanh series), elementwise."""
+    x = np.asarray(x, np.float32)
+    f = lib().orc_logf
+    return np.array([f(float(v)) for v in x.ravel()], np.float32).reshape(x.shape)
 
 
 def _p(a, ct):
@@ -141,13 +163,16 @@ class _Keep:
         return _p(a, ctypes.c_double)
 
 
-def _scene64(scene, keep: _Keep, cov3d=None):
+def _scene64(scene, keep: _Keep, cov3d=None, in_err=None):
     s = _Scene()
     s.n = scene.n
     s.sh_degree = scene.sh_degree
     for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh"):
         setattr(s, k, keep.d(getattr(scene, k)))
     s.cov3d = keep.d(cov3d)
+    if in_err is not None:
+        assert cov3d is not None and np.asarray(in_err).shape == (scene.n, 10)
+    s.in_err = keep.d(in_err)
     return s
 
 
@@ -174,38 +199,58 @@ def quat_to_rot(q) -> np.ndarray:
     return R.reshape(3, 3)
 
 
-def preprocess(scene, cam, t: float, temporal_cull: bool = True, cov3d=None) -> dict:
-    """FP64 dynamic 2D Gaussians at time t (dict of numpy arrays, length N)."""
+def preprocess(scene, cam, t: float, temporal_cull: bool = True, cov3d=None, in_err=None) -> dict:
+    """FP64 dynamic 2D Gaussians at time t (dict of numpy arrays, length N), with ``err``
+    (N x 16): what a binary32 evaluation makes of each Gaussian (oracle.c, orc_preprocess):
+    u, v, Z, o_hat and the inverse of Sigma' of its binary32 footprint, the mode (0 both
+    draw it, 1 only the definition, 2 only binary32), in cov3d mode a-priori bounds instead.
+    ``cov3d`` (N x 6) replaces scales and quaternions; ``in_err`` (N x 10, with ``cov3d``)
+    bounds the FP32 error of the mean at t (3), the relative error of the opacity at t (1)
+    and of Sigma3D (6) that an FP32 evaluation starts from."""
     n = scene.n
     keep = _Keep()
-    s = _scene64(scene, keep, cov3d)
+    s = _scene64(scene, keep, cov3d, in_err)
     c = _camera64(cam)
     out = dict(drawn=np.zeros(n, np.int32), u=np.zeros(n), v=np.zeros(n), depth=np.zeros(n),
                conic=np.zeros((n, 3)), cov2d=np.zeros((n, 3)), opacity_t=np.zeros(n),
-               rgb=np.zeros((n, 3)), lambda_max=np.zeros(n))
-    g = _G2D(_p(out["drawn"], ctypes.c_int32), *[_p(out[k], ctypes.c_double) for k in (
-        "u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max")])
+               rgb=np.zeros((n, 3)), lambda_max=np.zeros(n), err=np.zeros((n, 16)))
+    g = _G2D(_p(out["drawn"], ctypes.c_int32), *[_p(out[k], ctypes.c_double) for k in _G2D_FIELDS])
     lib().orc_preprocess(ctypes.byref(s), ctypes.byref(c), float(t), int(temporal_cull), ctypes.byref(g))
     out["drawn"] = out["drawn"].astype(bool)
     return out
 
 
-def default_eps_px(cam) -> float:
-    """Absolute FP32 error budget (pixels) of a projected mean: 2^-20 max(W, H)."""
-    return float(2.0 ** -20 * max(cam.width, cam.height))
+def _g2d_struct(g: dict):
+    fields = {k: _d(g[k]) for k in _G2D_FIELDS}
+    drawn = np.ascontiguousarray(g["drawn"], dtype=np.int32)
+    s = _G2D(_p(drawn, ctypes.c_int32), *[_p(fields[k], ctypes.c_double) for k in _G2D_FIELDS])
+    return s, [drawn] + list(fields.values())
 
 
-def render_g2d(g: dict, cam, pixels=None, bg=(0.0, 0.0, 0.0), eps_px=None) -> dict:
+def pair_windows(g: dict, gid, pixels) -> dict:
+    """For (Gaussian, pixel) pairs: the FP64 exponent p and unclamped alpha o_hat e^min(p,0),
+    the same for the binary32 footprint (p_f, alpha_f), and the relative window of an FP32
+    blend's alpha around alpha_f that the slack uses."""
+    gid = np.ascontiguousarray(gid, np.int32)
+    pixels = np.asarray(pixels, np.int32).reshape(-1, 2)
+    assert len(gid) == len(pixels)
+    px = np.ascontiguousarray(pixels[:, 0])
+    py = np.ascontiguousarray(pixels[:, 1])
+    s, keep = _g2d_struct(g)
+    out = np.zeros((len(gid), 5))
+    lib().orc_pair_windows(ctypes.byref(s), len(gid), _p(gid, ctypes.c_int32), _p(px, ctypes.c_int32),
+                           _p(py, ctypes.c_int32), _p(out, ctypes.c_double))
+    del keep
+    return dict(p=out[:, 0], alpha=out[:, 1], p_f=out[:, 2], alpha_f=out[:, 3], w=out[:, 4])
+
+
+def render_g2d(g: dict, cam, pixels=None, bg=(0.0, 0.0, 0.0)) -> dict:
     """Per-pixel brute-force compositing of precomputed FP64 2D Gaussians.
 
     ``pixels`` is None (whole image, row-major) or an (M, 2) int array of (x, y).
     Returns rgb (H,W,3) or (M,3), T, ncontrib, slack and Tw (see oracle.c)."""
     n = len(g["u"])
-    fields = ("u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max")
-    gg = {k: _d(g[k]) for k in fields}
-    drawn = np.ascontiguousarray(g["drawn"], dtype=np.int32)
-    s = _G2D(_p(drawn, ctypes.c_int32), *[_p(gg[k], ctypes.c_double) for k in fields])
-    keep = [drawn] + list(gg.values())
+    s, keep = _g2d_struct(g)
     c = _camera64(cam)
     if pixels is None:
         m = cam.width * cam.height
@@ -223,9 +268,8 @@ def render_g2d(g: dict, cam, pixels=None, bg=(0.0, 0.0, 0.0), eps_px=None) -> di
     slack = np.zeros(shape)
     Tw = np.zeros(shape)
     bgv = _d(np.asarray(bg, np.float64))
-    eps = default_eps_px(cam) if eps_px is None else float(eps_px)
     lib().orc_render_pixels(ctypes.byref(s), n, ctypes.byref(c), _p(bgv, ctypes.c_double), m,
-                            _p(px, ctypes.c_int32), _p(py, ctypes.c_int32), eps,
+                            _p(px, ctypes.c_int32), _p(py, ctypes.c_int32),
                             _p(rgb, ctypes.c_double), _p(T, ctypes.c_double), _p(nc, ctypes.c_int32),
                             _p(slack, ctypes.c_double), _p(Tw, ctypes.c_double))
     del keep
@@ -233,17 +277,18 @@ def render_g2d(g: dict, cam, pixels=None, bg=(0.0, 0.0, 0.0), eps_px=None) -> di
 
 
 def render(scene, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0), temporal_cull: bool = True,
-           cov3d=None, eps_px=None) -> dict:
+           cov3d=None, in_err=None) -> dict:
     """Render one frame (or the listed pixels) of ``scene`` at time ``t`` in FP64."""
-    g = preprocess(scene, cam, t, temporal_cull=temporal_cull, cov3d=cov3d)
-    out = render_g2d(g, cam, pixels=pixels, bg=bg, eps_px=eps_px)
+    g = preprocess(scene, cam, t, temporal_cull=temporal_cull, cov3d=cov3d, in_err=in_err)
+    out = render_g2d(g, cam, pixels=pixels, bg=bg)
     out["g2d"] = g
     return out
 
 
 def bin_f32(scene, cam, t: float, tile: int, trim: bool = False) -> dict:
     """FP32 binning mirror: depth key bits, radius, rect, column trims (``trim``: the renderer's
-    config trim; all zero otherwise), tile count, flags, uv."""
+    config trim; all zero otherwise), tile count, uv and ``foot`` (o_hat, Sigma'_00, Sigma'_01,
+    Sigma'_11 of the binary32 footprint) of every binned Gaussian."""
     n = scene.n
     f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     arrs = {k: f(getattr(scene, k)) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
@@ -256,12 +301,12 @@ def bin_f32(scene, cam, t: float, tile: int, trim: bool = False) -> dict:
     c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
     c.width, c.height = int(cam.width), int(cam.height)
     out = dict(depth_key=np.zeros(n, np.uint32), radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
-               tiles_touched=np.zeros(n, np.uint32), trims=np.zeros(n, np.uint64), flags=np.zeros(n, np.int32),
-               uv=np.zeros((n, 2), np.float32))
+               tiles_touched=np.zeros(n, np.uint32), trims=np.zeros(n, np.uint64), uv=np.zeros((n, 2), np.float32),
+               foot=np.zeros((n, 4), np.float32))
     lib().orc_bin_f32(ctypes.byref(s), ctypes.byref(c), ctypes.c_float(t), int(tile), 1 if trim else 0,
                       _p(out["depth_key"], ctypes.c_uint32), _p(out["radius"], ctypes.c_int32),
                       _p(out["rect"], ctypes.c_int32), _p(out["tiles_touched"], ctypes.c_uint32),
-                      _p(out["trims"], ctypes.c_uint64), _p(out["flags"], ctypes.c_int32), _p(out["uv"], ctypes.c_float))
+                      _p(out["trims"], ctypes.c_uint64), _p(out["uv"], ctypes.c_float), _p(out["foot"], ctypes.c_float))
     out["tiles_x"] = (cam.width + tile - 1) // tile
     out["tiles_y"] = (cam.height + tile - 1) // tile
     return out
@@ -288,22 +333,26 @@ def tile_list(b: dict) -> dict:
     return dict(tile=tile, depth=depth, id=ids, ranges=np.stack([starts, ends], axis=1).astype(np.uint32))
 
 
-def backward(scene, cam, t: float, dl_drgb, bg=(0.0, 0.0, 0.0)) -> dict:
+def backward(scene, cam, t: float, dl_drgb, bg=(0.0, 0.0, 0.0), with_slack: bool = False):
     """FP64 adjoint: gradients of sum(dl_drgb * image) w.r.t. every raw parameter
-    (dl_drgb: (H, W, 3); the render uses the temporal cull, as render() does)."""
+    (dl_drgb: (H, W, 3); the render uses the temporal cull, as render() does).
+    with_slack: also the per-element gradient slack (same keys and shapes): how far an FP32
+    renderer's gradient may move because a decision near its threshold goes the other way
+    (oracle.c, orc_backward); returns (grads, slack)."""
     keep = _Keep()
     s = _scene64(scene, keep)
     c = _camera64(cam)
-    grads = {k: np.zeros(np.asarray(getattr(scene, k)).shape) for k in (
-        "means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh")}
-    gs = _SceneGrad(*[_p(grads[k], ctypes.c_double) for k in (
-        "means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh")])
+    names = ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh")
+    grads = {k: np.zeros(np.asarray(getattr(scene, k)).shape) for k in names}
+    gs = _SceneGrad(*[_p(grads[k], ctypes.c_double) for k in names])
+    slack = {k: np.zeros(np.asarray(getattr(scene, k)).shape) for k in names} if with_slack else None
+    ss = _SceneGrad(*[_p(slack[k], ctypes.c_double) for k in names]) if with_slack else None
     dl = _d(dl_drgb)
     assert dl.shape == (cam.height, cam.width, 3)
     bgv = _d(np.asarray(bg, np.float64))
     lib().orc_backward(ctypes.byref(s), ctypes.byref(c), float(t), _p(dl, ctypes.c_double),
-                       _p(bgv, ctypes.c_double), ctypes.byref(gs))
-    return grads
+                       _p(bgv, ctypes.c_double), ctypes.byref(gs), ctypes.byref(ss) if with_slack else None)
+    return (grads, slack) if with_slack else grads
 
 
 def fingerprint(scene, cam, t: float) -> np.ndarray:
@@ -377,10 +426,65 @@ def slice4d(scene4d, t: float):
     return static, cov6
 
 
-def render_slicing(scene4d, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0), eps_px=None) -> dict:
-    """Slice every 4D Gaussian at t (Eq. 5-7), then render the static 3D result in FP64."""
+_U32 = 2.0 ** -24        # unit roundoff of binary32
+_FN_REL = 4.0 * _U32     # exp / log within 2 ulp
+
+
+def slice4d_fp32_bounds(scene4d, t: float) -> np.ndarray:
+    """(N, 10) bounds on the FP32 error of what an FP32 evaluation of the slice (Eq. 5-7)
+    hands to the projection: the mean at t (3, absolute), the opacity at t (1, relative) and
+    Sigma3D (6, absolute; xx, xy, xz, yy, yz, zz).  Same model as the oracle's projection
+    bounds (correctly rounded operations, a sum of k terms within k u of their magnitudes,
+    exp within 2 ulp).  Two FP32 routes are covered, so each bound is the sum of both:
+      * slicing first: R4 from the normalised quaternion pair (4u per component, 12u per
+        entry), M4 = R4 diag(e^s4), Sigma4D = M4 M4^T, V/W, Sigma3D = U - V (V/W)^T,
+        mean mu + tau V/W, opacity sigmoid(lg) exp(-tau^2 / (2W));
+      * the disentangled parameters rounded to binary32 (scales e^ls and quaternions of the
+        eigen-decomposition of Sigma3D, V/W, log sqrt(W)) and then the disentangled
+        projection, whose factor M3 = R(q) diag(s) the oracle's Sigma' bound takes as
+        64u |M3| |M3|^T on Sigma3D."""
+    u, E = _U32, _FN_REL
+    m4 = _d(scene4d.means4).reshape(-1, 4)
+    s4 = np.exp(_d(scene4d.log_scales4).reshape(-1, 4))
+    R4 = rot4(scene4d.quat_l, scene4d.quat_r)
+    M4 = R4 * s4[:, None, :]
+    dM4 = (16 * u + E) * np.broadcast_to(s4[:, None, :], M4.shape)
+    aM4 = np.abs(M4)
+    S4 = np.einsum("nik,njk->nij", M4, M4)
+    dS4 = (np.einsum("nik,njk->nij", aM4, dM4) + np.einsum("nik,njk->nij", dM4, aM4)
+           + 4 * u * np.einsum("nik,njk->nij", aM4, aM4))
+    V, W = S4[:, :3, 3], S4[:, 3, 3]
+    dV, dW = dS4[:, :3, 3], dS4[:, 3, 3]
+    v = V / W[:, None]
+    dv = (dV + np.abs(v) * dW[:, None]) / W[:, None] + u * np.abs(v)
+    S3 = S4[:, :3, :3] - V[:, :, None] * v[:, None, :]
+    dS3 = (dS4[:, :3, :3] + dV[:, :, None] * np.abs(v)[:, None, :] + np.abs(V)[:, :, None] * dv[:, None, :]
+           + u * np.abs(V[:, :, None] * v[:, None, :]) + u * np.abs(S3))
+    # the converted route: Sigma3D's factor and the rounding of its scales to binary32
+    evals, evecs = np.linalg.eigh(0.5 * (S3 + np.swapaxes(S3, 1, 2)))
+    M3 = evecs * np.sqrt(np.maximum(evals, 0.0))[:, None, :]
+    ls = 0.5 * np.log(np.maximum(evals, 1e-30))
+    aM3 = np.abs(M3)
+    dS3 = dS3 + (64 * u + 2 * u * np.abs(ls).max(axis=1))[:, None, None] * np.einsum("nik,njk->nij", aM3, aM3)
+    tau = t - m4[:, 3]
+    m = m4[:, :3] + tau[:, None] * v
+    dm = (np.abs(tau)[:, None] * dv + 2 * u * np.abs(tau[:, None] * v) + u * np.abs(m)
+          + 3 * u * np.abs(tau[:, None] * v) + u * np.abs(m))
+    x = 0.5 * tau * tau / W
+    lst = np.abs(0.5 * np.log(W))
+    dop = (2 * E + 3 * u + x * (5 * u + dW / W)) + (2 * E + 3 * u + x * (5 * u + 2 * E + 2 * u * lst))
+    out = np.zeros((len(m4), 10))
+    out[:, :3] = dm
+    out[:, 3] = dop
+    out[:, 4:] = dS3[:, [0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]
+    return out
+
+
+def render_slicing(scene4d, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0)) -> dict:
+    """Slice every 4D Gaussian at t (Eq. 5-7), then render the static 3D result in FP64
+    (the slack covers an FP32 slice as well as FP32 disentangled parameters)."""
     static, cov6 = slice4d(scene4d, t)
-    return render(static, cam, t, pixels=pixels, bg=bg, cov3d=cov6, eps_px=eps_px)
+    return render(static, cam, t, pixels=pixels, bg=bg, cov3d=cov6, in_err=slice4d_fp32_bounds(scene4d, t))
 
 
 # ---------------------------------------------------------------------------
@@ -402,17 +506,17 @@ def flow_g2d(scene, cam, t: float) -> np.ndarray:
     return np.stack([cam.fx * Vc[:, 0] / X[:, 2], cam.fy * Vc[:, 1] / X[:, 2]], axis=1)
 
 
-def render_flow(scene, cam, t: float, pixels=None, eps_px=None) -> dict:
+def render_flow(scene, cam, t: float, pixels=None) -> dict:
     """The blended flow image (H, W, 2) (or (M, 2) at `pixels`), composited with the colour
     weights; the slack is the per-pixel bound of `render` with the flow as colour."""
     g = preprocess(scene, cam, t)
     f = flow_g2d(scene, cam, t)
     gf = dict(g)
     gf["rgb"] = np.column_stack([f, np.zeros(len(f))])
-    out = render_g2d(gf, cam, pixels=pixels, bg=(0.0, 0.0, 0.0), eps_px=eps_px)
+    out = render_g2d(gf, cam, pixels=pixels, bg=(0.0, 0.0, 0.0))
     # the slack bound takes non-negative values: evaluate it on |flow|
     gf["rgb"] = np.abs(gf["rgb"])
-    mag = render_g2d(gf, cam, pixels=pixels, bg=(0.0, 0.0, 0.0), eps_px=eps_px)
+    mag = render_g2d(gf, cam, pixels=pixels, bg=(0.0, 0.0, 0.0))
     return dict(flow=out["rgb"][..., :2], slack=mag["slack"], T=out["T"])
 
 

@@ -13,12 +13,13 @@
 //   k^2 = 2 ln(255 o_hat) with a small margin); depth key = bits(Z)
 //   colour = max(0, SH . Y(normalize(mu(t) - campos)) + 0.5)
 //
-// The quantities that decide binning (Z, u, v, Sigma', lambda_max, radius,
-// rectangle) use explicitly rounded single-precision operations in a fixed
-// order (__fmul_rn/__fadd_rn/__fdiv_rn/__fsqrt_rn are never contracted into
-// FMAs), so a CPU evaluation in the same order reproduces the tile lists bit
-// for bit; only exp() of the scales and of the opacity terms may differ by an
-// ulp between math libraries.
+// The quantities that decide binning (Z, u, v, o_hat, Sigma', lambda_max,
+// radius, rectangle) use explicitly rounded single-precision operations in a
+// fixed order (__fmul_rn/__fadd_rn/__fdiv_rn/__fsqrt_rn are never contracted
+// into FMAs; the FMAs that are there are explicit), and exp and log are the
+// explicit methods below rather than a math library's, so a CPU evaluation of
+// the same steps reproduces every binning decision, and the tile lists, bit
+// for bit.
 #include "d4dgs_internal.cuh"
 #include "tile_trim.cuh"
 
@@ -30,6 +31,70 @@ __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b);
 __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float dvd(float a, float b) { return __fdiv_rn(a, b); }
+
+// exp and log of the binning arithmetic, each a published method in explicitly
+// rounded steps (within ~1 ulp of the exact function):
+//   bexp(x): Cody-Waite reduction x = n ln2 + r with n = rint(x log2 e) and ln2
+//            split into a 16-bit head (n ln2_hi is exact for |n| < 256) and a
+//            tail; e^r by its Taylor series to r^7/7! in Horner form with fused
+//            multiply-adds (|r| <= ln2/2, truncation below 0.1 ulp); times 2^n
+//            (exact); x < -87 gives 0 and x > 88.5 gives +inf.
+//   blog(x): x = m 2^e with m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1),
+//            log m = 2 atanh s = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9)
+//            (|s| <= 0.172, truncation below 1e-9 relative), plus e ln2.
+constexpr float kLn2Hi = 0.693145751953125f;   // ln 2 rounded to 16 significant bits
+constexpr float kLn2Lo = 1.42860682e-06f;      // float(ln 2 - kLn2Hi)
+constexpr float kLog2eF = 1.44269502f;         // float(1 / ln 2)
+constexpr float kSqrt2F = 1.41421354f;         // float(sqrt 2)
+
+__device__ __forceinline__ float bexp(float x) {
+    if (x != x) return x;
+    if (x < -87.0f) return 0.0f;
+    if (x > 88.5f) return __int_as_float(0x7F800000);
+    const float n = rintf(mul(x, kLog2eF));
+    float r = __fmaf_rn(-n, kLn2Hi, x);
+    r = __fmaf_rn(-n, kLn2Lo, r);
+    float p = 1.98412701e-04f;              // 1/7!
+    p = __fmaf_rn(p, r, 1.38888892e-03f);   // 1/6!
+    p = __fmaf_rn(p, r, 8.33333377e-03f);   // 1/5!
+    p = __fmaf_rn(p, r, 4.16666679e-02f);   // 1/4!
+    p = __fmaf_rn(p, r, 1.66666672e-01f);   // 1/3!
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    int k = (int)n;
+    if (k > 127) {
+        p = mul(p, 2.0f);
+        k -= 1;
+    }
+    return mul(p, __uint_as_float((uint32_t)(k + 127) << 23));
+}
+
+__device__ __forceinline__ float blog(float x) {
+    if (!(x > 0.0f)) return x == 0.0f ? __int_as_float(0xFF800000) : __int_as_float(0x7FC00000);
+    if (x == __int_as_float(0x7F800000)) return x;
+    int e = 0;
+    if (x < 1.17549435e-38f) {   // subnormal: times 2^23
+        x = mul(x, 8388608.0f);
+        e = -23;
+    }
+    uint32_t b = __float_as_uint(x);
+    e += (int)(b >> 23) - 127;
+    float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    if (m > kSqrt2F) {
+        m = mul(m, 0.5f);
+        e += 1;
+    }
+    const float s = dvd(sub(m, 1.0f), add(m, 1.0f));
+    const float z = mul(s, s);
+    float p = 1.11111112e-01f;              // 1/9
+    p = __fmaf_rn(p, z, 1.42857149e-01f);   // 1/7
+    p = __fmaf_rn(p, z, 2.00000003e-01f);   // 1/5
+    p = __fmaf_rn(p, z, 3.33333343e-01f);   // 1/3
+    const float lm = __fmaf_rn(mul(s, z), p, s);   // atanh s
+    const float ef = (float)e;
+    return __fmaf_rn(ef, kLn2Hi, __fmaf_rn(ef, kLn2Lo, mul(2.0f, lm)));
+}
 
 // Real SH basis (Condon-Shortley phase; coefficient k = l^2 + l + m), constants
 // from their closed forms.
@@ -118,9 +183,9 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
         const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
         if (!(Z > kNear)) break;
         // ---- temporal opacity
-        const float o = dvd(1.0f, add(1.0f, expf(-p_lg)));
-        const float st = expf(p_lt);
-        const float oh = mul(o, expf(dvd(mul(-0.5f, mul(tau, tau)), mul(st, st))));
+        const float o = dvd(1.0f, add(1.0f, bexp(-p_lg)));
+        const float st = bexp(p_lt);
+        const float oh = mul(o, bexp(dvd(mul(-0.5f, mul(tau, tau)), mul(st, st))));
         if (!(oh >= kAlphaMin)) break;
         // ---- projection of the mean and the Jacobian at the shifted mean
         const float xz = dvd(X, Z), yz = dvd(Y, Z);
@@ -141,7 +206,7 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
         Rq[6] = mul(2.0f, sub(mul(qx, qz), mul(qw, qy)));
         Rq[7] = mul(2.0f, add(mul(qy, qz), mul(qw, qx)));
         Rq[8] = sub(1.0f, mul(2.0f, add(mul(qx, qx), mul(qy, qy))));
-        const float sc[3] = {expf(p_s0), expf(p_s1), expf(p_s2)};
+        const float sc[3] = {bexp(p_s0), bexp(p_s1), bexp(p_s2)};
         float M[9];
 #pragma unroll
         for (int r = 0; r < 3; r++)
@@ -287,7 +352,7 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
             // ellipse d^T Sigma'^-1 d <= k^2, k^2 = 2 ln(255 o_hat) (+ margin), outside
             // which alpha = o_hat e^p < 1/255; half-extents k sqrt(Sigma'_00), k sqrt(Sigma'_11)
             if (!(isfinite(u) && isfinite(v))) break;
-            const float k2 = add(mul(mul(2.0f, logf(mul(255.0f, oh))), kK2Scale), kK2Pad);
+            const float k2 = add(mul(mul(2.0f, blog(mul(255.0f, oh))), kK2Scale), kK2Pad);
             const float ex = __fsqrt_rn(mul(k2, s00)), ey = __fsqrt_rn(mul(k2, s11));
             const float rx = ceilf(ex), ry = ceilf(ey);
             const float fx0 = floorf(dvd(sub(u, rx), tilef)), fx1 = floorf(dvd(add(u, rx), tilef));
@@ -326,8 +391,14 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
             rc = make_ushort4((unsigned short)x0, (unsigned short)x1, (unsigned short)y0, (unsigned short)y1);
             key = __float_as_uint(Z);
             nvis++;
-            // ---- conic (rendering only; ordinary arithmetic from here on)
-            const float inv_det = 1.0f / det;
+            // ---- conic (rendering only; ordinary arithmetic from here on): the inverse of
+            // Sigma' through a determinant with one compensation step (Kahan's 2x2 determinant:
+            // w = s01^2 rounded, its exact rounding error by an FMA, then s00 s11 - w by an FMA;
+            // within 2 ulp however close s00 s11 and s01^2 are), so a thin splat's conic carries
+            // only the rounding of Sigma' itself, not the cancellation of its determinant
+            const float w01 = __fmul_rn(s01, s01);
+            const float det_c = __fadd_rn(__fmaf_rn(s00, s11, -w01), __fmaf_rn(-s01, s01, w01));
+            const float inv_det = 1.0f / det_c;
             // ---- view-dependent colour in the direction of the shifted mean
             float dx = m0 - c.campos[0], dy = m1 - c.campos[1], dz = m2 - c.campos[2];
             const float inv_n = rsqrtf(dx * dx + dy * dy + dz * dz);

@@ -66,23 +66,17 @@ def expected_lists(scene, cam, t, tile, trim=False):
 
 
 def compare_lists(got, b, exp):
-    """Bit-exact (tile, id) sequence after removing the Gaussians the mirror
-    flags (decisions through expf within 3e-6 of a threshold)."""
-    flagged = np.nonzero(b["flags"] & 11)[0]   # rectangle, cull or column cut decided near a threshold
-    keep_g = ~np.isin(got["id"], flagged)
-    keep_e = ~np.isin(exp["id"], flagged)
-    gt, gi = got["tile"][keep_g], got["id"][keep_g]
-    et, ei = exp["tile"][keep_e], exp["id"][keep_e]
-    assert len(gt) == len(et), (len(gt), len(et), len(flagged))
-    assert np.array_equal(gt, et)
-    assert np.array_equal(gi, ei)
-    if len(flagged) == 0:
-        # non-empty tiles: identical [start, end); empty tiles: any empty range
-        gr, er = got["ranges"].astype(np.int64), exp["ranges"].astype(np.int64)
-        full = er[:, 1] > er[:, 0]
-        assert np.array_equal(gr[full], er[full])
-        assert np.all(gr[~full, 1] == gr[~full, 0])
-    return len(flagged)
+    """The (tile, id) sequence and every non-empty tile's [start, end) bit for bit
+    (empty tiles: any empty range).  The mirror's arithmetic, exp and log included,
+    is the kernel's, so no Gaussian is left out."""
+    assert len(got["tile"]) == len(exp["tile"]), (len(got["tile"]), len(exp["tile"]))
+    assert np.array_equal(got["tile"], exp["tile"])
+    assert np.array_equal(got["id"], exp["id"])
+    gr, er = got["ranges"].astype(np.int64), exp["ranges"].astype(np.int64)
+    full = er[:, 1] > er[:, 0]
+    assert np.array_equal(gr[full], er[full])
+    assert np.all(gr[~full, 1] == gr[~full, 0])
+    return 0
 
 
 def compare_image(got, ref, where=""):

@@ -42,12 +42,12 @@ def test_scene_preprocess_and_lists(scene_w, gpu_renderer, k, trim):
     rec = gu.gpu_records(r, n, cam)
     b = oracle.bin_f32(scene_w.scene, cam, t, 16, trim=trim)
     g = oracle.preprocess(scene_w.scene, cam, t)
-    flag = (b["flags"] & 11) != 0
-    vis = (b["tiles_touched"] > 0) & ~flag
+    vis = b["tiles_touched"] > 0
     assert vis.sum() > 100_000
-    rvis = vis & ((b["flags"] & 4) == 0)
-    assert np.array_equal(rec[rvis, 7].astype(np.int32), b["radius"][rvis])
+    assert np.array_equal(rec[vis, 7].astype(np.int32), b["radius"][vis])
     assert np.array_equal(rec[vis, 6].view(np.uint32), b["depth_key"][vis])
+    assert np.array_equal(rec[vis, 0:2], b["uv"][vis])
+    assert np.array_equal(rec[vis, 5], b["foot"][vis, 0])
     trims = r.view("trims", torch.int64, n, cam).cpu().numpy().view(np.uint64)
     assert np.array_equal(trims[vis], b["trims"][vis])
     np.testing.assert_allclose(rec[vis, 0], g["u"][vis], atol=2e-3)
@@ -59,10 +59,8 @@ def test_scene_preprocess_and_lists(scene_w, gpu_renderer, k, trim):
     got = gu.gpu_lists(r, cam)
     exp = oracle.tile_list(b)
     assert got["stats"]["status"] == 0
-    nflag = gu.compare_lists(got, b, exp)
-    # windows of 3e-6 relative on radii (rectangle) and on row extents over the tile size
-    # (up to 16 column-cut decisions per Gaussian) for splats up to ~200 px
-    assert nflag < 2e-3 * n
+    # every Gaussian, every tile: the whole list and every range bit for bit
+    gu.compare_lists(got, b, exp)
 
 
 @pytest.mark.parametrize("k", [0, 150, 299])
@@ -81,6 +79,9 @@ def test_scene_image_sampled(scene_w, gpu_renderer, k):
     s = gu.compare_image(got, ref, f"scene frame {k}")
     gu.compare_T(gu.gpu_final_T(r, cam)[pix[:, 1], pix[:, 0]], ref, f"scene frame {k}")
     assert float(np.abs(ref["rgb"]).max()) > 0.1
-    # the dense scene puts a near-threshold candidate on many pixels; the strict
-    # 2e-3 check must still cover a good share of them
-    assert s["flagged"] < 0.7 * len(pix)
+    # pixels with a decision within FP32 reach of its threshold (slack > 0) get the slack on top
+    # of 2e-3; at most 5% of the sampled pixels may be such (measured: 0.2-2.8% on frames 0, 150
+    # and 299 at 3000 random pixels)
+    share = s["flagged"] / len(pix)
+    print(f"scene frame {k}: flagged share {share:.4f}, max err {s['max']:.3g}, mean err {s['mean']:.3g}")
+    assert share <= 0.05, f"frame {k}: {share:.3f} of the sampled pixels flagged"

@@ -13,6 +13,7 @@ import pytest
 
 import tests.test_oracle_adjoint as adjoint_pins
 import tests.test_oracle_pins as pins
+import tests.test_oracle_slack as slack_pins
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -35,7 +36,7 @@ MUTANTS = [
      ["test_single_gaussian_off_axis_closed_form"]),
     ("pixel centre without +0.5", "double x = (px ? px[q] : (int32_t)(q % W)) + 0.5;",
      "double x = (px ? px[q] : (int32_t)(q % W));", ["test_single_gaussian_on_axis_closed_form"]),
-    ("blend after the stop test", "if (test < ORC_T_MIN) break;", "if (test < 0.0) break;", ["test_composite_golden"]),
+    ("blend after the stop test", "const int stop = test < ORC_T_MIN;", "const int stop = test < 0.0;", ["test_composite_golden"]),
     ("no alpha clamp", "double alpha = fmin(ORC_ALPHA_MAX,", "double alpha = fmin(1.0,", ["test_composite_golden"]),
     ("back-to-front order", "if (a->depth < b->depth) return -1;\n    if (a->depth > b->depth) return 1;",
      "if (a->depth < b->depth) return 1;\n    if (a->depth > b->depth) return -1;", ["test_composite_golden"]),
@@ -50,8 +51,8 @@ MUTANTS = [
      "out->rgb[3 * (size_t)i + ch] = s + 0.5;", ["test_negative_colour_is_clamped"]),
     ("FP32 radius factor 3.0", "float rf = ceilf(3.33f * sqrtf(lam));", "float rf = ceilf(3.0f * sqrtf(lam));",
      ["test_bin_f32_agrees_with_fp64"]),
-    ("FP32 binning ellipse without the factor 2", "float k2 = ((2.0f * logf(255.0f * oh)) * 1.0008f) + 0.0008f;",
-     "float k2 = ((1.0f * logf(255.0f * oh)) * 1.0008f) + 0.0008f;", ["test_tile_rect_covers_alpha_support"]),
+    ("FP32 binning ellipse without the factor 2", "float k2 = ((2.0f * orc_logf(255.0f * oh)) * 1.0008f) + 0.0008f;",
+     "float k2 = ((1.0f * orc_logf(255.0f * oh)) * 1.0008f) + 0.0008f;", ["test_tile_rect_covers_alpha_support"]),
     ("FP32 binning ellipse with the wrong axis", "float ex = sqrtf(k2 * s00), ey = sqrtf(k2 * s11);",
      "float ex = sqrtf(k2 * s11), ey = sqrtf(k2 * s00);", ["test_tile_rect_covers_alpha_support"]),
     ("FP32 rect with truncation", "float fx0 = floorf((u - rx) / tilef)", "float fx0 = floorf((u - rx) / tilef) + 1.0f",
@@ -62,10 +63,28 @@ MUTANTS = [
      "const float xt = fminf(fmaxf(xl, a), b)", ["test_column_trims_match_fp64_box_test"]),
     ("column cuts counted from the rectangle's last row", "cut_t = (int32_t)fminf(fmaxf(ceilf(flo) - (float)y0",
      "cut_t = (int32_t)fminf(fmaxf(ceilf(flo) - (float)(y0 + 1)", ["test_column_trims_match_fp64_box_test"]),
+    # the per-pixel slack (tests/test_oracle_slack.py)
+    ("slack window 10 times too wide", "    return ORC_SAFETY * w;\n}", "    return 10.0 * ORC_SAFETY * w;\n}",
+     ["test_blend_window_covers_fp32_and_is_tight"]),
+    ("slack window without the quadratic form's rounding (thin splats)",
+     "const double dp_eval = 13.0 * u * Q + u * fabs(p);", "const double dp_eval = u * fabs(p);",
+     ["test_blend_window_covers_fp32_and_is_tight"]),
+    ("a-priori camera-space bound without the mean's own error (cov3d mode)", "dX[r] = prop + 4.0 * u * mag;",
+     "dX[r] = 4.0 * u * mag;", ["test_apriori_bounds_cover_fp32_slicing"]),
+    ("a-priori bound of Sigma' without the propagated factor error", "dv += dF[3 * r + k] * fabs(G[3 * q2 + k]) + fabs(F[3 * r + k]) * dG[3 * q2 + k];",
+     "dv += 0.0;", ["test_apriori_bounds_cover_fp32_slicing"]),
+    ("depth-key order ignored", "if (!sorted) {", "if (0) {", ["test_slack_covers_depth_key_swap"]),
+    ("near-plane straddle ignored", "} else if (f32_draws == 0) {\n            mode = 1;", "} else if (0) {\n            mode = 1;",
+     ["test_near_plane_straddle_is_flagged"]),
+    ("slack of an alpha flip four times too big",
+     "slack += 2.0 * fmax(fabs(alpha), af) * (1.0 + cand[k].w) * cmax * T + 1e-7;",
+     "slack += 8.0 * fmax(fabs(alpha), af) * (1.0 + cand[k].w) * cmax * T + 1e-7;", ["test_slack_within_flip_bound"]),
+    ("slack on every pixel", "if (out_slack) out_slack[q] = slack;", "if (out_slack) out_slack[q] = slack + 1e-6;",
+     ["test_slack_zero_away_from_thresholds"]),
     # adjoint (caught by the finite-difference pin)
     ("adjoint: colour behind ignored", "dalpha += Ti * G[ch] * (c[ch] - B[ch]);", "dalpha += Ti * G[ch] * c[ch];",
      ["test_adjoint_matches_central_differences"]),
-    ("adjoint: conic off-diagonal", "gi[3] += -dp * dx * dy;", "gi[3] += -0.5 * dp * dx * dy;",
+    ("adjoint: conic off-diagonal", "gi[3] = -dp * dx * dy;", "gi[3] = -0.5 * dp * dx * dy;",
      ["test_adjoint_matches_central_differences"]),
     ("adjoint: velocity dropped from dtau", "dtau += sc->velocity[3 * (size_t)i + j] * dm[j];", "dtau += 0.0 * dm[j];",
      ["test_adjoint_matches_central_differences"]),
@@ -74,6 +93,9 @@ MUTANTS = [
 ]
 
 ARGSETS = {
+    "test_blend_window_covers_fp32_and_is_tight": [dict(kind="stress")],
+    "test_slack_within_flip_bound": [dict(kind="box")],
+    "test_slack_zero_away_from_thresholds": [dict(kind="tiny")],
     "test_single_gaussian_on_axis_closed_form": [dict(rotated=False), dict(rotated=True)],
     "test_column_trims_match_fp64_box_test": [dict(tile=16, frame=0), dict(tile=32, frame=150)],
     "test_tile_rect_covers_alpha_support": [dict(trim=True)],
@@ -100,9 +122,10 @@ def test_pins_catch_mutant(tmp_path, monkeypatch, name, old, new, tests):
     mod = _load_mutant(tmp_path, name, old, new)
     monkeypatch.setattr(pins, "oracle", mod)
     monkeypatch.setattr(adjoint_pins, "oracle", mod)
+    monkeypatch.setattr(slack_pins, "oracle", mod)
     caught = []
     for tname in tests:
-        fn = getattr(pins, tname, None) or getattr(adjoint_pins, tname)
+        fn = getattr(pins, tname, None) or getattr(slack_pins, tname, None) or getattr(adjoint_pins, tname)
         argsets = ARGSETS.get(tname, [{}])
         for kw in argsets:
             try:

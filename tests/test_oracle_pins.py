@@ -387,9 +387,12 @@ def test_bin_f32_agrees_with_fp64(trim):
     np.testing.assert_allclose(b["uv"][ok, 1], g["v"][ok], atol=1e-3)
     depth = b["depth_key"][ok].view(np.float32).astype(np.float64)
     np.testing.assert_allclose(depth, g["depth"][ok], rtol=1e-6)
-    r64 = np.ceil(3.33 * np.sqrt(g["lambda_max"][ok]))
-    unflagged = (b["flags"][ok] & 4) == 0
-    assert np.array_equal(b["radius"][ok][unflagged], r64[unflagged].astype(np.int32))
+    x64 = 3.33 * np.sqrt(g["lambda_max"][ok])
+    r64 = np.ceil(x64)
+    # FP32 and FP64 may round a radius within FP32 reach of an integer differently
+    clear = np.abs(x64 - np.round(x64)) > 1e-5 * x64
+    assert clear.mean() > 0.99
+    assert np.array_equal(b["radius"][ok][clear], r64[clear].astype(np.int32))
     rect = b["rect"][ok]
     area = (rect[:, 1] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 2] + 1)
     kept = np.array([kept_tiles(b, i).sum() for i in np.nonzero(ok)[0]])
@@ -440,7 +443,7 @@ def test_column_trims_match_fp64_box_test(tile, frame):
     b = oracle.bin_f32(scene, cam, t, tile, trim=True)
     g = oracle.preprocess(scene, cam, t)
     checked = cut = 0
-    for i in np.nonzero((b["tiles_touched"] > 0) & (b["flags"] == 0))[0]:
+    for i in np.nonzero(b["tiles_touched"] > 0)[0]:
         s00, s01, s11 = g["cov2d"][i]
         det = s00 * s11 - s01 * s01
         A00, A01, A11 = s11 / det, -s01 / det, s00 / det
