@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=40)
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-large", action="store_true", help="skip the 1M-Gaussian 2704x2028 line")
+    p.add_argument("--no-training", action="store_true", help="skip the 4-view training step line")
     p.add_argument("--serve-requests", type=int, default=2000)
     return p.parse_args()
 
@@ -209,10 +211,11 @@ def cpu_baseline(w, frame_idx: int, budget_s: float):
     cam, t = w.frames[frame_idx]
     frame_s, info = oracle_frame_sample(w.scene, cam, t, budget_s)
     return {"value": 1.0 / frame_s, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "extrapolated": True, "rows_timed_fraction": info["rows"] / info["height"],
             "sample": (f"frame {frame_idx}: FP64 preprocess of all {info['n']} Gaussians "
                        f"({info['t_pre']:.2f} s) + per-pixel brute force over all Gaussians for "
-                       f"{info['rows']} of {info['height']} pixel rows ({info['t_rows']:.2f} s), "
-                       f"extrapolated to the full frame")}
+                       f"{info['rows']} of {info['height']} pixel rows ({info['t_rows']:.2f} s); value "
+                       f"EXTRAPOLATED from those rows to the full frame")}
 
 
 def run_reference(args):
@@ -225,12 +228,13 @@ def run_reference(args):
     steps, warm = args.steps, args.warmup
     per_step = max(0.5, 150.0 / max(1, steps + warm))
     nf = len(w.frames)
-    frame_times = []
+    frame_times, fractions = [], []
     for k in range(warm + steps):
         cam, t = w.frames[k % nf]
         fs, info = oracle_frame_sample(w.scene, cam, t, per_step)
         if k >= warm:
             frame_times.append(fs)
+            fractions.append(info["rows"] / info["height"])
     total = sum(frame_times)
     value = steps / total
     cores = oracle.num_threads()
@@ -240,9 +244,11 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(w, args),
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "extrapolated": True, "rows_timed_fraction": float(sum(fractions) / len(fractions)),
                          "sample": (f"each step: one orbit frame, FP64 preprocess of all Gaussians + brute-force "
-                                    f"compositing of a band of pixel rows sized to ~{per_step:.1f} s, "
-                                    f"extrapolated to the full frame")},
+                                    f"compositing of a band of pixel rows sized to ~{per_step:.1f} s; the value is "
+                                    f"EXTRAPOLATED from the timed rows (mean fraction "
+                                    f"{sum(fractions) / len(fractions):.3f} of each frame) to whole frames")},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -418,7 +424,7 @@ def run_slicing_first(args, dev, d4):
     import torch
 
     import synth
-    from paper_2503_22159_gb300 import convert
+    from synth import convert
     stream = torch.cuda.current_stream(dev)
     cfg = d4.config_struct(args.tile, args.batch)
     frames = synth.orbit(1, 1352, 1014, 300)[::10]
@@ -505,6 +511,25 @@ def run_backward(args, dev, d4, w, scene, cfg, cap):
         raise RuntimeError("non-finite gradients")
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     sh_bytes = 4 * 3 * (w.scene.sh_degree + 1) ** 2
+    # per launch: the memset of the 2D gradient sums, K7 (tile replay), K8 (preprocess adjoint)
+    per = []
+    for k, (cam, t) in enumerate(frames):
+        d4.d4dgs_render(scene, cam, t, cfg, ws, out, stream)
+        torch.cuda._sleep(1_000_000)
+        flush.fill_(k & 255)
+        with d4.LaunchTimer(stream, 3) as lt:
+            d4.d4dgs_render_backward(scene, cam, t, cfg, ws, dl, grads, stream)
+        torch.cuda.synchronize(dev)
+        per.append(lt.times_ms())
+    per = np.mean(np.array(per), axis=0)
+    k8_bytes = scene.n * (64 + sh_bytes + 48 + 64 + sh_bytes)
+    peaks, _ = load_peaks()
+    launches = {"memset_grad2d_ms": float(per[0]), "blend_backward_ms": float(per[1]),
+                "preprocess_backward_ms": float(per[2]),
+                "preprocess_backward_roofline": {"bound": "hbm", "bytes_per_launch": k8_bytes, "unit": "GB/s",
+                                                 "peak": peaks["hbm_gbs"],
+                                                 "achieved": k8_bytes / (per[2] * 1e-3) / 1e9,
+                                                 "frac": k8_bytes / (per[2] * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
 
     # the optical-flow channel (Eq. 13) and the flow-gradient loss (Eq. 17-18): forward with flow,
     # loss with dL/dF, backward through both channels; device time per frame of each
@@ -558,9 +583,239 @@ def run_backward(args, dev, d4, w, scene, cfg, cap):
         sp_ms.append(e0.elapsed_time(e1))
     split = {"ms": float(np.median(sp_ms)), "n_before": scene.n, "n_after": new_n,
              "note": "median of 5 calls, the new count read back inside the call"}
-    return {"ms_per_frame": ms, "frames": len(frames), "frames_per_s": 1e3 / ms,
+    return {"ms_per_frame": ms, "frames": len(frames), "frames_per_s": 1e3 / ms, "launches": launches,
             "k8_bytes_per_frame": scene.n * (64 + sh_bytes + 48 + 64 + sh_bytes),
             "flow_ms_per_frame": flow_ms, "split": split}
+
+
+def launch_names(d4, n, cam, cfg, ws):
+    """Names of the launches of one d4dgs_render, in order (the C side's launch sequence)."""
+    L = d4.d4dgs_workspace_layout(n, cam, cfg, ws.numel())
+    names = ["clear", "preprocess"]
+    if (L["tiles_x"] + 1) * (L["tiles_y"] + 1) > 6144:
+        names.append("tilecount")
+    names += [f"depth_pass_{p}" for p in range(4)]
+    names.append("emit")
+    names += [f"row_pass_{p}" for p in range(1, L["tile_passes"])]
+    names.append("blend")
+    return names, L
+
+
+def run_kernel_times(dev, d4, w, scene, cfg, r, frames, peaks, alu_peak, evals_pf, work_pf):
+    """Device time of every launch of a frame (the launch timer: an event after each launch, so the
+    chained launches lose their overlap here), L2 flushed and the stream backlogged before each
+    frame; per kernel the algorithmic bytes (or FP32 lane operations) per launch and the fraction
+    of the measured peak they reach at that time."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    cam0 = frames[0][0]
+    names, L = launch_names(d4, scene.n, cam0, cfg, r.ws)
+    out = torch.empty((cam0.height, cam0.width, 3), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    per, keys = [], []
+    for k, (cam, t) in enumerate(frames):
+        torch.cuda._sleep(1_000_000)
+        flush.fill_(k & 255)
+        with d4.LaunchTimer(stream, len(names)) as lt:
+            d4.d4dgs_render(scene, cam, t, cfg, r.ws, out, stream)
+        torch.cuda.synchronize(dev)
+        ms = lt.times_ms()
+        if len(ms) != len(names):
+            raise RuntimeError(f"launch timer recorded {len(ms)} launches, expected {len(names)}")
+        per.append(ms)
+        keys.append(int(r.stats(cam)["n_keys"]))
+    ms = np.mean(np.array(per), axis=0)
+    n, K = scene.n, float(np.mean(keys))
+    sh_bytes = 4 * 3 * (w.scene.sh_degree + 1) ** 2
+    trim = 8 if cfg.trim else 0
+    pair_b = 4 if L["packed"] else 8
+    hbm = peaks["hbm_gbs"]
+    cells = (L["tiles_x"] + 1) * (L["tiles_y"] + 1)
+    bytes_of = {
+        "preprocess": (n * (64 + sh_bytes) + n * (64 + trim),
+                       "params + SH read (64 + 4*3*(deg+1)^2 B), record + key + count + rect (+ cuts) written"),
+        "tilecount": (cells * 8 + L["tiles_x"] * L["tiles_y"] * 8, "difference grid read and integrated, ranges written"),
+        "depth_pass_0": (n * 12, "depth key read, key + id written (ids generated)"),
+        "emit": (n * (16 + trim) + K * pair_b, "depth order, rectangle, count (+ cuts) read per Gaussian; a pair written"),
+        "blend": (K * 52 + L["tiles_x"] * L["tiles_y"] * 8 + cam0.width * cam0.height * 20,
+                  "per pair a 48-B record and its id staged; ranges; RGB + final T + walked count written"),
+    }
+    for p in range(1, 4):
+        bytes_of[f"depth_pass_{p}"] = (n * 16, "key + id read and written")
+    for p in range(1, L["tile_passes"]):
+        bytes_of[f"row_pass_{p}"] = (K * 2 * pair_b, "pair read and written")
+    kern = {}
+    for name, t_ms in zip(names, ms):
+        e = {"ms": float(t_ms)}
+        if name in bytes_of:
+            b, what = bytes_of[name]
+            ach = b / (t_ms * 1e-3) / 1e9
+            e.update({"bound": "hbm", "bytes_per_launch": b, "bytes": what, "achieved": ach, "peak": hbm,
+                      "unit": "GB/s", "frac": ach / hbm})
+        if name == "blend":
+            ops = FP32_OPS_PER_PAIR * evals_pf
+            ach = ops / (t_ms * 1e-3) / 1e12
+            e["alu"] = {"bound": "alu", "ops_per_launch": ops, "achieved": ach, "peak": alu_peak,
+                        "unit": "TOP/s (FP32 lane ops)", "frac": ach / alu_peak,
+                        "ops": f"{FP32_OPS_PER_PAIR} per (pixel, Gaussian) pair the kernel evaluates",
+                        "frac_tile_walk": FP32_OPS_PER_PAIR * work_pf / (t_ms * 1e-3) / 1e12 / alu_peak}
+        kern[name] = e
+    binning = [k for k in names if k.startswith(("tilecount", "depth_pass", "emit", "row_pass"))]
+    return {"frames": len(frames), "launches": names, "kernels": kern,
+            "binning_ms": float(sum(kern[k]["ms"] for k in binning)),
+            "sum_ms": float(ms.sum()), "keys_per_frame": K,
+            "note": "one event after every launch (d4dgs_launch_timer): the launches do not overlap here"}
+
+
+def perturbed_scene(scene, seed: int):
+    """A seeded perturbation of `scene` (the training workload's target): means N(0, 0.05) box
+    units, colour coefficients N(0, 0.02), opacity logits N(0, 0.1)."""
+    import numpy as np
+
+    import synth
+    rng = np.random.default_rng(seed)
+    a = {k: np.array(v, copy=True) for k, v in scene.arrays().items()}
+    a["means"] = (a["means"] + rng.normal(0, 0.05, a["means"].shape)).astype(np.float32)
+    a["sh"] = (a["sh"] + rng.normal(0, 0.02, a["sh"].shape)).astype(np.float32)
+    a["opacity_logit"] = (a["opacity_logit"] + rng.normal(0, 0.1, a["opacity_logit"].shape)).astype(np.float32)
+    return synth.Scene(**a, sh_degree=scene.sh_degree)
+
+
+def run_training_step(args, dev, d4, w, scene, cfg, peaks, steps=10, warm=3):
+    """The differentiable training workload: the benchmark scene (300k SH-3 Gaussians), 4 views at
+    1352x1014 (orbit poses and times t ~ U[0,1] drawn with seed 2), L1 against seeded targets
+    (the views rendered from a seed-3 perturbation of the scene), full backward into every raw
+    parameter.  A step = for each view: render, the L1 loss kernel (loss and dL/dI, mean over the
+    step's values), backward added into the gradients (the first view's overwrites them).  Device
+    time per step from events on the stream, L2 flushed before each step."""
+    import numpy as np
+    import torch
+
+    import synth
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(2)
+    orbit = synth.orbit(2, 1352, 1014, 300)
+    views = [(orbit[int(k)][0], float(np.float32(rng.uniform(0, 1)))) for k in rng.integers(0, 300, 4)]
+    tds = d4.DeviceScene.from_host(perturbed_scene(w.scene, 3), dev)
+    targets, rs = [], []
+    for cam, t in views:
+        rt = d4.Renderer(scene.n, cam, tile=int(cfg.tile), batch=int(cfg.batch), device=dev, trim=bool(cfg.trim))
+        targets.append(rt.render(tds, cam, t).clone())
+        r = d4.Renderer(scene.n, cam, tile=int(cfg.tile), batch=int(cfg.batch), device=dev, trim=bool(cfg.trim))
+        r.render(scene, cam, t)
+        r._alloc(int(r.stats(cam)["n_keys"] * 1.05) + 4096)
+        rs.append(r)
+    del tds
+    imgs = [torch.empty_like(targets[0]) for _ in views]
+    dls = [torch.empty_like(targets[0]) for _ in views]
+    grads = scene.zeros_like_grad()
+    losses = torch.zeros(steps + warm, dtype=torch.float32, device=dev)
+    scale = 1.0 / (len(views) * targets[0].numel())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = []
+    for s_ in range(steps + warm):
+        torch.cuda._sleep(1_000_000)
+        flush.fill_(s_ & 255)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(1 + 3 * len(views))]
+        e[0].record(stream)
+        for j, ((cam, t), r) in enumerate(zip(views, rs)):
+            d4.d4dgs_render(scene, cam, t, cfg, r.ws, imgs[j], stream)
+            e[1 + 3 * j].record(stream)
+            d4.d4dgs_l1_loss(imgs[j], targets[j], scale, dls[j], losses[s_:s_ + 1], stream)
+            e[2 + 3 * j].record(stream)
+            bw = d4.d4dgs_render_backward if j == 0 else d4.d4dgs_render_backward_accumulate
+            bw(scene, cam, t, cfg, r.ws, dls[j], grads, stream)
+            e[3 + 3 * j].record(stream)
+        if s_ >= warm:
+            ev.append(e)
+    torch.cuda.synchronize(dev)
+    for (cam, t), r in zip(views, rs):
+        if r.stats(cam)["status"] != 0:
+            raise RuntimeError("training-step view reported an error")
+    if not all(bool(torch.isfinite(v).all()) for v in grads.values()):
+        raise RuntimeError("non-finite gradients")
+    step = np.array([e[0].elapsed_time(e[-1]) for e in ev])
+    phase = {"render": 0.0, "l1_loss": 0.0, "backward": 0.0}
+    for e in ev:
+        for j in range(len(views)):
+            base = e[0] if j == 0 else e[3 * j]
+            phase["render"] += base.elapsed_time(e[1 + 3 * j])
+            phase["l1_loss"] += e[1 + 3 * j].elapsed_time(e[2 + 3 * j])
+            phase["backward"] += e[2 + 3 * j].elapsed_time(e[3 + 3 * j])
+    phase = {k: v / len(ev) for k, v in phase.items()}
+    loss_vals = losses[warm:].cpu().numpy()
+    l1_bytes = 12 * targets[0].numel()
+    return {"workload": f"train-{scene.n}-4x1352x1014", "views": len(views), "steps": steps,
+            "ms_per_step": float(step.mean()), "steps_per_s": float(1e3 / step.mean()),
+            "views_per_s": float(1e3 * len(views) / step.mean()), "ms_per_step_phases": phase,
+            "loss": float(loss_vals.mean()), "launches_per_step": len(views) * (d4.d4dgs_launches_per_frame(
+                scene.n, views[0][0], cfg) + 1 + 2),
+            "l1_kernel_roofline": {"bound": "hbm", "bytes_per_launch": l1_bytes, "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                                   "achieved": l1_bytes / (phase["l1_loss"] / len(views) * 1e-3) / 1e9,
+                                   "frac": l1_bytes / (phase["l1_loss"] / len(views) * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+            "l2": "flushed before every step"}
+
+
+def run_large(args, dev, d4, peaks, frames_timed=60):
+    """The large forward workload: 1M SH-3 Gaussians at 2704x2028 on the same orbit, tile size,
+    staging depth and column cuts from the autotuner's sweep (tile {8, 16, 32} x depth {64, 128,
+    256} x cuts, table included), device time per frame over `frames_timed` orbit frames, L2
+    flushed and the stream backlogged before each."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2503_22159_gb300 import autotune
+    stream = torch.cuda.current_stream(dev)
+    w = synth.large_workload()
+    scene = d4.DeviceScene.from_host(w.scene, dev)
+    nf = len(w.frames)
+    probe = [w.frames[k] for k in (0, nf // 2, nf - 1)]
+    (tile, batch, trim), table = autotune.tune(scene, probe, device=dev, force=True)
+    cfg = d4.config_struct(tile, batch, trim=trim)
+    frames = [w.frames[(7 * k) % nf] for k in range(frames_timed)]
+    cam0 = frames[0][0]
+    r = d4.Renderer(scene.n, cam0, tile=tile, batch=batch, device=dev, trim=trim, key_capacity=64 * scene.n)
+    mk = 0
+    for cam, t in frames:
+        r.render(scene, cam, t)
+        mk = max(mk, int(r.stats(cam)["n_keys"]))
+    r._alloc(int(mk * 1.02) + 4096)
+    out = torch.empty((cam0.height, cam0.width, 3), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for cam, t in frames[:3]:
+        d4.d4dgs_render(scene, cam, t, cfg, r.ws, out, stream)
+    ev = []
+    for k, (cam, t) in enumerate(frames):
+        torch.cuda._sleep(1_000_000)
+        flush.fill_(k & 255)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        d4.d4dgs_preprocess(scene, cam, t, cfg, r.ws, stream)
+        e[1].record(stream)
+        d4.d4dgs_sort(scene.n, cam, cfg, r.ws, stream)
+        e[2].record(stream)
+        d4.d4dgs_blend(scene.n, cam, cfg, r.ws, out, stream)
+        e[3].record(stream)
+        ev.append(e)
+    torch.cuda.synchronize(dev)
+    if r.stats(frames[-1][0])["status"] != 0:
+        raise RuntimeError("large frame reported an error")
+    st = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in ev])
+    ms = float(st.sum(axis=1).mean())
+    sh_bytes = 4 * 3 * 16
+    pre_b = scene.n * (64 + sh_bytes + 64 + (8 if trim else 0))
+    return {"workload": w.name, "gaussians": scene.n, "width": cam0.width, "height": cam0.height,
+            "frames": frames_timed, "ms_per_frame": ms, "frames_per_s": 1e3 / ms,
+            "stages_ms": {"preprocess": float(st[:, 0].mean()), "sort": float(st[:, 1].mean()),
+                          "blend": float(st[:, 2].mean())},
+            "preprocess_roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                                    "achieved": pre_b / (st[:, 0].mean() * 1e-3) / 1e9,
+                                    "frac": pre_b / (st[:, 0].mean() * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+            "keys_per_frame_max": mk,
+            "autotune": {"chosen": f"{tile}/{batch}" + ("/cut" if trim else ""), "ms_per_frame": table},
+            "l2": "flushed before every frame"}
 
 
 def run_ours(args):
@@ -677,7 +932,9 @@ def run_ours(args):
     sms = props.multi_processor_count
     sm_mhz = clk["sm_mhz"] if clk else peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
     blend_ms = float(stage[:, 2].sum())
-    alu_ops = FP32_OPS_PER_PAIR * work
+    # the blend's ALU work: the (pixel, Gaussian) pairs the kernel evaluates (its block masks skip
+    # the rest of the plain tile walk, whose count is reported beside it)
+    alu_ops = FP32_OPS_PER_PAIR * evals
     alu_achieved = alu_ops / (blend_ms * 1e-3) / 1e12
     alu_peak = sms * 128 * sm_mhz * 1e6 / 1e12
     pre_ms = float(stage[:, 0].sum()) / K
@@ -691,7 +948,8 @@ def run_ours(args):
                   "unit": "TOP/s (FP32 lane ops)", "frac": alu_achieved / alu_peak,
                   "traffic": traffic_for("blend_kernel"),
                   "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock of this run)",
-                  "ops": f"{FP32_OPS_PER_PAIR} per (pixel, Gaussian) pair of the plain tile walk",
+                  "ops": f"{FP32_OPS_PER_PAIR} per (pixel, Gaussian) pair the kernel evaluates",
+                  "frac_tile_walk": FP32_OPS_PER_PAIR * work / (blend_ms * 1e-3) / 1e12 / alu_peak,
                   "tile_walk_pairs_per_frame": work / K, "kernel_evaluated_pairs_per_frame": evals / K,
                   "blended_pairs_per_frame": blends / K}
     roof_pre = {"kernel": "preprocess_kernel", "bound": "hbm",
@@ -700,6 +958,8 @@ def run_ours(args):
                 "traffic": traffic_for("preprocess_kernel")}
     ms_per_step = elapsed / K
     value = world * K / (elapsed * 1e-3)
+    kernels_out = run_kernel_times(dev, d4, w, scene, cfg, r, [w.frames[order[W + k]] for k in range(min(K, 30))],
+                                   peaks, alu_peak, evals / K, work / K) if world == 1 else None
 
     # end to end through the host-buffer entry points: every step copies the scene
     # in (pinned host -> device) and the image out, inside the timed region
@@ -760,6 +1020,11 @@ def run_ours(args):
     serving_out = None
     if not args.no_serving and world == 1:
         serving_out = run_serving(args, dev, d4)
+    training_out = large_out = None
+    if not args.no_training and world == 1 and args.workload == "scene":
+        training_out = run_training_step(args, dev, d4, w, scene, cfg, peaks)
+    if not args.no_large and world == 1 and args.workload == "scene":
+        large_out = run_large(args, dev, d4, peaks)
 
     if rank != 0:
         return 0
@@ -778,6 +1043,7 @@ def run_ours(args):
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serving": serving_out, "time_groups": groups_out,
         "batched_orbit": batched_out,
         "slicing_first": slicing_out, "backward": backward_out,
+        "kernels": kernels_out, "training_step": training_out, "large": large_out,
         "autotune": {"chosen": f"{args.tile}/{args.batch}" + ("/cut" if args.trim else ""),
                      "ms_per_frame": tune_table} if tune_table else None,
     }

@@ -89,12 +89,20 @@ typedef struct {
  * each Gaussian into its whole tile rectangle, 1 cuts the rectangle's first
  * 8 columns to the tile rows its alpha >= 1/255 ellipse reaches (fewer
  * pairs, more binning arithmetic: worth it for large splats; the image is
- * the same either way). */
+ * the same either way); near: the near plane on camera z (Sec. III-B-2
+ * defers to the 3DGS rasteriser, whose plane is 0.2; 0 selects 0.2), a
+ * Gaussian is drawn only when its time-shifted mean lies beyond it;
+ * spin_limit: polls before a bounded device spin-wait (the sort's decoupled
+ * look-back) gives up and the frame reports D4DGS_ERR_TIMEOUT (0 selects
+ * 2^20; a small value makes the waits give up early, for failure-detection
+ * tests). */
 typedef struct {
     int32_t tile;
     int32_t batch;
     float bg[3];
     int32_t trim;
+    float near;
+    uint32_t spin_limit;
 } d4dgs_config;
 
 /* Counters read back after a frame (host struct). */
@@ -200,6 +208,39 @@ int d4dgs_render(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, con
 int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
                           void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
                           d4dgs_stream_t stream);
+
+/* d4dgs_render_backward for a step over several views: the same gradients,
+ * ADDED to the arrays of `grad` instead of overwriting them (the caller zeroes
+ * them once per step).  Same arguments, workspace rules and return codes. */
+int d4dgs_render_backward_accumulate(const d4dgs_scene *scene, const d4dgs_camera *cam, float t,
+                                     const d4dgs_config *cfg, void *ws, size_t ws_bytes, const float *dl_drgb,
+                                     d4dgs_scene_grad *grad, d4dgs_stream_t stream);
+
+/* The L1 photometric term of a training step (the 3DGS image loss the paper's
+ * training keeps, Sec. III-C) and its gradient, in one pass over `count`
+ * float32 values (device, caller-owned; img and target read, dl_dimg
+ * overwritten, all 4-byte aligned, 16 bytes for the vector path):
+ *   *loss += scale * sum_k |img_k - target_k|     (loss: one device float,
+ *                                                  accumulated, not zeroed)
+ *   dl_dimg_k = scale * sign(img_k - target_k)    (sign(0) = 0)
+ * scale = 1 / (values per image x views) gives the mean over a step's views.
+ * Stream-ordered; D4DGS_ERR_INVALID_ARG on a negative count, a non-finite
+ * scale, a null or misaligned pointer. */
+int d4dgs_l1_loss(const float *img, const float *target, int64_t count, float scale, float *dl_dimg, float *loss,
+                  d4dgs_stream_t stream);
+
+/* Launch timer (profiling; the paper has no counterpart): while installed on
+ * the calling host thread, every kernel launch that thread makes through this
+ * library (and each memset of the backward) is followed by a record of the
+ * next of `events` (cudaEvent_t handles, created by the caller with timing
+ * enabled) on the launch's stream; once they are used up, further launches
+ * record nothing.  With an event the caller records just before the first
+ * call, elapsed times between consecutive events are the device times of the
+ * individual launches, in order.  d4dgs_launch_timer_stop() uninstalls it and
+ * returns how many events were recorded.  INVALID_ARG for a null array or
+ * n_events < 1. */
+int d4dgs_launch_timer(void *const *events, int32_t n_events);
+int32_t d4dgs_launch_timer_stop(void);
 
 /* ---- optical-flow channel and flow-gradient consistency loss (Sec. III-C) -
  * A Gaussian's screen flow is its ray-space velocity (Eq. 13) in pixels per
@@ -369,15 +410,18 @@ int d4dgs_render_host_async(const d4dgs_scene *host_scene, const d4dgs_camera *c
  * GPU that loads the library holds it until the process exits, and the call
  * itself allocates nothing.  The caller passes the scene and the output image
  * (H x W x 3 float32 device) as for d4dgs_render.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress), so a device reset or a new primary context is
+ *     followed safely; the first call on a device also loads the library's
+ *     module there, so make that first call before any stream capture.
  *   - Returns D4DGS_ERR_WORKSPACE_TOO_SMALL when N and the image size leave
  *     no room for keys in 64 MiB; a frame with more (tile, Gaussian) pairs
  *     than fit is reported as D4DGS_ERR_CAPACITY only through `stats`.
  *   - stats: optional host struct; when non-NULL the call synchronises
  *     `stream` and fills it (returning stats->status), otherwise the call is
- *     asynchronous.
+ *     asynchronous -- and then a frame whose pairs overflowed the array's
+ *     key capacity comes back incomplete with return code D4DGS_OK: callers
+ *     that cannot re-render elsewhere should pass stats.
  *   - All calls share the array; calls whose work overlaps on the GPU race. */
 int d4dgs_render_static(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
                         float *out_rgb, d4dgs_stats *stats, d4dgs_stream_t stream);

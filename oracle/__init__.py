@@ -75,13 +75,13 @@ class _SceneGrad(ctypes.Structure):
 class _Camera(ctypes.Structure):
     _fields_ = [("R", ctypes.c_double * 9), ("T", ctypes.c_double * 3), ("fx", ctypes.c_double),
                 ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
-                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("near", ctypes.c_double)]
 
 
 class _CameraF32(ctypes.Structure):
     _fields_ = [("R", ctypes.c_float * 9), ("T", ctypes.c_float * 3), ("fx", ctypes.c_float),
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
-                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("near", ctypes.c_float)]
 
 
 _G2D_FIELDS = ("u", "v", "depth", "conic", "cov2d", "opacity_t", "rgb", "lambda_max", "err")
@@ -182,6 +182,7 @@ def _camera64(cam):
     c.T[:] = [float(x) for x in np.asarray(cam.T, np.float64).reshape(3)]
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.width, c.height = int(cam.width), int(cam.height)
+    c.near = float(getattr(cam, "near", 0.2))
     return c
 
 
@@ -300,6 +301,7 @@ def bin_f32(scene, cam, t: float, tile: int, trim: bool = False) -> dict:
     c.T[:] = [float(x) for x in f(cam.T).reshape(3)]
     c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
     c.width, c.height = int(cam.width), int(cam.height)
+    c.near = float(getattr(cam, "near", 0.2))
     out = dict(depth_key=np.zeros(n, np.uint32), radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
                tiles_touched=np.zeros(n, np.uint32), trims=np.zeros(n, np.uint64), uv=np.zeros((n, 2), np.float32),
                foot=np.zeros((n, 4), np.float32))
@@ -353,6 +355,14 @@ def backward(scene, cam, t: float, dl_drgb, bg=(0.0, 0.0, 0.0), with_slack: bool
     lib().orc_backward(ctypes.byref(s), ctypes.byref(c), float(t), _p(dl, ctypes.c_double),
                        _p(bgv, ctypes.c_double), ctypes.byref(gs), ctypes.byref(ss) if with_slack else None)
     return (grads, slack) if with_slack else grads
+
+
+def l1_loss(img, target, scale: float):
+    """The L1 photometric term of a training step and its gradient (the 3DGS image loss the
+    paper's training keeps, Sec. III-C), FP64: (scale * sum |img - target|,
+    scale * sign(img - target))."""
+    d = _d(img) - _d(target)
+    return float(scale * np.abs(d).sum()), scale * np.sign(d)
 
 
 def fingerprint(scene, cam, t: float) -> np.ndarray:

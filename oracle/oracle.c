@@ -35,7 +35,8 @@
  *     velocity is not used to render.
  *   - Depth for sorting is camera-space z (3DGS convention).
  *   - SH colour is evaluated in the direction of the time-shifted mean.
- *   - 3DGS constants (the paper defers to 3DGS for rasterisation): near 0.2,
+ *   - 3DGS constants (the paper defers to 3DGS for rasterisation): near plane
+ *     0.2 unless the camera sets another,
  *     +0.3 px^2 dilation, Jacobian clamp 1.3 x half-FoV, alpha <= 0.99, skip
  *     alpha < 1/255, stop before blending when T(1-alpha) < 1e-4, black
  *     background; tile radius 3.33 sqrt(lambda_max) (3.33^2 > 2 ln 255, so
@@ -50,7 +51,6 @@
 #include <omp.h>
 #endif
 
-#define ORC_NEAR 0.2
 #define ORC_DILATION 0.3
 #define ORC_ALPHA_MAX 0.99
 #define ORC_ALPHA_MIN (1.0 / 255.0)
@@ -77,6 +77,7 @@ typedef struct {
     double R[9], T[3];           /* world -> camera, row-major */
     double fx, fy, cx, cy;
     int32_t width, height;
+    double near;                 /* near plane on camera z (0.2, the 3DGS plane, unless set) */
 } orc_camera;
 
 typedef struct {                 /* per-Gaussian FP64 2D Gaussian, all arrays length N */
@@ -252,7 +253,7 @@ float orc_logf(float x) {
 }
 
 typedef struct { float mu[3], tm, vel[3], ls[3], lt, q[4], lg; } orc_param_f32;
-typedef struct { float R[9], T[3], fx, fy, cx, cy; int32_t width, height; } orc_camera_f32;
+typedef struct { float R[9], T[3], fx, fy, cx, cy; int32_t width, height; float near; } orc_camera_f32;
 typedef struct { float X, Y, Z, oh, u, v, s00, s01, s11, det; } orc_fp32;
 
 /* The 2D footprint of one Gaussian in binary32 (order above):
@@ -281,7 +282,7 @@ static int project_f32(const orc_param_f32 *P, const orc_camera_f32 *cam, float 
     f->Y = ((R[3] * m0 + R[4] * m1) + R[5] * m2) + cam->T[1];
     f->Z = ((R[6] * m0 + R[7] * m1) + R[8] * m2) + cam->T[2];
     const float X = f->X, Y = f->Y, Z = f->Z;
-    if (!(Z > 0.2f)) return 0;
+    if (!(Z > cam->near)) return 0;
     const float o = 1.0f / (1.0f + orc_expf(-P->lg));
     const float st = orc_expf(P->lt);
     f->oh = o * orc_expf((-0.5f * (tau * tau)) / (st * st));
@@ -498,6 +499,7 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, double t, int te
     for (int k = 0; k < 3; k++) cam32.T[k] = (float)cam->T[k];
     cam32.fx = (float)cam->fx; cam32.fy = (float)cam->fy; cam32.cx = (float)cam->cx; cam32.cy = (float)cam->cy;
     cam32.width = cam->width; cam32.height = cam->height;
+    cam32.near = (float)cam->near;
     const int with_f32 = out->err != NULL && sc->cov3d == NULL;
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++) {
@@ -529,10 +531,10 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, double t, int te
             P.lg = (float)sc->opacity_logit[i];
             f32_draws = project_f32(&P, &cam32, (float)t, &f) == 3 && isfinite(f.u) && isfinite(f.v);
         }
-        const int def_draws = X[2] > ORC_NEAR && (!temporal_cull || oh >= ORC_ALPHA_MIN);
+        const int def_draws = X[2] > cam->near && (!temporal_cull || oh >= ORC_ALPHA_MIN);
         if (!def_draws) {
             /* binary32 draws what the definition culls: only within its reach of the thresholds */
-            if (f32_draws != 1 || !(X[2] > 0.5 * ORC_NEAR)) continue;
+            if (f32_draws != 1 || !(X[2] > 0.5 * cam->near)) continue;
             mode = 2;
         } else if (f32_draws == 0) {
             mode = 1;

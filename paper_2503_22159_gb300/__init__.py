@@ -31,7 +31,7 @@ __all__ = ["DeviceScene", "Renderer", "BatchRenderer", "camera_struct", "config_
            "d4dgs_split",
            "d4dgs_render",
            "d4dgs_render_backward", "d4dgs_read_stats", "d4dgs_render_host", "d4dgs_render_host_async",
-           "d4dgs_launches_per_frame",
+           "d4dgs_launches_per_frame", "d4dgs_render_backward_accumulate", "d4dgs_l1_loss", "LaunchTimer",
            "D4DGSError", "D4DGS_OK", "D4DGS_ERR_CAPACITY", "D4DGS_ERR_TIMEOUT", "D4DGS_ERR_INVALID_ARG",
            "D4DGS_ERR_WORKSPACE_TOO_SMALL", "D4DGS_ERR_CUDA"]
 
@@ -114,11 +114,14 @@ def camera_struct(cam) -> _abi.d4dgs_camera:
     return c
 
 
-def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0), trim: bool = False) -> _abi.d4dgs_config:
+def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0), trim: bool = False, near: float = 0.2,
+                  spin_limit: int = 0) -> _abi.d4dgs_config:
     g = _abi.d4dgs_config()
     g.tile, g.batch = int(tile), int(batch)
     g.bg[:] = [float(x) for x in bg]
     g.trim = 1 if trim else 0
+    g.near = float(near)
+    g.spin_limit = int(spin_limit)
     return g
 
 
@@ -188,6 +191,56 @@ def d4dgs_render_backward(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tens
                                                  float(t), ctypes.byref(cfg), p, nb,
                                                  ctypes.c_void_p(dl_drgb.data_ptr()), ctypes.byref(g),
                                                  _stream_handle(stream)), "d4dgs_render_backward")
+
+
+def d4dgs_render_backward_accumulate(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tensor,
+                                     dl_drgb: torch.Tensor, grads: dict, stream=None):
+    """d4dgs_render_backward adding into `grads` (a step over several views)."""
+    p, nb = _ws(ws)
+    g = _abi.d4dgs_scene_grad(*[grads[k].data_ptr() for k in SCENE_FIELDS])
+    _abi.check(_abi.load().d4dgs_render_backward_accumulate(
+        ctypes.byref(scene.struct()), ctypes.byref(camera_struct(cam)), float(t), ctypes.byref(cfg), p, nb,
+        ctypes.c_void_p(dl_drgb.data_ptr()), ctypes.byref(g), _stream_handle(stream)),
+        "d4dgs_render_backward_accumulate")
+
+
+def d4dgs_l1_loss(img: torch.Tensor, target: torch.Tensor, scale: float, dl_dimg: torch.Tensor,
+                  loss: torch.Tensor, stream=None):
+    """loss (one device float) += scale * sum |img - target|; dl_dimg = scale * sign(img - target)."""
+    for x in (img, target, dl_dimg):
+        if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+            raise ValueError("d4dgs_l1_loss takes contiguous float32 CUDA tensors")
+    if img.numel() != target.numel() or img.numel() != dl_dimg.numel() or loss.numel() < 1:
+        raise ValueError("d4dgs_l1_loss: sizes differ")
+    _abi.check(_abi.load().d4dgs_l1_loss(ctypes.c_void_p(img.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                         int(img.numel()), float(scale), ctypes.c_void_p(dl_dimg.data_ptr()),
+                                         ctypes.c_void_p(loss.data_ptr()), _stream_handle(stream)), "d4dgs_l1_loss")
+
+
+class LaunchTimer:
+    """Per-launch device times of the library calls made inside ``with`` on this host thread:
+    ``times_ms()`` after the stream has been synchronised (d4dgs_launch_timer)."""
+
+    def __init__(self, stream=None, max_launches: int = 64):
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self.events = [torch.cuda.Event(enable_timing=True) for _ in range(max_launches + 1)]
+        for e in self.events:        # creates the underlying events
+            e.record(self.stream)
+        self.count = 0
+
+    def __enter__(self):
+        arr = (ctypes.c_void_p * (len(self.events) - 1))(*[e.cuda_event for e in self.events[1:]])
+        self._arr = arr
+        self.events[0].record(self.stream)
+        _abi.check(_abi.load().d4dgs_launch_timer(arr, len(arr)), "d4dgs_launch_timer")
+        return self
+
+    def __exit__(self, *exc):
+        self.count = int(_abi.load().d4dgs_launch_timer_stop())
+        return False
+
+    def times_ms(self):
+        return [self.events[i].elapsed_time(self.events[i + 1]) for i in range(self.count)]
 
 
 def d4dgs_render_flow(scene: DeviceScene, cam, t: float, cfg, ws: torch.Tensor, out: torch.Tensor,
@@ -408,9 +461,9 @@ class Renderer:
     capacity when a frame reports D4DGS_ERR_CAPACITY."""
 
     def __init__(self, n: int, cam, tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0),
-                 key_capacity: int | None = None, device="cuda", trim: bool = False):
+                 key_capacity: int | None = None, device="cuda", trim: bool = False, near: float = 0.2):
         self.n, self.device = int(n), torch.device(device)
-        self.cfg = config_struct(tile, batch, bg, trim)
+        self.cfg = config_struct(tile, batch, bg, trim, near)
         self.width, self.height = int(cam.width), int(cam.height)
         self.cam0 = cam
         cap = key_capacity if key_capacity is not None else max(1 << 16, 16 * self.n)

@@ -49,7 +49,7 @@ class d4dgs_camera(ctypes.Structure):
 
 class d4dgs_config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("bg", ctypes.c_float * 3),
-                ("trim", ctypes.c_int32)]
+                ("trim", ctypes.c_int32), ("near", ctypes.c_float), ("spin_limit", ctypes.c_uint32)]
 
 
 class d4dgs_view(ctypes.Structure):
@@ -89,6 +89,12 @@ PROTOTYPES = {
                                     ctypes.c_size_t, _vp, _vp]),
     "d4dgs_render_backward": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float, _P(d4dgs_config),
                                              _vp, ctypes.c_size_t, _vp, _P(d4dgs_scene_grad), _vp]),
+    "d4dgs_render_backward_accumulate": (ctypes.c_int, [_P(d4dgs_scene), _P(d4dgs_camera), ctypes.c_float,
+                                                        _P(d4dgs_config), _vp, ctypes.c_size_t, _vp,
+                                                        _P(d4dgs_scene_grad), _vp]),
+    "d4dgs_l1_loss": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_float, _vp, _vp, _vp]),
+    "d4dgs_launch_timer": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32]),
+    "d4dgs_launch_timer_stop": (ctypes.c_int32, []),
     "d4dgs_read_stats": (ctypes.c_int, [ctypes.c_int32, _P(d4dgs_camera), _P(d4dgs_config), _vp, ctypes.c_size_t,
                                         _P(d4dgs_stats), _vp]),
     "d4dgs_scene_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),

@@ -36,7 +36,7 @@ bool valid_config(const d4dgs_config *g) {
     if (g->trim != 0 && g->trim != 1) return false;
     for (int i = 0; i < 3; i++)
         if (!isfinite(g->bg[i])) return false;
-    return true;
+    return isfinite(g->near) && g->near >= 0.0f;
 }
 
 bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
@@ -166,7 +166,8 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     x.sh_degree = s.sh_degree;
     x.t = t;
     for (int i = 0; i < 3; i++) x.bg[i] = cfg.bg[i];
-    x.cam = make_cam_args(&cam, cfg.tile);
+    x.cam = make_cam_args(&cam, cfg.tile, cfg.near > 0.0f ? cfg.near : kNear);
+    x.spin_limit = cfg.spin_limit ? cfg.spin_limit : kSpinLimit;
     x.out_rgb = out_rgb;
     x.zero_base = at<char>(ws, 0);
     x.zero_bytes = L.zero_end;
@@ -260,6 +261,10 @@ bool finish_batch(BatchArgs *b) {
     return true;
 }
 
+}  // namespace d4dgs
+
+namespace d4dgs {
+thread_local LaunchTimer *g_launch_timer = nullptr;
 }  // namespace d4dgs
 
 using namespace d4dgs;
@@ -439,9 +444,9 @@ int d4dgs_render_slicing(const d4dgs_scene4d *scene, const d4dgs_camera *cam, fl
     return cuda_status(e);
 }
 
-int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
-                          void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
-                          d4dgs_stream_t stream) {
+static int backward_common(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                           void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
+                           d4dgs_stream_t stream, bool accumulate) {
     int rc = check_scene(scene);
     if (rc) return rc;
     if (!isfinite(t) || !dl_drgb || !grad) return D4DGS_ERR_INVALID_ARG;
@@ -455,7 +460,35 @@ int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, flo
     Layout L;
     if ((rc = single(scene, scene->n, cam, t, cfg, ws, ws_bytes, nullptr, &b, &L))) return rc;
     return cuda_status(launch_backward(b, at<char>(ws, L.batch), dl_drgb, nullptr, *grad,
-                                       reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
+                                       reinterpret_cast<cudaStream_t>(stream), num_sms_current(), accumulate));
+}
+
+int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,
+                          void *ws, size_t ws_bytes, const float *dl_drgb, d4dgs_scene_grad *grad,
+                          d4dgs_stream_t stream) {
+    return backward_common(scene, cam, t, cfg, ws, ws_bytes, dl_drgb, grad, stream, false);
+}
+
+int d4dgs_render_backward_accumulate(const d4dgs_scene *scene, const d4dgs_camera *cam, float t,
+                                     const d4dgs_config *cfg, void *ws, size_t ws_bytes, const float *dl_drgb,
+                                     d4dgs_scene_grad *grad, d4dgs_stream_t stream) {
+    return backward_common(scene, cam, t, cfg, ws, ws_bytes, dl_drgb, grad, stream, true);
+}
+
+int d4dgs_launch_timer(void *const *events, int32_t n_events) {
+    static thread_local LaunchTimer timer;
+    if (!events || n_events < 1) return D4DGS_ERR_INVALID_ARG;
+    timer.events = reinterpret_cast<cudaEvent_t *>(const_cast<void **>(events));
+    timer.n = n_events;
+    timer.used = 0;
+    g_launch_timer = &timer;
+    return D4DGS_OK;
+}
+
+int32_t d4dgs_launch_timer_stop(void) {
+    LaunchTimer *t = g_launch_timer;
+    g_launch_timer = nullptr;
+    return t ? t->used : 0;
 }
 
 int d4dgs_render_flow(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg, void *ws,

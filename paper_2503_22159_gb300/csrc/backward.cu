@@ -336,7 +336,8 @@ struct GradArgs {
     float *means, *t_mean, *velocity, *log_scales, *log_t_scale, *quats, *opacity_logit, *sh;
 };
 
-template <int DEG>
+// ACC: add to the gradient arrays instead of overwriting them (several views of one step).
+template <int DEG, bool ACC>
 __global__ void __launch_bounds__(256)
 preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
     const View &vw = view_of(ba, 0);
@@ -353,12 +354,18 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
     if (i >= n) return;
     float *gsh = o.sh + (size_t)i * 3 * K;
     if (tiles_touched[i] == 0) {   // culled or off screen: no pixel depends on it
+        if (ACC) return;
         for (int j = 0; j < 3; j++) o.means[3 * i + j] = o.velocity[3 * i + j] = o.log_scales[3 * i + j] = 0.0f;
         for (int j = 0; j < 4; j++) o.quats[4 * i + j] = 0.0f;
         for (int j = 0; j < 3 * K; j++) gsh[j] = 0.0f;
         o.t_mean[i] = o.log_t_scale[i] = o.opacity_logit[i] = 0.0f;
         return;
     }
+    // stores of the raw gradients: overwrite, or add (ACC)
+    auto put = [](float *p, float v) {
+        if (ACC) *p += v;
+        else *p = v;
+    };
     const float *G = g2 + (size_t)i * kG2;
     const float gU = G[0], gV = G[1], gA = G[2], gB = G[3], gCc = G[4], gO = G[5];
     const float gcol[3] = {G[6], G[7], G[8]};
@@ -460,7 +467,7 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
         for (int k = 0; k < 3; k++) dR[3 * r + k] = dM[3 * r + k] * sc[k];
 #pragma unroll
     for (int k = 0; k < 3; k++)
-        o.log_scales[3 * i + k] = (dM[k] * Rq[k] + dM[3 + k] * Rq[3 + k] + dM[6 + k] * Rq[6 + k]) * sc[k];
+        put(&o.log_scales[3 * i + k], (dM[k] * Rq[k] + dM[3 + k] * Rq[3 + k] + dM[6 + k] * Rq[6 + k]) * sc[k]);
     float dq[4];
     dq[0] = 2.0f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
     dq[1] = 2.0f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.0f * qx * dR[4] - qw * dR[5] + qz * dR[6] + qw * dR[7] - 2.0f * qx * dR[8]);
@@ -469,7 +476,7 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
     const float qdot = dq[0] * qw + dq[1] * qx + dq[2] * qy + dq[3] * qz;
     const float qv[4] = {qw, qx, qy, qz};
 #pragma unroll
-    for (int j = 0; j < 4; j++) o.quats[4 * i + j] = (dq[j] - qv[j] * qdot) / qn;
+    for (int j = 0; j < 4; j++) put(&o.quats[4 * i + j], (dq[j] - qv[j] * qdot) / qn);
     // ---- colour: clamp, SH coefficients, view direction
     float dir[3] = {m[0] - c.campos[0], m[1] - c.campos[1], m[2] - c.campos[2]};
     const float inv_n = rsqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
@@ -486,7 +493,7 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
         const float gch = raw < 0.0f ? 0.0f : gcol[ch];
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            gsh[3 * k + ch] = gch * Yb[k];
+            put(&gsh[3 * k + ch], gch * Yb[k]);
             dd[0] += gch * shp[3 * k + ch] * dY[k][0];
             dd[1] += gch * shp[3 * k + ch] * dY[k][1];
             dd[2] += gch * shp[3 * k + ch] * dY[k][2];
@@ -500,17 +507,17 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
     float dtau = 0.0f;
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        o.means[3 * i + j] = dm[j];
-        o.velocity[3 * i + j] = tau * dm[j] + R[j] * dVc0 + R[3 + j] * dVc1;
+        put(&o.means[3 * i + j], dm[j]);
+        put(&o.velocity[3 * i + j], tau * dm[j] + R[j] * dVc0 + R[3 + j] * dVc1);
         dtau += vel[j] * dm[j];
     }
     const float oh = rec[3 * (size_t)i + 1].y;
     const float st = expf(s.log_t_scale[i]);
     const float sig = 1.0f / (1.0f + expf(-s.opacity_logit[i]));
-    o.opacity_logit[i] = gO * oh * (1.0f - sig);
+    put(&o.opacity_logit[i], gO * oh * (1.0f - sig));
     dtau += gO * oh * (-tau / (st * st));
-    o.log_t_scale[i] = gO * oh * tau * tau / (st * st);
-    o.t_mean[i] = -dtau;
+    put(&o.log_t_scale[i], gO * oh * tau * tau / (st * st));
+    put(&o.t_mean[i], -dtau);
 }
 
 template <int TS, int BATCH>
@@ -519,28 +526,37 @@ void launch_bb(const char *ba, int ntiles, const float *dl, const float *dlf, cu
     else blend_backward_kernel<TS, BATCH, false><<<ntiles, BlendShape<TS>::NT, 0, st>>>(ba, dl, nullptr);
 }
 
+template <bool ACC>
+void launch_k8(int deg, int blocks, const char *ba, const GradArgs &o, cudaStream_t st) {
+    switch (deg) {
+        case 0: preprocess_backward_kernel<0, ACC><<<blocks, 256, 0, st>>>(ba, o); break;
+        case 1: preprocess_backward_kernel<1, ACC><<<blocks, 256, 0, st>>>(ba, o); break;
+        case 2: preprocess_backward_kernel<2, ACC><<<blocks, 256, 0, st>>>(ba, o); break;
+        default: preprocess_backward_kernel<3, ACC><<<blocks, 256, 0, st>>>(ba, o); break;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb, const float *dl_dflow,
-                            const d4dgs_scene_grad &g, cudaStream_t st, int num_sms) {
+                            const d4dgs_scene_grad &g, cudaStream_t st, int num_sms, bool accumulate) {
     (void)num_sms;
     const View &v = args.v[0];
     if (v.n == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(v.grad2d, 0, (size_t)v.n * kG2 * sizeof(float), st);
     if (e != cudaSuccess) return e;
+    note_launch(st);
     switch (args.tile) {   // the staging depth of the backward follows the tile size
         case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
         case 16: launch_bb<16, 128>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
         default: launch_bb<32, 128>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
     }
+    note_launch(st);
     GradArgs o{g.means, g.t_mean, g.velocity, g.log_scales, g.log_t_scale, g.quats, g.opacity_logit, g.sh};
     const int blocks = (v.n + 255) / 256;
-    switch (v.sh_degree) {
-        case 0: preprocess_backward_kernel<0><<<blocks, 256, 0, st>>>(batch_area, o); break;
-        case 1: preprocess_backward_kernel<1><<<blocks, 256, 0, st>>>(batch_area, o); break;
-        case 2: preprocess_backward_kernel<2><<<blocks, 256, 0, st>>>(batch_area, o); break;
-        default: preprocess_backward_kernel<3><<<blocks, 256, 0, st>>>(batch_area, o); break;
-    }
+    if (accumulate) launch_k8<true>(v.sh_degree, blocks, batch_area, o, st);
+    else launch_k8<false>(v.sh_degree, blocks, batch_area, o, st);
+    note_launch(st);
     return cudaGetLastError();
 }
 

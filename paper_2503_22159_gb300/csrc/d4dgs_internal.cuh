@@ -10,7 +10,7 @@
 namespace d4dgs {
 
 // ---- rasteriser constants (3DGS conventions the paper reuses, Sec. III-B-2)
-constexpr float kNear = 0.2f;          // near plane on camera z
+constexpr float kNear = 0.2f;          // default near plane on camera z (config near = 0)
 constexpr float kDilation = 0.3f;      // px^2 added to the 2D covariance diagonal
 constexpr float kJacClamp = 1.3f;      // x/z, y/z clamp, times half the field of view
 constexpr float kAlphaMax = 0.99f;
@@ -47,7 +47,8 @@ enum : int {
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
 
-// Bounded spin: polls before a wait gives up and latches kStatusTimeout.
+// Bounded spin: polls before a wait gives up and latches kStatusTimeout
+// (the default of config spin_limit).
 constexpr uint32_t kSpinLimit = 1u << 20;
 
 struct Layout {
@@ -94,9 +95,10 @@ struct CamArgs {
     float R[9], T[3];
     float fx, fy, cx, cy;
     float campos[3];       // -R^T T, for the SH view direction
+    float near;            // near plane on camera z
     int32_t width, height, tile, tiles_x, tiles_y;
 };
-CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile);
+CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile, float near);
 
 // Everything the kernels need about one frame (scene, camera, time, settings
 // and the absolute addresses of its workspace buffers).  A launch processes a
@@ -133,6 +135,7 @@ struct View {
     uint32_t cap;
     int32_t id_bits, col_bits, packed, tile_passes, ntiles;
     int32_t trim_on;                 // config trim: 1 rectangles cut per column
+    uint32_t spin_limit;             // polls before a look-back gives up (config spin_limit)
     int32_t tile_shift[3];
     uint32_t tile_mask[3];
     int32_t parts_depth, parts_dup, parts_tile;
@@ -187,7 +190,7 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
 cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, float *out0,
                          unsigned long long *counts = nullptr, bool persist = false);
 cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb, const float *dl_dflow,
-                            const d4dgs_scene_grad &g, cudaStream_t st, int num_sms);
+                            const d4dgs_scene_grad &g, cudaStream_t st, int num_sms, bool accumulate = false);
 int sort_launch_count(int n, int tile_passes, int grid_cells);
 
 __device__ __forceinline__ const View &view_of(const char *batch_area, int v) {
@@ -235,6 +238,19 @@ constexpr bool kChainedLaunch = true;
 
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Launch timer (d4dgs_launch_timer): while one is installed on a host thread,
+// every kernel launch of that thread is followed by a record of the next of
+// the caller's events on the launch's stream.
+struct LaunchTimer {
+    cudaEvent_t *events;
+    int n, used;
+};
+extern thread_local LaunchTimer *g_launch_timer;
+inline void note_launch(cudaStream_t st) {
+    LaunchTimer *t = g_launch_timer;
+    if (t && t->used < t->n && cudaEventRecord(t->events[t->used], st) == cudaSuccess) t->used++;
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_chained(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
                            Args... args) {
@@ -248,7 +264,9 @@ cudaError_t launch_chained(void (*kernel)(KArgs...), unsigned grid, unsigned blo
     attr[0].val.programmaticStreamSerializationAllowed = kChainedLaunch ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    if (e == cudaSuccess) note_launch(st);
+    return e;
 }
 
 }  // namespace d4dgs

@@ -24,21 +24,19 @@ constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB, stated in 
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch, looked up once per device.  In host code
-// the name g_static_scratch is only a host-side stand-in and must never be
-// handed to a kernel.
-constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {};
-
+// Device address of g_static_scratch on the current device.  In host code the
+// name g_static_scratch is only a host-side stand-in and must never be handed
+// to a kernel.  The address is looked up on every call (once the module is
+// loaded this is a table lookup, far cheaper than a frame) rather than cached:
+// after cudaDeviceReset, or when the primary context is torn down and made
+// again, the module is loaded anew and the array may move, and a cache shared
+// by several host threads would need synchronising.  The first call on a
+// device loads the module, which is why that call must come before any stream
+// capture.
 int scratch_address(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return D4DGS_ERR_CUDA;
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return D4DGS_ERR_CUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return D4DGS_ERR_CUDA;
+    *out = p;
     return D4DGS_OK;
 }
 

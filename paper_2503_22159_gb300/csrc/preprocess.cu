@@ -181,7 +181,7 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
         const float X = add(add(add(mul(R[0], m0), mul(R[1], m1)), mul(R[2], m2)), c.T[0]);
         const float Y = add(add(add(mul(R[3], m0), mul(R[4], m1)), mul(R[5], m2)), c.T[1]);
         const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
-        if (!(Z > kNear)) break;
+        if (!(Z > c.near)) break;
         // ---- temporal opacity
         const float o = dvd(1.0f, add(1.0f, bexp(-p_lg)));
         const float st = bexp(p_lt);
@@ -288,7 +288,7 @@ __device__ __forceinline__ bool footprint_slicing(const View &vw, int i, Footpri
     const float X = add(add(add(mul(R[0], m0), mul(R[1], m1)), mul(R[2], m2)), c.T[0]);
     const float Y = add(add(add(mul(R[3], m0), mul(R[4], m1)), mul(R[5], m2)), c.T[1]);
     const float Z = add(add(add(mul(R[6], m0), mul(R[7], m1)), mul(R[8], m2)), c.T[2]);
-    if (!(Z > kNear)) return false;
+    if (!(Z > c.near)) return false;
     const float o = dvd(1.0f, add(1.0f, expf(-__ldg(vw.opacity_logit + i))));
     const float oh = mul(o, expf(dvd(mul(-0.5f, mul(tau, tau)), W)));
     if (!(oh >= kAlphaMin)) return false;
@@ -574,8 +574,9 @@ clear_kernel(const __grid_constant__ BatchArgs args, const BatchArgs *args_dev, 
 
 }  // namespace
 
-CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile) {
+CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile, float near) {
     CamArgs a;
+    a.near = near;
     for (int i = 0; i < 9; i++) a.R[i] = cam->R[i];
     for (int i = 0; i < 3; i++) a.T[i] = cam->T[i];
     a.fx = cam->fx; a.fy = cam->fy; a.cx = cam->cx; a.cy = cam->cy;

@@ -99,14 +99,14 @@ __device__ __forceinline__ bool lookback_round(const uint32_t *base, size_t stri
 // round reads FIRST entries (usually enough: the predecessor has its
 // inclusive prefix), later rounds MORE at a time, so long chains of
 // aggregates -- partitions that all reach the look-back at once -- take few
-// round trips.  An unpublished entry is polled again (bounded: on timeout
-// the status word is latched and 0 is returned).  Every pass here uses 4
+// round trips.  An unpublished entry is polled again, at most `limit` times
+// (then the status word is latched and 0 is returned).  Every pass here uses 4
 // entries a round: on the benchmark frame wider windows cost more in polling
 // loads than they save in round trips (8: +10 us per frame, 32: +40 us),
 // narrower ones take too many trips.
 template <int FIRST, int MORE>
 __device__ __forceinline__ uint32_t lookback_serial(const uint32_t *base, size_t stride, int64_t from,
-                                                    uint32_t *status) {
+                                                    uint32_t *status, uint32_t limit) {
     uint32_t excl = 0, spins = 0;
     int64_t j = from;
     if (j < 0) return 0u;
@@ -114,7 +114,7 @@ __device__ __forceinline__ uint32_t lookback_serial(const uint32_t *base, size_t
     if (lookback_round<FIRST>(base, stride, j, excl, stalled)) return excl;
     for (;;) {
         if (stalled) {
-            if (++spins > kSpinLimit) {
+            if (++spins > limit) {
                 atomicOr(status, kStatusTimeout);
                 return 0u;
             }
@@ -365,7 +365,7 @@ onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells) {
         s_local_start[d] = lstart;
         uint32_t excl = 0;
         if (part > 0 && live) {
-            excl = lookback_serial<4, 4>(lookback + d, kRadix, (int64_t)part - 1, status);
+            excl = lookback_serial<4, 4>(lookback + d, kRadix, (int64_t)part - 1, status, v.spin_limit);
             st_volatile_u32(lb + d, kFlagInc | ((excl + bcount) & kValMask));
         }
         s_delta[d] = s_hist_excl[d] + excl - lstart;
@@ -501,7 +501,8 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
             st_volatile_u32(lb, (part == 0 ? kFlagInc : kFlagAgg) | (run & kValMask));
             uint32_t excl = 0;
             if (part > 0) {
-                excl = lookback_serial<4, 4>(v.lb_col + c, (size_t)ncols, (int64_t)part - 1, v.ctl + kCtlStatus);
+                excl = lookback_serial<4, 4>(v.lb_col + c, (size_t)ncols, (int64_t)part - 1, v.ctl + kCtlStatus,
+                                             v.spin_limit);
                 st_volatile_u32(lb, kFlagInc | ((excl + run) & kValMask));
             }
             const unsigned long long b = (unsigned long long)v.colbase[c] + excl;

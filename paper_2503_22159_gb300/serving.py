@@ -18,6 +18,15 @@ Latency = completion (observed by event query on the host) - arrival.
 ``on_done(request, image)`` is called when a request completes; the image's
 buffer goes back to the pool when it returns, so it must finish reading it
 (e.g. copy and synchronise) before returning.
+
+Faults stay with the request that has them.  A request whose camera or time
+is not finite (or whose size is out of range) is refused when it arrives
+(status D4DGS_ERR_INVALID_ARG, ``on_done(request, None)``) and never joins a
+batch, so the views around it render as they would alone.  A request whose
+``cancelled`` flag is set is dropped while it waits, or, if it is already on
+the GPU, its image is discarded when its batch retires (status
+STATUS_CANCELLED, ``on_done(request, None)``); its workspace slot goes back
+to the pool either way.
 """
 from __future__ import annotations
 
@@ -29,8 +38,12 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (D4DGS_ERR_CAPACITY, D4DGS_OK, BatchRenderer, DeviceScene, config_struct, d4dgs_read_stats,
+from . import (D4DGS_ERR_CAPACITY, D4DGS_ERR_INVALID_ARG, D4DGS_OK, BatchRenderer, DeviceScene, config_struct, d4dgs_read_stats,
                d4dgs_render, d4dgs_workspace_bytes, d4dgs_workspace_layout)
+
+
+# A request its caller cancelled (a serving status, not a library error code).
+STATUS_CANCELLED = -100
 
 
 @dataclass
@@ -42,6 +55,7 @@ class Request:
     arrival: float                   # seconds from the start of the trace
     done: float = math.nan           # completion time (same clock)
     status: int = D4DGS_OK
+    cancelled: bool = False          # set by the caller at any time
 
     @property
     def res(self):
@@ -108,6 +122,16 @@ class WorkspacePool:
         n = self.scenes[key[0]].n
         L = d4dgs_workspace_layout(n, cam, self.cfg, d4dgs_workspace_bytes(n, cam, self.cfg, 1024))
         return (L["packed"], L["tile_passes"])
+
+
+def request_valid(r: Request) -> bool:
+    """The checks the library's entry points make on a view (finite camera and time, image size
+    1..16384, positive focal lengths), made on the host before the request joins a batch."""
+    c = r.cam
+    vals = list(np.asarray(c.R, np.float64).reshape(-1)) + list(np.asarray(c.T, np.float64).reshape(-1))
+    vals += [c.fx, c.fy, c.cx, c.cy, r.t]
+    return (all(math.isfinite(float(v)) for v in vals) and c.fx > 0 and c.fy > 0
+            and 1 <= int(c.width) <= 16384 and 1 <= int(c.height) <= 16384)
 
 
 def make_trace(scenes: dict, n_requests: int = 2000, rate_hz: float = 500.0, seed: int = 4,
@@ -199,11 +223,19 @@ def serve_loop(scenes: dict, requests, cfg, caps: dict, device="cuda", realtime:
     stream = torch.cuda.Stream(device)
     reqs = sorted(requests, key=lambda r: r.arrival)
     t0 = time.perf_counter()
-    redo = 0
+    redo = refused = cancelled = 0
     for r in reqs:
         if realtime:
             while time.perf_counter() - t0 < r.arrival:
                 pass
+        if r.cancelled or not request_valid(r):
+            r.status = STATUS_CANCELLED if r.cancelled else D4DGS_ERR_INVALID_ARG
+            cancelled += r.cancelled
+            refused += not r.cancelled
+            r.done = time.perf_counter() - t0
+            if on_done:
+                on_done(r, None)
+            continue
         key = (r.scene, *r.res)
         slot = pool.acquire(key, r.cam)
         d4dgs_render(scenes[r.scene], r.cam, r.t, cfg, slot.ws, slot.out, stream)
@@ -217,13 +249,15 @@ def serve_loop(scenes: dict, requests, cfg, caps: dict, device="cuda", realtime:
             on_done(r, slot.out)
         pool.release(slot)
     t_first = min(r.arrival for r in reqs) if realtime else 0.0
-    return _summary("per-frame loop", reqs, t_first, max(r.done for r in reqs), rerendered=redo)
+    return _summary("per-frame loop", reqs, t_first, max(r.done for r in reqs), rerendered=redo,
+                    extra={"refused": refused, "cancelled": cancelled})
 
 
 def serve_batched(scenes: dict, requests, cfg, caps: dict, device="cuda", max_views: int = 16,
                   budget_bytes: int = 120 << 30, n_streams: int = 2, graph: bool = True,
-                  realtime: bool = True, on_done=None, stall_s: float = 30.0) -> ServeStats:
-    """Continuous batching (see the module docstring)."""
+                  realtime: bool = True, on_done=None, stall_s: float = 30.0, on_launch=None) -> ServeStats:
+    """Continuous batching (see the module docstring).  ``on_launch(requests)`` is called with the
+    requests of each batch right after it is launched."""
     device = torch.device(device)
     pool = WorkspacePool(cfg, scenes, caps, budget_bytes, device)
     br = BatchRenderer(cfg, device)
@@ -234,6 +268,7 @@ def serve_batched(scenes: dict, requests, cfg, caps: dict, device="cuda", max_vi
     busy = [False] * n_streams
     classes = {}
     nb, nviews_total, redo = 0, 0, 0
+    refused = cancelled = 0
     total = len(pending)
     finished = 0
     t0 = time.perf_counter()
@@ -245,7 +280,27 @@ def serve_batched(scenes: dict, requests, cfg, caps: dict, device="cuda", max_vi
         elif time.perf_counter() - last_progress > stall_s:
             raise RuntimeError(f"serving made no progress for {stall_s} s with {len(queue)} queued requests")
         while pending and (not realtime or pending[0].arrival <= now):
-            queue.append(pending.popleft())
+            r = pending.popleft()
+            if not request_valid(r):   # refused on arrival: it never joins a batch
+                r.status = D4DGS_ERR_INVALID_ARG
+                r.done = time.perf_counter() - t0
+                refused += 1
+                finished += 1
+                if on_done:
+                    on_done(r, None)
+                continue
+            queue.append(r)
+        # requests cancelled while they wait leave the queue
+        if any(r.cancelled for r in queue):
+            for r in queue:
+                if r.cancelled:
+                    r.status = STATUS_CANCELLED
+                    r.done = time.perf_counter() - t0
+                    cancelled += 1
+                    finished += 1
+                    if on_done:
+                        on_done(r, None)
+            queue = [r for r in queue if not r.cancelled]
         # retire completed batches
         still = []
         for si, ev, items in inflight:
@@ -253,6 +308,14 @@ def serve_batched(scenes: dict, requests, cfg, caps: dict, device="cuda", max_vi
                 tdone = time.perf_counter() - t0
                 for r, slot in items:
                     r.done = tdone
+                    if r.cancelled:   # cancelled while on the GPU: the image is discarded
+                        r.status = STATUS_CANCELLED
+                        cancelled += 1
+                        if on_done:
+                            on_done(r, None)
+                        pool.release(slot)
+                        finished += 1
+                        continue
                     st = d4dgs_read_stats(scenes[r.scene].n, r.cam, cfg, slot.ws, streams[si])
                     if st["status"] != D4DGS_OK:
                         redo += _redo_overflow(r, scenes[r.scene], cfg, device, slot)
@@ -291,6 +354,8 @@ def serve_batched(scenes: dict, requests, cfg, caps: dict, device="cuda", max_vi
                 ev.record(streams[si])
                 inflight.append((si, ev, batch))
                 busy[si] = True
+                if on_launch:
+                    on_launch([r for r, _ in batch])
                 nb += 1
                 nviews_total += len(batch)
                 continue
@@ -302,5 +367,6 @@ def serve_batched(scenes: dict, requests, cfg, caps: dict, device="cuda", max_vi
     t_first = min(r.arrival for r in reqs) if realtime else 0.0
     return _summary("continuous batching" + (" + CUDA graphs" if graph else ""), reqs, t_first,
                     max(r.done for r in reqs), batches=nb, mean_batch=nviews_total / max(nb, 1), rerendered=redo,
-                    extra={"workspace_gb": pool.used / 2**30, "evicted": pool.evicted,
+                    extra={"workspace_gb": pool.used / 2**30, "evicted": pool.evicted, "refused": refused,
+                           "cancelled": cancelled,
                            "slots": dict((f"{k[0]}@{k[1]}x{k[2]}", v) for k, v in pool.count.items())})

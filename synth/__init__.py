@@ -111,6 +111,7 @@ class Camera:
     cy: float
     width: int
     height: int
+    near: float = 0.2     # near plane on camera z (the renderer's config near)
 
     def __post_init__(self):
         self.R = np.ascontiguousarray(self.R, dtype=np.float32).reshape(3, 3)

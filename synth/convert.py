@@ -7,6 +7,11 @@ Sigma4D = R4 diag(s4^2) R4^T = [[U, V], [V^T, W]] (Eq. 5).  Its decomposition
 s_t = sqrt(W) and the 3D covariance Sigma3D = U - V V^T / W, which is stored
 as 3D scales and a unit quaternion (its eigen-decomposition).  Both forms
 give the same 3D Gaussian and opacity at every time (Eq. 7).  FP64 numpy.
+
+An input converter, kept beside the generators: the tests and the benchmark
+use it to build the disentangled form of a slicing-first scene.  The CUDA
+library does not import it, and neither does the oracle (which slices in its
+own code).
 """
 from __future__ import annotations
 

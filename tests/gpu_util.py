@@ -21,7 +21,8 @@ def d4():
 def render(scene, cam, t, tile=16, batch=256, bg=(0.0, 0.0, 0.0), cap=None, trim=False):
     m = d4()
     ds = m.DeviceScene.from_host(scene)
-    r = m.Renderer(scene.n, cam, tile=tile, batch=batch, bg=bg, key_capacity=cap, trim=trim)
+    r = m.Renderer(scene.n, cam, tile=tile, batch=batch, bg=bg, key_capacity=cap, trim=trim,
+                   near=getattr(cam, "near", 0.2))
     img = r.render(ds, cam, t)
     torch.cuda.synchronize()
     return r, ds, img

@@ -6,7 +6,7 @@ import numpy as np
 
 import oracle
 import synth
-from paper_2503_22159_gb300 import convert
+from synth import convert
 
 
 def test_disentangle_matches_the_oracle_slice():

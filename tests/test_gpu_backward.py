@@ -1,6 +1,13 @@
 """Gradients of the CUDA backward (through the C ABI) against the FP64 oracle
 adjoint, which is itself pinned to finite differences (test_oracle_adjoint.py).
-Needs a GPU."""
+Needs a GPU.
+
+Per element: |gpu - oracle| <= 1e-3 |oracle| + 1e-5 + slack, where slack is the
+oracle's gradient slack (oracle.backward(..., with_slack=True)): what a
+decision within FP32 reach of its threshold at some pixel (alpha against 1/255,
+the stop rule, the binary32 depth order) can change, carried through the
+chain's |Jacobian|; it is 0 for every element whose Gaussian has no such
+decision in any pixel it touches (pinned in test_oracle_slack.py)."""
 import numpy as np
 import pytest
 import torch
@@ -13,9 +20,9 @@ from tests.test_oracle_adjoint import FIELDS, fd_scene
 pytestmark = pytest.mark.gpu
 
 
-def gpu_grads(scene, cam, t, G, tile=16):
+def gpu_grads(scene, cam, t, G, tile=16, batch=256):
     m = gu.d4()
-    r, ds, img = gu.render(scene, cam, t, tile=tile)
+    r, ds, img = gu.render(scene, cam, t, tile=tile, batch=batch)
     grads = ds.zeros_like_grad()
     dl = torch.from_numpy(np.ascontiguousarray(G, dtype=np.float32)).cuda()
     m.d4dgs_render_backward(ds, cam, t, r.cfg, r.ws, dl, grads)
@@ -23,34 +30,51 @@ def gpu_grads(scene, cam, t, G, tile=16):
     return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
 
 
-def compare(got, ref, rel_l2=2e-3, frac_ok=0.995):
+def compare(got, ref, slack, max_flagged=0.10):
+    """Every element within 1e-3 relative / 1e-5 absolute plus its slack; at most max_flagged of a
+    field's elements carry a slack above a tenth of that tolerance (counted and printed)."""
     for f in FIELDS:
-        g, o = got[f].reshape(-1), ref[f].reshape(-1)
-        scale = np.abs(o).max()
-        assert scale > 0, f
-        assert np.linalg.norm(g - o) <= rel_l2 * np.linalg.norm(o), (f, np.linalg.norm(g - o) / np.linalg.norm(o))
-        ok = np.abs(g - o) <= 1e-3 * np.abs(o) + 1e-4 * scale
-        assert ok.mean() >= frac_ok, (f, ok.mean())
+        g, o, s = got[f].reshape(-1), ref[f].reshape(-1), slack[f].reshape(-1)
+        assert np.abs(o).max() > 0, f
+        tol = 1e-3 * np.abs(o) + 1e-5
+        err = np.abs(g - o)
+        bad = err > tol + s
+        assert not bad.any(), (f, int(bad.sum()), float((err / tol)[bad].max()))
+        flagged = float((s > 0.1 * tol).mean())
+        print(f"{f}: flagged {flagged:.4f}, worst err/tol where unflagged "
+              f"{float((err / tol)[s <= 0.1 * tol].max()):.3g}")
+        assert flagged <= max_flagged, (f, flagged)
 
 
-@pytest.mark.parametrize("deg,tile", [(0, 16), (3, 16), (3, 8), (1, 32)])
+@pytest.mark.parametrize("deg,tile", [(0, 16), (3, 16), (3, 8), (1, 32), (3, 32)])
 def test_backward_matches_oracle_adjoint_small(deg, tile):
     sc, cam = fd_scene(deg=deg)
     t = 0.5
     G = np.random.default_rng(3).standard_normal((cam.height, cam.width, 3))
     sc32 = synth.Scene(**{k: np.asarray(v, np.float32) for k, v in sc.arrays().items()}, sh_degree=deg)
-    ref = oracle.backward(sc32, cam, t, G)
+    ref, slack = oracle.backward(sc32, cam, t, G, with_slack=True)
     got = gpu_grads(sc32, cam, t, G, tile)
-    compare(got, ref)
+    compare(got, ref, slack)
 
 
 def test_backward_matches_oracle_adjoint_medium():
     sc = synth.make_scene(4000, 17, "box20", sh_degree=3)
     cam, t = synth.orbit(1, 200, 150, 300)[60]
     G = np.random.default_rng(4).standard_normal((cam.height, cam.width, 3))
-    ref = oracle.backward(sc, cam, t, G)
+    ref, slack = oracle.backward(sc, cam, t, G, with_slack=True)
     got = gpu_grads(sc, cam, t, G)
-    compare(got, ref, rel_l2=5e-3, frac_ok=0.99)
+    compare(got, ref, slack)
+
+
+def test_backward_matches_oracle_adjoint_bench_config():
+    """The benchmark's launch configuration: 32-px tiles, staging depth 256 (the backward's
+    3-CTAs-per-SM tile replay), SH degree 3, a multi-tile image (13 x 10 tiles)."""
+    sc = synth.make_scene(20000, 19, "box20", sh_degree=3)
+    cam, t = synth.orbit(5, 400, 300, 300)[90]
+    G = np.random.default_rng(5).standard_normal((cam.height, cam.width, 3))
+    ref, slack = oracle.backward(sc, cam, t, G, with_slack=True)
+    got = gpu_grads(sc, cam, t, G, tile=32, batch=256)
+    compare(got, ref, slack)
 
 
 def test_autograd_function_and_training_step():

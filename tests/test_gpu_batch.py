@@ -6,17 +6,20 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from tests import gpu_util as gu
 
 pytestmark = pytest.mark.gpu
 
 
+def host_scenes_small():
+    return {"A": synth.make_scene(6000, 51, "box20", sh_degree=3), "B": synth.make_scene(9000, 52, "box20", sh_degree=1)}
+
+
 def scenes_small():
     m = gu.d4()
-    a = synth.make_scene(6000, 51, "box20", sh_degree=3)
-    b = synth.make_scene(9000, 52, "box20", sh_degree=1)
-    return {"A": m.DeviceScene.from_host(a), "B": m.DeviceScene.from_host(b)}
+    return {k: m.DeviceScene.from_host(v) for k, v in host_scenes_small().items()}
 
 
 def solo(scene, cam, t, cfg):
@@ -61,10 +64,13 @@ def test_mixed_batch_equals_each_view_alone(graph, tile, trim):
 @pytest.mark.parametrize("graph", [False, True])
 def test_time_groups_equal_each_time_alone(graph):
     """Consecutive views of one scene and camera at different times form time groups (up to 4 views,
-    preprocessed together, each Gaussian read once); a view of another camera splits them.  Every
-    view's image and tile lists equal, bit for bit, those of the view rendered alone."""
+    preprocessed together, each Gaussian read once; Algorithm 1's camera-change caching and the
+    parallel multi-frame rendering of Sec. IV-C); a view of another camera splits them.  Every
+    view's image and tile lists equal, bit for bit, those of the view rendered alone, and every
+    view's image matches the oracle's render of that time."""
     m = gu.d4()
-    scenes = scenes_small()
+    hosts = host_scenes_small()
+    scenes = {k: m.DeviceScene.from_host(v) for k, v in hosts.items()}
     cfg = m.config_struct(16, 256)
     cam_a, _ = synth.orbit(7, 320, 240, 300)[40]
     cam_b, _ = synth.orbit(8, 200, 160, 300)[200]
@@ -88,6 +94,8 @@ def test_time_groups_equal_each_time_alone(graph):
         got = ws[L["tile_keys"]: L["tile_keys"] + 4 * k]
         ref = r.ws[La["tile_keys"]: La["tile_keys"] + 4 * k]
         assert k == r.stats(cam)["n_keys"] and torch.equal(got, ref), (name, t)
+        if not graph:
+            gu.compare_image(out.cpu().numpy(), oracle.render(hosts[name], cam, tt), f"group view {name} t={tt}")
 
 
 def test_batch_rejects_mixed_layout_classes():
@@ -131,3 +139,52 @@ def test_serving_returns_every_request_as_rendered_alone(mode, trim):
     assert all(r.status == 0 for r in reqs)
     for r in reqs[:16]:
         assert torch.equal(got[r.rid], solo(scenes[r.scene], r.cam, r.t, cfg)), r.rid
+
+
+def test_serving_isolates_a_poisoned_and_a_cancelled_request():
+    """Faults injected on the host stay with their request.  In a trace replayed by continuous
+    batching, one request carries a camera with a NaN principal point and another is cancelled
+    while its batch is on the GPU: the first is refused on arrival (D4DGS_ERR_INVALID_ARG, no
+    image), the second's image is discarded (cancelled), and every other request -- the views
+    batched around them included -- returns its image bit for bit as rendered alone.  The
+    per-frame loop refuses the same poisoned request and serves the rest likewise."""
+    from paper_2503_22159_gb300 import serving
+    m = gu.d4()
+    scenes = scenes_small()
+    cfg = m.config_struct(16, 256)
+    for mode in ("batched", "loop"):
+        reqs = serving.make_trace(scenes, n_requests=32, rate_hz=4000.0, seed=11,
+                                  resolutions=((160, 120), (256, 192)))
+        caps = serving.calibrate_capacity(scenes, reqs, cfg, "cuda")
+        bad = reqs[5]
+        bad.cam = synth.Camera(R=bad.cam.R, T=bad.cam.T, fx=bad.cam.fx, fy=bad.cam.fy, cx=float("nan"),
+                               cy=bad.cam.cy, width=bad.cam.width, height=bad.cam.height)
+        got, none = {}, set()
+        victim = []
+
+        def keep(r, out):
+            if out is None:
+                none.add(r.rid)
+                return
+            got[r.rid] = out.clone()
+            torch.cuda.current_stream().synchronize()
+
+        def cancel_one(batch):
+            # the first multi-view batch: cancel its second request while the batch runs
+            if not victim and len(batch) > 1:
+                victim.append(batch[1])
+                batch[1].cancelled = True
+
+        if mode == "batched":
+            st = serving.serve_batched(scenes, reqs, cfg, caps, max_views=8, budget_bytes=2 << 30, on_done=keep,
+                                       on_launch=cancel_one, realtime=False)
+            assert victim and victim[0].status == serving.STATUS_CANCELLED and victim[0].rid in none
+            assert st.extra["cancelled"] == 1 and st.mean_batch > 1.0
+        else:
+            st = serving.serve_loop(scenes, reqs, cfg, caps, on_done=keep, realtime=False)
+        torch.cuda.synchronize()
+        assert bad.status == m.D4DGS_ERR_INVALID_ARG and bad.rid in none and st.extra["refused"] == 1
+        served = [r for r in reqs if r is not bad and r not in victim]
+        assert all(r.status == 0 for r in served) and set(got) == {r.rid for r in served}
+        for r in served:
+            assert torch.equal(got[r.rid], solo(scenes[r.scene], r.cam, r.t, cfg)), (mode, r.rid)

@@ -242,6 +242,52 @@ def test_capacity_overflow_reported_without_writing_out_of_bounds():
     gu.compare_image(img.cpu().numpy(), ref, "after-grow")
 
 
+def test_near_plane_setting_matches_oracle():
+    """config near = 1.0 (the oracle's camera plane likewise): Gaussians whose time-shifted mean
+    is not beyond z = 1 are not drawn; the lists bit for bit against the mirror with that plane,
+    the image against the oracle; the frame differs from the one with the default plane."""
+    sc = synth.make_scene(3000, 27, "tiny")
+    sc.means[:, 2] = np.random.default_rng(27).uniform(0.4, 3.0, sc.n).astype(np.float32)
+    cam, t = synth.pinhole(160, 120), 0.5
+    cam.near = 1.0
+    r, _, img = gu.render(sc, cam, t)
+    b, exp = gu.expected_lists(sc, cam, t, 16)
+    gu.compare_lists(gu.gpu_lists(r, cam), b, exp)
+    gu.compare_image(img.cpu().numpy(), oracle.render(sc, cam, t), "near 1.0")
+    _, _, img02 = gu.render(sc, synth.pinhole(160, 120), t)
+    assert float((img - img02).abs().max()) > 0.05
+
+
+def test_bounded_spin_wait_gives_up_and_reports_timeout():
+    """config spin_limit = 1 on the 300k benchmark frame (hundreds of sort partitions per pass, so
+    decoupled look-backs wait): every wait gives up after one poll, the call returns, the frame
+    reports D4DGS_ERR_TIMEOUT, and no byte past the workspace is written; the next frame on the
+    same workspace with the default limit is correct."""
+    m = gu.d4()
+    w = synth.scene_workload()
+    cam, t = w.frames[150]
+    n = w.scene.n
+    ds = m.DeviceScene.from_host(w.scene)
+    impatient = m.config_struct(32, 256, spin_limit=1)
+    nbytes = m.d4dgs_workspace_bytes(n, cam, impatient, 40 * n)
+    buf = torch.full((nbytes + (1 << 20),), 0xA5, dtype=torch.uint8, device="cuda")
+    ws = buf[:nbytes]
+    out = torch.empty((cam.height, cam.width, 3), device="cuda")
+    m.d4dgs_render(ds, cam, t, impatient, ws, out)
+    torch.cuda.synchronize()
+    assert m.d4dgs_read_stats(n, cam, impatient, ws)["status"] == m.D4DGS_ERR_TIMEOUT
+    assert int((buf[nbytes:] != 0xA5).sum()) == 0
+    cfg = m.config_struct(32, 256)
+    m.d4dgs_render(ds, cam, t, cfg, ws, out)
+    torch.cuda.synchronize()
+    assert m.d4dgs_read_stats(n, cam, cfg, ws)["status"] == m.D4DGS_OK
+    assert int((buf[nbytes:] != 0xA5).sum()) == 0
+    pix = np.column_stack([np.random.default_rng(2).integers(0, cam.width, 400),
+                           np.random.default_rng(3).integers(0, cam.height, 400)])
+    ref = oracle.render(w.scene, cam, t, pixels=pix)
+    gu.compare_image(out.cpu().numpy()[pix[:, 1], pix[:, 0]], ref, "after a timed-out frame")
+
+
 def test_deterministic():
     scene, cam, t = medium(n=8000, w=160, h=120)
     _, _, a = gu.render(scene, cam, t)

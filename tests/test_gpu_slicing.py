@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import synth
-from paper_2503_22159_gb300 import convert
+from synth import convert
 from tests import gpu_util as gu
 
 pytestmark = pytest.mark.gpu

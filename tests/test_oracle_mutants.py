@@ -81,6 +81,10 @@ MUTANTS = [
      "slack += 8.0 * fmax(fabs(alpha), af) * (1.0 + cand[k].w) * cmax * T + 1e-7;", ["test_slack_within_flip_bound"]),
     ("slack on every pixel", "if (out_slack) out_slack[q] = slack;", "if (out_slack) out_slack[q] = slack + 1e-6;",
      ["test_slack_zero_away_from_thresholds"]),
+    ("gradient slack without the alpha flips", "if (cand[k].near_alpha) near_pos[nn++] = (int64_t)k;",
+     "if (0) near_pos[nn++] = (int64_t)k;", ["test_gradient_slack_covers_a_threshold_jump"]),
+    ("gradient slack through the signed Jacobian", "if (accumulate_abs) dst[f][j] += fabs(r[o]) * *w;",
+     "if (accumulate_abs) dst[f][j] += r[o] * *w;", ["test_gradient_slack_covers_a_threshold_jump"]),
     # adjoint (caught by the finite-difference pin)
     ("adjoint: colour behind ignored", "dalpha += Ti * G[ch] * (c[ch] - B[ch]);", "dalpha += Ti * G[ch] * c[ch];",
      ["test_adjoint_matches_central_differences"]),

@@ -405,3 +405,69 @@ def test_near_plane_straddle_is_flagged():
     assert g["drawn"][0] and g["err"][0, 7] == 1
     assert ref["rgb"][0].max() > 0.05
     assert ref["slack"][0] >= ref["rgb"][0].max()
+
+
+# ---------------------------------------------------------------------------
+# the gradient slack (oracle.backward with_slack)
+# ---------------------------------------------------------------------------
+
+def test_gradient_slack_zero_for_gaussians_away_from_near_decisions():
+    """Only a Gaussian that takes part in a pixel carrying image slack (alpha there at least
+    1/510 in FP64) can carry gradient slack: every other element's slack is exactly 0."""
+    sc = synth.make_scene(30000, 21, "box20", sh_degree=1)
+    cam, t = synth.orbit(4, 96, 72, 300)[150]
+    ref = oracle.render(sc, cam, t)
+    G = np.random.default_rng(1).standard_normal((cam.height, cam.width, 3))
+    _, slack = oracle.backward(sc, cam, t, G, with_slack=True)
+    g = ref["g2d"]
+    flagged = np.argwhere(ref["slack"] > 0)
+    assert len(flagged) >= 3
+    touch = np.zeros(sc.n, bool)
+    ids = np.nonzero(g["drawn"] | (g["err"][:, 7] == 2))[0]
+    for y, x in flagged:
+        dx, dy = g["u"][ids] - (x + 0.5), g["v"][ids] - (y + 0.5)
+        a, b, c = (g["conic"][ids, k] for k in range(3))
+        p = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+        touch[ids[g["opacity_t"][ids] * np.exp(np.minimum(p, 0)) >= AMIN / 2]] = True
+    any_slack = np.zeros(sc.n, bool)
+    for f, v in slack.items():
+        per = np.abs(v.reshape(sc.n, -1)).max(axis=1)
+        assert np.all(per[~touch] == 0.0), f
+        any_slack |= per > 0
+    assert any_slack.sum() >= 3
+
+
+def test_gradient_slack_covers_a_threshold_jump():
+    """Two splats on the optical axis, the front one's alpha at the four pixels around the axis
+    set 1e-9 above 1/255: a renderer that drops it there changes the back splat's gradients by
+    the jump between the FP64 gradients just above and just below the threshold; the slack at
+    the threshold covers that jump."""
+    cam = synth.pinhole(32, 32)
+
+    def scene(logit_a):
+        sc = synth.make_scene(2, 0, "tiny", sh_degree=0)
+        sc = synth.Scene(**{k: np.asarray(v, np.float64).copy() for k, v in sc.arrays().items()}, sh_degree=0)
+        sc.means[:] = [[0.0, 0.0, 2.0], [0.01, -0.02, 3.0]]
+        sc.velocity[:] = 0.0
+        sc.t_mean[:] = 0.5
+        sc.log_t_scale[:] = 30.0
+        sc.log_scales[:] = np.log(0.02)
+        sc.quats[:] = [1.0, 0.0, 0.0, 0.0]
+        sc.opacity_logit[:] = [logit_a, 0.5]
+        sc.sh[:, 0, :] = (np.array([[0.9, 0.2, 0.4], [0.1, 0.7, 0.3]]) - 0.5) / synth.SH_C0
+        return sc
+
+    g = oracle.preprocess(scene(0.0), cam, 0.5)
+    dx, dy = g["u"][0] - 16.5, g["v"][0] - 16.5
+    a, b, c = g["conic"][0]
+    p = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+    logit = lambda oh: math.log(oh / (1.0 - oh))
+    oh0 = AMIN * (1 + 1e-9) / math.exp(p)
+    G = np.ones((32, 32, 3))
+    base, slack = oracle.backward(scene(logit(oh0)), cam, 0.5, G, with_slack=True)
+    hi = oracle.backward(scene(logit(oh0 * (1 + 1e-7))), cam, 0.5, G)
+    lo = oracle.backward(scene(logit(oh0 * (1 - 1e-7))), cam, 0.5, G)
+    for f in ("sh", "opacity_logit", "means", "log_scales"):
+        jump = np.abs(hi[f][1] - lo[f][1]).max()
+        assert jump > 1e-6, f
+        assert slack[f][1].max() >= 0.99 * jump, (f, slack[f][1].max(), jump)

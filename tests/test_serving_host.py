@@ -33,13 +33,12 @@ def test_pool_admission_eviction_and_refusal(serving):
     need_s = pool._bytes(("A", 64, 64), cam_s)
     need_l = pool._bytes(("B", 256, 256), cam_l)
     pool.budget = 2 * need_s + need_l - 1          # room for two small slots, or one large + one small
+    assert need_s < need_l
     a1 = pool.acquire(("A", 64, 64), cam_s)
     a2 = pool.acquire(("A", 64, 64), cam_s)
-    assert a1 is not None and a2 is not None
-    assert pool.acquire(("A", 64, 64), cam_s) is not None or True
-    # both small slots busy: the large class has to wait
-    pool.used = 2 * need_s
-    assert pool.acquire(("B", 256, 256), cam_l) is None
+    assert a1 is not None and a2 is not None and a1 is not a2 and pool.used == 2 * need_s
+    # both small slots busy: the large class does not fit beside them and nothing is idle to evict
+    assert pool.acquire(("B", 256, 256), cam_l) is None and pool.used == 2 * need_s and pool.evicted == 0
     # one small slot idle again: it is evicted to admit the large one
     pool.release(a1)
     b = pool.acquire(("B", 256, 256), cam_l)
