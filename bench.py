@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-large", action="store_true", help="skip the 1M-Gaussian 2704x2028 line")
     p.add_argument("--no-training", action="store_true", help="skip the 4-view training step line")
+    p.add_argument("--profile", choices=["forward", "backward"], default=None,
+                   help="short run for a profiler: 3 + 2 frames of the workload (forward only, or forward + "
+                        "backward), no JSON line")
     p.add_argument("--serve-requests", type=int, default=2000)
     return p.parse_args()
 
@@ -1053,10 +1056,53 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    """A short, fixed sequence for profiler captures: the workload's frames 150..154 at 32-px tiles,
+    staging depth 256 (the autotuner's choice), each rendered (and, --profile backward, followed
+    by the backward with a seeded dL/dC); prints one line of device times."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_22159_gb300 as d4
+    w = workload(args.workload)
+    dev = torch.device("cuda", 0)
+    scene = d4.DeviceScene.from_host(w.scene, dev)
+    cfg = d4.config_struct(32, 256)
+    frames = [w.frames[150 + k] for k in range(5)]
+    cam0 = frames[0][0]
+    r = d4.Renderer(scene.n, cam0, tile=32, batch=256, device=dev)
+    for cam, t in frames:
+        r.render(scene, cam, t)
+    out = torch.empty((cam0.height, cam0.width, 3), device=dev)
+    dl = torch.randn((cam0.height, cam0.width, 3), generator=torch.Generator().manual_seed(5)).to(dev)
+    grads = scene.zeros_like_grad()
+    ms = []
+    for cam, t in frames:
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        d4.d4dgs_render(scene, cam, t, cfg, r.ws, out)
+        e[1].record()
+        if args.profile == "backward":
+            d4.d4dgs_render_backward(scene, cam, t, cfg, r.ws, dl, grads)
+        e[2].record()
+        ms.append(e)
+    torch.cuda.synchronize()
+    if r.stats(cam0)["status"] != 0:
+        raise RuntimeError("profile frame reported an error")
+    f = np.mean([a[0].elapsed_time(a[1]) for a in ms])
+    b = np.mean([a[1].elapsed_time(a[2]) for a in ms])
+    print(f"profile {args.profile}: forward {f:.3f} ms, backward {b:.3f} ms per frame (5 frames)")
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
     return run_ours(args)
 
 

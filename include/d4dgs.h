@@ -202,7 +202,9 @@ int d4dgs_render(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, con
 /* Backward of d4dgs_render (Sec. III-B-2, "differentiable projection-first
  * splatting"): given dL/dC (H x W x 3 float32 device) and the workspace of
  * the forward call with the same scene, camera, t and config, writes
- * dL/d(raw parameters) into `grad` (overwritten).  The per-tile lists are
+ * dL/d(raw parameters) into `grad` (overwritten; for SH degree 1 and 3 the
+ * coefficient gradients, like the coefficients, must be 16-byte aligned:
+ * D4DGS_ERR_INVALID_ARG otherwise).  The per-tile lists are
  * replayed back to front from the stored final T; no per-pixel lists are
  * kept. */
 int d4dgs_render_backward(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, const d4dgs_config *cfg,

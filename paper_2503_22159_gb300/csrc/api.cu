@@ -455,6 +455,8 @@ static int backward_common(const d4dgs_scene *scene, const d4dgs_camera *cam, fl
                        grad->opacity_logit, grad->sh};
         for (float *p : gp)
             if (!p || !aligned(p, 4)) return D4DGS_ERR_INVALID_ARG;
+        // the coefficient gradients are written as float4 rows (degree 1 and 3), like the scene's rows
+        if ((scene->sh_degree == 1 || scene->sh_degree == 3) && !aligned(grad->sh, 16)) return D4DGS_ERR_INVALID_ARG;
     }
     static thread_local BatchArgs b;
     Layout L;
@@ -522,6 +524,8 @@ int d4dgs_render_backward_flow(const d4dgs_scene *scene, const d4dgs_camera *cam
                        grad->opacity_logit, grad->sh};
         for (float *p : gp)
             if (!p || !aligned(p, 4)) return D4DGS_ERR_INVALID_ARG;
+        // the coefficient gradients are written as float4 rows (degree 1 and 3), like the scene's rows
+        if ((scene->sh_degree == 1 || scene->sh_degree == 3) && !aligned(grad->sh, 16)) return D4DGS_ERR_INVALID_ARG;
     }
     static thread_local BatchArgs b;
     Layout L;

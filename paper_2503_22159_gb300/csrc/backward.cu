@@ -65,9 +65,19 @@ __device__ __forceinline__ float warp_sum8(const float (&x)[8], int lane) {
 // Gaussians from the highest position down, skipping those whose
 // alpha >= 1/255 ellipse misses its block or that lie past every pixel's
 // walked range.  Per pixel the exponent is the forward's, so the same pairs
-// pass and alpha has the same bits.  A thread sums its pixels' gradients;
-// a warp reduces them once per Gaussian and adds them into shared memory;
-// each batch is flushed to the global 2D-gradient sums once per Gaussian.
+// pass and alpha has the same bits.  A thread's pixels are worked as pixel
+// pairs in packed FP32x2 (a pixel that does not take the pair contributes
+// alpha = 0: T, B and the sums stay as they are).  Since the thread's pixels
+// share dx, the geometric gradients need only three sums per thread,
+//   A0 = sum dp, A1 = sum dp dy, A2 = sum dp dy^2   (dp = dL/dalpha alpha),
+// and, over the warp, the six moments sum dp, dp dx, dp dx^2, dp dy, dp dx dy,
+// dp dy^2 (with dx per thread) plus the colour sums: one 9-value warp
+// reduction per (warp, Gaussian) into shared memory.  When a batch is
+// flushed the moments become the gradients of the 2D Gaussian, once per
+// (tile, Gaussian):
+//   dL/du = -(a M_x + b M_y), dL/dv = -(b M_x + c M_y), dL/da = -M_xx / 2,
+//   dL/db = -M_xy, dL/dc = -M_yy / 2, dL/do_hat = M_0 / o_hat
+// (M_x = sum dp dx, M_y = sum dp dy, ...; p = -(a dx^2 + c dy^2)/2 - b dx dy).
 // FLOW: the forward also composited the screen flow; dl_dflow (H x W x 2)
 // adds its terms to dL/dalpha and gives dL/d(flow) of every Gaussian.
 template <int TS, int BATCH, bool FLOW = false>
@@ -76,6 +86,7 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                       const float *__restrict__ dl_dflow) {
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
+    constexpr int NA = FLOW ? 11 : 9;   // shared sums per staged Gaussian
     const View &v = view_of(ba, 0);
     const uint32_t id_mask = v.packed ? (uint32_t)((1ull << v.id_bits) - 1ull) : 0xFFFFFFFFu;
     const uint32_t *ids = v.packed ? v.tkeys[v.tile_passes & 1] : v.tvals[v.tile_passes & 1];
@@ -91,7 +102,8 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
     __shared__ uint32_t s_m[BATCH];   // blocks the alpha >= 1/255 ellipse reaches
     __shared__ uint32_t s_id[BATCH];
     __shared__ float2 s_f[FLOW ? BATCH : 1];   // screen flow
-    __shared__ float s_acc[BATCH][FLOW ? 11 : 9];
+    // moments M_0, M_x, M_xx, M_y, M_xy, M_yy, colour sums r, g, b (, flow u, v)
+    __shared__ float s_acc[BATCH][NA];
     __shared__ uint32_t s_maxw;
 
     const int tile = blockIdx.x;
@@ -107,31 +119,36 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
     rg.x = min(rg.x, rg.y);
     const uint32_t len = rg.y - rg.x;
 
-    float2 pyf[NP];
-    float T[PX], G[PX][3], Bc[PX][3], GF[FLOW ? PX : 1][2], BF[FLOW ? PX : 1][2];
+    float2 pyf[NP], T[NP], G[NP][3], Bc[NP][3], GF[FLOW ? NP : 1][2], BF[FLOW ? NP : 1][2];
     uint32_t walked[PX];
     uint32_t tmax = 0;
 #pragma unroll
-    for (int j = 0; j < NP; j++) pyf[j] = make_float2((float)(py + 2 * j) + 0.5f, (float)(py + 2 * j + 1) + 0.5f);
-#pragma unroll
-    for (int i = 0; i < PX; i++) {
-        T[i] = 1.0f;
-        walked[i] = 0;
+    for (int j = 0; j < NP; j++) {
+        pyf[j] = make_float2((float)(py + 2 * j) + 0.5f, (float)(py + 2 * j + 1) + 0.5f);
+        T[j] = make_float2(1.0f, 1.0f);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            G[i][c] = 0.0f;
-            Bc[i][c] = v.bg[c];
+            G[j][c] = make_float2(0.0f, 0.0f);
+            Bc[j][c] = make_float2(v.bg[c], v.bg[c]);
         }
-        if (FLOW) GF[FLOW ? i : 0][0] = GF[FLOW ? i : 0][1] = BF[FLOW ? i : 0][0] = BF[FLOW ? i : 0][1] = 0.0f;
+        if (FLOW) {
+            GF[FLOW ? j : 0][0] = GF[FLOW ? j : 0][1] = make_float2(0.0f, 0.0f);
+            BF[FLOW ? j : 0][0] = BF[FLOW ? j : 0][1] = make_float2(0.0f, 0.0f);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PX; i++) {
+        walked[i] = 0;
         if (px < width && py + i < height) {
             const size_t p = (size_t)(py + i) * width + px;
-            T[i] = v.final_T[p];
+            float *tj = (i & 1) ? &T[i >> 1].y : &T[i >> 1].x;
+            *tj = v.final_T[p];
             walked[i] = min(v.n_contrib[p], len);
 #pragma unroll
-            for (int c = 0; c < 3; c++) G[i][c] = dl_drgb[3 * p + c];
+            for (int c = 0; c < 3; c++) ((i & 1) ? G[i >> 1][c].y : G[i >> 1][c].x) = dl_drgb[3 * p + c];
             if (FLOW) {
-                GF[FLOW ? i : 0][0] = dl_dflow[2 * p];
-                GF[FLOW ? i : 0][1] = dl_dflow[2 * p + 1];
+                ((i & 1) ? GF[FLOW ? i >> 1 : 0][0].y : GF[FLOW ? i >> 1 : 0][0].x) = dl_dflow[2 * p];
+                ((i & 1) ? GF[FLOW ? i >> 1 : 0][1].y : GF[FLOW ? i >> 1 : 0][1].x) = dl_dflow[2 * p + 1];
             }
         }
         tmax = max(tmax, walked[i]);
@@ -143,6 +160,8 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
     __syncthreads();
     const uint32_t maxw = s_maxw;
     const uint32_t wbit = 1u << warp;
+    const float2 one2 = make_float2(1.0f, 1.0f);
+    const float2 zero2 = make_float2(0.0f, 0.0f);
 
     // positions are 1-based: list entry rg.x + pos - 1; walk pos = maxw .. 1 in batches
     for (int32_t hi = (int32_t)maxw; hi > 0; hi -= BATCH) {
@@ -164,7 +183,7 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
             s_id[k] = id;
             if (FLOW) s_f[FLOW ? k : 0] = v.flow2d[id];
 #pragma unroll
-            for (int j = 0; j < (FLOW ? 11 : 9); j++) s_acc[k][j] = 0.0f;
+            for (int j = 0; j < NA; j++) s_acc[k][j] = 0.0f;
         }
         __syncthreads();
         if ((uint32_t)lo < wmax) {
@@ -182,76 +201,76 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
                     const float2 dx2 = f2_sub(make_float2(ua.x, ua.y), pxf2);
                     const float2 axx = f2_mul(f2_mul(make_float2(ua.z, ua.w), dx2), dx2);
                     const float2 bx = f2_mul(make_float2(bc.x, bc.y), dx2);
-                    float q[PX], p[PX], dy[PX];
+                    float2 dy[NP], qv[NP];
                     bool e[PX];
                     bool any = false;
 #pragma unroll
                     for (int j = 0; j < NP; j++) {
                         const float2 d = f2_sub(make_float2(vl.x, vl.y), pyf[j]);
                         const float2 pp = f2_fma(f2_fma(make_float2(bc.z, bc.w), d, bx), d, axx);
-                        const float2 qq = f2_add(pp, make_float2(vl.z, vl.w));
-                        p[2 * j] = pp.x; p[2 * j + 1] = pp.y;
-                        q[2 * j] = qq.x; q[2 * j + 1] = qq.y;
-                        dy[2 * j] = d.x; dy[2 * j + 1] = d.y;
+                        qv[j] = f2_add(pp, make_float2(vl.z, vl.w));
+                        dy[j] = d;
+                        e[2 * j] = pos <= walked[2 * j] && pp.x <= 0.0f && qv[j].x >= kLog2AlphaMin;
+                        e[2 * j + 1] = pos <= walked[2 * j + 1] && pp.y <= 0.0f && qv[j].y >= kLog2AlphaMin;
+                        any |= e[2 * j] | e[2 * j + 1];
                     }
-#pragma unroll
-                    for (int i = 0; i < PX; i++) {
-                        e[i] = pos <= walked[i] && p[i] <= 0.0f && q[i] >= kLog2AlphaMin;
-                        any |= e[i];
-                    }
-                    float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
-                    float gfu = 0.f, gfv = 0.f;
+                    // per thread: colour sums and the three dp moments (FLOW: flow sums), as pairs
+                    float2 sr = zero2, sg = zero2, sb = zero2, m0 = zero2, m1 = zero2, m2 = zero2;
+                    float2 sfu = zero2, sfv = zero2;
                     if (any) {
                         const float4 c = s_c[k];
-                        const float4 kk = s_k[k];
+                        const float2 cr = make_float2(c.x, c.x), cg = make_float2(c.y, c.y), cb = make_float2(c.z, c.z);
                         const float2 fl = FLOW ? s_f[FLOW ? k : 0] : make_float2(0.0f, 0.0f);
-                        const float dx = dx2.x;
 #pragma unroll
-                        for (int i = 0; i < PX; i++) {
-                            if (!e[i]) continue;
-                            const float raw = alpha_exp2(q[i]);
-                            const float alpha = fminf(kAlphaMax, raw);
-                            const float Ti = __fdividef(T[i], 1.0f - alpha);
-                            const float w = alpha * Ti;
-                            gr += w * G[i][0];
-                            gg += w * G[i][1];
-                            gbl += w * G[i][2];
-                            float dalpha =
-                                Ti * (G[i][0] * (c.x - Bc[i][0]) + G[i][1] * (c.y - Bc[i][1]) + G[i][2] * (c.z - Bc[i][2]));
-                            Bc[i][0] = alpha * c.x + (1.0f - alpha) * Bc[i][0];
-                            Bc[i][1] = alpha * c.y + (1.0f - alpha) * Bc[i][1];
-                            Bc[i][2] = alpha * c.z + (1.0f - alpha) * Bc[i][2];
+                        for (int j = 0; j < NP; j++) {
+                            const bool ex = e[2 * j], ey = e[2 * j + 1];
+                            if (!(ex | ey)) continue;
+                            const float rx = ex ? alpha_exp2(qv[j].x) : 0.0f, ry = ey ? alpha_exp2(qv[j].y) : 0.0f;
+                            const float2 al = make_float2(fminf(kAlphaMax, rx), fminf(kAlphaMax, ry));
+                            const float2 Ti = make_float2(__fdividef(T[j].x, 1.0f - al.x), __fdividef(T[j].y, 1.0f - al.y));
+                            const float2 w = f2_mul(al, Ti);
+                            sr = f2_fma(w, G[j][0], sr);
+                            sg = f2_fma(w, G[j][1], sg);
+                            sb = f2_fma(w, G[j][2], sb);
+                            const float2 d0 = f2_sub(cr, Bc[j][0]), d1 = f2_sub(cg, Bc[j][1]), d2 = f2_sub(cb, Bc[j][2]);
+                            float2 gs = f2_fma(G[j][2], d2, f2_fma(G[j][1], d1, f2_mul(G[j][0], d0)));
+                            Bc[j][0] = f2_fma(al, d0, Bc[j][0]);
+                            Bc[j][1] = f2_fma(al, d1, Bc[j][1]);
+                            Bc[j][2] = f2_fma(al, d2, Bc[j][2]);
                             if (FLOW) {
-                                const int fi = FLOW ? i : 0;
-                                gfu += w * GF[fi][0];
-                                gfv += w * GF[fi][1];
-                                dalpha += Ti * (GF[fi][0] * (fl.x - BF[fi][0]) + GF[fi][1] * (fl.y - BF[fi][1]));
-                                BF[fi][0] = alpha * fl.x + (1.0f - alpha) * BF[fi][0];
-                                BF[fi][1] = alpha * fl.y + (1.0f - alpha) * BF[fi][1];
+                                const int fj = FLOW ? j : 0;
+                                sfu = f2_fma(w, GF[fj][0], sfu);
+                                sfv = f2_fma(w, GF[fj][1], sfv);
+                                const float2 fu = f2_sub(make_float2(fl.x, fl.x), BF[fj][0]);
+                                const float2 fv = f2_sub(make_float2(fl.y, fl.y), BF[fj][1]);
+                                gs = f2_fma(GF[fj][1], fv, f2_fma(GF[fj][0], fu, gs));
+                                BF[fj][0] = f2_fma(al, fu, BF[fj][0]);
+                                BF[fj][1] = f2_fma(al, fv, BF[fj][1]);
                             }
-                            T[i] = Ti;
-                            if (raw <= kAlphaMax) {
-                                const float dp = dalpha * alpha, ddy = dy[i];
-                                go += __fdividef(dp, kk.w);
-                                gu += -dp * (kk.x * dx + kk.y * ddy);
-                                gv += -dp * (kk.y * dx + kk.z * ddy);
-                                ga += -0.5f * dp * dx * dx;
-                                gb += -dp * dx * ddy;
-                                gc += -0.5f * dp * ddy * ddy;
-                            }
+                            T[j] = Ti;
+                            // dL/dp = dL/dalpha * alpha, none through a clamped alpha
+                            float2 dp = f2_mul(f2_mul(Ti, gs), al);
+                            if (rx > kAlphaMax) dp.x = 0.0f;
+                            if (ry > kAlphaMax) dp.y = 0.0f;
+                            const float2 dpy = f2_mul(dp, dy[j]);
+                            m0 = f2_add(m0, dp);
+                            m1 = f2_add(m1, dpy);
+                            m2 = f2_fma(dpy, dy[j], m2);
                         }
                     }
                     if (__any_sync(0xFFFFFFFFu, any)) {
-                        const float x8[8] = {gu, gv, ga, gb, gc, gr, gg, gbl};
+                        const float dx = dx2.x;
+                        const float a0 = m0.x + m0.y, a1 = m1.x + m1.y;
+                        const float x8[8] = {a0, dx * a0, dx * dx * a0, a1, dx * a1, m2.x + m2.y, sr.x + sr.y, sg.x + sg.y};
                         const float tot = warp_sum8(x8, lane);
-                        const float tgo = warp_sum(go);
+                        const float tb = warp_sum(sb.x + sb.y);
                         if ((lane & 3) == 0) {   // lanes 0, 4, .., 28 hold values 0..7
                             const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                            atomicAdd(&s_acc[k][idx < 5 ? idx : idx + 1], tot);
+                            atomicAdd(&s_acc[k][idx], tot);
                         }
-                        if (lane == 0) atomicAdd(&s_acc[k][5], tgo);
+                        if (lane == 0) atomicAdd(&s_acc[k][8], tb);
                         if (FLOW) {
-                            const float tfu = warp_sum(gfu), tfv = warp_sum(gfv);
+                            const float tfu = warp_sum(sfu.x + sfu.y), tfv = warp_sum(sfv.x + sfv.y);
                             if (lane == 0) {
                                 atomicAdd(&s_acc[k][FLOW ? 9 : 0], tfu);
                                 atomicAdd(&s_acc[k][FLOW ? 10 : 0], tfv);
@@ -262,17 +281,34 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
             }
         }
         __syncthreads();
-        // flush: one set of global atomics per (tile, Gaussian) that received anything
+        // flush: moments -> gradients of (u, v, a, b, c, o_hat, r, g, b) (, flow), one set of
+        // global atomics per (tile, Gaussian) that received anything
         for (int k = threadIdx.x; k < nb; k += NT) {
-            constexpr int NA = FLOW ? 11 : 9;
             bool anyg = false;
 #pragma unroll
             for (int j = 0; j < NA; j++) anyg |= s_acc[k][j] != 0.0f;
             if (anyg) {
+                const float4 kk = s_k[k];   // a, b, c, o_hat
+                const float M0 = s_acc[k][0], Mx = s_acc[k][1], Mxx = s_acc[k][2], My = s_acc[k][3];
+                const float Mxy = s_acc[k][4], Myy = s_acc[k][5];
+                float gv[NA];
+                gv[0] = -(kk.x * Mx + kk.y * My);
+                gv[1] = -(kk.y * Mx + kk.z * My);
+                gv[2] = -0.5f * Mxx;
+                gv[3] = -Mxy;
+                gv[4] = -0.5f * Myy;
+                gv[5] = __fdividef(M0, kk.w);
+                gv[6] = s_acc[k][6];
+                gv[7] = s_acc[k][7];
+                gv[8] = s_acc[k][8];
+                if (FLOW) {
+                    gv[FLOW ? 9 : 0] = s_acc[k][FLOW ? 9 : 0];
+                    gv[FLOW ? 10 : 0] = s_acc[k][FLOW ? 10 : 0];
+                }
                 float *dst = g2 + (size_t)s_id[k] * kG2;
 #pragma unroll
                 for (int j = 0; j < NA; j++)
-                    if (s_acc[k][j] != 0.0f) atomicAdd(dst + j, s_acc[k][j]);
+                    if (gv[j] != 0.0f) atomicAdd(dst + j, gv[j]);
             }
         }
         __syncthreads();
@@ -366,10 +402,12 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
         if (ACC) *p += v;
         else *p = v;
     };
-    const float *G = g2 + (size_t)i * kG2;
-    const float gU = G[0], gV = G[1], gA = G[2], gB = G[3], gCc = G[4], gO = G[5];
-    const float gcol[3] = {G[6], G[7], G[8]};
-    const float gFu = G[9], gFv = G[10];   // screen flow (zero unless the frame had a flow channel)
+    // the 2D gradient sums (12 floats, 16-byte aligned): three vector loads
+    const float4 *G4 = reinterpret_cast<const float4 *>(g2 + (size_t)i * kG2);
+    const float4 Ga = G4[0], Gb = G4[1], Gc = G4[2];
+    const float gU = Ga.x, gV = Ga.y, gA = Ga.z, gB = Ga.w, gCc = Gb.x, gO = Gb.y;
+    const float gcol[3] = {Gb.z, Gb.w, Gc.x};
+    const float gFu = Gc.y, gFv = Gc.z;   // screen flow (zero unless the frame had a flow channel)
     // ---- forward quantities (the decisions use the forward's rounded operations)
     const float tau = __fsub_rn(t, s.t_mean[i]);
     const float vel[3] = {s.velocity[3 * i], s.velocity[3 * i + 1], s.velocity[3 * i + 2]};
@@ -485,18 +523,58 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
     sh_basis_and_grad<DEG>(d[0], d[1], d[2], Yb, dY);
     const float *shp = s.sh + (size_t)i * 3 * K;
     float dd[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr ((3 * K) % 4 == 0) {
+        // 16-byte aligned rows (degree 1 and 3): the coefficients and their gradients as float4s;
+        // flat index f = 3 k + ch.  Pass 1: the raw colour (clamp decisions); pass 2 (the row again,
+        // from L1): the gradients of the coefficients and of the view direction.
+        const float4 *sh4 = reinterpret_cast<const float4 *>(shp);
+        float4 *gsh4 = reinterpret_cast<float4 *>(gsh);
+        float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-    for (int ch = 0; ch < 3; ch++) {
-        float raw = 0.5f;
+        for (int j = 0; j < (3 * K) / 4; j++) {
+            const float4 w4 = __ldg(sh4 + j);
+            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-        for (int k = 0; k < K; k++) raw = fmaf(shp[3 * k + ch], Yb[k], raw);
-        const float gch = raw < 0.0f ? 0.0f : gcol[ch];
+            for (int e = 0; e < 4; e++) raw[(4 * j + e) % 3] = fmaf(w[e], Yb[(4 * j + e) / 3], raw[(4 * j + e) % 3]);
+        }
+        float gch[3];
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            put(&gsh[3 * k + ch], gch * Yb[k]);
-            dd[0] += gch * shp[3 * k + ch] * dY[k][0];
-            dd[1] += gch * shp[3 * k + ch] * dY[k][1];
-            dd[2] += gch * shp[3 * k + ch] * dY[k][2];
+        for (int ch = 0; ch < 3; ch++) gch[ch] = raw[ch] < 0.0f ? 0.0f : gcol[ch];
+#pragma unroll
+        for (int j = 0; j < (3 * K) / 4; j++) {
+            const float4 w4 = __ldg(sh4 + j);
+            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+            float o[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int k = (4 * j + e) / 3, ch = (4 * j + e) % 3;
+                o[e] = gch[ch] * Yb[k];
+                const float gw = gch[ch] * w[e];
+                dd[0] += gw * dY[k][0];
+                dd[1] += gw * dY[k][1];
+                dd[2] += gw * dY[k][2];
+            }
+            float4 ov = make_float4(o[0], o[1], o[2], o[3]);
+            if (ACC) {
+                const float4 prev = gsh4[j];
+                ov = make_float4(prev.x + ov.x, prev.y + ov.y, prev.z + ov.z, prev.w + ov.w);
+            }
+            gsh4[j] = ov;
+        }
+    } else {
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; k++) raw = fmaf(shp[3 * k + ch], Yb[k], raw);
+            const float gch = raw < 0.0f ? 0.0f : gcol[ch];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                put(&gsh[3 * k + ch], gch * Yb[k]);
+                dd[0] += gch * shp[3 * k + ch] * dY[k][0];
+                dd[1] += gch * shp[3 * k + ch] * dY[k][1];
+                dd[2] += gch * shp[3 * k + ch] * dY[k][2];
+            }
         }
     }
     const float ddot = dd[0] * d[0] + dd[1] * d[1] + dd[2] * d[2];
