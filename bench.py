@@ -356,6 +356,12 @@ def run_time_groups(args, dev, d4, w, scene, cfg, cap, peaks):
     pre_single = timed(single_pre) / B
     all_group = timed(lambda: br.render(views, stream)) / B
     all_single = timed(single_all) / B
+    # the colour cache (SH towards the static mean, once per group): an approximation, timed beside
+    cfg_c = d4.config_struct(int(cfg.tile), int(cfg.batch), trim=bool(cfg.trim), colour_cache=True)
+    br_c = d4.BatchRenderer(cfg_c, dev)
+    views_c = [(sc, c, t, ws, out) for sc, c, t, ws, out in views]
+    pre_cache = timed(lambda: br_c.render_stages(views_c, 1, stream)) / B
+    all_cache = timed(lambda: br_c.render(views_c, stream)) / B
     for sc, c, t, ws, out in views:
         if d4.d4dgs_read_stats(sc.n, c, cfg, ws)["status"] != 0:
             raise RuntimeError("time-group frame reported an error")
@@ -364,9 +370,13 @@ def run_time_groups(args, dev, d4, w, scene, cfg, cap, peaks):
     read_b, write_b = n * (64 + sh_bytes), n * 64
     gbs = lambda byts, ms: byts / (ms * 1e-3) / 1e9
     return {"views": B, "camera_frame": k0, "times": [float(t) for t in times],
-            "preprocess_us_per_frame": {"group": 1e3 * pre_group, "single": 1e3 * pre_single},
-            "frame_us": {"group": 1e3 * all_group, "single": 1e3 * all_single},
-            "frames_per_s": {"group": 1e3 / all_group, "single": 1e3 / all_single},
+            "preprocess_us_per_frame": {"group": 1e3 * pre_group, "single": 1e3 * pre_single,
+                                        "group_colour_cache": 1e3 * pre_cache},
+            "frame_us": {"group": 1e3 * all_group, "single": 1e3 * all_single, "group_colour_cache": 1e3 * all_cache},
+            "frames_per_s": {"group": 1e3 / all_group, "single": 1e3 / all_single,
+                             "group_colour_cache": 1e3 / all_cache},
+            "colour_cache_tolerance": "approximation: max-abs 0.05, mean-abs 0.005 against the definition "
+                                      "(tests/test_gpu_batch.py::test_colour_cache_time_group)",
             "preprocess_roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
                                     "bytes_per_frame_group": read_b / B + write_b,
                                     "bytes_per_frame_single": read_b + write_b,

@@ -95,7 +95,12 @@ typedef struct {
  * spin_limit: polls before a bounded device spin-wait (the sort's decoupled
  * look-back) gives up and the frame reports D4DGS_ERR_TIMEOUT (0 selects
  * 2^20; a small value makes the waits give up early, for failure-detection
- * tests). */
+ * tests); colour_cache: 0 evaluates each Gaussian's SH colour in the
+ * direction of its time-shifted mean (the definition), 1 in the direction of
+ * its static mean -- an approximation that makes the colour depend on the
+ * camera only, so the views of a time group (one scene and camera, several
+ * times; Algorithm 1's camera-change caching) share one evaluation of it
+ * (disentangled scenes; the slicing-first form ignores it). */
 typedef struct {
     int32_t tile;
     int32_t batch;
@@ -103,6 +108,7 @@ typedef struct {
     int32_t trim;
     float near;
     uint32_t spin_limit;
+    int32_t colour_cache;
 } d4dgs_config;
 
 /* Counters read back after a frame (host struct). */

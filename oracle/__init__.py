@@ -58,7 +58,8 @@ def build(force: bool = False) -> Path:
 class _Scene(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)] + [
         (k, c_double_p) for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale",
-                                  "quats", "opacity_logit", "sh", "cov3d", "in_err")]
+                                  "quats", "opacity_logit", "sh", "cov3d", "in_err")] + [
+        ("colour_static", ctypes.c_int32)]
 
 
 class _SceneF32(ctypes.Structure):
@@ -163,8 +164,9 @@ class _Keep:
         return _p(a, ctypes.c_double)
 
 
-def _scene64(scene, keep: _Keep, cov3d=None, in_err=None):
+def _scene64(scene, keep: _Keep, cov3d=None, in_err=None, colour_static=False):
     s = _Scene()
+    s.colour_static = 1 if colour_static else 0
     s.n = scene.n
     s.sh_degree = scene.sh_degree
     for k in ("means", "t_mean", "velocity", "log_scales", "log_t_scale", "quats", "opacity_logit", "sh"):
@@ -200,17 +202,20 @@ def quat_to_rot(q) -> np.ndarray:
     return R.reshape(3, 3)
 
 
-def preprocess(scene, cam, t: float, temporal_cull: bool = True, cov3d=None, in_err=None) -> dict:
+def preprocess(scene, cam, t: float, temporal_cull: bool = True, cov3d=None, in_err=None,
+               colour_static: bool = False) -> dict:
     """FP64 dynamic 2D Gaussians at time t (dict of numpy arrays, length N), with ``err``
     (N x 16): what a binary32 evaluation makes of each Gaussian (oracle.c, orc_preprocess):
     u, v, Z, o_hat and the inverse of Sigma' of its binary32 footprint, the mode (0 both
     draw it, 1 only the definition, 2 only binary32), in cov3d mode a-priori bounds instead.
     ``cov3d`` (N x 6) replaces scales and quaternions; ``in_err`` (N x 10, with ``cov3d``)
     bounds the FP32 error of the mean at t (3), the relative error of the opacity at t (1)
-    and of Sigma3D (6) that an FP32 evaluation starts from."""
+    and of Sigma3D (6) that an FP32 evaluation starts from.  ``colour_static``: the SH colour in the
+    direction of the static mean instead of the time-shifted one (the per-camera colour cache of the
+    time-grouped renderer, an approximation of the definition)."""
     n = scene.n
     keep = _Keep()
-    s = _scene64(scene, keep, cov3d, in_err)
+    s = _scene64(scene, keep, cov3d, in_err, colour_static)
     c = _camera64(cam)
     out = dict(drawn=np.zeros(n, np.int32), u=np.zeros(n), v=np.zeros(n), depth=np.zeros(n),
                conic=np.zeros((n, 3)), cov2d=np.zeros((n, 3)), opacity_t=np.zeros(n),
@@ -278,9 +283,11 @@ def render_g2d(g: dict, cam, pixels=None, bg=(0.0, 0.0, 0.0)) -> dict:
 
 
 def render(scene, cam, t: float, pixels=None, bg=(0.0, 0.0, 0.0), temporal_cull: bool = True,
-           cov3d=None, in_err=None) -> dict:
-    """Render one frame (or the listed pixels) of ``scene`` at time ``t`` in FP64."""
-    g = preprocess(scene, cam, t, temporal_cull=temporal_cull, cov3d=cov3d, in_err=in_err)
+           cov3d=None, in_err=None, colour_static: bool = False) -> dict:
+    """Render one frame (or the listed pixels) of ``scene`` at time ``t`` in FP64 (``colour_static``:
+    the colour-cache approximation, SH evaluated towards the static mean)."""
+    g = preprocess(scene, cam, t, temporal_cull=temporal_cull, cov3d=cov3d, in_err=in_err,
+                   colour_static=colour_static)
     out = render_g2d(g, cam, pixels=pixels, bg=bg)
     out["g2d"] = g
     return out

@@ -71,6 +71,8 @@ typedef struct {
     const double *cov3d;         /* optional N x 6 (xx,xy,xz,yy,yz,zz): replaces scales+quats */
     const double *in_err;        /* optional N x 10, with cov3d: bounds on the FP32 error of the inputs an
                                     FP32 evaluation starts from (see fp32_bounds) */
+    int32_t colour_static;       /* 1: SH colour in the direction of the static mean mu (the per-camera
+                                    colour cache, an approximation); 0: of the time-shifted mean mu(t) */
 } orc_scene;
 
 typedef struct {
@@ -566,7 +568,9 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, double t, int te
         out->lambda_max[i] = mid + sqrt(fmax(0.1, mid * mid - det));
         out->u[i] = cam->fx * xz + cam->cx;
         out->v[i] = cam->fy * yz + cam->cy;
-        double d[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};
+        /* view direction of the colour: the time-shifted mean, or (colour cache) the static one */
+        const double *cm = sc->colour_static ? sc->means + 3 * (size_t)i : m;
+        double d[3] = {cm[0] - campos[0], cm[1] - campos[1], cm[2] - campos[2]};
         double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         d[0] /= dn; d[1] /= dn; d[2] /= dn;
         double Y[16];

@@ -115,13 +115,14 @@ def camera_struct(cam) -> _abi.d4dgs_camera:
 
 
 def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0), trim: bool = False, near: float = 0.2,
-                  spin_limit: int = 0) -> _abi.d4dgs_config:
+                  spin_limit: int = 0, colour_cache: bool = False) -> _abi.d4dgs_config:
     g = _abi.d4dgs_config()
     g.tile, g.batch = int(tile), int(batch)
     g.bg[:] = [float(x) for x in bg]
     g.trim = 1 if trim else 0
     g.near = float(near)
     g.spin_limit = int(spin_limit)
+    g.colour_cache = 1 if colour_cache else 0
     return g
 
 

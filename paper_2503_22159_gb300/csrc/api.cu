@@ -34,6 +34,7 @@ bool valid_config(const d4dgs_config *g) {
     if (g->tile != 8 && g->tile != 16 && g->tile != 32) return false;
     if (g->batch != 64 && g->batch != 128 && g->batch != 256) return false;
     if (g->trim != 0 && g->trim != 1) return false;
+    if (g->colour_cache != 0 && g->colour_cache != 1) return false;
     for (int i = 0; i < 3; i++)
         if (!isfinite(g->bg[i])) return false;
     return isfinite(g->near) && g->near >= 0.0f;
@@ -168,6 +169,7 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     for (int i = 0; i < 3; i++) x.bg[i] = cfg.bg[i];
     x.cam = make_cam_args(&cam, cfg.tile, cfg.near > 0.0f ? cfg.near : kNear);
     x.spin_limit = cfg.spin_limit ? cfg.spin_limit : kSpinLimit;
+    x.colour_cache = cfg.colour_cache;
     x.out_rgb = out_rgb;
     x.zero_base = at<char>(ws, 0);
     x.zero_bytes = L.zero_end;
@@ -216,7 +218,7 @@ static bool same_scene_and_camera(const View &a, const View &b) {
            a.log_scales == b.log_scales && a.log_t_scale == b.log_t_scale && a.quats == b.quats &&
            a.means4 == b.means4 && a.log_scales4 == b.log_scales4 && a.quat_l == b.quat_l && a.quat_r == b.quat_r &&
            a.opacity_logit == b.opacity_logit && a.sh == b.sh && a.n == b.n && a.sh_degree == b.sh_degree &&
-           memcmp(&a.cam, &b.cam, sizeof(CamArgs)) == 0;
+           a.colour_cache == b.colour_cache && memcmp(&a.cam, &b.cam, sizeof(CamArgs)) == 0;
 }
 
 bool finish_batch(BatchArgs *b) {
@@ -231,7 +233,7 @@ bool finish_batch(BatchArgs *b) {
     for (int i = 0; i < b->nviews; i++) {
         View &v = b->v[i];
         if (v.packed != b->packed || v.tile_passes != b->tile_passes || v.cam.tile != b->tile || v.trim_on != b->trim_on ||
-            v.kind != b->v[0].kind)
+            v.kind != b->v[0].kind || v.colour_cache != b->v[0].colour_cache)
             return false;
         // time groups: a view joins the group of the view before it when it shares its scene and camera
         if (lead >= 0 && b->v[lead].group_size < kMaxGroup && same_scene_and_camera(b->v[lead], v)) {

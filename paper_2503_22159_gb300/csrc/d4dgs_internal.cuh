@@ -136,6 +136,7 @@ struct View {
     int32_t id_bits, col_bits, packed, tile_passes, ntiles;
     int32_t trim_on;                 // config trim: 1 rectangles cut per column
     uint32_t spin_limit;             // polls before a look-back gives up (config spin_limit)
+    int32_t colour_cache;            // config colour_cache: SH colour towards the static mean
     int32_t tile_shift[3];
     uint32_t tile_mask[3];
     int32_t parts_depth, parts_dup, parts_tile;

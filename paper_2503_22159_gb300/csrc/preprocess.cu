@@ -323,8 +323,11 @@ __device__ __forceinline__ bool footprint_slicing(const View &vw, int i, Footpri
 // difference grid (2D differences of the rectangle, or per-column
 // differences of the cut columns), and counts it in the shared depth-digit
 // histogram.
-template <int DEG, int KIND>
-__device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *hist, uint32_t &nvis, int *sgrid) {
+// CACHE (config colour_cache): cc holds the Gaussian's colour once a view of its time group has
+// evaluated it (towards the static mean, the same for every view of the group) for the group's next views.
+template <int DEG, int KIND, bool CACHE>
+__device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *hist, uint32_t &nvis, int *sgrid,
+                                               float4 &cc) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const CamArgs &c = vw.cam;
     const float tilef = (float)c.tile;
@@ -399,13 +402,25 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
             const float w01 = __fmul_rn(s01, s01);
             const float det_c = __fadd_rn(__fmaf_rn(s00, s11, -w01), __fmaf_rn(-s01, s01, w01));
             const float inv_det = 1.0f / det_c;
-            // ---- view-dependent colour in the direction of the shifted mean
-            float dx = m0 - c.campos[0], dy = m1 - c.campos[1], dz = m2 - c.campos[2];
+            // ---- view-dependent colour in the direction of the shifted mean (colour cache: of the
+            // static mean, evaluated once per time group)
+            constexpr bool cache = KIND == 0 && CACHE;
+            float col[3] = {0.5f, 0.5f, 0.5f};
+            if (cache && cc.w != 0.0f) {
+                col[0] = cc.x; col[1] = cc.y; col[2] = cc.z;
+            } else {
+            float dx, dy, dz;
+            if (cache) {
+                dx = __ldg(vw.means + 3 * i) - c.campos[0];
+                dy = __ldg(vw.means + 3 * i + 1) - c.campos[1];
+                dz = __ldg(vw.means + 3 * i + 2) - c.campos[2];
+            } else {
+                dx = m0 - c.campos[0]; dy = m1 - c.campos[1]; dz = m2 - c.campos[2];
+            }
             const float inv_n = rsqrtf(dx * dx + dy * dy + dz * dz);
             dx *= inv_n; dy *= inv_n; dz *= inv_n;
             float Yb[16];
             sh_basis<DEG>(dx, dy, dz, Yb);
-            float col[3] = {0.5f, 0.5f, 0.5f};
             const float *shp = vw.sh + (size_t)i * (3 * K);
             if constexpr ((3 * K) % 4 == 0) {
                 // 16-byte aligned rows (degree 1 and 3): vector loads
@@ -429,6 +444,8 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
                     col[1] = fmaf(__ldg(shp + 3 * k + 1), Yb[k], col[1]);
                     col[2] = fmaf(__ldg(shp + 3 * k + 2), Yb[k], col[2]);
                 }
+            }
+            if (cache) cc = make_float4(col[0], col[1], col[2], 1.0f);
             }
             r0 = make_float4(u, v, s11 * inv_det, -s01 * inv_det);
             r1 = make_float4(s00 * inv_det, oh, Z, rf);
@@ -480,7 +497,8 @@ __device__ __forceinline__ void flush_view(const View &v, uint32_t *hist, uint32
 // of them fit, tile-count grid.  The per-view arithmetic is the same as for a
 // view alone, so a grouped view's outputs equal the ungrouped ones bit for bit.
 // KIND: 0 disentangled, 1 slicing-first (every view of a launch has the same kind).
-template <int KIND>
+// CACHE: config colour_cache (shared by every view of a launch).
+template <int KIND, bool CACHE>
 __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restrict__ ba, int smem_cells) {
     __shared__ uint32_t hist[kMaxGroup][4 * kRadix];
     __shared__ int32_t s_chunk;
@@ -524,15 +542,16 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restri
         const View &l = view_of(ba, lead);
         const int i = (chunk - l.chunk_base) * kPreChunk + (int)threadIdx.x;
         const int gs = l.group_size;
+        float4 cc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // colour cache of this Gaussian (w = 1: valid)
         for (int b = 0; b < gs; b++) {
             const View &v = view_of(ba, lead + b);
             int *sg = slot_grid(lead, b);
             if (i < v.n) {
                 switch (v.sh_degree) {
-                    case 0: preprocess_one<0, KIND>(v, i, hist[b], nvis[b], sg); break;
-                    case 1: preprocess_one<1, KIND>(v, i, hist[b], nvis[b], sg); break;
-                    case 2: preprocess_one<2, KIND>(v, i, hist[b], nvis[b], sg); break;
-                    default: preprocess_one<3, KIND>(v, i, hist[b], nvis[b], sg); break;
+                    case 0: preprocess_one<0, KIND, CACHE>(v, i, hist[b], nvis[b], sg, cc); break;
+                    case 1: preprocess_one<1, KIND, CACHE>(v, i, hist[b], nvis[b], sg, cc); break;
+                    case 2: preprocess_one<2, KIND, CACHE>(v, i, hist[b], nvis[b], sg, cc); break;
+                    default: preprocess_one<3, KIND, CACHE>(v, i, hist[b], nvis[b], sg, cc); break;
                 }
             }
         }
@@ -604,10 +623,12 @@ cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cud
     // 6144 cells (e.g. 1352x1014 at 32-px tiles) are aggregated in shared memory
     constexpr int kSmemCells = 6144;
     const cudaError_t e =
-        args.v[0].kind == 0
-            ? launch_chained(preprocess_kernel<0>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
+        args.v[0].kind == 1 ? launch_chained(preprocess_kernel<1, false>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
+                                             (const char *)batch_area, kSmemCells)
+        : args.v[0].colour_cache
+            ? launch_chained(preprocess_kernel<0, true>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
                              (const char *)batch_area, kSmemCells)
-            : launch_chained(preprocess_kernel<1>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
+            : launch_chained(preprocess_kernel<0, false>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
                              (const char *)batch_area, kSmemCells);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -188,3 +188,34 @@ def test_serving_isolates_a_poisoned_and_a_cancelled_request():
         assert all(r.status == 0 for r in served) and set(got) == {r.rid for r in served}
         for r in served:
             assert torch.equal(got[r.rid], solo(scenes[r.scene], r.cam, r.t, cfg)), (mode, r.rid)
+
+
+def test_colour_cache_time_group():
+    """config colour_cache (Algorithm 1's per-camera caching carried to the colour): SH evaluated
+    towards the static mean, once per time group.  Each grouped view matches the oracle's render with
+    the same colour rule within the image tolerance and equals the same view rendered alone bit for
+    bit; against the definition (colour towards the time-shifted mean) it stays within the stated
+    approximation bound, max-abs 0.05 and mean-abs 0.005 (on the 300k benchmark frames the oracle
+    measures at most 0.023 and 0.0019)."""
+    m = gu.d4()
+    hosts = host_scenes_small()
+    sc = hosts["A"]
+    ds = m.DeviceScene.from_host(sc)
+    cfg = m.config_struct(16, 256, colour_cache=True)
+    cam, _ = synth.orbit(7, 320, 240, 300)[40]
+    times = [float(np.float32(t)) for t in (0.05, 0.3, 0.55, 0.8)]
+    views = []
+    for t in times:
+        ws = torch.empty(m.d4dgs_workspace_bytes(sc.n, cam, cfg, 40 * sc.n), dtype=torch.uint8, device="cuda")
+        views.append((ds, cam, t, ws, torch.full((cam.height, cam.width, 3), -1.0, device="cuda")))
+    m.BatchRenderer(cfg).render(views)
+    torch.cuda.synchronize()
+    for (_, _, t, ws, out) in views:
+        assert m.d4dgs_read_stats(sc.n, cam, cfg, ws)["status"] == 0
+        img = out.cpu().numpy()
+        gu.compare_image(img, oracle.render(sc, cam, t, colour_static=True), f"colour cache t={t}")
+        exact = oracle.render(sc, cam, t)["rgb"]
+        assert np.abs(img - exact).max() <= 0.05 and np.abs(img - exact).mean() <= 0.005
+        r = m.Renderer(sc.n, cam, tile=16, batch=256, key_capacity=40 * sc.n)
+        r.cfg = cfg
+        assert torch.equal(r.render(ds, cam, t), out)

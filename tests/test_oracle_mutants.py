@@ -44,8 +44,8 @@ MUTANTS = [
      "double x = q[0], y = q[1], z = q[2], w = q[3];", ["test_quat_to_rot_matches_scipy"]),
     ("SH degree-1 sign", "Y[1] = -c1 * y;", "Y[1] = c1 * y;", ["test_sh_basis_matches_scipy"]),
     ("SH direction of the static mean",
-     "double d[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};",
-     "double d[3] = {sc->means[3 * (size_t)i] - campos[0], sc->means[3 * (size_t)i + 1] - campos[1], sc->means[3 * (size_t)i + 2] - campos[2]};",
+     "const double *cm = sc->colour_static ? sc->means + 3 * (size_t)i : m;",
+     "const double *cm = sc->means + 3 * (size_t)i;",
      ["test_time_shift_equivalence"]),
     ("colour not clamped at zero", "out->rgb[3 * (size_t)i + ch] = fmax(0.0, s + 0.5);",
      "out->rgb[3 * (size_t)i + ch] = s + 0.5;", ["test_negative_colour_is_clamped"]),

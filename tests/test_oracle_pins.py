@@ -690,3 +690,17 @@ def test_split_nothing_below_thresholds():
     out, ss, tt = oracle.split_scene(sc, stats, np.zeros((30, 4)), 0.5, 0.5, -10, -10)
     assert not ss.any() and not tt.any() and out.n == 30
     np.testing.assert_array_equal(out.means, sc.means.astype(np.float64))
+
+
+def test_colour_static_mode_reduces_to_the_definition_without_motion():
+    """The colour-cache mode evaluates SH towards the static mean: identical to the definition when
+    no Gaussian moves (mu(t) = mu), different once they do (the approximation is real)."""
+    sc = synth.make_scene(300, 61, "tiny", sh_degree=3)
+    cam = synth.pinhole(48, 40)
+    moving = oracle.render(sc, cam, 0.8)
+    moving_c = oracle.render(sc, cam, 0.8, colour_static=True)
+    assert np.abs(moving["rgb"] - moving_c["rgb"]).max() > 1e-4
+    sc.velocity[:] = 0.0
+    still = oracle.render(sc, cam, 0.8)
+    still_c = oracle.render(sc, cam, 0.8, colour_static=True)
+    assert np.array_equal(still["rgb"], still_c["rgb"])
