@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--tile", default="auto", help="8, 16, 32 or auto (autotuner sweep)")
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--trim", action="store_true", help="cut binning rectangles per column (--tile auto decides)")
+    p.add_argument("--binning", type=int, default=0, choices=(0, 1, 2),
+                   help="config binning of the main frames: 0 library choice, 1 column path, 2 direct")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-e2e", action="store_true")
@@ -608,8 +610,11 @@ def launch_names(d4, n, cam, cfg, ws):
     if (L["tiles_x"] + 1) * (L["tiles_y"] + 1) > 6144:
         names.append("tilecount")
     names += [f"depth_pass_{p}" for p in range(4)]
-    names.append("emit")
-    names += [f"row_pass_{p}" for p in range(1, L["tile_passes"])]
+    if L["tile_passes"] == 1:   # direct binning
+        names += ["dir_count", "dir_scan", "dir_emit"]
+    else:
+        names.append("emit")
+        names += [f"row_pass_{p}" for p in range(1, L["tile_passes"])]
     names.append("blend")
     return names, L
 
@@ -658,6 +663,12 @@ def run_kernel_times(dev, d4, w, scene, cfg, r, frames, peaks, alu_peak, evals_p
         bytes_of[f"depth_pass_{p}"] = (n * 16, "key + id read and written")
     for p in range(1, L["tile_passes"]):
         bytes_of[f"row_pass_{p}"] = (K * 2 * pair_b, "pair read and written")
+    ntiles = L["tiles_x"] * L["tiles_y"]
+    cm = 4 * ntiles * ((n + 1023) // 1024)   # the (1024-Gaussian partition, tile) count matrix
+    bytes_of["dir_count"] = (n * (16 + trim) + cm, "depth order, rectangle, count (+ cuts) read; count matrix written")
+    bytes_of["dir_scan"] = (3 * cm + ntiles * 8, "count matrix read twice and rewritten as offsets; ranges read")
+    bytes_of["dir_emit"] = (n * (16 + trim) + cm + K * pair_b,
+                            "depth order, rectangle, count (+ cuts) and offsets read; a pair written")
     kern = {}
     for name, t_ms in zip(names, ms):
         e = {"ms": float(t_ms)}
@@ -674,7 +685,7 @@ def run_kernel_times(dev, d4, w, scene, cfg, r, frames, peaks, alu_peak, evals_p
                         "ops": f"{FP32_OPS_PER_PAIR} per (pixel, Gaussian) pair the kernel evaluates",
                         "frac_tile_walk": FP32_OPS_PER_PAIR * work_pf / (t_ms * 1e-3) / 1e12 / alu_peak}
         kern[name] = e
-    binning = [k for k in names if k.startswith(("tilecount", "depth_pass", "emit", "row_pass"))]
+    binning = [k for k in names if k.startswith(("tilecount", "depth_pass", "emit", "row_pass", "dir_"))]
     return {"frames": len(frames), "launches": names, "kernels": kern,
             "binning_ms": float(sum(kern[k]["ms"] for k in binning)),
             "sum_ms": float(ms.sum()), "keys_per_frame": K,
@@ -862,14 +873,14 @@ def run_ours(args):
         (tile, batch, trim), tune_table = autotune.tune(scene, probe, device=dev, force=True)
         args.tile, args.batch, args.trim = tile, batch, trim
     args.tile = int(args.tile)
-    cfg = d4.config_struct(args.tile, args.batch, trim=args.trim)
+    cfg = d4.config_struct(args.tile, args.batch, trim=args.trim, binning=args.binning)
     cam0 = w.frames[0][0]
     K, W = args.steps, args.warmup
     order = rank_frames(rank, world, nf, W + K)
 
     # size the key capacity on this rank's frames (untimed)
     r = d4.Renderer(scene.n, cam0, tile=args.tile, batch=args.batch, key_capacity=160 * scene.n, device=dev,
-                    trim=args.trim)
+                    trim=args.trim, binning=args.binning)
     max_keys = 0
     for fi in sorted(set(order)):
         cam, t = w.frames[fi]

@@ -115,7 +115,9 @@ def camera_struct(cam) -> _abi.d4dgs_camera:
 
 
 def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0), trim: bool = False, near: float = 0.2,
-                  spin_limit: int = 0, colour_cache: bool = False) -> _abi.d4dgs_config:
+                  spin_limit: int = 0, colour_cache: bool = False, binning: int = 0) -> _abi.d4dgs_config:
+    """binning: 0 the library's choice (column), 1 column buckets + row passes, 2 straight into the
+    tiles' lists (<= 2048 tiles)."""
     g = _abi.d4dgs_config()
     g.tile, g.batch = int(tile), int(batch)
     g.bg[:] = [float(x) for x in bg]
@@ -123,6 +125,7 @@ def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0), trim: bo
     g.near = float(near)
     g.spin_limit = int(spin_limit)
     g.colour_cache = 1 if colour_cache else 0
+    g.binning = int(binning)
     return g
 
 
@@ -452,9 +455,10 @@ class BatchRenderer:
 
     @staticmethod
     def _class_key(host: torch.Tensor):
-        # nviews, tile, batch, packed, tile_passes, column capacity, trim (leading int32 fields of the encoded batch)
-        head = host[:28].view(torch.int32).tolist()
-        return (head[1], head[2], head[3], head[4], head[5], head[6])
+        # nviews, tile, batch, packed, tile_passes, column capacity, trim, tile and grid-cell capacities
+        # (leading int32 fields of the encoded batch)
+        head = host[:36].view(torch.int32).tolist()
+        return tuple(head[1:9])
 
 
 class Renderer:
@@ -462,9 +466,10 @@ class Renderer:
     capacity when a frame reports D4DGS_ERR_CAPACITY."""
 
     def __init__(self, n: int, cam, tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0),
-                 key_capacity: int | None = None, device="cuda", trim: bool = False, near: float = 0.2):
+                 key_capacity: int | None = None, device="cuda", trim: bool = False, near: float = 0.2,
+                 binning: int = 0):
         self.n, self.device = int(n), torch.device(device)
-        self.cfg = config_struct(tile, batch, bg, trim, near)
+        self.cfg = config_struct(tile, batch, bg, trim, near, binning=binning)
         self.width, self.height = int(cam.width), int(cam.height)
         self.cam0 = cam
         cap = key_capacity if key_capacity is not None else max(1 << 16, 16 * self.n)

@@ -50,7 +50,8 @@ class d4dgs_camera(ctypes.Structure):
 class d4dgs_config(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("batch", ctypes.c_int32), ("bg", ctypes.c_float * 3),
                 ("trim", ctypes.c_int32), ("near", ctypes.c_float), ("spin_limit", ctypes.c_uint32),
-                ("colour_cache", ctypes.c_int32)]
+                ("colour_cache", ctypes.c_int32),
+                ("binning", ctypes.c_int32)]
 
 
 class d4dgs_view(ctypes.Structure):

@@ -33,6 +33,12 @@ constexpr int kDepthItems = kSortThreads * kDepthIPT;     // the few-key depth p
 constexpr int kRadix = 256;                               // digit bins (<= 8 bits per pass)
 constexpr int kDupThreads = 256;
 constexpr int kDupItems = kDupThreads;                    // depth-ordered Gaussians per scan partition
+// direct binning (config binning 2): per-(partition, tile) pair counts over
+// partitions of kDirItems depth-ordered Gaussians, scanned down each tile's
+// column of the count matrix in bands of kDirBand tiles
+constexpr int kDirItems = 256;
+constexpr int kDirMaxTiles = 2048;
+constexpr int kDirBand = 8;
 
 // ---- control block (uint32 words at layout.control)
 enum : int {
@@ -58,7 +64,7 @@ struct Layout {
     // pass 0 of the tile sort is the column bucketing done by the emission;
     // passes 1.. sort stably by the tile row, so a pair's key is its tile row
     // (tile_bits = row_bits; tile_shift / tile_pass_bits of passes 1.. are
-    // relative to it)
+    // relative to it); direct binning has the one pass of its emission
     int32_t col_bits = 0, row_bits = 0, tile_bits = 0, tile_passes = 0;
     int32_t tile_shift[3] = {0, 0, 0}, tile_pass_bits[3] = {0, 0, 0};
     // pairs are packed as (row << id_bits | id) in one uint32 when they fit,
@@ -67,10 +73,13 @@ struct Layout {
     bool packed = true;
     int32_t trim_on = 0;   // config trim: 1 rectangles cut per column (tile_trim.cuh), 0 whole
     int64_t cap = 0;
-    int64_t parts_depth = 0, parts_dup = 0, parts_tile = 0;
+    int64_t parts_depth = 0, parts_dup = 0, parts_tile = 0, parts_dir = 0;
+    bool direct = false;   // config binning 2: pairs emitted straight into their tiles' lists (tile_passes 1)
     // zero-initialised region [0, zero_end)
     int64_t control = 0, grid = 0, lb_depth = 0, lb_col = 0, lb_tile = 0, zero_end = 0;
     // the rest
+    int64_t cmat = 0;      // direct binning: parts_dir x ntiles uint32 (not cleared: every entry is written)
+    int64_t cgrp = 0;      // direct binning: parts_dir x ntiles uint64 group counts (likewise)
     int64_t colbase = 0, ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
     int64_t trim = 0;   // per-Gaussian column trims of the rectangle (tile_trim.cuh)
     int64_t final_T = 0, n_contrib = 0, grad2d = 0, flow2d = 0, batch = 0, tile_keys[2] = {0, 0}, tile_vals[2] = {-1, -1};
@@ -132,6 +141,8 @@ struct View {
     uint32_t *tkeys[2], *tvals[2];
     uint32_t *lb_depth, *lb_tile, *lb_col;
     uint32_t *colbase;               // first position of each tile column's bucket (clamped to cap)
+    uint32_t *cmat;                  // direct binning: parts_dir x ntiles pair counts, then list offsets
+    unsigned long long *cgrp;        // direct binning: parts_dir x ntiles, byte g = pairs of group g
     uint32_t cap;
     int32_t id_bits, col_bits, packed, tile_passes, ntiles;
     int32_t trim_on;                 // config trim: 1 rectangles cut per column
@@ -139,13 +150,13 @@ struct View {
     int32_t colour_cache;            // config colour_cache: SH colour towards the static mean
     int32_t tile_shift[3];
     uint32_t tile_mask[3];
-    int32_t parts_depth, parts_dup, parts_tile;
+    int32_t parts_depth, parts_dup, parts_tile, parts_dir;
     // time group: consecutive views of one scene seen by one camera (times may
     // differ) are preprocessed together, reading each Gaussian once; the
     // group's first view carries group_size (others 0) and the chunk base
     int32_t group_size;
     // first flattened work item of this view within its table
-    int32_t chunk_base, depth_part_base, dup_part_base, tile_base;
+    int32_t chunk_base, depth_part_base, dup_part_base, tile_base, dir_part_base, band_base;
 };
 
 // Descriptor table as kernel parameters (it travels by value: 32 views fit in
@@ -155,7 +166,9 @@ struct BatchArgs {
     int32_t tile, batch, packed, tile_passes;   // shared by every view of a launch
     int32_t col_cap;                            // power of two >= every view's tile columns
     int32_t trim_on;                            // config trim, shared by every view of a launch
-    int32_t total_chunks, total_depth_parts, total_dup_parts, total_tiles;
+    int32_t tile_cap;                           // direct binning: multiple of 256 >= every view's tiles
+    int32_t cells_cap;                          // direct binning: multiple of 256 >= every (tiles_x+1)(tiles_y+1)
+    int32_t total_chunks, total_depth_parts, total_dup_parts, total_tiles, total_dir_parts, total_bands;
     int32_t max_n;
     View v[kMaxViews];
 };
@@ -169,7 +182,10 @@ enum : int {
     kBaTile = 6,           // 6..8 tile passes
     kBaBlend = 9,
     kBaBack = 10,
-    kBaNViews = 16, kBaTotalChunks, kBaTotalDepthParts, kBaTotalDupParts, kBaTotalTiles,
+    kBaDirCount = 11,      // direct binning: counts, emission
+    kBaDirEmit = 12,
+    kBaNViews = 16, kBaTotalChunks, kBaTotalDepthParts, kBaTotalDupParts, kBaTotalTiles, kBaTotalDirParts,
+    kBaTotalBands,
     kBaWords = 64
 };
 constexpr int64_t kBatchTableOffset = 256;
@@ -192,7 +208,7 @@ cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t s
                          unsigned long long *counts = nullptr, bool persist = false);
 cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb, const float *dl_dflow,
                             const d4dgs_scene_grad &g, cudaStream_t st, int num_sms, bool accumulate = false);
-int sort_launch_count(int n, int tile_passes, int grid_cells);
+int sort_launch_count(int n, int tile_passes, int grid_cells);   // tile_passes 1: direct binning
 
 __device__ __forceinline__ const View &view_of(const char *batch_area, int v) {
     return reinterpret_cast<const View *>(batch_area + kBatchTableOffset)[v];

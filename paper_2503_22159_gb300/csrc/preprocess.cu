@@ -577,6 +577,8 @@ clear_kernel(const __grid_constant__ BatchArgs args, const BatchArgs *args_dev, 
             bw[kBaTotalDepthParts] = (uint32_t)A->total_depth_parts;
             bw[kBaTotalDupParts] = (uint32_t)A->total_dup_parts;
             bw[kBaTotalTiles] = (uint32_t)A->total_tiles;
+            bw[kBaTotalDirParts] = (uint32_t)A->total_dir_parts;
+            bw[kBaTotalBands] = (uint32_t)A->total_bands;
         }
         const uint32_t *src = reinterpret_cast<const uint32_t *>(A->v);
         uint32_t *dst = reinterpret_cast<uint32_t *>(ba + kBatchTableOffset);

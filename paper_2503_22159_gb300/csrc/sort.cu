@@ -549,6 +549,337 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
     }
 }
 
+// ---- direct binning (config binning 2): the pairs go straight into their
+// tiles' lists, so the lists need no sort by tile after the emission.
+// Partitions of kDirItems (256) depth-ordered Gaussians, each 8 groups of 32.
+//   D1. per partition, from difference grids in shared memory (one per group:
+//       a rectangle's 4 corners, and 4 per trimmed column) integrated along
+//       rows, then columns: the pair count of every group in every tile
+//       (cgrp[p][t], one byte per group) and of the partition (cmat[p][t]);
+//   D2. each tile's column of cmat scanned over the partitions and offset by
+//       the tile's range start: cmat[p][t] = first position of partition p's
+//       pairs in tile t's list;
+//   D3. per partition again: each group's start in every tile (cmat plus the
+//       counts of the groups before it), then each warp walks its group's
+//       Gaussians in depth order and puts a Gaussian's pair of tile t at the
+//       group's running position in t (a Gaussian has one pair per tile, so
+//       the lanes never share a counter).  Each tile's list comes out in
+//       (depth, id) order, the order the column path's stable passes give.
+// No step waits on another CTA: the counts, not a look-back, order the
+// partitions.
+
+// The Gaussian at position pos of a view's depth order: its id (0 past the
+// end), its rectangle clamped to the grid (empty, x0 > x1, when it touches
+// no tile) and its column trims.
+template <bool TRIM>
+__device__ __forceinline__ void dir_load(const View &v, uint32_t pos, uint32_t &id, ushort4 &r,
+                                         unsigned long long &tw) {
+    const uint32_t n = (uint32_t)v.n;
+    id = 0;
+    r = make_ushort4(1, 0, 0, 0);
+    tw = 0ull;
+    if (pos < n) {
+        const uint32_t g = v.dvals[0][pos];   // after the 4 depth passes
+        if (g < n) {   // always true unless a depth pass gave up on a spin-wait
+            id = g;
+            if (v.tiles_touched[g]) {
+                r = v.rect[g];
+                if (TRIM) tw = v.trim[g];
+            }
+        }
+    }
+    r.y = (unsigned short)min((int)r.y, v.cam.tiles_x - 1);
+    r.w = (unsigned short)min((int)r.w, v.cam.tiles_y - 1);
+    if (r.z > r.w) r = make_ushort4(1, 0, 0, 0);
+}
+
+// Pairs the Gaussian keeps: its rectangle less the trimmed rows of its first
+// kTrimCols columns.
+template <bool TRIM>
+__device__ __forceinline__ int kept_pairs(ushort4 r, unsigned long long tw) {
+    if (r.x > r.y) return 0;
+    const int w = (int)r.y - (int)r.x + 1, h = (int)r.w - (int)r.z + 1;
+    if (!TRIM) return w * h;
+    const int nc = min(w, kTrimCols);
+    int k = (w - nc) * h;
+    for (int j = 0; j < nc; j++) k += trim_count(tw, j, h);
+    return k;
+}
+
+// View of a flattened direct-binning work item (partition or band).
+__device__ __forceinline__ int dir_view(const char *ba, int nviews, uint32_t g, bool bands) {
+    int vi = 0;
+    for (int u = 1; u < nviews; u++)
+        if ((uint32_t)(bands ? view_of(ba, u).band_base : view_of(ba, u).dir_part_base) <= g) vi = u;
+    return vi;
+}
+
+// D1: CTAs take partitions from a counter; warp w holds group w (one
+// Gaussian per lane).  Dynamic shared memory: 8 (tiles_x + 1) x (tiles_y + 1)
+// int grids of cells_cap each, one per group.  A trimmed column c with kept
+// rows [a, b] enters its group's grid as +1 at (c, a) and (c + 1, b + 1), -1
+// at (c + 1, a) and (c, b + 1): the 2D form of a single column's difference.
+template <bool TRIM>
+__global__ void __launch_bounds__(256, 4) dir_count_kernel(char *__restrict__ ba, int cells_cap) {
+    static_assert(kDirItems == 256, "one Gaussian per thread, 8 groups");
+    extern __shared__ int s_grid[];
+    __shared__ uint32_t s_part;
+    grid_dependency_wait();
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
+    const int nviews = (int)bw[kBaNViews];
+    const uint32_t total = bw[kBaTotalDirParts];
+    for (;;) {
+        if (tid == 0) s_part = atomicAdd(bw + kBaDirCount, 1u);
+        __syncthreads();
+        const uint32_t g = s_part;
+        if (g >= total) break;
+        const View &v = view_of(ba, dir_view(ba, nviews, g, false));
+        const uint32_t part = g - (uint32_t)v.dir_part_base;
+        const int tx = v.cam.tiles_x, ty = v.cam.tiles_y, gw = tx + 1, T = tx * ty;
+        const int cells = gw * (ty + 1);
+        if (cells > cells_cap) {   // a table with larger grids than this launch was sized for
+            if (tid == 0) atomicOr(v.ctl + kCtlStatus, kStatusCapacity);
+            __syncthreads();
+            continue;
+        }
+        uint32_t id;
+        ushort4 r;
+        unsigned long long tw;
+        dir_load<TRIM>(v, part * kDirItems + tid, id, r, tw);
+        for (int i = tid; i < 8 * cells_cap; i += 256) s_grid[i] = 0;
+        __syncthreads();
+        int *gg = s_grid + warp * cells_cap;
+        if (r.x <= r.y) {
+            int x0 = r.x;
+            bool rest = true;
+            if (TRIM) {   // leading columns: each its own kept rows
+                const int w = (int)r.y - (int)r.x + 1, h = (int)r.w - (int)r.z + 1, nc = min(w, kTrimCols);
+                for (int j = 0; j < nc; j++) {
+                    if (trim_count(tw, j, h) == 0) continue;
+                    const int a = (int)r.z + trim_top(tw, j), b1 = (int)r.w + 1 - trim_bot(tw, j), c = x0 + j;
+                    atomicAdd(&gg[a * gw + c], 1);
+                    atomicAdd(&gg[a * gw + c + 1], -1);
+                    atomicAdd(&gg[b1 * gw + c], -1);
+                    atomicAdd(&gg[b1 * gw + c + 1], 1);
+                }
+                x0 += nc;
+                rest = x0 <= (int)r.y;
+            }
+            if (rest) {
+                atomicAdd(&gg[(int)r.z * gw + x0], 1);
+                atomicAdd(&gg[(int)r.z * gw + r.y + 1], -1);
+                atomicAdd(&gg[((int)r.w + 1) * gw + x0], -1);
+                atomicAdd(&gg[((int)r.w + 1) * gw + r.y + 1], 1);
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < 8 * ty; i += 256) {   // along x: one row of one group per thread
+            const int w = i / ty, y = i - w * ty;
+            int *rowp = s_grid + w * cells_cap + y * gw;
+            int acc = 0;
+            for (int x = 0; x < tx; x++) {
+                acc += rowp[x];
+                rowp[x] = acc;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < 8 * tx; i += 256) {   // along y: one column of one group per thread
+            const int w = i / tx, x = i - w * tx;
+            int *colp = s_grid + w * cells_cap + x;
+            int acc = 0;
+            for (int y = 0; y < ty; y++) {
+                acc += colp[y * gw];
+                colp[y * gw] = acc;
+            }
+        }
+        __syncthreads();
+        uint32_t *crow = v.cmat + (size_t)part * T;
+        unsigned long long *grow = v.cgrp + (size_t)part * T;
+        for (int t = tid; t < T; t += 256) {
+            const int y = t / tx, cell = y * gw + (t - y * tx);
+            unsigned long long packed = 0ull;
+            uint32_t sum = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                const uint32_t k = (uint32_t)s_grid[w * cells_cap + cell];   // 0..32
+                packed |= (unsigned long long)k << (8 * w);
+                sum += k;
+            }
+            grow[t] = packed;
+            crow[t] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// D2: per band of kDirBand (8) tiles, the 128 row groups of the CTA (4 per
+// warp, lane = group << 3 | tile) split the partitions into runs, sum their
+// runs, take the exclusive prefix over the runs before them plus the tile's
+// range start, and rewrite their runs as running offsets.  Offsets stay
+// below 2^32: a range start is below 2^30 and a tile gets at most one pair
+// per Gaussian.
+__global__ void __launch_bounds__(1024, 1) dir_scan_kernel(char *__restrict__ ba) {
+    static_assert(kDirBand == 8, "8 tiles x 128 row groups per CTA");
+    __shared__ uint32_t s_tot[128][kDirBand];
+    grid_dependency_wait();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int k = tid & 7, grp = tid >> 3;
+    const uint32_t *bw = reinterpret_cast<const uint32_t *>(ba);
+    const int nviews = (int)bw[kBaNViews];
+    const uint32_t total = bw[kBaTotalBands];
+    for (uint32_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const View &v = view_of(ba, dir_view(ba, nviews, g, true));
+        const int T = v.ntiles, P = v.parts_dir;
+        const int t = (int)(g - (uint32_t)v.band_base) * kDirBand + k;
+        const int R = (P + 127) / 128, p0 = min(grp * R, P), p1 = min(p0 + R, P);
+        uint32_t *col = v.cmat + t;
+        uint32_t sum = 0;
+        if (t < T) {
+            int p = p0;
+            for (; p + 4 <= p1; p += 4) {
+                const uint32_t a = col[(size_t)p * T], b = col[(size_t)(p + 1) * T];
+                const uint32_t c = col[(size_t)(p + 2) * T], d = col[(size_t)(p + 3) * T];
+                sum += a + b + c + d;
+            }
+            for (; p < p1; p++) sum += col[(size_t)p * T];
+        }
+        s_tot[grp][k] = sum;
+        __syncthreads();
+        if (warp < kDirBand) {   // warp w scans tile w's 128 run totals, 4 per lane
+            uint32_t x[4], acc = 0;
+#pragma unroll
+            for (int i = 0; i < 4; i++) { x[i] = s_tot[lane * 4 + i][warp]; acc += x[i]; }
+            uint32_t incl = acc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint32_t run = incl - acc;
+#pragma unroll
+            for (int i = 0; i < 4; i++) { s_tot[lane * 4 + i][warp] = run; run += x[i]; }
+        }
+        __syncthreads();
+        if (t < T) {
+            uint32_t run = v.ranges[t].x + s_tot[grp][k];
+            for (int p = p0; p < p1; p++) {
+                const uint32_t c = col[(size_t)p * T];
+                col[(size_t)p * T] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// D3: the emission, one partition per CTA at a time; warp w walks group w.
+// Dynamic shared memory of a launch with tile capacity C: [C] uint32 list
+// positions of the partition's runs, [8][C] uint16 running positions of the
+// groups within them.
+template <bool TRIM>
+__global__ void __launch_bounds__(256, 4) dir_emit_kernel(char *__restrict__ ba, int tile_cap) {
+    static_assert(kDirItems == 256, "one Gaussian per thread, 8 groups");
+    extern __shared__ uint32_t s_dyn[];
+    uint32_t *s_run = s_dyn;
+    uint16_t *s_off = reinterpret_cast<uint16_t *>(s_dyn + tile_cap);
+    __shared__ uint32_t s_part;
+    grid_dependency_wait();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
+    const int nviews = (int)bw[kBaNViews];
+    const uint32_t total = bw[kBaTotalDirParts];
+    for (;;) {
+        if (tid == 0) s_part = atomicAdd(bw + kBaDirEmit, 1u);
+        __syncthreads();
+        const uint32_t g = s_part;
+        if (g >= total) break;
+        const View &v = view_of(ba, dir_view(ba, nviews, g, false));
+        const uint32_t part = g - (uint32_t)v.dir_part_base;
+        const int T = v.ntiles, tx = v.cam.tiles_x;
+        if (T > tile_cap) {
+            if (tid == 0) atomicOr(v.ctl + kCtlStatus, kStatusCapacity);
+            __syncthreads();
+            continue;
+        }
+        uint32_t id;
+        ushort4 r;
+        unsigned long long tw;
+        dir_load<TRIM>(v, part * kDirItems + tid, id, r, tw);
+        const uint32_t *crow = v.cmat + (size_t)part * T;
+        const unsigned long long *grow = v.cgrp + (size_t)part * T;
+        for (int t = tid; t < T; t += 256) {
+            s_run[t] = crow[t];
+            const unsigned long long packed = grow[t];
+            uint32_t pre = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                s_off[w * tile_cap + t] = (uint16_t)pre;
+                pre += (uint32_t)(packed >> (8 * w)) & 0xFFu;
+            }
+        }
+        __syncthreads();
+        const uint32_t cap = v.cap;
+        const int id_bits = v.id_bits;
+        const bool packed = v.packed != 0;
+        uint32_t *keys_out = v.tkeys[1], *vals_out = v.tvals[1];
+        uint16_t *my_off = s_off + warp * tile_cap;
+        const int kept = kept_pairs<TRIM>(r, tw);
+        const int wd = (int)r.y - (int)r.x + 1, ht = (int)r.w - (int)r.z + 1;
+        const uint32_t xy = (uint32_t)r.x | ((uint32_t)r.z << 16), wh = (uint32_t)wd | ((uint32_t)ht << 16);
+        const float inv_h = kept > 0 ? 1.0f / (float)ht : 0.0f;
+        uint32_t todo = __ballot_sync(0xFFFFFFFFu, kept > 0);
+        while (todo) {   // the group's Gaussians with pairs, in depth order
+            const int q = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int kq = __shfl_sync(0xFFFFFFFFu, kept, q);
+            const uint32_t qxy = __shfl_sync(0xFFFFFFFFu, xy, q), qwh = __shfl_sync(0xFFFFFFFFu, wh, q);
+            const float qinv = __shfl_sync(0xFFFFFFFFu, inv_h, q);
+            const uint32_t gid = __shfl_sync(0xFFFFFFFFu, id, q);
+            unsigned long long qt = 0ull;
+            if (TRIM)
+                qt = ((unsigned long long)__shfl_sync(0xFFFFFFFFu, (uint32_t)(tw >> 32), q) << 32) |
+                     __shfl_sync(0xFFFFFFFFu, (uint32_t)tw, q);
+            const int qh = (int)(qwh >> 16), qnc = TRIM ? min((int)(qwh & 0xFFFFu), kTrimCols) : 0;
+            for (int j = lane; j < kq; j += 32) {
+                int rr = j, c0 = 0, row = -1;
+                if (TRIM) {
+                    for (; c0 < qnc; c0++) {
+                        const int kk = trim_count(qt, c0, qh);
+                        if (rr < kk) {
+                            row = trim_top(qt, c0) + rr;
+                            break;
+                        }
+                        rr -= kk;
+                    }
+                }
+                if (row < 0) {   // an untrimmed column: rr counts whole columns of qh rows
+                    int cc = __float2int_rz((float)rr * qinv);
+                    int rw = rr - cc * qh;
+                    if (rw < 0) { cc--; rw += qh; } else if (rw >= qh) { cc++; rw -= qh; }
+                    c0 += cc;
+                    row = rw;
+                }
+                const int trow = (int)(qxy >> 16) + row;
+                const int tile = trow * tx + (int)(qxy & 0xFFFFu) + c0;
+                const uint32_t k = my_off[tile];
+                my_off[tile] = (uint16_t)(k + 1u);
+                const uint32_t o = s_run[tile] + k;
+                if (o < cap) {
+                    if (packed) {
+                        keys_out[o] = ((uint32_t)trow << id_bits) | gid;
+                    } else {
+                        keys_out[o] = (uint32_t)trow;
+                        vals_out[o] = gid;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -565,9 +896,49 @@ int occupancy_blocks(const void *fn, int threads, size_t smem = 0) {
 constexpr size_t emit_smem(int col_cap) { return (size_t)9 * col_cap * sizeof(uint32_t); }
 
 int sort_launch_count(int n, int tile_passes, int grid_cells) {
-    // tile counts (own launch unless they ride with the first depth pass) + 4 depth passes + emit + row passes
-    return n == 0 ? 1 : (grid_cells <= kTileCountCells ? 0 : 1) + 4 + 1 + (tile_passes - 1);
+    // tile counts (own launch unless they ride with the first depth pass) + 4 depth passes + either
+    // counts, scan and emission (direct binning) or column emission + row passes
+    return n == 0 ? 1 : (grid_cells <= kTileCountCells ? 0 : 1) + 4 + (tile_passes == 1 ? 3 : 1 + (tile_passes - 1));
 }
+
+// dynamic shared memory of the direct binning: the counts' 8 group grids of a
+// launch's grid-cell capacity, the emission's positions for its tile capacity
+constexpr size_t dir_count_smem(int cells_cap) { return (size_t)8 * cells_cap * sizeof(int); }
+constexpr size_t dir_emit_smem(int tile_cap) { return (size_t)20 * tile_cap; }
+
+namespace {
+
+cudaError_t launch_direct(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
+    // grids of at most kDirMaxTiles tiles have at most 2 kDirMaxTiles + 2 cells
+    constexpr int kMaxCells = 2 * kDirMaxTiles + 256;
+    const int tc = args.tile_cap, cc = args.cells_cap;
+    if (tc < 256 || tc > kDirMaxTiles || tc % 256 || cc < 256 || cc > kMaxCells || cc % 256)
+        return cudaErrorInvalidValue;
+    static int occ_count[2][kMaxCells / 256 + 1] = {}, occ_emit[2][kDirMaxTiles / 256 + 1] = {};
+    static bool attr = false;
+    if (!attr) {
+        for (const void *fn : {(const void *)dir_count_kernel<false>, (const void *)dir_count_kernel<true>})
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dir_count_smem(kMaxCells));
+        for (const void *fn : {(const void *)dir_emit_kernel<false>, (const void *)dir_emit_kernel<true>})
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dir_emit_smem(kDirMaxTiles));
+        attr = true;
+    }
+    const int ti = args.trim_on ? 1 : 0;
+    const void *count_fn = ti ? (const void *)dir_count_kernel<true> : (const void *)dir_count_kernel<false>;
+    const void *emit_fn = ti ? (const void *)dir_emit_kernel<true> : (const void *)dir_emit_kernel<false>;
+    int &oc = occ_count[ti][cc / 256], &oe = occ_emit[ti][tc / 256];
+    if (!oc) oc = occupancy_blocks(count_fn, 256, dir_count_smem(cc));
+    if (!oe) oe = occupancy_blocks(emit_fn, 256, dir_emit_smem(tc));
+    cudaError_t e = ti ? launch_chained(dir_count_kernel<true>, oc * num_sms, 256, dir_count_smem(cc), st, batch_area, cc)
+                       : launch_chained(dir_count_kernel<false>, oc * num_sms, 256, dir_count_smem(cc), st, batch_area, cc);
+    if (e == cudaSuccess) e = launch_chained(dir_scan_kernel, num_sms, 1024, 0, st, batch_area);
+    if (e == cudaSuccess)
+        e = ti ? launch_chained(dir_emit_kernel<true>, oe * num_sms, 256, dir_emit_smem(tc), st, batch_area, tc)
+               : launch_chained(dir_emit_kernel<false>, oe * num_sms, 256, dir_emit_smem(tc), st, batch_area, tc);
+    return e;
+}
+
+}  // namespace
 
 cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
     static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0;
@@ -621,6 +992,8 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
         }
     }
     if (e != cudaSuccess) return e;
+    // ---- 2-3 (direct binning): counts, their column scan, emission into the tiles' lists
+    if (args.tile_passes == 1) return launch_direct(args, batch_area, st, num_sms);
     // ---- 2. emission in depth order into tile-column buckets (tile pass 0)
     int lc = 0;
     while ((1 << lc) < args.col_cap) lc++;

@@ -18,11 +18,11 @@ def d4():
     return m
 
 
-def render(scene, cam, t, tile=16, batch=256, bg=(0.0, 0.0, 0.0), cap=None, trim=False):
+def render(scene, cam, t, tile=16, batch=256, bg=(0.0, 0.0, 0.0), cap=None, trim=False, binning=0):
     m = d4()
     ds = m.DeviceScene.from_host(scene)
     r = m.Renderer(scene.n, cam, tile=tile, batch=batch, bg=bg, key_capacity=cap, trim=trim,
-                   near=getattr(cam, "near", 0.2))
+                   near=getattr(cam, "near", 0.2), binning=binning)
     img = r.render(ds, cam, t)
     torch.cuda.synchronize()
     return r, ds, img

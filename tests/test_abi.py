@@ -70,14 +70,37 @@ def test_workspace_bytes_monotone_and_layout(d4):
                                              (16, 16, 16, 2), (7, 5, 32, 2), (4096, 4096, 8, 3),
                                              (16384, 2048, 8, 2)])
 def test_tile_pass_count(d4, w, h, tile, passes):
-    """Pass 0 buckets the pairs by tile column; 8-bit passes over the row bits follow (at least one)."""
+    """Column binning: pass 0 buckets the pairs by tile column; 8-bit passes over the row bits
+    follow (at least one)."""
     cam = synth.pinhole(w, h)
-    cfg = d4.config_struct(tile, 64)
+    cfg = d4.config_struct(tile, 64, binning=1)
     L = d4.d4dgs_workspace_layout(10, cam, cfg, d4.d4dgs_workspace_bytes(10, cam, cfg, 100))
     cols, rows = math.ceil(w / tile), math.ceil(h / tile)
     assert L["tile_passes"] == passes
     assert 2 ** (8 * (passes - 1)) >= rows
     assert 2 ** L["col_bits"] >= cols > 2 ** (L["col_bits"] - 1) or cols == 1
+
+
+@pytest.mark.parametrize("w,h,tile,fits", [(128, 128, 16, True), (1352, 1014, 32, True),
+                                                  (1920, 1080, 32, True), (1352, 1014, 16, False),
+                                                  (2704, 2028, 32, False), (7, 5, 32, True), (1440, 1440, 32, True),
+                                                  (1472, 1440, 32, False)])
+def test_binning_choice(d4, w, h, tile, fits):
+    """Direct binning (pairs straight into the tiles' lists, tile_passes 1) on request for grids of
+    at most 2048 tiles, where it is an invalid config beyond; binning 0 takes the column path."""
+    cam = synth.pinhole(w, h)
+    ntiles = math.ceil(w / tile) * math.ceil(h / tile)
+    assert fits == (ntiles <= 2048)
+    for binning, direct in ((0, False), (1, False), (2, True)):
+        cfg = d4.config_struct(tile, 64, binning=binning)
+        if binning == 2 and not fits:
+            assert d4._abi.load().d4dgs_workspace_bytes(10, ctypes.byref(d4.camera_struct(cam)), ctypes.byref(cfg),
+                                                        100) == 0
+            continue
+        L = d4.d4dgs_workspace_layout(10, cam, cfg, d4.d4dgs_workspace_bytes(10, cam, cfg, 100))
+        assert (L["tile_passes"] == 1) == direct
+    assert d4._abi.load().d4dgs_workspace_bytes(10, ctypes.byref(d4.camera_struct(cam)),
+                                                ctypes.byref(d4.config_struct(tile, 64, binning=3)), 100) == 0
 
 
 def test_invalid_arguments_rejected_on_host(d4):
@@ -118,6 +141,10 @@ def test_launch_count(d4):
     assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(1352, 1014), cfg) == 9
     # 2704 x 2028 at 16 px: 171 x 128 grid cells are too many to ride along, tile counts launch alone
     assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(2704, 2028), cfg) == 10
+    # 1352 x 1014 at 32 px (1376 tiles), direct binning: counts + scan + emission instead of the
+    # column emission and the row pass
+    assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(1352, 1014), d4.config_struct(32, 256, binning=2)) == 10
+    assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(1352, 1014), d4.config_struct(32, 256)) == 9
 
 
 def test_packing_decision(d4):

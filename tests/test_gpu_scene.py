@@ -29,18 +29,22 @@ def gpu_renderer(scene_w):
     return m, ds, r
 
 
-@pytest.mark.parametrize("k,trim", [(150, False), (150, True)])
-def test_scene_preprocess_and_lists(scene_w, gpu_renderer, k, trim):
+@pytest.mark.parametrize("k,trim,tile,binning", [(150, False, 16, 0), (150, True, 16, 0), (150, False, 32, 0),
+                                                  (150, False, 32, 2), (150, True, 32, 2)])
+def test_scene_preprocess_and_lists(scene_w, gpu_renderer, k, trim, tile, binning):
+    """Tile 16 and 32 (the benchmark's launch configuration) with the column binning; tile 32
+    (1376 tiles) with the direct binning too."""
     m, ds, r = gpu_renderer
-    if trim:
-        r = m.Renderer(scene_w.scene.n, scene_w.frames[0][0], tile=16, batch=256, key_capacity=40 * scene_w.scene.n,
-                       trim=True)
+    if trim or tile != 16 or binning:
+        r = m.Renderer(scene_w.scene.n, scene_w.frames[0][0], tile=tile, batch=256, key_capacity=40 * scene_w.scene.n,
+                       trim=trim, binning=binning)
     cam, t = scene_w.frames[k]
     r.render(ds, cam, t)
     torch.cuda.synchronize()
+    assert (r.layout(cam)["tile_passes"] == 1) == (binning == 2)
     n = scene_w.scene.n
     rec = gu.gpu_records(r, n, cam)
-    b = oracle.bin_f32(scene_w.scene, cam, t, 16, trim=trim)
+    b = oracle.bin_f32(scene_w.scene, cam, t, tile, trim=trim)
     g = oracle.preprocess(scene_w.scene, cam, t)
     vis = b["tiles_touched"] > 0
     assert vis.sum() > 100_000
