@@ -260,7 +260,7 @@ __device__ __forceinline__ void tile_count_view(const View &v, int *s_grid, int 
 // tc_cells ints of dynamic shared memory) instead of sorting, so that work
 // overlaps the pass rather than taking a launch of its own.
 template <bool KV, bool IOTA, bool TILE>
-__global__ void __launch_bounds__(kSortThreads, TILE ? (KV ? 3 : 4) : 4)
+__global__ void __launch_bounds__(kSortThreads, TILE ? (KV ? 3 : 4) : 2)
 onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells) {
     constexpr int IPT = TILE ? kTileIPT : kDepthIPT;
     constexpr int ITEMS = kSortThreads * IPT;
@@ -329,20 +329,54 @@ onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells) {
             keys[k] = ok ? keys_in[idx] : 0xFFFFFFFFu;
             if (KV) vals[KV ? k : 0] = IOTA ? idx : (ok ? vals_in[idx] : 0u);
         }
-        // ---- stable rank within the warp (match-any on the digit)
+        // ---- stable rank within the warp
+        if (TILE && mask <= 63u) {
+            // at most 64 digits (row passes of up to 64 tile rows): multisplit in registers.  The
+            // peers of an item are the lanes whose digit bits match its own in all 6 ballots; lane
+            // l keeps the running counts of digits l and l + 32.
+            const uint32_t lt = lanemask_lt();
+            uint32_t cnt_lo = 0, cnt_hi = 0;
 #pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            const uint32_t d = (keys[k] >> shift) & mask;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-            const int leader = __ffs(peers) - 1;
-            uint32_t old = 0;
-            if (lane == leader) {
-                old = s_warp_hist[warp][d];
-                s_warp_hist[warp][d] = old + __popc(peers);
+            for (int k = 0; k < IPT; k++) {
+                const uint32_t d = (keys[k] >> shift) & mask;
+                uint32_t bal[6];
+#pragma unroll
+                for (int b = 0; b < 6; b++) bal[b] = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+                uint32_t peers = 0xFFFFFFFFu, m_lo = 0xFFFFFFFFu, m_hi;
+#pragma unroll
+                for (int b = 0; b < 6; b++) peers &= ((d >> b) & 1u) ? bal[b] : ~bal[b];
+#pragma unroll
+                for (int b = 0; b < 5; b++) m_lo &= ((lane >> b) & 1) ? bal[b] : ~bal[b];
+                m_hi = m_lo & bal[5];
+                m_lo &= ~bal[5];
+                const uint32_t before_lo = __shfl_sync(0xFFFFFFFFu, cnt_lo, (int)(d & 31u));
+                const uint32_t before_hi = __shfl_sync(0xFFFFFFFFu, cnt_hi, (int)(d & 31u));
+                rank[k] = ((d >> 5) ? before_hi : before_lo) + __popc(peers & lt);
+                cnt_lo += __popc(m_lo);
+                cnt_hi += __popc(m_hi);
             }
-            __syncwarp();
-            old = __shfl_sync(0xFFFFFFFFu, old, leader);
-            rank[k] = old + __popc(peers & lanemask_lt());
+            s_warp_hist[warp][lane] = cnt_lo;
+            s_warp_hist[warp][lane + 32] = cnt_hi;
+        } else {
+            // 8-bit digits: the peers of an item from 8 ballots (match-any's cost grows with the
+            // number of distinct digits in the warp); the warp's running digit counts in shared
+            // memory, read by every peer and advanced by the highest one
+            const uint32_t lt = lanemask_lt();
+#pragma unroll
+            for (int k = 0; k < IPT; k++) {
+                const uint32_t d = (keys[k] >> shift) & mask;
+                uint32_t peers = 0xFFFFFFFFu;
+#pragma unroll
+                for (int b = 0; b < 8; b++) {
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+                    peers &= ((d >> b) & 1u) ? bal : ~bal;
+                }
+                const uint32_t old = s_warp_hist[warp][d];
+                __syncwarp();
+                if (lane == 31 - __clz(peers)) s_warp_hist[warp][d] = old + __popc(peers);
+                __syncwarp();
+                rank[k] = old + __popc(peers & lt);
+            }
         }
         __syncthreads();
         // ---- per digit: prefix over warps, block count, publish, look back
@@ -948,6 +982,9 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
         occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false, false>, kSortThreads);
         occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false, true>, kSortThreads);
         occ_tkv = occupancy_blocks((const void *)onesweep_kernel<true, false, true>, kSortThreads);
+        // the first depth pass carries the tile counts' grid (up to kTileCountCells ints) on top of its own arrays
+        cudaFuncSetAttribute(onesweep_kernel<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((3 * kRadix + 64 + kTileCountCells) * sizeof(int)));
         cudaFuncSetAttribute(emit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
         cudaFuncSetAttribute(emit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
     }
