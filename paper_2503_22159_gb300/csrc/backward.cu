@@ -422,8 +422,7 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
                                     __fmul_rn(R[3 * r + 2], m[2])), c.T[r]);
     const float Z = Xc[2];
     const float xz = __fdiv_rn(Xc[0], Z), yz = __fdiv_rn(Xc[1], Z);
-    const float limx = __fmul_rn(kJacClamp, __fdiv_rn(__fmul_rn(0.5f, (float)c.width), c.fx));
-    const float limy = __fmul_rn(kJacClamp, __fdiv_rn(__fmul_rn(0.5f, (float)c.height), c.fy));
+    const float limx = c.limx, limy = c.limy;
     const bool clx = xz < -limx || xz > limx, cly = yz < -limy || yz > limy;
     const float xzc = fminf(limx, fmaxf(-limx, xz)), yzc = fminf(limy, fmaxf(-limy, yz));
     const float iz = 1.0f / Z;

@@ -105,6 +105,9 @@ struct CamArgs {
     float fx, fy, cx, cy;
     float campos[3];       // -R^T T, for the SH view direction
     float near;            // near plane on camera z
+    // limits of the Jacobian's x/z and y/z clamp, 1.3 times the half field of view:
+    // kJacClamp * ((width / 2) / fx) with each operation rounded to single precision
+    float limx, limy;
     int32_t width, height, tile, tiles_x, tiles_y;
 };
 CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile, float near);

@@ -159,8 +159,7 @@ __device__ __forceinline__ void screen_flow(const CamArgs &c, float v0, float v1
 __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Footprint &f) {
     const CamArgs &c = vw.cam;
     const float t = vw.t;
-    const float limx = mul(kJacClamp, dvd(mul(0.5f, (float)c.width), c.fx));
-    const float limy = mul(kJacClamp, dvd(mul(0.5f, (float)c.height), c.fy));
+    const float limx = c.limx, limy = c.limy;
     // every geometric parameter is loaded before the first cull test, so a Gaussian
     // costs one DRAM round trip instead of one per test
     const float p_tm = __ldg(vw.t_mean + i);
@@ -247,8 +246,7 @@ __device__ __forceinline__ bool footprint_disentangled(const View &vw, int i, Fo
 // like for like.
 __device__ __forceinline__ bool footprint_slicing(const View &vw, int i, Footprint &f) {
     const CamArgs &c = vw.cam;
-    const float limx = mul(kJacClamp, dvd(mul(0.5f, (float)c.width), c.fx));
-    const float limy = mul(kJacClamp, dvd(mul(0.5f, (float)c.height), c.fy));
+    const float limx = c.limx, limy = c.limy;
     const float4 m4 = __ldg(reinterpret_cast<const float4 *>(vw.means4) + i);
     const float4 l4 = __ldg(reinterpret_cast<const float4 *>(vw.log_scales4) + i);
     float4 a = __ldg(reinterpret_cast<const float4 *>(vw.quat_l) + i);
@@ -358,8 +356,10 @@ __device__ __forceinline__ void preprocess_one(const View &vw, int i, uint32_t *
             const float k2 = add(mul(mul(2.0f, blog(mul(255.0f, oh))), kK2Scale), kK2Pad);
             const float ex = __fsqrt_rn(mul(k2, s00)), ey = __fsqrt_rn(mul(k2, s11));
             const float rx = ceilf(ex), ry = ceilf(ey);
-            const float fx0 = floorf(dvd(sub(u, rx), tilef)), fx1 = floorf(dvd(add(u, rx), tilef));
-            const float fy0 = floorf(dvd(sub(v, ry), tilef)), fy1 = floorf(dvd(add(v, ry), tilef));
+            // division by the tile size (a power of two) as the exact product with its reciprocal
+            const float itile = 1.0f / tilef;
+            const float fx0 = floorf(mul(sub(u, rx), itile)), fx1 = floorf(mul(add(u, rx), itile));
+            const float fy0 = floorf(mul(sub(v, ry), itile)), fy1 = floorf(mul(add(v, ry), itile));
             if (!(fx1 >= 0.0f) || !(fx0 <= (float)(c.tiles_x - 1))) break;
             if (!(fy1 >= 0.0f) || !(fy0 <= (float)(c.tiles_y - 1))) break;
             const int x0 = (int)fmaxf(fx0, 0.0f), x1 = (int)fminf(fx1, (float)(c.tiles_x - 1));
@@ -606,6 +606,12 @@ CamArgs make_cam_args(const d4dgs_camera *cam, int32_t tile, float near) {
         a.campos[j] = (float)p;
     }
     a.width = cam->width; a.height = cam->height; a.tile = tile;
+    {   // one IEEE single-precision product, quotient and product each, as the kernels would round them
+        const float hw = 0.5f * (float)cam->width, hh = 0.5f * (float)cam->height;
+        const float qx = hw / cam->fx, qy = hh / cam->fy;
+        a.limx = kJacClamp * qx;
+        a.limy = kJacClamp * qy;
+    }
     a.tiles_x = (cam->width + tile - 1) / tile;
     a.tiles_y = (cam->height + tile - 1) / tile;
     return a;
@@ -621,17 +627,27 @@ cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batc
 
 cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms) {
     if (args.total_chunks == 0) return cudaSuccess;
-    // persistent grid: 8 resident CTAs of 256 threads per SM; grids of up to
+    // persistent grid of the CTAs that are resident at once (a CTA beyond them would only start
+    // once the chunks are gone, and still clear and flush its shared sums); grids of up to
     // 6144 cells (e.g. 1352x1014 at 32-px tiles) are aggregated in shared memory
     constexpr int kSmemCells = 6144;
+    constexpr size_t kSmem = kSmemCells * sizeof(int);
+    static int occ[3] = {0, 0, 0};   // by variant, queried once
+    auto resident = [&](const void *fn, int which) {
+        if (!occ[which] && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[which], fn, 256, kSmem) != cudaSuccess ||
+                            occ[which] < 1))
+            occ[which] = 1;
+        return occ[which] * num_sms;
+    };
     const cudaError_t e =
-        args.v[0].kind == 1 ? launch_chained(preprocess_kernel<1, false>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
-                                             (const char *)batch_area, kSmemCells)
+        args.v[0].kind == 1
+            ? launch_chained(preprocess_kernel<1, false>, resident((const void *)preprocess_kernel<1, false>, 0), 256,
+                             kSmem, st, (const char *)batch_area, kSmemCells)
         : args.v[0].colour_cache
-            ? launch_chained(preprocess_kernel<0, true>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
-                             (const char *)batch_area, kSmemCells)
-            : launch_chained(preprocess_kernel<0, false>, num_sms * 8, 256, kSmemCells * sizeof(int), st,
-                             (const char *)batch_area, kSmemCells);
+            ? launch_chained(preprocess_kernel<0, true>, resident((const void *)preprocess_kernel<0, true>, 1), 256,
+                             kSmem, st, (const char *)batch_area, kSmemCells)
+            : launch_chained(preprocess_kernel<0, false>, resident((const void *)preprocess_kernel<0, false>, 2), 256,
+                             kSmem, st, (const char *)batch_area, kSmemCells);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
