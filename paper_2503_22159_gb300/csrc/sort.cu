@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
     extern __shared__ uint32_t s_dyn[];   // [8][col_cap] per-warp column counts, then [col_cap] bases
     __shared__ uint32_t s_id[kDupItems];
     __shared__ ushort4 s_rect[kDupItems];
+    __shared__ float s_inv[kDupItems];   // 1 / rectangle height, once per Gaussian by its own thread
     __shared__ unsigned long long s_trim[TRIM ? kDupItems : 1];
     __shared__ uint32_t s_part;
     grid_dependency_wait();
@@ -509,6 +510,7 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
         r.w = (unsigned short)min((int)r.w, v.cam.tiles_y - 1);
         s_id[tid] = id;
         s_rect[tid] = r;
+        s_inv[tid] = r.x <= r.y ? 1.0f / (float)((int)r.w - (int)r.z + 1) : 0.0f;
         if (TRIM) s_trim[TRIM ? tid : 0] = tw;
         for (int w = 0; w < 8; w++)
             for (int c = tid; c < ncols; c += kDupThreads) s_dyn[w * col_cap + c] = 0u;
@@ -555,7 +557,7 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
             const unsigned long long tq = TRIM ? s_trim[TRIM ? q : 0] : 0ull;
             const int wdt = (int)rq.y - (int)rq.x + 1, hgt = (int)rq.w - (int)rq.z + 1;
             const int cnt = wdt * hgt;
-            const float inv_h = 1.0f / (float)hgt;
+            const float inv_h = s_inv[q];
             for (int j = lane; j < cnt; j += 32) {
                 int cc = __float2int_rz((float)j * inv_h);
                 int rr = j - cc * hgt;
