@@ -153,6 +153,10 @@ typedef struct {
                                     top | rows cut at the bottom << 4 (0..15 each); the
                                     Gaussian's tiles are the rectangle minus these cuts,
                                     tiles_touched of them                                    */
+    int64_t tile_order;          /* tiles uint32: the order in which the backward's tile replay
+                                    takes the tiles, most work first (quarter-octave classes
+                                    of the list entries the forward walked over the tile's
+                                    pixels; written by d4dgs_render_backward)                  */
 } d4dgs_layout;
 
 /* Bytes of workspace for N Gaussians, this camera and config, and room for

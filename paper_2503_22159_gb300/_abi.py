@@ -70,7 +70,7 @@ class d4dgs_layout(ctypes.Structure):
                                                "control", "key_capacity")] + [
         ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("depth_passes", ctypes.c_int32),
         ("tile_passes", ctypes.c_int32), ("id_bits", ctypes.c_int32), ("packed", ctypes.c_int32),
-        ("col_bits", ctypes.c_int32), ("trims", ctypes.c_int64)]
+        ("col_bits", ctypes.c_int32), ("trims", ctypes.c_int64), ("tile_order", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); the exported symbols of include/d4dgs.h

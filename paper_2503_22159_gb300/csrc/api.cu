@@ -135,6 +135,8 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.cgrp = off; off += l.direct ? align256(l.parts_dir * l.ntiles * 8) : 0;
     l.batch = off; off += align256(kBatchAreaBytes);
     l.ranges = off; off += align256((int64_t)l.ntiles * 8);
+    l.tile_order = off; off += align256((int64_t)l.ntiles * 4);
+    l.tile_work = off; off += align256((int64_t)l.ntiles * 4);
     l.records = off; off += align256((int64_t)n * 48);
     for (int b = 0; b < 2; b++) { l.depth_keys[b] = off; off += align256((int64_t)n * 4); }
     for (int b = 0; b < 2; b++) { l.depth_vals[b] = off; off += align256((int64_t)n * 4); }
@@ -195,6 +197,8 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     x.rect = at<ushort4>(ws, L.rect);
     x.trim = at<unsigned long long>(ws, L.trim);
     x.ranges = at<uint2>(ws, L.ranges);
+    x.tile_order = at<uint32_t>(ws, L.tile_order);
+    x.tile_work = at<uint32_t>(ws, L.tile_work);
     x.final_T = at<float>(ws, L.final_T);
     x.n_contrib = at<uint32_t>(ws, L.n_contrib);
     x.grad2d = at<float>(ws, L.grad2d);
@@ -317,6 +321,7 @@ int d4dgs_workspace_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_confi
     out->tile_keys = L.tile_keys[L.final_buf()];
     out->tile_vals = L.packed ? -1 : L.tile_vals[L.final_buf()];
     out->ranges = L.ranges;
+    out->tile_order = L.tile_order;
     out->final_T = L.final_T;
     out->n_contrib = L.n_contrib;
     out->control = L.control;

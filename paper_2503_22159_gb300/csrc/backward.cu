@@ -106,7 +106,11 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
     __shared__ float s_acc[BATCH][NA];
     __shared__ uint32_t s_maxw;
 
-    const int tile = blockIdx.x;
+    int tile = blockIdx.x;
+    {   // the forward's tile order: longest lists first; kept in range whatever the buffer holds
+        const uint32_t o = v.tile_order[tile];
+        if (o < (uint32_t)v.ntiles) tile = (int)o;
+    }
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int x0 = tx * TS, y0 = ty * TS;
     const int lane = (int)(threadIdx.x & 31u), warp = (int)(threadIdx.x >> 5);
@@ -597,6 +601,65 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
     put(&o.t_mean[i], -dtau);
 }
 
+// ---------------------------------------------------------------------------
+// Tile order of the replay.  A tile's replay time follows the list entries its
+// pixels walked in the forward (n_contrib); taken in row-major order, the
+// heaviest tiles can be among the last to start and leave most SMs idle while
+// they finish.  So the replay takes the tiles heaviest first: per tile the
+// walked entries summed over its pixels, then (one CTA) quarter-octave classes
+// of that sum counted, scanned from the heaviest down and the tiles scattered
+// (order within a class: whatever the atomics give; any order gives the same
+// gradients up to the order of their floating-point sums).
+__device__ __forceinline__ int work_class(uint32_t k) {
+    if (k == 0u) return 0;
+    const int l = 31 - __clz(k);
+    const uint32_t f = l >= 2 ? (k >> (l - 2)) & 3u : (k << (2 - l)) & 3u;
+    return 1 + 4 * l + (int)f;
+}
+constexpr int kWorkClasses = 1 + 4 * 32;
+
+template <int TS>
+__global__ void __launch_bounds__(256) tile_work_kernel(const char *__restrict__ ba) {
+    __shared__ float s_w[8];
+    const View &v = view_of(ba, 0);
+    const int tile = blockIdx.x, tiles_x = v.cam.tiles_x;
+    const int x0 = (tile % tiles_x) * TS, y0 = (tile / tiles_x) * TS;
+    float sum = 0.0f;   // a weight: float keeps large sums without overflow
+    for (int p = threadIdx.x; p < TS * TS; p += 256) {
+        const int x = x0 + p % TS, y = y0 + p / TS;
+        if (x < v.cam.width && y < v.cam.height) sum += (float)v.n_contrib[(size_t)y * v.cam.width + x];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < 8; w++) t += s_w[w];
+        v.tile_work[tile] = t >= 4.0e9f ? 4000000000u : (uint32_t)t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) tile_order_kernel(const char *__restrict__ ba) {
+    __shared__ uint32_t s_cls[kWorkClasses];
+    const View &v = view_of(ba, 0);
+    const int T = v.ntiles, tid = threadIdx.x;
+    for (int i = tid; i < kWorkClasses; i += 1024) s_cls[i] = 0u;
+    __syncthreads();
+    for (int t = tid; t < T; t += 1024) atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u);
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t pos = 0;
+        for (int c = kWorkClasses - 1; c >= 0; c--) {
+            const uint32_t k = s_cls[c];
+            s_cls[c] = pos;
+            pos += k;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < T; t += 1024) v.tile_order[atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u)] = (uint32_t)t;
+}
+
 template <int TS, int BATCH>
 void launch_bb(const char *ba, int ntiles, const float *dl, const float *dlf, cudaStream_t st) {
     if (dlf) blend_backward_kernel<TS, BATCH, true><<<ntiles, BlendShape<TS>::NT, 0, st>>>(ba, dl, dlf);
@@ -622,6 +685,14 @@ cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float
     if (v.n == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(v.grad2d, 0, (size_t)v.n * kG2 * sizeof(float), st);
     if (e != cudaSuccess) return e;
+    note_launch(st);
+    switch (args.tile) {   // the replay's tile order (heaviest first) from the forward's walked entries
+        case 8: tile_work_kernel<8><<<v.ntiles, 256, 0, st>>>(batch_area); break;
+        case 16: tile_work_kernel<16><<<v.ntiles, 256, 0, st>>>(batch_area); break;
+        default: tile_work_kernel<32><<<v.ntiles, 256, 0, st>>>(batch_area); break;
+    }
+    note_launch(st);
+    tile_order_kernel<<<1, 1024, 0, st>>>(batch_area);
     note_launch(st);
     switch (args.tile) {   // the staging depth of the backward follows the tile size
         case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;

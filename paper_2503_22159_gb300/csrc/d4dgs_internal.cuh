@@ -78,6 +78,7 @@ struct Layout {
     // zero-initialised region [0, zero_end)
     int64_t control = 0, grid = 0, lb_depth = 0, lb_col = 0, lb_tile = 0, zero_end = 0;
     // the rest
+    int64_t tile_order = 0, tile_work = 0;   // ntiles uint32 each, written by the backward
     int64_t cmat = 0;      // direct binning: parts_dir x ntiles uint32 (not cleared: every entry is written)
     int64_t cgrp = 0;      // direct binning: parts_dir x ntiles uint64 group counts (likewise)
     int64_t colbase = 0, ranges = 0, records = 0, depth_keys[2] = {0, 0}, depth_vals[2] = {0, 0}, tiles_touched = 0, rect = 0;
@@ -136,6 +137,8 @@ struct View {
     ushort4 *rect;
     unsigned long long *trim;        // column trims of each rectangle (tile_trim.cuh)
     uint2 *ranges;
+    uint32_t *tile_order;            // tiles, most walked entries first (written by the backward)
+    uint32_t *tile_work;             // per tile: list entries the forward walked, summed over its pixels
     float *final_T;
     uint32_t *n_contrib;
     float *grad2d;

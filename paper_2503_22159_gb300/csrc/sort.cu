@@ -458,14 +458,13 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
 template <bool TRIM>
 __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__ ba, int col_cap) {
     static_assert(kDupThreads == 256 && kDupItems == 256, "8 warps of 32 Gaussians per partition");
-    extern __shared__ uint32_t s_dyn[];   // [8][col_cap] per-warp column counts, then [col_cap] bases
+    extern __shared__ uint32_t s_dyn[];   // [8][col_cap] per-warp column counts, then running positions
     __shared__ uint32_t s_id[kDupItems];
     __shared__ ushort4 s_rect[kDupItems];
     __shared__ float s_inv[kDupItems];   // 1 / rectangle height, once per Gaussian by its own thread
     __shared__ unsigned long long s_trim[TRIM ? kDupItems : 1];
     __shared__ uint32_t s_part;
     grid_dependency_wait();
-    uint32_t *s_base = s_dyn + 8 * col_cap;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
     const int nviews = (int)bw[kBaNViews];
@@ -541,8 +540,11 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
                                              v.spin_limit);
                 st_volatile_u32(lb, kFlagInc | ((excl + run) & kValMask));
             }
+            // the warps' running positions in column c: bucket start + partition offset + warp prefix
             const unsigned long long b = (unsigned long long)v.colbase[c] + excl;
-            s_base[c] = (uint32_t)(b < cap ? b : cap);
+            const uint32_t base = (uint32_t)(b < cap ? b : cap);
+#pragma unroll
+            for (int w = 0; w < 8; w++) s_dyn[w * col_cap + c] += base;
         }
         __syncthreads();
         // ---- 3. emission, warp w: Gaussians w*32 .. w*32+31 in order
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
                 const int top = TRIM ? trim_top(tq, cc) : 0;
                 if (TRIM && (rr < top || rr >= hgt - trim_bot(tq, cc))) continue;   // cut away
                 const int c = (int)rq.x + cc;
-                const uint32_t o = s_base[c] + wcnt[c] + (uint32_t)(rr - top);
+                const uint32_t o = wcnt[c] + (uint32_t)(rr - top);
                 if (o < cap) {
                     const uint32_t tk = (uint32_t)((int)rq.z + rr);   // the tile row
                     if (packed) {
@@ -929,7 +931,7 @@ int occupancy_blocks(const void *fn, int threads, size_t smem = 0) {
 }  // namespace
 
 // dynamic shared memory of the emission for a launch's column capacity
-constexpr size_t emit_smem(int col_cap) { return (size_t)9 * col_cap * sizeof(uint32_t); }
+constexpr size_t emit_smem(int col_cap) { return (size_t)8 * col_cap * sizeof(uint32_t); }
 
 int sort_launch_count(int n, int tile_passes, int grid_cells) {
     // tile counts (own launch unless they ride with the first depth pass) + 4 depth passes + either
