@@ -153,10 +153,12 @@ typedef struct {
                                     top | rows cut at the bottom << 4 (0..15 each); the
                                     Gaussian's tiles are the rectangle minus these cuts,
                                     tiles_touched of them                                    */
-    int64_t tile_order;          /* tiles uint32: the order in which the backward's tile replay
-                                    takes the tiles, most work first (quarter-octave classes
-                                    of the list entries the forward walked over the tile's
-                                    pixels; written by d4dgs_render_backward)                  */
+    int64_t tile_order;          /* tiles uint32: the order in which the blend and the
+                                    backward's tile replay take the tiles, most work first
+                                    (quarter-octave classes of the list entries walked over
+                                    each tile's pixels: for the blend those of the frame last
+                                    blended in this workspace, for the backward those of its
+                                    own frame).  Any order gives the same image.               */
 } d4dgs_layout;
 
 /* Bytes of workspace for N Gaussians, this camera and config, and room for

@@ -603,43 +603,13 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
 
 // ---------------------------------------------------------------------------
 // Tile order of the replay.  A tile's replay time follows the list entries its
-// pixels walked in the forward (n_contrib); taken in row-major order, the
-// heaviest tiles can be among the last to start and leave most SMs idle while
-// they finish.  So the replay takes the tiles heaviest first: per tile the
-// walked entries summed over its pixels, then (one CTA) quarter-octave classes
-// of that sum counted, scanned from the heaviest down and the tiles scattered
-// (order within a class: whatever the atomics give; any order gives the same
-// gradients up to the order of their floating-point sums).
-__device__ __forceinline__ int work_class(uint32_t k) {
-    if (k == 0u) return 0;
-    const int l = 31 - __clz(k);
-    const uint32_t f = l >= 2 ? (k >> (l - 2)) & 3u : (k << (2 - l)) & 3u;
-    return 1 + 4 * l + (int)f;
-}
-constexpr int kWorkClasses = 1 + 4 * 32;
-
-template <int TS>
-__global__ void __launch_bounds__(256) tile_work_kernel(const char *__restrict__ ba) {
-    __shared__ float s_w[8];
-    const View &v = view_of(ba, 0);
-    const int tile = blockIdx.x, tiles_x = v.cam.tiles_x;
-    const int x0 = (tile % tiles_x) * TS, y0 = (tile / tiles_x) * TS;
-    float sum = 0.0f;   // a weight: float keeps large sums without overflow
-    for (int p = threadIdx.x; p < TS * TS; p += 256) {
-        const int x = x0 + p % TS, y = y0 + p / TS;
-        if (x < v.cam.width && y < v.cam.height) sum += (float)v.n_contrib[(size_t)y * v.cam.width + x];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.0f;
-        for (int w = 0; w < 8; w++) t += s_w[w];
-        v.tile_work[tile] = t >= 4.0e9f ? 4000000000u : (uint32_t)t;
-    }
-}
-
+// pixels walked in the forward, which the blend left per tile (tile_work); taken
+// in row-major order, the heaviest tiles can be among the last to start and
+// leave most SMs idle while they finish.  So the replay takes the tiles
+// heaviest first: (one CTA) quarter-octave classes of the work counted,
+// scanned from the heaviest down and the tiles scattered (order within a
+// class: whatever the atomics give; any order gives the same gradients up to
+// the order of their floating-point sums).
 __global__ void __launch_bounds__(1024) tile_order_kernel(const char *__restrict__ ba) {
     __shared__ uint32_t s_cls[kWorkClasses];
     const View &v = view_of(ba, 0);
@@ -686,13 +656,7 @@ cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float
     cudaError_t e = cudaMemsetAsync(v.grad2d, 0, (size_t)v.n * kG2 * sizeof(float), st);
     if (e != cudaSuccess) return e;
     note_launch(st);
-    switch (args.tile) {   // the replay's tile order (heaviest first) from the forward's walked entries
-        case 8: tile_work_kernel<8><<<v.ntiles, 256, 0, st>>>(batch_area); break;
-        case 16: tile_work_kernel<16><<<v.ntiles, 256, 0, st>>>(batch_area); break;
-        default: tile_work_kernel<32><<<v.ntiles, 256, 0, st>>>(batch_area); break;
-    }
-    note_launch(st);
-    tile_order_kernel<<<1, 1024, 0, st>>>(batch_area);
+    tile_order_kernel<<<1, 1024, 0, st>>>(batch_area);   // the replay's order from this frame's tile work
     note_launch(st);
     switch (args.tile) {   // the staging depth of the backward follows the tile size
         case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;

@@ -37,6 +37,12 @@ namespace d4dgs {
 namespace {
 
 
+// warps of a forward CTA
+template <int TS>
+struct FwdWarps {
+    static constexpr int value = BlendShape<TS>::NT / 32;
+};
+
 // COUNT: instrumented variant for profiling (not used on the render path),
 // which also totals into counts[0..2]: (pixel, Gaussian) pairs the warps
 // evaluated, pairs blended, and the tile-algorithm work sum over tiles of
@@ -58,6 +64,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
     __shared__ uint32_t s_m[BATCH];  // blocks the Gaussian's alpha >= 1/255 ellipse reaches
     __shared__ int32_t s_item;
     __shared__ uint32_t s_stop;
+    __shared__ float s_wsum[FwdWarps<TS>::value];   // per warp: list entries its pixels walked
     grid_dependency_wait();
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
     const int nviews = (int)bw[kBaNViews];
@@ -82,7 +89,12 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
         for (int u = 1; u < nviews; u++)
             if (view_of(ba, u).tile_base <= item) vi = u;
         const View &v = view_of(ba, vi);
-        const int tile = item - v.tile_base;
+        int tile = item - v.tile_base;
+        {   // heaviest tiles first (the order the binning derived from the previous frame's walked
+            // entries: nearby frames load nearby tiles alike); kept in range whatever the buffer holds
+            const uint32_t o = v.tile_order[tile];
+            if (o < (uint32_t)v.ntiles) tile = (int)o;
+        }
         const int tiles_x = v.cam.tiles_x, width = v.cam.width, height = v.cam.height;
         const uint32_t n = (uint32_t)v.n, cap = v.cap;
         const bool packed = v.packed != 0;
@@ -280,6 +292,23 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
             const int npx = min(TS, width - x0) * min(TS, height - y0);
             if (threadIdx.x == 0) n_work += (unsigned long long)npx * s_stop;
             __syncthreads();
+        }
+        {   // this tile's work for the next frame's order and this frame's backward: entries walked,
+            // summed over the tile's pixels (a float weight: no overflow)
+            float ws = 0.0f;
+#pragma unroll
+            for (int i = 0; i < PX; i++)
+                if (px < width && py + i < height) ws += (float)walked[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xFFFFFFFFu, ws, o);
+            if (lane == 0) s_wsum[warp] = ws;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float t = 0.0f;
+#pragma unroll
+                for (int w = 0; w < FwdWarps<TS>::value; w++) t += s_wsum[w];
+                v.tile_work[tile] = t >= 4.0e9f ? 4000000000u : (uint32_t)t;
+            }
         }
         const float bg0 = v.bg[0], bg1 = v.bg[1], bg2 = v.bg[2];
 #pragma unroll

@@ -245,6 +245,16 @@ __device__ __forceinline__ float alpha_exp2(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// Class of a tile's work (list entries walked, summed over its pixels) for the
+// heaviest-first tile orders: 0 for none, else 1 + 4 floor(log2 k) + the two
+// bits below k's leading one (quarter octaves).
+constexpr int kWorkClasses = 1 + 4 * 32;
+__device__ __forceinline__ int work_class(uint32_t k) {
+    if (k == 0u) return 0;
+    const int l = 31 - __clz(k);
+    const uint32_t f = l >= 2 ? (k >> (l - 2)) & 3u : (k << (2 - l)) & 3u;
+    return 1 + 4 * l + (int)f;
+}
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

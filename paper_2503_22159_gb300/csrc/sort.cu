@@ -253,6 +253,28 @@ __device__ __forceinline__ void tile_count_view(const View &v, int *s_grid, int 
         ctl[kCtlNumKeys] = all > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)all;
         if (all > cap) atomicOr(ctl + kCtlStatus, kStatusCapacity);
     }
+    // ---- the blend's tile order, heaviest first: a tile's blend time follows the list entries its
+    // pixels walk, which the last frame blended in this workspace left per tile (tile_work; a frame
+    // of an animation loads its tiles much like its predecessor).  Taken in row-major order, heavy
+    // tiles late in the grid leave most SMs idle while they finish.  Quarter-octave classes of the
+    // work, counted, scanned from the heaviest down, the tiles scattered; any order (stale, or from
+    // whatever the buffer held) gives the same image.
+    __syncthreads();
+    uint32_t *s_cls = s_hist;   // class counts, then each class's next position
+    for (int i = tid; i < kWorkClasses; i += nt) s_cls[i] = 0u;
+    __syncthreads();
+    for (int t = tid; t < ntiles; t += nt) atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u);
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t pos = 0;
+        for (int c = kWorkClasses - 1; c >= 0; c--) {
+            const uint32_t k = s_cls[c];
+            s_cls[c] = pos;
+            pos += k;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < ntiles; t += nt) v.tile_order[atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u)] = (uint32_t)t;
 }
 
 // tc_cells (first depth pass only): when positive, the launch's first
