@@ -282,7 +282,7 @@ __device__ __forceinline__ void tile_count_view(const View &v, int *s_grid, int 
 // tc_cells ints of dynamic shared memory) instead of sorting, so that work
 // overlaps the pass rather than taking a launch of its own.
 template <bool KV, bool IOTA, bool TILE>
-__global__ void __launch_bounds__(kSortThreads, TILE ? (KV ? 3 : 4) : 2)
+__global__ void __launch_bounds__(kSortThreads, TILE ? (KV ? 2 : 3) : 2)
 onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells) {
     constexpr int IPT = TILE ? kTileIPT : kDepthIPT;
     constexpr int ITEMS = kSortThreads * IPT;

@@ -96,7 +96,7 @@ def test_lists_bit_exact_medium_ragged(tile, trim, binning):
     assert (r.layout(cam)["tile_passes"] == 1) == (binning == 2)
     got = gu.gpu_lists(r, cam)
     b, exp = gu.expected_lists(scene, cam, t, tile, trim=trim)
-    assert len(exp["tile"]) > 10 * 3840, "the case should span many sort partitions"
+    assert len(exp["tile"]) > 10 * 5120, "the case should span many sort partitions"
     gu.compare_lists(got, b, exp)
 
 
