@@ -665,7 +665,7 @@ def run_kernel_times(dev, d4, w, scene, cfg, r, frames, peaks, alu_peak, evals_p
     for p in range(1, L["tile_passes"]):
         bytes_of[f"row_pass_{p}"] = (K * 2 * pair_b, "pair read and written")
     ntiles = L["tiles_x"] * L["tiles_y"]
-    cm = 4 * ntiles * ((n + 1023) // 1024)   # the (1024-Gaussian partition, tile) count matrix
+    cm = 4 * ntiles * ((n + 255) // 256)     # the (256-Gaussian partition, tile) count matrix
     bytes_of["dir_count"] = (n * (16 + trim) + cm, "depth order, rectangle, count (+ cuts) read; count matrix written")
     bytes_of["dir_scan"] = (3 * cm + ntiles * 8, "count matrix read twice and rewritten as offsets; ranges read")
     bytes_of["dir_emit"] = (n * (16 + trim) + cm + K * pair_b,
@@ -686,7 +686,7 @@ def run_kernel_times(dev, d4, w, scene, cfg, r, frames, peaks, alu_peak, evals_p
                         "ops": f"{FP32_OPS_PER_PAIR} per (pixel, Gaussian) pair the kernel evaluates",
                         "frac_tile_walk": FP32_OPS_PER_PAIR * work_pf / (t_ms * 1e-3) / 1e12 / alu_peak}
         kern[name] = e
-    binning = [k for k in names if k.startswith(("tilecount", "depth_pass", "emit", "row_pass", "dir_"))]
+    binning = [k for k in names if k.startswith(("tilecount", "depth_pass", "emit", "row_", "dir_"))]
     return {"frames": len(frames), "launches": names, "kernels": kern,
             "binning_ms": float(sum(kern[k]["ms"] for k in binning)),
             "sum_ms": float(ms.sum()), "keys_per_frame": K,
