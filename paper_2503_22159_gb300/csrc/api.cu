@@ -371,7 +371,7 @@ int d4dgs_preprocess(const d4dgs_scene *scene, const d4dgs_camera *cam, float t,
     char *ba = at<char>(ws, L.batch);
     const int sms = num_sms_current();
     cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
-    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms, true);
     return cuda_status(e);
 }
 
@@ -423,7 +423,7 @@ int d4dgs_render(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, con
     char *ba = at<char>(ws, L.batch);
     const int sms = num_sms_current();
     cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
-    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms, true);
     if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
     if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
     return cuda_status(e);
@@ -454,7 +454,7 @@ int d4dgs_preprocess_slicing(const d4dgs_scene4d *scene, const d4dgs_camera *cam
     char *ba = at<char>(ws, L.batch);
     const int sms = num_sms_current();
     cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
-    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms, true);
     return cuda_status(e);
 }
 
@@ -469,7 +469,7 @@ int d4dgs_render_slicing(const d4dgs_scene4d *scene, const d4dgs_camera *cam, fl
     char *ba = at<char>(ws, L.batch);
     const int sms = num_sms_current();
     cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
-    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms, true);
     if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
     if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
     return cuda_status(e);
@@ -538,7 +538,7 @@ int d4dgs_render_flow(const d4dgs_scene *scene, const d4dgs_camera *cam, float t
     char *ba = at<char>(ws, L.batch);
     const int sms = num_sms_current();
     cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
-    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms, true);
     if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
     if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
     return cuda_status(e);
@@ -603,7 +603,7 @@ int d4dgs_render_batch_stages(const void *args_host, const void *args_dev, void 
     const int sms = num_sms_current();
     cudaError_t e = cudaSuccess;
     if (stages & 1) e = launch_clear(b, args_dev, ba, st, sms);
-    if (e == cudaSuccess && (stages & 1)) e = launch_preprocess(b, ba, st, sms);
+    if (e == cudaSuccess && (stages & 1)) e = launch_preprocess(b, ba, st, sms, args_dev == nullptr);
     if (e == cudaSuccess && (stages & 2)) e = launch_sort(b, ba, st, sms);
     if (e == cudaSuccess && (stages & 4)) e = launch_blend(b, ba, st, sms, nullptr, nullptr, /*persist=*/true);
     return cuda_status(e);

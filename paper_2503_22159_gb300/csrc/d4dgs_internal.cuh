@@ -208,7 +208,10 @@ bool finish_batch(BatchArgs *b);
 // host copy; `args_dev`, when not null, is a device copy the first kernel reads
 // instead of its by-value parameter (for CUDA graphs whose descriptors change).
 cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batch_area, cudaStream_t st, int num_sms);
-cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms);
+// host_views: args is the batch the kernels will read (false when the first
+// kernel takes the descriptors from device memory instead)
+cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms,
+                              bool host_views);
 cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms);
 cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, float *out0,
                          unsigned long long *counts = nullptr, bool persist = false);

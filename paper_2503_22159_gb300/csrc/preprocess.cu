@@ -498,8 +498,11 @@ __device__ __forceinline__ void flush_view(const View &v, uint32_t *hist, uint32
 // view alone, so a grouped view's outputs equal the ungrouped ones bit for bit.
 // KIND: 0 disentangled, 1 slicing-first (every view of a launch has the same kind).
 // CACHE: config colour_cache (shared by every view of a launch).
-template <int KIND, bool CACHE>
-__global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restrict__ ba, int smem_cells) {
+// PARAM: a launch of one view whose descriptor also travels as the kernel
+// parameter v0, read from the constant bank instead of the batch table.
+template <int KIND, bool CACHE, bool PARAM>
+__global__ void __launch_bounds__(256, 4)
+preprocess_kernel(const char *__restrict__ ba, int smem_cells, const __grid_constant__ View v0) {
     __shared__ uint32_t hist[kMaxGroup][4 * kRadix];
     __shared__ int32_t s_chunk;
     extern __shared__ int s_grid[];
@@ -513,16 +516,20 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restri
     uint32_t nvis[kMaxGroup];
 #pragma unroll
     for (int b = 0; b < kMaxGroup; b++) nvis[b] = 0;
+    auto view = [&](int u) -> const View & {
+        if constexpr (PARAM) return v0;
+        else return view_of(ba, u);
+    };
     int cur = -1;   // first view of the group whose sums the CTA holds
     // shared-memory grid of slot b of group `lead` (null: the group's grids go to global memory)
     auto slot_grid = [&](int lead, int b) -> int * {
-        const View &l = view_of(ba, lead);
+        const View &l = view(lead);
         const int cells = grid_cells(l);
         return cells * l.group_size <= smem_cells ? s_grid + b * cells : nullptr;
     };
     auto flush_group = [&](int lead) {
-        const int gs = view_of(ba, lead).group_size;
-        for (int b = 0; b < gs; b++) flush_view(view_of(ba, lead + b), hist[b], nvis[b], slot_grid(lead, b));
+        const int gs = view(lead).group_size;
+        for (int b = 0; b < gs; b++) flush_view(view(lead + b), hist[b], nvis[b], slot_grid(lead, b));
     };
     for (;;) {
         if (threadIdx.x == 0) s_chunk = (int32_t)atomicAdd(counter, 1u);
@@ -531,20 +538,20 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const char *__restri
         __syncthreads();
         if (chunk >= total) break;
         int lead = 0;
-        for (int u = 1; u < nviews; u++) {
-            const View &w = view_of(ba, u);
+        for (int u = 1; u < (PARAM ? 1 : nviews); u++) {
+            const View &w = view(u);
             if (w.group_size > 0 && w.chunk_base <= chunk) lead = u;
         }
         if (lead != cur) {
             if (cur >= 0) flush_group(cur);
             cur = lead;
         }
-        const View &l = view_of(ba, lead);
+        const View &l = view(lead);
         const int i = (chunk - l.chunk_base) * kPreChunk + (int)threadIdx.x;
         const int gs = l.group_size;
         float4 cc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // colour cache of this Gaussian (w = 1: valid)
         for (int b = 0; b < gs; b++) {
-            const View &v = view_of(ba, lead + b);
+            const View &v = view(lead + b);
             int *sg = slot_grid(lead, b);
             if (i < v.n) {
                 switch (v.sh_degree) {
@@ -625,29 +632,35 @@ cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batc
     return cudaGetLastError();
 }
 
-cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms) {
+cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms,
+                              bool host_views) {
     if (args.total_chunks == 0) return cudaSuccess;
     // persistent grid of the CTAs that are resident at once (a CTA beyond them would only start
     // once the chunks are gone, and still clear and flush its shared sums); grids of up to
     // 6144 cells (e.g. 1352x1014 at 32-px tiles) are aggregated in shared memory
     constexpr int kSmemCells = 6144;
     constexpr size_t kSmem = kSmemCells * sizeof(int);
-    static int occ[3] = {0, 0, 0};   // by variant, queried once
-    auto resident = [&](const void *fn, int which) {
-        if (!occ[which] && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[which], fn, 256, kSmem) != cudaSuccess ||
+    static int occ[6] = {0, 0, 0, 0, 0, 0};   // by variant, queried once
+    auto go = [&](auto fn, int which) {
+        if (!occ[which] && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[which], (const void *)fn, 256, kSmem) !=
+                                cudaSuccess ||
                             occ[which] < 1))
             occ[which] = 1;
-        return occ[which] * num_sms;
+        return launch_chained(fn, occ[which] * num_sms, 256, kSmem, st, (const char *)batch_area, kSmemCells,
+                              args.v[0]);
     };
-    const cudaError_t e =
-        args.v[0].kind == 1
-            ? launch_chained(preprocess_kernel<1, false>, resident((const void *)preprocess_kernel<1, false>, 0), 256,
-                             kSmem, st, (const char *)batch_area, kSmemCells)
-        : args.v[0].colour_cache
-            ? launch_chained(preprocess_kernel<0, true>, resident((const void *)preprocess_kernel<0, true>, 1), 256,
-                             kSmem, st, (const char *)batch_area, kSmemCells)
-            : launch_chained(preprocess_kernel<0, false>, resident((const void *)preprocess_kernel<0, false>, 2), 256,
-                             kSmem, st, (const char *)batch_area, kSmemCells);
+    // one view whose descriptor the host holds: the descriptor as a kernel parameter
+    const bool param = host_views && args.nviews == 1;
+    const int kind = args.v[0].kind == 1 ? 0 : args.v[0].colour_cache ? 1 : 2;
+    cudaError_t e;
+    if (param)
+        e = kind == 0 ? go(preprocess_kernel<1, false, true>, 3)
+            : kind == 1 ? go(preprocess_kernel<0, true, true>, 4)
+                        : go(preprocess_kernel<0, false, true>, 5);
+    else
+        e = kind == 0 ? go(preprocess_kernel<1, false, false>, 0)
+            : kind == 1 ? go(preprocess_kernel<0, true, false>, 1)
+                        : go(preprocess_kernel<0, false, false>, 2);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
