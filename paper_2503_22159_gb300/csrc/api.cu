@@ -381,7 +381,7 @@ int d4dgs_sort(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void
     Layout L;
     int rc = single(nullptr, n, cam, 0.0f, cfg, ws, ws_bytes, nullptr, &b, &L);
     if (rc) return rc;
-    return cuda_status(launch_sort(b, at<char>(ws, L.batch), reinterpret_cast<cudaStream_t>(stream), num_sms_current()));
+    return cuda_status(launch_sort(b, at<char>(ws, L.batch), reinterpret_cast<cudaStream_t>(stream), num_sms_current(), true));
 }
 
 int d4dgs_blend(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
@@ -424,7 +424,7 @@ int d4dgs_render(const d4dgs_scene *scene, const d4dgs_camera *cam, float t, con
     const int sms = num_sms_current();
     cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
     if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms, true);
-    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms, true);
     if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
     return cuda_status(e);
 }
@@ -470,7 +470,7 @@ int d4dgs_render_slicing(const d4dgs_scene4d *scene, const d4dgs_camera *cam, fl
     const int sms = num_sms_current();
     cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
     if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms, true);
-    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms, true);
     if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
     return cuda_status(e);
 }
@@ -539,7 +539,7 @@ int d4dgs_render_flow(const d4dgs_scene *scene, const d4dgs_camera *cam, float t
     const int sms = num_sms_current();
     cudaError_t e = launch_clear(b, nullptr, ba, st, sms);
     if (e == cudaSuccess) e = launch_preprocess(b, ba, st, sms, true);
-    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess) e = launch_sort(b, ba, st, sms, true);
     if (e == cudaSuccess) e = launch_blend(b, ba, st, sms, nullptr);
     return cuda_status(e);
 }
@@ -604,7 +604,7 @@ int d4dgs_render_batch_stages(const void *args_host, const void *args_dev, void 
     cudaError_t e = cudaSuccess;
     if (stages & 1) e = launch_clear(b, args_dev, ba, st, sms);
     if (e == cudaSuccess && (stages & 1)) e = launch_preprocess(b, ba, st, sms, args_dev == nullptr);
-    if (e == cudaSuccess && (stages & 2)) e = launch_sort(b, ba, st, sms);
+    if (e == cudaSuccess && (stages & 2)) e = launch_sort(b, ba, st, sms, args_dev == nullptr);
     if (e == cudaSuccess && (stages & 4)) e = launch_blend(b, ba, st, sms, nullptr, nullptr, /*persist=*/true);
     return cuda_status(e);
 }

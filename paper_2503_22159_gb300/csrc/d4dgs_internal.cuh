@@ -212,7 +212,7 @@ cudaError_t launch_clear(const BatchArgs &args, const void *args_dev, char *batc
 // kernel takes the descriptors from device memory instead)
 cudaError_t launch_preprocess(const BatchArgs &args, const char *batch_area, cudaStream_t st, int num_sms,
                               bool host_views);
-cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms);
+cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, bool host_views);
 cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, float *out0,
                          unsigned long long *counts = nullptr, bool persist = false);
 cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb, const float *dl_dflow,

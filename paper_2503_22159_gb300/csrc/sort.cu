@@ -126,12 +126,12 @@ __device__ __forceinline__ uint32_t lookback_serial(const uint32_t *base, size_t
 
 // Partition bases of a pass over the views of a launch (prefix sums of each
 // view's partition count), in shared memory; returns the total.
-template <bool TILE>
-__device__ __forceinline__ uint32_t pass_bases(const char *ba, int nviews, uint32_t *s_base) {
+template <bool TILE, bool PARAM>
+__device__ __forceinline__ uint32_t pass_bases(const char *ba, int nviews, uint32_t *s_base, const View &v0) {
     if (threadIdx.x == 0) {
         uint32_t acc = 0;
         for (int u = 0; u < nviews; u++) {
-            const View &v = view_of(ba, u);
+            const View &v = PARAM ? v0 : view_of(ba, u);
             s_base[u] = acc;
             uint32_t parts;
             if (TILE) {
@@ -277,13 +277,15 @@ __device__ __forceinline__ void tile_count_view(const View &v, int *s_grid, int 
     for (int t = tid; t < ntiles; t += nt) v.tile_order[atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u)] = (uint32_t)t;
 }
 
+// PARAM: a launch of one view whose descriptor also travels as the kernel
+// parameter v0 (constant bank) instead of being read from the batch table.
 // tc_cells (first depth pass only): when positive, the launch's first
 // kMaxViews CTAs do the tile counts of the views (tile_count_view, grid in
 // tc_cells ints of dynamic shared memory) instead of sorting, so that work
 // overlaps the pass rather than taking a launch of its own.
-template <bool KV, bool IOTA, bool TILE>
+template <bool KV, bool IOTA, bool TILE, bool PARAM>
 __global__ void __launch_bounds__(kSortThreads, TILE ? (KV ? 2 : 3) : 2)
-onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells) {
+onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells, const __grid_constant__ View v0) {
     constexpr int IPT = TILE ? kTileIPT : kDepthIPT;
     constexpr int ITEMS = kSortThreads * IPT;
     __shared__ uint32_t s_warp_hist[8][kRadix];
@@ -299,17 +301,17 @@ onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells) {
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
-    const int nviews = (int)bw[kBaNViews];
+    const int nviews = PARAM ? 1 : (int)bw[kBaNViews];
     if (IOTA && tc_cells > 0 && (int)blockIdx.x < kMaxViews) {
         // leading CTAs (dispatched first, so they run beside the sort): tile counts
         extern __shared__ int s_tc[];   // [3 * kRadix] digit counts, [64] scan words, [tc_cells] grid
         if ((int)blockIdx.x < nviews)
-            tile_count_view(view_of(ba, blockIdx.x), s_tc + 3 * kRadix + 64, tc_cells,
+            tile_count_view(PARAM ? v0 : view_of(ba, blockIdx.x), s_tc + 3 * kRadix + 64, tc_cells,
                             reinterpret_cast<uint32_t *>(s_tc), reinterpret_cast<unsigned long long *>(s_tc + 3 * kRadix));
         return;
     }
     uint32_t *part_counter = bw + (TILE ? kBaTile : kBaDepth) + pass;
-    const uint32_t total = pass_bases<TILE>(ba, nviews, s_base);
+    const uint32_t total = pass_bases<TILE, PARAM>(ba, nviews, s_base, v0);
     int cur = -1;
 
     for (;;) {
@@ -321,7 +323,7 @@ onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells) {
         int vi = 0;
         for (int u = 1; u < nviews; u++)
             if (s_base[u] <= g) vi = u;
-        const View &v = view_of(ba, vi);
+        const View &v = PARAM ? v0 : view_of(ba, vi);
         const uint32_t part = g - s_base[vi];
         const uint32_t *keys_in = TILE ? v.tkeys[pass & 1] : v.dkeys[pass & 1];
         uint32_t *keys_out = TILE ? v.tkeys[(pass + 1) & 1] : v.dkeys[(pass + 1) & 1];
@@ -477,8 +479,10 @@ __global__ void __launch_bounds__(1024) tilecount_kernel(char *__restrict__ ba, 
 // The stable row passes that follow leave every tile's list in (depth, id)
 // order.
 // TRIM: the launch's views cut their rectangles per column (config trim).
-template <bool TRIM>
-__global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__ ba, int col_cap) {
+// PARAM: one view, its descriptor the kernel parameter v0.
+template <bool TRIM, bool PARAM>
+__global__ void __launch_bounds__(kDupThreads, 6)
+emit_kernel(char *__restrict__ ba, int col_cap, const __grid_constant__ View v0) {
     static_assert(kDupThreads == 256 && kDupItems == 256, "8 warps of 32 Gaussians per partition");
     extern __shared__ uint32_t s_dyn[];   // [8][col_cap] per-warp column counts, then running positions
     __shared__ uint32_t s_id[kDupItems];
@@ -489,8 +493,8 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
     grid_dependency_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
-    const int nviews = (int)bw[kBaNViews];
-    const uint32_t total = bw[kBaTotalDupParts];
+    const int nviews = PARAM ? 1 : (int)bw[kBaNViews];
+    const uint32_t total = PARAM ? (uint32_t)v0.parts_dup : bw[kBaTotalDupParts];
     uint32_t *part_counter = bw + kBaDup;
 
     for (;;) {
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(kDupThreads, 6) emit_kernel(char *__restrict__
         int vi = 0;
         for (int u = 1; u < nviews; u++)
             if ((uint32_t)view_of(ba, u).dup_part_base <= g) vi = u;
-        const View &v = view_of(ba, vi);
+        const View &v = PARAM ? v0 : view_of(ba, vi);
         const uint32_t part = g - (uint32_t)v.dup_part_base;
         const uint32_t n = (uint32_t)v.n, cap = v.cap;
         const int ncols = v.cam.tiles_x;
@@ -1000,19 +1004,23 @@ cudaError_t launch_direct(const BatchArgs &args, char *batch_area, cudaStream_t 
 
 }  // namespace
 
-cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
-    static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0;
+namespace {
+
+template <bool PARAM>
+cudaError_t sort_passes(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
+    const View &v0 = args.v[0];
+    static int occ_iota = 0, occ_kv = 0, occ_k = 0, occ_tkv = 0;   // per PARAM instantiation
     static int occ_emit[2][16] = {};   // by trim and log2 of the column capacity
     if (!occ_kv) {
-        occ_iota = occupancy_blocks((const void *)onesweep_kernel<true, true, false>, kSortThreads);
-        occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false, false>, kSortThreads);
-        occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false, true>, kSortThreads);
-        occ_tkv = occupancy_blocks((const void *)onesweep_kernel<true, false, true>, kSortThreads);
+        occ_iota = occupancy_blocks((const void *)onesweep_kernel<true, true, false, PARAM>, kSortThreads);
+        occ_kv = occupancy_blocks((const void *)onesweep_kernel<true, false, false, PARAM>, kSortThreads);
+        occ_k = occupancy_blocks((const void *)onesweep_kernel<false, false, true, false>, kSortThreads);
+        occ_tkv = occupancy_blocks((const void *)onesweep_kernel<true, false, true, false>, kSortThreads);
         // the first depth pass carries the tile counts' grid (up to kTileCountCells ints) on top of its own arrays
-        cudaFuncSetAttribute(onesweep_kernel<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(onesweep_kernel<true, true, false, PARAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((3 * kRadix + 64 + kTileCountCells) * sizeof(int)));
-        cudaFuncSetAttribute(emit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
-        cudaFuncSetAttribute(emit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
+        cudaFuncSetAttribute(emit_kernel<false, PARAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
+        cudaFuncSetAttribute(emit_kernel<true, PARAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emit_smem(kMaxCols));
     }
     // ---- 0. per-tile counts, ranges, tile digit histograms (always: ranges are written for every tile).
     // When every view's grid fits kTileCountCells, leading CTAs of the first depth pass do it (in
@@ -1046,12 +1054,12 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
             const size_t tc_smem = tc_cells ? (size_t)(3 * kRadix + 64 + tc_cells) * sizeof(int) : 0;
             static int occ_tc[kTileCountCells / 256 + 1] = {0};   // by grid cells / 256
             int &occ = tc_cells ? occ_tc[tc_cells / 256] : occ_iota;
-            if (!occ) occ = occupancy_blocks((const void *)onesweep_kernel<true, true, false>, kSortThreads, tc_smem);
-            e = launch_chained(onesweep_kernel<true, true, false>, occ * num_sms + (tc_cells ? kMaxViews : 0),
-                               kSortThreads, tc_smem, st, batch_area, p, tc_cells);
+            if (!occ) occ = occupancy_blocks((const void *)onesweep_kernel<true, true, false, PARAM>, kSortThreads, tc_smem);
+            e = launch_chained(onesweep_kernel<true, true, false, PARAM>, occ * num_sms + (tc_cells ? kMaxViews : 0),
+                               kSortThreads, tc_smem, st, batch_area, p, tc_cells, v0);
         } else {
-            e = launch_chained(onesweep_kernel<true, false, false>, occ_kv * num_sms, kSortThreads, 0, st, batch_area, p,
-                               0);
+            e = launch_chained(onesweep_kernel<true, false, false, PARAM>, occ_kv * num_sms, kSortThreads, 0, st, batch_area, p,
+                               0, v0);
         }
     }
     if (e != cudaSuccess) return e;
@@ -1062,22 +1070,31 @@ cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st
     while ((1 << lc) < args.col_cap) lc++;
     if (args.col_cap > kMaxCols || lc >= 16) return cudaErrorInvalidValue;
     const int ti = args.trim_on ? 1 : 0;
-    const void *emit_fn = args.trim_on ? (const void *)emit_kernel<true> : (const void *)emit_kernel<false>;
+    const void *emit_fn = args.trim_on ? (const void *)emit_kernel<true, PARAM> : (const void *)emit_kernel<false, PARAM>;
     if (!occ_emit[ti][lc]) occ_emit[ti][lc] = occupancy_blocks(emit_fn, kDupThreads, emit_smem(args.col_cap));
-    e = args.trim_on ? launch_chained(emit_kernel<true>, occ_emit[ti][lc] * num_sms, kDupThreads, emit_smem(args.col_cap), st,
-                                   batch_area, (int)args.col_cap)
-                  : launch_chained(emit_kernel<false>, occ_emit[ti][lc] * num_sms, kDupThreads, emit_smem(args.col_cap), st,
-                                   batch_area, (int)args.col_cap);
-    // ---- 3. stable sort of the pairs by tile-row bits (tile passes 1..)
+    e = args.trim_on ? launch_chained(emit_kernel<true, PARAM>, occ_emit[ti][lc] * num_sms, kDupThreads, emit_smem(args.col_cap), st,
+                                   batch_area, (int)args.col_cap, v0)
+                  : launch_chained(emit_kernel<false, PARAM>, occ_emit[ti][lc] * num_sms, kDupThreads, emit_smem(args.col_cap), st,
+                                   batch_area, (int)args.col_cap, v0);
+    // ---- 3. stable sort of the pairs by tile-row bits (tile passes 1..); these read the descriptor
+    // from the batch table whatever PARAM (the parameter form measured 2-3 us slower here)
     for (int p = 1; p < args.tile_passes && e == cudaSuccess; p++) {
         if (args.packed)
-            e = launch_chained(onesweep_kernel<false, false, true>, occ_k * num_sms, kSortThreads, 0, st, batch_area, p,
-                               0);
+            e = launch_chained(onesweep_kernel<false, false, true, false>, occ_k * num_sms, kSortThreads, 0, st, batch_area, p,
+                               0, v0);
         else
-            e = launch_chained(onesweep_kernel<true, false, true>, occ_tkv * num_sms, kSortThreads, 0, st, batch_area, p,
-                               0);
+            e = launch_chained(onesweep_kernel<true, false, true, false>, occ_tkv * num_sms, kSortThreads, 0, st, batch_area, p,
+                               0, v0);
     }
     return e;
+}
+
+}  // namespace
+
+cudaError_t launch_sort(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, bool host_views) {
+    // one view whose descriptor the host holds: the descriptor as a kernel parameter
+    const bool param = host_views && args.nviews == 1;
+    return param ? sort_passes<true>(args, batch_area, st, num_sms) : sort_passes<false>(args, batch_area, st, num_sms);
 }
 
 }  // namespace d4dgs
