@@ -49,8 +49,9 @@ def parse():
     p.add_argument("--tile", default="auto", help="8, 16, 32 or auto (autotuner sweep)")
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--trim", action="store_true", help="cut binning rectangles per column (--tile auto decides)")
-    p.add_argument("--binning", type=int, default=0, choices=(0, 1, 2),
-                   help="config binning of the main frames: 0 library choice, 1 column path, 2 direct")
+    p.add_argument("--binning", type=int, default=0, choices=(0, 1, 2, 3),
+                   help="config binning of the main frames: 0 library choice, 1 column path, 2 direct, "
+                        "3 rank lists")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-e2e", action="store_true")
@@ -613,6 +614,8 @@ def launch_names(d4, n, cam, cfg, ws):
     names += [f"depth_pass_{p}" for p in range(4)]
     if L["tile_passes"] == 1:   # direct binning
         names += ["dir_count", "dir_scan", "dir_emit"]
+    elif L["tile_passes"] == 0:   # rank lists
+        names += ["emit_rank", "rank_list"]
     else:
         names.append("emit")
         names += [f"row_pass_{p}" for p in range(1, L["tile_passes"])]
@@ -666,6 +669,9 @@ def run_kernel_times(dev, d4, w, scene, cfg, r, frames, peaks, alu_peak, evals_p
         bytes_of[f"row_pass_{p}"] = (K * 2 * pair_b, "pair read and written")
     ntiles = L["tiles_x"] * L["tiles_y"]
     cm = 4 * ntiles * ((n + 255) // 256)     # the (256-Gaussian partition, tile) count matrix
+    bytes_of["emit_rank"] = (n * (16 + trim) + K * 4, "depth order, rectangle, count (+ cuts) read; a rank written")
+    bytes_of["rank_list"] = (K * 16, "per pair its rank read, written in order, read again and its id gathered "
+                                     "and written")
     bytes_of["dir_count"] = (n * (16 + trim) + cm, "depth order, rectangle, count (+ cuts) read; count matrix written")
     bytes_of["dir_scan"] = (3 * cm + ntiles * 8, "count matrix read twice and rewritten as offsets; ranges read")
     bytes_of["dir_emit"] = (n * (16 + trim) + cm + K * pair_b,
@@ -686,7 +692,7 @@ def run_kernel_times(dev, d4, w, scene, cfg, r, frames, peaks, alu_peak, evals_p
                         "ops": f"{FP32_OPS_PER_PAIR} per (pixel, Gaussian) pair the kernel evaluates",
                         "frac_tile_walk": FP32_OPS_PER_PAIR * work_pf / (t_ms * 1e-3) / 1e12 / alu_peak}
         kern[name] = e
-    binning = [k for k in names if k.startswith(("tilecount", "depth_pass", "emit", "row_", "dir_"))]
+    binning = [k for k in names if k.startswith(("tilecount", "depth_pass", "emit", "row_", "dir_", "rank_"))]
     return {"frames": len(frames), "launches": names, "kernels": kern,
             "binning_ms": float(sum(kern[k]["ms"] for k in binning)),
             "sum_ms": float(ms.sum()), "keys_per_frame": K,
@@ -1109,7 +1115,7 @@ def run_ours(args):
 
 def run_profile(args):
     """A short, fixed sequence for profiler captures: the workload's frames 150..154 at 32-px tiles,
-    staging depth 256 (the autotuner's choice), each rendered (and, --profile backward, followed
+    staging depth 256 (the autotuner's choice), config binning --binning, each rendered (and, --profile backward, followed
     by the backward with a seeded dL/dC); prints one line of device times."""
     import numpy as np
     import torch
@@ -1120,10 +1126,10 @@ def run_profile(args):
     w = workload(args.workload)
     dev = torch.device("cuda", 0)
     scene = d4.DeviceScene.from_host(w.scene, dev)
-    cfg = d4.config_struct(32, 256)
+    cfg = d4.config_struct(32, 256, binning=args.binning)
     frames = [w.frames[150 + k] for k in range(5)]
     cam0 = frames[0][0]
-    r = d4.Renderer(scene.n, cam0, tile=32, batch=256, device=dev)
+    r = d4.Renderer(scene.n, cam0, tile=32, batch=256, device=dev, binning=args.binning)
     for cam, t in frames:
         r.render(scene, cam, t)
     out = torch.empty((cam0.height, cam0.width, 3), device=dev)

@@ -104,9 +104,10 @@ typedef struct {
  * the depth-ordered pairs reach their tiles' lists -- 1 column buckets then
  * a stable radix sort by tile row (any grid), 2 straight into each tile's
  * list from per-(256-Gaussian partition, tile) counts (grids of at most
- * 2048 tiles; a larger grid makes the config invalid), 0 the library's
- * choice (currently 1, the faster of the two on the 300k-Gaussian 1352x1014
- * frame).  The lists are the same, entry for entry, either way. */
+ * 2048 tiles; a larger grid makes the config invalid), 3 each pair's depth
+ * rank into its tile's range in no order, then per tile a bitmap over the
+ * depth order read back in order (any grid), 0 the library's choice
+ * (currently 1).  The lists are the same, entry for entry, every way. */
 typedef struct {
     int32_t tile;
     int32_t batch;
@@ -144,7 +145,7 @@ typedef struct {
     int64_t control;             /* device status word and counters                           */
     int64_t key_capacity;
     int32_t tiles_x, tiles_y;
-    int32_t depth_passes, tile_passes;
+    int32_t depth_passes, tile_passes;   /* tile_passes 0: binning 3 (no pass sorts the pairs) */
     int32_t id_bits;             /* ceil(log2 N) */
     int32_t packed;              /* 1: pairs packed in one uint32 (row bits + id_bits <= 32) */
     int32_t col_bits;            /* ceil(log2 tiles_x) (the pair keys carry the row only)     */
@@ -191,8 +192,9 @@ int d4dgs_preprocess(const d4dgs_scene *scene, const d4dgs_camera *cam, float t,
  * offsets from per-(256-Gaussian partition, tile) counts and their column
  * scan, or (binning 1) into per-tile-column buckets followed by a onesweep
  * radix sort of the pairs by tile row (stable, so each tile's list stays in
- * (depth, id) order); per-tile [start, end) ranges.  Widths up to 2048
- * tiles. */
+ * (depth, id) order), or (binning 3) as depth ranks into each tile's range
+ * in no order, each list then read back in depth order from a bitmap of its
+ * ranks; per-tile [start, end) ranges.  Widths up to 2048 tiles. */
 int d4dgs_sort(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, void *ws, size_t ws_bytes,
                d4dgs_stream_t stream);
 

@@ -117,7 +117,8 @@ def camera_struct(cam) -> _abi.d4dgs_camera:
 def config_struct(tile: int = 16, batch: int = 256, bg=(0.0, 0.0, 0.0), trim: bool = False, near: float = 0.2,
                   spin_limit: int = 0, colour_cache: bool = False, binning: int = 0) -> _abi.d4dgs_config:
     """binning: 0 the library's choice (column), 1 column buckets + row passes, 2 straight into the
-    tiles' lists (<= 2048 tiles)."""
+    tiles' lists (<= 2048 tiles), 3 depth ranks into the tiles' ranges, each list read back in depth
+    order from a bitmap."""
     g = _abi.d4dgs_config()
     g.tile, g.batch = int(tile), int(batch)
     g.bg[:] = [float(x) for x in bg]

@@ -35,7 +35,7 @@ bool valid_config(const d4dgs_config *g) {
     if (g->batch != 64 && g->batch != 128 && g->batch != 256) return false;
     if (g->trim != 0 && g->trim != 1) return false;
     if (g->colour_cache != 0 && g->colour_cache != 1) return false;
-    if (g->binning < 0 || g->binning > 2) return false;
+    if (g->binning < 0 || g->binning > 3) return false;
     for (int i = 0; i < 3; i++)
         if (!isfinite(g->bg[i])) return false;
     return isfinite(g->near) && g->near >= 0.0f;
@@ -103,8 +103,9 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     // path's counts, scan and emission measured 33 + 16 + 57 us against 50 + 52 us for the column
     // emission and its row pass)
     l.direct = cfg->binning == 2;
+    l.rank_lists = cfg->binning == 3;
     if (l.direct && l.ntiles > kDirMaxTiles) return false;
-    l.tile_passes = l.direct ? 1 : 1 + row_passes;
+    l.tile_passes = l.rank_lists ? 0 : l.direct ? 1 : 1 + row_passes;
     l.tile_shift[0] = 0;
     l.tile_pass_bits[0] = l.col_bits;
     int sh = 0;
@@ -123,12 +124,14 @@ bool make_layout(int32_t n, const d4dgs_camera *cam, const d4dgs_config *cfg, in
     l.parts_dup = n > 0 ? ((int64_t)n + kDupItems - 1) / kDupItems : 1;
     l.parts_tile = cap > 0 ? (cap + kTileItems - 1) / kTileItems : 1;
     l.parts_dir = n > 0 ? ((int64_t)n + kDirItems - 1) / kDirItems : 1;
+    l.parts_rank = n > 0 ? ((int64_t)n + kRankItems - 1) / kRankItems : 1;
     int64_t off = 0;
     l.control = off; off += align256((int64_t)kCtlWords * 4);
     l.grid = off; off += align256((int64_t)(l.tiles_x + 1) * (l.tiles_y + 1) * 4);
     l.lb_depth = off; off += align256((int64_t)l.depth_passes * l.parts_depth * kRadix * 4);
-    l.lb_col = off; off += l.direct ? 0 : align256(l.parts_dup * l.tiles_x * 4);
-    l.lb_tile = off; off += align256((int64_t)(l.tile_passes - 1) * l.parts_tile * kRadix * 4);
+    l.lb_col = off; off += l.direct || l.rank_lists ? 0 : align256(l.parts_dup * l.tiles_x * 4);
+    l.lb_tile = off; off += l.tile_passes > 1 ? align256((int64_t)(l.tile_passes - 1) * l.parts_tile * kRadix * 4) : 0;
+    l.cursor = off; off += l.rank_lists ? align256((int64_t)l.ntiles * 4) : 0;
     l.zero_end = off;
     l.colbase = off; off += align256((int64_t)l.tiles_x * 4);
     l.cmat = off; off += l.direct ? align256(l.parts_dir * l.ntiles * 4) : 0;
@@ -209,6 +212,7 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     x.colbase = at<uint32_t>(ws, L.colbase);
     x.cmat = L.direct ? at<uint32_t>(ws, L.cmat) : nullptr;
     x.cgrp = L.direct ? at<unsigned long long>(ws, L.cgrp) : nullptr;
+    x.cursor = L.rank_lists ? at<uint32_t>(ws, L.cursor) : nullptr;
     x.cap = (uint32_t)L.cap;
     x.id_bits = L.id_bits;
     x.col_bits = L.col_bits;
@@ -224,6 +228,7 @@ void make_view(const d4dgs_scene &s, const d4dgs_camera &cam, float t, const d4d
     x.parts_dup = (int32_t)L.parts_dup;
     x.parts_tile = (int32_t)L.parts_tile;
     x.parts_dir = (int32_t)L.parts_dir;
+    x.parts_rank = (int32_t)L.parts_rank;
     *v = x;
 }
 
@@ -239,7 +244,7 @@ static bool same_scene_and_camera(const View &a, const View &b) {
 
 bool finish_batch(BatchArgs *b) {
     if (b->nviews < 1 || b->nviews > kMaxViews) return false;
-    int64_t chunks = 0, dparts = 0, uparts = 0, tiles = 0, xparts = 0, bands = 0;
+    int64_t chunks = 0, dparts = 0, uparts = 0, tiles = 0, xparts = 0, bands = 0, rparts = 0;
     b->max_n = 0;
     b->col_cap = 32;
     b->tile_cap = 256;
@@ -251,7 +256,8 @@ bool finish_batch(BatchArgs *b) {
     for (int i = 0; i < b->nviews; i++) {
         View &v = b->v[i];
         if (v.packed != b->packed || v.tile_passes != b->tile_passes || v.cam.tile != b->tile || v.trim_on != b->trim_on ||
-            v.kind != b->v[0].kind || v.colour_cache != b->v[0].colour_cache)
+            v.kind != b->v[0].kind || v.colour_cache != b->v[0].colour_cache ||
+            (v.cmat != nullptr) != (b->v[0].cmat != nullptr) || (v.cursor != nullptr) != (b->v[0].cursor != nullptr))
             return false;
         // time groups: a view joins the group of the view before it when it shares its scene and camera
         if (lead >= 0 && b->v[lead].group_size < kMaxGroup && same_scene_and_camera(b->v[lead], v)) {
@@ -269,9 +275,11 @@ bool finish_batch(BatchArgs *b) {
         v.tile_base = (int32_t)tiles;
         v.dir_part_base = (int32_t)xparts;
         v.band_base = (int32_t)bands;
+        v.rank_part_base = (int32_t)rparts;
         dparts += v.parts_depth;
         uparts += v.parts_dup;
         tiles += v.ntiles;
+        if (v.cursor) rparts += v.parts_rank;   // rank lists (every view of the launch)
         if (v.cmat) {   // direct binning (tile_passes 1, so every view of the launch)
             xparts += v.parts_dir;
             bands += (v.ntiles + kDirBand - 1) / kDirBand;
@@ -281,7 +289,8 @@ bool finish_batch(BatchArgs *b) {
         while (b->tile_cap < v.ntiles) b->tile_cap += 256;
         while (b->cells_cap < (v.cam.tiles_x + 1) * (v.cam.tiles_y + 1)) b->cells_cap += 256;
     }
-    if (chunks > INT32_MAX || tiles > INT32_MAX || xparts > INT32_MAX) return false;
+    if (chunks > INT32_MAX || tiles > INT32_MAX || xparts > INT32_MAX || rparts > INT32_MAX) return false;
+    b->total_rank_parts = (int32_t)rparts;
     b->total_dir_parts = (int32_t)xparts;
     b->total_bands = (int32_t)bands;
     b->total_chunks = (int32_t)chunks;

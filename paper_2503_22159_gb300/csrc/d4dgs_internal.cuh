@@ -39,6 +39,12 @@ constexpr int kDupItems = kDupThreads;                    // depth-ordered Gauss
 constexpr int kDirItems = 256;
 constexpr int kDirMaxTiles = 2048;
 constexpr int kDirBand = 8;
+// rank lists (config binning 3): emission partitions of kRankItems depth-ordered
+// Gaussians; the list kernel's depth-order bitmap is at most kRankMaxWords words
+constexpr int kRankThreads = 1024;
+constexpr int kRankItems = 1024;
+constexpr int kRankListThreads = 256;
+constexpr int kRankMaxWords = 40960;   // 160 KB: one window covers 1.3 M Gaussians
 
 // ---- control block (uint32 words at layout.control)
 enum : int {
@@ -75,8 +81,12 @@ struct Layout {
     int64_t cap = 0;
     int64_t parts_depth = 0, parts_dup = 0, parts_tile = 0, parts_dir = 0;
     bool direct = false;   // config binning 2: pairs emitted straight into their tiles' lists (tile_passes 1)
+    // config binning 3: ranks emitted unordered, each tile's list built from a depth-order bitmap
+    // (tile_passes 0: the lists end in tile_keys[0], the unordered ranks go to tile_keys[1])
+    bool rank_lists = false;
+    int64_t parts_rank = 0;
     // zero-initialised region [0, zero_end)
-    int64_t control = 0, grid = 0, lb_depth = 0, lb_col = 0, lb_tile = 0, zero_end = 0;
+    int64_t control = 0, grid = 0, lb_depth = 0, lb_col = 0, lb_tile = 0, cursor = 0, zero_end = 0;
     // the rest
     int64_t tile_order = 0, tile_work = 0;   // ntiles uint32 each, written by the backward
     int64_t cmat = 0;      // direct binning: parts_dir x ntiles uint32 (not cleared: every entry is written)
@@ -149,6 +159,7 @@ struct View {
     uint32_t *colbase;               // first position of each tile column's bucket (clamped to cap)
     uint32_t *cmat;                  // direct binning: parts_dir x ntiles pair counts, then list offsets
     unsigned long long *cgrp;        // direct binning: parts_dir x ntiles, byte g = pairs of group g
+    uint32_t *cursor;                // rank lists: per tile, the pairs reserved so far (zeroed per frame)
     uint32_t cap;
     int32_t id_bits, col_bits, packed, tile_passes, ntiles;
     int32_t trim_on;                 // config trim: 1 rectangles cut per column
@@ -156,13 +167,13 @@ struct View {
     int32_t colour_cache;            // config colour_cache: SH colour towards the static mean
     int32_t tile_shift[3];
     uint32_t tile_mask[3];
-    int32_t parts_depth, parts_dup, parts_tile, parts_dir;
+    int32_t parts_depth, parts_dup, parts_tile, parts_dir, parts_rank;
     // time group: consecutive views of one scene seen by one camera (times may
     // differ) are preprocessed together, reading each Gaussian once; the
     // group's first view carries group_size (others 0) and the chunk base
     int32_t group_size;
     // first flattened work item of this view within its table
-    int32_t chunk_base, depth_part_base, dup_part_base, tile_base, dir_part_base, band_base;
+    int32_t chunk_base, depth_part_base, dup_part_base, tile_base, dir_part_base, band_base, rank_part_base;
 };
 
 // Descriptor table as kernel parameters (it travels by value: 32 views fit in
@@ -175,6 +186,7 @@ struct BatchArgs {
     int32_t tile_cap;                           // direct binning: multiple of 256 >= every view's tiles
     int32_t cells_cap;                          // direct binning: multiple of 256 >= every (tiles_x+1)(tiles_y+1)
     int32_t total_chunks, total_depth_parts, total_dup_parts, total_tiles, total_dir_parts, total_bands;
+    int32_t total_rank_parts;                   // rank lists: emission partitions of every view
     int32_t max_n;
     View v[kMaxViews];
 };
@@ -190,8 +202,10 @@ enum : int {
     kBaBack = 10,
     kBaDirCount = 11,      // direct binning: counts, emission
     kBaDirEmit = 12,
+    kBaRankEmit = 13,      // rank lists: emission, list building
+    kBaRankList = 14,
     kBaNViews = 16, kBaTotalChunks, kBaTotalDepthParts, kBaTotalDupParts, kBaTotalTiles, kBaTotalDirParts,
-    kBaTotalBands,
+    kBaTotalBands, kBaTotalRankParts,
     kBaWords = 64
 };
 constexpr int64_t kBatchTableOffset = 256;

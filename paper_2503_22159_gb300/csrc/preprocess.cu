@@ -586,6 +586,7 @@ clear_kernel(const __grid_constant__ BatchArgs args, const BatchArgs *args_dev, 
             bw[kBaTotalTiles] = (uint32_t)A->total_tiles;
             bw[kBaTotalDirParts] = (uint32_t)A->total_dir_parts;
             bw[kBaTotalBands] = (uint32_t)A->total_bands;
+            bw[kBaTotalRankParts] = (uint32_t)A->total_rank_parts;
         }
         const uint32_t *src = reinterpret_cast<const uint32_t *>(A->v);
         uint32_t *dst = reinterpret_cast<uint32_t *>(ba + kBatchTableOffset);

@@ -30,6 +30,9 @@
 // predecessor partitions (bounded spin: on timeout the status word is latched
 // and the pass completes without hanging), and scatter through shared memory
 // so that global writes are runs of consecutive addresses.
+#include <map>
+#include <utility>
+
 #include "d4dgs_internal.cuh"
 #include "tile_trim.cuh"
 
@@ -613,6 +616,251 @@ emit_kernel(char *__restrict__ ba, int col_cap, const __grid_constant__ View v0)
     }
 }
 
+// ---- rank lists (config binning 3): every tile's list in depth order
+// without a sort by tile.
+//   R1. emit_rank_kernel, over partitions of kRankItems positions of the
+//       depth order: the partition's pairs counted per tile (shared memory),
+//       one reservation per (partition, tile) on the tile's cursor (a global
+//       atomic), then each pair written at one of its partition's reserved
+//       slots of the tile's range of the unordered buffer: the Gaussian's
+//       depth rank (its position in the depth order).  Slots follow no order.
+//   R2. rank_list_kernel, a tile at a time: the tile's ranks set as bits of a
+//       bitmap over the depth order (shared memory, in windows of words * 32
+//       positions), the set bits read back in order and written out, then each
+//       rank replaced by the pair (tile row, id at that position of the depth
+//       order), packed as the other binnings pack it.  A tile
+//       holds a Gaussian once, so the bits are its list in depth order; the
+//       depth order breaks ties by id, so every list equals, bit for bit, the
+//       one the column path's stable passes give.
+// No kernel here waits on another CTA.
+
+// The tile (row-major index) of pair j of a Gaussian's rectangle r (column-
+// major over its columns, hgt rows each; inv_h = 1 / hgt), or -1 when a column
+// trim cuts it away.
+template <bool TRIM>
+__device__ __forceinline__ int rank_pair_tile(ushort4 r, unsigned long long tw, int hgt, float inv_h, int j,
+                                              int tiles_x) {
+    int cc = __float2int_rz((float)j * inv_h);
+    int rr = j - cc * hgt;
+    if (rr < 0) { cc--; rr += hgt; } else if (rr >= hgt) { cc++; rr -= hgt; }
+    if (TRIM && (rr < trim_top(tw, cc) || rr >= hgt - trim_bot(tw, cc))) return -1;
+    return ((int)r.z + rr) * tiles_x + (int)r.x + cc;
+}
+
+// smem_tiles: tiles whose counts fit the dynamic shared memory (views with
+// more tiles reserve a slot per pair instead of per partition).
+// PARAM: one view, its descriptor the kernel parameter v0.
+template <bool TRIM, bool PARAM>
+__global__ void __launch_bounds__(kRankThreads, 1)
+emit_rank_kernel(char *__restrict__ ba, int smem_tiles, const __grid_constant__ View v0) {
+    extern __shared__ uint32_t s_cnt[];   // [smem_tiles] pairs per tile, then next slot per tile
+    __shared__ ushort4 s_rect[kRankItems];
+    __shared__ float s_inv[kRankItems];
+    __shared__ unsigned long long s_trim[TRIM ? kRankItems : 1];
+    __shared__ uint32_t s_part;
+    grid_dependency_wait();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
+    const int nviews = PARAM ? 1 : (int)bw[kBaNViews];
+    const uint32_t total = PARAM ? (uint32_t)v0.parts_rank : bw[kBaTotalRankParts];
+    constexpr int kPerWarp = kRankItems / (kRankThreads / 32);
+    for (;;) {
+        if (tid == 0) s_part = atomicAdd(bw + kBaRankEmit, 1u);
+        __syncthreads();
+        const uint32_t g = s_part;
+        if (g >= total) break;
+        int vi = 0;
+        for (int u = 1; u < nviews; u++)
+            if ((uint32_t)view_of(ba, u).rank_part_base <= g) vi = u;
+        const View &v = PARAM ? v0 : view_of(ba, vi);
+        const uint32_t part = g - (uint32_t)v.rank_part_base;
+        const uint32_t n = (uint32_t)v.n, cap = v.cap;
+        const int tiles_x = v.cam.tiles_x, tiles_y = v.cam.tiles_y, ntiles = tiles_x * tiles_y;
+        const bool agg = ntiles <= smem_tiles;
+        const uint32_t *order = v.dvals[0];   // after the 4 depth passes
+        const uint32_t p0 = part * kRankItems;
+        for (int q = tid; q < kRankItems; q += kRankThreads) {
+            const uint32_t pos = p0 + (uint32_t)q;
+            ushort4 r = make_ushort4(1, 0, 0, 0);   // empty: x0 > x1
+            unsigned long long tw = 0;
+            if (pos < n) {
+                const uint32_t id = order[pos];
+                if (id < n && v.tiles_touched[id]) {   // id < n unless a depth pass gave up on a spin-wait
+                    r = v.rect[id];
+                    if (TRIM) tw = v.trim[id];
+                }
+            }
+            // rectangles are clamped to the grid by the preprocess; clamp again for the tile index
+            r.y = (unsigned short)min((int)r.y, tiles_x - 1);
+            r.w = (unsigned short)min((int)r.w, tiles_y - 1);
+            s_rect[q] = r;
+            s_inv[q] = r.x <= r.y ? 1.0f / (float)((int)r.w - (int)r.z + 1) : 0.0f;
+            if (TRIM) s_trim[TRIM ? q : 0] = tw;
+        }
+        if (agg)
+            for (int t = tid; t < ntiles; t += kRankThreads) s_cnt[t] = 0u;
+        __syncthreads();
+        // ---- 1. pairs per tile (warp w: Gaussians w*kPerWarp .. in turn, a pair per lane)
+        if (agg) {
+            for (int q = warp * kPerWarp; q < (warp + 1) * kPerWarp; q++) {
+                const ushort4 rq = s_rect[q];
+                if (rq.x > rq.y) continue;
+                const unsigned long long tq = TRIM ? s_trim[TRIM ? q : 0] : 0ull;
+                const int hgt = (int)rq.w - (int)rq.z + 1, cnt = ((int)rq.y - (int)rq.x + 1) * hgt;
+                const float inv_h = s_inv[q];
+                for (int j = lane; j < cnt; j += 32) {
+                    const int t = rank_pair_tile<TRIM>(rq, tq, hgt, inv_h, j, tiles_x);
+                    if (t >= 0) atomicAdd(&s_cnt[t], 1u);
+                }
+            }
+            __syncthreads();
+            // ---- 2. one reservation per touched tile: s_cnt becomes the partition's next slot
+            for (int t = tid; t < ntiles; t += kRankThreads) {
+                const uint32_t c = s_cnt[t];
+                if (c) s_cnt[t] = v.ranges[t].x + atomicAdd(v.cursor + t, c);
+            }
+            __syncthreads();
+        }
+        // ---- 3. each pair's rank at a reserved slot (past cap: dropped, the capacity status is set)
+        uint32_t *out = v.tkeys[1];
+        for (int q = warp * kPerWarp; q < (warp + 1) * kPerWarp; q++) {
+            const ushort4 rq = s_rect[q];
+            if (rq.x > rq.y) continue;
+            const unsigned long long tq = TRIM ? s_trim[TRIM ? q : 0] : 0ull;
+            const int hgt = (int)rq.w - (int)rq.z + 1, cnt = ((int)rq.y - (int)rq.x + 1) * hgt;
+            const float inv_h = s_inv[q];
+            const uint32_t rank = p0 + (uint32_t)q;
+            for (int j = lane; j < cnt; j += 32) {
+                const int t = rank_pair_tile<TRIM>(rq, tq, hgt, inv_h, j, tiles_x);
+                if (t < 0) continue;
+                const uint32_t o = agg ? atomicAdd(&s_cnt[t], 1u) : v.ranges[t].x + atomicAdd(v.cursor + t, 1u);
+                if (o < cap) out[o] = rank;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of one value per thread over a kRankListThreads block; *total: the sum.
+__device__ __forceinline__ uint32_t rank_block_scan(uint32_t v, uint32_t *s_scan, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kRankListThreads / 32; w++) {
+        const uint32_t c = s_scan[w];
+        if (w < warp) before += c;
+        all += c;
+    }
+    *total = all;
+    __syncthreads();
+    return before + x - v;
+}
+
+// Persistent: CTAs take tiles (of every view of the launch) from a counter.
+// words: bitmap words of dynamic shared memory (a window of 32 * words
+// positions of the depth order at a time).
+template <bool PARAM>
+__global__ void __launch_bounds__(kRankListThreads, 3)
+rank_list_kernel(char *__restrict__ ba, int words, const __grid_constant__ View v0) {
+    extern __shared__ uint32_t s_bits[];
+    __shared__ uint32_t s_scan[kRankListThreads / 32];
+    __shared__ int32_t s_item;
+    grid_dependency_wait();
+    const int tid = threadIdx.x;
+    uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
+    const int nviews = PARAM ? 1 : (int)bw[kBaNViews];
+    const int total = PARAM ? v0.ntiles : (int)bw[kBaTotalTiles];
+    const uint32_t span = 32u * (uint32_t)words;
+    const int per = (words + kRankListThreads - 1) / kRankListThreads;   // bitmap words per thread
+    for (;;) {
+        if (tid == 0) s_item = (int32_t)atomicAdd(bw + kBaRankList, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        int vi = 0;
+        for (int u = 1; u < nviews; u++)
+            if (view_of(ba, u).tile_base <= item) vi = u;
+        const View &v = PARAM ? v0 : view_of(ba, vi);
+        const int tile = item - v.tile_base;
+        const uint32_t n = (uint32_t)v.n, cap = v.cap;
+        uint2 rg = v.ranges[tile];
+        rg.y = min(rg.y, cap);
+        rg.x = min(rg.x, rg.y);
+        if (rg.x == rg.y) continue;   // uniform: every thread read the same range
+        const uint32_t *in = v.tkeys[1];
+        uint32_t *lst = v.packed ? v.tkeys[0] : v.tvals[0];
+        uint32_t out = rg.x;
+        for (uint32_t w0 = 0; w0 < n; w0 += span) {
+            for (int w = tid; w < words; w += kRankListThreads) s_bits[w] = 0u;
+            __syncthreads();
+            for (uint32_t i0 = rg.x + (uint32_t)tid; i0 < rg.y; i0 += 8u * kRankListThreads) {
+                uint32_t r[8];   // 8 loads in flight, then their bits
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const uint32_t i = i0 + (uint32_t)(k * kRankListThreads);
+                    r[k] = i < rg.y ? in[i] - w0 : span;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    if (r[k] < span) atomicOr(&s_bits[r[k] >> 5], 1u << (r[k] & 31u));
+            }
+            __syncthreads();
+            const int b0 = min(tid * per, words), b1 = min(b0 + per, words);
+            uint32_t c = 0;
+            for (int w = b0; w < b1; w++) c += __popc(s_bits[w]);
+            uint32_t all;
+            uint32_t k = out + rank_block_scan(c, s_scan, &all);
+            for (int w = b0; w < b1; w++) {
+                uint32_t m = s_bits[w];
+                while (m) {
+                    const int b = __ffs((int)m) - 1;
+                    m &= m - 1u;
+                    if (k < rg.y) lst[k] = w0 + 32u * (uint32_t)w + (uint32_t)b;
+                    k++;
+                }
+            }
+            out += all;
+            __syncthreads();
+        }
+        // ranks -> pairs as every binning leaves them: (tile row << id_bits | id) packed, else the row
+        // key and the id apart (the block's own writes above are visible after the barrier)
+        const uint32_t *order = v.dvals[0];
+        const uint32_t row = (uint32_t)(tile / v.cam.tiles_x);
+        const int id_bits = v.id_bits;
+        for (uint32_t i0 = rg.x + (uint32_t)tid; i0 < rg.y; i0 += 8u * kRankListThreads) {
+            uint32_t id[8];   // 8 ranks, then 8 gathers in flight, then the stores
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t i = i0 + (uint32_t)(k * kRankListThreads);
+                id[k] = i < rg.y ? lst[i] : n;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) id[k] = id[k] < n ? order[id[k]] : 0u;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t i = i0 + (uint32_t)(k * kRankListThreads);
+                if (i >= rg.y) continue;
+                if (v.packed) {
+                    lst[i] = (row << id_bits) | id[k];
+                } else {
+                    v.tkeys[0][i] = row;
+                    lst[i] = id[k];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---- direct binning (config binning 2): the pairs go straight into their
 // tiles' lists, so the lists need no sort by tile after the emission.
 // Partitions of kDirItems (256) depth-ordered Gaussians, each 8 groups of 32.
@@ -962,7 +1210,11 @@ constexpr size_t emit_smem(int col_cap) { return (size_t)8 * col_cap * sizeof(ui
 int sort_launch_count(int n, int tile_passes, int grid_cells) {
     // tile counts (own launch unless they ride with the first depth pass) + 4 depth passes + either
     // counts, scan and emission (direct binning) or column emission + row passes
-    return n == 0 ? 1 : (grid_cells <= kTileCountCells ? 0 : 1) + 4 + (tile_passes == 1 ? 3 : 1 + (tile_passes - 1));
+    // counts, scan and emission (direct binning), emission and list building (rank lists), or column
+    // emission + row passes
+    return n == 0 ? 1
+                  : (grid_cells <= kTileCountCells ? 0 : 1) + 4 +
+                        (tile_passes == 0 ? 2 : tile_passes == 1 ? 3 : 1 + (tile_passes - 1));
 }
 
 // dynamic shared memory of the direct binning: the counts' 8 group grids of a
@@ -971,6 +1223,45 @@ constexpr size_t dir_count_smem(int cells_cap) { return (size_t)8 * cells_cap * 
 constexpr size_t dir_emit_smem(int tile_cap) { return (size_t)20 * tile_cap; }
 
 namespace {
+
+// Resident CTAs per SM of `fn` at `threads` and `smem` (queried once per pair).
+int occupancy_cached(const void *fn, int threads, size_t smem) {
+    static std::map<std::pair<const void *, size_t>, int> cache;
+    const auto key = std::make_pair(fn, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const int b = occupancy_blocks(fn, threads, smem);
+    cache[key] = b;
+    return b;
+}
+
+// Rank lists: the emission (per-tile counts of up to kRankSmemTiles tiles in shared memory)
+// and the list building (a bitmap window covering the launch's largest view when it fits).
+constexpr int kRankSmemTiles = 40960;
+template <bool PARAM>
+cudaError_t launch_rank(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms, const View &v0) {
+    static bool attr = false;
+    if (!attr) {
+        for (const void *fn : {(const void *)emit_rank_kernel<false, PARAM>, (const void *)emit_rank_kernel<true, PARAM>})
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kRankSmemTiles * 4);
+        cudaFuncSetAttribute(rank_list_kernel<PARAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRankMaxWords * 4);
+        attr = true;
+    }
+    const int smem_tiles = args.tile_cap <= kRankSmemTiles ? args.tile_cap : 0;
+    int words = ((args.max_n + 31) / 32 + 255) / 256 * 256;
+    words = words < 256 ? 256 : words > kRankMaxWords ? kRankMaxWords : words;
+    const void *efn = args.trim_on ? (const void *)emit_rank_kernel<true, PARAM> : (const void *)emit_rank_kernel<false, PARAM>;
+    const int oe = occupancy_cached(efn, kRankThreads, (size_t)smem_tiles * 4);
+    const int ol = occupancy_cached((const void *)rank_list_kernel<PARAM>, kRankListThreads, (size_t)words * 4);
+    cudaError_t e = args.trim_on ? launch_chained(emit_rank_kernel<true, PARAM>, oe * num_sms, kRankThreads,
+                                                  (size_t)smem_tiles * 4, st, batch_area, smem_tiles, v0)
+                                 : launch_chained(emit_rank_kernel<false, PARAM>, oe * num_sms, kRankThreads,
+                                                  (size_t)smem_tiles * 4, st, batch_area, smem_tiles, v0);
+    if (e == cudaSuccess)
+        e = launch_chained(rank_list_kernel<PARAM>, ol * num_sms, kRankListThreads, (size_t)words * 4, st, batch_area,
+                           words, v0);
+    return e;
+}
 
 cudaError_t launch_direct(const BatchArgs &args, char *batch_area, cudaStream_t st, int num_sms) {
     // grids of at most kDirMaxTiles tiles have at most 2 kDirMaxTiles + 2 cells
@@ -1063,6 +1354,8 @@ cudaError_t sort_passes(const BatchArgs &args, char *batch_area, cudaStream_t st
         }
     }
     if (e != cudaSuccess) return e;
+    // ---- 2-3 (rank lists): unordered emission of depth ranks, lists from depth-order bitmaps
+    if (args.tile_passes == 0) return launch_rank<PARAM>(args, batch_area, st, num_sms, v0);
     // ---- 2-3 (direct binning): counts, their column scan, emission into the tiles' lists
     if (args.tile_passes == 1) return launch_direct(args, batch_area, st, num_sms);
     // ---- 2. emission in depth order into tile-column buckets (tile pass 0)

@@ -91,7 +91,7 @@ def test_binning_choice(d4, w, h, tile, fits):
     cam = synth.pinhole(w, h)
     ntiles = math.ceil(w / tile) * math.ceil(h / tile)
     assert fits == (ntiles <= 2048)
-    for binning, direct in ((0, False), (1, False), (2, True)):
+    for binning, direct in ((0, False), (1, False), (2, True), (3, False)):
         cfg = d4.config_struct(tile, 64, binning=binning)
         if binning == 2 and not fits:
             assert d4._abi.load().d4dgs_workspace_bytes(10, ctypes.byref(d4.camera_struct(cam)), ctypes.byref(cfg),
@@ -99,8 +99,10 @@ def test_binning_choice(d4, w, h, tile, fits):
             continue
         L = d4.d4dgs_workspace_layout(10, cam, cfg, d4.d4dgs_workspace_bytes(10, cam, cfg, 100))
         assert (L["tile_passes"] == 1) == direct
+        # rank lists (binning 3, any grid): no pass sorts the pairs; the lists end in the first buffer
+        assert (L["tile_passes"] == 0) == (binning == 3)
     assert d4._abi.load().d4dgs_workspace_bytes(10, ctypes.byref(d4.camera_struct(cam)),
-                                                ctypes.byref(d4.config_struct(tile, 64, binning=3)), 100) == 0
+                                                ctypes.byref(d4.config_struct(tile, 64, binning=4)), 100) == 0
 
 
 def test_invalid_arguments_rejected_on_host(d4):

@@ -72,7 +72,7 @@ def test_preprocess_matches_oracle(trim):
     assert L["key_capacity"] > 0
 
 
-@pytest.mark.parametrize("binning", [1, 2])
+@pytest.mark.parametrize("binning", [1, 2, 3])
 @pytest.mark.parametrize("trim", [False, True])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_lists_bit_exact_tiny(tile, trim, binning):
@@ -80,6 +80,7 @@ def test_lists_bit_exact_tiny(tile, trim, binning):
     cam, t = w.frames[0]
     r, _, _ = gu.render(w.scene, cam, t, tile=tile, batch=64, trim=trim, binning=binning)
     assert (r.layout(cam)["tile_passes"] == 1) == (binning == 2)
+    assert (r.layout(cam)["tile_passes"] == 0) == (binning == 3)
     got = gu.gpu_lists(r, cam)
     b, exp = gu.expected_lists(w.scene, cam, t, tile, trim=trim)
     assert got["stats"]["status"] == 0
@@ -87,13 +88,14 @@ def test_lists_bit_exact_tiny(tile, trim, binning):
     gu.compare_lists(got, b, exp)
 
 
-@pytest.mark.parametrize("binning", [1, 2])
+@pytest.mark.parametrize("binning", [1, 2, 3])
 @pytest.mark.parametrize("trim", [False, True])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_lists_bit_exact_medium_ragged(tile, trim, binning):
     scene, cam, t = medium()
     r, _, _ = gu.render(scene, cam, t, tile=tile, batch=128, trim=trim, binning=binning)
     assert (r.layout(cam)["tile_passes"] == 1) == (binning == 2)
+    assert (r.layout(cam)["tile_passes"] == 0) == (binning == 3)
     got = gu.gpu_lists(r, cam)
     b, exp = gu.expected_lists(scene, cam, t, tile, trim=trim)
     assert len(exp["tile"]) > 10 * 5120, "the case should span many sort partitions"

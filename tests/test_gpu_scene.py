@@ -30,10 +30,11 @@ def gpu_renderer(scene_w):
 
 
 @pytest.mark.parametrize("k,trim,tile,binning", [(150, False, 16, 0), (150, True, 16, 0), (150, False, 32, 0),
-                                                  (150, False, 32, 2), (150, True, 32, 2)])
+                                                  (150, False, 32, 2), (150, True, 32, 2), (150, False, 32, 3),
+                                                  (150, True, 16, 3)])
 def test_scene_preprocess_and_lists(scene_w, gpu_renderer, k, trim, tile, binning):
     """Tile 16 and 32 (the benchmark's launch configuration) with the column binning; tile 32
-    (1376 tiles) with the direct binning too."""
+    (1376 tiles) with the direct binning and the rank lists too."""
     m, ds, r = gpu_renderer
     if trim or tile != 16 or binning:
         r = m.Renderer(scene_w.scene.n, scene_w.frames[0][0], tile=tile, batch=256, key_capacity=40 * scene_w.scene.n,
@@ -42,6 +43,7 @@ def test_scene_preprocess_and_lists(scene_w, gpu_renderer, k, trim, tile, binnin
     r.render(ds, cam, t)
     torch.cuda.synchronize()
     assert (r.layout(cam)["tile_passes"] == 1) == (binning == 2)
+    assert (r.layout(cam)["tile_passes"] == 0) == (binning == 3)
     n = scene_w.scene.n
     rec = gu.gpu_records(r, n, cam)
     b = oracle.bin_f32(scene_w.scene, cam, t, tile, trim=trim)
