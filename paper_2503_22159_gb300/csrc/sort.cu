@@ -357,7 +357,27 @@ onesweep_kernel(char *__restrict__ ba, int pass, int tc_cells, const __grid_cons
             if (KV) vals[KV ? k : 0] = IOTA ? idx : (ok ? vals_in[idx] : 0u);
         }
         // ---- stable rank within the warp
-        if (TILE && mask <= 63u) {
+        if (TILE && mask <= 31u) {
+            // at most 32 digits (row passes of up to 32 tile rows): lane l keeps the running count of
+            // digit l; the peers of an item match its digit in all 5 ballots
+            const uint32_t lt = lanemask_lt();
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int k = 0; k < IPT; k++) {
+                const uint32_t d = (keys[k] >> shift) & mask;
+                uint32_t peers = 0xFFFFFFFFu, mine = 0xFFFFFFFFu;
+#pragma unroll
+                for (int b = 0; b < 5; b++) {
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+                    peers &= ((d >> b) & 1u) ? bal : ~bal;
+                    mine &= ((lane >> b) & 1) ? bal : ~bal;
+                }
+                rank[k] = __shfl_sync(0xFFFFFFFFu, cnt, (int)d) + __popc(peers & lt);
+                cnt += __popc(mine);
+            }
+            s_warp_hist[warp][lane] = cnt;
+            s_warp_hist[warp][lane + 32] = 0u;
+        } else if (TILE && mask <= 63u) {
             // at most 64 digits (row passes of up to 64 tile rows): multisplit in registers.  The
             // peers of an item are the lanes whose digit bits match its own in all 6 ballots; lane
             // l keeps the running counts of digits l and l + 32.
