@@ -84,6 +84,7 @@ template <int TS, int BATCH, bool FLOW = false>
 __global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 16 : (TS == 16 ? 8 : 3))
 blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_drgb,
                       const float *__restrict__ dl_dflow) {
+    grid_dependency_wait();
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
     constexpr int NA = FLOW ? 11 : 9;   // shared sums per staged Gaussian
@@ -94,16 +95,18 @@ blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_
     const uint32_t n = (uint32_t)v.n, cap = v.cap;
     const int width = v.cam.width, height = v.cam.height, tiles_x = v.cam.tiles_x;
     float *g2 = v.grad2d;
-    __shared__ float4 s_ua[BATCH];    // u, u, A, A (forward exponent form, pairs)
-    __shared__ float4 s_bc[BATCH];    // B, B, C, C
-    __shared__ float4 s_vl[BATCH];    // v, v, L, L
-    __shared__ float4 s_c[BATCH];     // r, g, b
-    __shared__ float4 s_k[BATCH];     // a, b, c, o_hat (natural conic)
-    __shared__ uint32_t s_m[BATCH];   // blocks the alpha >= 1/255 ellipse reaches
-    __shared__ uint32_t s_id[BATCH];
-    __shared__ float2 s_f[FLOW ? BATCH : 1];   // screen flow
+    // the staged batch in dynamic shared memory (k7_smem bytes)
+    extern __shared__ float4 s_dyn4[];
+    float4 *s_ua = s_dyn4;            // u, u, A, A (forward exponent form, pairs)
+    float4 *s_bc = s_ua + BATCH;      // B, B, C, C
+    float4 *s_vl = s_bc + BATCH;      // v, v, L, L
+    float4 *s_c = s_vl + BATCH;       // r, g, b
+    float4 *s_k = s_c + BATCH;        // a, b, c, o_hat (natural conic)
+    uint32_t *s_m = reinterpret_cast<uint32_t *>(s_k + BATCH);   // blocks the alpha >= 1/255 ellipse reaches
+    uint32_t *s_id = s_m + BATCH;
+    float2 *s_f = reinterpret_cast<float2 *>(s_id + BATCH);      // screen flow (FLOW)
     // moments M_0, M_x, M_xx, M_y, M_xy, M_yy, colour sums r, g, b (, flow u, v)
-    __shared__ float s_acc[BATCH][NA];
+    float (*s_acc)[NA] = reinterpret_cast<float (*)[NA]>(s_f + (FLOW ? BATCH : 0));
     __shared__ uint32_t s_maxw;
 
     int tile = blockIdx.x;
@@ -380,6 +383,7 @@ struct GradArgs {
 template <int DEG, bool ACC>
 __global__ void __launch_bounds__(256)
 preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
+    grid_dependency_wait();
     const View &vw = view_of(ba, 0);
     const SceneArgs s{vw.means, vw.t_mean, vw.velocity, vw.log_scales, vw.log_t_scale, vw.quats, vw.opacity_logit,
                       vw.sh};
@@ -610,7 +614,17 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
 // scanned from the heaviest down and the tiles scattered (order within a
 // class: whatever the atomics give; any order gives the same gradients up to
 // the order of their floating-point sums).
-__global__ void __launch_bounds__(1024) tile_order_kernel(const char *__restrict__ ba) {
+// Block 0 orders the replay's tiles; the other blocks clear the per-Gaussian
+// 2D gradient sums (n4 float4) that the replay adds into.
+__global__ void __launch_bounds__(1024) backward_prologue_kernel(const char *__restrict__ ba, float4 *__restrict__ g2,
+                                                                 int64_t n4) {
+    grid_dependency_wait();
+    if (blockIdx.x > 0) {
+        const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
+        for (int64_t i = (int64_t)(blockIdx.x - 1) * blockDim.x + threadIdx.x; i < n4; i += stride)
+            g2[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
     __shared__ uint32_t s_cls[kWorkClasses];
     const View &v = view_of(ba, 0);
     const int T = v.ntiles, tid = threadIdx.x;
@@ -618,31 +632,42 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const char *__restrict
     __syncthreads();
     for (int t = tid; t < T; t += 1024) atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u);
     __syncthreads();
-    if (tid == 0) {
-        uint32_t pos = 0;
-        for (int c = kWorkClasses - 1; c >= 0; c--) {
-            const uint32_t k = s_cls[c];
-            s_cls[c] = pos;
-            pos += k;
-        }
-    }
+    if (tid < 32) work_class_scan(s_cls);
     __syncthreads();
     for (int t = tid; t < T; t += 1024) v.tile_order[atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u)] = (uint32_t)t;
 }
 
+// dynamic shared memory of a K7 CTA: the staged batch (5 float4, 2 words, the flow and the sums
+// per Gaussian)
+constexpr size_t k7_smem(int batch, bool flow) {
+    return (size_t)batch * (5 * 16 + 2 * 4 + (flow ? 8 : 0) + 4 * (flow ? 11 : 9));
+}
+
 template <int TS, int BATCH>
 void launch_bb(const char *ba, int ntiles, const float *dl, const float *dlf, cudaStream_t st) {
-    if (dlf) blend_backward_kernel<TS, BATCH, true><<<ntiles, BlendShape<TS>::NT, 0, st>>>(ba, dl, dlf);
-    else blend_backward_kernel<TS, BATCH, false><<<ntiles, BlendShape<TS>::NT, 0, st>>>(ba, dl, nullptr);
+    static bool attr = false;
+    if (!attr) {   // above the 48 KB default
+        cudaFuncSetAttribute(blend_backward_kernel<TS, BATCH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)k7_smem(BATCH, true));
+        cudaFuncSetAttribute(blend_backward_kernel<TS, BATCH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)k7_smem(BATCH, false));
+        attr = true;
+    }
+    if (dlf)
+        launch_chained(blend_backward_kernel<TS, BATCH, true>, ntiles, BlendShape<TS>::NT, k7_smem(BATCH, true), st, ba,
+                       dl, dlf);
+    else
+        launch_chained(blend_backward_kernel<TS, BATCH, false>, ntiles, BlendShape<TS>::NT, k7_smem(BATCH, false), st,
+                       ba, dl, static_cast<const float *>(nullptr));
 }
 
 template <bool ACC>
 void launch_k8(int deg, int blocks, const char *ba, const GradArgs &o, cudaStream_t st) {
     switch (deg) {
-        case 0: preprocess_backward_kernel<0, ACC><<<blocks, 256, 0, st>>>(ba, o); break;
-        case 1: preprocess_backward_kernel<1, ACC><<<blocks, 256, 0, st>>>(ba, o); break;
-        case 2: preprocess_backward_kernel<2, ACC><<<blocks, 256, 0, st>>>(ba, o); break;
-        default: preprocess_backward_kernel<3, ACC><<<blocks, 256, 0, st>>>(ba, o); break;
+        case 0: launch_chained(preprocess_backward_kernel<0, ACC>, blocks, 256, 0, st, ba, o); break;
+        case 1: launch_chained(preprocess_backward_kernel<1, ACC>, blocks, 256, 0, st, ba, o); break;
+        case 2: launch_chained(preprocess_backward_kernel<2, ACC>, blocks, 256, 0, st, ba, o); break;
+        default: launch_chained(preprocess_backward_kernel<3, ACC>, blocks, 256, 0, st, ba, o); break;
     }
 }
 
@@ -650,25 +675,22 @@ void launch_k8(int deg, int blocks, const char *ba, const GradArgs &o, cudaStrea
 
 cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float *dl_drgb, const float *dl_dflow,
                             const d4dgs_scene_grad &g, cudaStream_t st, int num_sms, bool accumulate) {
-    (void)num_sms;
     const View &v = args.v[0];
     if (v.n == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(v.grad2d, 0, (size_t)v.n * kG2 * sizeof(float), st);
+    // the replay's order from this frame's tile work, beside the clearing of the gradient sums; the
+    // three launches chained like the forward's
+    cudaError_t e = launch_chained(backward_prologue_kernel, 1 + 2 * num_sms, 1024, 0, st, (const char *)batch_area,
+                                   reinterpret_cast<float4 *>(v.grad2d), (int64_t)v.n * kG2 / 4);
     if (e != cudaSuccess) return e;
-    note_launch(st);
-    tile_order_kernel<<<1, 1024, 0, st>>>(batch_area);   // the replay's order from this frame's tile work
-    note_launch(st);
     switch (args.tile) {   // the staging depth of the backward follows the tile size
         case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
         case 16: launch_bb<16, 128>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
-        default: launch_bb<32, 128>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
+        default: launch_bb<32, 512>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
     }
-    note_launch(st);
     GradArgs o{g.means, g.t_mean, g.velocity, g.log_scales, g.log_t_scale, g.quats, g.opacity_logit, g.sh};
     const int blocks = (v.n + 255) / 256;
     if (accumulate) launch_k8<true>(v.sh_degree, blocks, batch_area, o, st);
     else launch_k8<false>(v.sh_degree, blocks, batch_area, o, st);
-    note_launch(st);
     return cudaGetLastError();
 }
 

@@ -272,6 +272,33 @@ __device__ __forceinline__ int work_class(uint32_t k) {
     const uint32_t f = l >= 2 ? (k >> (l - 2)) & 3u : (k << (2 - l)) & 3u;
     return 1 + 4 * l + (int)f;
 }
+// The work classes' first positions from the heaviest down (s_cls[c]: the count of class c in,
+// its first position out), by one whole warp: lane l takes kWorkClassRun consecutive classes
+// below the heaviest l * kWorkClassRun, then a warp scan of the lanes' totals.
+constexpr int kWorkClassRun = (kWorkClasses + 31) / 32;
+__device__ __forceinline__ void work_class_scan(uint32_t *s_cls) {
+    const int lane = (int)(threadIdx.x & 31u);
+    uint32_t cnt[kWorkClassRun], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kWorkClassRun; j++) {
+        const int c = kWorkClasses - 1 - lane * kWorkClassRun - j;
+        cnt[j] = c >= 0 ? s_cls[c] : 0u;
+        sum += cnt[j];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t pos = x - sum;
+#pragma unroll
+    for (int j = 0; j < kWorkClassRun; j++) {
+        const int c = kWorkClasses - 1 - lane * kWorkClassRun - j;
+        if (c >= 0) s_cls[c] = pos;
+        pos += cnt[j];
+    }
+}
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -268,14 +268,7 @@ __device__ __forceinline__ void tile_count_view(const View &v, int *s_grid, int 
     __syncthreads();
     for (int t = tid; t < ntiles; t += nt) atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u);
     __syncthreads();
-    if (tid == 0) {
-        uint32_t pos = 0;
-        for (int c = kWorkClasses - 1; c >= 0; c--) {
-            const uint32_t k = s_cls[c];
-            s_cls[c] = pos;
-            pos += k;
-        }
-    }
+    if (tid < 32) work_class_scan(s_cls);
     __syncthreads();
     for (int t = tid; t < ntiles; t += nt) v.tile_order[atomicAdd(&s_cls[work_class(v.tile_work[t])], 1u)] = (uint32_t)t;
 }
