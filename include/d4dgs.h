@@ -84,7 +84,8 @@ typedef struct {
 } d4dgs_camera;
 
 /* Rasteriser settings.  tile: 8, 16 or 32 pixels; batch: Gaussians staged
- * per shared-memory batch in the blend, 64, 128 or 256 (<= tile*tile);
+ * per shared-memory batch in the blend, 64, 128 or 256, or 512 at 32-px
+ * tiles;
  * bg: background colour added with the final transmittance; trim: 0 bins
  * each Gaussian into its whole tile rectangle, 1 cuts the rectangle's first
  * 8 columns to the tile rows its alpha >= 1/255 ellipse reaches (fewer

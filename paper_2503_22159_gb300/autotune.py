@@ -16,7 +16,7 @@ import os
 from pathlib import Path
 
 TILES = (8, 16, 32)
-BATCHES = (64, 128, 256)
+BATCHES = (64, 128, 256, 512)   # 512: 32-px tiles only
 TRIMS = (False, True)
 
 
@@ -68,6 +68,8 @@ def sweep(time_config, tiles=TILES, batches=BATCHES, trims=TRIMS):
     table, cfgs = {}, {}
     for t in tiles:
         for b in batches:
+            if b == 512 and t != 32:   # the library stages 512 at 32-px tiles only
+                continue
             for c in trims:
                 ms = time_config(t, b, c)
                 name = config_name(t, b, c)

@@ -32,7 +32,7 @@ bool valid_camera(const d4dgs_camera *c) {
 bool valid_config(const d4dgs_config *g) {
     if (!g) return false;
     if (g->tile != 8 && g->tile != 16 && g->tile != 32) return false;
-    if (g->batch != 64 && g->batch != 128 && g->batch != 256) return false;
+    if (g->batch != 64 && g->batch != 128 && g->batch != 256 && !(g->batch == 512 && g->tile == 32)) return false;
     if (g->trim != 0 && g->trim != 1) return false;
     if (g->colour_cache != 0 && g->colour_cache != 1) return false;
     if (g->binning < 0 || g->binning > 3) return false;

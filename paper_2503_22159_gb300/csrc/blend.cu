@@ -60,8 +60,9 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
     // one 128-byte record per staged Gaussian (one address for all of its loads):
     // [0] u, u, A, A  [1] B, B, C, C  [2] v, v, L, L  [3] r, r, g, g  [4] b, b
     // [5] flow u, u, v, v (FLOW)
-    __shared__ float4 s_rec[BATCH][8];
-    __shared__ uint32_t s_m[BATCH];  // blocks the Gaussian's alpha >= 1/255 ellipse reaches
+    extern __shared__ float4 s_dynb[];   // blend_smem(BATCH) bytes
+    float4 (*s_rec)[8] = reinterpret_cast<float4 (*)[8]>(s_dynb);
+    uint32_t *s_m = reinterpret_cast<uint32_t *>(s_dynb + BATCH * 8);   // blocks the Gaussian's alpha >= 1/255 ellipse reaches
     __shared__ int32_t s_item;
     __shared__ uint32_t s_stop;
     __shared__ float s_wsum[FwdWarps<TS>::value];   // per warp: list entries its pixels walked
@@ -341,27 +342,39 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
     }
 }
 
+// dynamic shared memory of a blend CTA: the staged records and block masks
+constexpr size_t blend_smem(int batch) { return (size_t)batch * (8 * 16 + 4); }
+
 template <int TS, int BATCH>
 cudaError_t launch_ts(char *ba, int total_tiles, bool persist, cudaStream_t st, int num_sms, float *out0,
                       unsigned long long *counts, bool flow) {
+    constexpr size_t smem = blend_smem(BATCH);
+    static bool attr = false;
+    if (!attr && smem > 48 * 1024) {   // above the default
+        for (const void *fn : {(const void *)blend_kernel<TS, BATCH, false, false, true>,
+                               (const void *)blend_kernel<TS, BATCH, true, true>, (const void *)blend_kernel<TS, BATCH, false, true>,
+                               (const void *)blend_kernel<TS, BATCH, true, false>, (const void *)blend_kernel<TS, BATCH, false, false>})
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    attr = true;
     if (flow)   // single frames only
-        return launch_chained(blend_kernel<TS, BATCH, false, false, true>, total_tiles, BlendShape<TS>::NT, 0, st, ba,
+        return launch_chained(blend_kernel<TS, BATCH, false, false, true>, total_tiles, BlendShape<TS>::NT, smem, st, ba,
                               out0, counts);
     auto go = [&](auto kernel) {
         static int occ = 0;   // per instantiation; queried once, before any graph capture uses it
-        if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BlendShape<TS>::NT, 0) != cudaSuccess ||
+        if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BlendShape<TS>::NT, smem) != cudaSuccess ||
                      occ < 1))
             occ = 1;
-        return launch_chained(kernel, occ * num_sms, BlendShape<TS>::NT, 0, st, ba, out0, counts);
+        return launch_chained(kernel, occ * num_sms, BlendShape<TS>::NT, smem, st, ba, out0, counts);
     };
     if (persist) {
         if (counts) return go(blend_kernel<TS, BATCH, true, true>);
         return go(blend_kernel<TS, BATCH, false, true>);
     } else if (counts) {
-        return launch_chained(blend_kernel<TS, BATCH, true, false>, total_tiles, BlendShape<TS>::NT, 0, st, ba, out0,
+        return launch_chained(blend_kernel<TS, BATCH, true, false>, total_tiles, BlendShape<TS>::NT, smem, st, ba, out0,
                               counts);
     } else {
-        return launch_chained(blend_kernel<TS, BATCH, false, false>, total_tiles, BlendShape<TS>::NT, 0, st, ba, out0,
+        return launch_chained(blend_kernel<TS, BATCH, false, false>, total_tiles, BlendShape<TS>::NT, smem, st, ba, out0,
                               counts);
     }
 }
@@ -381,7 +394,9 @@ cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t s
     switch (args.tile) {
         case 8: D4DGS_BATCHES(8)
         case 16: D4DGS_BATCHES(16)
-        case 32: D4DGS_BATCHES(32)
+        case 32:   // 32-px tiles also stage 512 Gaussians a batch
+            if (args.batch == 512) return launch_ts<32, 512>(batch_area, nt, persist, st, num_sms, out0, counts, flow);
+            D4DGS_BATCHES(32)
         default: return cudaErrorInvalidValue;
     }
 #undef D4DGS_BATCHES

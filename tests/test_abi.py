@@ -172,3 +172,16 @@ def test_product_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "orc_" not in src, f
+
+
+def test_staging_depth_512_only_at_32px_tiles(d4):
+    """The blend stages 64, 128 or 256 Gaussians a batch at any tile size and 512 at 32-px tiles."""
+    cam = synth.pinhole(640, 480)
+    lib = d4._abi.load()
+    for tile in (8, 16, 32):
+        for batch in (64, 128, 256, 512, 1024):
+            ok = batch in (64, 128, 256) or (batch == 512 and tile == 32)
+            n = lib.d4dgs_workspace_bytes(10, ctypes.byref(d4.camera_struct(cam)),
+                                          ctypes.byref(d4.config_struct(tile, batch)), 100)
+            assert (n > 0) == ok, (tile, batch)
+

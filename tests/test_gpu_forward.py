@@ -371,3 +371,16 @@ def test_render_host_async_two_slots_match_device_path():
         got[pending[j]] = slots[j]["out"].clone()
     for a, b in zip(got, refs):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("trim", [False, True])
+def test_staging_depth_512_renders_as_256(trim):
+    """32-px tiles also stage 512 Gaussians a batch: the walk, its stops and the image are the
+    ones a 256-deep staging gives, bit for bit."""
+    scene, cam, t = medium()
+    r256, _, a = gu.render(scene, cam, t, tile=32, batch=256, trim=trim)
+    r512, _, b = gu.render(scene, cam, t, tile=32, batch=512, trim=trim)
+    assert torch.equal(a, b)
+    px = cam.width * cam.height
+    for name in ("final_T", "n_contrib"):
+        assert torch.equal(r256.view(name, torch.int32, px, cam), r512.view(name, torch.int32, px, cam)), name
