@@ -1115,7 +1115,7 @@ def run_ours(args):
 
 def run_profile(args):
     """A short, fixed sequence for profiler captures: the workload's frames 150..154 at 32-px tiles,
-    staging depth 256 (the autotuner's choice), config binning --binning, each rendered (and, --profile backward, followed
+    staging depth --batch, config binning --binning, each rendered (and, --profile backward, followed
     by the backward with a seeded dL/dC); prints one line of device times."""
     import numpy as np
     import torch
@@ -1126,10 +1126,10 @@ def run_profile(args):
     w = workload(args.workload)
     dev = torch.device("cuda", 0)
     scene = d4.DeviceScene.from_host(w.scene, dev)
-    cfg = d4.config_struct(32, 256, binning=args.binning)
+    cfg = d4.config_struct(32, args.batch, binning=args.binning)
     frames = [w.frames[150 + k] for k in range(5)]
     cam0 = frames[0][0]
-    r = d4.Renderer(scene.n, cam0, tile=32, batch=256, device=dev, binning=args.binning)
+    r = d4.Renderer(scene.n, cam0, tile=32, batch=args.batch, device=dev, binning=args.binning)
     for cam, t in frames:
         r.render(scene, cam, t)
     out = torch.empty((cam0.height, cam0.width, 3), device=dev)
