@@ -52,9 +52,11 @@ struct FwdWarps {
 // grid, for batched and graph-captured launches); otherwise one CTA per tile.
 // FLOW: also composites the per-Gaussian screen flow into the view's flow
 // output (two channels, background 0) with the same weights.
-template <int TS, int BATCH, bool COUNT, bool PERSIST, bool FLOW = false>
+// PARAM: a launch of one view whose descriptor also travels as the kernel parameter v0.
+template <int TS, int BATCH, bool COUNT, bool PERSIST, bool FLOW = false, bool PARAM = false>
 __global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 24 : (TS == 16 ? 10 : 3))
-blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts) {
+blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts,
+             const __grid_constant__ View v0) {
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
     // one 128-byte record per staged Gaussian (one address for all of its loads):
@@ -68,8 +70,8 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
     __shared__ float s_wsum[FwdWarps<TS>::value];   // per warp: list entries its pixels walked
     grid_dependency_wait();
     uint32_t *bw = reinterpret_cast<uint32_t *>(ba);
-    const int nviews = (int)bw[kBaNViews];
-    const int total = (int)bw[kBaTotalTiles];
+    const int nviews = PARAM ? 1 : (int)bw[kBaNViews];
+    const int total = PARAM ? v0.ntiles : (int)bw[kBaTotalTiles];
     const int lane = (int)(threadIdx.x & 31u), warp = (int)(threadIdx.x >> 5);
     uint32_t n_eval = 0, n_blend = 0;
     unsigned long long n_work = 0;
@@ -89,7 +91,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
         int vi = 0;
         for (int u = 1; u < nviews; u++)
             if (view_of(ba, u).tile_base <= item) vi = u;
-        const View &v = view_of(ba, vi);
+        const View &v = PARAM ? v0 : view_of(ba, vi);
         int tile = item - v.tile_base;
         {   // heaviest tiles first (the order the binning derived from the previous frame's walked
             // entries: nearby frames load nearby tiles alike); kept in range whatever the buffer holds
@@ -347,35 +349,36 @@ constexpr size_t blend_smem(int batch) { return (size_t)batch * (8 * 16 + 4); }
 
 template <int TS, int BATCH>
 cudaError_t launch_ts(char *ba, int total_tiles, bool persist, cudaStream_t st, int num_sms, float *out0,
-                      unsigned long long *counts, bool flow) {
+                      unsigned long long *counts, bool flow, const View &v0) {
     constexpr size_t smem = blend_smem(BATCH);
     static bool attr = false;
     if (!attr && smem > 48 * 1024) {   // above the default
-        for (const void *fn : {(const void *)blend_kernel<TS, BATCH, false, false, true>,
+        for (const void *fn : {(const void *)blend_kernel<TS, BATCH, false, false, true, true>,
                                (const void *)blend_kernel<TS, BATCH, true, true>, (const void *)blend_kernel<TS, BATCH, false, true>,
-                               (const void *)blend_kernel<TS, BATCH, true, false>, (const void *)blend_kernel<TS, BATCH, false, false>})
+                               (const void *)blend_kernel<TS, BATCH, true, false, false, true>,
+                               (const void *)blend_kernel<TS, BATCH, false, false, false, true>})
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     attr = true;
     if (flow)   // single frames only
-        return launch_chained(blend_kernel<TS, BATCH, false, false, true>, total_tiles, BlendShape<TS>::NT, smem, st, ba,
-                              out0, counts);
+        return launch_chained(blend_kernel<TS, BATCH, false, false, true, true>, total_tiles, BlendShape<TS>::NT, smem, st,
+                              ba, out0, counts, v0);
     auto go = [&](auto kernel) {
         static int occ = 0;   // per instantiation; queried once, before any graph capture uses it
         if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BlendShape<TS>::NT, smem) != cudaSuccess ||
                      occ < 1))
             occ = 1;
-        return launch_chained(kernel, occ * num_sms, BlendShape<TS>::NT, smem, st, ba, out0, counts);
+        return launch_chained(kernel, occ * num_sms, BlendShape<TS>::NT, smem, st, ba, out0, counts, v0);
     };
     if (persist) {
         if (counts) return go(blend_kernel<TS, BATCH, true, true>);
         return go(blend_kernel<TS, BATCH, false, true>);
     } else if (counts) {
-        return launch_chained(blend_kernel<TS, BATCH, true, false>, total_tiles, BlendShape<TS>::NT, smem, st, ba, out0,
-                              counts);
+        return launch_chained(blend_kernel<TS, BATCH, true, false, false, true>, total_tiles, BlendShape<TS>::NT, smem, st,
+                              ba, out0, counts, v0);
     } else {
-        return launch_chained(blend_kernel<TS, BATCH, false, false>, total_tiles, BlendShape<TS>::NT, smem, st, ba, out0,
-                              counts);
+        return launch_chained(blend_kernel<TS, BATCH, false, false, false, true>, total_tiles, BlendShape<TS>::NT, smem, st,
+                              ba, out0, counts, v0);
     }
 }
 
@@ -387,15 +390,15 @@ cudaError_t launch_blend(const BatchArgs &args, char *batch_area, cudaStream_t s
     const int nt = args.total_tiles;
     const bool flow = args.nviews == 1 && args.v[0].out_flow != nullptr && !counts && !persist;
 #define D4DGS_BATCHES(TS)                                                                                    \
-    if (args.batch == 64) return launch_ts<TS, 64>(batch_area, nt, persist, st, num_sms, out0, counts, flow);   \
-    if (args.batch == 128) return launch_ts<TS, 128>(batch_area, nt, persist, st, num_sms, out0, counts, flow); \
-    if (args.batch == 256) return launch_ts<TS, 256>(batch_area, nt, persist, st, num_sms, out0, counts, flow); \
+    if (args.batch == 64) return launch_ts<TS, 64>(batch_area, nt, persist, st, num_sms, out0, counts, flow, args.v[0]);   \
+    if (args.batch == 128) return launch_ts<TS, 128>(batch_area, nt, persist, st, num_sms, out0, counts, flow, args.v[0]); \
+    if (args.batch == 256) return launch_ts<TS, 256>(batch_area, nt, persist, st, num_sms, out0, counts, flow, args.v[0]); \
     return cudaErrorInvalidValue;
     switch (args.tile) {
         case 8: D4DGS_BATCHES(8)
         case 16: D4DGS_BATCHES(16)
         case 32:   // 32-px tiles also stage 512 Gaussians a batch
-            if (args.batch == 512) return launch_ts<32, 512>(batch_area, nt, persist, st, num_sms, out0, counts, flow);
+            if (args.batch == 512) return launch_ts<32, 512>(batch_area, nt, persist, st, num_sms, out0, counts, flow, args.v[0]);
             D4DGS_BATCHES(32)
         default: return cudaErrorInvalidValue;
     }
