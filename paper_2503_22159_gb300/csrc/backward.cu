@@ -83,12 +83,11 @@ __device__ __forceinline__ float warp_sum8(const float (&x)[8], int lane) {
 template <int TS, int BATCH, bool FLOW = false>
 __global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 16 : (TS == 16 ? 8 : 3))
 blend_backward_kernel(const char *__restrict__ ba, const float *__restrict__ dl_drgb,
-                      const float *__restrict__ dl_dflow) {
+                      const float *__restrict__ dl_dflow, const __grid_constant__ View v) {
     grid_dependency_wait();
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
     constexpr int NA = FLOW ? 11 : 9;   // shared sums per staged Gaussian
-    const View &v = view_of(ba, 0);
     const uint32_t id_mask = v.packed ? (uint32_t)((1ull << v.id_bits) - 1ull) : 0xFFFFFFFFu;
     const uint32_t *ids = v.packed ? v.tkeys[v.tile_passes & 1] : v.tvals[v.tile_passes & 1];
     const float4 *rec = v.rec;
@@ -382,9 +381,8 @@ struct GradArgs {
 // ACC: add to the gradient arrays instead of overwriting them (several views of one step).
 template <int DEG, bool ACC>
 __global__ void __launch_bounds__(256)
-preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
+preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o, const __grid_constant__ View vw) {
     grid_dependency_wait();
-    const View &vw = view_of(ba, 0);
     const SceneArgs s{vw.means, vw.t_mean, vw.velocity, vw.log_scales, vw.log_t_scale, vw.quats, vw.opacity_logit,
                       vw.sh};
     const CamArgs &c = vw.cam;
@@ -617,7 +615,7 @@ preprocess_backward_kernel(const char *__restrict__ ba, GradArgs o) {
 // Block 0 orders the replay's tiles; the other blocks clear the per-Gaussian
 // 2D gradient sums (n4 float4) that the replay adds into.
 __global__ void __launch_bounds__(1024) backward_prologue_kernel(const char *__restrict__ ba, float4 *__restrict__ g2,
-                                                                 int64_t n4) {
+                                                                 int64_t n4, const __grid_constant__ View v) {
     grid_dependency_wait();
     if (blockIdx.x > 0) {
         const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
@@ -626,7 +624,6 @@ __global__ void __launch_bounds__(1024) backward_prologue_kernel(const char *__r
         return;
     }
     __shared__ uint32_t s_cls[kWorkClasses];
-    const View &v = view_of(ba, 0);
     const int T = v.ntiles, tid = threadIdx.x;
     for (int i = tid; i < kWorkClasses; i += 1024) s_cls[i] = 0u;
     __syncthreads();
@@ -644,7 +641,7 @@ constexpr size_t k7_smem(int batch, bool flow) {
 }
 
 template <int TS, int BATCH>
-void launch_bb(const char *ba, int ntiles, const float *dl, const float *dlf, cudaStream_t st) {
+void launch_bb(const char *ba, int ntiles, const float *dl, const float *dlf, cudaStream_t st, const View &v) {
     static bool attr = false;
     if (!attr) {   // above the 48 KB default
         cudaFuncSetAttribute(blend_backward_kernel<TS, BATCH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -655,19 +652,19 @@ void launch_bb(const char *ba, int ntiles, const float *dl, const float *dlf, cu
     }
     if (dlf)
         launch_chained(blend_backward_kernel<TS, BATCH, true>, ntiles, BlendShape<TS>::NT, k7_smem(BATCH, true), st, ba,
-                       dl, dlf);
+                       dl, dlf, v);
     else
         launch_chained(blend_backward_kernel<TS, BATCH, false>, ntiles, BlendShape<TS>::NT, k7_smem(BATCH, false), st,
-                       ba, dl, static_cast<const float *>(nullptr));
+                       ba, dl, static_cast<const float *>(nullptr), v);
 }
 
 template <bool ACC>
-void launch_k8(int deg, int blocks, const char *ba, const GradArgs &o, cudaStream_t st) {
+void launch_k8(int deg, int blocks, const char *ba, const GradArgs &o, cudaStream_t st, const View &v) {
     switch (deg) {
-        case 0: launch_chained(preprocess_backward_kernel<0, ACC>, blocks, 256, 0, st, ba, o); break;
-        case 1: launch_chained(preprocess_backward_kernel<1, ACC>, blocks, 256, 0, st, ba, o); break;
-        case 2: launch_chained(preprocess_backward_kernel<2, ACC>, blocks, 256, 0, st, ba, o); break;
-        default: launch_chained(preprocess_backward_kernel<3, ACC>, blocks, 256, 0, st, ba, o); break;
+        case 0: launch_chained(preprocess_backward_kernel<0, ACC>, blocks, 256, 0, st, ba, o, v); break;
+        case 1: launch_chained(preprocess_backward_kernel<1, ACC>, blocks, 256, 0, st, ba, o, v); break;
+        case 2: launch_chained(preprocess_backward_kernel<2, ACC>, blocks, 256, 0, st, ba, o, v); break;
+        default: launch_chained(preprocess_backward_kernel<3, ACC>, blocks, 256, 0, st, ba, o, v); break;
     }
 }
 
@@ -680,17 +677,17 @@ cudaError_t launch_backward(const BatchArgs &args, char *batch_area, const float
     // the replay's order from this frame's tile work, beside the clearing of the gradient sums; the
     // three launches chained like the forward's
     cudaError_t e = launch_chained(backward_prologue_kernel, 1 + 2 * num_sms, 1024, 0, st, (const char *)batch_area,
-                                   reinterpret_cast<float4 *>(v.grad2d), (int64_t)v.n * kG2 / 4);
+                                   reinterpret_cast<float4 *>(v.grad2d), (int64_t)v.n * kG2 / 4, v);
     if (e != cudaSuccess) return e;
     switch (args.tile) {   // the staging depth of the backward follows the tile size
-        case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
-        case 16: launch_bb<16, 128>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
-        default: launch_bb<32, 512>(batch_area, v.ntiles, dl_drgb, dl_dflow, st); break;
+        case 8: launch_bb<8, 64>(batch_area, v.ntiles, dl_drgb, dl_dflow, st, v); break;
+        case 16: launch_bb<16, 128>(batch_area, v.ntiles, dl_drgb, dl_dflow, st, v); break;
+        default: launch_bb<32, 512>(batch_area, v.ntiles, dl_drgb, dl_dflow, st, v); break;
     }
     GradArgs o{g.means, g.t_mean, g.velocity, g.log_scales, g.log_t_scale, g.quats, g.opacity_logit, g.sh};
     const int blocks = (v.n + 255) / 256;
-    if (accumulate) launch_k8<true>(v.sh_degree, blocks, batch_area, o, st);
-    else launch_k8<false>(v.sh_degree, blocks, batch_area, o, st);
+    if (accumulate) launch_k8<true>(v.sh_degree, blocks, batch_area, o, st, v);
+    else launch_k8<false>(v.sh_degree, blocks, batch_area, o, st, v);
     return cudaGetLastError();
 }
 
