@@ -81,10 +81,13 @@ def sweep(time_config, tiles=TILES, batches=BATCHES, trims=TRIMS):
     return cfgs[min(feasible, key=feasible.get)], table
 
 
-def time_frames(scene, frames, tile: int, batch: int, trim: bool = False, warmup: int = 2, reps: int = 1,
+def time_frames(scene, frames, tile: int, batch: int, trim: bool = False, warmup: int = 2, reps: int = 2,
                 device="cuda") -> float:
     """Mean ms per frame of d4dgs_render for one (tile, batch) over `frames` [(camera, t)];
-    None when a frame has more (tile, Gaussian) pairs than a workspace can hold at this tile size."""
+    None when a frame has more (tile, Gaussian) pairs than a workspace can hold at this tile size.
+    Each timed render follows an untimed render of the same frame, so the blend's tile order comes
+    from that frame's own work, as it does from its predecessor's in an animation (the probe frames
+    are far apart: timed one after another, each would take the order of an unrelated frame)."""
     import torch
 
     from . import D4DGS_ERR_CAPACITY, D4DGSError, Renderer, d4dgs_render
@@ -102,14 +105,17 @@ def time_frames(scene, frames, tile: int, batch: int, trim: bool = False, warmup
     for k in range(warmup):
         cam, t = frames[k % len(frames)]
         d4dgs_render(scene, cam, t, r.cfg, r.ws, out, stream)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    evs = []
     for _ in range(reps):
         for cam, t in frames:
             d4dgs_render(scene, cam, t, r.cfg, r.ws, out, stream)
-    ev1.record(stream)
-    ev1.synchronize()
-    return ev0.elapsed_time(ev1) / (reps * len(frames))
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            d4dgs_render(scene, cam, t, r.cfg, r.ws, out, stream)
+            ev1.record(stream)
+            evs.append((ev0, ev1))
+    evs[-1][1].synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / len(evs)
 
 
 def tune(scene, frames, cache: TuneCache | None = None, device="cuda", force: bool = False):
