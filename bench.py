@@ -55,7 +55,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=40)
+    p.add_argument("--e2e-steps", type=int, default=120)
+    p.add_argument("--e2e-slots", type=int, default=3,
+                   help="frames in flight in the end-to-end loop (each its own staging buffer, workspace, "
+                        "images and stream)")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-large", action="store_true", help="skip the 1M-Gaussian 2704x2028 line")
     p.add_argument("--no-training", action="store_true", help="skip the 4-view training step line")
@@ -1024,10 +1027,11 @@ def run_ours(args):
         host["sh_degree"] = w.scene.sh_degree
         h2d = sum(int(v.numel() * v.element_size()) for k, v in host.items() if k != "sh_degree")
         E = args.e2e_steps
-        # two slots (staging buffer, workspace, device image, pinned image, stream): while one
-        # frame's copies run, the other's kernels do
+        # args.e2e_slots slots (staging buffer, workspace, device image, pinned image, stream): while
+        # one frame's upload runs, the others' kernels and downloads do (a slot's upload, render and
+        # download take about twice a frame's render, and the uploads share one copy engine)
         slots = []
-        for j in range(2):
+        for j in range(args.e2e_slots):
             rj = r if j == 0 else d4.Renderer(n, cam0, tile=int(cfg.tile), batch=int(cfg.batch),
                                               key_capacity=r.key_capacity, device=dev, trim=bool(cfg.trim))
             slots.append(dict(r=rj, st=stream if j == 0 else torch.cuda.Stream(device=dev),
@@ -1039,7 +1043,7 @@ def run_ours(args):
 
         def host_frames(steps, first):
             for k in range(steps):
-                s_ = slots[k % 2]
+                s_ = slots[k % len(slots)]
                 s_["st"].synchronize()   # the slot's previous frame is in its pinned image
                 cam, t = w.frames[order[(first + k) % len(order)]]
                 d4.d4dgs_render_host_async(host, cam, t, cfg, s_["buf"], s_["r"].ws, s_["rgb"], s_["img"], s_["st"])
@@ -1061,7 +1065,7 @@ def run_ours(args):
             d4.d4dgs_render_host(host, cam, t, cfg, slots[0]["buf"], r.ws, out, slots[0]["img"], stream)
         ts = reduce_max(time.perf_counter() - t0, pg, dev)
         e2e = {"value": world * E / te, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "steps": E, "api": "d4dgs_render_host_async, two slots",
+               "steps": E, "api": f"d4dgs_render_host_async, {len(slots)} slots",
                "blocking": {"value": world * E / ts, "unit": "frames/s", "api": "d4dgs_render_host"}}
 
     groups_out = slicing_out = batched_out = None
