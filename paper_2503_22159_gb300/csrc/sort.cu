@@ -31,6 +31,7 @@
 // and the pass completes without hanging), and scatter through shared memory
 // so that global writes are runs of consecutive addresses.
 #include <map>
+#include <mutex>
 #include <utility>
 
 #include "d4dgs_internal.cuh"
@@ -1237,13 +1238,19 @@ constexpr size_t dir_emit_smem(int tile_cap) { return (size_t)20 * tile_cap; }
 
 namespace {
 
-// Resident CTAs per SM of `fn` at `threads` and `smem` (queried once per pair).
+// Resident CTAs per SM of `fn` at `threads` and `smem` (queried once per pair; callers may be
+// on several host threads).
 int occupancy_cached(const void *fn, int threads, size_t smem) {
+    static std::mutex mu;
     static std::map<std::pair<const void *, size_t>, int> cache;
     const auto key = std::make_pair(fn, smem);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
     const int b = occupancy_blocks(fn, threads, smem);
+    std::lock_guard<std::mutex> lock(mu);
     cache[key] = b;
     return b;
 }
