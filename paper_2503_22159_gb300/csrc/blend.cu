@@ -53,8 +53,9 @@ struct FwdWarps {
 // FLOW: also composites the per-Gaussian screen flow into the view's flow
 // output (two channels, background 0) with the same weights.
 // PARAM: a launch of one view whose descriptor also travels as the kernel parameter v0.
+// 32-px tiles: 4 CTAs per SM (64 registers) where the staging's shared memory allows, else 3.
 template <int TS, int BATCH, bool COUNT, bool PERSIST, bool FLOW = false, bool PARAM = false>
-__global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 24 : (TS == 16 ? 10 : 3))
+__global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 24 : (TS == 16 ? 10 : (BATCH <= 256 ? 4 : 3)))
 blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts,
              const __grid_constant__ View v0) {
     using S = BlendShape<TS>;
