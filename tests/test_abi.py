@@ -147,6 +147,10 @@ def test_launch_count(d4):
     # column emission and the row pass
     assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(1352, 1014), d4.config_struct(32, 256, binning=2)) == 10
     assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(1352, 1014), d4.config_struct(32, 256)) == 9
+    # rank lists: the rank emission and the list building instead of the column emission and the row pass
+    assert d4.d4dgs_launches_per_frame(300_000, synth.pinhole(1352, 1014), d4.config_struct(32, 256, binning=3)) == 9
+    # an empty scene: clear and blend around one launch of the tile counts
+    assert d4.d4dgs_launches_per_frame(0, synth.pinhole(1352, 1014), d4.config_struct(32, 512)) == 3
 
 
 def test_packing_decision(d4):
