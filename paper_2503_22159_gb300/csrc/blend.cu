@@ -53,19 +53,20 @@ struct FwdWarps {
 // FLOW: also composites the per-Gaussian screen flow into the view's flow
 // output (two channels, background 0) with the same weights.
 // PARAM: a launch of one view whose descriptor also travels as the kernel parameter v0.
-// 32-px tiles: 4 CTAs per SM (64 registers) where the staging's shared memory allows, else 3.
+// 32-px tiles: 4 CTAs per SM (64 registers; a 512-deep staging takes 51 KB).
 template <int TS, int BATCH, bool COUNT, bool PERSIST, bool FLOW = false, bool PARAM = false>
-__global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 24 : (TS == 16 ? 10 : (BATCH <= 256 ? 4 : 3)))
+__global__ void __launch_bounds__(BlendShape<TS>::NT, TS == 8 ? 24 : (TS == 16 ? 10 : 4))
 blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long *counts,
              const __grid_constant__ View v0) {
     using S = BlendShape<TS>;
     constexpr int PX = S::PX, NP = S::NP, BH = S::BH, NT = S::NT, BX = S::BX;
-    // one 128-byte record per staged Gaussian (one address for all of its loads):
+    // one 96-byte record per staged Gaussian (a 128-byte stride put the 16-byte staging stores of
+    // a warp's lanes in the same four banks; at 96 bytes they spread over all of them):
     // [0] u, u, A, A  [1] B, B, C, C  [2] v, v, L, L  [3] r, r, g, g  [4] b, b
     // [5] flow u, u, v, v (FLOW)
     extern __shared__ float4 s_dynb[];   // blend_smem(BATCH) bytes
-    float4 (*s_rec)[8] = reinterpret_cast<float4 (*)[8]>(s_dynb);
-    uint32_t *s_m = reinterpret_cast<uint32_t *>(s_dynb + BATCH * 8);   // blocks the Gaussian's alpha >= 1/255 ellipse reaches
+    float4 (*s_rec)[6] = reinterpret_cast<float4 (*)[6]>(s_dynb);
+    uint32_t *s_m = reinterpret_cast<uint32_t *>(s_dynb + BATCH * 6);   // blocks the Gaussian's alpha >= 1/255 ellipse reaches
     __shared__ int32_t s_item;
     __shared__ uint32_t s_stop;
     __shared__ float s_wsum[FwdWarps<TS>::value];   // per warp: list entries its pixels walked
@@ -346,7 +347,7 @@ blend_kernel(char *__restrict__ ba, float *__restrict__ out0, unsigned long long
 }
 
 // dynamic shared memory of a blend CTA: the staged records and block masks
-constexpr size_t blend_smem(int batch) { return (size_t)batch * (8 * 16 + 4); }
+constexpr size_t blend_smem(int batch) { return (size_t)batch * (6 * 16 + 4); }
 
 template <int TS, int BATCH>
 cudaError_t launch_ts(char *ba, int total_tiles, bool persist, cudaStream_t st, int num_sms, float *out0,
